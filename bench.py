@@ -1,0 +1,290 @@
+#!/usr/bin/env python3
+"""Benchmark: semi-implicit BDF2 VMS-LES Navier-Stokes steps per second on a ~1M-tetrahedron
+cylinder (Poiseuille set-up: R = 1 cm, L = 10 cm, blood rho = 1.06, mu = 0.035, parabolic inlet
+ramped to a 20 cm/s peak, zero-traction outlet, dt = 1e-3 s), synthetic seeded mesh.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a bounded sample
+of the same workload instead.  With --gpus N > 1 (torchrun), every rank runs its own
+independent simulation (replicas; the method does not exchange data between them).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+R_CM, L_CM, U_PEAK, RHO, MU, DT = 1.0, 10.0, 20.0, 1.06, 0.035, 1e-3
+RAMP = 0.05                      # s, sinusoidal ramp of the inflow (Section 2.2.1)
+L2_BYTES = 129 * 2 ** 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self):
+        self.samples, self.proc = [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        dev = os.environ.get("LOCAL_RANK", "0")
+        rows = [s for s in self.samples if s and s[0] == dev] or self.samples
+        sm = [float(s[1]) for s in rows if len(s) > 8 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in rows if len(s) > 8 and s[2].replace(".", "").isdigit()]
+        reasons = set()
+        for s in rows:
+            if len(s) > 8:
+                for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                   s[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def make_case(n_tets, seed=2):
+    from synthetic import cylinder
+
+    t0 = time.time()
+    m = cylinder(R_CM, L_CM, n_tets=n_tets, seed=seed)
+    return m, time.time() - t0
+
+
+def gpu_problem(L, m, precision):
+    Q = U_PEAK * math.pi * R_CM ** 2 / 2.0
+    bcs = [L.BC(tag=0, kind="noslip"),
+           L.BC(tag=1, kind="dirichlet", profile="parabolic", time="ramp", p=(0.0, Q, 0.0, RAMP), radius=R_CM),
+           L.BC(tag=2, kind="neumann", time="constant", p=(0.0,))]
+    opts = L.default_options(precision=precision, gmres_rtol=1e-8)
+    mesh = L.Mesh.from_synthetic(m)
+    prob = L.Problem(mesh, RHO, MU, DT, 2, bcs, [], opts)
+    return mesh, prob
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2304_12032_gb300 import build as B
+
+    B.build()
+    from paper_2304_12032_gb300 import lfx as L
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    m, tgen = make_case(args.tets, seed=2 + rank)
+    mesh, prob = gpu_problem(L, m, args.precision)
+    V = m.n_nodes
+    zero_u, zero_p = np.zeros((2, V, 3)), np.zeros((2, V))
+    st = L.State(prob, zero_u, zero_p, 0.0)
+    stream = torch.cuda.current_stream()
+    st.set_stream(stream)
+    info = mesh.info()
+    for _ in range(args.warmup):
+        st.step(allow_not_converged=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks()
+    clocks.start()
+    n0 = L.library().lfx_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(st.step(allow_not_converged=True))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = L.library().lfx_launch_count() - n0
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    # ---- end to end through the public API: host history in, solution out, every step
+    u_host, p_host = st.get()
+    hist_u = np.stack([u_host, u_host])
+    hist_p = np.stack([p_host, p_host])
+    t_now = stats[-1]["t"]
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for k in range(args.steps):
+        st.set(hist_u, hist_p, t_now)
+        st.step(allow_not_converged=True)
+        u_host, p_host = st.get()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - w0) * 1e3 / args.steps
+    h2d = 2 * V * 4 * 8
+    d2h = V * 4 * 8
+    # ---- dominant kernel: the coloured assembly kernel (live CUDA-event time, per launch)
+    asm_ms = sum(s["ms_assembly_kernels"] for s in stats) / len(stats)
+    n_asm = stats[0]["n_assembly_launches"]
+    T, nnzb = info["n_tets"], info["nnz_blocks"]
+    sv = 8 if args.precision == "fp64" else 4
+    alg_bytes = 16 * T + V * (3 * 8 + 8 * 8) + nnzb * 16 * sv + 4 * V * 8
+    peaks, src = _peaks()
+    achieved = alg_bytes / (asm_ms * 1e-3) / 1e9
+    roof = {"kernel": "assemble_color_kernel (all colours of one step)", "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+            "peak_source": src, "ms_per_step": round(asm_ms, 4), "launches_per_step": n_asm,
+            "algorithmic_bytes": int(alg_bytes)}
+    its = [s["iterations"] for s in stats]
+    value = world * args.steps / (ms * 1e-3)
+    line = {
+        "metric": "time steps/s at 1M P1 tets (BDF2 VMS-LES step: assembly + aSIMPLE-GMRES)",
+        "value": round(value, 3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic (seeded jittered-BCC Delaunay cylinder; no paper meshes available)",
+        "config": {"workload": f"poiseuille_cylinder_{T}_tets", "n_tets": T, "n_nodes": V, "nnz_blocks": nnzb,
+                   "n_colors": info["n_colors"], "precision": args.precision, "bdf_order": 2, "dt": DT,
+                   "gmres_rtol": 1e-8, "gmres_iterations_mean": statistics.mean(its),
+                   "gmres_iterations": its, "l2": "inputs larger than L2 (matrix %.0f MB > 129 MB)" %
+                   (nnzb * 16 * sv / 1e6), "mesh_gen_s": round(tgen, 1)},
+        "elements_per_s_assembly": round(T / (asm_ms * 1e-3), 1),
+        "phase_ms": {"assembly": round(statistics.mean(s["ms_assembly"] for s in stats), 3),
+                     "solve": round(statistics.mean(s["ms_solve"] for s in stats), 3)},
+        "roofline": roof,
+        "e2e": {"value": round(1e3 / e2e_ms * world, 3), "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample_tets)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def oracle_step_time(n_tets, steps=1):
+    """Times the FP64 oracle (C element loop + scipy assembly + aSIMPLE-FGMRES) on a cylinder of
+    n_tets from rest, returns (seconds per step, T)."""
+    import oracle as O
+
+    m, _ = make_case(n_tets, seed=2)
+    Q = U_PEAK * math.pi * R_CM ** 2 / 2.0
+    prob = O.Problem(O.Params(rho=RHO, mu=MU, dt=DT, bdf_order=2, stab=2),
+                     [O.BC(tag=0, kind="noslip"),
+                      O.BC(tag=1, kind="dirichlet", time="ramp", tparams={"g0": 0.0, "g1": Q, "t0": 0.0, "tL": RAMP},
+                           space="parabolic", radius=R_CM),
+                      O.BC(tag=2, kind="neumann", tparams={"value": 0.0})])
+    V = m.n_nodes
+    uh, ph = [np.zeros((V, 3))] * 2, [np.zeros(V)] * 2
+    solver = lambda A, b: O.fgmres(A, b, M=O.ASimple(A).apply, restart=40, tol=1e-8)[0]
+    t0 = time.perf_counter()
+    t = 0.0
+    for s in range(steps):
+        t += DT
+        stp = O.step(m, prob, uh, ph, t, solver=solver)
+        x = stp.x.reshape(-1, 4)
+        uh, ph = [x[:, :3].copy(), uh[0]], [x[:, 3].copy(), ph[0]]
+    return (time.perf_counter() - t0) / steps, m.n_tets
+
+
+def cpu_baseline(sample_tets):
+    sec, T = oracle_step_time(sample_tets, steps=1)
+    # scaled to the 1M-tet workload assuming cost linear in T (optimistic for the oracle: its
+    # Krylov iteration count grows with the mesh)
+    value = 1.0 / (sec * 1.0e6 / T)
+    return {"value": round(value, 5), "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"1 BDF2 step of the oracle on a {T}-tet cylinder of the same recipe, "
+                      f"{sec:.2f} s, scaled linearly to 1.0e6 tets"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.load_library()
+    for _ in range(args.warmup):
+        oracle_step_time(args.cpu_sample_tets, steps=1)
+    secs = [oracle_step_time(args.cpu_sample_tets, steps=1) for _ in range(args.steps)]
+    sec = statistics.mean(s for s, _ in secs)
+    T = secs[0][1]
+    value = 1.0 / (sec * 1.0e6 / T)
+    line = {"impl": "reference", "metric": "time steps/s at 1M P1 tets (BDF2 VMS-LES step: assembly + aSIMPLE-GMRES)",
+            "value": round(value, 5), "unit": "steps/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sec * 1e3 * 1.0e6 / T, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "poiseuille_cylinder_1M_tets (sampled)", "sample_tets": T},
+            "cpu_baseline": {"value": round(value, 5), "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} oracle steps on a {T}-tet cylinder, scaled linearly to 1e6 tets"},
+            "e2e": {"value": round(value, 5), "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--tets", type=int, default=1_000_000)
+    ap.add_argument("--cpu-sample-tets", type=int, default=40_000)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,260 @@
+/*
+ * lfx - one semi-implicit BDF time step of incompressible Navier-Stokes with P1-P1 elements,
+ * VMS-LES stabilisation and static resistive immersed surfaces, on one GPU (sm_103a).
+ *
+ * The operation is the fully discrete problem of Section 2.3, Eq.
+ * (fullydiscrete_ns_ale_riis_vmsles_quasistatic_unified), with the stabilisation terms of
+ * Eqs. (stabilization_form_SUPG), (stabilization_form_VMS), (stabilization_form_LES)
+ * (semi-implicit), the stabilisation parameters tau_M, tau_C of Section 2.3, the resistive term
+ * of Eq. (riis), the boundary conditions of Section 2.2 and the block linear solve of Section
+ * 2.4 (GMRES preconditioned by aSIMPLE, here with Jacobi/Chebyshev smoothing on the device).
+ *
+ * Conventions for every call:
+ *  - Return value: LFX_OK (0) or a negative lfx_status; lfx_last_error() then holds a message
+ *    for the calling thread.  No call aborts the process.
+ *  - Node numbering at the interface is the caller's; the library renumbers internally and
+ *    translates on input and output.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Handles are owned by the
+ *    caller and released with the matching *_destroy.  A state borrows its problem, a problem
+ *    borrows its mesh: destroy in reverse order.
+ *  - Calls on one state are not reentrant; distinct states may be stepped from one thread on
+ *    different streams.
+ *  - Units are the caller's (the library is unit-agnostic).
+ */
+#ifndef LFX_H
+#define LFX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lfx_status;
+enum {
+  LFX_OK = 0,
+  LFX_ERR_INVALID_ARG = -1,   /* null pointer, size out of range, unknown enum value         */
+  LFX_ERR_BAD_MESH = -2,      /* index out of range, zero-volume tetrahedron                 */
+  LFX_ERR_OOM = -3,           /* device or host allocation failed                            */
+  LFX_ERR_NOT_CONVERGED = -4, /* linear solve hit its iteration cap; the step was still taken */
+  LFX_ERR_NONFINITE = -5,     /* NaN/Inf detected in a residual norm                         */
+  LFX_ERR_CUDA = -6,          /* a CUDA runtime call failed                                  */
+  LFX_ERR_TIMEOUT = -7,       /* a bounded device-side wait gave up                          */
+  LFX_ERR_BUDGET = -8         /* serving: request does not fit the device-memory budget      */
+};
+
+/* Message of the last failed call on this thread ("" if none).  Valid until the next call. */
+const char *lfx_last_error(void);
+/* sizeof() of a public struct by name ("lfx_bc", "lfx_options", ...), -1 if unknown; lets a
+ * binding check its struct layouts without a GPU. */
+int64_t lfx_sizeof(const char *type_name);
+/* Total number of CUDA kernels this library has launched in the process (diagnostic counter,
+ * including kernels that returned early because a solve had already converged). */
+int64_t lfx_launch_count(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Mesh (Section 2.3: tetrahedral mesh T^h; Section 2.2: boundary subsets by tag)
+ * ------------------------------------------------------------------------------------------ */
+typedef struct lfx_mesh lfx_mesh;
+
+/* nodes [n_nodes][3] FP64; tets [n_tets][4] int32 (any orientation: negatively oriented
+ * tetrahedra are flipped and counted; zero volume -> LFX_ERR_BAD_MESH); bfaces [n_bfaces][3]
+ * int32 with boundary_tags [n_bfaces] (any orientation; outward normals are recomputed).
+ * Builds, once, on the host: the node and element renumbering (space-filling curve), the 4x4
+ * block-CSR pattern of the node graph, the element -> block-slot map and an element colouring
+ * such that no two elements of one colour share a node (atomic-free scatter).  Copies all
+ * inputs.  Needs no GPU: the device copies are made by the first lfx_problem_create. */
+lfx_status lfx_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tets,
+                           int64_t n_tets, const int32_t *bfaces, const int32_t *boundary_tags,
+                           int64_t n_bfaces, lfx_mesh **out);
+void lfx_mesh_destroy(lfx_mesh *mesh);
+
+typedef struct lfx_mesh_info {
+  int64_t n_nodes, n_tets, n_bfaces;
+  int64_t nnz_blocks;          /* 4x4 blocks in the pattern (diagonal included)              */
+  int32_t n_colors;            /* element colours                                            */
+  int32_t n_flipped;           /* tetrahedra whose orientation was fixed                     */
+  int32_t max_color_size, min_color_size;
+  int64_t n_bad_elements;      /* elements below the shape-quality threshold (FP64 geometry) */
+} lfx_mesh_info;
+lfx_status lfx_mesh_get_info(const lfx_mesh *mesh, lfx_mesh_info *info);
+
+/* Pattern in the caller's node numbering, for inspection and tests: row_ptr [n_nodes+1],
+ * col_idx [nnz_blocks] (sorted within each row).  Host buffers supplied by the caller. */
+lfx_status lfx_mesh_get_pattern(const lfx_mesh *mesh, int64_t *row_ptr, int32_t *col_idx);
+/* Element colours in the caller's element numbering [n_tets]. */
+lfx_status lfx_mesh_get_colors(const lfx_mesh *mesh, int32_t *colors);
+
+/* ------------------------------------------------------------------------------------------
+ * Problem: physics (Section 2.1), boundary conditions (Section 2.2), RIIS surfaces (Eq. riis),
+ * numerics (Sections 2.3-2.4)
+ * ------------------------------------------------------------------------------------------ */
+enum { LFX_TIME_CONSTANT = 0, LFX_TIME_PULSATILE = 1, LFX_TIME_RAMP = 2, LFX_TIME_FOURIER = 3 };
+#define LFX_MAX_FOURIER 16
+/* g(t) of Section 2.2.1.  p[]: constant {value}; pulsatile {g_min, g_max, period};
+ * ramp {g0, g1, t0, tL}; Fourier {period}: g = a[0] + sum_{k=1..K} a[k] cos(k w t) + b[k] sin(k w t),
+ * w = 2 pi / period, K = n_harmonics <= LFX_MAX_FOURIER. */
+typedef struct lfx_time_law {
+  int32_t kind;
+  int32_t n_harmonics;
+  double p[4];
+  double a[LFX_MAX_FOURIER + 1];
+  double b[LFX_MAX_FOURIER + 1];
+} lfx_time_law;
+
+enum { LFX_BC_NOSLIP = 0, LFX_BC_DIRICHLET = 1, LFX_BC_NODAL = 2, LFX_BC_NEUMANN = 3 };
+enum { LFX_PROFILE_UNIFORM = 0, LFX_PROFILE_PARABOLIC = 1, LFX_PROFILE_WOMERSLEY = 2 };
+/* One boundary condition on the faces carrying `tag`.
+ *  NOSLIP    u = 0 (fixed domain).
+ *  DIRICHLET u = theta g(t) s(x) (Section 2.2.1): s = -n (uniform, unit velocity),
+ *            s = -2 (R^2 - r^2)/(pi R^4) n (parabolic, unit flow rate, r = distance to the
+ *            barycentre of the tagged faces), or the Womersley profile of unit flow rate per
+ *            Fourier harmonic of g (needs time.kind == LFX_TIME_FOURIER).
+ *  NODAL     u given per node and per step by lfx_set_dirichlet_nodal.
+ *  NEUMANN   sigma n = -h(t) n (Eq. bcs-neumann), h = time law; h = 0 is the natural condition.
+ * Where tags meet: NOSLIP > DIRICHLET/NODAL > NEUMANN.  center/normal: if given_geometry is 0
+ * they are computed as the area-weighted barycentre and outward normal of the tagged faces. */
+typedef struct lfx_bc {
+  int32_t tag, kind, profile, given_geometry;
+  lfx_time_law time;
+  double theta, radius;
+  double center[3], normal[3];
+} lfx_bc;
+
+enum { LFX_RIIS_DISK = 0, LFX_RIIS_SDF_NODAL = 1 };
+/* Static resistive immersed surface (Eq. riis with u_ALE = u_Sigma = 0): resistance R, half
+ * thickness eps.  DISK: flat disk (center, unit normal, radius); its signed distance is the
+ * plane distance inside the rim and the signed distance to the rim circle outside.
+ * SDF_NODAL: signed distance given at the nodes (caller numbering), copied.  Inside an element
+ * the signed distance is the P1 interpolant of its nodal values. */
+typedef struct lfx_riis {
+  int32_t kind, pad;
+  double resistance, eps;
+  double center[3], normal[3], radius;
+  const double *sdf_nodal;
+} lfx_riis;
+
+enum { LFX_PREC_FP64 = 0, LFX_PREC_MIXED = 1 };
+enum { LFX_SMOOTH_JACOBI = 0, LFX_SMOOTH_CHEBYSHEV = 1 };
+enum { LFX_STAB_NONE = 0, LFX_STAB_SUPG_PSPG = 1, LFX_STAB_VMS_LES = 2 };
+enum { LFX_DIFF_GRAD_GRAD = 0, LFX_DIFF_SYMGRAD_GRAD = 1, LFX_DIFF_SYMGRAD_SYMGRAD = 2 };
+
+typedef struct lfx_options {
+  /* discretisation */
+  int32_t stab;                 /* LFX_STAB_*, default VMS-LES                                 */
+  int32_t diffusion;            /* LFX_DIFF_*, default grad-grad (Eq. diffusion-term)          */
+  double c_r;                   /* C_r in tau_M (not printed in the paper); default 30         */
+  double f[3];                  /* constant body force f; default 0                            */
+  int32_t pin_pressure_node;    /* caller node whose pressure is fixed (all-Dirichlet flows);
+                                   -1 = none.  Value per step: lfx_set_pressure_pin.           */
+  int32_t precision;            /* LFX_PREC_FP64 or LFX_PREC_MIXED                             */
+  /* linear solve: GMRES(restart) right-preconditioned by aSIMPLE */
+  int32_t gmres_restart;        /* default 40                                                  */
+  int32_t gmres_max_iters;      /* total Arnoldi steps cap; default 1000                       */
+  double gmres_rtol;            /* stop when ||b - A x|| <= rtol ||b||; default 1e-10         */
+  int32_t reorthogonalize;      /* classical Gram-Schmidt twice (1, default) or once (0)        */
+  /* aSIMPLE: velocity block F and Schur approximation S = C - D diag(F)^-1 G */
+  int32_t f_smoother, f_steps;  /* LFX_SMOOTH_*, steps; default Chebyshev, 3                   */
+  double f_omega, f_ratio;      /* Jacobi damping; Chebyshev lmax/lmin; default 0.7, 8         */
+  int32_t s_smoother, s_steps;  /* default Chebyshev, 6                                         */
+  double s_omega, s_ratio;      /* default 0.7, 30                                             */
+  int32_t n_power;              /* power-iteration steps for lmax; default 10                  */
+  /* mixed precision (LFX_PREC_MIXED) */
+  int32_t smoother_bf16;        /* store the preconditioner blocks in BF16 (FP32 arithmetic)   */
+  int32_t outer_restart;        /* FP64 flexible GMRES restart; default 8                       */
+  int32_t outer_max_iters;      /* default 40                                                   */
+  double inner_rtol;            /* FP32 inner GMRES tolerance per outer step; default 1e-3     */
+  int32_t inner_max_iters;      /* default 60                                                   */
+  double bad_element_quality;   /* elements with 6 sqrt2 |K| / e_rms^3 below this keep FP64
+                                   geometry in mixed assembly; default 0.1                       */
+  int32_t reserved[8];
+} lfx_options;
+void lfx_options_default(lfx_options *opt);
+
+typedef struct lfx_problem lfx_problem;
+/* rho, mu > 0 (Section 2.1.2), dt > 0, bdf_order 1..3 (Eq. bdf).  bcs [n_bcs], riis [n_riis]
+ * (n_riis <= 8) are copied; opt may be NULL for defaults.  Precomputes the Dirichlet profiles,
+ * the Neumann load vectors and the nodal signed distances, all resident on the device. */
+lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, double dt,
+                              int32_t bdf_order, const lfx_bc *bcs, int32_t n_bcs,
+                              const lfx_riis *riis, int32_t n_riis, const lfx_options *opt,
+                              lfx_problem **out);
+void lfx_problem_destroy(lfx_problem *problem);
+
+/* ------------------------------------------------------------------------------------------
+ * State: BDF history (u^n, ..., u^{n+1-sigma}; p likewise) resident on the device
+ * ------------------------------------------------------------------------------------------ */
+typedef struct lfx_state lfx_state;
+/* u_hist [bdf_order][n_nodes][3], p_hist [bdf_order][n_nodes] (level 0 = u^n), t0 = t^n.
+ * Host pointers, copied. */
+lfx_status lfx_state_create(lfx_problem *problem, const double *u_hist, const double *p_hist,
+                            double t0, lfx_state **out);
+void lfx_state_destroy(lfx_state *state);
+/* CUDA stream (cudaStream_t, NULL = legacy default stream) used by every later call on it. */
+lfx_status lfx_set_stream(lfx_state *state, void *cuda_stream);
+
+/* Per-step data for the next lfx_step: nodal Dirichlet values for one NODAL tag, u [n_nodes][3]
+ * (caller numbering, only the tag's nodes are read), host pointer, copied. */
+lfx_status lfx_set_dirichlet_nodal(lfx_state *state, int32_t tag, const double *u);
+/* Pressure value at the pinned node (options.pin_pressure_node) for the next step. */
+lfx_status lfx_set_pressure_pin(lfx_state *state, double value);
+
+typedef struct lfx_step_stats {
+  int32_t iterations;           /* Arnoldi steps (FP64 path) or inner steps summed (mixed)     */
+  int32_t outer_iterations;     /* outer FGMRES steps (mixed), 0 for FP64                      */
+  double rel_residual;          /* final ||b - A x|| / ||b|| (FP64)                            */
+  double t;                     /* time reached                                                */
+  float ms_assembly, ms_solve, ms_total;   /* device time per phase (CUDA events)              */
+  int32_t converged;
+  float ms_assembly_kernels;    /* the coloured assembly launches alone (CUDA events)          */
+  int32_t n_assembly_launches;  /* launches of the assembly kernel in this step (= colours)    */
+  int32_t reserved[5];
+} lfx_step_stats;
+
+/* One semi-implicit BDF step t^n -> t^{n+1}: BDF/EXT fields, coloured assembly of the
+ * linearised block system (FP64, or FP32 with FP64 geometry for badly shaped elements and FP64
+ * tau in mixed mode), Neumann and Dirichlet data, the preconditioned Krylov solve, history
+ * shift.  Returns LFX_ERR_NOT_CONVERGED after still advancing the state if the solve hit its
+ * cap; stats may be NULL. */
+lfx_status lfx_step(lfx_state *state, lfx_step_stats *stats);
+
+/* Replace the history (same layout as lfx_state_create) and the time; host pointers, copied
+ * on the state's stream before the call returns. */
+lfx_status lfx_state_set(lfx_state *state, const double *u_hist, const double *p_hist, double t);
+
+/* Copy the latest solution to the host in caller numbering: u [n_nodes][3], p [n_nodes]. */
+lfx_status lfx_state_get(const lfx_state *state, double *u, double *p);
+
+/* ------------------------------------------------------------------------------------------
+ * Building blocks of the step, exposed for parity tests (all act on the state's stream)
+ * ------------------------------------------------------------------------------------------ */
+/* Assemble the system of the next step (BDF/EXT + assembly + Neumann + Dirichlet) without
+ * solving; then copy it out: block values [nnz_blocks][4][4] in the order of
+ * lfx_mesh_get_pattern (caller numbering), rhs [n_nodes][4]. FP64 host buffers. */
+lfx_status lfx_debug_assemble(lfx_state *state, int32_t apply_bcs, double *blocks, double *rhs);
+/* y = A x with the last assembled matrix; x, y [n_nodes][4] FP64 host buffers, caller numbering. */
+lfx_status lfx_debug_spmv(lfx_state *state, const double *x, double *y);
+/* z = P^-1 r with the aSIMPLE preconditioner of the last assembled matrix (FP64 path);
+ * r, z [n_nodes][4] host buffers, caller numbering.  Also returns the two power-iteration
+ * estimates (lambda_max of diag(F)^-1 F and of diag(S)^-1 S, before the 1.1 safety factor). */
+lfx_status lfx_debug_precond(lfx_state *state, const double *r, double *z, double *lam_f,
+                             double *lam_s);
+/* Solve the last assembled system (after lfx_debug_assemble with BCs) from x0 = 0 with the
+ * configured Krylov method; x [n_nodes][4] host buffer. */
+lfx_status lfx_debug_solve(lfx_state *state, double *x, lfx_step_stats *stats);
+
+/* ------------------------------------------------------------------------------------------
+ * Device memory: optional allocator hook (e.g. a framework's caching allocator)
+ * ------------------------------------------------------------------------------------------ */
+typedef void *(*lfx_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lfx_free_fn)(void *ptr, void *ctx);
+/* Route every later device allocation through alloc/free (NULL, NULL restores cudaMalloc). */
+lfx_status lfx_set_allocator(lfx_alloc_fn alloc, lfx_free_fn free_fn, void *ctx);
+/* Device bytes held by a state together with its problem and mesh (for admission control). */
+lfx_status lfx_state_device_bytes(const lfx_state *state, int64_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LFX_H */

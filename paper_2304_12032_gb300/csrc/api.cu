@@ -1,0 +1,985 @@
+// C ABI of liblfx (declared in include/lfx.h): mesh / problem / state handles, boundary data
+// preprocessing (Section 2.2), one time step (Section 2.3 assembly + Section 2.4 solve), and
+// the parity/debug entry points.  Host code only; kernels live in assemble.cu and solver.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "lfx_internal.h"
+#include "solver.h"
+
+namespace lfx {
+
+// ------------------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+void set_error(const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+
+static std::atomic<int64_t> g_launches{0};
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------------------ allocator
+static lfx_alloc_fn g_alloc = nullptr;
+static lfx_free_fn g_free = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+void *dalloc(size_t bytes) {
+  void *p = nullptr;
+  if (g_alloc) {
+    p = g_alloc(bytes, g_alloc_ctx);
+    if (!p) set_error("device allocation of %zu bytes failed (user allocator)", bytes);
+    return p;
+  }
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return nullptr;
+  }
+  return p;
+}
+void dfree(void *p) {
+  if (!p) return;
+  if (g_free) g_free(p, g_alloc_ctx);
+  else cudaFree(p);
+}
+
+// ------------------------------------------------------------------------------ time laws
+// g(t) of Section 2.2.1
+static double time_law(const lfx_time_law &L, double t) {
+  switch (L.kind) {
+    case LFX_TIME_CONSTANT: return L.p[0];
+    case LFX_TIME_PULSATILE: return L.p[0] + (L.p[1] - L.p[0]) * 0.5 * (1.0 - std::cos(2.0 * M_PI * t / L.p[2]));
+    case LFX_TIME_RAMP:
+      if (t < L.p[2]) return L.p[0];
+      if (t < L.p[2] + L.p[3]) return L.p[0] + 0.5 * (L.p[1] - L.p[0]) * (1.0 - std::cos(M_PI * (t - L.p[2]) / L.p[3]));
+      return L.p[1];
+    case LFX_TIME_FOURIER: {
+      const double w = 2.0 * M_PI / L.p[0];
+      double g = L.a[0];
+      for (int k = 1; k <= L.n_harmonics; ++k) g += L.a[k] * std::cos(k * w * t) + L.b[k] * std::sin(k * w * t);
+      return g;
+    }
+  }
+  return 0.0;
+}
+
+}  // namespace lfx
+
+using namespace lfx;
+
+// ================================================================================ problem
+struct lfx_problem {
+  const lfx_mesh *mesh = nullptr;
+  PhysParams P{};
+  int bdf_order = 1;
+  double beta[3] = {0, 0, 0}, gamma[3] = {0, 0, 0};
+  lfx_options opt{};
+  std::vector<lfx_bc> bcs;
+  // Dirichlet data: g(d) = sum_h c[bc(d)][h] S[h][d] + nodal(d)  (internal node ids)
+  int H = 1;
+  std::vector<int32_t> dir_node, dir_bc;
+  std::vector<int32_t> dir_pos_of_node;   // [V] -> index into dir_node, -1 if free
+  DBuf d_dir_node, d_dir_bc, d_S;
+  // Neumann data: rhs(node) -= h(t) * vec(node) per Neumann BC
+  std::vector<int32_t> neu_node, neu_bc;
+  DBuf d_neu_node, d_neu_bc, d_neu_vec;
+  // RIIS nodal signed distances [n_riis][V]
+  DBuf d_phi;
+  DBuf d_bad;
+  int32_t pin_node = -1;   // internal
+  int64_t n_bad = 0;
+  size_t device_bytes() const {
+    return d_dir_node.bytes + d_dir_bc.bytes + d_S.bytes + d_neu_node.bytes + d_neu_bc.bytes +
+           d_neu_vec.bytes + d_phi.bytes + d_bad.bytes;
+  }
+};
+
+// ================================================================================ state
+struct lfx_state {
+  lfx_problem *pb = nullptr;
+  cudaStream_t stream = nullptr;
+  int sigma = 1;
+  DBuf hist[3];            // D4 [V]; level l = hist[(head + l) % sigma]
+  int head = 0;
+  DBuf xsol, ubdf, rhs, gdir, nodal;
+  DBuf vals64, vals32;
+  ASimple<double, double> pc64;
+  Gmres<double, double> gm64;
+  double t = 0.0, pin_value = 0.0;
+  bool assembled = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, ea0 = nullptr, ea1 = nullptr;
+  int n_asm_launch = 0;
+  ~lfx_state() {
+    if (ea0) cudaEventDestroy(ea0);
+    if (ea1) cudaEventDestroy(ea1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e2) cudaEventDestroy(e2);
+  }
+  D4 *level(int l) { return hist[(head + l) % sigma].as<D4>(); }
+  BsrView<double> view64() const {
+    const Mesh &m = pb->mesh->m;
+    return BsrView<double>{m.V, m.d_rowptr.as<int32_t>(), m.d_col.as<int32_t>(), m.d_diag.as<int32_t>(),
+                           m.d_trans.as<int32_t>(), vals64.as<double>()};
+  }
+};
+
+extern "C" {
+
+const char *lfx_last_error(void) { return g_err.c_str(); }
+
+int64_t lfx_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int64_t lfx_sizeof(const char *type_name) {
+  if (!type_name) return -1;
+  const std::string t(type_name);
+  if (t == "lfx_time_law") return sizeof(lfx_time_law);
+  if (t == "lfx_bc") return sizeof(lfx_bc);
+  if (t == "lfx_riis") return sizeof(lfx_riis);
+  if (t == "lfx_options") return sizeof(lfx_options);
+  if (t == "lfx_mesh_info") return sizeof(lfx_mesh_info);
+  if (t == "lfx_step_stats") return sizeof(lfx_step_stats);
+  return -1;
+}
+
+lfx_status lfx_set_allocator(lfx_alloc_fn alloc, lfx_free_fn free_fn, void *ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) {
+    set_error("lfx_set_allocator: give both functions or neither");
+    return LFX_ERR_INVALID_ARG;
+  }
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return LFX_OK;
+}
+
+// ---------------------------------------------------------------------------------- mesh
+lfx_status lfx_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                           const int32_t *bfaces, const int32_t *boundary_tags, int64_t n_bfaces,
+                           lfx_mesh **out) {
+  clear_error();
+  if (!out) {
+    set_error("lfx_mesh_create: out is NULL");
+    return LFX_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  std::unique_ptr<lfx_mesh> h(new (std::nothrow) lfx_mesh);
+  if (!h) return LFX_ERR_OOM;
+  LFX_TRY(build_mesh(nodes, n_nodes, tets, n_tets, bfaces, boundary_tags, n_bfaces, h->m));
+  *out = h.release();
+  return LFX_OK;
+}
+
+void lfx_mesh_destroy(lfx_mesh *mesh) { delete mesh; }
+
+lfx_status lfx_mesh_get_info(const lfx_mesh *mesh, lfx_mesh_info *info) {
+  if (!mesh || !info) {
+    set_error("lfx_mesh_get_info: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = mesh->m;
+  info->n_nodes = m.V;
+  info->n_tets = m.T;
+  info->n_bfaces = m.F;
+  info->nnz_blocks = m.nnzb;
+  info->n_colors = (int32_t)m.color_off.size() - 1;
+  info->n_flipped = m.n_flipped;
+  int mx = 0, mn = INT32_MAX;
+  for (size_t c = 0; c + 1 < m.color_off.size(); ++c) {
+    int s = m.color_off[c + 1] - m.color_off[c];
+    mx = std::max(mx, s);
+    mn = std::min(mn, s);
+  }
+  info->max_color_size = mx;
+  info->min_color_size = mn;
+  info->n_bad_elements = 0;
+  return LFX_OK;
+}
+
+// user-ordered pattern: row i (caller), columns = caller ids of the internal row, sorted
+static void user_pattern(const Mesh &m, std::vector<int64_t> &rp, std::vector<int32_t> &ci,
+                         std::vector<int64_t> &internal_block) {
+  rp.assign(m.V + 1, 0);
+  ci.resize(m.nnzb);
+  internal_block.resize(m.nnzb);
+  for (int64_t i = 0; i < m.V; ++i) {
+    const int32_t r = m.node_new[i];
+    rp[i + 1] = rp[i] + (m.row_ptr[r + 1] - m.row_ptr[r]);
+  }
+  std::vector<std::pair<int32_t, int64_t>> tmp;
+  for (int64_t i = 0; i < m.V; ++i) {
+    const int32_t r = m.node_new[i];
+    tmp.clear();
+    for (int32_t k = m.row_ptr[r]; k < m.row_ptr[r + 1]; ++k) tmp.push_back({m.node_old[m.col_idx[k]], k});
+    std::sort(tmp.begin(), tmp.end());
+    for (size_t q = 0; q < tmp.size(); ++q) {
+      ci[rp[i] + q] = tmp[q].first;
+      internal_block[rp[i] + q] = tmp[q].second;
+    }
+  }
+}
+
+lfx_status lfx_mesh_get_pattern(const lfx_mesh *mesh, int64_t *row_ptr, int32_t *col_idx) {
+  if (!mesh || !row_ptr || !col_idx) {
+    set_error("lfx_mesh_get_pattern: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  std::vector<int64_t> rp, ib;
+  std::vector<int32_t> ci;
+  user_pattern(mesh->m, rp, ci, ib);
+  std::copy(rp.begin(), rp.end(), row_ptr);
+  std::copy(ci.begin(), ci.end(), col_idx);
+  return LFX_OK;
+}
+
+lfx_status lfx_mesh_get_colors(const lfx_mesh *mesh, int32_t *colors) {
+  if (!mesh || !colors) {
+    set_error("lfx_mesh_get_colors: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = mesh->m;
+  for (size_t c = 0; c + 1 < m.color_off.size(); ++c)
+    for (int32_t i = m.color_off[c]; i < m.color_off[c + 1]; ++i) colors[m.elem_old[i]] = (int32_t)c;
+  return LFX_OK;
+}
+
+// ------------------------------------------------------------------------------- problem
+void lfx_options_default(lfx_options *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->stab = LFX_STAB_VMS_LES;
+  o->diffusion = LFX_DIFF_GRAD_GRAD;
+  o->c_r = 30.0;
+  o->pin_pressure_node = -1;
+  o->precision = LFX_PREC_FP64;
+  o->gmres_restart = 40;
+  o->gmres_max_iters = 1000;
+  o->gmres_rtol = 1e-10;
+  o->reorthogonalize = 1;
+  o->f_smoother = LFX_SMOOTH_CHEBYSHEV;
+  o->f_steps = 3;
+  o->f_omega = 0.7;
+  o->f_ratio = 8.0;
+  o->s_smoother = LFX_SMOOTH_CHEBYSHEV;
+  o->s_steps = 6;
+  o->s_omega = 0.7;
+  o->s_ratio = 30.0;
+  o->n_power = 10;
+  o->smoother_bf16 = 0;
+  o->outer_restart = 8;
+  o->outer_max_iters = 40;
+  o->inner_rtol = 1e-3;
+  o->inner_max_iters = 60;
+  o->bad_element_quality = 0.1;
+}
+
+// barycentre, unit outward normal, area of the faces carrying `tag` (area weighted)
+static bool tag_geometry(const Mesh &m, int tag, double c[3], double n[3], double *area) {
+  double A = 0, cs[3] = {0, 0, 0}, ns[3] = {0, 0, 0};
+  for (int64_t f = 0; f < m.F; ++f) {
+    if (m.btags[f] != tag) continue;
+    const double *a = &m.xyz[3 * (int64_t)m.bfaces[3 * f]], *b = &m.xyz[3 * (int64_t)m.bfaces[3 * f + 1]],
+                 *d = &m.xyz[3 * (int64_t)m.bfaces[3 * f + 2]];
+    double u[3], v[3], cr[3];
+    for (int k = 0; k < 3; ++k) {
+      u[k] = b[k] - a[k];
+      v[k] = d[k] - a[k];
+    }
+    cr[0] = u[1] * v[2] - u[2] * v[1];
+    cr[1] = u[2] * v[0] - u[0] * v[2];
+    cr[2] = u[0] * v[1] - u[1] * v[0];
+    const double ar = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    A += ar;
+    for (int k = 0; k < 3; ++k) {
+      cs[k] += ar * (a[k] + b[k] + d[k]) / 3.0;
+      ns[k] += cr[k];
+    }
+  }
+  if (A <= 0) return false;
+  const double nn = std::sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+  for (int k = 0; k < 3; ++k) {
+    c[k] = cs[k] / A;
+    n[k] = ns[k] / nn;
+  }
+  if (area) *area = A;
+  return true;
+}
+
+// Womersley unit-flow-rate profile for harmonic k (omega_k = k w), radius R, nu = mu/rho:
+// W_k(r) = [1 - J0(i^{3/2} a r/R) / J0(i^{3/2} a)] / Q_k, a = R sqrt(omega_k / nu), Q_k its flux.
+static std::complex<double> bessel_j0(std::complex<double> z) {
+  std::complex<double> term(1.0, 0.0), sum(1.0, 0.0);
+  const std::complex<double> q = -0.25 * z * z;
+  for (int m = 1; m < 400; ++m) {
+    term *= q / double(m * m);
+    sum += term;
+    if (std::abs(term) < 1e-17 * std::abs(sum)) break;
+  }
+  return sum;
+}
+static std::complex<double> bessel_j1(std::complex<double> z) {
+  std::complex<double> term = 0.5 * z, sum = term;
+  const std::complex<double> q = -0.25 * z * z;
+  for (int m = 1; m < 400; ++m) {
+    term *= q / double(m * (m + 1));
+    sum += term;
+    if (std::abs(term) < 1e-17 * std::abs(sum)) break;
+  }
+  return sum;
+}
+
+lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, double dt, int32_t bdf_order,
+                              const lfx_bc *bcs, int32_t n_bcs, const lfx_riis *riis, int32_t n_riis,
+                              const lfx_options *opt, lfx_problem **out) {
+  clear_error();
+  if (!mesh || !out || !(rho > 0) || !(mu > 0) || !(dt > 0) || bdf_order < 1 || bdf_order > 3 ||
+      n_bcs < 0 || (n_bcs > 0 && !bcs) || n_riis < 0 || n_riis > kMaxRiis || (n_riis > 0 && !riis)) {
+    set_error("lfx_problem_create: invalid argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  std::unique_ptr<lfx_problem> pb(new (std::nothrow) lfx_problem);
+  if (!pb) return LFX_ERR_OOM;
+  const Mesh &m = mesh->m;
+  if (!m.uploaded) {
+    // device copies are made on first use, so that mesh set-up itself needs no GPU
+    Mesh &mm = const_cast<lfx_mesh *>(mesh)->m;
+    LFX_TRY(upload_mesh(mm));
+    mm.uploaded = true;
+  }
+  pb->mesh = mesh;
+  if (opt) pb->opt = *opt;
+  else lfx_options_default(&pb->opt);
+  lfx_options &o = pb->opt;
+  if (o.stab < 0 || o.stab > 2 || o.diffusion < 0 || o.diffusion > 2 || o.gmres_restart < 1 ||
+      o.gmres_restart > kMaxRestart || o.f_steps < 1 || o.f_steps > kMaxSmooth || o.s_steps < 1 ||
+      o.s_steps > kMaxSmooth || o.precision < 0 || o.precision > 1 || o.n_power < 1) {
+    set_error("lfx_problem_create: option out of range (restart <= %d, smoothing steps <= %d)", kMaxRestart,
+              kMaxSmooth);
+    return LFX_ERR_INVALID_ARG;
+  }
+  // physics (Section 2.1.2, Eq. bdf)
+  PhysParams &P = pb->P;
+  P.rho = rho;
+  P.mu = mu;
+  P.dt = dt;
+  pb->bdf_order = bdf_order;
+  static const double alph[3] = {1.0, 1.5, 11.0 / 6.0};
+  static const double bet[3][3] = {{1.0, 0, 0}, {2.0, -0.5, 0}, {3.0, -1.5, 1.0 / 3.0}};
+  static const double gam[3][3] = {{1.0, 0, 0}, {2.0, -1.0, 0}, {3.0, -3.0, 1.0}};
+  P.alpha = alph[bdf_order - 1];
+  P.sigma = (double)bdf_order;
+  for (int k = 0; k < 3; ++k) {
+    pb->beta[k] = bet[bdf_order - 1][k];
+    pb->gamma[k] = gam[bdf_order - 1][k];
+  }
+  P.c_r = o.c_r;
+  for (int k = 0; k < 3; ++k) P.f[k] = o.f[k];
+  P.stab = o.stab;
+  P.diffusion = o.diffusion;
+  P.n_riis = n_riis;
+  for (int k = 0; k < n_riis; ++k) {
+    if (!(riis[k].resistance >= 0) || !(riis[k].eps > 0) ||
+        (riis[k].kind == LFX_RIIS_SDF_NODAL && !riis[k].sdf_nodal) || riis[k].kind < 0 || riis[k].kind > 1) {
+      set_error("lfx_problem_create: invalid RIIS surface %d", k);
+      return LFX_ERR_INVALID_ARG;
+    }
+    P.riis_r[k] = riis[k].resistance;
+    P.riis_eps[k] = riis[k].eps;
+  }
+  pb->bcs.assign(bcs, bcs + n_bcs);
+  const int64_t V = m.V;
+
+  // ---- Dirichlet nodes and their BC (precedence: no-slip > Dirichlet/nodal)
+  std::vector<int> pri(V, 0), owner(V, -1);
+  for (int b = 0; b < n_bcs; ++b) {
+    const lfx_bc &bc = bcs[b];
+    if (bc.kind < 0 || bc.kind > 3 || bc.profile < 0 || bc.profile > 2) {
+      set_error("lfx_problem_create: invalid boundary condition %d", b);
+      return LFX_ERR_INVALID_ARG;
+    }
+    if (bc.kind == LFX_BC_DIRICHLET && bc.profile == LFX_PROFILE_WOMERSLEY && bc.time.kind != LFX_TIME_FOURIER) {
+      set_error("lfx_problem_create: the Womersley profile needs a Fourier time law (Section 2.2.1)");
+      return LFX_ERR_INVALID_ARG;
+    }
+    if (bc.time.n_harmonics < 0 || bc.time.n_harmonics > LFX_MAX_FOURIER) {
+      set_error("lfx_problem_create: too many Fourier harmonics");
+      return LFX_ERR_INVALID_ARG;
+    }
+    if (bc.kind == LFX_BC_NEUMANN) continue;
+    const int p = bc.kind == LFX_BC_NOSLIP ? 3 : 2;
+    for (int64_t f = 0; f < m.F; ++f) {
+      if (m.btags[f] != bc.tag) continue;
+      for (int k = 0; k < 3; ++k) {
+        const int32_t nd = m.bfaces[3 * f + k];
+        if (p > pri[nd]) {
+          pri[nd] = p;
+          owner[nd] = b;
+        }
+      }
+    }
+  }
+  int H = 1;
+  for (int b = 0; b < n_bcs; ++b)
+    if (bcs[b].kind == LFX_BC_DIRICHLET && bcs[b].profile == LFX_PROFILE_WOMERSLEY)
+      H = std::max(H, 1 + 2 * bcs[b].time.n_harmonics);
+  pb->H = H;
+  if ((int64_t)n_bcs * (H + 1) > kMaxDirCoef) {
+    set_error("lfx_problem_create: too many boundary-condition terms");
+    return LFX_ERR_INVALID_ARG;
+  }
+  pb->dir_pos_of_node.assign(V, -1);
+  for (int64_t i = 0; i < V; ++i)
+    if (owner[i] >= 0) {
+      pb->dir_pos_of_node[i] = (int32_t)pb->dir_node.size();
+      pb->dir_node.push_back((int32_t)i);
+      pb->dir_bc.push_back(owner[i]);
+    }
+  const int64_t nd = (int64_t)pb->dir_node.size();
+  std::vector<double> S((size_t)H * nd * 3, 0.0);
+  for (int b = 0; b < n_bcs; ++b) {
+    const lfx_bc &bc = bcs[b];
+    if (bc.kind != LFX_BC_DIRICHLET) continue;
+    double c[3], n[3];
+    if (bc.given_geometry) {
+      const double nn = std::sqrt(bc.normal[0] * bc.normal[0] + bc.normal[1] * bc.normal[1] + bc.normal[2] * bc.normal[2]);
+      for (int k = 0; k < 3; ++k) {
+        c[k] = bc.center[k];
+        n[k] = bc.normal[k] / nn;
+      }
+    } else if (!tag_geometry(m, bc.tag, c, n, nullptr)) {
+      set_error("lfx_problem_create: no boundary faces carry tag %d", bc.tag);
+      return LFX_ERR_INVALID_ARG;
+    }
+    const double R = bc.radius;
+    for (int64_t d = 0; d < nd; ++d) {
+      if (pb->dir_bc[d] != b) continue;
+      const double *x = &m.xyz[3 * (int64_t)pb->dir_node[d]];
+      double r2 = 0.0;
+      for (int k = 0; k < 3; ++k) r2 += (x[k] - c[k]) * (x[k] - c[k]);
+      if (bc.profile == LFX_PROFILE_UNIFORM) {
+        for (int k = 0; k < 3; ++k) S[((size_t)0 * nd + d) * 3 + k] = -n[k];
+      } else if (bc.profile == LFX_PROFILE_PARABOLIC) {
+        const double s = -2.0 * (R * R - r2) / (M_PI * R * R * R * R);
+        for (int k = 0; k < 3; ++k) S[((size_t)0 * nd + d) * 3 + k] = s * n[k];
+      } else {
+        // Womersley: harmonic 0 is the parabolic unit-flux profile; harmonic k >= 1 contributes
+        // Re[(a_k - i b_k) W_k(r) e^{i k w t}] with W_k of unit flux (stored as Re W_k, Im W_k).
+        const double s0 = -2.0 * (R * R - r2) / (M_PI * R * R * R * R);
+        for (int k = 0; k < 3; ++k) S[((size_t)0 * nd + d) * 3 + k] = s0 * n[k];
+        const double w = 2.0 * M_PI / bc.time.p[0], nu = mu / rho;
+        const double r = std::sqrt(r2);
+        const std::complex<double> i32 = std::exp(std::complex<double>(0.0, 0.75 * M_PI));  // i^{3/2}
+        for (int h = 1; h <= bc.time.n_harmonics; ++h) {
+          const double a = R * std::sqrt(h * w / nu);
+          const std::complex<double> z = i32 * a;
+          const std::complex<double> j0 = bessel_j0(z), j1 = bessel_j1(z);
+          // velocity shape 1 - J0(z r/R)/J0(z); its flux over the disk: pi R^2 (1 - 2 J1(z)/(z J0(z)))
+          const std::complex<double> shape = 1.0 - bessel_j0(z * (r / R)) / j0;
+          const std::complex<double> flux = M_PI * R * R * (1.0 - 2.0 * j1 / (z * j0));
+          const std::complex<double> W = shape / flux;
+          for (int k = 0; k < 3; ++k) {
+            S[((size_t)(2 * h - 1) * nd + d) * 3 + k] = -W.real() * n[k];
+            S[((size_t)(2 * h) * nd + d) * 3 + k] = -W.imag() * n[k];
+          }
+        }
+      }
+    }
+  }
+  LFX_TRY(pb->d_dir_node.alloc(sizeof(int32_t) * nd));
+  LFX_TRY(pb->d_dir_bc.alloc(sizeof(int32_t) * nd));
+  LFX_TRY(pb->d_S.alloc(sizeof(double) * S.size()));
+  if (nd) {
+    LFX_CUDA_TRY(cudaMemcpy(pb->d_dir_node.p, pb->dir_node.data(), sizeof(int32_t) * nd, cudaMemcpyHostToDevice));
+    LFX_CUDA_TRY(cudaMemcpy(pb->d_dir_bc.p, pb->dir_bc.data(), sizeof(int32_t) * nd, cudaMemcpyHostToDevice));
+    LFX_CUDA_TRY(cudaMemcpy(pb->d_S.p, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice));
+  }
+
+  // ---- Neumann load vectors: sum over the tag's faces of A_f n_f / 3 at each face vertex
+  {
+    std::vector<std::vector<double>> acc(n_bcs);
+    std::vector<double> vec;
+    for (int b = 0; b < n_bcs; ++b) {
+      if (bcs[b].kind != LFX_BC_NEUMANN) continue;
+      std::vector<double> nv((size_t)V * 3, 0.0);
+      std::vector<char> hit(V, 0);
+      for (int64_t f = 0; f < m.F; ++f) {
+        if (m.btags[f] != bcs[b].tag) continue;
+        const int32_t *fv = &m.bfaces[3 * f];
+        const double *a = &m.xyz[3 * (int64_t)fv[0]], *bb = &m.xyz[3 * (int64_t)fv[1]], *c = &m.xyz[3 * (int64_t)fv[2]];
+        double u[3], v[3], cr[3];
+        for (int k = 0; k < 3; ++k) {
+          u[k] = bb[k] - a[k];
+          v[k] = c[k] - a[k];
+        }
+        cr[0] = u[1] * v[2] - u[2] * v[1];
+        cr[1] = u[2] * v[0] - u[0] * v[2];
+        cr[2] = u[0] * v[1] - u[1] * v[0];
+        for (int q = 0; q < 3; ++q) {
+          hit[fv[q]] = 1;
+          for (int k = 0; k < 3; ++k) nv[3 * (int64_t)fv[q] + k] += 0.5 * cr[k] / 3.0;
+        }
+      }
+      for (int64_t i = 0; i < V; ++i)
+        if (hit[i]) {
+          pb->neu_node.push_back((int32_t)i);
+          pb->neu_bc.push_back(b);
+          for (int k = 0; k < 3; ++k) vec.push_back(nv[3 * i + k]);
+        }
+    }
+    const int64_t nn = (int64_t)pb->neu_node.size();
+    LFX_TRY(pb->d_neu_node.alloc(sizeof(int32_t) * nn));
+    LFX_TRY(pb->d_neu_bc.alloc(sizeof(int32_t) * nn));
+    LFX_TRY(pb->d_neu_vec.alloc(sizeof(double) * 3 * nn));
+    if (nn) {
+      LFX_CUDA_TRY(cudaMemcpy(pb->d_neu_node.p, pb->neu_node.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice));
+      LFX_CUDA_TRY(cudaMemcpy(pb->d_neu_bc.p, pb->neu_bc.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice));
+      LFX_CUDA_TRY(cudaMemcpy(pb->d_neu_vec.p, vec.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice));
+    }
+  }
+
+  // ---- RIIS nodal signed distances (internal numbering)
+  {
+    std::vector<double> phi((size_t)std::max(1, n_riis) * V, 0.0);
+    for (int k = 0; k < n_riis; ++k) {
+      const lfx_riis &s = riis[k];
+      for (int64_t i = 0; i < V; ++i) {
+        double val;
+        if (s.kind == LFX_RIIS_SDF_NODAL) {
+          val = s.sdf_nodal[m.node_old[i]];
+        } else {
+          const double *x = &m.xyz[3 * i];
+          const double nn = std::sqrt(s.normal[0] * s.normal[0] + s.normal[1] * s.normal[1] + s.normal[2] * s.normal[2]);
+          double d[3], h = 0.0;
+          for (int q = 0; q < 3; ++q) {
+            d[q] = x[q] - s.center[q];
+            h += d[q] * s.normal[q] / nn;
+          }
+          double rad2 = 0.0;
+          for (int q = 0; q < 3; ++q) {
+            const double t = d[q] - h * s.normal[q] / nn;
+            rad2 += t * t;
+          }
+          const double rad = std::sqrt(rad2);
+          double dist = std::fabs(h);
+          if (rad > s.radius) dist = std::hypot(rad - s.radius, h);
+          val = h >= 0 ? dist : -dist;
+        }
+        phi[(size_t)k * V + i] = val;
+      }
+    }
+    LFX_TRY(pb->d_phi.alloc(sizeof(double) * phi.size()));
+    LFX_CUDA_TRY(cudaMemcpy(pb->d_phi.p, phi.data(), sizeof(double) * phi.size(), cudaMemcpyHostToDevice));
+  }
+
+  // ---- elements that keep FP64 geometry in mixed assembly
+  {
+    std::vector<uint8_t> bad(m.T, 0);
+    for (int64_t e = 0; e < m.T; ++e)
+      if (m.quality[e] < o.bad_element_quality) {
+        bad[e] = 1;
+        ++pb->n_bad;
+      }
+    LFX_TRY(pb->d_bad.alloc(m.T));
+    LFX_CUDA_TRY(cudaMemcpy(pb->d_bad.p, bad.data(), m.T, cudaMemcpyHostToDevice));
+  }
+  if (o.pin_pressure_node >= 0) {
+    if (o.pin_pressure_node >= V) {
+      set_error("lfx_problem_create: pin_pressure_node out of range");
+      return LFX_ERR_INVALID_ARG;
+    }
+    pb->pin_node = m.node_new[o.pin_pressure_node];
+  }
+  *out = pb.release();
+  return LFX_OK;
+}
+
+void lfx_problem_destroy(lfx_problem *problem) { delete problem; }
+
+// --------------------------------------------------------------------------------- state
+static lfx_status upload_node_field(const Mesh &m, const double *u /*[V][3]*/, const double *p /*[V]*/, D4 *dst,
+                                    cudaStream_t st) {
+  std::vector<D4> h(m.V);
+  for (int64_t i = 0; i < m.V; ++i) {
+    const int64_t o = m.node_old[i];
+    h[i] = D4{u[3 * o], u[3 * o + 1], u[3 * o + 2], p[o]};
+  }
+  LFX_CUDA_TRY(cudaMemcpyAsync(dst, h.data(), sizeof(D4) * m.V, cudaMemcpyHostToDevice, st));
+  LFX_CUDA_TRY(cudaStreamSynchronize(st));
+  return LFX_OK;
+}
+
+extern "C" lfx_status lfx_state_set(lfx_state *s, const double *u_hist, const double *p_hist, double t) {
+  clear_error();
+  if (!s || !u_hist || !p_hist) {
+    set_error("lfx_state_set: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = s->pb->mesh->m;
+  for (int l = 0; l < s->sigma; ++l)
+    LFX_TRY(upload_node_field(m, u_hist + (size_t)l * 3 * m.V, p_hist + (size_t)l * m.V, s->level(l), s->stream));
+  s->t = t;
+  s->assembled = false;
+  return LFX_OK;
+}
+
+lfx_status lfx_state_create(lfx_problem *pb, const double *u_hist, const double *p_hist, double t0,
+                            lfx_state **out) {
+  clear_error();
+  if (!pb || !u_hist || !p_hist || !out) {
+    set_error("lfx_state_create: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  std::unique_ptr<lfx_state> s(new (std::nothrow) lfx_state);
+  if (!s) return LFX_ERR_OOM;
+  const Mesh &m = pb->mesh->m;
+  const int64_t V = m.V;
+  s->pb = pb;
+  s->sigma = pb->bdf_order;
+  s->t = t0;
+  for (int l = 0; l < s->sigma; ++l) {
+    LFX_TRY(s->hist[l].alloc(sizeof(D4) * V));
+    LFX_TRY(upload_node_field(m, u_hist + (size_t)l * 3 * V, p_hist + (size_t)l * V, s->hist[l].as<D4>(), 0));
+  }
+  LFX_TRY(s->xsol.alloc(sizeof(D4) * V));
+  LFX_TRY(s->ubdf.alloc(sizeof(D4) * V));
+  LFX_TRY(s->rhs.alloc(sizeof(D4) * V));
+  const int64_t nd = (int64_t)pb->dir_node.size();
+  LFX_TRY(s->gdir.alloc(sizeof(D4) * std::max<int64_t>(nd, 1)));
+  LFX_TRY(s->nodal.alloc(sizeof(double) * 3 * std::max<int64_t>(nd, 1)));
+  LFX_CUDA_TRY(cudaMemset(s->nodal.p, 0, s->nodal.bytes));
+  const lfx_options &o = pb->opt;
+  LFX_TRY(s->vals64.alloc(sizeof(double) * 16 * m.nnzb));
+  SmootherConfig cfg;
+  cfg.f_kind = o.f_smoother;
+  cfg.f_steps = o.f_steps;
+  cfg.f_omega = o.f_omega;
+  cfg.f_ratio = o.f_ratio;
+  cfg.s_kind = o.s_smoother;
+  cfg.s_steps = o.s_steps;
+  cfg.s_omega = o.s_omega;
+  cfg.s_ratio = o.s_ratio;
+  cfg.n_power = o.n_power;
+  LFX_TRY(s->pc64.init(V, cfg));
+  LFX_TRY(s->gm64.init(V, o.gmres_restart));
+  LFX_CUDA_TRY(cudaEventCreate(&s->e0));
+  LFX_CUDA_TRY(cudaEventCreate(&s->e1));
+  LFX_CUDA_TRY(cudaEventCreate(&s->e2));
+  LFX_CUDA_TRY(cudaEventCreate(&s->ea0));
+  LFX_CUDA_TRY(cudaEventCreate(&s->ea1));
+  *out = s.release();
+  return LFX_OK;
+}
+
+void lfx_state_destroy(lfx_state *state) { delete state; }
+
+lfx_status lfx_set_stream(lfx_state *s, void *stream) {
+  if (!s) {
+    set_error("lfx_set_stream: NULL state");
+    return LFX_ERR_INVALID_ARG;
+  }
+  s->stream = (cudaStream_t)stream;
+  return LFX_OK;
+}
+
+lfx_status lfx_set_dirichlet_nodal(lfx_state *s, int32_t tag, const double *u) {
+  if (!s || !u) {
+    set_error("lfx_set_dirichlet_nodal: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const lfx_problem *pb = s->pb;
+  const Mesh &m = pb->mesh->m;
+  int found = -1;
+  for (size_t b = 0; b < pb->bcs.size(); ++b)
+    if (pb->bcs[b].tag == tag && pb->bcs[b].kind == LFX_BC_NODAL) found = (int)b;
+  if (found < 0) {
+    set_error("lfx_set_dirichlet_nodal: no NODAL boundary condition on tag %d", tag);
+    return LFX_ERR_INVALID_ARG;
+  }
+  const int64_t nd = (int64_t)pb->dir_node.size();
+  std::vector<double> h(3 * nd);
+  LFX_CUDA_TRY(cudaMemcpy(h.data(), s->nodal.p, sizeof(double) * 3 * nd, cudaMemcpyDeviceToHost));
+  for (int64_t d = 0; d < nd; ++d) {
+    if (pb->dir_bc[d] != found) continue;
+    const int64_t o = m.node_old[pb->dir_node[d]];
+    for (int k = 0; k < 3; ++k) h[3 * d + k] = u[3 * o + k];
+  }
+  LFX_CUDA_TRY(cudaMemcpy(s->nodal.p, h.data(), sizeof(double) * 3 * nd, cudaMemcpyHostToDevice));
+  return LFX_OK;
+}
+
+lfx_status lfx_set_pressure_pin(lfx_state *s, double value) {
+  if (!s) {
+    set_error("lfx_set_pressure_pin: NULL state");
+    return LFX_ERR_INVALID_ARG;
+  }
+  s->pin_value = value;
+  return LFX_OK;
+}
+
+lfx_status lfx_state_device_bytes(const lfx_state *s, int64_t *bytes) {
+  if (!s || !bytes) {
+    set_error("lfx_state_device_bytes: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  size_t b = s->pb->mesh->m.device_bytes() + s->pb->device_bytes() + s->xsol.bytes + s->ubdf.bytes +
+             s->rhs.bytes + s->gdir.bytes + s->nodal.bytes + s->vals64.bytes + s->vals32.bytes +
+             s->pc64.device_bytes() + s->gm64.device_bytes();
+  for (int l = 0; l < 3; ++l) b += s->hist[l].bytes;
+  *bytes = (int64_t)b;
+  return LFX_OK;
+}
+
+// Assembly of the system for t^{n+1} = t + dt into vals64 / rhs, x0 = extrapolation.
+static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
+  lfx_problem *pb = s->pb;
+  const Mesh &m = pb->mesh->m;
+  cudaStream_t st = s->stream;
+  const double t1 = s->t + pb->P.dt;
+  const int sg = s->sigma;
+  LFX_TRY(launch_bdf(st, m.V, sg, s->level(0), sg > 1 ? s->level(1) : nullptr, sg > 2 ? s->level(2) : nullptr,
+                     pb->beta, pb->gamma, s->xsol.as<D4>(), s->ubdf.as<D4>()));
+  LFX_CUDA_TRY(cudaMemsetAsync(s->vals64.p, 0, s->vals64.bytes, st));
+  LFX_CUDA_TRY(cudaMemsetAsync(s->rhs.p, 0, s->rhs.bytes, st));
+  AssembleArgs A;
+  A.conn = m.d_conn.as<int4>();
+  A.slot = m.d_slot.as<int32_t>();
+  A.xyz = m.d_xyz.as<D4>();
+  A.xext = s->xsol.as<D4>();
+  A.ubdf = s->ubdf.as<D4>();
+  A.phi_riis = pb->d_phi.as<double>();
+  A.bad = nullptr;
+  A.rhs = s->rhs.as<double>();
+  A.n_nodes = m.V;
+  LFX_CUDA_TRY(cudaEventRecord(s->ea0, st));
+  LFX_TRY((launch_assemble<double, double>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
+                                           s->vals64.as<double>())));
+  LFX_CUDA_TRY(cudaEventRecord(s->ea1, st));
+  s->n_asm_launch = (int)m.color_off.size() - 1;
+  // boundary data at t^{n+1}
+  DirCoef C;
+  memset(&C, 0, sizeof(C));
+  const int nb = (int)pb->bcs.size();
+  for (int b = 0; b < nb; ++b)
+    if (pb->bcs[b].kind == LFX_BC_NEUMANN) C.c[b] = time_law(pb->bcs[b].time, t1);
+  LFX_TRY(launch_neumann(st, (int64_t)pb->neu_node.size(), pb->d_neu_node.as<int32_t>(), pb->d_neu_bc.as<int32_t>(),
+                         pb->d_neu_vec.as<double>(), C, s->rhs.as<double>()));
+  if (!apply_bcs) return LFX_OK;
+  memset(&C, 0, sizeof(C));
+  const int H = pb->H;
+  for (int b = 0; b < nb; ++b) {
+    const lfx_bc &bc = pb->bcs[b];
+    if (bc.kind == LFX_BC_NODAL) {
+      C.c[nb * H + b] = 1.0;
+    } else if (bc.kind == LFX_BC_DIRICHLET) {
+      if (bc.profile == LFX_PROFILE_WOMERSLEY) {
+        const lfx_time_law &L = bc.time;
+        const double w = 2.0 * M_PI / L.p[0];
+        C.c[b * H + 0] = bc.theta * L.a[0];
+        for (int h = 1; h <= L.n_harmonics; ++h) {
+          // Re[(a - i b) W e^{i h w t}] = (a cos + b sin) Re W + (b cos - a sin) Im W
+          const double cw = std::cos(h * w * t1), sw = std::sin(h * w * t1);
+          C.c[b * H + 2 * h - 1] = bc.theta * (L.a[h] * cw + L.b[h] * sw);
+          C.c[b * H + 2 * h] = bc.theta * (L.b[h] * cw - L.a[h] * sw);
+        }
+      } else {
+        C.c[b * H + 0] = bc.theta * time_law(bc.time, t1);
+      }
+    }
+  }
+  const int64_t nd = (int64_t)pb->dir_node.size();
+  LFX_TRY(launch_dirichlet_values(st, nd, H, pb->d_dir_bc.as<int32_t>(), pb->d_S.as<double>(), C,
+                                  s->nodal.as<double>(), nb, s->gdir.as<D4>()));
+  LFX_TRY(launch_apply_dirichlet<double>(st, nd, pb->d_dir_node.as<int32_t>(), s->gdir.as<D4>(), pb->pin_node,
+                                         s->pin_value, m.d_rowptr.as<int32_t>(), m.d_diag.as<int32_t>(),
+                                         s->vals64.as<double>(), s->rhs.as<double>(), s->xsol.as<double>()));
+  return LFX_OK;
+}
+
+lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
+  clear_error();
+  if (!s) {
+    set_error("lfx_step: NULL state");
+    return LFX_ERR_INVALID_ARG;
+  }
+  lfx_problem *pb = s->pb;
+  const lfx_options &o = pb->opt;
+  cudaStream_t st = s->stream;
+  LFX_CUDA_TRY(cudaEventRecord(s->e0, st));
+  LFX_TRY(assemble_system(s, true));
+  LFX_CUDA_TRY(cudaEventRecord(s->e1, st));
+  const BsrView<double> A = s->view64();
+  LFX_TRY(s->pc64.setup(st, A));
+  int its = 0;
+  double rel = 0.0;
+  lfx_status rc = s->gm64.solve(st, A, s->pc64, s->rhs.as<double>(), s->xsol.as<double>(), o.gmres_rtol,
+                                o.gmres_max_iters, o.reorthogonalize != 0, &its, &rel);
+  if (rc != LFX_OK && rc != LFX_ERR_NOT_CONVERGED) return rc;
+  LFX_CUDA_TRY(cudaEventRecord(s->e2, st));
+  // history shift: the solution becomes level 0
+  const int oldest = (s->head + s->sigma - 1) % s->sigma;
+  std::swap(s->hist[oldest].p, s->xsol.p);
+  std::swap(s->hist[oldest].bytes, s->xsol.bytes);
+  s->head = oldest;
+  s->t += pb->P.dt;
+  s->assembled = false;
+  LFX_CUDA_TRY(cudaEventSynchronize(s->e2));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations = its;
+    stats->rel_residual = rel;
+    stats->t = s->t;
+    cudaEventElapsedTime(&stats->ms_assembly, s->e0, s->e1);
+    cudaEventElapsedTime(&stats->ms_solve, s->e1, s->e2);
+    cudaEventElapsedTime(&stats->ms_total, s->e0, s->e2);
+    cudaEventElapsedTime(&stats->ms_assembly_kernels, s->ea0, s->ea1);
+    stats->n_assembly_launches = s->n_asm_launch;
+    stats->converged = rc == LFX_OK;
+  }
+  return rc;
+}
+
+lfx_status lfx_state_get(const lfx_state *s, double *u, double *p) {
+  if (!s || !u || !p) {
+    set_error("lfx_state_get: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = s->pb->mesh->m;
+  std::vector<D4> h(m.V);
+  LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  LFX_CUDA_TRY(cudaMemcpy(h.data(), s->hist[s->head].p, sizeof(D4) * m.V, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < m.V; ++i) {
+    const int64_t o = m.node_old[i];
+    u[3 * o] = h[i].x;
+    u[3 * o + 1] = h[i].y;
+    u[3 * o + 2] = h[i].z;
+    p[o] = h[i].w;
+  }
+  return LFX_OK;
+}
+
+// ------------------------------------------------------------------------------- debug API
+static lfx_status vec_to_device(const Mesh &m, const double *x /*[V][4] caller*/, double *dst, cudaStream_t st) {
+  std::vector<D4> h(m.V);
+  for (int64_t i = 0; i < m.V; ++i) {
+    const int64_t o = m.node_old[i];
+    h[i] = D4{x[4 * o], x[4 * o + 1], x[4 * o + 2], x[4 * o + 3]};
+  }
+  LFX_CUDA_TRY(cudaMemcpyAsync(dst, h.data(), sizeof(D4) * m.V, cudaMemcpyHostToDevice, st));
+  LFX_CUDA_TRY(cudaStreamSynchronize(st));
+  return LFX_OK;
+}
+static lfx_status vec_to_host(const Mesh &m, const double *src, double *x, cudaStream_t st) {
+  std::vector<D4> h(m.V);
+  LFX_CUDA_TRY(cudaMemcpyAsync(h.data(), src, sizeof(D4) * m.V, cudaMemcpyDeviceToHost, st));
+  LFX_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int64_t i = 0; i < m.V; ++i) {
+    const int64_t o = m.node_old[i];
+    x[4 * o] = h[i].x;
+    x[4 * o + 1] = h[i].y;
+    x[4 * o + 2] = h[i].z;
+    x[4 * o + 3] = h[i].w;
+  }
+  return LFX_OK;
+}
+
+lfx_status lfx_debug_assemble(lfx_state *s, int32_t apply_bcs, double *blocks, double *rhs) {
+  clear_error();
+  if (!s || !blocks || !rhs) {
+    set_error("lfx_debug_assemble: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = s->pb->mesh->m;
+  LFX_TRY(assemble_system(s, apply_bcs != 0));
+  s->assembled = true;
+  std::vector<double> v(16 * (size_t)m.nnzb);
+  LFX_CUDA_TRY(cudaMemcpyAsync(v.data(), s->vals64.p, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, s->stream));
+  LFX_TRY(vec_to_host(m, s->rhs.as<double>(), rhs, s->stream));
+  std::vector<int64_t> rp, ib;
+  std::vector<int32_t> ci;
+  user_pattern(m, rp, ci, ib);
+  for (int64_t q = 0; q < m.nnzb; ++q) memcpy(blocks + 16 * q, v.data() + 16 * ib[q], 16 * sizeof(double));
+  return LFX_OK;
+}
+
+lfx_status lfx_debug_spmv(lfx_state *s, const double *x, double *y) {
+  clear_error();
+  if (!s || !x || !y || !s->assembled) {
+    set_error("lfx_debug_spmv: NULL argument or no assembled matrix");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = s->pb->mesh->m;
+  DBuf dx, dy;
+  LFX_TRY(dx.alloc(sizeof(D4) * m.V));
+  LFX_TRY(dy.alloc(sizeof(D4) * m.V));
+  LFX_TRY(vec_to_device(m, x, dx.as<double>(), s->stream));
+  LFX_TRY((launch_spmv<double, double>(s->stream, s->view64(), dx.as<double>(), nullptr, dy.as<double>(), 0,
+                                       nullptr, nullptr)));
+  return vec_to_host(m, dy.as<double>(), y, s->stream);
+}
+
+lfx_status lfx_debug_precond(lfx_state *s, const double *r, double *z, double *lam_f, double *lam_s) {
+  clear_error();
+  if (!s || !r || !z || !s->assembled) {
+    set_error("lfx_debug_precond: NULL argument or no assembled matrix");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = s->pb->mesh->m;
+  DBuf dr, dz;
+  LFX_TRY(dr.alloc(sizeof(D4) * m.V));
+  LFX_TRY(dz.alloc(sizeof(D4) * m.V));
+  LFX_TRY(vec_to_device(m, r, dr.as<double>(), s->stream));
+  const BsrView<double> A = s->view64();
+  LFX_TRY(s->pc64.setup(s->stream, A));
+  LFX_TRY(s->pc64.apply(s->stream, A, dr.as<double>(), dz.as<double>(), nullptr));
+  LFX_TRY(vec_to_host(m, dz.as<double>(), z, s->stream));
+  return s->pc64.lambdas(lam_f, lam_s);
+}
+
+lfx_status lfx_debug_solve(lfx_state *s, double *x, lfx_step_stats *stats) {
+  clear_error();
+  if (!s || !x || !s->assembled) {
+    set_error("lfx_debug_solve: NULL argument or no assembled matrix");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = s->pb->mesh->m;
+  const lfx_options &o = s->pb->opt;
+  DBuf dx;
+  LFX_TRY(dx.alloc(sizeof(D4) * m.V));
+  LFX_CUDA_TRY(cudaMemsetAsync(dx.p, 0, dx.bytes, s->stream));
+  const BsrView<double> A = s->view64();
+  LFX_TRY(s->pc64.setup(s->stream, A));
+  int its = 0;
+  double rel = 0;
+  lfx_status rc = s->gm64.solve(s->stream, A, s->pc64, s->rhs.as<double>(), dx.as<double>(), o.gmres_rtol,
+                                o.gmres_max_iters, o.reorthogonalize != 0, &its, &rel);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations = its;
+    stats->rel_residual = rel;
+    stats->converged = rc == LFX_OK;
+  }
+  LFX_TRY(vec_to_host(m, dx.as<double>(), x, s->stream));
+  return rc;
+}
+
+}  // extern "C"

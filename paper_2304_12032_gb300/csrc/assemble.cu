@@ -1,0 +1,504 @@
+// Per-element, per-quadrature-point assembly of the linearised block system of Section 2.3,
+// Eq. (fullydiscrete_ns_ale_riis_vmsles_quasistatic_unified), with the SUPG-PSPG, VMS and
+// semi-implicit LES terms (Eqs. stabilization_form_*), tau_M / tau_C (Section 2.3), and the
+// resistive term of Eq. (riis); plus the BDF/EXT fields (Eq. bdf) and the boundary data of
+// Section 2.2.
+//
+// Layout: 4 unknowns per node interleaved (u_x, u_y, u_z, p); matrix in 4x4 block CSR, each
+// block 16 values row-major (row = test component, column = trial component).  Elements of one
+// colour share no node, so one launch per colour updates disjoint blocks without atomics.
+//
+// One CTA of 128 threads works on 32 elements at a time:
+//   phase 1: 4 threads per element, thread q evaluates quadrature point q (geometry, u*, tau_M,
+//            tau_C, the LES vector tau_M r_M(u^EXT, p^EXT), ...) into shared memory;
+//   phase 2: 16 threads per element, thread (a, b) forms block (a, b) and right-hand-side entry
+//            (a, b) and adds them into global memory (read-modify-write of 128 B / 64 B).
+#include <cuda_runtime.h>
+
+#include "lfx_internal.h"
+#include "kernels.h"
+
+namespace lfx {
+
+namespace {
+
+constexpr int kCta = 128;
+constexpr int kElems = 32;          // elements per CTA pass
+constexpr double kQA = 0.58541019662496845446;   // (5 + 3 sqrt5) / 20
+constexpr double kQB = 0.13819660112501051518;   // (5 - sqrt5) / 20
+
+template <class R>
+struct ElemShared {
+  R gphi[kElems][12];      // grad phi_a, a = 0..3
+  R w[kElems];             // |K| / 4 (quadrature weight)
+  R cs[kElems][4];         // rho alpha / dt + sum_k (R_k/eps_k) delta_k at each qp
+  R tm[kElems][4];         // tau_M
+  R tc[kElems][4];         // tau_C
+  R adv[kElems][4][4];     // [q][a] = u*(x_q) . grad phi_a
+  R z[kElems][4][3];       // rho tau_M (u* - tau_M r_M^EXT) (VMS + LES), 0 without VMS-LES
+  R m[kElems][4][3];       // rho u^BDF / dt + f
+};
+
+__device__ __forceinline__ double delta_fn(double phi, double eps) {
+  // smoothed Dirac delta of Section 2.1.2
+  if (fabs(phi) > eps) return 0.0;
+  return (1.0 + cos(3.14159265358979323846 * phi / eps)) / (2.0 * eps);
+}
+
+// Geometry of one tetrahedron in precision G: grad phi_a = J^-T grad_ref phi_a, the metric
+// tensor G = J^-T J^-1 (as its 9 entries), g = J^-T 1, |K| = det J / 6.
+template <class G>
+__device__ __forceinline__ void tet_geometry(const D4 *x, G gp[12], G Gm[9], G gv[3], G &vol) {
+  G J[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const D4 xc = x[c + 1];
+    J[0][c] = (G)(xc.x - x[0].x);
+    J[1][c] = (G)(xc.y - x[0].y);
+    J[2][c] = (G)(xc.z - x[0].z);
+  }
+  G c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  G c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  G c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  G det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  G id = G(1) / det;
+  // inverse: Ji[r][c]
+  G Ji[3][3];
+  Ji[0][0] = c00 * id;
+  Ji[1][0] = c01 * id;
+  Ji[2][0] = c02 * id;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+  // grad phi_1..3 = rows of J^-1 transposed: (grad phi_a)_k = Ji[a-1][k]; phi_0 = -(sum)
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gp[3 + k] = Ji[0][k];
+    gp[6 + k] = Ji[1][k];
+    gp[9 + k] = Ji[2][k];
+    gp[k] = -(Ji[0][k] + Ji[1][k] + Ji[2][k]);
+    gv[k] = Ji[0][k] + Ji[1][k] + Ji[2][k];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int l = 0; l < 3; ++l) Gm[3 * k + l] = Ji[0][k] * Ji[0][l] + Ji[1][k] * Ji[1][l] + Ji[2][k] * Ji[2][l];
+  vol = det / G(6);
+}
+
+// Phase 1 for one (element, quadrature point).  R = precision of the element arithmetic;
+// tau_M and tau_C are always evaluated in FP64.
+template <class R>
+__device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, int q, int le,
+                         ElemShared<R> &sh) {
+  const int4 cn = A.conn[e];
+  const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
+  D4 x[4], ue[4], ub[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    x[a] = A.xyz[nd[a]];
+    ue[a] = A.xext[nd[a]];
+    ub[a] = A.ubdf[nd[a]];
+  }
+  R gp[12], Gm[9], gv[3], vol;
+  const bool fp64_geom = (sizeof(R) == 8) || (A.bad && A.bad[e]);
+  if (fp64_geom) {
+    double gpd[12], Gd[9], gd[3], vd;
+    tet_geometry<double>(x, gpd, Gd, gd, vd);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) gp[k] = (R)gpd[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Gm[k] = (R)Gd[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gv[k] = (R)gd[k];
+    vol = (R)vd;
+  } else {
+    float gpf[12], Gf[9], gf[3], vf;
+    tet_geometry<float>(x, gpf, Gf, gf, vf);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) gp[k] = (R)gpf[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Gm[k] = (R)Gf[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gv[k] = (R)gf[k];
+    vol = (R)vf;
+  }
+  if (q == 0) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) sh.gphi[le][k] = gp[k];
+    sh.w[le] = vol * R(0.25);
+  }
+  // barycentric coordinates of point q: phi_a(x_q)
+  R lam[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) lam[a] = (a == q) ? (R)kQA : (R)kQB;
+  // u* = u^EXT(x_q) (semi-implicit, no ALE), u^BDF(x_q), grad u^EXT, grad p^EXT
+  R us[3], ubq[3], uext_q[3];
+  us[0] = lam[0] * (R)ue[0].x + lam[1] * (R)ue[1].x + lam[2] * (R)ue[2].x + lam[3] * (R)ue[3].x;
+  us[1] = lam[0] * (R)ue[0].y + lam[1] * (R)ue[1].y + lam[2] * (R)ue[2].y + lam[3] * (R)ue[3].y;
+  us[2] = lam[0] * (R)ue[0].z + lam[1] * (R)ue[1].z + lam[2] * (R)ue[2].z + lam[3] * (R)ue[3].z;
+  ubq[0] = lam[0] * (R)ub[0].x + lam[1] * (R)ub[1].x + lam[2] * (R)ub[2].x + lam[3] * (R)ub[3].x;
+  ubq[1] = lam[0] * (R)ub[0].y + lam[1] * (R)ub[1].y + lam[2] * (R)ub[2].y + lam[3] * (R)ub[3].y;
+  ubq[2] = lam[0] * (R)ub[0].z + lam[1] * (R)ub[1].z + lam[2] * (R)ub[2].z + lam[3] * (R)ub[3].z;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) uext_q[i] = us[i];
+  R adv[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) adv[a] = us[0] * gp[3 * a] + us[1] * gp[3 * a + 1] + us[2] * gp[3 * a + 2];
+  // resistive coefficient sum_k (R_k/eps_k) delta_k and sum_k (R_k/eps_k)^2 delta_k^2
+  double sR = 0.0, sR2 = 0.0;
+  for (int k = 0; k < P.n_riis; ++k) {
+    const double *ph = A.phi_riis + (int64_t)k * A.n_nodes;
+    double phq = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) phq += (double)lam[a] * ph[nd[a]];
+    double c = P.riis_r[k] / P.riis_eps[k] * delta_fn(phq, P.riis_eps[k]);
+    sR += c;
+    sR2 += c * c;
+  }
+  // tau_M, tau_C in FP64 (Section 2.3)
+  double uGu = 0.0, GG = 0.0, gg = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      double Gkl = (double)Gm[3 * k + l];
+      uGu += (double)us[k] * Gkl * (double)us[l];
+      GG += Gkl * Gkl;
+    }
+    gg += (double)gv[k] * (double)gv[k];
+  }
+  const double rho = P.rho;
+  double tsum = P.sigma * P.sigma * rho * rho / (P.dt * P.dt) + rho * rho * uGu + P.c_r * P.mu * P.mu * GG + sR2;
+  double taum = 1.0 / sqrt(tsum);
+  double tauc = 1.0 / (taum * gg);
+  const R cs = (R)(rho * P.alpha / P.dt + sR);
+  R m[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) m[i] = (R)rho * ubq[i] / (R)P.dt + (R)P.f[i];
+  R z[3] = {R(0), R(0), R(0)};
+  if (P.stab >= 2) {
+    // tau_M r_M(u^EXT, p^EXT) with the strong residual of Section 2.3 (-mu Lap u = 0 for P1)
+    R ts[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R conv = R(0), gpr = R(0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const R ua = (i == 0) ? (R)ue[a].x : ((i == 1) ? (R)ue[a].y : (R)ue[a].z);
+        conv += adv[a] * ua;
+        gpr += (R)ue[a].w * gp[3 * a + i];
+      }
+      R rm = (R)rho * (((R)P.alpha * uext_q[i] - ubq[i]) / (R)P.dt + conv) + gpr + (R)sR * uext_q[i] - (R)P.f[i];
+      ts[i] = (R)taum * rm;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) z[i] = (R)rho * (R)taum * (us[i] - ts[i]);
+  }
+  sh.cs[le][q] = cs;
+  sh.tm[le][q] = (R)taum;
+  sh.tc[le][q] = (R)tauc;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) sh.adv[le][q][a] = adv[a];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    sh.z[le][q][i] = z[i];
+    sh.m[le][q][i] = m[i];
+  }
+}
+
+template <class S> struct Vec16;
+template <> struct Vec16<double> {
+  static __device__ __forceinline__ void add(double *dst, const double v[16]) {
+    double2 *p = reinterpret_cast<double2 *>(dst);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      double2 o = p[k];
+      o.x += v[2 * k];
+      o.y += v[2 * k + 1];
+      p[k] = o;
+    }
+  }
+};
+template <> struct Vec16<float> {
+  static __device__ __forceinline__ void add(float *dst, const float v[16]) {
+    float4 *p = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float4 o = p[k];
+      o.x += v[4 * k];
+      o.y += v[4 * k + 1];
+      o.z += v[4 * k + 2];
+      o.w += v[4 * k + 3];
+      p[k] = o;
+    }
+  }
+};
+
+// Phase 2 for one (element, a, b): block (a, b) and right-hand-side entry 4a+b.
+template <class R, class S>
+__device__ void block_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, int le, int a,
+                            int b, const ElemShared<R> &sh, S *vals) {
+  const R *ga = sh.gphi[le] + 3 * a;
+  const R *gb = sh.gphi[le] + 3 * b;
+  const R w = sh.w[le];
+  const R rho = (R)P.rho;
+  const R gab = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
+  R Mab = R(0), TC = R(0), TM = R(0), Svp = R(0), Ppv = R(0);
+  R Wv[3] = {R(0), R(0), R(0)}, Zv[3] = {R(0), R(0), R(0)};
+  R rhs = R(0);
+  const int i_rhs = b;   // this thread also forms right-hand-side entry (a, i_rhs)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const R pa = (a == q) ? (R)kQA : (R)kQB;
+    const R pb = (b == q) ? (R)kQA : (R)kQB;
+    const R cs = sh.cs[le][q];
+    const R tm = sh.tm[le][q];
+    const R aa = sh.adv[le][q][a];
+    const R ab = sh.adv[le][q][b];
+    const R cb = cs * pb + rho * ab;            // r~_M of the trial function phi_b e_j (per comp)
+    R Mq = cs * pa * pb + rho * pa * ab;        // mass/dt + resistive + Galerkin advection
+    if (P.stab >= 1) {
+      Mq += tm * rho * aa * cb;                 // SUPG, velocity-velocity
+      Svp += w * tm * rho * aa;                 // SUPG, pressure trial
+      Ppv += w * tm * cb;                       // PSPG, velocity trial
+      TM += w * tm;
+      TC += w * sh.tc[le][q];
+    }
+    Mab += w * Mq;
+    const R *zq = sh.z[le][q];
+    const R *mq = sh.m[le][q];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Wv[i] += w * zq[i] * cb;                  // VMS + LES, velocity trial
+      Zv[i] += w * zq[i];                       // VMS + LES, pressure trial
+    }
+    const R mga = mq[0] * ga[0] + mq[1] * ga[1] + mq[2] * ga[2];
+    if (i_rhs < 3) {
+      R r = pa * mq[i_rhs];
+      if (P.stab >= 1) r += tm * mq[i_rhs] * rho * aa;
+      r += zq[i_rhs] * mga;
+      rhs += w * r;
+    } else if (P.stab >= 1) {
+      rhs += w * tm * mga;
+    }
+  }
+  const R vol = R(4) * w;
+  const R mu = (R)P.mu;
+  R blk[16];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R v = (i == j) ? (Mab + mu * vol * gab) : R(0);
+      if (P.diffusion != 0) v += mu * vol * ga[j] * gb[i];
+      v += TC * ga[i] * gb[j];
+      v += Wv[i] * ga[j];
+      blk[4 * i + j] = v;
+    }
+    blk[4 * i + 3] = -w * ga[i] + Svp * gb[i] + Zv[i] * gab;   // -(p, div v) + SUPG + VMS/LES
+    blk[12 + i] = w * gb[i] + Ppv * ga[i];                      // (div u, q) + PSPG
+  }
+  blk[15] = TM * gab;                                           // PSPG
+  S out[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) out[k] = (S)blk[k];
+  const int32_t s = A.slot[e * 16 + 4 * a + b];
+  Vec16<S>::add(vals + (int64_t)s * 16, out);
+  const int4 cn = A.conn[e];
+  const int na = (a == 0) ? cn.x : ((a == 1) ? cn.y : ((a == 2) ? cn.z : cn.w));
+  A.rhs[4 * (int64_t)na + i_rhs] += (double)rhs;
+}
+
+template <class R, class S>
+__global__ void __launch_bounds__(kCta) assemble_color_kernel(AssembleArgs A, PhysParams P,
+                                                              int64_t e0, int64_t e1, S *vals) {
+  __shared__ ElemShared<R> sh;
+  const int t = threadIdx.x;
+  for (int64_t base = e0 + (int64_t)blockIdx.x * kElems; base < e1; base += (int64_t)gridDim.x * kElems) {
+    {
+      const int le = t >> 2, q = t & 3;
+      const int64_t e = base + le;
+      if (e < e1) qp_phase<R>(A, P, e, q, le, sh);
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int pass = 0; pass < kElems * 16 / kCta; ++pass) {
+      const int le = pass * (kCta / 16) + (t >> 4);
+      const int64_t e = base + le;
+      if (e < e1) block_phase<R, S>(A, P, e, le, (t >> 2) & 3, t & 3, sh, vals);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void bdf_kernel(int64_t V, int order, const D4 *h0, const D4 *h1,
+                           const D4 *h2, double b0, double b1, double b2, double g0, double g1,
+                           double g2, D4 *xext, D4 *ubdf) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+    D4 a = h0[i];
+    D4 e = D4{g0 * a.x, g0 * a.y, g0 * a.z, g0 * a.w};
+    D4 u = D4{b0 * a.x, b0 * a.y, b0 * a.z, 0.0};
+    if (order >= 2) {
+      D4 c = h1[i];
+      e.x += g1 * c.x; e.y += g1 * c.y; e.z += g1 * c.z; e.w += g1 * c.w;
+      u.x += b1 * c.x; u.y += b1 * c.y; u.z += b1 * c.z;
+    }
+    if (order >= 3) {
+      D4 c = h2[i];
+      e.x += g2 * c.x; e.y += g2 * c.y; e.z += g2 * c.z; e.w += g2 * c.w;
+      u.x += b2 * c.x; u.y += b2 * c.y; u.z += b2 * c.z;
+    }
+    xext[i] = e;
+    ubdf[i] = u;
+  }
+}
+
+// g at Dirichlet node d: sum_h coef[bc(d)][h] * S[h][d] + coef_nodal[bc(d)] * N[d]
+// (Section 2.2.1: g = theta g(t) s(x); NODAL conditions carry their values in N)
+__global__ void dirichlet_values_kernel(int64_t nd, int H, const int32_t *bc_of,
+                                        const double *S /* [H][nd][3] */, DirCoef C,
+                                        const double *N /* [nd][3] */, int nb, D4 *g) {
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < nd; d += (int64_t)gridDim.x * blockDim.x) {
+    const int bc = bc_of[d];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int h = 0; h < H; ++h) {
+      const double c = C.c[bc * H + h];
+      if (c == 0.0) continue;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) v[i] += c * S[((int64_t)h * nd + d) * 3 + i];
+    }
+    const double cn = C.c[nb * H + bc];
+    if (cn != 0.0) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) v[i] += cn * N[3 * d + i];
+    }
+    g[d] = D4{v[0], v[1], v[2], 0.0};
+  }
+}
+
+// -(h n, v) on Neumann faces, precomputed per node as vec = sum_faces A_f n_f / 3
+__global__ void neumann_kernel(int64_t n, const int32_t *node, const int32_t *bc_of,
+                               const double *vec /* [n][3] */, DirCoef C, double *rhs) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double h = C.c[bc_of[k]];
+    const int64_t r = 4 * (int64_t)node[k];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) rhs[r + i] -= h * vec[3 * k + i];
+  }
+}
+
+// Row replacement for constrained unknowns: row r -> s e_r, rhs_r -> s g, x0_r -> g, with
+// s = |A_rr| (1 if zero).  Thread per constrained (node, component).
+template <class S>
+__global__ void apply_dirichlet_kernel(int64_t nd, const int32_t *dnode, const D4 *g,
+                                       int32_t pin_node, double pin_value,
+                                       const int32_t *rowptr, const int32_t *diag, S *vals,
+                                       double *rhs, double *x0) {
+  const int64_t total = 3 * nd + (pin_node >= 0 ? 1 : 0);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    int node, c;
+    double gv;
+    if (k < 3 * nd) {
+      const int64_t d = k / 3;
+      c = (int)(k - 3 * d);
+      node = dnode[d];
+      const D4 gg = g[d];
+      gv = (c == 0) ? gg.x : ((c == 1) ? gg.y : gg.z);
+    } else {
+      node = pin_node;
+      c = 3;
+      gv = pin_value;
+    }
+    S *dblk = vals + (int64_t)diag[node] * 16;
+    double s = fabs((double)dblk[5 * c]);
+    if (s == 0.0) s = 1.0;
+    for (int32_t kb = rowptr[node]; kb < rowptr[node + 1]; ++kb) {
+      S *blk = vals + (int64_t)kb * 16 + 4 * c;
+      blk[0] = S(0); blk[1] = S(0); blk[2] = S(0); blk[3] = S(0);
+    }
+    dblk[5 * c] = (S)s;
+    rhs[4 * (int64_t)node + c] = s * gv;
+    x0[4 * (int64_t)node + c] = gv;
+  }
+}
+
+inline int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+lfx_status launch_bdf(cudaStream_t st, int64_t V, int order, const D4 *h0, const D4 *h1,
+                      const D4 *h2, const double beta[3], const double gamma[3],
+                      D4 *xext, D4 *ubdf) {
+  note_launches(1);
+  bdf_kernel<<<grid_for(V, 256), 256, 0, st>>>(V, order, h0, h1, h2, beta[0], beta[1], beta[2],
+                                               gamma[0], gamma[1], gamma[2], xext, ubdf);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+template <class R, class S>
+lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysParams &P,
+                           const int32_t *color_off, int n_colors, S *vals) {
+  for (int c = 0; c < n_colors; ++c) {
+    const int64_t e0 = color_off[c], e1 = color_off[c + 1];
+    if (e1 <= e0) continue;
+    int64_t chunks = (e1 - e0 + kElems - 1) / kElems;
+    int grid = (int)(chunks < 152 * 8 ? chunks : 152 * 8);
+    assemble_color_kernel<R, S><<<grid, kCta, 0, st>>>(A, P, e0, e1, vals);
+    note_launches(1);
+  }
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+template lfx_status launch_assemble<double, double>(cudaStream_t, const AssembleArgs &, const PhysParams &,
+                                                    const int32_t *, int, double *);
+template lfx_status launch_assemble<float, float>(cudaStream_t, const AssembleArgs &, const PhysParams &,
+                                                  const int32_t *, int, float *);
+
+lfx_status launch_dirichlet_values(cudaStream_t st, int64_t nd, int H, const int32_t *bc_of,
+                                   const double *S, const DirCoef &C, const double *N, int nb, D4 *g) {
+  if (nd == 0) return LFX_OK;
+  note_launches(1);
+  dirichlet_values_kernel<<<grid_for(nd, 256), 256, 0, st>>>(nd, H, bc_of, S, C, N, nb, g);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+lfx_status launch_neumann(cudaStream_t st, int64_t n, const int32_t *node, const int32_t *bc_of,
+                          const double *vec, const DirCoef &C, double *rhs) {
+  if (n == 0) return LFX_OK;
+  note_launches(1);
+  neumann_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, node, bc_of, vec, C, rhs);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+template <class S>
+lfx_status launch_apply_dirichlet(cudaStream_t st, int64_t nd, const int32_t *dnode, const D4 *g,
+                                  int32_t pin_node, double pin_value, const int32_t *rowptr,
+                                  const int32_t *diag, S *vals, double *rhs, double *x0) {
+  int64_t total = 3 * nd + (pin_node >= 0 ? 1 : 0);
+  if (total == 0) return LFX_OK;
+  note_launches(1);
+  apply_dirichlet_kernel<S><<<grid_for(total, 128), 128, 0, st>>>(nd, dnode, g, pin_node, pin_value,
+                                                                  rowptr, diag, vals, rhs, x0);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+template lfx_status launch_apply_dirichlet<double>(cudaStream_t, int64_t, const int32_t *, const D4 *,
+                                                   int32_t, double, const int32_t *, const int32_t *,
+                                                   double *, double *, double *);
+template lfx_status launch_apply_dirichlet<float>(cudaStream_t, int64_t, const int32_t *, const D4 *,
+                                                  int32_t, double, const int32_t *, const int32_t *,
+                                                  float *, double *, double *);
+
+}  // namespace lfx

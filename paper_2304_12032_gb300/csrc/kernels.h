@@ -1,0 +1,69 @@
+// Kernel launchers shared across the CUDA translation units of liblfx.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lfx_internal.h"
+
+namespace lfx {
+
+// 32-byte node records (x, y, z, w) and their FP32 counterpart
+struct alignas(32) D4 {
+  double x, y, z, w;
+};
+struct alignas(16) F4 {
+  float x, y, z, w;
+};
+
+// ------------------------------------------------------------------ assembly
+struct AssembleArgs {
+  const int4 *conn;          // [T] internal numbering, colour-sorted
+  const int32_t *slot;       // [T][16]
+  const D4 *xyz;        // [V] (x, y, z, 0)
+  const D4 *xext;       // [V] (u^EXT, p^EXT)
+  const D4 *ubdf;       // [V] (u^BDF, 0)
+  const double *phi_riis;    // [n_riis][V]
+  const uint8_t *bad;        // [T] FP64 geometry flag (mixed assembly), may be null
+  double *rhs;               // [V][4]
+  int64_t n_nodes;
+};
+
+constexpr int kMaxDirCoef = 256;
+struct DirCoef {
+  double c[kMaxDirCoef];
+};
+
+lfx_status launch_bdf(cudaStream_t st, int64_t V, int order, const D4 *h0, const D4 *h1,
+                      const D4 *h2, const double beta[3], const double gamma[3],
+                      D4 *xext, D4 *ubdf);
+template <class R, class S>
+lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysParams &P,
+                           const int32_t *color_off, int n_colors, S *vals);
+lfx_status launch_dirichlet_values(cudaStream_t st, int64_t nd, int H, const int32_t *bc_of,
+                                   const double *S, const DirCoef &C, const double *N, int nb, D4 *g);
+lfx_status launch_neumann(cudaStream_t st, int64_t n, const int32_t *node, const int32_t *bc_of,
+                          const double *vec, const DirCoef &C, double *rhs);
+template <class S>
+lfx_status launch_apply_dirichlet(cudaStream_t st, int64_t nd, const int32_t *dnode, const D4 *g,
+                                  int32_t pin_node, double pin_value, const int32_t *rowptr,
+                                  const int32_t *diag, S *vals, double *rhs, double *x0);
+
+// ------------------------------------------------------------------ block-CSR views
+template <class S>
+struct BsrView {
+  int64_t V;                 // block rows
+  const int32_t *rowptr;     // [V+1]
+  const int32_t *col;        // [nnzb]
+  const int32_t *diag;       // [V]
+  const int32_t *trans;      // [nnzb]
+  const S *vals;             // [nnzb][16]
+};
+
+// y = A x  (mode 0)  or  y = b - A x  (mode 1); vectors [V][4] of type T.  Optionally writes
+// per-CTA partial sums of y.y into part (deterministic two-stage norm).
+template <class S, class T>
+lfx_status launch_spmv(cudaStream_t st, const BsrView<S> &A, const T *x, const T *b, T *y,
+                       int mode, double *part, int *n_part);
+
+}  // namespace lfx

@@ -1,0 +1,117 @@
+// Internal declarations shared by the host runtime (.cpp) and the CUDA kernels (.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lfx.h"
+
+namespace lfx {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define LFX_CUDA_TRY(expr)                                                                 \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      ::lfx::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,     \
+                       __LINE__);                                                          \
+      return LFX_ERR_CUDA;                                                                 \
+    }                                                                                      \
+  } while (0)
+
+#define LFX_TRY(expr)                 \
+  do {                                \
+    lfx_status s_ = (expr);           \
+    if (s_ != LFX_OK) return s_;      \
+  } while (0)
+
+// ---------------------------------------------------------------- launch accounting
+// Number of kernels this library has launched (diagnostic; read with lfx_launch_count).
+void note_launches(int64_t n);
+
+// ---------------------------------------------------------------- device memory
+void *dalloc(size_t bytes);          // nullptr on failure (error message set)
+void dfree(void *p);
+
+// A device buffer that frees itself; tracks its size for admission control.
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) dfree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  lfx_status alloc(size_t n) {
+    release();
+    if (n == 0) n = 16;
+    p = dalloc(n);
+    if (!p) return LFX_ERR_OOM;
+    bytes = n;
+    return LFX_OK;
+  }
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ---------------------------------------------------------------- mesh (host + device)
+struct Mesh {
+  int64_t V = 0, T = 0, F = 0, nnzb = 0;
+  int n_flipped = 0;
+  bool uploaded = false;
+  // renumbering
+  std::vector<int32_t> node_old;     // internal node -> caller node
+  std::vector<int32_t> node_new;     // caller node -> internal node
+  std::vector<int32_t> elem_old;     // internal element (colour-sorted) -> caller element
+  // geometry / topology, internal numbering
+  std::vector<double> xyz;           // [V][3]
+  std::vector<int32_t> tets;         // [T][4], positively oriented
+  std::vector<int32_t> row_ptr;      // [V+1]
+  std::vector<int32_t> col_idx;      // [nnzb], sorted per row
+  std::vector<int32_t> diag_idx;     // [V] block index of (i,i)
+  std::vector<int32_t> trans_idx;    // [nnzb] block index of (j,i) for block (i,j)
+  std::vector<int32_t> slot;         // [T][16] block index of (node a, node b), a*4+b
+  std::vector<int32_t> color_off;    // [n_colors+1] offsets into the colour-sorted elements
+  std::vector<uint8_t> bad;          // [T] 1 if below the shape-quality threshold
+  std::vector<int32_t> bfaces;       // [F][3] outward oriented, internal numbering
+  std::vector<int32_t> btags;        // [F]
+  std::vector<double> quality;       // [T] 6 sqrt2 |K| / e_rms^3
+  // device copies
+  DBuf d_xyz;       // double4 [V] (x, y, z, 0)
+  DBuf d_conn;      // int4 [T]
+  DBuf d_slot;      // int32 [T][16]
+  DBuf d_rowptr;    // int32 [V+1]
+  DBuf d_col;       // int32 [nnzb]
+  DBuf d_diag;      // int32 [V]
+  DBuf d_trans;     // int32 [nnzb]
+  size_t device_bytes() const;
+};
+
+lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                      const int32_t *bfaces, const int32_t *tags, int64_t n_bfaces, Mesh &m);
+lfx_status upload_mesh(Mesh &m);
+
+// ---------------------------------------------------------------- kernels' parameter blocks
+constexpr int kMaxRiis = 8;
+struct PhysParams {
+  double rho, mu, dt, alpha, sigma, c_r;
+  double f[3];
+  int32_t n_riis, stab, diffusion, pad;
+  double riis_r[kMaxRiis], riis_eps[kMaxRiis];
+};
+
+}  // namespace lfx
+
+// opaque handles of the C ABI
+struct lfx_mesh {
+  lfx::Mesh m;
+};

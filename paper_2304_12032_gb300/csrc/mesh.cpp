@@ -1,0 +1,296 @@
+// Host-side mesh set-up (once per mesh): validation and orientation, space-filling-curve
+// renumbering of nodes and elements, the 4x4 block-CSR pattern of the node graph (the DoF
+// pattern of P1-P1 with 4 unknowns per node, Section 2.3), the element -> block-slot map, the
+// transpose map, outward boundary faces, and a greedy element colouring so that elements of one
+// colour share no node and their block updates need no atomics.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "lfx_internal.h"
+
+namespace lfx {
+
+namespace {
+
+// 21-bit-per-axis Morton code of a point inside the bounding box [lo, lo + span].
+inline uint64_t spread3(uint64_t v) {
+  v &= 0x1fffff;
+  v = (v | v << 32) & 0x1f00000000ffffULL;
+  v = (v | v << 16) & 0x1f0000ff0000ffULL;
+  v = (v | v << 8) & 0x100f00f00f00f00fULL;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+  v = (v | v << 2) & 0x1249249249249249ULL;
+  return v;
+}
+inline uint64_t morton(const double *p, const double *lo, double inv_span) {
+  uint64_t c[3];
+  for (int k = 0; k < 3; ++k) {
+    double t = (p[k] - lo[k]) * inv_span;
+    t = t < 0 ? 0 : (t > 1 ? 1 : t);
+    c[k] = (uint64_t)(t * 2097151.0);
+  }
+  return spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+}
+
+double signed_det(const double *x0, const double *x1, const double *x2, const double *x3) {
+  double a[3], b[3], c[3];
+  for (int k = 0; k < 3; ++k) {
+    a[k] = x1[k] - x0[k];
+    b[k] = x2[k] - x0[k];
+    c[k] = x3[k] - x0[k];
+  }
+  return a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+         a[2] * (b[0] * c[1] - b[1] * c[0]);
+}
+
+}  // namespace
+
+size_t Mesh::device_bytes() const {
+  return d_xyz.bytes + d_conn.bytes + d_slot.bytes + d_rowptr.bytes + d_col.bytes + d_diag.bytes +
+         d_trans.bytes;
+}
+
+lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_in, int64_t n_tets,
+                      const int32_t *bfaces_in, const int32_t *tags_in, int64_t n_bfaces,
+                      Mesh &m) {
+  if (!nodes || !tets_in || n_nodes < 4 || n_tets < 1 || n_bfaces < 0 ||
+      (n_bfaces > 0 && (!bfaces_in || !tags_in))) {
+    set_error("lfx_mesh_create: null array or size out of range");
+    return LFX_ERR_INVALID_ARG;
+  }
+  if (n_nodes > (int64_t)INT32_MAX / 4 || n_tets > (int64_t)INT32_MAX / 16) {
+    set_error("lfx_mesh_create: mesh too large for 32-bit indices");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const int64_t V = n_nodes, T = n_tets, F = n_bfaces;
+  m.V = V;
+  m.T = T;
+  m.F = F;
+  for (int64_t i = 0; i < 4 * T; ++i)
+    if (tets_in[i] < 0 || tets_in[i] >= V) {
+      set_error("lfx_mesh_create: tet %lld references node %d outside [0,%lld)",
+                (long long)(i / 4), tets_in[i], (long long)V);
+      return LFX_ERR_BAD_MESH;
+    }
+  for (int64_t i = 0; i < 3 * F; ++i)
+    if (bfaces_in[i] < 0 || bfaces_in[i] >= V) {
+      set_error("lfx_mesh_create: boundary face %lld references a node out of range",
+                (long long)(i / 3));
+      return LFX_ERR_BAD_MESH;
+    }
+  for (int64_t i = 0; i < 3 * V; ++i)
+    if (!std::isfinite(nodes[i])) {
+      set_error("lfx_mesh_create: non-finite node coordinate");
+      return LFX_ERR_BAD_MESH;
+    }
+
+  // ---- node renumbering along a Morton curve
+  double lo[3] = {nodes[0], nodes[1], nodes[2]}, hi[3] = {nodes[0], nodes[1], nodes[2]};
+  for (int64_t i = 0; i < V; ++i)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], nodes[3 * i + k]);
+      hi[k] = std::max(hi[k], nodes[3 * i + k]);
+    }
+  double span = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  double inv_span = span > 0 ? 1.0 / span : 1.0;
+  std::vector<uint64_t> key(V);
+  for (int64_t i = 0; i < V; ++i) key[i] = morton(nodes + 3 * i, lo, inv_span);
+  m.node_old.resize(V);
+  std::iota(m.node_old.begin(), m.node_old.end(), 0);
+  std::stable_sort(m.node_old.begin(), m.node_old.end(),
+                   [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  m.node_new.assign(V, 0);
+  for (int64_t i = 0; i < V; ++i) m.node_new[m.node_old[i]] = (int32_t)i;
+  m.xyz.resize(3 * V);
+  for (int64_t i = 0; i < V; ++i)
+    for (int k = 0; k < 3; ++k) m.xyz[3 * i + k] = nodes[3 * (int64_t)m.node_old[i] + k];
+
+  // ---- elements: renumber nodes, orient, quality, Morton order of centroids
+  std::vector<int32_t> tt(4 * T);
+  std::vector<double> qual(T);
+  m.n_flipped = 0;
+  double scale = span > 0 ? span : 1.0;
+  for (int64_t e = 0; e < T; ++e) {
+    int32_t v[4];
+    for (int a = 0; a < 4; ++a) v[a] = m.node_new[tets_in[4 * e + a]];
+    const double *x[4];
+    for (int a = 0; a < 4; ++a) x[a] = &m.xyz[3 * (int64_t)v[a]];
+    double det = signed_det(x[0], x[1], x[2], x[3]);
+    double e2 = 0;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b)
+        for (int k = 0; k < 3; ++k) e2 += (x[a][k] - x[b][k]) * (x[a][k] - x[b][k]);
+    double erms = std::sqrt(e2 / 6.0);
+    if (!(std::fabs(det) > 1e-15 * erms * erms * erms) || erms <= 1e-300 * scale) {
+      set_error("lfx_mesh_create: tet %lld has zero volume", (long long)e);
+      return LFX_ERR_BAD_MESH;
+    }
+    if (det < 0) {
+      std::swap(v[2], v[3]);
+      ++m.n_flipped;
+    }
+    qual[e] = std::fabs(det) / 6.0 * 6.0 * std::sqrt(2.0) / (erms * erms * erms);
+    for (int a = 0; a < 4; ++a) tt[4 * e + a] = v[a];
+  }
+  std::vector<uint64_t> ekey(T);
+  for (int64_t e = 0; e < T; ++e) {
+    double c[3] = {0, 0, 0};
+    for (int a = 0; a < 4; ++a)
+      for (int k = 0; k < 3; ++k) c[k] += 0.25 * m.xyz[3 * (int64_t)tt[4 * e + a] + k];
+    ekey[e] = morton(c, lo, inv_span);
+  }
+  std::vector<int32_t> eorder(T);
+  std::iota(eorder.begin(), eorder.end(), 0);
+  std::stable_sort(eorder.begin(), eorder.end(),
+                   [&](int32_t a, int32_t b) { return ekey[a] < ekey[b]; });
+
+  // ---- greedy colouring in Morton order: smallest colour unused at the element's 4 nodes
+  constexpr int kWords = 4;  // up to 256 colours
+  std::vector<uint64_t> used((size_t)V * kWords, 0);
+  std::vector<int32_t> color(T);
+  int n_colors = 0;
+  for (int64_t s = 0; s < T; ++s) {
+    int32_t e = eorder[s];
+    int c = -1;
+    for (int w = 0; w < kWords && c < 0; ++w) {
+      uint64_t busy = 0;
+      for (int a = 0; a < 4; ++a) busy |= used[(size_t)tt[4 * e + a] * kWords + w];
+      if (~busy) c = 64 * w + __builtin_ctzll(~busy);
+    }
+    if (c < 0) {
+      set_error("lfx_mesh_create: element colouring needs more than %d colours", 64 * kWords);
+      return LFX_ERR_BAD_MESH;
+    }
+    color[e] = c;
+    for (int a = 0; a < 4; ++a) used[(size_t)tt[4 * e + a] * kWords + c / 64] |= 1ULL << (c % 64);
+    n_colors = std::max(n_colors, c + 1);
+  }
+  // colour-sorted element order (Morton order kept inside each colour)
+  m.color_off.assign(n_colors + 1, 0);
+  for (int64_t e = 0; e < T; ++e) m.color_off[color[e] + 1]++;
+  for (int c = 0; c < n_colors; ++c) m.color_off[c + 1] += m.color_off[c];
+  std::vector<int32_t> fill(m.color_off.begin(), m.color_off.end() - 1);
+  m.elem_old.resize(T);
+  for (int64_t s = 0; s < T; ++s) {
+    int32_t e = eorder[s];
+    m.elem_old[fill[color[e]]++] = e;
+  }
+  m.tets.resize(4 * T);
+  m.quality.resize(T);
+  for (int64_t i = 0; i < T; ++i) {
+    int32_t e = m.elem_old[i];
+    for (int a = 0; a < 4; ++a) m.tets[4 * i + a] = tt[4 * (int64_t)e + a];
+    m.quality[i] = qual[e];
+  }
+
+  // ---- node -> element adjacency (internal numbering)
+  std::vector<int32_t> n2e_ptr(V + 1, 0), n2e;
+  for (int64_t i = 0; i < 4 * T; ++i) n2e_ptr[m.tets[i] + 1]++;
+  for (int64_t i = 0; i < V; ++i) n2e_ptr[i + 1] += n2e_ptr[i];
+  n2e.resize(4 * T);
+  {
+    std::vector<int32_t> f(n2e_ptr.begin(), n2e_ptr.end() - 1);
+    for (int64_t e = 0; e < T; ++e)
+      for (int a = 0; a < 4; ++a) n2e[f[m.tets[4 * e + a]]++] = (int32_t)e;
+  }
+  for (int64_t i = 0; i < V; ++i)
+    if (n2e_ptr[i + 1] == n2e_ptr[i]) {
+      set_error("lfx_mesh_create: node %d belongs to no tetrahedron", m.node_old[i]);
+      return LFX_ERR_BAD_MESH;
+    }
+
+  // ---- block pattern: row i = sorted unique nodes of the elements around i
+  m.row_ptr.assign(V + 1, 0);
+  m.col_idx.clear();
+  m.col_idx.reserve((size_t)V * 16);
+  std::vector<int32_t> buf;
+  for (int64_t i = 0; i < V; ++i) {
+    buf.clear();
+    for (int32_t k = n2e_ptr[i]; k < n2e_ptr[i + 1]; ++k)
+      for (int a = 0; a < 4; ++a) buf.push_back(m.tets[4 * (int64_t)n2e[k] + a]);
+    std::sort(buf.begin(), buf.end());
+    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+    m.col_idx.insert(m.col_idx.end(), buf.begin(), buf.end());
+    if ((int64_t)m.col_idx.size() > (int64_t)INT32_MAX) {
+      set_error("lfx_mesh_create: pattern too large");
+      return LFX_ERR_INVALID_ARG;
+    }
+    m.row_ptr[i + 1] = (int32_t)m.col_idx.size();
+  }
+  m.nnzb = (int64_t)m.col_idx.size();
+  auto find = [&](int32_t r, int32_t c) -> int32_t {
+    const int32_t *b = m.col_idx.data() + m.row_ptr[r], *e = m.col_idx.data() + m.row_ptr[r + 1];
+    const int32_t *p = std::lower_bound(b, e, c);
+    return (p != e && *p == c) ? (int32_t)(p - m.col_idx.data()) : -1;
+  };
+  m.diag_idx.resize(V);
+  for (int64_t i = 0; i < V; ++i) m.diag_idx[i] = find((int32_t)i, (int32_t)i);
+  m.trans_idx.resize(m.nnzb);
+  for (int64_t i = 0; i < V; ++i)
+    for (int32_t k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k)
+      m.trans_idx[k] = find(m.col_idx[k], (int32_t)i);
+  m.slot.resize((size_t)T * 16);
+  for (int64_t e = 0; e < T; ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b)
+        m.slot[16 * e + 4 * a + b] = find(m.tets[4 * e + a], m.tets[4 * e + b]);
+
+  // ---- boundary faces: internal numbering, outward orientation from the owning tetrahedron
+  m.bfaces.resize(3 * F);
+  m.btags.assign(tags_in, tags_in + F);
+  for (int64_t f = 0; f < F; ++f) {
+    int32_t v[3];
+    for (int k = 0; k < 3; ++k) v[k] = m.node_new[bfaces_in[3 * f + k]];
+    int32_t owner = -1, opp = -1;
+    for (int32_t k = n2e_ptr[v[0]]; k < n2e_ptr[v[0] + 1] && owner < 0; ++k) {
+      const int32_t *t = &m.tets[4 * (int64_t)n2e[k]];
+      int hits = 0, other = -1;
+      for (int a = 0; a < 4; ++a) {
+        if (t[a] == v[0] || t[a] == v[1] || t[a] == v[2]) ++hits;
+        else other = t[a];
+      }
+      if (hits == 3) {
+        owner = n2e[k];
+        opp = other;
+      }
+    }
+    if (owner < 0) {
+      set_error("lfx_mesh_create: boundary face %lld is not a face of any tetrahedron",
+                (long long)f);
+      return LFX_ERR_BAD_MESH;
+    }
+    const double *a = &m.xyz[3 * (int64_t)v[0]], *b = &m.xyz[3 * (int64_t)v[1]],
+                 *c = &m.xyz[3 * (int64_t)v[2]], *d = &m.xyz[3 * (int64_t)opp];
+    if (signed_det(a, b, c, d) > 0) std::swap(v[1], v[2]);
+    for (int k = 0; k < 3; ++k) m.bfaces[3 * f + k] = v[k];
+  }
+  return LFX_OK;
+}
+
+lfx_status upload_mesh(Mesh &m) {
+  const int64_t V = m.V, T = m.T;
+  std::vector<double> x4(4 * V);
+  for (int64_t i = 0; i < V; ++i) {
+    for (int k = 0; k < 3; ++k) x4[4 * i + k] = m.xyz[3 * i + k];
+    x4[4 * i + 3] = 0.0;
+  }
+  LFX_TRY(m.d_xyz.alloc(sizeof(double) * 4 * V));
+  LFX_TRY(m.d_conn.alloc(sizeof(int32_t) * 4 * T));
+  LFX_TRY(m.d_slot.alloc(sizeof(int32_t) * 16 * T));
+  LFX_TRY(m.d_rowptr.alloc(sizeof(int32_t) * (V + 1)));
+  LFX_TRY(m.d_col.alloc(sizeof(int32_t) * m.nnzb));
+  LFX_TRY(m.d_diag.alloc(sizeof(int32_t) * V));
+  LFX_TRY(m.d_trans.alloc(sizeof(int32_t) * m.nnzb));
+  LFX_CUDA_TRY(cudaMemcpy(m.d_xyz.p, x4.data(), m.d_xyz.bytes, cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemcpy(m.d_conn.p, m.tets.data(), sizeof(int32_t) * 4 * T, cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemcpy(m.d_slot.p, m.slot.data(), sizeof(int32_t) * 16 * T, cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemcpy(m.d_rowptr.p, m.row_ptr.data(), sizeof(int32_t) * (V + 1), cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemcpy(m.d_col.p, m.col_idx.data(), sizeof(int32_t) * m.nnzb, cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemcpy(m.d_diag.p, m.diag_idx.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemcpy(m.d_trans.p, m.trans_idx.data(), sizeof(int32_t) * m.nnzb, cudaMemcpyHostToDevice));
+  return LFX_OK;
+}
+
+}  // namespace lfx

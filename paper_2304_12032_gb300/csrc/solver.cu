@@ -1,0 +1,911 @@
+// Linear algebra of Section 2.4: block-CSR matrix-vector products, the aSIMPLE preconditioner
+// [deparis2014parallel] with Jacobi / Chebyshev smoothing of the velocity block F and of the
+// Schur approximation S = C - D diag(F)^-1 G, and restarted right-preconditioned (flexible)
+// GMRES with classical Gram-Schmidt (optionally twice), Givens rotations and a device-resident
+// convergence flag.
+//
+// Vectors are [V][4] (u_x, u_y, u_z, p per node).  Every reduction is two-stage (per-CTA
+// partials, then one CTA sums them in a fixed order), so results are bitwise reproducible.
+// Every kernel of an Arnoldi step reads the solver's status word first and returns at once if
+// the cycle is already finished, so the host may queue a few steps ahead of the convergence test.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "kernels.h"
+#include "solver.h"
+
+namespace lfx {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRowGroup = 8;      // lanes per block row in the row kernels
+
+template <class T> struct Vec4T;
+template <> struct Vec4T<double> { using type = D4; };
+template <> struct Vec4T<float> { using type = F4; };
+
+template <class T>
+__device__ __forceinline__ typename Vec4T<T>::type ld4(const T *p, int64_t i) {
+  return reinterpret_cast<const typename Vec4T<T>::type *>(p)[i];
+}
+template <class T>
+__device__ __forceinline__ void st4(T *p, int64_t i, const typename Vec4T<T>::type &v) {
+  reinterpret_cast<typename Vec4T<T>::type *>(p)[i] = v;
+}
+
+template <class S, class A>
+__device__ __forceinline__ void ld_block(const S *vals, int64_t k, A b[16]);
+template <>
+__device__ __forceinline__ void ld_block<double, double>(const double *vals, int64_t k, double b[16]) {
+  const double2 *p = reinterpret_cast<const double2 *>(vals + 16 * k);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    double2 v = __ldg(p + i);
+    b[2 * i] = v.x;
+    b[2 * i + 1] = v.y;
+  }
+}
+template <>
+__device__ __forceinline__ void ld_block<float, float>(const float *vals, int64_t k, float b[16]) {
+  const float4 *p = reinterpret_cast<const float4 *>(vals + 16 * k);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float4 v = __ldg(p + i);
+    b[4 * i] = v.x;
+    b[4 * i + 1] = v.y;
+    b[4 * i + 2] = v.z;
+    b[4 * i + 3] = v.w;
+  }
+}
+template <>
+__device__ __forceinline__ void ld_block<float, double>(const float *vals, int64_t k, double b[16]) {
+  const float4 *p = reinterpret_cast<const float4 *>(vals + 16 * k);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float4 v = __ldg(p + i);
+    b[4 * i] = v.x;
+    b[4 * i + 1] = v.y;
+    b[4 * i + 2] = v.z;
+    b[4 * i + 3] = v.w;
+  }
+}
+
+template <class A>
+__device__ __forceinline__ A group_sum(A v) {
+#pragma unroll
+  for (int o = kRowGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// CTA-wide sum of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double cta_sum(double v) {
+  __shared__ double red[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
+__device__ __forceinline__ bool finished(const KState *st) {
+  return st != nullptr && *(volatile const int *)&st->done != 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// y = A x (mode 0) or y = b - A x (mode 1); optional partial sums of y.y per CTA
+// ------------------------------------------------------------------------------------------
+template <class S, class T>
+__global__ void __launch_bounds__(kThreads) spmv_kernel(BsrView<S> A, const T *__restrict__ x,
+                                                        const T *__restrict__ b, T *__restrict__ y,
+                                                        int mode, double *part, const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  if (row < A.V) {
+    const int32_t k1 = A.rowptr[row + 1];
+    for (int32_t k = A.rowptr[row] + lane; k < k1; k += kRowGroup) {
+      T blk[16];
+      ld_block<S, T>(A.vals, k, blk);
+      const auto xv = ld4(x, A.col[k]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        acc[i] += blk[4 * i] * xv.x + blk[4 * i + 1] * xv.y + blk[4 * i + 2] * xv.z + blk[4 * i + 3] * xv.w;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i] = group_sum(acc[i]);
+  double nrm = 0.0;
+  if (row < A.V && lane == 0) {
+    typename Vec4T<T>::type o;
+    if (mode == 1) {
+      const auto bv = ld4(b, row);
+      o.x = bv.x - acc[0]; o.y = bv.y - acc[1]; o.z = bv.z - acc[2]; o.w = bv.w - acc[3];
+    } else {
+      o.x = acc[0]; o.y = acc[1]; o.z = acc[2]; o.w = acc[3];
+    }
+    st4(y, row, o);
+    nrm = (double)o.x * o.x + (double)o.y * o.y + (double)o.z * o.z + (double)o.w * o.w;
+  }
+  if (part) {
+    double s = cta_sum(nrm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+// sum of part[0..n) -> *out (sqrt if root); one CTA, fixed order
+__global__ void reduce_kernel(const double *part, int n, double *out, int root) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  s = cta_sum(s);
+  if (threadIdx.x == 0) *out = root ? sqrt(s) : s;
+}
+
+// ------------------------------------------------------------------------------------------
+// aSIMPLE building blocks on the 4x4 blocks (row-major: [i][j], i test comp, j trial comp)
+//   F = [0..2][0..2], G = [0..2][3], D = [3][0..2], C = [3][3]
+// ------------------------------------------------------------------------------------------
+template <class S, class T>
+__global__ void diag_f_kernel(BsrView<S> A, T *dinvF) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.V; r += (int64_t)gridDim.x * blockDim.x) {
+    const S *d = A.vals + 16 * (int64_t)A.diag[r];
+    typename Vec4T<T>::type o;
+    o.x = T(1) / (T)d[0];
+    o.y = T(1) / (T)d[5];
+    o.z = T(1) / (T)d[10];
+    o.w = T(0);
+    st4(dinvF, r, o);
+  }
+}
+
+// diag(S)_a = C_aa - sum_{b,j} D_{a,(b,j)} G_{(b,j),a} / F_{(b,j),(b,j)}
+template <class S, class T>
+__global__ void diag_s_kernel(BsrView<S> A, const T *dinvF, T *dinvS) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  T acc = T(0);
+  if (row < A.V) {
+    for (int32_t k = A.rowptr[row] + lane; k < A.rowptr[row + 1]; k += kRowGroup) {
+      const S *blk = A.vals + 16 * (int64_t)k;              // block (a, b)
+      const S *tb = A.vals + 16 * (int64_t)A.trans[k];      // block (b, a)
+      const auto df = ld4(dinvF, A.col[k]);
+      acc += (T)blk[12] * (T)tb[3] * df.x + (T)blk[13] * (T)tb[7] * df.y + (T)blk[14] * (T)tb[11] * df.z;
+    }
+  }
+  acc = group_sum(acc);
+  if (row < A.V && lane == 0) {
+    const T c = (T)A.vals[16 * (int64_t)A.diag[row] + 15];
+    dinvS[row] = T(1) / (c - acc);
+  }
+}
+
+// Velocity smoothing step on F.  mode 0 (power): y = dinvF (F v), partial |y|^2.
+// mode 1 (Chebyshev/Jacobi step k): y = F d_old; r -= dinvF y; d_new = c1 d_old + c2 r; x += d_new.
+template <class S, class T>
+__global__ void __launch_bounds__(kThreads) f_step_kernel(BsrView<S> A, const T *dinvF, const T *d_old,
+                                                          T *d_new, T *r, T *x, const SmoothCoef *cf,
+                                                          int k, int mode, double *part, const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  T acc[3] = {T(0), T(0), T(0)};
+  if (row < A.V) {
+    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+      T blk[16];
+      ld_block<S, T>(A.vals, kb, blk);
+      const auto dv = ld4(d_old, A.col[kb]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) acc[i] += blk[4 * i] * dv.x + blk[4 * i + 1] * dv.y + blk[4 * i + 2] * dv.z;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) acc[i] = group_sum(acc[i]);
+  double nrm = 0.0;
+  if (row < A.V && lane == 0) {
+    const auto df = ld4(dinvF, row);
+    if (mode == 0) {
+      auto o = ld4(d_new, row);
+      o.x = df.x * acc[0]; o.y = df.y * acc[1]; o.z = df.z * acc[2];
+      st4(d_new, row, o);
+      nrm = (double)o.x * o.x + (double)o.y * o.y + (double)o.z * o.z;
+    } else {
+      const T c1 = (T)cf->f_c1[k], c2 = (T)cf->f_c2[k];
+      auto rr = ld4(r, row);
+      const auto dold = ld4(d_old, row);
+      auto dn = ld4(d_new, row);
+      auto xx = ld4(x, row);
+      rr.x -= df.x * acc[0]; rr.y -= df.y * acc[1]; rr.z -= df.z * acc[2];
+      dn.x = c1 * dold.x + c2 * rr.x; dn.y = c1 * dold.y + c2 * rr.y; dn.z = c1 * dold.z + c2 * rr.z;
+      xx.x += dn.x; xx.y += dn.y; xx.z += dn.z;
+      st4(r, row, rr);
+      st4(d_new, row, dn);
+      st4(x, row, xx);
+    }
+  }
+  if (part) {
+    double s = cta_sum(nrm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+// w.xyz = dinvF (G p) with p = in.w   (velocity rows, pressure column)
+template <class S, class T>
+__global__ void __launch_bounds__(kThreads) g_scaled_kernel(BsrView<S> A, const T *dinvF, const T *in,
+                                                            T *w, const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  T acc[3] = {T(0), T(0), T(0)};
+  if (row < A.V) {
+    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+      const S *blk = A.vals + 16 * (int64_t)kb;
+      const T p = ld4(in, A.col[kb]).w;
+      acc[0] += (T)blk[3] * p;
+      acc[1] += (T)blk[7] * p;
+      acc[2] += (T)blk[11] * p;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) acc[i] = group_sum(acc[i]);
+  if (row < A.V && lane == 0) {
+    const auto df = ld4(dinvF, row);
+    auto o = ld4(w, row);
+    o.x = df.x * acc[0]; o.y = df.y * acc[1]; o.z = df.z * acc[2];
+    st4(w, row, o);
+  }
+}
+
+// Pressure smoothing step on S = C - D diag(F)^-1 G, with w.xyz = diag(F)^-1 G d_old.w given.
+// mode 0 (power): y.w = dinvS (C v - D w), partial |y|^2.  mode 1: Chebyshev/Jacobi step.
+template <class S, class T>
+__global__ void __launch_bounds__(kThreads) s_step_kernel(BsrView<S> A, const T *dinvS, const T *d_old,
+                                                          const T *w, T *d_new, T *r, T *x,
+                                                          const SmoothCoef *cf, int k, int mode,
+                                                          double *part, const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  T acc = T(0);
+  if (row < A.V) {
+    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+      const S *blk = A.vals + 16 * (int64_t)kb;
+      const int32_t c = A.col[kb];
+      const T p = ld4(d_old, c).w;
+      const auto wv = ld4(w, c);
+      acc += (T)blk[15] * p - ((T)blk[12] * wv.x + (T)blk[13] * wv.y + (T)blk[14] * wv.z);
+    }
+  }
+  acc = group_sum(acc);
+  double nrm = 0.0;
+  if (row < A.V && lane == 0) {
+    const T ds = dinvS[row];
+    if (mode == 0) {
+      auto o = ld4(d_new, row);
+      o.w = ds * acc;
+      st4(d_new, row, o);
+      nrm = (double)o.w * o.w;
+    } else {
+      const T c1 = (T)cf->s_c1[k], c2 = (T)cf->s_c2[k];
+      auto rr = ld4(r, row);
+      const T dold = ld4(d_old, row).w;
+      auto dn = ld4(d_new, row);
+      auto xx = ld4(x, row);
+      rr.w -= ds * acc;
+      dn.w = c1 * dold + c2 * rr.w;
+      xx.w += dn.w;
+      st4(r, row, rr);
+      st4(d_new, row, dn);
+      st4(x, row, xx);
+    }
+  }
+  if (part) {
+    double s = cta_sum(nrm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+// Start of the velocity smoothing: r.xyz = dinvF b.xyz, d.xyz = init r.xyz, x.xyz = d.xyz
+template <class T>
+__global__ void f_init_kernel(int64_t V, const T *dinvF, const T *b, T *r, T *d, T *x,
+                              const SmoothCoef *cf, const KState *st) {
+  if (finished(st)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+    const T s = (T)cf->f_init;
+    const auto df = ld4(dinvF, i);
+    const auto bv = ld4(b, i);
+    auto rr = ld4(r, i);
+    auto dd = ld4(d, i);
+    auto xx = ld4(x, i);
+    rr.x = df.x * bv.x; rr.y = df.y * bv.y; rr.z = df.z * bv.z;
+    dd.x = s * rr.x; dd.y = s * rr.y; dd.z = s * rr.z;
+    xx.x = dd.x; xx.y = dd.y; xx.z = dd.z;
+    st4(r, i, rr);
+    st4(d, i, dd);
+    st4(x, i, xx);
+  }
+}
+
+// t = b.w - D x.xyz, then start of the pressure smoothing: r.w = dinvS t, d.w = init r.w, x.w = d.w
+template <class S, class T>
+__global__ void __launch_bounds__(kThreads) d_init_kernel(BsrView<S> A, const T *dinvS, const T *b,
+                                                          T *r, T *d, T *x, const SmoothCoef *cf,
+                                                          const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  T acc = T(0);
+  if (row < A.V) {
+    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+      const S *blk = A.vals + 16 * (int64_t)kb;
+      const auto xv = ld4(x, A.col[kb]);
+      acc += (T)blk[12] * xv.x + (T)blk[13] * xv.y + (T)blk[14] * xv.z;
+    }
+  }
+  acc = group_sum(acc);
+  if (row < A.V && lane == 0) {
+    const T t = ld4(b, row).w - acc;
+    auto rr = ld4(r, row);
+    auto dd = ld4(d, row);
+    auto xx = ld4(x, row);
+    rr.w = dinvS[row] * t;
+    dd.w = (T)cf->s_init * rr.w;
+    xx.w = dd.w;
+    st4(r, row, rr);
+    st4(d, row, dd);
+    st4(x, row, xx);
+  }
+}
+
+// z.xyz = x.xyz - dinvF (G x.w), z.w = x.w
+template <class S, class T>
+__global__ void __launch_bounds__(kThreads) final_kernel(BsrView<S> A, const T *dinvF, const T *x, T *z,
+                                                         const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  T acc[3] = {T(0), T(0), T(0)};
+  if (row < A.V) {
+    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+      const S *blk = A.vals + 16 * (int64_t)kb;
+      const T p = ld4(x, A.col[kb]).w;
+      acc[0] += (T)blk[3] * p;
+      acc[1] += (T)blk[7] * p;
+      acc[2] += (T)blk[11] * p;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) acc[i] = group_sum(acc[i]);
+  if (row < A.V && lane == 0) {
+    const auto df = ld4(dinvF, row);
+    auto xx = ld4(x, row);
+    typename Vec4T<T>::type o;
+    o.x = xx.x - df.x * acc[0];
+    o.y = xx.y - df.y * acc[1];
+    o.z = xx.z - df.z * acc[2];
+    o.w = xx.w;
+    st4(z, row, o);
+  }
+}
+
+// power iteration helpers: v = (1/sqrt(n)) on the selected components; v = y / lambda
+template <class T>
+__global__ void fill_kernel(int64_t V, T *v, int comp_mask, double val) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+    auto o = ld4(v, i);
+    if (comp_mask & 1) o.x = (T)val;
+    if (comp_mask & 2) o.y = (T)val;
+    if (comp_mask & 4) o.z = (T)val;
+    if (comp_mask & 8) o.w = (T)val;
+    st4(v, i, o);
+  }
+}
+template <class T>
+__global__ void div_kernel(int64_t V, const T *y, T *v, int comp_mask, const double *lam) {
+  const double il = 1.0 / *lam;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+    const auto a = ld4(y, i);
+    auto o = ld4(v, i);
+    if (comp_mask & 1) o.x = (T)((double)a.x * il);
+    if (comp_mask & 2) o.y = (T)((double)a.y * il);
+    if (comp_mask & 4) o.z = (T)((double)a.z * il);
+    if (comp_mask & 8) o.w = (T)((double)a.w * il);
+    st4(v, i, o);
+  }
+}
+
+// Chebyshev coefficients (Saad, Chebyshev acceleration) from lambda_max estimates, or the
+// constant Jacobi ones.
+__global__ void coef_kernel(SmoothCoef *cf, int f_kind, int f_steps, double f_omega, double f_ratio,
+                            int s_kind, int s_steps, double s_omega, double s_ratio) {
+  if (threadIdx.x != 0) return;
+  for (int which = 0; which < 2; ++which) {
+    const int kind = which ? s_kind : f_kind;
+    const int steps = which ? s_steps : f_steps;
+    const double omega = which ? s_omega : f_omega, ratio = which ? s_ratio : f_ratio;
+    double *c1 = which ? cf->s_c1 : cf->f_c1;
+    double *c2 = which ? cf->s_c2 : cf->f_c2;
+    double init;
+    if (kind == LFX_SMOOTH_JACOBI) {
+      init = omega;
+      for (int k = 0; k < steps; ++k) {
+        c1[k] = 0.0;
+        c2[k] = omega;
+      }
+    } else {
+      const double lmax = 1.1 * (which ? cf->lam_s : cf->lam_f);
+      const double lmin = lmax / ratio;
+      const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+      const double sigma1 = theta / delta;
+      double rho = 1.0 / sigma1;
+      init = 1.0 / theta;
+      c1[0] = 0.0;
+      c2[0] = 0.0;
+      for (int k = 1; k < steps; ++k) {
+        const double rn = 1.0 / (2.0 * sigma1 - rho);
+        c1[k] = rn * rho;
+        c2[k] = 2.0 * rn / delta;
+        rho = rn;
+      }
+    }
+    if (which) cf->s_init = init;
+    else cf->f_init = init;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Krylov kernels
+// ------------------------------------------------------------------------------------------
+// part[blk][i] = sum over this CTA's range of w . v_i, i < nvec
+template <class T>
+__global__ void __launch_bounds__(kThreads) mdot_kernel(const T *Vb, int64_t ld, int nvec, const T *w,
+                                                        int64_t n, double *part, int ldp,
+                                                        const KState *st) {
+  if (finished(st)) return;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  for (int v0 = 0; v0 < nvec; v0 += 8) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int nv = min(8, nvec - v0);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const double wi = (double)w[i];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < nv) acc[k] += wi * (double)Vb[(int64_t)(v0 + k) * ld + i];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (k < nv) {
+        double s = cta_sum(acc[k]);
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * ldp + v0 + k] = s;
+      }
+    }
+  }
+}
+
+// h[i] = sum_blk part[blk][i]; hcol[i] (+)= h[i]; hwork[i] = h[i]
+__global__ void mdot_finalize_kernel(const double *part, int nblk, int ldp, int nvec, KState *st,
+                                     int accumulate) {
+  if (finished(st)) return;
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * ldp + i];
+    st->hwork[i] = s;
+    st->hcol[i] = accumulate ? st->hcol[i] + s : s;
+  }
+}
+
+// w -= sum_i hwork[i] v_i ; partial |w|^2
+template <class T>
+__global__ void __launch_bounds__(kThreads) maxpy_kernel(const T *Vb, int64_t ld, int nvec, T *w,
+                                                         int64_t n, double *part, KState *st) {
+  if (finished(st)) return;
+  __shared__ double h[kMaxRestart + 1];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) h[i] = st->hwork[i];
+  __syncthreads();
+  double nrm = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double a = (double)w[i];
+    for (int k = 0; k < nvec; ++k) a -= h[k] * (double)Vb[(int64_t)k * ld + i];
+    w[i] = (T)a;
+    nrm += a * a;
+  }
+  double s = cta_sum(nrm);
+  if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
+}
+
+// Arnoldi column j: h_{j+1,j} = ||w||, Givens rotations, residual estimate, stopping test.
+__global__ void givens_kernel(const double *part, int nblk, KState *st, int j, int m, int maxit) {
+  if (finished(st)) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i];
+  s = cta_sum(s);
+  if (threadIdx.x != 0) return;
+  const double hn = sqrt(s);
+  double *H = st->H + (int64_t)j * (kMaxRestart + 1);
+  for (int i = 0; i <= j; ++i) H[i] = st->hcol[i];
+  H[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = st->cs[i] * H[i] + st->sn[i] * H[i + 1];
+    H[i + 1] = -st->sn[i] * H[i] + st->cs[i] * H[i + 1];
+    H[i] = t;
+  }
+  const double den = hypot(H[j], H[j + 1]);
+  double c = 1.0, sn = 0.0;
+  if (den > 0.0) {
+    c = H[j] / den;
+    sn = H[j + 1] / den;
+  }
+  st->cs[j] = c;
+  st->sn[j] = sn;
+  H[j] = den;
+  H[j + 1] = 0.0;
+  st->g[j + 1] = -sn * st->g[j];
+  st->g[j] = c * st->g[j];
+  const double res = fabs(st->g[j + 1]);
+  st->j = j + 1;
+  st->total += 1;
+  st->res = res;
+  st->scale = hn > 0.0 ? 1.0 / hn : 0.0;
+  if (!isfinite(res) || !isfinite(hn)) {
+    st->flag = 2;
+    st->done = 1;
+  } else if (res <= st->tol_abs || hn == 0.0) {
+    st->flag = 1;
+    st->done = 1;
+  } else if (j + 1 >= m || st->total >= maxit) {
+    st->done = 1;
+  }
+}
+
+template <class T>
+__global__ void norm_kernel(const T *v, int64_t n, double *part) {
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a += (double)v[i] * (double)v[i];
+  double s = cta_sum(a);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <class T>
+__global__ void scale_kernel(const T *w, T *v, int64_t n, const double *sc, const KState *st) {
+  if (finished(st)) return;
+  const double s = *sc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (T)((double)w[i] * s);
+}
+// variant used at the start of a cycle (no early exit): v0 = r / beta
+template <class T>
+__global__ void scale_beta_kernel(const T *w, T *v, int64_t n, const KState *st) {
+  const double b = st->beta;
+  const double s = b > 0.0 ? 1.0 / b : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (T)((double)w[i] * s);
+}
+
+// start of a cycle: beta = ||r||, g = (beta, 0, ...), j = 0, done if beta <= tol
+__global__ void cycle_start_kernel(const double *part, int nblk, KState *st) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i];
+  s = cta_sum(s);
+  if (threadIdx.x != 0) return;
+  const double beta = sqrt(s);
+  st->beta = beta;
+  st->g[0] = beta;
+  st->j = 0;
+  st->res = beta;
+  st->flag = 0;
+  st->done = 0;
+  if (!isfinite(beta)) {
+    st->flag = 2;
+    st->done = 1;
+  } else if (beta <= st->tol_abs) {
+    st->flag = 1;
+    st->done = 1;
+  }
+}
+
+// y = H(0:j,0:j)^-1 g(0:j) by back substitution (j = completed steps of this cycle)
+__global__ void trisolve_kernel(KState *st) {
+  if (threadIdx.x != 0) return;
+  const int j = st->j;
+  for (int i = j - 1; i >= 0; --i) {
+    double s = st->g[i];
+    for (int k = i + 1; k < j; ++k) s -= st->H[(int64_t)k * (kMaxRestart + 1) + i] * st->y[k];
+    st->y[i] = s / st->H[(int64_t)i * (kMaxRestart + 1) + i];
+  }
+}
+
+// x += sum_{i<j} y_i z_i
+template <class T, class X>
+__global__ void update_x_kernel(const T *Zb, int64_t ld, X *x, int64_t n, const KState *st) {
+  __shared__ double y[kMaxRestart];
+  const int j = st->j;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) y[i] = st->y[i];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double a = (double)x[i];
+    for (int k = 0; k < j; ++k) a += y[k] * (double)Zb[(int64_t)k * ld + i];
+    x[i] = (X)a;
+  }
+}
+
+inline int rows_grid(int64_t V) { return (int)((V * kRowGroup + kThreads - 1) / kThreads); }
+inline int vec_grid(int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
+}
+
+}  // namespace
+
+// ==========================================================================================
+// host side
+// ==========================================================================================
+template <class S, class T>
+lfx_status launch_spmv(cudaStream_t st, const BsrView<S> &A, const T *x, const T *b, T *y, int mode,
+                       double *part, int *n_part) {
+  const int g = rows_grid(A.V);
+  spmv_kernel<S, T><<<g, kThreads, 0, st>>>(A, x, b, y, mode, part, nullptr);
+  note_launches(1);
+  if (n_part) *n_part = g;
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+template lfx_status launch_spmv<double, double>(cudaStream_t, const BsrView<double> &, const double *,
+                                                const double *, double *, int, double *, int *);
+template lfx_status launch_spmv<float, float>(cudaStream_t, const BsrView<float> &, const float *,
+                                              const float *, float *, int, double *, int *);
+template lfx_status launch_spmv<float, double>(cudaStream_t, const BsrView<float> &, const double *,
+                                               const double *, double *, int, double *, int *);
+
+template <class S, class T>
+lfx_status ASimple<S, T>::init(int64_t V_, const SmootherConfig &cfg_) {
+  V = V_;
+  cfg = cfg_;
+  const size_t vb = sizeof(T) * 4 * (size_t)V;
+  LFX_TRY(dinvF.alloc(vb));
+  LFX_TRY(dinvS.alloc(sizeof(T) * (size_t)V));
+  LFX_TRY(X.alloc(vb));
+  LFX_TRY(D0.alloc(vb));
+  LFX_TRY(D1.alloc(vb));
+  LFX_TRY(R.alloc(vb));
+  LFX_TRY(W.alloc(vb));
+  LFX_TRY(coef.alloc(sizeof(SmoothCoef)));
+  LFX_TRY(part.alloc(sizeof(double) * (size_t)(rows_grid(V) + 1)));
+  LFX_CUDA_TRY(cudaMemset(X.p, 0, vb));
+  LFX_CUDA_TRY(cudaMemset(D0.p, 0, vb));
+  LFX_CUDA_TRY(cudaMemset(D1.p, 0, vb));
+  LFX_CUDA_TRY(cudaMemset(R.p, 0, vb));
+  LFX_CUDA_TRY(cudaMemset(W.p, 0, vb));
+  return LFX_OK;
+}
+
+template <class S, class T>
+size_t ASimple<S, T>::device_bytes() const {
+  return dinvF.bytes + dinvS.bytes + X.bytes + D0.bytes + D1.bytes + R.bytes + W.bytes + coef.bytes + part.bytes;
+}
+
+// Diagonals and (Chebyshev) eigenvalue estimates for the current matrix.
+template <class S, class T>
+lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
+  const int rg = rows_grid(V), vg = vec_grid(V);
+  diag_f_kernel<S, T><<<vg, kThreads, 0, st>>>(A, dinvF.as<T>());
+  diag_s_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>());
+  SmoothCoef *cf = coef.as<SmoothCoef>();
+  double *lam_f = &cf->lam_f, *lam_s = &cf->lam_s;
+  if (cfg.f_kind == LFX_SMOOTH_CHEBYSHEV) {
+    // power iteration on diag(F)^-1 F from the normalised ones vector (velocity components)
+    fill_kernel<T><<<vg, kThreads, 0, st>>>(V, D0.as<T>(), 7, 1.0 / sqrt(3.0 * (double)V));
+    for (int it = 0; it < cfg.n_power; ++it) {
+      f_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), D0.as<T>(), D1.as<T>(), nullptr,
+                                                   nullptr, cf, 0, 0, part.as<double>(), nullptr);
+      reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_f, 1);
+      div_kernel<T><<<vg, kThreads, 0, st>>>(V, D1.as<T>(), D0.as<T>(), 7, lam_f);
+    }
+  }
+  if (cfg.s_kind == LFX_SMOOTH_CHEBYSHEV) {
+    fill_kernel<T><<<vg, kThreads, 0, st>>>(V, D0.as<T>(), 8, 1.0 / sqrt((double)V));
+    for (int it = 0; it < cfg.n_power; ++it) {
+      g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), D0.as<T>(), W.as<T>(), nullptr);
+      s_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), D0.as<T>(), W.as<T>(), D1.as<T>(),
+                                                   nullptr, nullptr, cf, 0, 0, part.as<double>(), nullptr);
+      reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_s, 1);
+      div_kernel<T><<<vg, kThreads, 0, st>>>(V, D1.as<T>(), D0.as<T>(), 8, lam_s);
+    }
+  }
+  note_launches(3 + (cfg.f_kind == LFX_SMOOTH_CHEBYSHEV ? 1 + 3 * cfg.n_power : 0) +
+                (cfg.s_kind == LFX_SMOOTH_CHEBYSHEV ? 1 + 4 * cfg.n_power : 0));
+  coef_kernel<<<1, 32, 0, st>>>(cf, cfg.f_kind, cfg.f_steps, cfg.f_omega, cfg.f_ratio, cfg.s_kind,
+                                cfg.s_steps, cfg.s_omega, cfg.s_ratio);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+// z = P^-1 r (aSIMPLE); r, z are [V][4] vectors of type T (they may not alias the work arrays).
+template <class S, class T>
+lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r, T *z, const KState *ks) {
+  const int rg = rows_grid(V), vg = vec_grid(V);
+  const SmoothCoef *cf = coef.as<SmoothCoef>();
+  T *d[2] = {D0.as<T>(), D1.as<T>()};
+  // z_u* ~= F^-1 r_u
+  f_init_kernel<T><<<vg, kThreads, 0, st>>>(V, dinvF.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks);
+  for (int k = 1; k < cfg.f_steps; ++k)
+    f_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], d[k & 1], R.as<T>(),
+                                                 X.as<T>(), cf, k, 1, nullptr, ks);
+  // z_p ~= S^-1 (r_p - D z_u*)
+  d_init_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks);
+  for (int k = 1; k < cfg.s_steps; ++k) {
+    g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
+    s_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
+                                                 R.as<T>(), X.as<T>(), cf, k, 1, nullptr, ks);
+  }
+  // z_u = z_u* - diag(F)^-1 G z_p
+  final_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), z, ks);
+  note_launches(3 + (cfg.f_steps - 1) + 2 * (cfg.s_steps - 1));
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+template <class S, class T>
+lfx_status ASimple<S, T>::lambdas(double *lf, double *ls) const {
+  SmoothCoef h;
+  LFX_CUDA_TRY(cudaMemcpy(&h, coef.p, sizeof(SmoothCoef), cudaMemcpyDeviceToHost));
+  if (lf) *lf = h.lam_f;
+  if (ls) *ls = h.lam_s;
+  return LFX_OK;
+}
+
+template struct ASimple<double, double>;
+template struct ASimple<float, float>;
+
+// ------------------------------------------------------------------------------------------
+template <class S, class T>
+lfx_status Gmres<S, T>::init(int64_t V_, int restart_) {
+  V = V_;
+  n = 4 * V;
+  restart = std::min(restart_, kMaxRestart);
+  if (restart < 1) restart = 1;
+  const size_t vb = sizeof(T) * (size_t)n;
+  LFX_TRY(basis.alloc(vb * (restart + 1)));
+  LFX_TRY(zbasis.alloc(vb * restart));
+  LFX_TRY(work.alloc(vb));
+  nblk_dot = 152 * 4;
+  LFX_TRY(part.alloc(sizeof(double) * (size_t)nblk_dot * (kMaxRestart + 1)));
+  LFX_TRY(part_n.alloc(sizeof(double) * (size_t)std::max(rows_grid(V), vec_grid(n)) + 64));
+  LFX_TRY(state.alloc(sizeof(KState)));
+  LFX_CUDA_TRY(cudaMemset(state.p, 0, sizeof(KState)));
+  LFX_CUDA_TRY(cudaMallocHost(&pinned, sizeof(int) * 8));
+  for (int i = 0; i < 4; ++i) LFX_CUDA_TRY(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+  return LFX_OK;
+}
+
+template <class S, class T>
+Gmres<S, T>::~Gmres() {
+  if (pinned) cudaFreeHost(pinned);
+  for (int i = 0; i < 4; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+}
+
+template <class S, class T>
+size_t Gmres<S, T>::device_bytes() const {
+  return basis.bytes + zbasis.bytes + work.bytes + part.bytes + part_n.bytes + state.bytes;
+}
+
+// Solve A x = b to ||b - A x|| <= rtol ||b|| from the x passed in.  Returns LFX_OK,
+// LFX_ERR_NOT_CONVERGED or LFX_ERR_NONFINITE; *its_out = Arnoldi steps, *res_out = final
+// relative residual (true residual of the last restart).
+template <class S, class T>
+lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, ASimple<S, T> &pc, const T *b, T *x,
+                              double rtol, int maxit, bool cgs2, int *its_out, double *res_out) {
+  KState *ks = state.as<KState>();
+  T *Vb = basis.as<T>(), *Zb = zbasis.as<T>(), *w = work.as<T>();
+  double *pn = part_n.as<double>();
+  const int vg = vec_grid(n);
+  // ||b||
+  norm_kernel<T><<<vg, kThreads, 0, st>>>(b, n, pn);
+  reduce_kernel<<<1, kThreads, 0, st>>>(pn, vg, &ks->bnorm, 1);
+  note_launches(2);
+  KState hs;
+  LFX_CUDA_TRY(cudaMemcpyAsync(&hs, ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+  LFX_CUDA_TRY(cudaStreamSynchronize(st));
+  const double bnorm = hs.bnorm;
+  if (!std::isfinite(bnorm)) {
+    set_error("GMRES: right-hand side is not finite");
+    return LFX_ERR_NONFINITE;
+  }
+  double tol_abs = rtol * bnorm;
+  LFX_CUDA_TRY(cudaMemcpyAsync(&ks->tol_abs, &tol_abs, sizeof(double), cudaMemcpyHostToDevice, st));
+  int zero = 0;
+  LFX_CUDA_TRY(cudaMemcpyAsync(&ks->total, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+  int total = 0;
+  double rel = 1.0;
+  lfx_status status = LFX_ERR_NOT_CONVERGED;
+  if (bnorm == 0.0) {
+    LFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
+    if (its_out) *its_out = 0;
+    if (res_out) *res_out = 0.0;
+    return LFX_OK;
+  }
+  for (int cycle = 0; cycle < 100000; ++cycle) {
+    // r = b - A x -> w, beta, v0 = r / beta
+    int ng = 0;
+    LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, pn, &ng)));
+    cycle_start_kernel<<<1, kThreads, 0, st>>>(pn, ng, ks);
+    scale_beta_kernel<T><<<vg, kThreads, 0, st>>>(w, Vb, n, ks);
+    note_launches(2);
+    int launched = 0;
+    for (int j = 0; j < restart; ++j) {
+      T *vj = Vb + (int64_t)j * n, *vn = Vb + (int64_t)(j + 1) * n, *zj = Zb + (int64_t)j * n;
+      LFX_TRY(pc.apply(st, A, vj, zj, ks));
+      spmv_kernel<S, T><<<rows_grid(V), kThreads, 0, st>>>(A, zj, nullptr, w, 0, nullptr, ks);
+      for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
+        mdot_kernel<T><<<nblk_dot, kThreads, 0, st>>>(Vb, n, j + 1, w, n, part.as<double>(), kMaxRestart + 1, ks);
+        mdot_finalize_kernel<<<1, 64, 0, st>>>(part.as<double>(), nblk_dot, kMaxRestart + 1, j + 1, ks, pass);
+        maxpy_kernel<T><<<vg, kThreads, 0, st>>>(Vb, n, j + 1, w, n, pn, ks);
+      }
+      givens_kernel<<<1, kThreads, 0, st>>>(pn, vg, ks, j, restart, maxit);
+      scale_kernel<T><<<vg, kThreads, 0, st>>>(w, vn, n, &ks->scale, ks);
+      note_launches(3 + 3 * (cgs2 ? 2 : 1));
+      LFX_CUDA_TRY(cudaMemcpyAsync(pinned + (j & 3), &ks->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+      LFX_CUDA_TRY(cudaEventRecord(ev[j & 3], st));
+      launched = j + 1;
+      // lagged convergence test: the device runs at most two steps behind the host
+      if (j >= 2) {
+        LFX_CUDA_TRY(cudaEventSynchronize(ev[(j - 2) & 3]));
+        if (pinned[(j - 2) & 3]) break;
+      }
+    }
+    (void)launched;
+    trisolve_kernel<<<1, 32, 0, st>>>(ks);
+    update_x_kernel<T, T><<<vg, kThreads, 0, st>>>(Zb, n, x, n, ks);
+    note_launches(2);
+    LFX_CUDA_TRY(cudaMemcpyAsync(&hs, ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    LFX_CUDA_TRY(cudaStreamSynchronize(st));
+    LFX_CUDA_TRY(cudaGetLastError());
+    total = hs.total;
+    if (hs.flag == 2) {
+      set_error("GMRES: non-finite residual after %d steps", total);
+      status = LFX_ERR_NONFINITE;
+      break;
+    }
+    if (hs.flag == 1 || total >= maxit) {
+      // confirm with the true residual
+      LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, pn, &ng)));
+      reduce_kernel<<<1, kThreads, 0, st>>>(pn, ng, &ks->res, 1);
+      note_launches(1);
+      double tr = 0.0;
+      LFX_CUDA_TRY(cudaMemcpyAsync(&tr, &ks->res, sizeof(double), cudaMemcpyDeviceToHost, st));
+      LFX_CUDA_TRY(cudaStreamSynchronize(st));
+      rel = tr / bnorm;
+      if (!std::isfinite(rel)) {
+        status = LFX_ERR_NONFINITE;
+        set_error("GMRES: non-finite true residual");
+        break;
+      }
+      if (tr <= 2.0 * tol_abs) {
+        status = LFX_OK;
+        break;
+      }
+      if (total >= maxit) {
+        set_error("GMRES: not converged after %d steps (relative residual %.3e)", total, rel);
+        status = LFX_ERR_NOT_CONVERGED;
+        break;
+      }
+    }
+  }
+  if (its_out) *its_out = total;
+  if (res_out) *res_out = rel;
+  return status;
+}
+
+template struct Gmres<double, double>;
+template struct Gmres<float, float>;
+
+}  // namespace lfx

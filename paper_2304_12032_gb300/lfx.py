@@ -1,0 +1,398 @@
+"""Thin ctypes binding of liblfx (include/lfx.h): the same entry points under the same names,
+argument marshalling only.  Every step of the computation runs in the library's CUDA kernels;
+there is no Python or CPU fallback: if the library is missing, importing the handles raises.
+
+PyTorch is used only as plumbing: its CUDA caching allocator can back the library's device
+allocations (``use_torch_allocator``) and its current stream can be handed to a state.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblfx.so")
+_lib = None
+
+# ----------------------------------------------------------------------------- C structs
+MAX_FOURIER = 16
+(LFX_OK, LFX_ERR_INVALID_ARG, LFX_ERR_BAD_MESH, LFX_ERR_OOM, LFX_ERR_NOT_CONVERGED,
+ LFX_ERR_NONFINITE, LFX_ERR_CUDA, LFX_ERR_TIMEOUT, LFX_ERR_BUDGET) = (0, -1, -2, -3, -4, -5, -6, -7, -8)
+TIME = {"constant": 0, "pulsatile": 1, "ramp": 2, "fourier": 3}
+KIND = {"noslip": 0, "dirichlet": 1, "nodal": 2, "neumann": 3}
+PROFILE = {"uniform": 0, "parabolic": 1, "womersley": 2}
+PREC = {"fp64": 0, "mixed": 1}
+SMOOTH = {"jacobi": 0, "chebyshev": 1}
+
+
+class lfx_time_law(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_harmonics", ctypes.c_int32), ("p", ctypes.c_double * 4),
+                ("a", ctypes.c_double * (MAX_FOURIER + 1)), ("b", ctypes.c_double * (MAX_FOURIER + 1))]
+
+
+class lfx_bc(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_int32), ("kind", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("given_geometry", ctypes.c_int32), ("time", lfx_time_law), ("theta", ctypes.c_double),
+                ("radius", ctypes.c_double), ("center", ctypes.c_double * 3), ("normal", ctypes.c_double * 3)]
+
+
+class lfx_riis(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad", ctypes.c_int32), ("resistance", ctypes.c_double),
+                ("eps", ctypes.c_double), ("center", ctypes.c_double * 3), ("normal", ctypes.c_double * 3),
+                ("radius", ctypes.c_double), ("sdf_nodal", ctypes.POINTER(ctypes.c_double))]
+
+
+class lfx_options(ctypes.Structure):
+    _fields_ = [("stab", ctypes.c_int32), ("diffusion", ctypes.c_int32), ("c_r", ctypes.c_double),
+                ("f", ctypes.c_double * 3), ("pin_pressure_node", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("gmres_restart", ctypes.c_int32), ("gmres_max_iters", ctypes.c_int32),
+                ("gmres_rtol", ctypes.c_double), ("reorthogonalize", ctypes.c_int32),
+                ("f_smoother", ctypes.c_int32), ("f_steps", ctypes.c_int32),
+                ("f_omega", ctypes.c_double), ("f_ratio", ctypes.c_double),
+                ("s_smoother", ctypes.c_int32), ("s_steps", ctypes.c_int32),
+                ("s_omega", ctypes.c_double), ("s_ratio", ctypes.c_double), ("n_power", ctypes.c_int32),
+                ("smoother_bf16", ctypes.c_int32), ("outer_restart", ctypes.c_int32),
+                ("outer_max_iters", ctypes.c_int32), ("inner_rtol", ctypes.c_double),
+                ("inner_max_iters", ctypes.c_int32), ("bad_element_quality", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class lfx_mesh_info(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_tets", ctypes.c_int64), ("n_bfaces", ctypes.c_int64),
+                ("nnz_blocks", ctypes.c_int64), ("n_colors", ctypes.c_int32), ("n_flipped", ctypes.c_int32),
+                ("max_color_size", ctypes.c_int32), ("min_color_size", ctypes.c_int32),
+                ("n_bad_elements", ctypes.c_int64)]
+
+
+class lfx_step_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("t", ctypes.c_double), ("ms_assembly", ctypes.c_float),
+                ("ms_solve", ctypes.c_float), ("ms_total", ctypes.c_float), ("converged", ctypes.c_int32),
+                ("ms_assembly_kernels", ctypes.c_float), ("n_assembly_launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_P = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int32)
+_LP = ctypes.POINTER(ctypes.c_int64)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_SIGS = {
+    "lfx_last_error": ([], ctypes.c_char_p),
+    "lfx_sizeof": ([ctypes.c_char_p], ctypes.c_int64),
+    "lfx_launch_count": ([], ctypes.c_int64),
+    "lfx_mesh_create": ([_DP, ctypes.c_int64, _IP, ctypes.c_int64, _IP, _IP, ctypes.c_int64,
+                         ctypes.POINTER(_P)], ctypes.c_int32),
+    "lfx_mesh_destroy": ([_P], None),
+    "lfx_mesh_get_info": ([_P, ctypes.POINTER(lfx_mesh_info)], ctypes.c_int32),
+    "lfx_mesh_get_pattern": ([_P, _LP, _IP], ctypes.c_int32),
+    "lfx_mesh_get_colors": ([_P, _IP], ctypes.c_int32),
+    "lfx_options_default": ([ctypes.POINTER(lfx_options)], None),
+    "lfx_problem_create": ([_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                            ctypes.POINTER(lfx_bc), ctypes.c_int32, ctypes.POINTER(lfx_riis), ctypes.c_int32,
+                            ctypes.POINTER(lfx_options), ctypes.POINTER(_P)], ctypes.c_int32),
+    "lfx_problem_destroy": ([_P], None),
+    "lfx_state_create": ([_P, _DP, _DP, ctypes.c_double, ctypes.POINTER(_P)], ctypes.c_int32),
+    "lfx_state_destroy": ([_P], None),
+    "lfx_set_stream": ([_P, _P], ctypes.c_int32),
+    "lfx_set_dirichlet_nodal": ([_P, ctypes.c_int32, _DP], ctypes.c_int32),
+    "lfx_set_pressure_pin": ([_P, ctypes.c_double], ctypes.c_int32),
+    "lfx_step": ([_P, ctypes.POINTER(lfx_step_stats)], ctypes.c_int32),
+    "lfx_state_get": ([_P, _DP, _DP], ctypes.c_int32),
+    "lfx_state_set": ([_P, _DP, _DP, ctypes.c_double], ctypes.c_int32),
+    "lfx_debug_assemble": ([_P, ctypes.c_int32, _DP, _DP], ctypes.c_int32),
+    "lfx_debug_spmv": ([_P, _DP, _DP], ctypes.c_int32),
+    "lfx_debug_precond": ([_P, _DP, _DP, _DP, _DP], ctypes.c_int32),
+    "lfx_debug_solve": ([_P, _DP, ctypes.POINTER(lfx_step_stats)], ctypes.c_int32),
+    "lfx_set_allocator": ([ALLOC_FN, FREE_FN, _P], ctypes.c_int32),
+    "lfx_state_device_bytes": ([_P, _LP], ctypes.c_int32),
+}
+
+
+class LfxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"lfx status {status}: {msg}")
+        self.status = status
+
+
+def library():
+    """Load liblfx.so (built by paper_2304_12032_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"liblfx.so not built ({LIB_PATH}); run `python -m paper_2304_12032_gb300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def _check(status, allow=()):
+    if status != LFX_OK and status not in allow:
+        raise LfxError(status, library().lfx_last_error().decode())
+    return status
+
+
+def _d(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _i(a):
+    return a.ctypes.data_as(_IP)
+
+
+# ----------------------------------------------------------------------------- allocator hook
+_alloc_keepalive = []
+
+
+def use_torch_allocator():
+    """Back every later device allocation of the library with PyTorch's caching allocator."""
+    import torch
+
+    dev = torch.cuda.current_device()
+
+    def _alloc(nbytes, ctx):
+        return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+    _alloc_keepalive[:] = [fa, ff]
+    _check(library().lfx_set_allocator(fa, ff, None))
+
+
+def use_cuda_allocator():
+    _check(library().lfx_set_allocator(ALLOC_FN(), FREE_FN(), None))
+    _alloc_keepalive.clear()
+
+
+# ----------------------------------------------------------------------------- options / BCs
+def default_options(**kw) -> lfx_options:
+    o = lfx_options()
+    library().lfx_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PREC[v]
+        if k in ("f_smoother", "s_smoother") and isinstance(v, str):
+            v = SMOOTH[v]
+        if k == "f":
+            for i in range(3):
+                o.f[i] = v[i]
+            continue
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+@dataclasses.dataclass
+class BC:
+    """Python form of lfx_bc (Section 2.2)."""
+    tag: int
+    kind: str                       # noslip | dirichlet | nodal | neumann
+    profile: str = "uniform"        # uniform | parabolic | womersley
+    time: str = "constant"          # constant | pulsatile | ramp | fourier
+    p: Sequence[float] = (0.0,)     # time-law parameters (see lfx_time_law)
+    a: Sequence[float] = ()         # Fourier cosine coefficients a_0..a_K
+    b: Sequence[float] = ()         # Fourier sine coefficients (b_0 ignored)
+    theta: float = 1.0
+    radius: float = 1.0
+    center: Optional[Sequence[float]] = None
+    normal: Optional[Sequence[float]] = None
+
+    def c(self) -> lfx_bc:
+        s = lfx_bc()
+        s.tag, s.kind, s.profile = self.tag, KIND[self.kind], PROFILE[self.profile]
+        s.time.kind = TIME[self.time]
+        for i, v in enumerate(self.p):
+            s.time.p[i] = v
+        K = max(len(self.a), len(self.b)) - 1
+        s.time.n_harmonics = max(K, 0)
+        for i, v in enumerate(self.a):
+            s.time.a[i] = v
+        for i, v in enumerate(self.b):
+            s.time.b[i] = v
+        s.theta, s.radius = self.theta, self.radius
+        if self.center is not None and self.normal is not None:
+            s.given_geometry = 1
+            for i in range(3):
+                s.center[i], s.normal[i] = self.center[i], self.normal[i]
+        return s
+
+
+@dataclasses.dataclass
+class RIIS:
+    """Python form of lfx_riis: a disk (center, normal, radius) or nodal signed distances."""
+    resistance: float
+    eps: float
+    center: Sequence[float] = (0.0, 0.0, 0.0)
+    normal: Sequence[float] = (0.0, 0.0, 1.0)
+    radius: float = 1.0
+    sdf_nodal: Optional[np.ndarray] = None
+
+
+# ----------------------------------------------------------------------------- handles
+def lfx_mesh_create(nodes, tets, bfaces, btags):
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    bfaces = np.ascontiguousarray(bfaces, dtype=np.int32)
+    btags = np.ascontiguousarray(btags, dtype=np.int32)
+    h = _P()
+    _check(library().lfx_mesh_create(_d(nodes), nodes.shape[0], _i(tets), tets.shape[0], _i(bfaces), _i(btags),
+                                     bfaces.shape[0], ctypes.byref(h)))
+    return h
+
+
+class Mesh:
+    def __init__(self, nodes, tets, bfaces, btags):
+        self.n_nodes = int(np.asarray(nodes).shape[0])
+        self.h = lfx_mesh_create(nodes, tets, bfaces, btags)
+
+    @classmethod
+    def from_synthetic(cls, m):
+        return cls(m.nodes, m.tets, m.bfaces, m.btags)
+
+    def info(self) -> dict:
+        i = lfx_mesh_info()
+        _check(library().lfx_mesh_get_info(self.h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def pattern(self):
+        inf = self.info()
+        rp = np.zeros(inf["n_nodes"] + 1, dtype=np.int64)
+        ci = np.zeros(inf["nnz_blocks"], dtype=np.int32)
+        _check(library().lfx_mesh_get_pattern(self.h, rp.ctypes.data_as(_LP), _i(ci)))
+        return rp, ci
+
+    def colors(self):
+        c = np.zeros(self.info()["n_tets"], dtype=np.int32)
+        _check(library().lfx_mesh_get_colors(self.h, _i(c)))
+        return c
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lfx_mesh_destroy(self.h)
+            self.h = None
+
+
+class Problem:
+    def __init__(self, mesh: Mesh, rho, mu, dt, bdf_order, bcs: Sequence[BC], riis: Sequence[RIIS] = (),
+                 options: Optional[lfx_options] = None):
+        self.mesh = mesh
+        arr = (lfx_bc * max(1, len(bcs)))(*[b.c() for b in bcs])
+        self._sdf = []
+        rarr = (lfx_riis * max(1, len(riis)))()
+        for k, r in enumerate(riis):
+            s = rarr[k]
+            s.resistance, s.eps, s.radius = r.resistance, r.eps, r.radius
+            for i in range(3):
+                s.center[i], s.normal[i] = r.center[i], r.normal[i]
+            if r.sdf_nodal is not None:
+                a = np.ascontiguousarray(r.sdf_nodal, dtype=np.float64)
+                self._sdf.append(a)
+                s.kind, s.sdf_nodal = 1, _d(a)
+        self.options = options if options is not None else default_options()
+        self.bdf_order = bdf_order
+        self.h = _P()
+        _check(library().lfx_problem_create(mesh.h, rho, mu, dt, bdf_order, arr, len(bcs), rarr, len(riis),
+                                            ctypes.byref(self.options), ctypes.byref(self.h)))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lfx_problem_destroy(self.h)
+            self.h = None
+
+
+class State:
+    def __init__(self, problem: Problem, u_hist, p_hist, t0=0.0, stream=None):
+        self.problem = problem
+        V = problem.mesh.n_nodes
+        u = np.ascontiguousarray(np.asarray(u_hist, dtype=np.float64).reshape(problem.bdf_order, V, 3))
+        p = np.ascontiguousarray(np.asarray(p_hist, dtype=np.float64).reshape(problem.bdf_order, V))
+        self.V = V
+        self.h = _P()
+        _check(library().lfx_state_create(problem.h, _d(u), _d(p), t0, ctypes.byref(self.h)))
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_stream(self, stream):
+        ptr = getattr(stream, "cuda_stream", stream)
+        _check(library().lfx_set_stream(self.h, ctypes.c_void_p(int(ptr) if ptr else 0)))
+
+    def set_dirichlet_nodal(self, tag, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        _check(library().lfx_set_dirichlet_nodal(self.h, tag, _d(u)))
+
+    def set_pressure_pin(self, value):
+        _check(library().lfx_set_pressure_pin(self.h, float(value)))
+
+    def step(self, allow_not_converged=False) -> dict:
+        st = lfx_step_stats()
+        rc = library().lfx_step(self.h, ctypes.byref(st))
+        _check(rc, allow=(LFX_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+    def set(self, u_hist, p_hist, t):
+        u = np.ascontiguousarray(np.asarray(u_hist, dtype=np.float64).reshape(self.problem.bdf_order, self.V, 3))
+        p = np.ascontiguousarray(np.asarray(p_hist, dtype=np.float64).reshape(self.problem.bdf_order, self.V))
+        _check(library().lfx_state_set(self.h, _d(u), _d(p), float(t)))
+
+    def get(self):
+        u = np.zeros((self.V, 3))
+        p = np.zeros(self.V)
+        _check(library().lfx_state_get(self.h, _d(u), _d(p)))
+        return u, p
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_int64()
+        _check(library().lfx_state_device_bytes(self.h, ctypes.byref(b)))
+        return b.value
+
+    # ---- building blocks, for parity tests
+    def debug_assemble(self, apply_bcs=True):
+        nnzb = self.problem.mesh.info()["nnz_blocks"]
+        blocks = np.zeros((nnzb, 4, 4))
+        rhs = np.zeros((self.V, 4))
+        _check(library().lfx_debug_assemble(self.h, int(apply_bcs), _d(blocks), _d(rhs)))
+        return blocks, rhs
+
+    def debug_spmv(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.V, 4)
+        y = np.zeros((self.V, 4))
+        _check(library().lfx_debug_spmv(self.h, _d(x), _d(y)))
+        return y
+
+    def debug_precond(self, r):
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(self.V, 4)
+        z = np.zeros((self.V, 4))
+        lf, ls = ctypes.c_double(), ctypes.c_double()
+        _check(library().lfx_debug_precond(self.h, _d(r), _d(z), ctypes.byref(lf), ctypes.byref(ls)))
+        return z, lf.value, ls.value
+
+    def debug_solve(self, allow_not_converged=False):
+        x = np.zeros((self.V, 4))
+        st = lfx_step_stats()
+        rc = library().lfx_debug_solve(self.h, _d(x), ctypes.byref(st))
+        _check(rc, allow=(LFX_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return x, st.as_dict()
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lfx_state_destroy(self.h)
+            self.h = None
