@@ -96,10 +96,26 @@ def gpu_problem(L, m, precision):
     bcs = [L.BC(tag=0, kind="noslip"),
            L.BC(tag=1, kind="dirichlet", profile="parabolic", time="ramp", p=(0.0, Q, 0.0, RAMP), radius=R_CM),
            L.BC(tag=2, kind="neumann", time="constant", p=(0.0,))]
-    opts = L.default_options(precision=precision, gmres_rtol=1e-8)
+    extra = dict(smoother_bf16=1) if precision == "mixed" else {}
+    opts = L.default_options(precision=precision, gmres_rtol=1e-8, **extra)
     mesh = L.Mesh.from_synthetic(m)
     prob = L.Problem(mesh, RHO, MU, DT, 2, bcs, [], opts)
     return mesh, prob
+
+
+def timed_steps(L, st, steps, warmup, stream):
+    import torch
+
+    for _ in range(warmup):
+        st.step(allow_not_converged=True)
+    torch.cuda.synchronize()
+    n0 = L.library().lfx_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [st.step(allow_not_converged=True) for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), stats, L.library().lfx_launch_count() - n0
 
 
 def run_gpu(args):
@@ -120,58 +136,56 @@ def run_gpu(args):
 
         dist.init_process_group("nccl")
     m, tgen = make_case(args.tets, seed=2 + rank)
-    mesh, prob = gpu_problem(L, m, args.precision)
     V = m.n_nodes
-    zero_u, zero_p = np.zeros((2, V, 3)), np.zeros((2, V))
-    st = L.State(prob, zero_u, zero_p, 0.0)
     stream = torch.cuda.current_stream()
-    st.set_stream(stream)
-    info = mesh.info()
+    # common starting state: the FP64 path run through the warm-up steps from rest
+    mesh64, prob64 = gpu_problem(L, m, "fp64")
+    st64 = L.State(prob64, np.zeros((2, V, 3)), np.zeros((2, V)), 0.0, stream=stream)
     for _ in range(args.warmup):
-        st.step(allow_not_converged=True)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = Clocks()
-    clocks.start()
-    n0 = L.library().lfx_launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    stats = []
-    for _ in range(args.steps):
-        stats.append(st.step(allow_not_converged=True))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    launches = L.library().lfx_launch_count() - n0
-    clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+        st64.step(allow_not_converged=True)
+    u1, p1 = st64.get()
+    # history level 1 from a second FP64 step snapshot is not kept by the API: restart BDF2 from
+    # two copies of the warm state
+    hist_u, hist_p, t_start = np.stack([u1, u1]), np.stack([p1, p1]), args.warmup * DT
+    results = {}
+    for prec in (["mixed", "fp64"] if args.precision == "both" else [args.precision]):
+        mesh, prob = (mesh64, prob64) if prec == "fp64" else gpu_problem(L, m, prec)
+        st = L.State(prob, hist_u, hist_p, t_start, stream=stream)
+        if dist:
+            dist.barrier()
+        clocks = Clocks()
+        clocks.start()
+        ms, stats, launches = timed_steps(L, st, args.steps, 1, stream)
+        clk = clocks.stop()
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        u, p = st.get()
+        results[prec] = dict(ms=ms, stats=stats, launches=launches, clocks=clk, u=u, p=p, st=st, mesh=mesh)
+    prim = results["mixed"] if "mixed" in results else results[args.precision]
+    prim_prec = "mixed" if "mixed" in results else args.precision
+    info = prim["mesh"].info()
+    st = prim["st"]
     # ---- end to end through the public API: host history in, solution out, every step
-    u_host, p_host = st.get()
-    hist_u = np.stack([u_host, u_host])
-    hist_p = np.stack([p_host, p_host])
-    t_now = stats[-1]["t"]
+    u_host, p_host = prim["u"], prim["p"]
+    hu, hp = np.stack([u_host, u_host]), np.stack([p_host, p_host])
+    t_now = prim["stats"][-1]["t"]
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     for k in range(args.steps):
-        st.set(hist_u, hist_p, t_now)
+        st.set(hu, hp, t_now)
         st.step(allow_not_converged=True)
         u_host, p_host = st.get()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - w0) * 1e3 / args.steps
-    h2d = 2 * V * 4 * 8
-    d2h = V * 4 * 8
+    h2d, d2h = 2 * V * 4 * 8, V * 4 * 8
     # ---- dominant kernel: the coloured assembly kernel (live CUDA-event time, per launch)
+    stats = prim["stats"]
     asm_ms = sum(s["ms_assembly_kernels"] for s in stats) / len(stats)
     n_asm = stats[0]["n_assembly_launches"]
     T, nnzb = info["n_tets"], info["nnz_blocks"]
-    sv = 8 if args.precision == "fp64" else 4
-    alg_bytes = 16 * T + V * (3 * 8 + 8 * 8) + nnzb * 16 * sv + 4 * V * 8
+    alg_bytes = 16 * T + V * (3 * 8 + 8 * 8) + nnzb * 16 * 8 + 4 * V * 8
     peaks, src = _peaks()
     achieved = alg_bytes / (asm_ms * 1e-3) / 1e9
     roof = {"kernel": "assemble_color_kernel (all colours of one step)", "bound": "hbm",
@@ -180,28 +194,40 @@ def run_gpu(args):
             "peak_source": src, "ms_per_step": round(asm_ms, 4), "launches_per_step": n_asm,
             "algorithmic_bytes": int(alg_bytes)}
     its = [s["iterations"] for s in stats]
+    ms = prim["ms"]
     value = world * args.steps / (ms * 1e-3)
     line = {
         "metric": "time steps/s at 1M P1 tets (BDF2 VMS-LES step: assembly + aSIMPLE-GMRES)",
         "value": round(value, 3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "dtype": "f64" if prim_prec == "fp64" else "f32+f64",
         "data": "synthetic (seeded jittered-BCC Delaunay cylinder; no paper meshes available)",
         "config": {"workload": f"poiseuille_cylinder_{T}_tets", "n_tets": T, "n_nodes": V, "nnz_blocks": nnzb,
-                   "n_colors": info["n_colors"], "precision": args.precision, "bdf_order": 2, "dt": DT,
-                   "gmres_rtol": 1e-8, "gmres_iterations_mean": statistics.mean(its),
-                   "gmres_iterations": its, "l2": "inputs larger than L2 (matrix %.0f MB > 129 MB)" %
-                   (nnzb * 16 * sv / 1e6), "mesh_gen_s": round(tgen, 1)},
+                   "n_colors": info["n_colors"], "precision": prim_prec, "bdf_order": 2, "dt": DT,
+                   "gmres_rtol": 1e-8, "krylov_iterations_mean": statistics.mean(its),
+                   "outer_iterations_mean": statistics.mean(s["outer_iterations"] for s in stats),
+                   "l2": "inputs larger than L2 (FP64 matrix %.0f MB > 129 MB)" % (nnzb * 16 * 8 / 1e6),
+                   "mesh_gen_s": round(tgen, 1), "start": f"from rest, {args.warmup} FP64 warm-up steps"},
         "elements_per_s_assembly": round(T / (asm_ms * 1e-3), 1),
         "phase_ms": {"assembly": round(statistics.mean(s["ms_assembly"] for s in stats), 3),
                      "solve": round(statistics.mean(s["ms_solve"] for s in stats), 3)},
         "roofline": roof,
         "e2e": {"value": round(1e3 / e2e_ms * world, 3), "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
-        "clocks": clk,
+        "gpu_launches": int(prim["launches"]),
+        "clocks": prim["clocks"],
     }
+    if "fp64" in results and prim_prec != "fp64":
+        r64 = results["fp64"]
+        v64 = world * args.steps / (r64["ms"] * 1e-3)
+        du = np.linalg.norm(prim["u"] - r64["u"]) / np.linalg.norm(r64["u"])
+        dp = np.linalg.norm(prim["p"] - r64["p"]) / np.linalg.norm(r64["p"])
+        line["fp64_gpu"] = {"value": round(v64, 3), "unit": "steps/s", "ms_per_step": round(r64["ms"] / args.steps, 3),
+                            "krylov_iterations_mean": statistics.mean(s["iterations"] for s in r64["stats"]),
+                            "gpu_launches": int(r64["launches"])}
+        line["speedup_mixed_vs_fp64"] = round(value / v64, 3)
+        line["mixed_vs_fp64_rel_l2_after_steps"] = {"u": float(du), "p": float(dp)}
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_tets)
     if rank == 0:
@@ -275,7 +301,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--tets", type=int, default=1_000_000)
     ap.add_argument("--cpu-sample-tets", type=int, default=40_000)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -136,7 +136,10 @@ typedef struct lfx_riis {
 } lfx_riis;
 
 enum { LFX_PREC_FP64 = 0, LFX_PREC_MIXED = 1 };
-enum { LFX_SMOOTH_JACOBI = 0, LFX_SMOOTH_CHEBYSHEV = 1 };
+/* Smoothers of the aSIMPLE blocks.  LFX_SMOOTH_AMG (Schur block only): one V-cycle of a
+ * smoothed-aggregation AMG hierarchy of S = C - D diag(F)^-1 G, Chebyshev smoothing (s_steps
+ * pre and post) on every level, dense solve on the coarsest. */
+enum { LFX_SMOOTH_JACOBI = 0, LFX_SMOOTH_CHEBYSHEV = 1, LFX_SMOOTH_AMG = 2 };
 enum { LFX_STAB_NONE = 0, LFX_STAB_SUPG_PSPG = 1, LFX_STAB_VMS_LES = 2 };
 enum { LFX_DIFF_GRAD_GRAD = 0, LFX_DIFF_SYMGRAD_GRAD = 1, LFX_DIFF_SYMGRAD_SYMGRAD = 2 };
 
@@ -157,7 +160,7 @@ typedef struct lfx_options {
   /* aSIMPLE: velocity block F and Schur approximation S = C - D diag(F)^-1 G */
   int32_t f_smoother, f_steps;  /* LFX_SMOOTH_*, steps; default Chebyshev, 3                   */
   double f_omega, f_ratio;      /* Jacobi damping; Chebyshev lmax/lmin; default 0.7, 8         */
-  int32_t s_smoother, s_steps;  /* default Chebyshev, 6                                         */
+  int32_t s_smoother, s_steps;  /* default AMG with 2 Chebyshev steps pre and post              */
   double s_omega, s_ratio;      /* default 0.7, 30                                             */
   int32_t n_power;              /* power-iteration steps for lmax; default 10                  */
   /* mixed precision (LFX_PREC_MIXED) */
@@ -168,6 +171,11 @@ typedef struct lfx_options {
   int32_t inner_max_iters;      /* default 60                                                   */
   double bad_element_quality;   /* elements with 6 sqrt2 |K| / e_rms^3 below this keep FP64
                                    geometry in mixed assembly; default 0.1                       */
+  /* Schur AMG (s_smoother == LFX_SMOOTH_AMG) */
+  int32_t amg_refresh;          /* rebuild the hierarchy every this many steps (0 = build once) */
+  int32_t amg_coarse_size;      /* dense solve below this many unknowns; default 400           */
+  double amg_theta;             /* strength threshold on coarse levels; default 0.08           */
+  double amg_alpha;             /* scaling of the coarse correction; default 1.0               */
   int32_t reserved[8];
 } lfx_options;
 void lfx_options_default(lfx_options *opt);

@@ -107,7 +107,10 @@ class ASimple:
         dF = F.diagonal()
         self.dFinv = 1.0 / dF
         self.S = (C - D @ sp.diags(self.dFinv) @ G).tocsr()
-        self.dSinv = 1.0 / self.S.diagonal()
+        dS = self.S.diagonal()
+        # a vanishing diagonal of S (no pressure stabilisation, all velocity neighbours
+        # constrained) leaves that pressure unknown unsmoothed
+        self.dSinv = np.divide(1.0, dS, out=np.zeros_like(dS), where=dS != 0.0)
         self.lam_f = power_lambda_max(F, self.dFinv, opts.f.n_power) * 1.1 if opts.f.kind == "chebyshev" else None
         self.lam_s = power_lambda_max(self.S, self.dSinv, opts.s.n_power) * 1.1 if opts.s.kind == "chebyshev" else None
 

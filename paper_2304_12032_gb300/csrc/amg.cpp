@@ -1,0 +1,307 @@
+// Host set-up of a smoothed-aggregation algebraic multigrid hierarchy for the Schur
+// approximation S = C - D diag(F)^-1 G of the aSIMPLE preconditioner (Section 2.4 names AMG
+// as one of the approximations of the velocity and Schur blocks).  Built from the assembled
+// block matrix (downloaded once per set-up); applied on the device by the V-cycle in solver.cu.
+//
+// Steps: explicit S (distance-2 pattern); greedy aggregation (the mesh node graph on the
+// finest level, strength-filtered matrix graphs below); tentative piecewise-constant
+// prolongator smoothed by one damped Jacobi step, P = (I - w D^-1 A) P_tent,
+// w = 4 / (3 lambda_max(D^-1 A)); Galerkin coarse operators P^T A P; dense inverse at the
+// coarsest level.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "amg.h"
+
+namespace lfx {
+
+namespace {
+
+// C = A * B (Gustavson, dense marker)
+CsrHost multiply(const CsrHost &A, const CsrHost &B) {
+  CsrHost C;
+  C.n = A.n;
+  C.m = B.m;
+  C.rp.assign(A.n + 1, 0);
+  std::vector<int64_t> mark(B.m, -1);
+  std::vector<double> acc(B.m, 0.0);
+  std::vector<int32_t> cols;
+  for (int64_t i = 0; i < A.n; ++i) {
+    cols.clear();
+    for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+      const int32_t a = A.ci[k];
+      const double av = A.v[k];
+      for (int32_t q = B.rp[a]; q < B.rp[a + 1]; ++q) {
+        const int32_t c = B.ci[q];
+        if (mark[c] != i) {
+          mark[c] = i;
+          acc[c] = 0.0;
+          cols.push_back(c);
+        }
+        acc[c] += av * B.v[q];
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int32_t c : cols) {
+      C.ci.push_back(c);
+      C.v.push_back(acc[c]);
+    }
+    C.rp[i + 1] = (int32_t)C.ci.size();
+  }
+  return C;
+}
+
+CsrHost transpose(const CsrHost &A) {
+  CsrHost T;
+  T.n = A.m;
+  T.m = A.n;
+  T.rp.assign(A.m + 1, 0);
+  for (int32_t c : A.ci) T.rp[c + 1]++;
+  for (int64_t i = 0; i < A.m; ++i) T.rp[i + 1] += T.rp[i];
+  T.ci.resize(A.ci.size());
+  T.v.resize(A.v.size());
+  std::vector<int32_t> f(T.rp.begin(), T.rp.end() - 1);
+  for (int64_t i = 0; i < A.n; ++i)
+    for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+      const int32_t p = f[A.ci[k]]++;
+      T.ci[p] = (int32_t)i;
+      T.v[p] = A.v[k];
+    }
+  return T;
+}
+
+std::vector<double> diag_of(const CsrHost &A) {
+  std::vector<double> d(A.n, 0.0);
+  for (int64_t i = 0; i < A.n; ++i)
+    for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k)
+      if (A.ci[k] == i) d[i] += A.v[k];
+  return d;
+}
+
+std::vector<double> safe_inverse(const std::vector<double> &d) {
+  std::vector<double> r(d.size());
+  for (size_t i = 0; i < d.size(); ++i) r[i] = d[i] != 0.0 ? 1.0 / d[i] : 0.0;
+  return r;
+}
+
+// power iteration on D^-1 A from the normalised ones vector
+double lambda_max(const CsrHost &A, const std::vector<double> &dinv, int iters) {
+  std::vector<double> v(A.n, 1.0 / std::sqrt((double)A.n)), w(A.n);
+  double lam = 1.0;
+  for (int it = 0; it < iters; ++it) {
+    double nrm = 0.0;
+    for (int64_t i = 0; i < A.n; ++i) {
+      double s = 0.0;
+      for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) s += A.v[k] * v[A.ci[k]];
+      w[i] = dinv[i] * s;
+      nrm += w[i] * w[i];
+    }
+    lam = std::sqrt(nrm);
+    if (!(lam > 0)) return 1.0;
+    for (int64_t i = 0; i < A.n; ++i) v[i] = w[i] / lam;
+  }
+  return lam;
+}
+
+// Greedy aggregation: a node whose neighbours are all free starts an aggregate with them;
+// remaining nodes join a neighbouring aggregate, or start their own.
+int64_t aggregate(int64_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                  std::vector<int32_t> &agg) {
+  agg.assign(n, -1);
+  int64_t na = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (agg[i] >= 0) continue;
+    bool free_all = true;
+    for (int32_t k = rp[i]; k < rp[i + 1] && free_all; ++k)
+      if (agg[ci[k]] >= 0) free_all = false;
+    if (!free_all) continue;
+    agg[i] = (int32_t)na;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) agg[ci[k]] = (int32_t)na;
+    ++na;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (agg[i] >= 0) continue;
+    int32_t a = -1;
+    for (int32_t k = rp[i]; k < rp[i + 1] && a < 0; ++k)
+      if (agg[ci[k]] >= 0) a = agg[ci[k]];
+    agg[i] = a >= 0 ? a : (int32_t)na++;
+  }
+  return na;
+}
+
+// strong-connection graph |a_ij| >= theta sqrt(|a_ii a_jj|), i != j
+void strength_graph(const CsrHost &A, const std::vector<double> &d, double theta, std::vector<int32_t> &rp,
+                    std::vector<int32_t> &ci) {
+  rp.assign(A.n + 1, 0);
+  ci.clear();
+  for (int64_t i = 0; i < A.n; ++i) {
+    for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+      const int32_t j = A.ci[k];
+      if (j == i) continue;
+      if (std::fabs(A.v[k]) >= theta * std::sqrt(std::fabs(d[i] * d[j]))) ci.push_back(j);
+    }
+    rp[i + 1] = (int32_t)ci.size();
+  }
+}
+
+}  // namespace
+
+// Explicit S = C - D diag(F)^-1 G from 4x4 blocks (row-major, [i][j], F = [0..2][0..2],
+// G = [0..2][3], D = [3][0..2], C = [3][3]).
+CsrHost schur_explicit(int64_t V, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                       const std::vector<int32_t> &diag, const double *vals) {
+  std::vector<double> dinvF(3 * V);
+  for (int64_t b = 0; b < V; ++b)
+    for (int j = 0; j < 3; ++j) {
+      const double f = vals[16 * (int64_t)diag[b] + 5 * j];
+      dinvF[3 * b + j] = f != 0.0 ? 1.0 / f : 0.0;
+    }
+  CsrHost S;
+  S.n = S.m = V;
+  S.rp.assign(V + 1, 0);
+  std::vector<int64_t> mark(V, -1);
+  std::vector<double> acc(V, 0.0);
+  std::vector<int32_t> cols;
+  for (int64_t a = 0; a < V; ++a) {
+    cols.clear();
+    auto add = [&](int32_t c, double val) {
+      if (mark[c] != a) {
+        mark[c] = a;
+        acc[c] = 0.0;
+        cols.push_back(c);
+      }
+      acc[c] += val;
+    };
+    for (int32_t k = rp[a]; k < rp[a + 1]; ++k) {
+      const int32_t b = ci[k];
+      const double *blk = vals + 16 * (int64_t)k;
+      add(b, blk[15]);
+      for (int j = 0; j < 3; ++j) {
+        const double d = blk[12 + j] * dinvF[3 * b + j];
+        if (d == 0.0) continue;
+        for (int32_t k2 = rp[b]; k2 < rp[b + 1]; ++k2) {
+          const double g = vals[16 * (int64_t)k2 + 4 * j + 3];
+          if (g != 0.0) add(ci[k2], -d * g);
+        }
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int32_t c : cols) {
+      S.ci.push_back(c);
+      S.v.push_back(acc[c]);
+    }
+    S.rp[a + 1] = (int32_t)S.ci.size();
+  }
+  return S;
+}
+
+lfx_status amg_setup_host(const CsrHost &S0, const std::vector<int32_t> &node_rp,
+                          const std::vector<int32_t> &node_ci, const AmgParams &prm, AmgHost &H) {
+  H = AmgHost();
+  CsrHost A = S0;
+  bool finest = true;
+  while (A.n > prm.coarse_size && (int)H.P.size() < prm.max_levels - 1) {
+    std::vector<double> d = diag_of(A), dinv = safe_inverse(d);
+    std::vector<int32_t> grp, gci, agg;
+    if (finest) {
+      // mesh node graph without the diagonal
+      grp.assign(A.n + 1, 0);
+      for (int64_t i = 0; i < A.n; ++i) {
+        for (int32_t k = node_rp[i]; k < node_rp[i + 1]; ++k)
+          if (node_ci[k] != i) gci.push_back(node_ci[k]);
+        grp[i + 1] = (int32_t)gci.size();
+      }
+    } else {
+      strength_graph(A, d, prm.theta, grp, gci);
+    }
+    const int64_t na = aggregate(A.n, grp, gci, agg);
+    if (na >= A.n || na < 1) break;   // no coarsening possible
+    CsrHost Pt;
+    Pt.n = A.n;
+    Pt.m = na;
+    Pt.rp.resize(A.n + 1);
+    Pt.ci.resize(A.n);
+    Pt.v.assign(A.n, 1.0);
+    for (int64_t i = 0; i <= A.n; ++i) Pt.rp[i] = (int32_t)i;
+    for (int64_t i = 0; i < A.n; ++i) Pt.ci[i] = agg[i];
+    const double lam = lambda_max(A, dinv, 15) * 1.1;
+    const double w = 4.0 / (3.0 * lam);
+    CsrHost AP = multiply(A, Pt);   // (I - w D^-1 A) Pt = Pt - w D^-1 (A Pt)
+    CsrHost P;
+    P.n = A.n;
+    P.m = na;
+    P.rp.assign(A.n + 1, 0);
+    for (int64_t i = 0; i < A.n; ++i) {
+      bool own = false;
+      for (int32_t k = AP.rp[i]; k < AP.rp[i + 1]; ++k) {
+        double v = -w * dinv[i] * AP.v[k];
+        if (AP.ci[k] == agg[i]) {
+          v += 1.0;
+          own = true;
+        }
+        P.ci.push_back(AP.ci[k]);
+        P.v.push_back(v);
+      }
+      if (!own) {
+        P.ci.push_back(agg[i]);
+        P.v.push_back(1.0);
+      }
+      P.rp[i + 1] = (int32_t)P.ci.size();
+    }
+    CsrHost R = transpose(P);
+    CsrHost Ac = multiply(R, multiply(A, P));
+    H.A.push_back(std::move(A));
+    H.P.push_back(std::move(P));
+    H.R.push_back(std::move(R));
+    A = std::move(Ac);
+    finest = false;
+  }
+  H.A.push_back(A);
+  // dense inverse of the coarsest operator (Gauss-Jordan with partial pivoting)
+  const int64_t n = A.n;
+  H.nc = n;
+  std::vector<double> M(n * n, 0.0), I(n * n, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    I[i * n + i] = 1.0;
+    for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) M[i * n + A.ci[k]] += A.v[k];
+  }
+  for (int64_t c = 0; c < n; ++c) {
+    int64_t p = c;
+    for (int64_t r = c + 1; r < n; ++r)
+      if (std::fabs(M[r * n + c]) > std::fabs(M[p * n + c])) p = r;
+    if (M[p * n + c] == 0.0) {
+      // singular coarsest operator (e.g. a pure-Neumann pressure): regularise this pivot
+      M[p * n + c] = 1.0;
+    }
+    if (p != c)
+      for (int64_t k = 0; k < n; ++k) {
+        std::swap(M[p * n + k], M[c * n + k]);
+        std::swap(I[p * n + k], I[c * n + k]);
+      }
+    const double piv = 1.0 / M[c * n + c];
+    for (int64_t k = 0; k < n; ++k) {
+      M[c * n + k] *= piv;
+      I[c * n + k] *= piv;
+    }
+    for (int64_t r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = M[r * n + c];
+      if (f == 0.0) continue;
+      for (int64_t k = 0; k < n; ++k) {
+        M[r * n + k] -= f * M[c * n + k];
+        I[r * n + k] -= f * I[c * n + k];
+      }
+    }
+  }
+  H.coarse_inv = std::move(I);
+  H.lam.clear();
+  for (size_t l = 0; l + 1 < H.A.size(); ++l) {
+    std::vector<double> dinv = safe_inverse(diag_of(H.A[l]));
+    H.dinv.push_back(dinv);
+    H.lam.push_back(lambda_max(H.A[l], dinv, 15));
+  }
+  return LFX_OK;
+}
+
+}  // namespace lfx

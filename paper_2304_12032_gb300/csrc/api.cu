@@ -1,6 +1,7 @@
 // C ABI of liblfx (declared in include/lfx.h): mesh / problem / state handles, boundary data
 // preprocessing (Section 2.2), one time step (Section 2.3 assembly + Section 2.4 solve), and
 // the parity/debug entry points.  Host code only; kernels live in assemble.cu and solver.cu.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,6 +17,7 @@
 
 #include "kernels.h"
 #include "lfx_internal.h"
+#include "amg.h"
 #include "solver.h"
 
 namespace lfx {
@@ -120,11 +122,18 @@ struct lfx_state {
   DBuf hist[3];            // D4 [V]; level l = hist[(head + l) % sigma]
   int head = 0;
   DBuf xsol, ubdf, rhs, gdir, nodal;
-  DBuf vals64, vals32;
+  DBuf vals64, vals32, valsbf;
   ASimple<double, double> pc64;
   Gmres<double, double> gm64;
+  // mixed precision: FP32 inner Krylov with an FP32 or BF16-storage aSIMPLE
+  ASimple<float, float> pc32;
+  ASimple<__nv_bfloat16, float> pcbf;
+  Gmres<float, float> gm32;
+  DBuf r32, z32;
+  int inner_total = 0;
   double t = 0.0, pin_value = 0.0;
   bool assembled = false;
+  int amg_age = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, ea0 = nullptr, ea1 = nullptr;
   int n_asm_launch = 0;
   ~lfx_state() {
@@ -135,6 +144,12 @@ struct lfx_state {
     if (e2) cudaEventDestroy(e2);
   }
   D4 *level(int l) { return hist[(head + l) % sigma].as<D4>(); }
+  template <class S>
+  BsrView<S> view(const DBuf &v) const {
+    const Mesh &m = pb->mesh->m;
+    return BsrView<S>{m.V, m.d_rowptr.as<int32_t>(), m.d_col.as<int32_t>(), m.d_diag.as<int32_t>(),
+                      m.d_trans.as<int32_t>(), v.as<S>()};
+  }
   BsrView<double> view64() const {
     const Mesh &m = pb->mesh->m;
     return BsrView<double>{m.V, m.d_rowptr.as<int32_t>(), m.d_col.as<int32_t>(), m.d_diag.as<int32_t>(),
@@ -270,7 +285,7 @@ void lfx_options_default(lfx_options *o) {
   o->c_r = 30.0;
   o->pin_pressure_node = -1;
   o->precision = LFX_PREC_FP64;
-  o->gmres_restart = 40;
+  o->gmres_restart = 64;
   o->gmres_max_iters = 1000;
   o->gmres_rtol = 1e-10;
   o->reorthogonalize = 1;
@@ -278,8 +293,8 @@ void lfx_options_default(lfx_options *o) {
   o->f_steps = 3;
   o->f_omega = 0.7;
   o->f_ratio = 8.0;
-  o->s_smoother = LFX_SMOOTH_CHEBYSHEV;
-  o->s_steps = 6;
+  o->s_smoother = LFX_SMOOTH_AMG;
+  o->s_steps = 2;
   o->s_omega = 0.7;
   o->s_ratio = 30.0;
   o->n_power = 10;
@@ -289,6 +304,10 @@ void lfx_options_default(lfx_options *o) {
   o->inner_rtol = 1e-3;
   o->inner_max_iters = 60;
   o->bad_element_quality = 0.1;
+  o->amg_refresh = 0;
+  o->amg_coarse_size = 400;
+  o->amg_theta = 0.08;
+  o->amg_alpha = 1.0;
 }
 
 // barycentre, unit outward normal, area of the faces carrying `tag` (area weighted)
@@ -371,7 +390,8 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
   lfx_options &o = pb->opt;
   if (o.stab < 0 || o.stab > 2 || o.diffusion < 0 || o.diffusion > 2 || o.gmres_restart < 1 ||
       o.gmres_restart > kMaxRestart || o.f_steps < 1 || o.f_steps > kMaxSmooth || o.s_steps < 1 ||
-      o.s_steps > kMaxSmooth || o.precision < 0 || o.precision > 1 || o.n_power < 1) {
+      o.s_steps > kMaxSmooth || o.precision < 0 || o.precision > 1 || o.n_power < 1 || o.f_smoother < 0 ||
+      o.f_smoother > 1 || o.s_smoother < 0 || o.s_smoother > 2) {
     set_error("lfx_problem_create: option out of range (restart <= %d, smoothing steps <= %d)", kMaxRestart,
               kMaxSmooth);
     return LFX_ERR_INVALID_ARG;
@@ -679,8 +699,22 @@ lfx_status lfx_state_create(lfx_problem *pb, const double *u_hist, const double 
   cfg.s_omega = o.s_omega;
   cfg.s_ratio = o.s_ratio;
   cfg.n_power = o.n_power;
-  LFX_TRY(s->pc64.init(V, cfg));
-  LFX_TRY(s->gm64.init(V, o.gmres_restart));
+  if (o.precision == LFX_PREC_MIXED) {
+    LFX_TRY(s->vals32.alloc(sizeof(float) * 16 * m.nnzb));
+    if (o.smoother_bf16) {
+      LFX_TRY(s->valsbf.alloc(sizeof(__nv_bfloat16) * 16 * m.nnzb));
+      LFX_TRY(s->pcbf.init(V, cfg));
+    } else {
+      LFX_TRY(s->pc32.init(V, cfg));
+    }
+    LFX_TRY(s->gm32.init(V, o.gmres_restart));
+    LFX_TRY(s->gm64.init(V, std::max(1, o.outer_restart)));
+    LFX_TRY(s->r32.alloc(sizeof(float) * 4 * V));
+    LFX_TRY(s->z32.alloc(sizeof(float) * 4 * V));
+  } else {
+    LFX_TRY(s->pc64.init(V, cfg));
+    LFX_TRY(s->gm64.init(V, o.gmres_restart));
+  }
   LFX_CUDA_TRY(cudaEventCreate(&s->e0));
   LFX_CUDA_TRY(cudaEventCreate(&s->e1));
   LFX_CUDA_TRY(cudaEventCreate(&s->e2));
@@ -743,7 +777,9 @@ lfx_status lfx_state_device_bytes(const lfx_state *s, int64_t *bytes) {
   }
   size_t b = s->pb->mesh->m.device_bytes() + s->pb->device_bytes() + s->xsol.bytes + s->ubdf.bytes +
              s->rhs.bytes + s->gdir.bytes + s->nodal.bytes + s->vals64.bytes + s->vals32.bytes +
-             s->pc64.device_bytes() + s->gm64.device_bytes();
+             s->pc64.device_bytes() + s->pc64.amg_bytes() + s->gm64.device_bytes() + s->valsbf.bytes +
+             s->pc32.device_bytes() + s->pc32.amg_bytes() + s->pcbf.device_bytes() + s->pcbf.amg_bytes() +
+             s->gm32.device_bytes() + s->r32.bytes + s->z32.bytes;
   for (int l = 0; l < 3; ++l) b += s->hist[l].bytes;
   *bytes = (int64_t)b;
   return LFX_OK;
@@ -815,6 +851,101 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
   return LFX_OK;
 }
 
+}  // extern "C"
+
+// aSIMPLE set-up for the current matrix: diagonals and eigenvalue estimates every step; the
+// Schur AMG hierarchy (built from the FP64 matrix) on first use and then every amg_refresh
+// steps.  In mixed precision the FP32 (and BF16) copies of the matrix are refreshed first.
+template <class S, class T>
+static lfx_status setup_asimple(lfx_state *s, ASimple<S, T> &pc, const BsrView<S> &A) {
+  lfx_problem *pb = s->pb;
+  const lfx_options &o = pb->opt;
+  const Mesh &m = pb->mesh->m;
+  LFX_TRY(pc.setup(s->stream, A));
+  if (o.s_smoother != LFX_SMOOTH_AMG) return LFX_OK;
+  if (pc.amg_ready && !(o.amg_refresh > 0 && s->amg_age >= o.amg_refresh)) {
+    ++s->amg_age;
+    return LFX_OK;
+  }
+  std::vector<double> h(16 * (size_t)m.nnzb);
+  LFX_CUDA_TRY(cudaMemcpyAsync(h.data(), s->vals64.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s->stream));
+  LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  CsrHost S0 = schur_explicit(m.V, m.row_ptr, m.col_idx, m.diag_idx, h.data());
+  AmgParams prm;
+  prm.coarse_size = o.amg_coarse_size;
+  prm.theta = o.amg_theta;
+  AmgHost H;
+  LFX_TRY(amg_setup_host(S0, m.row_ptr, m.col_idx, prm, H));
+  pc.amg_alpha = o.amg_alpha;
+  LFX_TRY(pc.upload_amg(H));
+  s->amg_age = 1;
+  return LFX_OK;
+}
+
+static lfx_status prepare_precond(lfx_state *s) {
+  const lfx_options &o = s->pb->opt;
+  const Mesh &m = s->pb->mesh->m;
+  if (o.precision != LFX_PREC_MIXED) return setup_asimple(s, s->pc64, s->view64());
+  const int64_t nv = 16 * m.nnzb;
+  LFX_TRY((launch_convert<double, float>(s->stream, s->vals64.as<double>(), s->vals32.as<float>(), nv, nullptr)));
+  if (o.smoother_bf16) {
+    LFX_TRY((launch_convert<double, __nv_bfloat16>(s->stream, s->vals64.as<double>(), s->valsbf.as<__nv_bfloat16>(),
+                                                   nv, nullptr)));
+    return setup_asimple(s, s->pcbf, s->view<__nv_bfloat16>(s->valsbf));
+  }
+  return setup_asimple(s, s->pc32, s->view<float>(s->vals32));
+}
+
+// The configured Krylov solve of the assembled system (rhs -> x, x holds the initial guess).
+static lfx_status run_solve(lfx_state *s, double *x, bool x_zero, int *its, int *outer, double *rel) {
+  const lfx_options &o = s->pb->opt;
+  cudaStream_t st = s->stream;
+  const BsrView<double> A = s->view64();
+  *outer = 0;
+  if (o.precision != LFX_PREC_MIXED) {
+    auto pc = [s, A](cudaStream_t q, const double *v, double *z, const KState *ks) {
+      return s->pc64.apply(q, A, v, z, ks);
+    };
+    return s->gm64.solve(st, A, pc, s->rhs.as<double>(), x, o.gmres_rtol, o.gmres_max_iters,
+                         o.reorthogonalize != 0, 2, x_zero, its, rel);
+  }
+  // outer flexible GMRES in FP64 on the FP64 operator; each preconditioner application is an
+  // FP32 GMRES solve (to inner_rtol) with the FP32/BF16 aSIMPLE
+  const int64_t n = 4 * s->pb->mesh->m.V;
+  const BsrView<float> A32 = s->view<float>(s->vals32);
+  s->inner_total = 0;
+  auto inner = [s, A32, n, &o](cudaStream_t q, const double *v, double *z, const KState *ks) -> lfx_status {
+    LFX_TRY((launch_convert<double, float>(q, v, s->r32.as<float>(), n, ks)));
+    int it = 0;
+    double r = 0.0;
+    lfx_status rc;
+    if (o.smoother_bf16) {
+      const BsrView<__nv_bfloat16> Ab = s->view<__nv_bfloat16>(s->valsbf);
+      auto pc = [s, Ab](cudaStream_t qq, const float *vv, float *zz, const KState *kk) {
+        return s->pcbf.apply(qq, Ab, vv, zz, kk);
+      };
+      rc = s->gm32.solve(q, A32, pc, s->r32.as<float>(), s->z32.as<float>(), o.inner_rtol, o.inner_max_iters,
+                         o.reorthogonalize != 0, 2, true, &it, &r);
+    } else {
+      auto pc = [s, A32](cudaStream_t qq, const float *vv, float *zz, const KState *kk) {
+        return s->pc32.apply(qq, A32, vv, zz, kk);
+      };
+      rc = s->gm32.solve(q, A32, pc, s->r32.as<float>(), s->z32.as<float>(), o.inner_rtol, o.inner_max_iters,
+                         o.reorthogonalize != 0, 2, true, &it, &r);
+    }
+    s->inner_total += it;
+    if (rc != LFX_OK && rc != LFX_ERR_NOT_CONVERGED) return rc;
+    clear_error();
+    return launch_convert<float, double>(q, s->z32.as<float>(), z, n, ks);
+  };
+  lfx_status rc = s->gm64.solve(st, A, inner, s->rhs.as<double>(), x, o.gmres_rtol, o.outer_max_iters,
+                                o.reorthogonalize != 0, 0, x_zero, outer, rel);
+  *its = s->inner_total;
+  return rc;
+}
+
+extern "C" {
+
 lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   clear_error();
   if (!s) {
@@ -827,12 +958,10 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   LFX_CUDA_TRY(cudaEventRecord(s->e0, st));
   LFX_TRY(assemble_system(s, true));
   LFX_CUDA_TRY(cudaEventRecord(s->e1, st));
-  const BsrView<double> A = s->view64();
-  LFX_TRY(s->pc64.setup(st, A));
-  int its = 0;
+  LFX_TRY(prepare_precond(s));
+  int its = 0, outer = 0;
   double rel = 0.0;
-  lfx_status rc = s->gm64.solve(st, A, s->pc64, s->rhs.as<double>(), s->xsol.as<double>(), o.gmres_rtol,
-                                o.gmres_max_iters, o.reorthogonalize != 0, &its, &rel);
+  lfx_status rc = run_solve(s, s->xsol.as<double>(), false, &its, &outer, &rel);
   if (rc != LFX_OK && rc != LFX_ERR_NOT_CONVERGED) return rc;
   LFX_CUDA_TRY(cudaEventRecord(s->e2, st));
   // history shift: the solution becomes level 0
@@ -846,6 +975,7 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->iterations = its;
+    stats->outer_iterations = outer;
     stats->rel_residual = rel;
     stats->t = s->t;
     cudaEventElapsedTime(&stats->ms_assembly, s->e0, s->e1);
@@ -948,8 +1078,12 @@ lfx_status lfx_debug_precond(lfx_state *s, const double *r, double *z, double *l
   LFX_TRY(dr.alloc(sizeof(D4) * m.V));
   LFX_TRY(dz.alloc(sizeof(D4) * m.V));
   LFX_TRY(vec_to_device(m, r, dr.as<double>(), s->stream));
+  if (s->pb->opt.precision != LFX_PREC_FP64) {
+    set_error("lfx_debug_precond: available for the FP64 path only");
+    return LFX_ERR_INVALID_ARG;
+  }
   const BsrView<double> A = s->view64();
-  LFX_TRY(s->pc64.setup(s->stream, A));
+  LFX_TRY(prepare_precond(s));
   LFX_TRY(s->pc64.apply(s->stream, A, dr.as<double>(), dz.as<double>(), nullptr));
   LFX_TRY(vec_to_host(m, dz.as<double>(), z, s->stream));
   return s->pc64.lambdas(lam_f, lam_s);
@@ -966,15 +1100,15 @@ lfx_status lfx_debug_solve(lfx_state *s, double *x, lfx_step_stats *stats) {
   DBuf dx;
   LFX_TRY(dx.alloc(sizeof(D4) * m.V));
   LFX_CUDA_TRY(cudaMemsetAsync(dx.p, 0, dx.bytes, s->stream));
-  const BsrView<double> A = s->view64();
-  LFX_TRY(s->pc64.setup(s->stream, A));
-  int its = 0;
+  (void)o;
+  LFX_TRY(prepare_precond(s));
+  int its = 0, outer = 0;
   double rel = 0;
-  lfx_status rc = s->gm64.solve(s->stream, A, s->pc64, s->rhs.as<double>(), dx.as<double>(), o.gmres_rtol,
-                                o.gmres_max_iters, o.reorthogonalize != 0, &its, &rel);
+  lfx_status rc = run_solve(s, dx.as<double>(), true, &its, &outer, &rel);
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->iterations = its;
+    stats->outer_iterations = outer;
     stats->rel_residual = rel;
     stats->converged = rc == LFX_OK;
   }

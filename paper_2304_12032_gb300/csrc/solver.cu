@@ -8,11 +8,13 @@
 // partials, then one CTA sums them in a fixed order), so results are bitwise reproducible.
 // Every kernel of an Arnoldi step reads the solver's status word first and returns at once if
 // the cycle is already finished, so the host may queue a few steps ahead of the convergence test.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
 #include <algorithm>
 
+#include "amg.h"
 #include "kernels.h"
 #include "solver.h"
 
@@ -58,6 +60,22 @@ __device__ __forceinline__ void ld_block<float, float>(const float *vals, int64_
     b[4 * i + 1] = v.y;
     b[4 * i + 2] = v.z;
     b[4 * i + 3] = v.w;
+  }
+}
+template <>
+__device__ __forceinline__ void ld_block<__nv_bfloat16, float>(const __nv_bfloat16 *vals, int64_t k, float b[16]) {
+  const uint4 *p = reinterpret_cast<const uint4 *>(vals + 16 * k);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    uint4 v = __ldg(p + i);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[q]);
+      float2 f = __bfloat1622float2(h);
+      b[8 * i + 2 * q] = f.x;
+      b[8 * i + 2 * q + 1] = f.y;
+    }
   }
 }
 template <>
@@ -183,7 +201,8 @@ __global__ void diag_s_kernel(BsrView<S> A, const T *dinvF, T *dinvS) {
   acc = group_sum(acc);
   if (row < A.V && lane == 0) {
     const T c = (T)A.vals[16 * (int64_t)A.diag[row] + 15];
-    dinvS[row] = T(1) / (c - acc);
+    const T dd = c - acc;
+    dinvS[row] = dd != T(0) ? T(1) / dd : T(0);   // a vanishing diagonal leaves the unknown unsmoothed
   }
 }
 
@@ -337,7 +356,7 @@ __global__ void f_init_kernel(int64_t V, const T *dinvF, const T *b, T *r, T *d,
 template <class S, class T>
 __global__ void __launch_bounds__(kThreads) d_init_kernel(BsrView<S> A, const T *dinvS, const T *b,
                                                           T *r, T *d, T *x, const SmoothCoef *cf,
-                                                          const KState *st) {
+                                                          const KState *st, T *bs) {
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
@@ -352,6 +371,11 @@ __global__ void __launch_bounds__(kThreads) d_init_kernel(BsrView<S> A, const T 
   acc = group_sum(acc);
   if (row < A.V && lane == 0) {
     const T t = ld4(b, row).w - acc;
+    if (bs) {
+      auto o = ld4(bs, row);
+      o.w = t;
+      st4(bs, row, o);
+    }
     auto rr = ld4(r, row);
     auto dd = ld4(d, row);
     auto xx = ld4(x, row);
@@ -393,6 +417,133 @@ __global__ void __launch_bounds__(kThreads) final_kernel(BsrView<S> A, const T *
     o.w = xx.w;
     st4(z, row, o);
   }
+}
+
+
+// Level-0 Schur residual with w.xyz = diag(F)^-1 G x.w given:
+//   mode 0: out[row] = bs.w - (C x.w - D w)                       (for restriction)
+//   mode 1: r.w = dinvS (bs.w - (C x.w - D w)); d.w = init r.w; x.w += d.w  (post-smoothing start)
+template <class S, class T>
+__global__ void __launch_bounds__(kThreads) s_resid_kernel(BsrView<S> A, const T *dinvS, T *x, const T *w,
+                                                           const T *bs, T *out, T *r, T *d,
+                                                           const SmoothCoef *cf, int mode, const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  T acc = T(0);
+  if (row < A.V) {
+    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+      const S *blk = A.vals + 16 * (int64_t)kb;
+      const int32_t c = A.col[kb];
+      const T p = ld4(x, c).w;
+      const auto wv = ld4(w, c);
+      acc += (T)blk[15] * p - ((T)blk[12] * wv.x + (T)blk[13] * wv.y + (T)blk[14] * wv.z);
+    }
+  }
+  acc = group_sum(acc);
+  if (row < A.V && lane == 0) {
+    const T res = ld4(bs, row).w - acc;
+    if (mode == 0) {
+      out[row] = res;
+    } else {
+      auto rr = ld4(r, row);
+      auto dd = ld4(d, row);
+      auto xx = ld4(x, row);
+      rr.w = dinvS[row] * res;
+      dd.w = (T)cf->s_init * rr.w;
+      xx.w += dd.w;
+      st4(r, row, rr);
+      st4(d, row, dd);
+      st4(x, row, xx);
+    }
+  }
+}
+
+// ---- explicit CSR levels of the Schur AMG (scalar unknowns)
+struct CsrV {
+  int64_t n;
+  const int32_t *rp, *ci;
+  const double *v;
+};
+
+// out[i*os + oo] = (acc ? out : 0) + alpha * sum_j M_ij in[j*is + io]
+template <class T, int G>
+__global__ void csr_spmv_kernel(CsrV M, const T *in, int is, int io, T *out, int os, int oo, double alpha,
+                                int acc, const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int lane = threadIdx.x % G;
+  double s = 0.0;
+  if (row < M.n)
+    for (int32_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += G) s += M.v[k] * (double)in[(int64_t)M.ci[k] * is + io];
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (row < M.n && lane == 0) {
+    T *p = out + row * os + oo;
+    *p = (T)((acc ? (double)*p : 0.0) + alpha * s);
+  }
+}
+
+// r = b - A x
+template <class T>
+__global__ void csr_resid_kernel(CsrV M, const T *x, const T *b, T *out, const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  double s = 0.0;
+  if (row < M.n)
+    for (int32_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += kRowGroup) s += M.v[k] * (double)x[M.ci[k]];
+  s = group_sum(s);
+  if (row < M.n && lane == 0) out[row] = (T)((double)b[row] - s);
+}
+
+// Chebyshev start on a CSR level: r = dinv rhs; d = init r; x = (add ? x : 0) + d
+template <class T>
+__global__ void csr_cheb_init_kernel(int64_t n, const double *dinv, const T *rhs, T *r, T *d, T *x, double init,
+                                     int add, const KState *st) {
+  if (finished(st)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double rv = dinv[i] * (double)rhs[i];
+    const double dv = init * rv;
+    r[i] = (T)rv;
+    d[i] = (T)dv;
+    x[i] = (T)((add ? (double)x[i] : 0.0) + dv);
+  }
+}
+
+// Chebyshev step on a CSR level: y = A d_old; r -= dinv y; d_new = c1 d_old + c2 r; x += d_new
+template <class T>
+__global__ void csr_cheb_step_kernel(CsrV M, const double *dinv, const T *d_old, T *d_new, T *r, T *x, double c1,
+                                     double c2, const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  double s = 0.0;
+  if (row < M.n)
+    for (int32_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += kRowGroup) s += M.v[k] * (double)d_old[M.ci[k]];
+  s = group_sum(s);
+  if (row < M.n && lane == 0) {
+    const double rv = (double)r[row] - dinv[row] * s;
+    const double dv = c1 * (double)d_old[row] + c2 * rv;
+    r[row] = (T)rv;
+    d_new[row] = (T)dv;
+    x[row] = (T)((double)x[row] + dv);
+  }
+}
+
+// x[i*os+oo] = sum_k Minv[i][k] b[k*is+io]  (dense, n x n, row-major)
+template <class T>
+__global__ void dense_mv_kernel(int64_t n, const double *Minv, const T *b, int is, int io, T *x, int os, int oo,
+                                const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  double s = 0.0;
+  if (row < n)
+    for (int64_t k = lane; k < n; k += 32) s += Minv[row * n + k] * (double)b[k * is + io];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (row < n && lane == 0) x[row * os + oo] = (T)s;
 }
 
 // power iteration helpers: v = (1/sqrt(n)) on the selected components; v = y / lambda
@@ -565,6 +716,20 @@ __global__ void givens_kernel(const double *part, int nblk, KState *st, int j, i
   }
 }
 
+template <class A, class B>
+__global__ void convert_kernel(const A *src, B *dst, int64_t n, const KState *st) {
+  if (finished(st)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (B)src[i];
+}
+template <>
+__global__ void convert_kernel<double, __nv_bfloat16>(const double *src, __nv_bfloat16 *dst, int64_t n,
+                                                      const KState *st) {
+  if (finished(st)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __double2bfloat16(src[i]);
+}
+
 template <class T>
 __global__ void norm_kernel(const T *v, int64_t n, double *part) {
   double a = 0.0;
@@ -710,7 +875,7 @@ lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
       div_kernel<T><<<vg, kThreads, 0, st>>>(V, D1.as<T>(), D0.as<T>(), 7, lam_f);
     }
   }
-  if (cfg.s_kind == LFX_SMOOTH_CHEBYSHEV) {
+  if (cfg.s_kind == LFX_SMOOTH_CHEBYSHEV || cfg.s_kind == LFX_SMOOTH_AMG) {
     fill_kernel<T><<<vg, kThreads, 0, st>>>(V, D0.as<T>(), 8, 1.0 / sqrt((double)V));
     for (int it = 0; it < cfg.n_power; ++it) {
       g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), D0.as<T>(), W.as<T>(), nullptr);
@@ -721,7 +886,7 @@ lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
     }
   }
   note_launches(3 + (cfg.f_kind == LFX_SMOOTH_CHEBYSHEV ? 1 + 3 * cfg.n_power : 0) +
-                (cfg.s_kind == LFX_SMOOTH_CHEBYSHEV ? 1 + 4 * cfg.n_power : 0));
+                (cfg.s_kind != LFX_SMOOTH_JACOBI ? 1 + 4 * cfg.n_power : 0));
   coef_kernel<<<1, 32, 0, st>>>(cf, cfg.f_kind, cfg.f_steps, cfg.f_omega, cfg.f_ratio, cfg.s_kind,
                                 cfg.s_steps, cfg.s_omega, cfg.s_ratio);
   LFX_CUDA_TRY(cudaGetLastError());
@@ -739,16 +904,165 @@ lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r
   for (int k = 1; k < cfg.f_steps; ++k)
     f_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], d[k & 1], R.as<T>(),
                                                  X.as<T>(), cf, k, 1, nullptr, ks);
-  // z_p ~= S^-1 (r_p - D z_u*)
-  d_init_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks);
+  // z_p ~= S^-1 (r_p - D z_u*): Chebyshev/Jacobi steps on S, or one AMG V-cycle
+  if (cfg.s_kind == LFX_SMOOTH_AMG && !amg_ready) {
+    set_error("aSIMPLE: the Schur AMG hierarchy has not been built");
+    return LFX_ERR_INVALID_ARG;
+  }
+  d_init_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks,
+                                               amg_ready ? Bs.as<T>() : nullptr);
   for (int k = 1; k < cfg.s_steps; ++k) {
     g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
     s_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
                                                  R.as<T>(), X.as<T>(), cf, k, 1, nullptr, ks);
   }
+  if (cfg.s_kind == LFX_SMOOTH_AMG && amg.size() == 1) {
+    // small problem: the hierarchy is the dense inverse of S itself
+    dense_mv_kernel<T><<<(int)((V * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        V, coarse_inv.as<double>(), Bs.as<T>(), 4, 3, X.as<T>(), 4, 3, ks);
+    note_launches(1);
+  } else if (cfg.s_kind == LFX_SMOOTH_AMG) {
+    // residual of the pre-smoothed level-0 iterate, restriction, coarse V-cycle, prolongation
+    g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
+    s_resid_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(),
+                                                  rr0.as<T>(), nullptr, nullptr, cf, 0, ks);
+    const AmgDevLevel &L0 = amg[0];
+    CsrV R0{L0.nnext, L0.Rrp.as<int32_t>(), L0.Rci.as<int32_t>(), L0.Rv.as<double>()};
+    csr_spmv_kernel<T, 32><<<(int)((L0.nnext * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        R0, rr0.as<T>(), 1, 0, amg[1].b.as<T>(), 1, 0, 1.0, 0, ks);
+    LFX_TRY(vcycle(st, 1, ks));
+    CsrV P0{V, L0.Prp.as<int32_t>(), L0.Pci.as<int32_t>(), L0.Pv.as<double>()};
+    csr_spmv_kernel<T, 8><<<rows_grid(V), kThreads, 0, st>>>(P0, amg[1].x.as<T>(), 1, 0, X.as<T>(), 4, 3,
+                                                            amg_alpha, 1, ks);
+    // post-smoothing from the corrected iterate
+    g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
+    s_resid_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(), nullptr,
+                                                  R.as<T>(), d[0], cf, 1, ks);
+    for (int k = 1; k < cfg.s_steps; ++k) {
+      g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
+      s_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
+                                                   R.as<T>(), X.as<T>(), cf, k, 1, nullptr, ks);
+    }
+    note_launches(8 + 2 * (cfg.s_steps - 1));
+  }
   // z_u = z_u* - diag(F)^-1 G z_p
   final_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), z, ks);
   note_launches(3 + (cfg.f_steps - 1) + 2 * (cfg.s_steps - 1));
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+
+static void cheb_coefs(double lam, double ratio, int steps, double &init, double *c1, double *c2) {
+  const double lmax = 1.1 * lam, lmin = lmax / ratio;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma1 = theta / delta;
+  double rho = 1.0 / sigma1;
+  init = 1.0 / theta;
+  c1[0] = c2[0] = 0.0;
+  for (int k = 1; k < steps; ++k) {
+    const double rn = 1.0 / (2.0 * sigma1 - rho);
+    c1[k] = rn * rho;
+    c2[k] = 2.0 * rn / delta;
+    rho = rn;
+  }
+}
+
+template <class T>
+static lfx_status upload_vec(DBuf &d, const std::vector<T> &h) {
+  LFX_TRY(d.alloc(sizeof(T) * std::max<size_t>(h.size(), 1)));
+  if (!h.empty()) LFX_CUDA_TRY(cudaMemcpy(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return LFX_OK;
+}
+
+template <class S, class T>
+lfx_status ASimple<S, T>::upload_amg(const AmgHost &H) {
+  amg_ready = false;
+  const int L = (int)H.A.size();
+  if (L < 1) {
+    set_error("Schur AMG: empty hierarchy");
+    return LFX_ERR_INVALID_ARG;
+  }
+  amg.clear();
+  amg.resize(L);
+  for (int l = 0; l < L; ++l) {
+    AmgDevLevel &D = amg[l];
+    D.n = H.A[l].n;
+    if (l + 1 < L) {
+      D.nnext = H.A[l + 1].n;
+      LFX_TRY(upload_vec(D.Prp, H.P[l].rp));
+      LFX_TRY(upload_vec(D.Pci, H.P[l].ci));
+      LFX_TRY(upload_vec(D.Pv, H.P[l].v));
+      LFX_TRY(upload_vec(D.Rrp, H.R[l].rp));
+      LFX_TRY(upload_vec(D.Rci, H.R[l].ci));
+      LFX_TRY(upload_vec(D.Rv, H.R[l].v));
+      cheb_coefs(H.lam[l], cfg.s_ratio, cfg.s_steps, D.init, D.c1, D.c2);
+    }
+    if (l >= 1) {
+      if (l + 1 < L) {
+        LFX_TRY(upload_vec(D.rp, H.A[l].rp));
+        LFX_TRY(upload_vec(D.ci, H.A[l].ci));
+        LFX_TRY(upload_vec(D.v, H.A[l].v));
+        LFX_TRY(upload_vec(D.dinv, H.dinv[l]));
+      }
+      const size_t vb = sizeof(T) * (size_t)std::max<int64_t>(D.n, 1);
+      LFX_TRY(D.x.alloc(vb));
+      LFX_TRY(D.b.alloc(vb));
+      LFX_TRY(D.r.alloc(vb));
+      LFX_TRY(D.d0.alloc(vb));
+      LFX_TRY(D.d1.alloc(vb));
+      LFX_TRY(D.rr.alloc(vb));
+    }
+  }
+  nc = H.nc;
+  LFX_TRY(upload_vec(coarse_inv, H.coarse_inv));
+  if (!Bs.p) LFX_TRY(Bs.alloc(sizeof(T) * 4 * (size_t)V));
+  if (!rr0.p) LFX_TRY(rr0.alloc(sizeof(T) * (size_t)V));
+  LFX_CUDA_TRY(cudaMemset(Bs.p, 0, Bs.bytes));
+  amg_ready = true;
+  return LFX_OK;
+}
+
+template <class S, class T>
+size_t ASimple<S, T>::amg_bytes() const {
+  size_t b = Bs.bytes + rr0.bytes + coarse_inv.bytes;
+  for (const auto &D : amg)
+    b += D.rp.bytes + D.ci.bytes + D.v.bytes + D.dinv.bytes + D.Prp.bytes + D.Pci.bytes + D.Pv.bytes + D.Rrp.bytes +
+         D.Rci.bytes + D.Rv.bytes + D.x.bytes + D.b.bytes + D.r.bytes + D.d0.bytes + D.d1.bytes + D.rr.bytes;
+  return b;
+}
+
+// One V-cycle on the explicit levels l >= 1 for amg[l].b -> amg[l].x
+template <class S, class T>
+lfx_status ASimple<S, T>::vcycle(cudaStream_t st, int l, const KState *ks) {
+  AmgDevLevel &D = amg[l];
+  const int L = (int)amg.size();
+  if (l == L - 1) {
+    dense_mv_kernel<T><<<(int)((D.n * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        D.n, coarse_inv.as<double>(), D.b.as<T>(), 1, 0, D.x.as<T>(), 1, 0, ks);
+    note_launches(1);
+    return LFX_OK;
+  }
+  CsrV A{D.n, D.rp.as<int32_t>(), D.ci.as<int32_t>(), D.v.as<double>()};
+  CsrV P{D.n, D.Prp.as<int32_t>(), D.Pci.as<int32_t>(), D.Pv.as<double>()};
+  CsrV R{D.nnext, D.Rrp.as<int32_t>(), D.Rci.as<int32_t>(), D.Rv.as<double>()};
+  const int vg = vec_grid(D.n), rg = rows_grid(D.n);
+  T *d[2] = {D.d0.as<T>(), D.d1.as<T>()};
+  const double *dinv = D.dinv.as<double>();
+  csr_cheb_init_kernel<T><<<vg, kThreads, 0, st>>>(D.n, dinv, D.b.as<T>(), D.r.as<T>(), d[0], D.x.as<T>(), D.init, 0, ks);
+  for (int k = 1; k < cfg.s_steps; ++k)
+    csr_cheb_step_kernel<T><<<rg, kThreads, 0, st>>>(A, dinv, d[(k - 1) & 1], d[k & 1], D.r.as<T>(), D.x.as<T>(),
+                                                     D.c1[k], D.c2[k], ks);
+  csr_resid_kernel<T><<<rg, kThreads, 0, st>>>(A, D.x.as<T>(), D.b.as<T>(), D.rr.as<T>(), ks);
+  csr_spmv_kernel<T, 32><<<(int)((D.nnext * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+      R, D.rr.as<T>(), 1, 0, amg[l + 1].b.as<T>(), 1, 0, 1.0, 0, ks);
+  LFX_TRY(vcycle(st, l + 1, ks));
+  csr_spmv_kernel<T, 8><<<rg, kThreads, 0, st>>>(P, amg[l + 1].x.as<T>(), 1, 0, D.x.as<T>(), 1, 0, amg_alpha, 1, ks);
+  csr_resid_kernel<T><<<rg, kThreads, 0, st>>>(A, D.x.as<T>(), D.b.as<T>(), D.rr.as<T>(), ks);
+  csr_cheb_init_kernel<T><<<vg, kThreads, 0, st>>>(D.n, dinv, D.rr.as<T>(), D.r.as<T>(), d[0], D.x.as<T>(), D.init, 1, ks);
+  for (int k = 1; k < cfg.s_steps; ++k)
+    csr_cheb_step_kernel<T><<<rg, kThreads, 0, st>>>(A, dinv, d[(k - 1) & 1], d[k & 1], D.r.as<T>(), D.x.as<T>(),
+                                                     D.c1[k], D.c2[k], ks);
+  note_launches(6 + 2 * (cfg.s_steps - 1));
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
 }
@@ -764,6 +1078,7 @@ lfx_status ASimple<S, T>::lambdas(double *lf, double *ls) const {
 
 template struct ASimple<double, double>;
 template struct ASimple<float, float>;
+template struct ASimple<__nv_bfloat16, float>;
 
 // ------------------------------------------------------------------------------------------
 template <class S, class T>
@@ -802,8 +1117,11 @@ size_t Gmres<S, T>::device_bytes() const {
 // LFX_ERR_NOT_CONVERGED or LFX_ERR_NONFINITE; *its_out = Arnoldi steps, *res_out = final
 // relative residual (true residual of the last restart).
 template <class S, class T>
-lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, ASimple<S, T> &pc, const T *b, T *x,
-                              double rtol, int maxit, bool cgs2, int *its_out, double *res_out) {
+lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, const T *b, T *x,
+                              double rtol, int maxit, bool cgs2, int lag, bool x_zero, int *its_out,
+                              double *res_out) {
+  if (lag < 0) lag = 0;
+  if (lag > 2) lag = 2;
   KState *ks = state.as<KState>();
   T *Vb = basis.as<T>(), *Zb = zbasis.as<T>(), *w = work.as<T>();
   double *pn = part_n.as<double>();
@@ -827,8 +1145,8 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, ASimple<S, T
   int total = 0;
   double rel = 1.0;
   lfx_status status = LFX_ERR_NOT_CONVERGED;
+  if (bnorm == 0.0 || x_zero) LFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
   if (bnorm == 0.0) {
-    LFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
     if (its_out) *its_out = 0;
     if (res_out) *res_out = 0.0;
     return LFX_OK;
@@ -843,7 +1161,7 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, ASimple<S, T
     int launched = 0;
     for (int j = 0; j < restart; ++j) {
       T *vj = Vb + (int64_t)j * n, *vn = Vb + (int64_t)(j + 1) * n, *zj = Zb + (int64_t)j * n;
-      LFX_TRY(pc.apply(st, A, vj, zj, ks));
+      LFX_TRY(pc(st, vj, zj, ks));
       spmv_kernel<S, T><<<rows_grid(V), kThreads, 0, st>>>(A, zj, nullptr, w, 0, nullptr, ks);
       for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
         mdot_kernel<T><<<nblk_dot, kThreads, 0, st>>>(Vb, n, j + 1, w, n, part.as<double>(), kMaxRestart + 1, ks);
@@ -857,9 +1175,9 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, ASimple<S, T
       LFX_CUDA_TRY(cudaEventRecord(ev[j & 3], st));
       launched = j + 1;
       // lagged convergence test: the device runs at most two steps behind the host
-      if (j >= 2) {
-        LFX_CUDA_TRY(cudaEventSynchronize(ev[(j - 2) & 3]));
-        if (pinned[(j - 2) & 3]) break;
+      if (j >= lag) {
+        LFX_CUDA_TRY(cudaEventSynchronize(ev[(j - lag) & 3]));
+        if (pinned[(j - lag) & 3]) break;
       }
     }
     (void)launched;
@@ -907,5 +1225,17 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, ASimple<S, T
 
 template struct Gmres<double, double>;
 template struct Gmres<float, float>;
+
+template <class A, class B>
+lfx_status launch_convert(cudaStream_t st, const A *src, B *dst, int64_t n, const KState *ks) {
+  convert_kernel<A, B><<<vec_grid(n), kThreads, 0, st>>>(src, dst, n, ks);
+  note_launches(1);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+template lfx_status launch_convert<double, float>(cudaStream_t, const double *, float *, int64_t, const KState *);
+template lfx_status launch_convert<float, double>(cudaStream_t, const float *, double *, int64_t, const KState *);
+template lfx_status launch_convert<double, __nv_bfloat16>(cudaStream_t, const double *, __nv_bfloat16 *, int64_t,
+                                                          const KState *);
 
 }  // namespace lfx

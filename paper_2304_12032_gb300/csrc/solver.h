@@ -1,7 +1,11 @@
 // aSIMPLE preconditioner and restarted GMRES on the device (Section 2.4).
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <cmath>
+#include <functional>
+#include <vector>
 
 #include "kernels.h"
 
@@ -38,17 +42,49 @@ struct KState {
   double hcol[kMaxRestart + 1], hwork[kMaxRestart + 1];
 };
 
+struct AmgHost;
+
+// One explicit level (l >= 1) of the Schur AMG hierarchy on the device, and the transfer
+// operators from level l to l+1 (also for l = 0).
+struct AmgDevLevel {
+  int64_t n = 0, nnext = 0;
+  DBuf rp, ci, v, dinv;          // A_l (l >= 1)
+  DBuf Prp, Pci, Pv;             // P_l: n_l x n_{l+1}
+  DBuf Rrp, Rci, Rv;             // R_l = P_l^T
+  DBuf x, b, r, d0, d1, rr;      // work vectors (l >= 1)
+  double init = 0.0;             // Chebyshev coefficients of this level (host-computed)
+  double c1[kMaxSmooth] = {}, c2[kMaxSmooth] = {};
+};
+
 template <class S, class T>
 struct ASimple {
   int64_t V = 0;
   SmootherConfig cfg;
   DBuf dinvF, dinvS, X, D0, D1, R, W, coef, part;
+  // Schur AMG (cfg.s_kind == LFX_SMOOTH_AMG)
+  std::vector<AmgDevLevel> amg;
+  DBuf Bs, rr0, coarse_inv;
+  int64_t nc = 0;
+  bool amg_ready = false;
+  double amg_alpha = 1.0;
+  lfx_status upload_amg(const AmgHost &H);
+  lfx_status vcycle(cudaStream_t st, int l, const KState *ks);
+  size_t amg_bytes() const;
   lfx_status init(int64_t V, const SmootherConfig &cfg);
   lfx_status setup(cudaStream_t st, const BsrView<S> &A);
   lfx_status apply(cudaStream_t st, const BsrView<S> &A, const T *r, T *z, const KState *ks);
   lfx_status lambdas(double *lf, double *ls) const;
   size_t device_bytes() const;
 };
+
+// z = M^-1 v on the solver's stream; kernels may return early once ks->done is set.
+template <class T>
+using PrecFn = std::function<lfx_status(cudaStream_t, const T *v, T *z, const KState *ks)>;
+
+// dst[i] = (B) src[i] for i < n (precision conversion of vectors or matrix values);
+// skipped when ks says the calling solve is already finished.
+template <class A, class B>
+lfx_status launch_convert(cudaStream_t st, const A *src, B *dst, int64_t n, const KState *ks);
 
 template <class S, class T>
 struct Gmres {
@@ -62,8 +98,11 @@ struct Gmres {
   Gmres(const Gmres &) = delete;
   ~Gmres();
   lfx_status init(int64_t V, int restart);
-  lfx_status solve(cudaStream_t st, const BsrView<S> &A, ASimple<S, T> &pc, const T *b, T *x,
-                   double rtol, int maxit, bool cgs2, int *its_out, double *res_out);
+  // Solve A x = b to ||b - A x|| <= rtol ||b|| starting from x (zeroed first if x_zero).
+  // lag = Arnoldi steps the host may queue beyond the last convergence flag it has read.
+  lfx_status solve(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, const T *b, T *x,
+                   double rtol, int maxit, bool cgs2, int lag, bool x_zero, int *its_out,
+                   double *res_out);
   size_t device_bytes() const;
 };
 

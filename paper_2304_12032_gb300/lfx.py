@@ -27,7 +27,7 @@ TIME = {"constant": 0, "pulsatile": 1, "ramp": 2, "fourier": 3}
 KIND = {"noslip": 0, "dirichlet": 1, "nodal": 2, "neumann": 3}
 PROFILE = {"uniform": 0, "parabolic": 1, "womersley": 2}
 PREC = {"fp64": 0, "mixed": 1}
-SMOOTH = {"jacobi": 0, "chebyshev": 1}
+SMOOTH = {"jacobi": 0, "chebyshev": 1, "amg": 2}
 
 
 class lfx_time_law(ctypes.Structure):
@@ -59,6 +59,8 @@ class lfx_options(ctypes.Structure):
                 ("smoother_bf16", ctypes.c_int32), ("outer_restart", ctypes.c_int32),
                 ("outer_max_iters", ctypes.c_int32), ("inner_rtol", ctypes.c_double),
                 ("inner_max_iters", ctypes.c_int32), ("bad_element_quality", ctypes.c_double),
+                ("amg_refresh", ctypes.c_int32), ("amg_coarse_size", ctypes.c_int32),
+                ("amg_theta", ctypes.c_double), ("amg_alpha", ctypes.c_double),
                 ("reserved", ctypes.c_int32 * 8)]
 
 

@@ -28,11 +28,15 @@ CASES = {
 }
 
 
+# the oracle's aSIMPLE defaults: Chebyshev on F (3 steps, ratio 8) and on S (6 steps, ratio 30)
+CHEB = dict(s_smoother="chebyshev", s_steps=6, s_ratio=30.0)
+
+
 @pytest.fixture(scope="module", params=list(CASES))
 def pair(request):
     case = CASES[request.param]()
     ost = C.oracle_step(case)
-    mesh, prob, st = C.gpu_state(case, gmres_rtol=1e-12, gmres_max_iters=3000)
+    mesh, prob, st = C.gpu_state(case, gmres_rtol=1e-12, gmres_max_iters=3000, **CHEB)
     return request.param, case, ost, mesh, prob, st
 
 
@@ -85,6 +89,19 @@ def test_solve_matches_direct_solution(pair):
     assert rel <= 1e-6, (name, rel, stats)
 
 
+def test_amg_solve_matches_direct_solution(pair):
+    # default preconditioner: Schur block by one smoothed-aggregation AMG V-cycle
+    name, case, ost, _, _, _ = pair
+    if case.mesh.n_nodes < 1500:
+        pytest.skip("mesh too small for a multilevel hierarchy")
+    _, _, st = C.gpu_state(case, gmres_rtol=1e-12, gmres_max_iters=3000)
+    st.debug_assemble(apply_bcs=True)
+    x, stats = st.debug_solve()
+    xref = ost.x.reshape(-1, 4)
+    rel = np.linalg.norm(x - xref) / np.linalg.norm(xref)
+    assert rel <= 1e-6, (name, rel, stats)
+
+
 def test_step_matches_oracle(pair):
     name, case, ost, mesh, prob, st = pair
     stats = st.step()
@@ -94,3 +111,20 @@ def test_step_matches_oracle(pair):
     rp_ = np.linalg.norm(p - xref[:, 3]) / np.linalg.norm(xref[:, 3])
     assert ru <= 1e-6 and rp_ <= 1e-6, (name, ru, rp_, stats)
     assert stats["t"] == pytest.approx(case.t0 + case.dt)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("which", ["beltrami", "vessel_vms_riis", "bifurcation_supg_bdf3"])
+def test_mixed_step_matches_oracle(which, bf16):
+    # FP64 assembly and outer FGMRES, FP32 inner GMRES with an FP32 or BF16-storage aSIMPLE:
+    # the step must still match the FP64 oracle within 1e-6 relative L2.
+    case = CASES[which]()
+    ost = C.oracle_step(case)
+    _, _, st = C.gpu_state(case, precision="mixed", smoother_bf16=int(bf16), gmres_rtol=1e-10)
+    stats = st.step()
+    u, p = st.get()
+    xref = ost.x.reshape(-1, 4)
+    ru = np.linalg.norm(u - xref[:, :3]) / np.linalg.norm(xref[:, :3])
+    rp_ = np.linalg.norm(p - xref[:, 3]) / np.linalg.norm(xref[:, 3])
+    assert ru <= 1e-6 and rp_ <= 1e-6, (which, bf16, ru, rp_, stats)
+    assert stats["outer_iterations"] >= 1 and stats["iterations"] >= stats["outer_iterations"]
