@@ -159,10 +159,11 @@ typedef struct lfx_options {
   int32_t reorthogonalize;      /* classical Gram-Schmidt twice (1, default) or once (0)        */
   /* aSIMPLE: velocity block F and Schur approximation S = C - D diag(F)^-1 G */
   int32_t f_smoother, f_steps;  /* LFX_SMOOTH_*, steps; default Chebyshev, 3                   */
-  double f_omega, f_ratio;      /* Jacobi damping; Chebyshev lmax/lmin; default 0.7, 8         */
+  double f_omega, f_ratio;      /* Jacobi damping; Chebyshev lmax/lmin; default 0.7, 20        */
   int32_t s_smoother, s_steps;  /* default AMG with 2 Chebyshev steps pre and post              */
   double s_omega, s_ratio;      /* default 0.7, 30                                             */
-  int32_t n_power;              /* power-iteration steps for lmax; default 10                  */
+  int32_t n_power;              /* 0 (default): Chebyshev lmax = Gershgorin bound (holds for every
+                                   eigenvalue); > 0: this many power-iteration steps x 1.1       */
   /* mixed precision (LFX_PREC_MIXED) */
   int32_t smoother_bf16;        /* store the preconditioner blocks in BF16 (FP32 arithmetic)   */
   int32_t outer_restart;        /* FP64 flexible GMRES restart; default 8                       */
@@ -244,8 +245,8 @@ lfx_status lfx_debug_assemble(lfx_state *state, int32_t apply_bcs, double *block
 /* y = A x with the last assembled matrix; x, y [n_nodes][4] FP64 host buffers, caller numbering. */
 lfx_status lfx_debug_spmv(lfx_state *state, const double *x, double *y);
 /* z = P^-1 r with the aSIMPLE preconditioner of the last assembled matrix (FP64 path);
- * r, z [n_nodes][4] host buffers, caller numbering.  Also returns the two power-iteration
- * estimates (lambda_max of diag(F)^-1 F and of diag(S)^-1 S, before the 1.1 safety factor). */
+ * r, z [n_nodes][4] host buffers, caller numbering.  Also returns the lambda_max values of
+ * diag(F)^-1 F and diag(S)^-1 S that set the Chebyshev intervals. */
 lfx_status lfx_debug_precond(lfx_state *state, const double *r, double *z, double *lam_f,
                              double *lam_s);
 /* Solve the last assembled system (after lfx_debug_assemble with BCs) from x0 = 0 with the

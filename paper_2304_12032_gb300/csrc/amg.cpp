@@ -297,9 +297,16 @@ lfx_status amg_setup_host(const CsrHost &S0, const std::vector<int32_t> &node_rp
   H.coarse_inv = std::move(I);
   H.lam.clear();
   for (size_t l = 0; l + 1 < H.A.size(); ++l) {
+    // Gershgorin bound of D^-1 A_l for the Chebyshev interval of the level smoother
     std::vector<double> dinv = safe_inverse(diag_of(H.A[l]));
+    double g = 0.0;
+    for (int64_t i = 0; i < H.A[l].n; ++i) {
+      double s = 0.0;
+      for (int32_t k = H.A[l].rp[i]; k < H.A[l].rp[i + 1]; ++k) s += std::fabs(H.A[l].v[k]);
+      g = std::max(g, std::fabs(dinv[i]) * s);
+    }
     H.dinv.push_back(dinv);
-    H.lam.push_back(lambda_max(H.A[l], dinv, 15));
+    H.lam.push_back(g > 0 ? g : 1.0);
   }
   return LFX_OK;
 }

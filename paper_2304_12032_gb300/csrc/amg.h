@@ -25,7 +25,7 @@ struct AmgHost {
   std::vector<CsrHost> A;        // A[0] = S (finest), ..., A[L-1] coarsest
   std::vector<CsrHost> P, R;     // P[l]: n_l x n_{l+1}, R[l] = P[l]^T
   std::vector<std::vector<double>> dinv;   // 1/diag(A_l), l < L-1
-  std::vector<double> lam;       // lambda_max(D^-1 A_l) (power iteration), l < L-1
+  std::vector<double> lam;       // Gershgorin bound of lambda_max(D^-1 A_l), l < L-1
   std::vector<double> coarse_inv;
   int64_t nc = 0;
 };

@@ -292,12 +292,12 @@ void lfx_options_default(lfx_options *o) {
   o->f_smoother = LFX_SMOOTH_CHEBYSHEV;
   o->f_steps = 3;
   o->f_omega = 0.7;
-  o->f_ratio = 8.0;
+  o->f_ratio = 20.0;
   o->s_smoother = LFX_SMOOTH_AMG;
   o->s_steps = 2;
   o->s_omega = 0.7;
   o->s_ratio = 30.0;
-  o->n_power = 10;
+  o->n_power = 0;
   o->smoother_bf16 = 0;
   o->outer_restart = 8;
   o->outer_max_iters = 40;
@@ -390,7 +390,7 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
   lfx_options &o = pb->opt;
   if (o.stab < 0 || o.stab > 2 || o.diffusion < 0 || o.diffusion > 2 || o.gmres_restart < 1 ||
       o.gmres_restart > kMaxRestart || o.f_steps < 1 || o.f_steps > kMaxSmooth || o.s_steps < 1 ||
-      o.s_steps > kMaxSmooth || o.precision < 0 || o.precision > 1 || o.n_power < 1 || o.f_smoother < 0 ||
+      o.s_steps > kMaxSmooth || o.precision < 0 || o.precision > 1 || o.n_power < 0 || o.f_smoother < 0 ||
       o.f_smoother > 1 || o.s_smoother < 0 || o.s_smoother > 2) {
     set_error("lfx_problem_create: option out of range (restart <= %d, smoothing steps <= %d)", kMaxRestart,
               kMaxSmooth);

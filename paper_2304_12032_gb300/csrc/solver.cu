@@ -113,6 +113,21 @@ __device__ __forceinline__ double cta_sum(double v) {
   return s;
 }
 
+// CTA-wide max of one double per thread; result valid in thread 0.
+__device__ __forceinline__ double cta_max(double v) {
+  __shared__ double red[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s = fmax(s, red[i]);
+  return s;
+}
+
 __device__ __forceinline__ bool finished(const KState *st) {
   return st != nullptr && *(volatile const int *)&st->done != 0;
 }
@@ -159,12 +174,73 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(BsrView<S> A, const T *_
   }
 }
 
-// sum of part[0..n) -> *out (sqrt if root); one CTA, fixed order
+// sum of part[0..n) -> *out (sqrt if root == 1, max instead of sum if root == 2); one CTA
 __global__ void reduce_kernel(const double *part, int n, double *out, int root) {
   double s = 0.0;
+  if (root == 2) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s = fmax(s, part[i]);
+    s = cta_max(s);
+    if (threadIdx.x == 0) *out = s;
+    return;
+  }
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
   s = cta_sum(s);
   if (threadIdx.x == 0) *out = root ? sqrt(s) : s;
+}
+
+// Gershgorin bounds for the Chebyshev intervals (every eigenvalue lies in a Gershgorin disc):
+//   mode 0: per row max_i |dinvF_i| sum_{k,j<3} |F_k[i][j]|                    -> part (max)
+//   mode 1: gs.xyz = sum_k |G_k[i][3]| (absolute row sums of G)                 -> gs
+//   mode 2: |dinvS| (sum_k |C_k| + sum_{k,j} |D_k[3][j]| |dinvF_col,j| gs_col,j) -> part (max)
+template <class S, class T>
+__global__ void __launch_bounds__(kThreads) bound_kernel(BsrView<S> A, const T *dinvF, const T *dinvS, T *gs,
+                                                         double *part, int mode) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  if (row < A.V) {
+    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+      T blk[16];
+      ld_block<S, T>(A.vals, kb, blk);
+      if (mode == 0) {
+        a0 += fabs((double)blk[0]) + fabs((double)blk[1]) + fabs((double)blk[2]);
+        a1 += fabs((double)blk[4]) + fabs((double)blk[5]) + fabs((double)blk[6]);
+        a2 += fabs((double)blk[8]) + fabs((double)blk[9]) + fabs((double)blk[10]);
+      } else if (mode == 1) {
+        a0 += fabs((double)blk[3]);
+        a1 += fabs((double)blk[7]);
+        a2 += fabs((double)blk[11]);
+      } else {
+        const auto df = ld4(dinvF, A.col[kb]);
+        const auto g = ld4(gs, A.col[kb]);
+        a0 += fabs((double)blk[15]) + fabs((double)blk[12]) * fabs((double)df.x) * (double)g.x +
+              fabs((double)blk[13]) * fabs((double)df.y) * (double)g.y +
+              fabs((double)blk[14]) * fabs((double)df.z) * (double)g.z;
+      }
+    }
+  }
+  a0 = group_sum(a0);
+  a1 = group_sum(a1);
+  a2 = group_sum(a2);
+  double val = 0.0;
+  if (row < A.V && lane == 0) {
+    if (mode == 0) {
+      const auto df = ld4(dinvF, row);
+      val = fmax(fabs((double)df.x) * a0, fmax(fabs((double)df.y) * a1, fabs((double)df.z) * a2));
+    } else if (mode == 1) {
+      auto o = ld4(gs, row);
+      o.x = (T)a0;
+      o.y = (T)a1;
+      o.z = (T)a2;
+      st4(gs, row, o);
+    } else {
+      val = fabs((double)dinvS[row]) * a0;
+    }
+  }
+  if (mode != 1) {
+    double m = cta_max(val);
+    if (threadIdx.x == 0) part[blockIdx.x] = m;
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -575,7 +651,7 @@ __global__ void div_kernel(int64_t V, const T *y, T *v, int comp_mask, const dou
 // Chebyshev coefficients (Saad, Chebyshev acceleration) from lambda_max estimates, or the
 // constant Jacobi ones.
 __global__ void coef_kernel(SmoothCoef *cf, int f_kind, int f_steps, double f_omega, double f_ratio,
-                            int s_kind, int s_steps, double s_omega, double s_ratio) {
+                            int s_kind, int s_steps, double s_omega, double s_ratio, double safety) {
   if (threadIdx.x != 0) return;
   for (int which = 0; which < 2; ++which) {
     const int kind = which ? s_kind : f_kind;
@@ -591,7 +667,7 @@ __global__ void coef_kernel(SmoothCoef *cf, int f_kind, int f_steps, double f_om
         c2[k] = omega;
       }
     } else {
-      const double lmax = 1.1 * (which ? cf->lam_s : cf->lam_f);
+      const double lmax = safety * (which ? cf->lam_s : cf->lam_f);
       const double lmin = lmax / ratio;
       const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
       const double sigma1 = theta / delta;
@@ -635,19 +711,23 @@ __global__ void __launch_bounds__(kThreads) mdot_kernel(const T *Vb, int64_t ld,
     for (int k = 0; k < 8; ++k) {
       if (k < nv) {
         double s = cta_sum(acc[k]);
-        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * ldp + v0 + k] = s;
+        if (threadIdx.x == 0) part[(int64_t)(v0 + k) * ldp + blockIdx.x] = s;   // [vector][block]
       }
     }
   }
 }
 
-// h[i] = sum_blk part[blk][i]; hcol[i] (+)= h[i]; hwork[i] = h[i]
+// h[i] = sum_blk part[i][blk]; hcol[i] (+)= h[i]; hwork[i] = h[i].  One warp per vector i.
 __global__ void mdot_finalize_kernel(const double *part, int nblk, int ldp, int nvec, KState *st,
                                      int accumulate) {
   if (finished(st)) return;
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * ldp + i];
+  const int i = blockIdx.x;
+  if (i >= nvec) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += 32) s += part[(int64_t)i * ldp + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) {
     st->hwork[i] = s;
     st->hcol[i] = accumulate ? st->hcol[i] + s : s;
   }
@@ -865,7 +945,17 @@ lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
   diag_s_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>());
   SmoothCoef *cf = coef.as<SmoothCoef>();
   double *lam_f = &cf->lam_f, *lam_s = &cf->lam_s;
-  if (cfg.f_kind == LFX_SMOOTH_CHEBYSHEV) {
+  const bool bound = cfg.n_power <= 0;
+  if (bound) {
+    // Gershgorin bounds (hold for every eigenvalue; no safety factor)
+    bound_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 0);
+    reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_f, 2);
+    bound_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 1);
+    bound_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 2);
+    reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_s, 2);
+    note_launches(5);
+  }
+  if (!bound && cfg.f_kind == LFX_SMOOTH_CHEBYSHEV) {
     // power iteration on diag(F)^-1 F from the normalised ones vector (velocity components)
     fill_kernel<T><<<vg, kThreads, 0, st>>>(V, D0.as<T>(), 7, 1.0 / sqrt(3.0 * (double)V));
     for (int it = 0; it < cfg.n_power; ++it) {
@@ -874,8 +964,9 @@ lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
       reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_f, 1);
       div_kernel<T><<<vg, kThreads, 0, st>>>(V, D1.as<T>(), D0.as<T>(), 7, lam_f);
     }
+    note_launches(1 + 3 * cfg.n_power);
   }
-  if (cfg.s_kind == LFX_SMOOTH_CHEBYSHEV || cfg.s_kind == LFX_SMOOTH_AMG) {
+  if (!bound && cfg.s_kind != LFX_SMOOTH_JACOBI) {
     fill_kernel<T><<<vg, kThreads, 0, st>>>(V, D0.as<T>(), 8, 1.0 / sqrt((double)V));
     for (int it = 0; it < cfg.n_power; ++it) {
       g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), D0.as<T>(), W.as<T>(), nullptr);
@@ -884,11 +975,11 @@ lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
       reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_s, 1);
       div_kernel<T><<<vg, kThreads, 0, st>>>(V, D1.as<T>(), D0.as<T>(), 8, lam_s);
     }
+    note_launches(1 + 4 * cfg.n_power);
   }
-  note_launches(3 + (cfg.f_kind == LFX_SMOOTH_CHEBYSHEV ? 1 + 3 * cfg.n_power : 0) +
-                (cfg.s_kind != LFX_SMOOTH_JACOBI ? 1 + 4 * cfg.n_power : 0));
+  note_launches(3);
   coef_kernel<<<1, 32, 0, st>>>(cf, cfg.f_kind, cfg.f_steps, cfg.f_omega, cfg.f_ratio, cfg.s_kind,
-                                cfg.s_steps, cfg.s_omega, cfg.s_ratio);
+                                cfg.s_steps, cfg.s_omega, cfg.s_ratio, bound ? 1.0 : 1.1);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
 }
@@ -954,7 +1045,7 @@ lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r
 
 
 static void cheb_coefs(double lam, double ratio, int steps, double &init, double *c1, double *c2) {
-  const double lmax = 1.1 * lam, lmin = lmax / ratio;
+  const double lmax = lam, lmin = lmax / ratio;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma1 = theta / delta;
   double rho = 1.0 / sigma1;
   init = 1.0 / theta;
@@ -1071,8 +1162,9 @@ template <class S, class T>
 lfx_status ASimple<S, T>::lambdas(double *lf, double *ls) const {
   SmoothCoef h;
   LFX_CUDA_TRY(cudaMemcpy(&h, coef.p, sizeof(SmoothCoef), cudaMemcpyDeviceToHost));
-  if (lf) *lf = h.lam_f;
-  if (ls) *ls = h.lam_s;
+  const double f = cfg.n_power > 0 ? 1.1 : 1.0;
+  if (lf) *lf = f * h.lam_f;
+  if (ls) *ls = f * h.lam_s;
   return LFX_OK;
 }
 
@@ -1164,8 +1256,8 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
       LFX_TRY(pc(st, vj, zj, ks));
       spmv_kernel<S, T><<<rows_grid(V), kThreads, 0, st>>>(A, zj, nullptr, w, 0, nullptr, ks);
       for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
-        mdot_kernel<T><<<nblk_dot, kThreads, 0, st>>>(Vb, n, j + 1, w, n, part.as<double>(), kMaxRestart + 1, ks);
-        mdot_finalize_kernel<<<1, 64, 0, st>>>(part.as<double>(), nblk_dot, kMaxRestart + 1, j + 1, ks, pass);
+        mdot_kernel<T><<<nblk_dot, kThreads, 0, st>>>(Vb, n, j + 1, w, n, part.as<double>(), nblk_dot, ks);
+        mdot_finalize_kernel<<<j + 1, 32, 0, st>>>(part.as<double>(), nblk_dot, nblk_dot, j + 1, ks, pass);
         maxpy_kernel<T><<<vg, kThreads, 0, st>>>(Vb, n, j + 1, w, n, pn, ks);
       }
       givens_kernel<<<1, kThreads, 0, st>>>(pn, vg, ks, j, restart, maxit);

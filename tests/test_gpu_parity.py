@@ -28,7 +28,8 @@ CASES = {
 }
 
 
-# the oracle's aSIMPLE defaults: Chebyshev on F (3 steps, ratio 8) and on S (6 steps, ratio 30)
+# the oracle's aSIMPLE defaults: Chebyshev on F (3 steps, ratio 20) and on S (6 steps, ratio 30),
+# Gershgorin bounds for lambda_max
 CHEB = dict(s_smoother="chebyshev", s_steps=6, s_ratio=30.0)
 
 
@@ -73,15 +74,21 @@ def test_preconditioner_matches_oracle(pair):
     r = np.random.default_rng(6).standard_normal((case.mesh.n_nodes, 4))
     z, lam_f, lam_s = st.debug_precond(r)
     pc = O.ASimple(ost.A)                     # defaults equal the library's defaults
-    assert lam_f * 1.1 == pytest.approx(pc.lam_f, rel=1e-10)
-    assert lam_s * 1.1 == pytest.approx(pc.lam_s, rel=1e-10)
+    assert lam_f == pytest.approx(pc.lam_f, rel=1e-10)
+    assert lam_s == pytest.approx(pc.lam_s, rel=1e-10)
     zref = pc.apply(r.ravel()).reshape(-1, 4)
     assert np.linalg.norm(z - zref) <= 1e-10 * np.linalg.norm(zref), name
     assert np.abs(z - zref).max() <= 1e-9 * np.abs(zref).max(), name
 
 
+def _needs_stable(name):
+    if name == "galerkin_only":
+        pytest.skip("P1-P1 without stabilisation is not inf-sup stable: the system is singular")
+
+
 def test_solve_matches_direct_solution(pair):
     name, case, ost, mesh, prob, st = pair
+    _needs_stable(name)
     st.debug_assemble(apply_bcs=True)
     x, stats = st.debug_solve()
     xref = ost.x.reshape(-1, 4)
@@ -92,6 +99,7 @@ def test_solve_matches_direct_solution(pair):
 def test_amg_solve_matches_direct_solution(pair):
     # default preconditioner: Schur block by one smoothed-aggregation AMG V-cycle
     name, case, ost, _, _, _ = pair
+    _needs_stable(name)
     if case.mesh.n_nodes < 1500:
         pytest.skip("mesh too small for a multilevel hierarchy")
     _, _, st = C.gpu_state(case, gmres_rtol=1e-12, gmres_max_iters=3000)
@@ -104,6 +112,7 @@ def test_amg_solve_matches_direct_solution(pair):
 
 def test_step_matches_oracle(pair):
     name, case, ost, mesh, prob, st = pair
+    _needs_stable(name)
     stats = st.step()
     u, p = st.get()
     xref = ost.x.reshape(-1, 4)
