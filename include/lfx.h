@@ -63,8 +63,11 @@ typedef struct lfx_mesh lfx_mesh;
  * int32 with boundary_tags [n_bfaces] (any orientation; outward normals are recomputed).
  * Builds, once, on the host: the node and element renumbering (space-filling curve), the 4x4
  * block-CSR pattern of the node graph, the element -> block-slot map and an element colouring
- * such that no two elements of one colour share a node (atomic-free scatter).  Copies all
- * inputs.  Needs no GPU: the device copies are made by the first lfx_problem_create. */
+ * such that no two elements of one colour share a node (atomic-free scatter).  Disconnected
+ * pieces (several independent meshes passed together, "batching") are detected and numbered
+ * contiguously; they are assembled by the same launches and solved as one block-diagonal
+ * system.  Copies all inputs.  Needs no GPU: the device copies are made by the first
+ * lfx_problem_create. */
 lfx_status lfx_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *tets,
                            int64_t n_tets, const int32_t *bfaces, const int32_t *boundary_tags,
                            int64_t n_bfaces, lfx_mesh **out);
@@ -77,6 +80,8 @@ typedef struct lfx_mesh_info {
   int32_t n_flipped;           /* tetrahedra whose orientation was fixed                     */
   int32_t max_color_size, min_color_size;
   int64_t n_bad_elements;      /* elements below the shape-quality threshold (FP64 geometry) */
+  int32_t n_components;        /* connected components: independent meshes batched together  */
+  int32_t pad;
 } lfx_mesh_info;
 lfx_status lfx_mesh_get_info(const lfx_mesh *mesh, lfx_mesh_info *info);
 
@@ -177,7 +182,11 @@ typedef struct lfx_options {
   int32_t amg_coarse_size;      /* dense solve below this many unknowns; default 400           */
   double amg_theta;             /* strength threshold on coarse levels; default 0.08           */
   double amg_alpha;             /* scaling of the coarse correction; default 1.0               */
-  int32_t reserved[8];
+  /* batching: a mesh made of several disconnected meshes is stepped as one system; with
+   * batch_normalize (default 1) each component's rows are scaled by 1/||its rhs|| so that the
+   * solve meets every component's own relative tolerance */
+  int32_t batch_normalize;
+  int32_t reserved[7];
 } lfx_options;
 void lfx_options_default(lfx_options *opt);
 
@@ -262,6 +271,39 @@ typedef void (*lfx_free_fn)(void *ptr, void *ctx);
 lfx_status lfx_set_allocator(lfx_alloc_fn alloc, lfx_free_fn free_fn, void *ctx);
 /* Device bytes held by a state together with its problem and mesh (for admission control). */
 lfx_status lfx_state_device_bytes(const lfx_state *state, int64_t *bytes);
+/* Device bytes a new state of this problem will take (excluding the mesh and problem, which are
+ * already resident), an upper estimate used for admission. */
+lfx_status lfx_problem_state_bytes(const lfx_problem *problem, int64_t *bytes);
+
+/* ------------------------------------------------------------------------------------------
+ * Serving (not in the paper): continuous batching of independent simulations on one GPU.
+ * Requests wait FIFO until the device-memory budget admits them; admitted simulations keep
+ * their state resident, each on its own stream, and n_workers host threads step them
+ * round-robin one step at a time, so kernels of different simulations overlap.  When one
+ * finishes, its result is copied to host memory, its device memory released and waiting
+ * requests are admitted.  Results are independent of the mix (no shared reductions).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct lfx_server lfx_server;
+/* hbm_budget_bytes: device memory that admitted states may occupy in total (> 0);
+ * n_workers: host threads stepping simulations (1..64).  Uses the current CUDA device. */
+lfx_status lfx_server_create(int64_t hbm_budget_bytes, int32_t n_workers, lfx_server **out);
+/* Queue a simulation of `problem` (borrowed; must outlive the request) from the history
+ * u_hist [bdf_order][n_nodes][3], p_hist [bdf_order][n_nodes] (copied) at t0, for n_steps
+ * steps.  LFX_ERR_BUDGET if it can never fit the budget. */
+lfx_status lfx_server_submit(lfx_server *server, lfx_problem *problem, const double *u_hist,
+                             const double *p_hist, double t0, int32_t n_steps, int64_t *ticket);
+/* done = 1 once all steps ran (or the request failed: the failure status is returned). */
+lfx_status lfx_server_poll(lfx_server *server, int64_t ticket, int32_t *done, int32_t *steps_done,
+                           lfx_step_stats *last);
+/* Final u [n_nodes][3], p [n_nodes] (caller numbering) of a finished request; frees the ticket. */
+lfx_status lfx_server_result(lfx_server *server, int64_t ticket, double *u, double *p);
+/* Per-step latencies in ms (wall time of each lfx_step, up to capacity entries), their count,
+ * the device bytes currently admitted, the queue length and the peak number of simulations
+ * resident at once. */
+lfx_status lfx_server_stats(lfx_server *server, float *latency_ms, int64_t capacity, int64_t *n_latencies,
+                            int64_t *used_bytes, int64_t *n_waiting, int64_t *max_active);
+/* Stops the workers after their current step and frees every remaining state. */
+void lfx_server_destroy(lfx_server *server);
 
 #ifdef __cplusplus
 }

@@ -121,7 +121,7 @@ struct lfx_state {
   int sigma = 1;
   DBuf hist[3];            // D4 [V]; level l = hist[(head + l) % sigma]
   int head = 0;
-  DBuf xsol, ubdf, rhs, gdir, nodal;
+  DBuf xsol, ubdf, rhs, gdir, nodal, comp_scale;
   DBuf vals64, vals32, valsbf;
   ASimple<double, double> pc64;
   Gmres<double, double> gm64;
@@ -226,6 +226,7 @@ lfx_status lfx_mesh_get_info(const lfx_mesh *mesh, lfx_mesh_info *info) {
   info->max_color_size = mx;
   info->min_color_size = mn;
   info->n_bad_elements = 0;
+  info->n_components = m.n_comp;
   return LFX_OK;
 }
 
@@ -308,6 +309,7 @@ void lfx_options_default(lfx_options *o) {
   o->amg_coarse_size = 400;
   o->amg_theta = 0.08;
   o->amg_alpha = 1.0;
+  o->batch_normalize = 1;
 }
 
 // barycentre, unit outward normal, area of the faces carrying `tag` (area weighted)
@@ -687,6 +689,7 @@ lfx_status lfx_state_create(lfx_problem *pb, const double *u_hist, const double 
   LFX_TRY(s->gdir.alloc(sizeof(D4) * std::max<int64_t>(nd, 1)));
   LFX_TRY(s->nodal.alloc(sizeof(double) * 3 * std::max<int64_t>(nd, 1)));
   LFX_CUDA_TRY(cudaMemset(s->nodal.p, 0, s->nodal.bytes));
+  LFX_TRY(s->comp_scale.alloc(sizeof(double) * (size_t)m.n_comp));
   const lfx_options &o = pb->opt;
   LFX_TRY(s->vals64.alloc(sizeof(double) * 16 * m.nnzb));
   SmootherConfig cfg;
@@ -848,6 +851,49 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
   LFX_TRY(launch_apply_dirichlet<double>(st, nd, pb->d_dir_node.as<int32_t>(), s->gdir.as<D4>(), pb->pin_node,
                                          s->pin_value, m.d_rowptr.as<int32_t>(), m.d_diag.as<int32_t>(),
                                          s->vals64.as<double>(), s->rhs.as<double>(), s->xsol.as<double>()));
+  if (m.n_comp > 1 && pb->opt.batch_normalize)
+    LFX_TRY(launch_comp_normalize(st, m.V, m.n_comp, m.d_comp_off.as<int32_t>(), s->comp_scale.as<double>(),
+                                  m.d_rowptr.as<int32_t>(), s->vals64.as<double>(), s->rhs.as<double>()));
+  return LFX_OK;
+}
+
+}  // extern "C"
+
+// Device bytes a state of this problem will allocate (mirrors lfx_state_create and the first
+// step's lazily built preconditioner data), plus 10 % slack.
+int64_t lfx_internal_state_bytes_estimate(const lfx_problem *pb, int64_t *V_out, int *sigma_out) {
+  const Mesh &m = pb->mesh->m;
+  const lfx_options &o = pb->opt;
+  const int64_t V = m.V, nnzb = m.nnzb;
+  const int sigma = pb->bdf_order;
+  if (V_out) *V_out = V;
+  if (sigma_out) *sigma_out = sigma;
+  const int64_t v64 = 32 * V, v32 = 16 * V;
+  int64_t b = (sigma + 3) * v64 + 64 * (int64_t)pb->dir_node.size() + 8 * m.n_comp;
+  b += 128 * nnzb;                                           // FP64 matrix
+  const int64_t amg = o.s_smoother == LFX_SMOOTH_AMG ? 300 * V + 8LL * o.amg_coarse_size * o.amg_coarse_size : 0;
+  const int64_t part = 8LL * 152 * 4 * 65 + 8 * (V * 8 / 256 + 64);
+  if (o.precision == LFX_PREC_MIXED) {
+    b += 64 * nnzb + (o.smoother_bf16 ? 32 * nnzb : 0);      // FP32 / BF16 copies
+    b += 7 * v32 + 4 * V + amg;                               // FP32 aSIMPLE work
+    b += (2 * (int64_t)o.gmres_restart + 2) * v32 + part;    // inner GMRES
+    b += (2 * (int64_t)std::max(1, o.outer_restart) + 2) * v64 + part;   // outer FGMRES
+    b += 2 * v32;
+  } else {
+    b += 7 * v64 + 8 * V + amg;
+    b += (2 * (int64_t)o.gmres_restart + 2) * v64 + part;
+  }
+  return b + b / 10;
+}
+
+extern "C" {
+
+lfx_status lfx_problem_state_bytes(const lfx_problem *pb, int64_t *bytes) {
+  if (!pb || !bytes) {
+    set_error("lfx_problem_state_bytes: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  *bytes = lfx_internal_state_bytes_estimate(pb, nullptr, nullptr);
   return LFX_OK;
 }
 

@@ -31,12 +31,19 @@ template <class R>
 struct ElemShared {
   R gphi[kElems][12];      // grad phi_a, a = 0..3
   R w[kElems];             // |K| / 4 (quadrature weight)
+  R Gm[kElems][9];         // metric tensor G = J^-T J^-1
+  R gg[kElems];            // g . g, g = J^-T 1
   R cs[kElems][4];         // rho alpha / dt + sum_k (R_k/eps_k) delta_k at each qp
   R tm[kElems][4];         // tau_M
   R tc[kElems][4];         // tau_C
   R adv[kElems][4][4];     // [q][a] = u*(x_q) . grad phi_a
   R z[kElems][4][3];       // rho tau_M (u* - tau_M r_M^EXT) (VMS + LES), 0 without VMS-LES
   R m[kElems][4][3];       // rho u^BDF / dt + f
+  // per (qp, node) and per element sums (phase 1c)
+  R E[kElems][4][4];       // [q][a] = w (phi_a(q) + tau_M rho adv_q(a))  (test-function weight)
+  R cb[kElems][4][4];      // [q][b] = cs_q phi_b(q) + rho adv_q(b)     (trial-function residual)
+  R mga[kElems][4][4];     // [q][a] = m_q . grad phi_a
+  R Svp[kElems][4], Ppv[kElems][4], Wv[kElems][4][3], Zv[kElems][3], TM[kElems], TC[kElems];
 };
 
 __device__ __forceinline__ double delta_fn(double phi, double eps) {
@@ -89,62 +96,60 @@ __device__ __forceinline__ void tet_geometry(const D4 *x, G gp[12], G Gm[9], G g
   vol = det / G(6);
 }
 
-// Phase 1 for one (element, quadrature point).  R = precision of the element arithmetic;
-// tau_M and tau_C are always evaluated in FP64.
+// Phase 1a (one thread per element): geometry in FP64 (FP64 assembly, or a badly shaped
+// element in mixed assembly), else FP32.
+template <class R>
+__device__ void geom_phase(const AssembleArgs &A, int64_t e, int le, ElemShared<R> &sh) {
+  const int4 cn = A.conn[e];
+  D4 x[4] = {A.xyz[cn.x], A.xyz[cn.y], A.xyz[cn.z], A.xyz[cn.w]};
+  const bool fp64_geom = (sizeof(R) == 8) || (A.bad && A.bad[e]);
+  if (fp64_geom) {
+    double gp[12], G[9], g[3], v;
+    tet_geometry<double>(x, gp, G, g, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) sh.gphi[le][k] = (R)gp[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sh.Gm[le][k] = (R)G[k];
+    sh.gg[le] = (R)(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    sh.w[le] = (R)(0.25 * v);
+  } else {
+    float gp[12], G[9], g[3], v;
+    tet_geometry<float>(x, gp, G, g, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) sh.gphi[le][k] = (R)gp[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sh.Gm[le][k] = (R)G[k];
+    sh.gg[le] = (R)(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    sh.w[le] = (R)(0.25f * v);
+  }
+}
+
+// Phase 1b for one (element, quadrature point): u*, u^BDF, tau_M and tau_C (always FP64),
+// the resistive coefficient, and the LES vector tau_M r_M(u^EXT, p^EXT).
 template <class R>
 __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, int q, int le,
                          ElemShared<R> &sh) {
   const int4 cn = A.conn[e];
   const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
-  D4 x[4], ue[4], ub[4];
+  D4 ue[4], ub[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    x[a] = A.xyz[nd[a]];
     ue[a] = A.xext[nd[a]];
     ub[a] = A.ubdf[nd[a]];
   }
-  R gp[12], Gm[9], gv[3], vol;
-  const bool fp64_geom = (sizeof(R) == 8) || (A.bad && A.bad[e]);
-  if (fp64_geom) {
-    double gpd[12], Gd[9], gd[3], vd;
-    tet_geometry<double>(x, gpd, Gd, gd, vd);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) gp[k] = (R)gpd[k];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Gm[k] = (R)Gd[k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) gv[k] = (R)gd[k];
-    vol = (R)vd;
-  } else {
-    float gpf[12], Gf[9], gf[3], vf;
-    tet_geometry<float>(x, gpf, Gf, gf, vf);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) gp[k] = (R)gpf[k];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Gm[k] = (R)Gf[k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) gv[k] = (R)gf[k];
-    vol = (R)vf;
-  }
-  if (q == 0) {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) sh.gphi[le][k] = gp[k];
-    sh.w[le] = vol * R(0.25);
-  }
+  const R *gp = sh.gphi[le];
   // barycentric coordinates of point q: phi_a(x_q)
   R lam[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) lam[a] = (a == q) ? (R)kQA : (R)kQB;
-  // u* = u^EXT(x_q) (semi-implicit, no ALE), u^BDF(x_q), grad u^EXT, grad p^EXT
-  R us[3], ubq[3], uext_q[3];
+  // u* = u^EXT(x_q) (semi-implicit, no ALE), u^BDF(x_q)
+  R us[3], ubq[3];
   us[0] = lam[0] * (R)ue[0].x + lam[1] * (R)ue[1].x + lam[2] * (R)ue[2].x + lam[3] * (R)ue[3].x;
   us[1] = lam[0] * (R)ue[0].y + lam[1] * (R)ue[1].y + lam[2] * (R)ue[2].y + lam[3] * (R)ue[3].y;
   us[2] = lam[0] * (R)ue[0].z + lam[1] * (R)ue[1].z + lam[2] * (R)ue[2].z + lam[3] * (R)ue[3].z;
   ubq[0] = lam[0] * (R)ub[0].x + lam[1] * (R)ub[1].x + lam[2] * (R)ub[2].x + lam[3] * (R)ub[3].x;
   ubq[1] = lam[0] * (R)ub[0].y + lam[1] * (R)ub[1].y + lam[2] * (R)ub[2].y + lam[3] * (R)ub[3].y;
   ubq[2] = lam[0] * (R)ub[0].z + lam[1] * (R)ub[1].z + lam[2] * (R)ub[2].z + lam[3] * (R)ub[3].z;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) uext_q[i] = us[i];
   R adv[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) adv[a] = us[0] * gp[3 * a] + us[1] * gp[3 * a + 1] + us[2] * gp[3 * a + 2];
@@ -160,29 +165,24 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, 
     sR2 += c * c;
   }
   // tau_M, tau_C in FP64 (Section 2.3)
-  double uGu = 0.0, GG = 0.0, gg = 0.0;
+  const R *Gm = sh.Gm[le];
+  double uGu = 0.0, GG = 0.0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-      double Gkl = (double)Gm[3 * k + l];
+      const double Gkl = (double)Gm[3 * k + l];
       uGu += (double)us[k] * Gkl * (double)us[l];
       GG += Gkl * Gkl;
     }
-    gg += (double)gv[k] * (double)gv[k];
   }
   const double rho = P.rho;
-  double tsum = P.sigma * P.sigma * rho * rho / (P.dt * P.dt) + rho * rho * uGu + P.c_r * P.mu * P.mu * GG + sR2;
-  double taum = 1.0 / sqrt(tsum);
-  double tauc = 1.0 / (taum * gg);
-  const R cs = (R)(rho * P.alpha / P.dt + sR);
-  R m[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) m[i] = (R)rho * ubq[i] / (R)P.dt + (R)P.f[i];
+  const double tsum = P.sigma * P.sigma * rho * rho / (P.dt * P.dt) + rho * rho * uGu + P.c_r * P.mu * P.mu * GG + sR2;
+  const double taum = 1.0 / sqrt(tsum);
+  const double tauc = 1.0 / (taum * (double)sh.gg[le]);
   R z[3] = {R(0), R(0), R(0)};
   if (P.stab >= 2) {
     // tau_M r_M(u^EXT, p^EXT) with the strong residual of Section 2.3 (-mu Lap u = 0 for P1)
-    R ts[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       R conv = R(0), gpr = R(0);
@@ -192,13 +192,11 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, 
         conv += adv[a] * ua;
         gpr += (R)ue[a].w * gp[3 * a + i];
       }
-      R rm = (R)rho * (((R)P.alpha * uext_q[i] - ubq[i]) / (R)P.dt + conv) + gpr + (R)sR * uext_q[i] - (R)P.f[i];
-      ts[i] = (R)taum * rm;
+      const R rm = (R)rho * (((R)P.alpha * us[i] - ubq[i]) / (R)P.dt + conv) + gpr + (R)sR * us[i] - (R)P.f[i];
+      z[i] = (R)rho * (R)taum * (us[i] - (R)taum * rm);
     }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) z[i] = (R)rho * (R)taum * (us[i] - ts[i]);
   }
-  sh.cs[le][q] = cs;
+  sh.cs[le][q] = (R)(rho * P.alpha / P.dt + sR);
   sh.tm[le][q] = (R)taum;
   sh.tc[le][q] = (R)tauc;
 #pragma unroll
@@ -206,7 +204,54 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, 
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     sh.z[le][q][i] = z[i];
-    sh.m[le][q][i] = m[i];
+    sh.m[le][q][i] = (R)rho * ubq[i] / (R)P.dt + (R)P.f[i];
+  }
+}
+
+// Phase 1c for one (element, node n): per-(qp, node) products and per-node sums over the
+// quadrature points, shared by the 16 blocks of the element.
+template <class R>
+__device__ void node_phase(const PhysParams &P, int n, int le, ElemShared<R> &sh) {
+  const R w = sh.w[le];
+  const R rho = (R)P.rho;
+  const R *gn = sh.gphi[le] + 3 * n;
+  R svp = R(0), ppv = R(0), wv0 = R(0), wv1 = R(0), wv2 = R(0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const R pn = (n == q) ? (R)kQA : (R)kQB;
+    const R an = sh.adv[le][q][n];
+    const R tm = sh.tm[le][q];
+    const R cbq = sh.cs[le][q] * pn + rho * an;
+    const R *mq = sh.m[le][q];
+    sh.cb[le][q][n] = cbq;
+    sh.E[le][q][n] = (P.stab >= 1) ? w * (pn + tm * rho * an) : w * pn;
+    sh.mga[le][q][n] = mq[0] * gn[0] + mq[1] * gn[1] + mq[2] * gn[2];
+    svp += w * tm * rho * an;
+    ppv += w * tm * cbq;
+    wv0 += w * sh.z[le][q][0] * cbq;
+    wv1 += w * sh.z[le][q][1] * cbq;
+    wv2 += w * sh.z[le][q][2] * cbq;
+  }
+  sh.Svp[le][n] = svp;
+  sh.Ppv[le][n] = ppv;
+  sh.Wv[le][n][0] = wv0;
+  sh.Wv[le][n][1] = wv1;
+  sh.Wv[le][n][2] = wv2;
+  if (n == 0) {
+    R tmw = R(0), tcw = R(0), z0 = R(0), z1 = R(0), z2 = R(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      tmw += w * sh.tm[le][q];
+      tcw += w * sh.tc[le][q];
+      z0 += w * sh.z[le][q][0];
+      z1 += w * sh.z[le][q][1];
+      z2 += w * sh.z[le][q][2];
+    }
+    sh.TM[le] = tmw;
+    sh.TC[le] = tcw;
+    sh.Zv[le][0] = z0;
+    sh.Zv[le][1] = z1;
+    sh.Zv[le][2] = z2;
   }
 }
 
@@ -245,64 +290,51 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, int64_t 
   const R *ga = sh.gphi[le] + 3 * a;
   const R *gb = sh.gphi[le] + 3 * b;
   const R w = sh.w[le];
-  const R rho = (R)P.rho;
   const R gab = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
-  R Mab = R(0), TC = R(0), TM = R(0), Svp = R(0), Ppv = R(0);
-  R Wv[3] = {R(0), R(0), R(0)}, Zv[3] = {R(0), R(0), R(0)};
-  R rhs = R(0);
+  // velocity-velocity scalar: sum_q E_q(a) cb_q(b) = mass/dt + resistive + Galerkin advection
+  // + SUPG (Eq. fullydiscrete..., Eq. stabilization_form_SUPG)
+  R Mab = R(0), rhs = R(0);
   const int i_rhs = b;   // this thread also forms right-hand-side entry (a, i_rhs)
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const R pa = (a == q) ? (R)kQA : (R)kQB;
-    const R pb = (b == q) ? (R)kQA : (R)kQB;
-    const R cs = sh.cs[le][q];
-    const R tm = sh.tm[le][q];
-    const R aa = sh.adv[le][q][a];
-    const R ab = sh.adv[le][q][b];
-    const R cb = cs * pb + rho * ab;            // r~_M of the trial function phi_b e_j (per comp)
-    R Mq = cs * pa * pb + rho * pa * ab;        // mass/dt + resistive + Galerkin advection
-    if (P.stab >= 1) {
-      Mq += tm * rho * aa * cb;                 // SUPG, velocity-velocity
-      Svp += w * tm * rho * aa;                 // SUPG, pressure trial
-      Ppv += w * tm * cb;                       // PSPG, velocity trial
-      TM += w * tm;
-      TC += w * sh.tc[le][q];
-    }
-    Mab += w * Mq;
-    const R *zq = sh.z[le][q];
-    const R *mq = sh.m[le][q];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      Wv[i] += w * zq[i] * cb;                  // VMS + LES, velocity trial
-      Zv[i] += w * zq[i];                       // VMS + LES, pressure trial
-    }
-    const R mga = mq[0] * ga[0] + mq[1] * ga[1] + mq[2] * ga[2];
-    if (i_rhs < 3) {
-      R r = pa * mq[i_rhs];
-      if (P.stab >= 1) r += tm * mq[i_rhs] * rho * aa;
-      r += zq[i_rhs] * mga;
-      rhs += w * r;
-    } else if (P.stab >= 1) {
-      rhs += w * tm * mga;
-    }
+    const R Eqa = sh.E[le][q][a];
+    Mab += Eqa * sh.cb[le][q][b];
+    if (i_rhs < 3) rhs += sh.m[le][q][i_rhs] * Eqa + w * sh.z[le][q][i_rhs] * sh.mga[le][q][a];
+    else if (P.stab >= 1) rhs += w * sh.tm[le][q] * sh.mga[le][q][a];
   }
   const R vol = R(4) * w;
   const R mu = (R)P.mu;
+  const R TC = (P.stab >= 1) ? sh.TC[le] : R(0);
+  const R *Wv = sh.Wv[le][b];
   R blk[16];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
+    const R tci = TC * ga[i];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      R v = (i == j) ? (Mab + mu * vol * gab) : R(0);
-      if (P.diffusion != 0) v += mu * vol * ga[j] * gb[i];
-      v += TC * ga[i] * gb[j];
-      v += Wv[i] * ga[j];
+      R v = tci * gb[j] + Wv[i] * ga[j];                          // tau_C div-div + VMS/LES
+      if (i == j) v += Mab + mu * vol * gab;                      // + grad-grad diffusion
+      if (P.diffusion != 0) v += mu * vol * ga[j] * gb[i];        // symmetric-gradient part
       blk[4 * i + j] = v;
     }
-    blk[4 * i + 3] = -w * ga[i] + Svp * gb[i] + Zv[i] * gab;   // -(p, div v) + SUPG + VMS/LES
-    blk[12 + i] = w * gb[i] + Ppv * ga[i];                      // (div u, q) + PSPG
   }
-  blk[15] = TM * gab;                                           // PSPG
+  if (P.stab >= 1) {
+    const R svp = sh.Svp[le][a], ppv = sh.Ppv[le][b];
+    const R *Zv = sh.Zv[le];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      blk[4 * i + 3] = -w * ga[i] + svp * gb[i] + Zv[i] * gab;   // -(p, div v) + SUPG + VMS/LES
+      blk[12 + i] = w * gb[i] + ppv * ga[i];                      // (div u, q) + PSPG
+    }
+    blk[15] = sh.TM[le] * gab;                                    // PSPG
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      blk[4 * i + 3] = -w * ga[i];
+      blk[12 + i] = w * gb[i];
+    }
+    blk[15] = R(0);
+  }
   S out[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) out[k] = (S)blk[k];
@@ -319,17 +351,19 @@ __global__ void __launch_bounds__(kCta) assemble_color_kernel(AssembleArgs A, Ph
   __shared__ ElemShared<R> sh;
   const int t = threadIdx.x;
   for (int64_t base = e0 + (int64_t)blockIdx.x * kElems; base < e1; base += (int64_t)gridDim.x * kElems) {
-    {
-      const int le = t >> 2, q = t & 3;
-      const int64_t e = base + le;
-      if (e < e1) qp_phase<R>(A, P, e, q, le, sh);
-    }
+    if (t < kElems && base + t < e1) geom_phase<R>(A, base + t, t, sh);
+    __syncthreads();
+    const int le = t >> 2, q = t & 3;
+    const bool live = base + le < e1;
+    if (live) qp_phase<R>(A, P, base + le, q, le, sh);
+    __syncthreads();
+    if (live) node_phase<R>(P, q, le, sh);
     __syncthreads();
 #pragma unroll 1
     for (int pass = 0; pass < kElems * 16 / kCta; ++pass) {
-      const int le = pass * (kCta / 16) + (t >> 4);
-      const int64_t e = base + le;
-      if (e < e1) block_phase<R, S>(A, P, e, le, (t >> 2) & 3, t & 3, sh, vals);
+      const int le2 = pass * (kCta / 16) + (t >> 4);
+      const int64_t e = base + le2;
+      if (e < e1) block_phase<R, S>(A, P, e, le2, (t >> 2) & 3, t & 3, sh, vals);
     }
     __syncthreads();
   }
@@ -426,6 +460,47 @@ __global__ void apply_dirichlet_kernel(int64_t nd, const int32_t *dnode, const D
   }
 }
 
+// ||rhs|| of each component (one CTA per component, contiguous node range, fixed order)
+__global__ void comp_norm_kernel(const int32_t *comp_off, const double *rhs, double *scale) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  const int64_t i0 = 4 * (int64_t)comp_off[c], i1 = 4 * (int64_t)comp_off[c + 1];
+  double s = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += rhs[i] * rhs[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) scale[c] = red[0] > 0.0 ? 1.0 / sqrt(red[0]) : 1.0;
+}
+
+// rows of component c (matrix and right-hand side) multiplied by scale[c]; thread per scalar row
+template <class S>
+__global__ void comp_scale_kernel(int64_t V, int n_comp, const int32_t *comp_off, const double *scale,
+                                  const int32_t *rowptr, S *vals, double *rhs) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 4 * V; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = k >> 2;
+    const int i = (int)(k & 3);
+    int lo = 0, hi = n_comp - 1;             // component containing node r
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (comp_off[mid] <= r) lo = mid;
+      else hi = mid - 1;
+    }
+    const double sc = scale[lo];
+    for (int32_t kb = rowptr[r]; kb < rowptr[r + 1]; ++kb) {
+      S *blk = vals + (int64_t)kb * 16 + 4 * i;
+      blk[0] = (S)(sc * (double)blk[0]);
+      blk[1] = (S)(sc * (double)blk[1]);
+      blk[2] = (S)(sc * (double)blk[2]);
+      blk[3] = (S)(sc * (double)blk[3]);
+    }
+    rhs[k] *= sc;
+  }
+}
+
 inline int grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   if (g > 152 * 32) g = 152 * 32;
@@ -478,6 +553,15 @@ lfx_status launch_neumann(cudaStream_t st, int64_t n, const int32_t *node, const
   if (n == 0) return LFX_OK;
   note_launches(1);
   neumann_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, node, bc_of, vec, C, rhs);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+lfx_status launch_comp_normalize(cudaStream_t st, int64_t V, int n_comp, const int32_t *comp_off, double *scale,
+                                 const int32_t *rowptr, double *vals, double *rhs) {
+  comp_norm_kernel<<<n_comp, 256, 0, st>>>(comp_off, rhs, scale);
+  comp_scale_kernel<double><<<grid_for(4 * V, 256), 256, 0, st>>>(V, n_comp, comp_off, scale, rowptr, vals, rhs);
+  note_launches(2);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
 }

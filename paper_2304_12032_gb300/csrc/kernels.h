@@ -49,6 +49,11 @@ lfx_status launch_apply_dirichlet(cudaStream_t st, int64_t nd, const int32_t *dn
                                   int32_t pin_node, double pin_value, const int32_t *rowptr,
                                   const int32_t *diag, S *vals, double *rhs, double *x0);
 
+// Batched independent meshes: each connected component's rows (matrix and rhs) scaled by
+// 1/||rhs_component|| so that one Krylov solve meets every component's own tolerance.
+lfx_status launch_comp_normalize(cudaStream_t st, int64_t V, int n_comp, const int32_t *comp_off, double *scale,
+                                 const int32_t *rowptr, double *vals, double *rhs);
+
 // ------------------------------------------------------------------ block-CSR views
 template <class S>
 struct BsrView {

@@ -99,6 +99,8 @@ struct Mesh {
   std::vector<int32_t> bfaces;       // [F][3] outward oriented, internal numbering
   std::vector<int32_t> btags;        // [F]
   std::vector<double> quality;       // [T] 6 sqrt2 |K| / e_rms^3
+  int32_t n_comp = 1;                // connected components (batched independent meshes)
+  std::vector<int32_t> comp_off;     // [n_comp+1] contiguous internal node range per component
   // device copies
   DBuf d_xyz;       // double4 [V] (x, y, z, 0)
   DBuf d_conn;      // int4 [T]
@@ -107,6 +109,7 @@ struct Mesh {
   DBuf d_col;       // int32 [nnzb]
   DBuf d_diag;      // int32 [V]
   DBuf d_trans;     // int32 [nnzb]
+  DBuf d_comp_off;  // int32 [n_comp+1]
   size_t device_bytes() const;
 };
 

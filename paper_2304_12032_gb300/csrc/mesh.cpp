@@ -49,7 +49,7 @@ double signed_det(const double *x0, const double *x1, const double *x2, const do
 
 size_t Mesh::device_bytes() const {
   return d_xyz.bytes + d_conn.bytes + d_slot.bytes + d_rowptr.bytes + d_col.bytes + d_diag.bytes +
-         d_trans.bytes;
+         d_trans.bytes + d_comp_off.bytes;
 }
 
 lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_in, int64_t n_tets,
@@ -97,15 +97,44 @@ lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_
   double inv_span = span > 0 ? 1.0 / span : 1.0;
   std::vector<uint64_t> key(V);
   for (int64_t i = 0; i < V; ++i) key[i] = morton(nodes + 3 * i, lo, inv_span);
+  // connected components of the element graph (independent simulations batched in one mesh):
+  // union-find over the element vertices, components numbered by their smallest caller node
+  std::vector<int32_t> uf(V);
+  std::iota(uf.begin(), uf.end(), 0);
+  auto findr = [&](int32_t x) {
+    while (uf[x] != x) {
+      uf[x] = uf[uf[x]];
+      x = uf[x];
+    }
+    return x;
+  };
+  for (int64_t e = 0; e < T; ++e)
+    for (int a = 1; a < 4; ++a) {
+      int32_t r0 = findr(tets_in[4 * e]), r1 = findr(tets_in[4 * e + a]);
+      if (r0 != r1) uf[std::max(r0, r1)] = std::min(r0, r1);
+    }
+  std::vector<int32_t> comp_of_root(V, -1), comp_in(V);
+  int32_t ncomp = 0;
+  for (int64_t i = 0; i < V; ++i) {
+    const int32_t r = findr((int32_t)i);
+    if (comp_of_root[r] < 0) comp_of_root[r] = ncomp++;
+    comp_in[i] = comp_of_root[r];
+  }
+  m.n_comp = ncomp;
   m.node_old.resize(V);
   std::iota(m.node_old.begin(), m.node_old.end(), 0);
-  std::stable_sort(m.node_old.begin(), m.node_old.end(),
-                   [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  std::stable_sort(m.node_old.begin(), m.node_old.end(), [&](int32_t a, int32_t b) {
+    return comp_in[a] != comp_in[b] ? comp_in[a] < comp_in[b] : key[a] < key[b];
+  });
   m.node_new.assign(V, 0);
   for (int64_t i = 0; i < V; ++i) m.node_new[m.node_old[i]] = (int32_t)i;
   m.xyz.resize(3 * V);
   for (int64_t i = 0; i < V; ++i)
     for (int k = 0; k < 3; ++k) m.xyz[3 * i + k] = nodes[3 * (int64_t)m.node_old[i] + k];
+  // contiguous node range of each component in the internal numbering
+  m.comp_off.assign(ncomp + 1, 0);
+  for (int64_t i = 0; i < V; ++i) m.comp_off[comp_in[m.node_old[i]] + 1]++;
+  for (int c = 0; c < ncomp; ++c) m.comp_off[c + 1] += m.comp_off[c];
 
   // ---- elements: renumber nodes, orient, quality, Morton order of centroids
   std::vector<int32_t> tt(4 * T);
@@ -283,6 +312,7 @@ lfx_status upload_mesh(Mesh &m) {
   LFX_TRY(m.d_col.alloc(sizeof(int32_t) * m.nnzb));
   LFX_TRY(m.d_diag.alloc(sizeof(int32_t) * V));
   LFX_TRY(m.d_trans.alloc(sizeof(int32_t) * m.nnzb));
+  LFX_TRY(m.d_comp_off.alloc(sizeof(int32_t) * m.comp_off.size()));
   LFX_CUDA_TRY(cudaMemcpy(m.d_xyz.p, x4.data(), m.d_xyz.bytes, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_conn.p, m.tets.data(), sizeof(int32_t) * 4 * T, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_slot.p, m.slot.data(), sizeof(int32_t) * 16 * T, cudaMemcpyHostToDevice));
@@ -290,6 +320,8 @@ lfx_status upload_mesh(Mesh &m) {
   LFX_CUDA_TRY(cudaMemcpy(m.d_col.p, m.col_idx.data(), sizeof(int32_t) * m.nnzb, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_diag.p, m.diag_idx.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_trans.p, m.trans_idx.data(), sizeof(int32_t) * m.nnzb, cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemcpy(m.d_comp_off.p, m.comp_off.data(), sizeof(int32_t) * m.comp_off.size(),
+                          cudaMemcpyHostToDevice));
   return LFX_OK;
 }
 

@@ -61,14 +61,14 @@ class lfx_options(ctypes.Structure):
                 ("inner_max_iters", ctypes.c_int32), ("bad_element_quality", ctypes.c_double),
                 ("amg_refresh", ctypes.c_int32), ("amg_coarse_size", ctypes.c_int32),
                 ("amg_theta", ctypes.c_double), ("amg_alpha", ctypes.c_double),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("batch_normalize", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class lfx_mesh_info(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("n_tets", ctypes.c_int64), ("n_bfaces", ctypes.c_int64),
                 ("nnz_blocks", ctypes.c_int64), ("n_colors", ctypes.c_int32), ("n_flipped", ctypes.c_int32),
                 ("max_color_size", ctypes.c_int32), ("min_color_size", ctypes.c_int32),
-                ("n_bad_elements", ctypes.c_int64)]
+                ("n_bad_elements", ctypes.c_int64), ("n_components", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class lfx_step_stats(ctypes.Structure):
@@ -117,6 +117,13 @@ _SIGS = {
     "lfx_debug_precond": ([_P, _DP, _DP, _DP, _DP], ctypes.c_int32),
     "lfx_debug_solve": ([_P, _DP, ctypes.POINTER(lfx_step_stats)], ctypes.c_int32),
     "lfx_set_allocator": ([ALLOC_FN, FREE_FN, _P], ctypes.c_int32),
+    "lfx_problem_state_bytes": ([_P, _LP], ctypes.c_int32),
+    "lfx_server_create": ([ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_P)], ctypes.c_int32),
+    "lfx_server_submit": ([_P, _P, _DP, _DP, ctypes.c_double, ctypes.c_int32, _LP], ctypes.c_int32),
+    "lfx_server_poll": ([_P, ctypes.c_int64, _IP, _IP, ctypes.POINTER(lfx_step_stats)], ctypes.c_int32),
+    "lfx_server_result": ([_P, ctypes.c_int64, _DP, _DP], ctypes.c_int32),
+    "lfx_server_stats": ([_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, _LP, _LP, _LP, _LP], ctypes.c_int32),
+    "lfx_server_destroy": ([_P], None),
     "lfx_state_device_bytes": ([_P, _LP], ctypes.c_int32),
 }
 
@@ -398,3 +405,56 @@ class State:
         if getattr(self, "h", None) and _lib is not None:
             _lib.lfx_state_destroy(self.h)
             self.h = None
+
+
+class Server:
+    """Continuous-batching request loop (lfx_server_*): admission by device-memory budget,
+    resident states, round-robin stepping by native worker threads on separate streams."""
+
+    def __init__(self, hbm_budget_bytes: int, n_workers: int = 4):
+        self.h = _P()
+        _check(library().lfx_server_create(int(hbm_budget_bytes), int(n_workers), ctypes.byref(self.h)))
+        self._keep = {}
+
+    def submit(self, problem: Problem, u_hist, p_hist, t0, n_steps) -> int:
+        V = problem.mesh.n_nodes
+        u = np.ascontiguousarray(np.asarray(u_hist, dtype=np.float64).reshape(problem.bdf_order, V, 3))
+        p = np.ascontiguousarray(np.asarray(p_hist, dtype=np.float64).reshape(problem.bdf_order, V))
+        t = ctypes.c_int64()
+        _check(library().lfx_server_submit(self.h, problem.h, _d(u), _d(p), float(t0), int(n_steps), ctypes.byref(t)))
+        self._keep[t.value] = (problem, V)
+        return t.value
+
+    def poll(self, ticket):
+        done, steps = ctypes.c_int32(), ctypes.c_int32()
+        st = lfx_step_stats()
+        _check(library().lfx_server_poll(self.h, ticket, ctypes.byref(done), ctypes.byref(steps), ctypes.byref(st)))
+        return bool(done.value), steps.value, st.as_dict()
+
+    def result(self, ticket):
+        problem, V = self._keep.pop(ticket)
+        u, p = np.zeros((V, 3)), np.zeros(V)
+        _check(library().lfx_server_result(self.h, ticket, _d(u), _d(p)))
+        return u, p
+
+    def stats(self, capacity=1 << 20):
+        lat = np.zeros(capacity, dtype=np.float32)
+        n, used, waiting, peak = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(library().lfx_server_stats(self.h, lat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), capacity,
+                                          ctypes.byref(n), ctypes.byref(used), ctypes.byref(waiting), ctypes.byref(peak)))
+        return {"latency_ms": lat[:min(n.value, capacity)].copy(), "used_bytes": used.value,
+                "waiting": waiting.value, "max_active": peak.value}
+
+    def close(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lfx_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+def problem_state_bytes(problem: Problem) -> int:
+    b = ctypes.c_int64()
+    _check(library().lfx_problem_state_bytes(problem.h, ctypes.byref(b)))
+    return b.value

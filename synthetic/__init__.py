@@ -6,10 +6,10 @@ Dirichlet values).  It holds none of the finite-element method's arithmetic (no 
 integrals, no stabilisation, no solver); both the oracle and the CUDA library compute those
 on their own.
 """
-from .meshes import (Mesh, cube_kuhn, cylinder, stenosis, bifurcation, single_tet,
+from .meshes import (Mesh, cube_kuhn, cylinder, stenosis, bifurcation, single_tet, batch,
                      mesh_stats, boundary_faces)
 from .flows import beltrami_u, beltrami_p, beltrami_grad_u, poiseuille_u, poiseuille_p, zero_net_flux
 
-__all__ = ["Mesh", "cube_kuhn", "cylinder", "stenosis", "bifurcation", "single_tet",
+__all__ = ["Mesh", "cube_kuhn", "cylinder", "stenosis", "bifurcation", "single_tet", "batch",
            "mesh_stats", "boundary_faces", "beltrami_u", "beltrami_p", "beltrami_grad_u",
            "poiseuille_u", "poiseuille_p", "zero_net_flux"]

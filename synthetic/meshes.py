@@ -429,3 +429,20 @@ def mesh_stats(m: Mesh) -> dict:
         "quality_min": float(_quality(m.nodes, m.tets).min()),
         "n_bfaces": int(m.bfaces.shape[0]),
     }
+
+
+def batch(meshes, tag_stride: int = 10) -> Mesh:
+    """Several independent meshes as one disconnected mesh: node and element indices offset,
+    boundary tag t of mesh i becomes t + tag_stride * i.  Returns the union with
+    meta['node_offsets'] (len n+1) for slicing per-mesh fields."""
+    nodes, tets, bf, tg, offs = [], [], [], [], [0]
+    for i, m in enumerate(meshes):
+        o = offs[-1]
+        nodes.append(m.nodes)
+        tets.append(m.tets.astype(np.int64) + o)
+        bf.append(m.bfaces.astype(np.int64) + o)
+        tg.append(m.btags.astype(np.int64) + tag_stride * i)
+        offs.append(o + m.n_nodes)
+    return Mesh(np.concatenate(nodes), np.concatenate(tets).astype(np.int32), np.concatenate(bf).astype(np.int32),
+                np.concatenate(tg).astype(np.int32), "batch_%d" % len(meshes),
+                {"node_offsets": offs, "tag_stride": tag_stride, "names": [m.name for m in meshes]})

@@ -1,0 +1,113 @@
+"""Batching (several meshes assembled and solved as one disconnected system) and serving
+(continuous batching by the native request loop): each simulation's result must equal its solo
+run within the solution tolerance (1e-6 relative L2), and the solo run must match the oracle."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+from synthetic import batch, bifurcation, cylinder
+from tests import cases as C
+
+RHO, MU, DT = 1.06, 0.035, 1e-3
+
+
+def _members():
+    return [cylinder(1.0, 3.0, n_tets=4000, seed=31), bifurcation(n_tets=6000, seed=1001, angle_deg=40.0),
+            cylinder(0.6, 2.0, n_tets=3000, seed=33)]
+
+
+def _bcs(i, m, stride=10):
+    if "bifurcation" in m.name:
+        return [dict(tag=0 + stride * i, kind="noslip"),
+                dict(tag=1 + stride * i, kind="dirichlet", profile="uniform", time="constant", p=(8.0,)),
+                dict(tag=2 + stride * i, kind="neumann", time="constant", p=(0.0,)),
+                dict(tag=3 + stride * i, kind="neumann", time="constant", p=(0.0,))]
+    R = m.meta["radius"]
+    Q = 15.0 * math.pi * R * R / 2
+    return [dict(tag=0 + stride * i, kind="noslip"),
+            dict(tag=1 + stride * i, kind="dirichlet", profile="parabolic", time="constant", p=(Q,), radius=R),
+            dict(tag=2 + stride * i, kind="neumann", time="constant", p=(0.0,))]
+
+
+def _hist(m, seed):
+    rng = np.random.default_rng(seed)
+    V = m.n_nodes
+    return np.stack([rng.standard_normal((V, 3)) for _ in range(2)]), np.stack([rng.standard_normal(V) for _ in range(2)])
+
+
+def test_batch_components_detected_on_cpu():
+    from paper_2304_12032_gb300 import build as B
+
+    B.build()
+    from paper_2304_12032_gb300 import lfx as L
+
+    ms = _members()
+    u = batch(ms)
+    info = L.Mesh.from_synthetic(u).info()
+    assert info["n_components"] == 3
+    rp, ci = L.Mesh.from_synthetic(u).pattern()
+    offs = u.meta["node_offsets"]
+    comp = np.searchsorted(offs, np.arange(u.n_nodes), side="right") - 1
+    rows = np.repeat(np.arange(u.n_nodes), np.diff(rp))
+    assert np.array_equal(comp[rows], comp[ci])          # no coupling between members
+
+
+@pytest.mark.gpu
+def test_batched_step_equals_solo_runs():
+    ms = _members()
+    u = batch(ms)
+    offs = u.meta["node_offsets"]
+    hs = [_hist(m, 100 + i) for i, m in enumerate(ms)]
+    uh = np.concatenate([h[0] for h in hs], axis=1)
+    ph = np.concatenate([h[1] for h in hs], axis=1)
+    bcs = sum((_bcs(i, m) for i, m in enumerate(ms)), [])
+    case = C.Case(u, RHO, MU, DT, 2, bcs, [], uh, ph, 0.0)
+    _, _, st = C.gpu_state(case, gmres_rtol=1e-10)
+    st.step()
+    ub, pb = st.get()
+    for i, m in enumerate(ms):
+        solo = C.Case(m, RHO, MU, DT, 2, _bcs(0, m), [], hs[i][0], hs[i][1], 0.0)
+        _, _, s1 = C.gpu_state(solo, gmres_rtol=1e-10)
+        s1.step()
+        u1, p1 = s1.get()
+        sl = slice(offs[i], offs[i + 1])
+        ru = np.linalg.norm(ub[sl] - u1) / np.linalg.norm(u1)
+        rp = np.linalg.norm(pb[sl] - p1) / np.linalg.norm(p1)
+        assert ru <= 1e-6 and rp <= 1e-6, (i, ru, rp)
+        if i == 0:
+            ref = C.oracle_step(solo).x.reshape(-1, 4)
+            assert np.linalg.norm(u1 - ref[:, :3]) / np.linalg.norm(ref[:, :3]) <= 1e-6
+
+
+@pytest.mark.gpu
+def test_server_admits_by_budget_and_results_match_solo():
+    from paper_2304_12032_gb300 import lfx as L
+
+    ms = _members()
+    cases = [C.Case(m, RHO, MU, DT, 2, _bcs(0, m), [], *_hist(m, 200 + i), 0.0) for i, m in enumerate(ms)]
+    handles = [C.gpu_state(c, gmres_rtol=1e-10) for c in cases]
+    need = [L.problem_state_bytes(h[1]) for h in handles]
+    # room for about two simulations at a time: the third must wait for memory
+    srv = L.Server(int(sorted(need)[-1] + sorted(need)[-2] + 1), n_workers=2)
+    tickets = [srv.submit(h[1], c.u_hist, c.p_hist, c.t0, 3) for c, h in zip(cases, handles)]
+    saw_wait = srv.stats()["waiting"] > 0
+    t0 = time.time()
+    while not all(srv.poll(t)[0] for t in tickets):
+        saw_wait |= srv.stats()["waiting"] > 0
+        assert time.time() - t0 < 300
+        time.sleep(0.01)
+    stats = srv.stats()
+    assert saw_wait and stats["max_active"] <= 2
+    assert len(stats["latency_ms"]) == 9
+    for c, h, t in zip(cases, handles, tickets):
+        u, p = srv.result(t)
+        st = h[2]
+        for _ in range(3):
+            st.step()
+        u1, p1 = st.get()
+        # independent states: same kernels, same reductions -> identical results
+        assert np.allclose(u, u1, rtol=0, atol=1e-12 * np.abs(u1).max())
+        assert np.allclose(p, p1, rtol=0, atol=1e-12 * np.abs(p1).max())
+    srv.close()
