@@ -236,6 +236,86 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_serving(args):
+    """Serving workload (continuous batching): Poisson arrivals (mean args.rate req/s) of
+    simulations on cylinder / stenosis geometries drawn from a pre-generated pool (sizes
+    log-uniform in [args.serve_min, args.serve_max] tets), each asking for args.req_steps BDF2
+    steps, admitted by a device-memory budget into the native request loop.  Reports p50/p99
+    per-step latency and aggregate steps/s, beside the same requests run back to back on one
+    stream (sequential FP64 GPU)."""
+    import torch
+
+    from paper_2304_12032_gb300 import build as B
+
+    B.build()
+    from paper_2304_12032_gb300 import lfx as L
+    from synthetic import stenosis
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.default_rng(5)
+    sizes = np.exp(np.linspace(math.log(args.serve_min), math.log(args.serve_max), args.pool))
+    pool = []
+    Q = U_PEAK * math.pi * R_CM ** 2 / 2.0
+    for i, nt in enumerate(sizes):
+        m = make_case(int(nt), seed=50 + i)[0] if i % 2 == 0 else stenosis(R_CM, L_CM, n_tets=int(nt), seed=50 + i)
+        bcs = [L.BC(tag=0, kind="noslip"),
+               L.BC(tag=1, kind="dirichlet", profile="parabolic", time="ramp", p=(0.0, Q, 0.0, RAMP), radius=R_CM),
+               L.BC(tag=2, kind="neumann", time="constant", p=(0.0,))]
+        mesh = L.Mesh.from_synthetic(m)
+        prob = L.Problem(mesh, RHO, MU, DT, 2, bcs, [], L.default_options(gmres_rtol=1e-8))
+        pool.append((m, mesh, prob))
+    free = torch.cuda.mem_get_info()[0]
+    budget = int(args.serve_budget_frac * free)
+    n_req = max(1, int(round(args.rate * args.serve_seconds)))
+    gaps = rng.exponential(1.0 / args.rate, n_req)
+    picks = rng.integers(0, len(pool), n_req)
+    srv = L.Server(budget, n_workers=args.workers)
+    t0 = time.perf_counter()
+    tickets, submit_t = [], []
+    arrival = 0.0
+    for k in range(n_req):
+        arrival += gaps[k]
+        while time.perf_counter() - t0 < arrival:
+            time.sleep(0.001)
+        m, mesh, prob = pool[picks[k]]
+        V = m.n_nodes
+        tickets.append(srv.submit(prob, np.zeros((2, V, 3)), np.zeros((2, V)), 0.0, args.req_steps))
+        submit_t.append(time.perf_counter() - t0)
+    while not all(srv.poll(t)[0] for t in tickets):
+        time.sleep(0.01)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    for t in tickets:
+        srv.result(t)
+    srv.close()
+    lat = st["latency_ms"]
+    total_steps = n_req * args.req_steps
+    # sequential FP64 GPU: every distinct pool entry stepped alone, scaled by how often it was picked
+    seq_ms = 0.0
+    for j, (m, mesh, prob) in enumerate(pool):
+        cnt = int(np.sum(picks == j))
+        if cnt == 0:
+            continue
+        s1 = L.State(prob, np.zeros((2, m.n_nodes, 3)), np.zeros((2, m.n_nodes)), 0.0)
+        s1.step(allow_not_converged=True)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(min(args.req_steps, 10)):
+            s1.step(allow_not_converged=True)
+        torch.cuda.synchronize()
+        seq_ms += (time.perf_counter() - w0) * 1e3 / min(args.req_steps, 10) * args.req_steps * cnt
+    line = {"metric": "serving: per-step latency p50/p99 and aggregate steps/s (continuous batching)",
+            "value": round(total_steps / wall, 2), "unit": "steps/s", "n_gpus": 1,
+            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "requests": n_req, "steps_per_request": args.req_steps, "wall_s": round(wall, 2),
+            "sequential_fp64_steps_per_s": round(total_steps / (seq_ms * 1e-3), 2),
+            "speedup_vs_sequential": round((total_steps / wall) / (total_steps / (seq_ms * 1e-3)), 3),
+            "max_resident": st["max_active"], "budget_bytes": budget, "workers": args.workers,
+            "pool_tets": [int(p[0].n_tets) for p in pool], "arrival_rate_req_s": args.rate,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def oracle_step_time(n_tets, steps=1):
     """Times the FP64 oracle (C element loop + scipy assembly + aSIMPLE-FGMRES) on a cylinder of
     n_tets from rest, returns (seconds per step, T)."""
@@ -305,8 +385,19 @@ def main():
     ap.add_argument("--tets", type=int, default=1_000_000)
     ap.add_argument("--cpu-sample-tets", type=int, default=40_000)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--mode", default="step", choices=["step", "serving"])
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--req-steps", type=int, default=100)
+    ap.add_argument("--serve-min", type=float, default=50_000)
+    ap.add_argument("--serve-max", type=float, default=400_000)
+    ap.add_argument("--pool", type=int, default=4)
+    ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--serve-budget-frac", type=float, default=0.5)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mode == "serving":
+        run_serving(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

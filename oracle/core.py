@@ -32,7 +32,7 @@ __all__ = [
     "Params", "BC", "RIIS", "Problem", "load_library", "bdf_coefficients", "element",
     "element_residual", "geometry", "tau", "assemble", "time_law", "boundary_geometry",
     "dirichlet_data", "neumann_rhs", "apply_dirichlet", "solve_direct", "Step",
-    "step", "relative_errors", "disk_sdf", "block_of",
+    "step", "relative_errors", "disk_sdf", "block_of", "womersley_profile",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -124,7 +124,7 @@ class BC:
           'neumann' (sigma n = -h(t) n).
     time: 'constant' {value} | 'pulsatile' {gmin, gmax, period} | 'ramp' {g0, g1, t0, tL} |
           'fourier' {period, a (cosine coefficients a_0..a_K), b (sine coefficients, b_0 unused)}.
-    space: 'parabolic' {radius} | 'uniform'.
+    space: 'parabolic' {radius} | 'uniform' | 'womersley' {radius; time must be 'fourier'}.
     """
     tag: int
     kind: str
@@ -310,6 +310,20 @@ def time_law(kind: str, t: float, tp: dict) -> float:
     raise ValueError(kind)
 
 
+def womersley_profile(r, radius, omega, nu):
+    """Unit-flow-rate Womersley shape for angular frequency omega > 0 (Section 2.2.1, the
+    inverse problem of [berselli2013exact] for one Fourier harmonic): the axial velocity
+    W(r) = (1 - J0(i^{3/2} a r/R) / J0(i^{3/2} a)) / Q with a = R sqrt(omega/nu) and
+    Q = pi R^2 (1 - 2 J1(z) / (z J0(z))), z = i^{3/2} a, so that the flux of W over the disk is 1.
+    Returns complex W at radii r."""
+    from scipy.special import jv
+
+    z = np.exp(0.75j * np.pi) * radius * math.sqrt(omega / nu)
+    shape = 1.0 - jv(0, z * np.asarray(r) / radius) / jv(0, z)
+    flux = math.pi * radius ** 2 * (1.0 - 2.0 * jv(1, z) / (z * jv(0, z)))
+    return shape / flux
+
+
 def boundary_geometry(nodes, bfaces, btags, tag):
     """(barycentre, unit outward normal, area) of the faces with this tag, area weighted."""
     f = bfaces[btags == tag]
@@ -346,6 +360,19 @@ def dirichlet_data(mesh, problem: Problem, t: float, nodal: Optional[dict] = Non
                     s = -2.0 * (R * R - r2)[:, None] / (math.pi * R ** 4) * n[None, :]
                 elif bc.space == "uniform":
                     s = -np.broadcast_to(n, (sel.size, 3))
+                elif bc.space == "womersley":
+                    # u = -n [a_0 W_0(r) + sum_k Re((a_k - i b_k) W_k(r) e^{i k w t})], W_0 parabolic
+                    tp, R = bc.tparams, bc.radius
+                    w = 2.0 * math.pi / tp["period"]
+                    r = np.sqrt(np.sum((mesh.nodes[sel] - cen) ** 2, axis=1))
+                    a, bb = tp["a"], tp.get("b", [0.0] * len(tp["a"]))
+                    amp = a[0] * 2.0 * (R * R - r * r) / (math.pi * R ** 4)
+                    for k in range(1, len(a)):
+                        W = womersley_profile(r, R, k * w, problem.params.mu / problem.params.rho)
+                        amp = amp + np.real((a[k] - 1j * bb[k]) * W * np.exp(1j * k * w * t))
+                    val[sel] = -bc.theta * amp[:, None] * n[None, :]
+                    pri[sel] = 2
+                    continue
                 else:
                     raise ValueError(bc.space)
                 val[sel] = g * s

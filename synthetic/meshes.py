@@ -251,9 +251,11 @@ def _disk_points(R, z, h, rng, jitter):
 
 
 def cylinder(radius: float = 1.0, length: float = 10.0, n_tets: int = 100_000, seed: int = 2,
-             jitter: float = 0.2) -> Mesh:
+             jitter: float = 0.2, radial_scale=None) -> Mesh:
     """Straight cylinder along z (inlet z=0 tag 1, outlet z=L tag 2, wall tag 0), about
-    ``n_tets`` tetrahedra from a jittered BCC interior lattice plus wall and cap points."""
+    ``n_tets`` tetrahedra from a jittered BCC interior lattice plus wall and cap points.
+    ``radial_scale(z)`` (optional) narrows the tube: the point set is mapped r -> r s(z) before
+    the Delaunay tetrahedralisation, so every tetrahedron of the narrowed tube is valid."""
     rng = np.random.default_rng(seed)
     R, L = radius, length
     a = (12.0 * math.pi * R * R * L / n_tets) ** (1.0 / 3.0)
@@ -268,9 +270,15 @@ def cylinder(radius: float = 1.0, length: float = 10.0, n_tets: int = 100_000, s
     cap0 = cap0[np.hypot(cap0[:, 0], cap0[:, 1]) < R - 0.4 * h]
     cap1 = cap1[np.hypot(cap1[:, 0], cap1[:, 1]) < R - 0.4 * h]
     pts = np.concatenate([P, wall, cap0, cap1], axis=0)
+    sc = (lambda z: np.ones_like(z)) if radial_scale is None else radial_scale
+    if radial_scale is not None:
+        f = sc(pts[:, 2])
+        pts = pts.copy()
+        pts[:, 0] *= f
+        pts[:, 1] *= f
 
     def inside(c):
-        return (np.hypot(c[:, 0], c[:, 1]) < R) & (c[:, 2] > 0) & (c[:, 2] < L)
+        return (np.hypot(c[:, 0], c[:, 1]) < R * sc(c[:, 2])) & (c[:, 2] > 0) & (c[:, 2] < L)
 
     tets = _delaunay_clean(pts, inside)
 
@@ -288,20 +296,21 @@ def cylinder(radius: float = 1.0, length: float = 10.0, n_tets: int = 100_000, s
 
 def stenosis(radius: float = 1.0, length: float = 10.0, n_tets: int = 400_000, seed: int = 3,
              z_center: float = 3.0, half_length: float = 1.0, severity: float = 0.25) -> Mesh:
-    """Cylinder with an axisymmetric cosine stenosis: the cylinder mesh radially mapped by
-    r -> r * (1 - severity*(1+cos(pi*(z-z_center)/half_length))) inside |z-z_center|<=half_length.
-    severity=0.25 gives a throat of half the radius, i.e. a 75% area reduction."""
-    m = cylinder(radius, length, n_tets, seed)
-    z = m.nodes[:, 2]
-    s = np.ones_like(z)
-    w = np.abs(z - z_center) <= half_length
-    s[w] = 1.0 - severity * (1.0 + np.cos(math.pi * (z[w] - z_center) / half_length))
-    nodes = m.nodes.copy()
-    nodes[:, 0] *= s
-    nodes[:, 1] *= s
+    """Cylinder with an axisymmetric cosine stenosis: radius R s(z), s = 1 - severity (1 + cos(pi
+    (z - z_center)/half_length)) inside |z - z_center| <= half_length.  severity = 0.25 gives a throat
+    of half the radius, i.e. a 75 % area reduction.  The cylinder's point set is mapped and then
+    tetrahedralised, so the elements are valid Delaunay tetrahedra of the narrowed tube."""
+
+    def scale(z):
+        s = np.ones_like(z)
+        w = np.abs(z - z_center) <= half_length
+        s[w] = 1.0 - severity * (1.0 + np.cos(math.pi * (z[w] - z_center) / half_length))
+        return s
+
+    m = cylinder(radius, length, n_tets, seed, radial_scale=scale)
     meta = dict(m.meta)
     meta.update(z_center=z_center, half_length=half_length, severity=severity)
-    return Mesh(nodes, m.tets, m.bfaces, m.btags, f"stenosis_{n_tets}_{seed}", meta)
+    return Mesh(m.nodes, m.tets, m.bfaces, m.btags, f"stenosis_{n_tets}_{seed}", meta)
 
 
 def _seg_cyl_sdf(p, a, b, r):

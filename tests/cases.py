@@ -9,7 +9,7 @@ from typing import Optional
 
 import numpy as np
 
-from synthetic import (beltrami_p, beltrami_u, bifurcation, cube_kuhn, cylinder, zero_net_flux)
+from synthetic import (beltrami_p, beltrami_u, bifurcation, cube_kuhn, cylinder, stenosis, zero_net_flux)
 
 
 @dataclasses.dataclass
@@ -62,6 +62,25 @@ def vessel_case(n_tets=6000, seed=21, order=2, stab=2, diffusion=0, riis=True, n
            dict(tag=2, kind="neumann", time="constant", p=(neumann_h,))]
     rs = [dict(resistance=1e4, eps=0.25, center=(0.0, 0.0, L / 2), normal=(0.0, 0.0, 1.0), radius=0.6)] if riis else []
     return Case(m, 1.06, 0.035, 1e-3, order, bcs, rs, uh, ph, 0.1, stab, diffusion, (0.0, 0.0, 0.0))
+
+
+def stenosis_case(n_tets=8000, seed=3, order=2, harmonics=3):
+    """Config-3 shape at small size: cosine stenosis (75 % area reduction), Womersley inlet
+    with a Fourier flow rate (period 1 s), a disk resistive surface downstream, VMS-LES."""
+    R, L = 1.0, 10.0
+    m = stenosis(R, L, n_tets=n_tets, seed=seed)
+    rng = np.random.default_rng(seed)
+    V = m.n_nodes
+    uh = np.stack([rng.standard_normal((V, 3)) for _ in range(order)])
+    ph = np.stack([rng.standard_normal(V) for _ in range(order)])
+    qpk = math.pi * R * R * 33.0
+    a = [0.5 * qpk] + [(-0.5 * qpk if k == 1 else 0.1 * qpk / k) for k in range(1, harmonics + 1)]
+    b = [0.0] + [0.05 * qpk * k for k in range(1, harmonics + 1)]
+    bcs = [dict(tag=0, kind="noslip"),
+           dict(tag=1, kind="dirichlet", profile="womersley", time="fourier", p=(1.0,), a=a, b=b, radius=R),
+           dict(tag=2, kind="neumann", time="constant", p=(0.0,))]
+    rs = [dict(resistance=1e4, eps=0.3, center=(0.0, 0.0, 5.0), normal=(0.0, 0.0, 1.0), radius=0.5)]
+    return Case(m, 1.06, 0.035, 5e-4, order, bcs, rs, uh, ph, 0.37, 2, 0, (0.0, 0.0, 0.0))
 
 
 def bifurcation_case(n_tets=8000, seed=1003, order=3, stab=1):

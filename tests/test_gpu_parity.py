@@ -24,6 +24,7 @@ CASES = {
     "vessel_vms_riis": lambda: C.vessel_case(6000, seed=21),
     "vessel_symgrad_bdf1": lambda: C.vessel_case(5000, seed=22, order=1, diffusion=2),
     "bifurcation_supg_bdf3": lambda: C.bifurcation_case(8000, seed=1003),
+    "stenosis_womersley_riis": lambda: C.stenosis_case(8000, seed=3),
     "galerkin_only": lambda: C.vessel_case(3000, seed=23, stab=0, riis=False),
 }
 

@@ -213,3 +213,37 @@ def test_asimple_gmres_solves_navier_stokes_system():
     xd = O.solve_direct(A, b)
     x, its, _ = O.fgmres(A, b, M=O.ASimple(A).apply, restart=40, tol=1e-13)
     assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+# ---------------------------- Womersley inlet profile (Section 2.2.1) ----------------------
+def test_womersley_unit_flux_and_wall_value():
+    from scipy.integrate import quad
+
+    R, nu = 1.0, 0.035 / 1.06
+    for omega in (2 * math.pi, 10 * math.pi):
+        re = quad(lambda r: np.real(O.womersley_profile(r, R, omega, nu)) * 2 * math.pi * r, 0, R, limit=200)[0]
+        im = quad(lambda r: np.imag(O.womersley_profile(r, R, omega, nu)) * 2 * math.pi * r, 0, R, limit=200)[0]
+        assert re == pytest.approx(1.0, abs=1e-9) and abs(im) < 1e-9
+        assert abs(O.womersley_profile(R, R, omega, nu)) < 1e-12
+
+
+def test_womersley_small_frequency_is_poiseuille():
+    R, nu = 0.8, 1.0
+    r = np.linspace(0, R, 9)
+    W = O.womersley_profile(r, R, 1e-6, nu)
+    assert np.allclose(W.real, 2 * (R * R - r * r) / (math.pi * R ** 4), rtol=1e-6, atol=1e-9)
+    assert np.abs(W.imag).max() < 1e-5
+
+
+def test_womersley_solves_the_oscillatory_pipe_equation():
+    # For u = W(r) e^{i w t}: i w W = -dp/dz + nu (W'' + W'/r) with a uniform pressure gradient,
+    # so W'' + W'/r - (i w / nu) W is the same constant at every radius.
+    R, nu, omega = 1.0, 0.05, 4.0
+    h = 1e-4
+    vals = []
+    for r in (0.2, 0.45, 0.7, 0.9):
+        Wm, W0, Wp = O.womersley_profile(np.array([r - h, r, r + h]), R, omega, nu)
+        lap = (Wp - 2 * W0 + Wm) / h ** 2 + (Wp - Wm) / (2 * h * r)
+        vals.append(lap - 1j * omega / nu * W0)
+    vals = np.array(vals)
+    assert np.abs(vals - vals[0]).max() <= 1e-5 * np.abs(vals[0])
