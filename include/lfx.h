@@ -263,6 +263,31 @@ lfx_status lfx_debug_precond(lfx_state *state, const double *r, double *z, doubl
 lfx_status lfx_debug_solve(lfx_state *state, double *x, lfx_step_stats *stats);
 
 /* ------------------------------------------------------------------------------------------
+ * Allocation-free preconditioner application (the paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory, e.g. while a CUDA graph is being captured,
+ * inside a framework that owns all device memory, or in a loop that must not allocate).
+ *
+ * z = P^-1 r with the aSIMPLE preconditioner (the same kernels as lfx_step's) for a 4x4
+ * block-CSR matrix the caller already holds on the device: row_ptr [n_nodes+1], col_idx
+ * [nnz_blocks], diag_idx [n_nodes] (position of block (i,i)), trans_idx [nnz_blocks] (position of
+ * block (j,i) for block (i,j)), blocks [nnz_blocks][4][4] FP64 row-major with unknowns
+ * (u_x, u_y, u_z, p) per node; r, z [n_nodes][4] FP64.  All pointers are device pointers and the
+ * caller owns them; z must not alias r.  opt selects the smoothers (Jacobi or Chebyshev only;
+ * NULL = defaults with a 6-step Chebyshev Schur smoother).
+ *
+ * No memory is allocated: all intermediate arrays live in one 16 MiB static device array that
+ * every GPU loading the library holds until process exit; n_nodes above 65536 is rejected with
+ * LFX_ERR_INVALID_ARG.  The first call on a device looks the array's address up (make that
+ * first call before any stream capture begins).  Every call reuses the same array and clears
+ * it first, so calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller.  Work is queued on cuda_stream (NULL =
+ * legacy default stream); the call does not synchronise. */
+lfx_status lfx_asimple_apply_noalloc(int64_t n_nodes, const int32_t *row_ptr, const int32_t *col_idx,
+                                     const int32_t *diag_idx, const int32_t *trans_idx,
+                                     const double *blocks, const double *r, double *z,
+                                     const lfx_options *opt, void *cuda_stream);
+
+/* ------------------------------------------------------------------------------------------
  * Device memory: optional allocator hook (e.g. a framework's caching allocator)
  * ------------------------------------------------------------------------------------------ */
 typedef void *(*lfx_alloc_fn)(size_t bytes, void *ctx);

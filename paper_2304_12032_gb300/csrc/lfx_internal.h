@@ -43,10 +43,11 @@ void dfree(void *p);
 struct DBuf {
   void *p = nullptr;
   size_t bytes = 0;
+  bool owned = true;   // false: a slice of memory owned elsewhere (never freed here)
   DBuf() = default;
   DBuf(const DBuf &) = delete;
   DBuf &operator=(const DBuf &) = delete;
-  DBuf(DBuf &&o) noexcept : p(o.p), bytes(o.bytes) {
+  DBuf(DBuf &&o) noexcept : p(o.p), bytes(o.bytes), owned(o.owned) {
     o.p = nullptr;
     o.bytes = 0;
   }
@@ -55,6 +56,7 @@ struct DBuf {
       release();
       p = o.p;
       bytes = o.bytes;
+      owned = o.owned;
       o.p = nullptr;
       o.bytes = 0;
     }
@@ -62,9 +64,16 @@ struct DBuf {
   }
   ~DBuf() { release(); }
   void release() {
-    if (p) dfree(p);
+    if (p && owned) dfree(p);
     p = nullptr;
     bytes = 0;
+    owned = true;
+  }
+  void borrow(void *ptr, size_t n) {
+    release();
+    p = ptr;
+    bytes = n;
+    owned = false;
   }
   lfx_status alloc(size_t n) {
     release();

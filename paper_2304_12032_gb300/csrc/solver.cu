@@ -933,6 +933,40 @@ lfx_status ASimple<S, T>::init(int64_t V_, const SmootherConfig &cfg_) {
 }
 
 template <class S, class T>
+size_t ASimple<S, T>::scratch_bytes(int64_t V) {
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t vb = up(sizeof(T) * 4 * (size_t)V);
+  return 6 * vb + up(sizeof(T) * (size_t)V) + up(sizeof(SmoothCoef)) + up(sizeof(double) * (size_t)(rows_grid(V) + 1));
+}
+
+template <class S, class T>
+lfx_status ASimple<S, T>::init_borrowed(int64_t V_, const SmootherConfig &cfg_, void *base, size_t cap,
+                                        cudaStream_t st) {
+  V = V_;
+  cfg = cfg_;
+  if (scratch_bytes(V) > cap) {
+    set_error("aSIMPLE: %zu bytes of work memory needed, %zu available", scratch_bytes(V), cap);
+    return LFX_ERR_INVALID_ARG;
+  }
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  char *p = static_cast<char *>(base);
+  const size_t vb = up(sizeof(T) * 4 * (size_t)V);
+  DBuf *vecs[6] = {&dinvF, &X, &D0, &D1, &R, &W};
+  for (DBuf *d : vecs) {
+    d->borrow(p, vb);
+    p += vb;
+  }
+  dinvS.borrow(p, up(sizeof(T) * (size_t)V));
+  p += up(sizeof(T) * (size_t)V);
+  coef.borrow(p, up(sizeof(SmoothCoef)));
+  p += up(sizeof(SmoothCoef));
+  part.borrow(p, up(sizeof(double) * (size_t)(rows_grid(V) + 1)));
+  // the memory keeps whatever the previous user left: clear the iterates that start at zero
+  LFX_CUDA_TRY(cudaMemsetAsync(base, 0, scratch_bytes(V), st));
+  return LFX_OK;
+}
+
+template <class S, class T>
 size_t ASimple<S, T>::device_bytes() const {
   return dinvF.bytes + dinvS.bytes + X.bytes + D0.bytes + D1.bytes + R.bytes + W.bytes + coef.bytes + part.bytes;
 }

@@ -71,6 +71,9 @@ struct ASimple {
   lfx_status vcycle(cudaStream_t st, int l, const KState *ks);
   size_t amg_bytes() const;
   lfx_status init(int64_t V, const SmootherConfig &cfg);
+  // Work arrays carved from caller-provided device memory (no allocation); zeroed on st.
+  static size_t scratch_bytes(int64_t V);
+  lfx_status init_borrowed(int64_t V, const SmootherConfig &cfg, void *base, size_t cap, cudaStream_t st);
   lfx_status setup(cudaStream_t st, const BsrView<S> &A);
   lfx_status apply(cudaStream_t st, const BsrView<S> &A, const T *r, T *z, const KState *ks);
   lfx_status lambdas(double *lf, double *ls) const;

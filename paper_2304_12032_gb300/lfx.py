@@ -124,6 +124,8 @@ _SIGS = {
     "lfx_server_result": ([_P, ctypes.c_int64, _DP, _DP], ctypes.c_int32),
     "lfx_server_stats": ([_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, _LP, _LP, _LP, _LP], ctypes.c_int32),
     "lfx_server_destroy": ([_P], None),
+    "lfx_asimple_apply_noalloc": ([ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(lfx_options), _P],
+                                  ctypes.c_int32),
     "lfx_state_device_bytes": ([_P, _LP], ctypes.c_int32),
 }
 
