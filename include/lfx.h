@@ -161,7 +161,8 @@ typedef struct lfx_options {
   int32_t gmres_restart;        /* default 40                                                  */
   int32_t gmres_max_iters;      /* total Arnoldi steps cap; default 1000                       */
   double gmres_rtol;            /* stop when ||b - A x|| <= rtol ||b||; default 1e-10         */
-  int32_t reorthogonalize;      /* classical Gram-Schmidt twice (1, default) or once (0)        */
+  int32_t reorthogonalize;      /* classical Gram-Schmidt twice (1, default) or once (0); in mixed
+                                   precision the FP32 inner solve orthogonalises twice only if 2  */
   /* aSIMPLE: velocity block F and Schur approximation S = C - D diag(F)^-1 G */
   int32_t f_smoother, f_steps;  /* LFX_SMOOTH_*, steps; default Chebyshev, 3                   */
   double f_omega, f_ratio;      /* Jacobi damping; Chebyshev lmax/lmin; default 0.7, 20        */

@@ -971,13 +971,13 @@ static lfx_status run_solve(lfx_state *s, double *x, bool x_zero, int *its, int 
         return s->pcbf.apply(qq, Ab, vv, zz, kk);
       };
       rc = s->gm32.solve(q, A32, pc, s->r32.as<float>(), s->z32.as<float>(), o.inner_rtol, o.inner_max_iters,
-                         o.reorthogonalize != 0, 2, true, &it, &r);
+                         o.reorthogonalize == 2, 2, true, &it, &r);
     } else {
       auto pc = [s, A32](cudaStream_t qq, const float *vv, float *zz, const KState *kk) {
         return s->pc32.apply(qq, A32, vv, zz, kk);
       };
       rc = s->gm32.solve(q, A32, pc, s->r32.as<float>(), s->z32.as<float>(), o.inner_rtol, o.inner_max_iters,
-                         o.reorthogonalize != 0, 2, true, &it, &r);
+                         o.reorthogonalize == 2, 2, true, &it, &r);
     }
     s->inner_total += it;
     if (rc != LFX_OK && rc != LFX_ERR_NOT_CONVERGED) return rc;

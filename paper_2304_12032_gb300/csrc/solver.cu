@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(BsrView<S> A, const T *_
   T acc[4] = {T(0), T(0), T(0), T(0)};
   if (row < A.V) {
     const int32_t k1 = A.rowptr[row + 1];
+#pragma unroll 2
     for (int32_t k = A.rowptr[row] + lane; k < k1; k += kRowGroup) {
       T blk[16];
       ld_block<S, T>(A.vals, k, blk);
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(kThreads) bound_kernel(BsrView<S> A, const T *
   const int lane = threadIdx.x % kRowGroup;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
   if (row < A.V) {
+#pragma unroll 2
     for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
       T blk[16];
       ld_block<S, T>(A.vals, kb, blk);
@@ -293,6 +295,7 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(BsrView<S> A, const T 
   const int lane = threadIdx.x % kRowGroup;
   T acc[3] = {T(0), T(0), T(0)};
   if (row < A.V) {
+#pragma unroll 2
     for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
       T blk[16];
       ld_block<S, T>(A.vals, kb, blk);
@@ -340,6 +343,7 @@ __global__ void __launch_bounds__(kThreads) g_scaled_kernel(BsrView<S> A, const 
   const int lane = threadIdx.x % kRowGroup;
   T acc[3] = {T(0), T(0), T(0)};
   if (row < A.V) {
+#pragma unroll 2
     for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
       const S *blk = A.vals + 16 * (int64_t)kb;
       const T p = ld4(in, A.col[kb]).w;
@@ -370,6 +374,7 @@ __global__ void __launch_bounds__(kThreads) s_step_kernel(BsrView<S> A, const T 
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
   if (row < A.V) {
+#pragma unroll 2
     for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
       const S *blk = A.vals + 16 * (int64_t)kb;
       const int32_t c = A.col[kb];
@@ -438,6 +443,7 @@ __global__ void __launch_bounds__(kThreads) d_init_kernel(BsrView<S> A, const T 
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
   if (row < A.V) {
+#pragma unroll 2
     for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
       const S *blk = A.vals + 16 * (int64_t)kb;
       const auto xv = ld4(x, A.col[kb]);
@@ -473,6 +479,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(BsrView<S> A, const T *
   const int lane = threadIdx.x % kRowGroup;
   T acc[3] = {T(0), T(0), T(0)};
   if (row < A.V) {
+#pragma unroll 2
     for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
       const S *blk = A.vals + 16 * (int64_t)kb;
       const T p = ld4(x, A.col[kb]).w;
@@ -508,6 +515,7 @@ __global__ void __launch_bounds__(kThreads) s_resid_kernel(BsrView<S> A, const T
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
   if (row < A.V) {
+#pragma unroll 2
     for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
       const S *blk = A.vals + 16 * (int64_t)kb;
       const int32_t c = A.col[kb];
@@ -560,16 +568,17 @@ __global__ void csr_spmv_kernel(CsrV M, const T *in, int is, int io, T *out, int
   }
 }
 
-// r = b - A x
-template <class T>
+// r = b - A x  (G lanes per row)
+template <class T, int G>
 __global__ void csr_resid_kernel(CsrV M, const T *x, const T *b, T *out, const KState *st) {
   if (finished(st)) return;
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
-  const int lane = threadIdx.x % kRowGroup;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int lane = threadIdx.x % G;
   double s = 0.0;
   if (row < M.n)
-    for (int32_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += kRowGroup) s += M.v[k] * (double)x[M.ci[k]];
-  s = group_sum(s);
+    for (int32_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += G) s += M.v[k] * (double)x[M.ci[k]];
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (row < M.n && lane == 0) out[row] = (T)((double)b[row] - s);
 }
 
@@ -588,16 +597,17 @@ __global__ void csr_cheb_init_kernel(int64_t n, const double *dinv, const T *rhs
 }
 
 // Chebyshev step on a CSR level: y = A d_old; r -= dinv y; d_new = c1 d_old + c2 r; x += d_new
-template <class T>
+template <class T, int G>
 __global__ void csr_cheb_step_kernel(CsrV M, const double *dinv, const T *d_old, T *d_new, T *r, T *x, double c1,
                                      double c2, const KState *st) {
   if (finished(st)) return;
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
-  const int lane = threadIdx.x % kRowGroup;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int lane = threadIdx.x % G;
   double s = 0.0;
   if (row < M.n)
-    for (int32_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += kRowGroup) s += M.v[k] * (double)d_old[M.ci[k]];
-  s = group_sum(s);
+    for (int32_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += G) s += M.v[k] * (double)d_old[M.ci[k]];
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (row < M.n && lane == 0) {
     const double rv = (double)r[row] - dinv[row] * s;
     const double dv = c1 * (double)d_old[row] + c2 * rv;
@@ -690,30 +700,45 @@ __global__ void coef_kernel(SmoothCoef *cf, int f_kind, int f_steps, double f_om
 // ------------------------------------------------------------------------------------------
 // Krylov kernels
 // ------------------------------------------------------------------------------------------
-// part[blk][i] = sum over this CTA's range of w . v_i, i < nvec
+// part[i][blk] = this CTA's share of w . v_i, i < nvec.  Vectors are read four values at a time
+// in a grid-strided (coalesced) order; eight basis vectors per pass over w.
 template <class T>
 __global__ void __launch_bounds__(kThreads) mdot_kernel(const T *Vb, int64_t ld, int nvec, const T *w,
                                                         int64_t n, double *part, int ldp,
                                                         const KState *st) {
   if (finished(st)) return;
-  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  using V4 = typename Vec4T<T>::type;
+  __shared__ double red[8][kThreads / 32];
+  const int64_t n4 = n >> 2, ld4 = ld >> 2;
+  const V4 *w4 = reinterpret_cast<const V4 *>(w);
+  const V4 *b4 = reinterpret_cast<const V4 *>(Vb);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int v0 = 0; v0 < nvec; v0 += 8) {
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int nv = min(8, nvec - v0);
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const double wi = (double)w[i];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+      const V4 wv = w4[i];
 #pragma unroll
       for (int k = 0; k < 8; ++k)
-        if (k < nv) acc[k] += wi * (double)Vb[(int64_t)(v0 + k) * ld + i];
+        if (k < nv) {
+          const V4 b = b4[(int64_t)(v0 + k) * ld4 + i];
+          acc[k] += (double)wv.x * (double)b.x + (double)wv.y * (double)b.y + (double)wv.z * (double)b.z +
+                    (double)wv.w * (double)b.w;
+        }
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      if (k < nv) {
-        double s = cta_sum(acc[k]);
-        if (threadIdx.x == 0) part[(int64_t)(v0 + k) * ldp + blockIdx.x] = s;   // [vector][block]
-      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+      if (lane == 0) red[k][warp] = acc[k];
     }
+    __syncthreads();
+    if ((int)threadIdx.x < nv) {
+      double s = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
+      part[(int64_t)(v0 + threadIdx.x) * ldp + blockIdx.x] = s;   // [vector][block]
+    }
+    __syncthreads();
   }
 }
 
@@ -733,20 +758,38 @@ __global__ void mdot_finalize_kernel(const double *part, int nblk, int ldp, int 
   }
 }
 
-// w -= sum_i hwork[i] v_i ; partial |w|^2
+// w -= sum_i hwork[i] v_i ; partial |w|^2 (four values per load, grid-strided)
 template <class T>
 __global__ void __launch_bounds__(kThreads) maxpy_kernel(const T *Vb, int64_t ld, int nvec, T *w,
                                                          int64_t n, double *part, KState *st) {
   if (finished(st)) return;
+  using V4 = typename Vec4T<T>::type;
   __shared__ double h[kMaxRestart + 1];
   for (int i = threadIdx.x; i < nvec; i += blockDim.x) h[i] = st->hwork[i];
   __syncthreads();
+  const int64_t n4 = n >> 2, ld4 = ld >> 2;
+  V4 *w4 = reinterpret_cast<V4 *>(w);
+  const V4 *b4 = reinterpret_cast<const V4 *>(Vb);
   double nrm = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double a = (double)w[i];
-    for (int k = 0; k < nvec; ++k) a -= h[k] * (double)Vb[(int64_t)k * ld + i];
-    w[i] = (T)a;
-    nrm += a * a;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const V4 wv = w4[i];
+    double a0 = (double)wv.x, a1 = (double)wv.y, a2 = (double)wv.z, a3 = (double)wv.w;
+#pragma unroll 4
+    for (int k = 0; k < nvec; ++k) {
+      const V4 b = b4[(int64_t)k * ld4 + i];
+      const double hk = h[k];
+      a0 -= hk * (double)b.x;
+      a1 -= hk * (double)b.y;
+      a2 -= hk * (double)b.z;
+      a3 -= hk * (double)b.w;
+    }
+    V4 o;
+    o.x = (T)a0;
+    o.y = (T)a1;
+    o.z = (T)a2;
+    o.w = (T)a3;
+    w4[i] = o;
+    nrm += a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3;
   }
   double s = cta_sum(nrm);
   if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
@@ -877,6 +920,7 @@ __global__ void update_x_kernel(const T *Zb, int64_t ld, X *x, int64_t n, const 
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double a = (double)x[i];
+#pragma unroll 4
     for (int k = 0; k < j; ++k) a += y[k] * (double)Zb[(int64_t)k * ld + i];
     x[i] = (X)a;
   }
@@ -1156,6 +1200,8 @@ size_t ASimple<S, T>::amg_bytes() const {
   return b;
 }
 
+static inline double H_nnz(const AmgDevLevel &D) { return (double)D.v.bytes / sizeof(double); }
+
 // One V-cycle on the explicit levels l >= 1 for amg[l].b -> amg[l].x
 template <class S, class T>
 lfx_status ASimple<S, T>::vcycle(cudaStream_t st, int l, const KState *ks) {
@@ -1173,20 +1219,32 @@ lfx_status ASimple<S, T>::vcycle(cudaStream_t st, int l, const KState *ks) {
   const int vg = vec_grid(D.n), rg = rows_grid(D.n);
   T *d[2] = {D.d0.as<T>(), D.d1.as<T>()};
   const double *dinv = D.dinv.as<double>();
+  const bool wide = D.rp.p && D.n > 0 && (double)(H_nnz(D)) / (double)D.n > 24.0;
+  const int rg32 = (int)((D.n * 32 + kThreads - 1) / kThreads);
+  auto cheb_step = [&](int k) {
+    if (wide)
+      csr_cheb_step_kernel<T, 32><<<rg32, kThreads, 0, st>>>(A, dinv, d[(k - 1) & 1], d[k & 1], D.r.as<T>(),
+                                                             D.x.as<T>(), D.c1[k], D.c2[k], ks);
+    else
+      csr_cheb_step_kernel<T, 8><<<rg, kThreads, 0, st>>>(A, dinv, d[(k - 1) & 1], d[k & 1], D.r.as<T>(),
+                                                          D.x.as<T>(), D.c1[k], D.c2[k], ks);
+  };
+  auto resid = [&]() {
+    if (wide)
+      csr_resid_kernel<T, 32><<<rg32, kThreads, 0, st>>>(A, D.x.as<T>(), D.b.as<T>(), D.rr.as<T>(), ks);
+    else
+      csr_resid_kernel<T, 8><<<rg, kThreads, 0, st>>>(A, D.x.as<T>(), D.b.as<T>(), D.rr.as<T>(), ks);
+  };
   csr_cheb_init_kernel<T><<<vg, kThreads, 0, st>>>(D.n, dinv, D.b.as<T>(), D.r.as<T>(), d[0], D.x.as<T>(), D.init, 0, ks);
-  for (int k = 1; k < cfg.s_steps; ++k)
-    csr_cheb_step_kernel<T><<<rg, kThreads, 0, st>>>(A, dinv, d[(k - 1) & 1], d[k & 1], D.r.as<T>(), D.x.as<T>(),
-                                                     D.c1[k], D.c2[k], ks);
-  csr_resid_kernel<T><<<rg, kThreads, 0, st>>>(A, D.x.as<T>(), D.b.as<T>(), D.rr.as<T>(), ks);
+  for (int k = 1; k < cfg.s_steps; ++k) cheb_step(k);
+  resid();
   csr_spmv_kernel<T, 32><<<(int)((D.nnext * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
       R, D.rr.as<T>(), 1, 0, amg[l + 1].b.as<T>(), 1, 0, 1.0, 0, ks);
   LFX_TRY(vcycle(st, l + 1, ks));
   csr_spmv_kernel<T, 8><<<rg, kThreads, 0, st>>>(P, amg[l + 1].x.as<T>(), 1, 0, D.x.as<T>(), 1, 0, amg_alpha, 1, ks);
-  csr_resid_kernel<T><<<rg, kThreads, 0, st>>>(A, D.x.as<T>(), D.b.as<T>(), D.rr.as<T>(), ks);
+  resid();
   csr_cheb_init_kernel<T><<<vg, kThreads, 0, st>>>(D.n, dinv, D.rr.as<T>(), D.r.as<T>(), d[0], D.x.as<T>(), D.init, 1, ks);
-  for (int k = 1; k < cfg.s_steps; ++k)
-    csr_cheb_step_kernel<T><<<rg, kThreads, 0, st>>>(A, dinv, d[(k - 1) & 1], d[k & 1], D.r.as<T>(), D.x.as<T>(),
-                                                     D.c1[k], D.c2[k], ks);
+  for (int k = 1; k < cfg.s_steps; ++k) cheb_step(k);
   note_launches(6 + 2 * (cfg.s_steps - 1));
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
