@@ -228,7 +228,9 @@ typedef struct lfx_step_stats {
   int32_t converged;
   float ms_assembly_kernels;    /* the coloured assembly launches alone (CUDA events)          */
   int32_t n_assembly_launches;  /* launches of the assembly kernel in this step (= colours)    */
-  int32_t reserved[5];
+  float ms_spmv;                /* Arnoldi block SpMV launches of the (inner) Krylov solve      */
+  int32_t n_spmv;               /* their number (FP64 matrix on the FP64 path, FP32 in mixed)   */
+  int32_t reserved[3];
 } lfx_step_stats;
 
 /* One semi-implicit BDF step t^n -> t^{n+1}: BDF/EXT fields, coloured assembly of the

@@ -1007,6 +1007,8 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   LFX_TRY(prepare_precond(s));
   int its = 0, outer = 0;
   double rel = 0.0;
+  s->gm64.n_tev = 0;
+  s->gm32.n_tev = 0;
   lfx_status rc = run_solve(s, s->xsol.as<double>(), false, &its, &outer, &rel);
   if (rc != LFX_OK && rc != LFX_ERR_NOT_CONVERGED) return rc;
   LFX_CUDA_TRY(cudaEventRecord(s->e2, st));
@@ -1029,6 +1031,14 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
     cudaEventElapsedTime(&stats->ms_total, s->e0, s->e2);
     cudaEventElapsedTime(&stats->ms_assembly_kernels, s->ea0, s->ea1);
     stats->n_assembly_launches = s->n_asm_launch;
+    if (o.precision == LFX_PREC_MIXED) {
+      s->gm32.read_spmv_timing(&stats->ms_spmv, &stats->n_spmv);
+      int dummy = 0;
+      float d2 = 0.0f;
+      s->gm64.read_spmv_timing(&d2, &dummy);
+    } else {
+      s->gm64.read_spmv_timing(&stats->ms_spmv, &stats->n_spmv);
+    }
     stats->converged = rc == LFX_OK;
   }
   return rc;
@@ -1148,6 +1158,8 @@ lfx_status lfx_debug_solve(lfx_state *s, double *x, lfx_step_stats *stats) {
   LFX_CUDA_TRY(cudaMemsetAsync(dx.p, 0, dx.bytes, s->stream));
   (void)o;
   LFX_TRY(prepare_precond(s));
+  s->gm64.n_tev = 0;
+  s->gm32.n_tev = 0;
   int its = 0, outer = 0;
   double rel = 0;
   lfx_status rc = run_solve(s, dx.as<double>(), true, &its, &outer, &rel);

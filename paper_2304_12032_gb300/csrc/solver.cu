@@ -1286,7 +1286,25 @@ lfx_status Gmres<S, T>::init(int64_t V_, int restart_) {
 }
 
 template <class S, class T>
+lfx_status Gmres<S, T>::read_spmv_timing(float *ms, int *count) {
+  float total = 0.0f;
+  int c = 0;
+  for (int i = 0; i + 1 < n_tev; i += 2) {
+    LFX_CUDA_TRY(cudaEventSynchronize(tev[i + 1]));
+    float t = 0.0f;
+    LFX_CUDA_TRY(cudaEventElapsedTime(&t, tev[i], tev[i + 1]));
+    total += t;
+    ++c;
+  }
+  n_tev = 0;
+  if (ms) *ms = total;
+  if (count) *count = c;
+  return LFX_OK;
+}
+
+template <class S, class T>
 Gmres<S, T>::~Gmres() {
+  for (cudaEvent_t e : tev) cudaEventDestroy(e);
   if (pinned) cudaFreeHost(pinned);
   for (int i = 0; i < 4; ++i)
     if (ev[i]) cudaEventDestroy(ev[i]);
@@ -1346,7 +1364,17 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
     for (int j = 0; j < restart; ++j) {
       T *vj = Vb + (int64_t)j * n, *vn = Vb + (int64_t)(j + 1) * n, *zj = Zb + (int64_t)j * n;
       LFX_TRY(pc(st, vj, zj, ks));
+      if (n_tev + 2 > (int)tev.size()) {
+        for (int q = 0; q < 64; ++q) {
+          cudaEvent_t e;
+          LFX_CUDA_TRY(cudaEventCreate(&e));
+          tev.push_back(e);
+        }
+      }
+      LFX_CUDA_TRY(cudaEventRecord(tev[n_tev], st));
       spmv_kernel<S, T><<<rows_grid(V), kThreads, 0, st>>>(A, zj, nullptr, w, 0, nullptr, ks);
+      LFX_CUDA_TRY(cudaEventRecord(tev[n_tev + 1], st));
+      n_tev += 2;
       for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
         mdot_kernel<T><<<nblk_dot, kThreads, 0, st>>>(Vb, n, j + 1, w, n, part.as<double>(), nblk_dot, ks);
         mdot_finalize_kernel<<<j + 1, 32, 0, st>>>(part.as<double>(), nblk_dot, nblk_dot, j + 1, ks, pass);

@@ -97,6 +97,10 @@ struct Gmres {
   DBuf basis, zbasis, work, part, part_n, state;
   int *pinned = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // CUDA-event timing of the Arnoldi SpMV launches (accumulated until read_spmv_timing)
+  std::vector<cudaEvent_t> tev;
+  int n_tev = 0;
+  lfx_status read_spmv_timing(float *ms, int *count);
   Gmres() = default;
   Gmres(const Gmres &) = delete;
   ~Gmres();

@@ -76,7 +76,7 @@ class lfx_step_stats(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("t", ctypes.c_double), ("ms_assembly", ctypes.c_float),
                 ("ms_solve", ctypes.c_float), ("ms_total", ctypes.c_float), ("converged", ctypes.c_int32),
                 ("ms_assembly_kernels", ctypes.c_float), ("n_assembly_launches", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("ms_spmv", ctypes.c_float), ("n_spmv", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
