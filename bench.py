@@ -105,6 +105,20 @@ def gpu_problem(L, m, precision):
     return mesh, prob
 
 
+def replica_throughput(ms_local, steps, dist=None, device=None):
+    """Whole-job throughput of independent replicas (one simulation per rank, no data exchange):
+    the slowest rank's time bounds the job, every rank contributes `steps` steps."""
+    import torch
+
+    world = dist.get_world_size() if dist is not None else 1
+    ms = ms_local
+    if dist is not None:
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * steps / (ms * 1e-3), ms
+
+
 def timed_steps(L, st, steps, warmup, stream):
     import torch
 
@@ -159,10 +173,7 @@ def run_gpu(args):
         clocks.start()
         ms, stats, launches = timed_steps(L, st, args.steps, 1, stream)
         clk = clocks.stop()
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        _, ms = replica_throughput(ms, args.steps, dist, "cuda")
         u, p = st.get()
         results[prec] = dict(ms=ms, stats=stats, launches=launches, clocks=clk, u=u, p=p, st=st, mesh=mesh)
     prim = results["mixed"] if "mixed" in results else results[args.precision]
