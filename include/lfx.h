@@ -161,12 +161,12 @@ typedef struct lfx_options {
   int32_t gmres_restart;        /* default 40                                                  */
   int32_t gmres_max_iters;      /* total Arnoldi steps cap; default 1000                       */
   double gmres_rtol;            /* stop when ||b - A x|| <= rtol ||b||; default 1e-10         */
-  int32_t reorthogonalize;      /* classical Gram-Schmidt twice (1, default) or once (0); in mixed
+  int32_t reorthogonalize;      /* classical Gram-Schmidt once (0, default) or twice (1); in mixed
                                    precision the FP32 inner solve orthogonalises twice only if 2  */
   /* aSIMPLE: velocity block F and Schur approximation S = C - D diag(F)^-1 G */
   int32_t f_smoother, f_steps;  /* LFX_SMOOTH_*, steps; default Chebyshev, 3                   */
   double f_omega, f_ratio;      /* Jacobi damping; Chebyshev lmax/lmin; default 0.7, 20        */
-  int32_t s_smoother, s_steps;  /* default AMG with 2 Chebyshev steps pre and post              */
+  int32_t s_smoother, s_steps;  /* default AMG with 1 Chebyshev step pre and post               */
   double s_omega, s_ratio;      /* default 0.7, 30                                             */
   int32_t n_power;              /* 0 (default): Chebyshev lmax = Gershgorin bound (holds for every
                                    eigenvalue); > 0: this many power-iteration steps x 1.1       */
@@ -174,7 +174,7 @@ typedef struct lfx_options {
   int32_t smoother_bf16;        /* store the preconditioner blocks in BF16 (FP32 arithmetic)   */
   int32_t outer_restart;        /* FP64 flexible GMRES restart; default 8                       */
   int32_t outer_max_iters;      /* default 40                                                   */
-  double inner_rtol;            /* FP32 inner GMRES tolerance per outer step; default 1e-3     */
+  double inner_rtol;            /* FP32 inner GMRES tolerance per outer step; default 1e-4     */
   int32_t inner_max_iters;      /* default 60                                                   */
   double bad_element_quality;   /* elements with 6 sqrt2 |K| / e_rms^3 below this keep FP64
                                    geometry in mixed assembly; default 0.1                       */

@@ -289,20 +289,20 @@ void lfx_options_default(lfx_options *o) {
   o->gmres_restart = 64;
   o->gmres_max_iters = 1000;
   o->gmres_rtol = 1e-10;
-  o->reorthogonalize = 1;
+  o->reorthogonalize = 0;
   o->f_smoother = LFX_SMOOTH_CHEBYSHEV;
   o->f_steps = 3;
   o->f_omega = 0.7;
   o->f_ratio = 20.0;
   o->s_smoother = LFX_SMOOTH_AMG;
-  o->s_steps = 2;
+  o->s_steps = 1;
   o->s_omega = 0.7;
   o->s_ratio = 30.0;
   o->n_power = 0;
   o->smoother_bf16 = 0;
   o->outer_restart = 8;
   o->outer_max_iters = 40;
-  o->inner_rtol = 1e-3;
+  o->inner_rtol = 1e-4;
   o->inner_max_iters = 60;
   o->bad_element_quality = 0.1;
   o->amg_refresh = 0;
@@ -426,6 +426,15 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
     }
     P.riis_r[k] = riis[k].resistance;
     P.riis_eps[k] = riis[k].eps;
+  }
+  P.rho_dt = rho / dt;
+  P.rho_alpha_dt = rho * P.alpha / dt;
+  P.tau_t = P.sigma * P.sigma * rho * rho / (dt * dt);
+  P.cr_mu2 = P.c_r * mu * mu;
+  for (int k = 0; k < n_riis; ++k) {
+    P.riis_coef[k] = P.riis_r[k] / P.riis_eps[k];
+    P.riis_pi_eps[k] = M_PI / P.riis_eps[k];
+    P.riis_inv2eps[k] = 0.5 / P.riis_eps[k];
   }
   pb->bcs.assign(bcs, bcs + n_bcs);
   const int64_t V = m.V;

@@ -32,7 +32,7 @@ struct ElemShared {
   R gphi[kElems][12];      // grad phi_a, a = 0..3
   R w[kElems];             // |K| / 4 (quadrature weight)
   R Gm[kElems][9];         // metric tensor G = J^-T J^-1
-  R gg[kElems];            // g . g, g = J^-T 1
+  R igg[kElems];           // 1 / (g . g), g = J^-T 1
   R cs[kElems][4];         // rho alpha / dt + sum_k (R_k/eps_k) delta_k at each qp
   R tm[kElems][4];         // tau_M
   R tc[kElems][4];         // tau_C
@@ -45,12 +45,6 @@ struct ElemShared {
   R mga[kElems][4][4];     // [q][a] = m_q . grad phi_a
   R Svp[kElems][4], Ppv[kElems][4], Wv[kElems][4][3], Zv[kElems][3], TM[kElems], TC[kElems];
 };
-
-__device__ __forceinline__ double delta_fn(double phi, double eps) {
-  // smoothed Dirac delta of Section 2.1.2
-  if (fabs(phi) > eps) return 0.0;
-  return (1.0 + cos(3.14159265358979323846 * phi / eps)) / (2.0 * eps);
-}
 
 // Geometry of one tetrahedron in precision G: grad phi_a = J^-T grad_ref phi_a, the metric
 // tensor G = J^-T J^-1 (as its 9 entries), g = J^-T 1, |K| = det J / 6.
@@ -110,7 +104,7 @@ __device__ void geom_phase(const AssembleArgs &A, int64_t e, int le, ElemShared<
     for (int k = 0; k < 12; ++k) sh.gphi[le][k] = (R)gp[k];
 #pragma unroll
     for (int k = 0; k < 9; ++k) sh.Gm[le][k] = (R)G[k];
-    sh.gg[le] = (R)(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    sh.igg[le] = (R)(1.0 / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
     sh.w[le] = (R)(0.25 * v);
   } else {
     float gp[12], G[9], g[3], v;
@@ -119,7 +113,7 @@ __device__ void geom_phase(const AssembleArgs &A, int64_t e, int le, ElemShared<
     for (int k = 0; k < 12; ++k) sh.gphi[le][k] = (R)gp[k];
 #pragma unroll
     for (int k = 0; k < 9; ++k) sh.Gm[le][k] = (R)G[k];
-    sh.gg[le] = (R)(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    sh.igg[le] = (R)(1.0f / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
     sh.w[le] = (R)(0.25f * v);
   }
 }
@@ -160,7 +154,9 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, 
     double phq = 0.0;
 #pragma unroll
     for (int a = 0; a < 4; ++a) phq += (double)lam[a] * ph[nd[a]];
-    double c = P.riis_r[k] / P.riis_eps[k] * delta_fn(phq, P.riis_eps[k]);
+    // smoothed Dirac delta of Section 2.1.2: (1 + cos(pi phi/eps)) / (2 eps) inside |phi| <= eps
+    const double dl = fabs(phq) > P.riis_eps[k] ? 0.0 : (1.0 + cos(P.riis_pi_eps[k] * phq)) * P.riis_inv2eps[k];
+    const double c = P.riis_coef[k] * dl;
     sR += c;
     sR2 += c * c;
   }
@@ -177,9 +173,9 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, 
     }
   }
   const double rho = P.rho;
-  const double tsum = P.sigma * P.sigma * rho * rho / (P.dt * P.dt) + rho * rho * uGu + P.c_r * P.mu * P.mu * GG + sR2;
-  const double taum = 1.0 / sqrt(tsum);
-  const double tauc = 1.0 / (taum * (double)sh.gg[le]);
+  const double tsum = P.tau_t + rho * rho * uGu + P.cr_mu2 * GG + sR2;
+  const double taum = rsqrt(tsum);                       // tau_M = tsum^-1/2
+  const double tauc = tsum * taum * (double)sh.igg[le];  // tau_C = 1/(tau_M g.g) = sqrt(tsum)/(g.g)
   R z[3] = {R(0), R(0), R(0)};
   if (P.stab >= 2) {
     // tau_M r_M(u^EXT, p^EXT) with the strong residual of Section 2.3 (-mu Lap u = 0 for P1)
@@ -192,11 +188,11 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, 
         conv += adv[a] * ua;
         gpr += (R)ue[a].w * gp[3 * a + i];
       }
-      const R rm = (R)rho * (((R)P.alpha * us[i] - ubq[i]) / (R)P.dt + conv) + gpr + (R)sR * us[i] - (R)P.f[i];
+      const R rm = (R)P.rho_dt * ((R)P.alpha * us[i] - ubq[i]) + (R)rho * conv + gpr + (R)sR * us[i] - (R)P.f[i];
       z[i] = (R)rho * (R)taum * (us[i] - (R)taum * rm);
     }
   }
-  sh.cs[le][q] = (R)(rho * P.alpha / P.dt + sR);
+  sh.cs[le][q] = (R)(P.rho_alpha_dt + sR);
   sh.tm[le][q] = (R)taum;
   sh.tc[le][q] = (R)tauc;
 #pragma unroll
@@ -204,7 +200,7 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, 
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     sh.z[le][q][i] = z[i];
-    sh.m[le][q][i] = (R)rho * ubq[i] / (R)P.dt + (R)P.f[i];
+    sh.m[le][q][i] = (R)P.rho_dt * ubq[i] + (R)P.f[i];
   }
 }
 

@@ -133,6 +133,14 @@ struct PhysParams {
   double f[3];
   int32_t n_riis, stab, diffusion, pad;
   double riis_r[kMaxRiis], riis_eps[kMaxRiis];
+  // derived once on the host so that the kernels need no divisions
+  double rho_dt;                 // rho / dt
+  double rho_alpha_dt;           // rho alpha / dt
+  double tau_t;                  // sigma^2 rho^2 / dt^2 (time part of tau_M^-2)
+  double cr_mu2;                 // C_r mu^2
+  double riis_coef[kMaxRiis];    // R_k / eps_k
+  double riis_pi_eps[kMaxRiis];  // pi / eps_k
+  double riis_inv2eps[kMaxRiis]; // 1 / (2 eps_k)
 };
 
 }  // namespace lfx

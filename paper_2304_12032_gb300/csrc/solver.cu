@@ -23,7 +23,10 @@ namespace lfx {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kRowGroup = 8;      // lanes per block row in the row kernels
+#ifndef LFX_ROW_GROUP
+#define LFX_ROW_GROUP 4
+#endif
+constexpr int kRowGroup = LFX_ROW_GROUP;   // lanes per block row in the row kernels
 
 template <class T> struct Vec4T;
 template <> struct Vec4T<double> { using type = D4; };
@@ -145,11 +148,11 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(BsrView<S> A, const T *_
   T acc[4] = {T(0), T(0), T(0), T(0)};
   if (row < A.V) {
     const int32_t k1 = A.rowptr[row + 1];
-#pragma unroll 2
+#pragma unroll 4
     for (int32_t k = A.rowptr[row] + lane; k < k1; k += kRowGroup) {
       T blk[16];
       ld_block<S, T>(A.vals, k, blk);
-      const auto xv = ld4(x, A.col[k]);
+      const auto xv = ld4(x, __ldg(A.col + k));
 #pragma unroll
       for (int i = 0; i < 4; ++i)
         acc[i] += blk[4 * i] * xv.x + blk[4 * i + 1] * xv.y + blk[4 * i + 2] * xv.z + blk[4 * i + 3] * xv.w;
@@ -200,8 +203,9 @@ __global__ void __launch_bounds__(kThreads) bound_kernel(BsrView<S> A, const T *
   const int lane = threadIdx.x % kRowGroup;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
   if (row < A.V) {
-#pragma unroll 2
-    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+    const int32_t kend = A.rowptr[row + 1];
+#pragma unroll 4
+    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
       T blk[16];
       ld_block<S, T>(A.vals, kb, blk);
       if (mode == 0) {
@@ -213,8 +217,8 @@ __global__ void __launch_bounds__(kThreads) bound_kernel(BsrView<S> A, const T *
         a1 += fabs((double)blk[7]);
         a2 += fabs((double)blk[11]);
       } else {
-        const auto df = ld4(dinvF, A.col[kb]);
-        const auto g = ld4(gs, A.col[kb]);
+        const auto df = ld4(dinvF, __ldg(A.col + kb));
+        const auto g = ld4(gs, __ldg(A.col + kb));
         a0 += fabs((double)blk[15]) + fabs((double)blk[12]) * fabs((double)df.x) * (double)g.x +
               fabs((double)blk[13]) * fabs((double)df.y) * (double)g.y +
               fabs((double)blk[14]) * fabs((double)df.z) * (double)g.z;
@@ -269,10 +273,12 @@ __global__ void diag_s_kernel(BsrView<S> A, const T *dinvF, T *dinvS) {
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
   if (row < A.V) {
-    for (int32_t k = A.rowptr[row] + lane; k < A.rowptr[row + 1]; k += kRowGroup) {
+    const int32_t kend = A.rowptr[row + 1];
+#pragma unroll 4
+    for (int32_t k = A.rowptr[row] + lane; k < kend; k += kRowGroup) {
       const S *blk = A.vals + 16 * (int64_t)k;              // block (a, b)
       const S *tb = A.vals + 16 * (int64_t)A.trans[k];      // block (b, a)
-      const auto df = ld4(dinvF, A.col[k]);
+      const auto df = ld4(dinvF, __ldg(A.col + k));
       acc += (T)blk[12] * (T)tb[3] * df.x + (T)blk[13] * (T)tb[7] * df.y + (T)blk[14] * (T)tb[11] * df.z;
     }
   }
@@ -295,11 +301,12 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(BsrView<S> A, const T 
   const int lane = threadIdx.x % kRowGroup;
   T acc[3] = {T(0), T(0), T(0)};
   if (row < A.V) {
-#pragma unroll 2
-    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+    const int32_t kend = A.rowptr[row + 1];
+#pragma unroll 4
+    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
       T blk[16];
       ld_block<S, T>(A.vals, kb, blk);
-      const auto dv = ld4(d_old, A.col[kb]);
+      const auto dv = ld4(d_old, __ldg(A.col + kb));
 #pragma unroll
       for (int i = 0; i < 3; ++i) acc[i] += blk[4 * i] * dv.x + blk[4 * i + 1] * dv.y + blk[4 * i + 2] * dv.z;
     }
@@ -343,10 +350,11 @@ __global__ void __launch_bounds__(kThreads) g_scaled_kernel(BsrView<S> A, const 
   const int lane = threadIdx.x % kRowGroup;
   T acc[3] = {T(0), T(0), T(0)};
   if (row < A.V) {
-#pragma unroll 2
-    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+    const int32_t kend = A.rowptr[row + 1];
+#pragma unroll 4
+    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
       const S *blk = A.vals + 16 * (int64_t)kb;
-      const T p = ld4(in, A.col[kb]).w;
+      const T p = ld4(in, __ldg(A.col + kb)).w;
       acc[0] += (T)blk[3] * p;
       acc[1] += (T)blk[7] * p;
       acc[2] += (T)blk[11] * p;
@@ -374,10 +382,11 @@ __global__ void __launch_bounds__(kThreads) s_step_kernel(BsrView<S> A, const T 
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
   if (row < A.V) {
-#pragma unroll 2
-    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+    const int32_t kend = A.rowptr[row + 1];
+#pragma unroll 4
+    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
       const S *blk = A.vals + 16 * (int64_t)kb;
-      const int32_t c = A.col[kb];
+      const int32_t c = __ldg(A.col + kb);
       const T p = ld4(d_old, c).w;
       const auto wv = ld4(w, c);
       acc += (T)blk[15] * p - ((T)blk[12] * wv.x + (T)blk[13] * wv.y + (T)blk[14] * wv.z);
@@ -443,10 +452,11 @@ __global__ void __launch_bounds__(kThreads) d_init_kernel(BsrView<S> A, const T 
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
   if (row < A.V) {
-#pragma unroll 2
-    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+    const int32_t kend = A.rowptr[row + 1];
+#pragma unroll 4
+    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
       const S *blk = A.vals + 16 * (int64_t)kb;
-      const auto xv = ld4(x, A.col[kb]);
+      const auto xv = ld4(x, __ldg(A.col + kb));
       acc += (T)blk[12] * xv.x + (T)blk[13] * xv.y + (T)blk[14] * xv.z;
     }
   }
@@ -460,13 +470,11 @@ __global__ void __launch_bounds__(kThreads) d_init_kernel(BsrView<S> A, const T 
     }
     auto rr = ld4(r, row);
     auto dd = ld4(d, row);
-    auto xx = ld4(x, row);
     rr.w = dinvS[row] * t;
     dd.w = (T)cf->s_init * rr.w;
-    xx.w = dd.w;
     st4(r, row, rr);
     st4(d, row, dd);
-    st4(x, row, xx);
+    x[4 * row + 3] = dd.w;   // only the pressure component: the velocity part is read at neighbours
   }
 }
 
@@ -479,10 +487,11 @@ __global__ void __launch_bounds__(kThreads) final_kernel(BsrView<S> A, const T *
   const int lane = threadIdx.x % kRowGroup;
   T acc[3] = {T(0), T(0), T(0)};
   if (row < A.V) {
-#pragma unroll 2
-    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+    const int32_t kend = A.rowptr[row + 1];
+#pragma unroll 4
+    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
       const S *blk = A.vals + 16 * (int64_t)kb;
-      const T p = ld4(x, A.col[kb]).w;
+      const T p = ld4(x, __ldg(A.col + kb)).w;
       acc[0] += (T)blk[3] * p;
       acc[1] += (T)blk[7] * p;
       acc[2] += (T)blk[11] * p;
@@ -505,7 +514,8 @@ __global__ void __launch_bounds__(kThreads) final_kernel(BsrView<S> A, const T *
 
 // Level-0 Schur residual with w.xyz = diag(F)^-1 G x.w given:
 //   mode 0: out[row] = bs.w - (C x.w - D w)                       (for restriction)
-//   mode 1: r.w = dinvS (bs.w - (C x.w - D w)); d.w = init r.w; x.w += d.w  (post-smoothing start)
+//   mode 1: r.w = dinvS (bs.w - (C x.w - D w)); d.w = init r.w     (post-smoothing start; the
+//           iterate is read at the neighbours here, so x.w += d.w is a separate kernel)
 template <class S, class T>
 __global__ void __launch_bounds__(kThreads) s_resid_kernel(BsrView<S> A, const T *dinvS, T *x, const T *w,
                                                            const T *bs, T *out, T *r, T *d,
@@ -515,10 +525,11 @@ __global__ void __launch_bounds__(kThreads) s_resid_kernel(BsrView<S> A, const T
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
   if (row < A.V) {
-#pragma unroll 2
-    for (int32_t kb = A.rowptr[row] + lane; kb < A.rowptr[row + 1]; kb += kRowGroup) {
+    const int32_t kend = A.rowptr[row + 1];
+#pragma unroll 4
+    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
       const S *blk = A.vals + 16 * (int64_t)kb;
-      const int32_t c = A.col[kb];
+      const int32_t c = __ldg(A.col + kb);
       const T p = ld4(x, c).w;
       const auto wv = ld4(w, c);
       acc += (T)blk[15] * p - ((T)blk[12] * wv.x + (T)blk[13] * wv.y + (T)blk[14] * wv.z);
@@ -532,14 +543,22 @@ __global__ void __launch_bounds__(kThreads) s_resid_kernel(BsrView<S> A, const T
     } else {
       auto rr = ld4(r, row);
       auto dd = ld4(d, row);
-      auto xx = ld4(x, row);
       rr.w = dinvS[row] * res;
       dd.w = (T)cf->s_init * rr.w;
-      xx.w += dd.w;
       st4(r, row, rr);
       st4(d, row, dd);
-      st4(x, row, xx);
     }
+  }
+}
+
+// x.w += d.w (elementwise)
+template <class T>
+__global__ void add_w_kernel(int64_t V, const T *d, T *x, const KState *st) {
+  if (finished(st)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+    auto xx = ld4(x, i);
+    xx.w += ld4(d, i).w;
+    st4(x, i, xx);
   }
 }
 
@@ -1107,12 +1126,13 @@ lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r
     g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
     s_resid_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(), nullptr,
                                                   R.as<T>(), d[0], cf, 1, ks);
+    add_w_kernel<T><<<vg, kThreads, 0, st>>>(V, d[0], X.as<T>(), ks);
     for (int k = 1; k < cfg.s_steps; ++k) {
       g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
       s_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
                                                    R.as<T>(), X.as<T>(), cf, k, 1, nullptr, ks);
     }
-    note_launches(8 + 2 * (cfg.s_steps - 1));
+    note_launches(9 + 2 * (cfg.s_steps - 1));
   }
   // z_u = z_u* - diag(F)^-1 G z_p
   final_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), z, ks);
