@@ -8,6 +8,7 @@
 // partials, then one CTA sums them in a fixed order), so results are bitwise reproducible.
 // Every kernel of an Arnoldi step reads the solver's status word first and returns at once if
 // the cycle is already finished, so the host may queue a few steps ahead of the convergence test.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -651,6 +652,129 @@ __global__ void dense_mv_kernel(int64_t n, const double *Minv, const T *b, int i
   if (row < n && lane == 0) x[row * os + oo] = (T)s;
 }
 
+
+// ---- the coarse part of the Schur AMG V-cycle (levels 1..L-1) in ONE cooperative launch:
+// every phase is a grid-strided loop (a warp per matrix row), phases are separated by grid-wide
+// barriers.  Replaces ~20 tiny launches per V-cycle whose cost is mostly launch latency.
+template <class T>
+struct CoarseLevel {
+  int64_t n, nnext;
+  const int32_t *rp, *ci;
+  const double *v, *dinv;
+  const int32_t *Prp, *Pci;
+  const double *Pv;
+  const int32_t *Rrp, *Rci;
+  const double *Rv;
+  T *x, *b, *r, *d0, *d1, *rr;
+  double init, c1[kMaxSmooth], c2[kMaxSmooth];
+};
+constexpr int kMaxCoarse = 8;
+template <class T>
+struct CoarseArgs {
+  int L;            // levels in amg[] (level 0 is matrix-free and not part of this launch)
+  int s_steps;
+  double alpha;
+  const double *coarse_inv;
+  int64_t nc;
+  CoarseLevel<T> lv[kMaxCoarse];
+};
+
+template <class T>
+__device__ __forceinline__ double warp_row_dot(const int32_t *rp, const int32_t *ci, const double *v, const T *x,
+                                               int64_t row, int lane) {
+  double s = 0.0;
+  for (int32_t k = rp[row] + lane; k < rp[row + 1]; k += 32) s += v[k] * (double)x[ci[k]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) amg_coarse_kernel(const CoarseArgs<T> *__restrict__ args, const KState *st) {
+  if (finished(st)) return;
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const CoarseArgs<T> &A = *args;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gwarp = tid >> 5, nwarps = nthreads >> 5;
+  const int lane = threadIdx.x & 31;
+  auto cheb_init = [&](const CoarseLevel<T> &D, const T *rhs, int add) {
+    for (int64_t i = tid; i < D.n; i += nthreads) {
+      const double rv = D.dinv[i] * (double)rhs[i];
+      const double dv = D.init * rv;
+      D.r[i] = (T)rv;
+      D.d0[i] = (T)dv;
+      D.x[i] = (T)((add ? (double)D.x[i] : 0.0) + dv);
+    }
+  };
+  auto cheb_steps = [&](const CoarseLevel<T> &D) {
+    for (int k = 1; k < A.s_steps; ++k) {
+      const T *dold = (k & 1) ? D.d0 : D.d1;
+      T *dnew = (k & 1) ? D.d1 : D.d0;
+      for (int64_t row = gwarp; row < D.n; row += nwarps) {
+        const double s = warp_row_dot(D.rp, D.ci, D.v, dold, row, lane);
+        if (lane == 0) {
+          const double rv = (double)D.r[row] - D.dinv[row] * s;
+          const double dv = D.c1[k] * (double)dold[row] + D.c2[k] * rv;
+          D.r[row] = (T)rv;
+          dnew[row] = (T)dv;
+          D.x[row] = (T)((double)D.x[row] + dv);
+        }
+      }
+      grid.sync();
+    }
+  };
+  auto resid = [&](const CoarseLevel<T> &D) {
+    for (int64_t row = gwarp; row < D.n; row += nwarps) {
+      const double s = warp_row_dot(D.rp, D.ci, D.v, D.x, row, lane);
+      if (lane == 0) D.rr[row] = (T)((double)D.b[row] - s);
+    }
+  };
+  // down-sweep
+  for (int l = 1; l < A.L - 1; ++l) {
+    const CoarseLevel<T> &D = A.lv[l];
+    cheb_init(D, D.b, 0);
+    grid.sync();
+    cheb_steps(D);
+    resid(D);
+    grid.sync();
+    const CoarseLevel<T> &C = A.lv[l + 1];
+    for (int64_t row = gwarp; row < D.nnext; row += nwarps) {
+      const double s = warp_row_dot(D.Rrp, D.Rci, D.Rv, D.rr, row, lane);
+      if (lane == 0) C.b[row] = (T)s;
+    }
+    grid.sync();
+  }
+  // coarsest: dense inverse
+  {
+    const CoarseLevel<T> &C = A.lv[A.L - 1];
+    for (int64_t row = gwarp; row < A.nc; row += nwarps) {
+      double s = 0.0;
+      for (int64_t k = lane; k < A.nc; k += 32) s += A.coarse_inv[row * A.nc + k] * (double)C.b[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) C.x[row] = (T)s;
+    }
+    grid.sync();
+  }
+  // up-sweep
+  for (int l = A.L - 2; l >= 1; --l) {
+    const CoarseLevel<T> &D = A.lv[l];
+    const CoarseLevel<T> &C = A.lv[l + 1];
+    for (int64_t row = gwarp; row < D.n; row += nwarps) {
+      const double s = warp_row_dot(D.Prp, D.Pci, D.Pv, C.x, row, lane);
+      if (lane == 0) D.x[row] = (T)((double)D.x[row] + A.alpha * s);
+    }
+    grid.sync();
+    resid(D);
+    grid.sync();
+    cheb_init(D, D.rr, 1);
+    grid.sync();
+    cheb_steps(D);
+  }
+}
+
 // power iteration helpers: v = (1/sqrt(n)) on the selected components; v = y / lambda
 template <class T>
 __global__ void fill_kernel(int64_t V, T *v, int comp_mask, double val) {
@@ -946,6 +1070,8 @@ __global__ void update_x_kernel(const T *Zb, int64_t ld, X *x, int64_t n, const 
 }
 
 inline int rows_grid(int64_t V) { return (int)((V * kRowGroup + kThreads - 1) / kThreads); }
+// grid for a CSR kernel with G lanes per row over n rows
+inline int lanes_grid(int64_t n, int G) { return (int)std::max<int64_t>(1, (n * G + kThreads - 1) / kThreads); }
 inline int vec_grid(int64_t n) {
   int64_t g = (n + kThreads - 1) / kThreads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
@@ -1118,9 +1244,17 @@ lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r
     CsrV R0{L0.nnext, L0.Rrp.as<int32_t>(), L0.Rci.as<int32_t>(), L0.Rv.as<double>()};
     csr_spmv_kernel<T, 32><<<(int)((L0.nnext * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
         R0, rr0.as<T>(), 1, 0, amg[1].b.as<T>(), 1, 0, 1.0, 0, ks);
-    LFX_TRY(vcycle(st, 1, ks));
+    if (coop_grid > 0) {
+      const CoarseArgs<T> *ca = coarse_args.as<CoarseArgs<T>>();
+      void *kargs[] = {(void *)&ca, (void *)&ks};
+      LFX_CUDA_TRY(cudaLaunchCooperativeKernel((void *)amg_coarse_kernel<T>, dim3(coop_grid), dim3(kThreads), kargs,
+                                               0, st));
+      note_launches(1);
+    } else {
+      LFX_TRY(vcycle(st, 1, ks));
+    }
     CsrV P0{V, L0.Prp.as<int32_t>(), L0.Pci.as<int32_t>(), L0.Pv.as<double>()};
-    csr_spmv_kernel<T, 8><<<rows_grid(V), kThreads, 0, st>>>(P0, amg[1].x.as<T>(), 1, 0, X.as<T>(), 4, 3,
+    csr_spmv_kernel<T, 8><<<lanes_grid(V, 8), kThreads, 0, st>>>(P0, amg[1].x.as<T>(), 1, 0, X.as<T>(), 4, 3,
                                                             amg_alpha, 1, ks);
     // post-smoothing from the corrected iterate
     g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
@@ -1204,6 +1338,51 @@ lfx_status ASimple<S, T>::upload_amg(const AmgHost &H) {
   }
   nc = H.nc;
   LFX_TRY(upload_vec(coarse_inv, H.coarse_inv));
+  // arguments of the fused coarse V-cycle (one cooperative launch for levels 1..L-1)
+  coop_grid = 0;
+  int coop = 0, dev = 0, nsm = 0, per_sm = 0;
+  LFX_CUDA_TRY(cudaGetDevice(&dev));
+  LFX_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  LFX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  LFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, amg_coarse_kernel<T>, kThreads, 0));
+  if (coop && per_sm > 0 && L >= 2 && L <= kMaxCoarse) {
+    CoarseArgs<T> h{};
+    h.L = L;
+    h.s_steps = cfg.s_steps;
+    h.alpha = amg_alpha;
+    h.coarse_inv = coarse_inv.as<double>();
+    h.nc = nc;
+    for (int l = 1; l < L; ++l) {
+      const AmgDevLevel &D = amg[l];
+      CoarseLevel<T> &c = h.lv[l];
+      c.n = D.n;
+      c.nnext = D.nnext;
+      c.rp = D.rp.as<int32_t>();
+      c.ci = D.ci.as<int32_t>();
+      c.v = D.v.as<double>();
+      c.dinv = D.dinv.as<double>();
+      c.Prp = D.Prp.as<int32_t>();
+      c.Pci = D.Pci.as<int32_t>();
+      c.Pv = D.Pv.as<double>();
+      c.Rrp = D.Rrp.as<int32_t>();
+      c.Rci = D.Rci.as<int32_t>();
+      c.Rv = D.Rv.as<double>();
+      c.x = D.x.as<T>();
+      c.b = D.b.as<T>();
+      c.r = D.r.as<T>();
+      c.d0 = D.d0.as<T>();
+      c.d1 = D.d1.as<T>();
+      c.rr = D.rr.as<T>();
+      c.init = D.init;
+      for (int k = 0; k < kMaxSmooth; ++k) {
+        c.c1[k] = D.c1[k];
+        c.c2[k] = D.c2[k];
+      }
+    }
+    LFX_TRY(coarse_args.alloc(sizeof(CoarseArgs<T>)));
+    LFX_CUDA_TRY(cudaMemcpy(coarse_args.p, &h, sizeof(h), cudaMemcpyHostToDevice));
+    coop_grid = std::min(per_sm, 2) * nsm;
+  }
   if (!Bs.p) LFX_TRY(Bs.alloc(sizeof(T) * 4 * (size_t)V));
   if (!rr0.p) LFX_TRY(rr0.alloc(sizeof(T) * (size_t)V));
   LFX_CUDA_TRY(cudaMemset(Bs.p, 0, Bs.bytes));
@@ -1236,7 +1415,7 @@ lfx_status ASimple<S, T>::vcycle(cudaStream_t st, int l, const KState *ks) {
   CsrV A{D.n, D.rp.as<int32_t>(), D.ci.as<int32_t>(), D.v.as<double>()};
   CsrV P{D.n, D.Prp.as<int32_t>(), D.Pci.as<int32_t>(), D.Pv.as<double>()};
   CsrV R{D.nnext, D.Rrp.as<int32_t>(), D.Rci.as<int32_t>(), D.Rv.as<double>()};
-  const int vg = vec_grid(D.n), rg = rows_grid(D.n);
+  const int vg = vec_grid(D.n), rg = lanes_grid(D.n, 8);
   T *d[2] = {D.d0.as<T>(), D.d1.as<T>()};
   const double *dinv = D.dinv.as<double>();
   const bool wide = D.rp.p && D.n > 0 && (double)(H_nnz(D)) / (double)D.n > 24.0;

@@ -63,8 +63,9 @@ struct ASimple {
   DBuf dinvF, dinvS, X, D0, D1, R, W, coef, part;
   // Schur AMG (cfg.s_kind == LFX_SMOOTH_AMG)
   std::vector<AmgDevLevel> amg;
-  DBuf Bs, rr0, coarse_inv;
+  DBuf Bs, rr0, coarse_inv, coarse_args;
   int64_t nc = 0;
+  int coop_grid = 0;   // > 0: the coarse V-cycle runs as one cooperative launch of this many CTAs
   bool amg_ready = false;
   double amg_alpha = 1.0;
   lfx_status upload_amg(const AmgHost &H);
