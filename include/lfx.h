@@ -290,6 +290,15 @@ lfx_status lfx_asimple_apply_noalloc(int64_t n_nodes, const int32_t *row_ptr, co
                                      const double *blocks, const double *r, double *z,
                                      const lfx_options *opt, void *cuda_stream);
 
+/* Shape of the algebraic-multigrid hierarchy of the Schur approximation (s_smoother ==
+ * LFX_SMOOTH_AMG; Section 2.4 lists AMG among the block approximations of aSIMPLE), as built at
+ * the last set-up: *n_levels levels (0 until the first step or debug call builds it); rows[l]
+ * and nnz[l] = rows and stored nonzeros of the level-l operator (level 0 = the explicit
+ * S = C - D diag(F)^-1 G, the last level = the dense-inverted coarsest one), written for
+ * l < min(*n_levels, capacity) into caller-owned host arrays.  Host-only; no device work. */
+lfx_status lfx_state_amg_levels(const lfx_state *state, int32_t *n_levels, int64_t *rows, int64_t *nnz,
+                                int32_t capacity);
+
 /* ------------------------------------------------------------------------------------------
  * Device memory: optional allocator hook (e.g. a framework's caching allocator)
  * ------------------------------------------------------------------------------------------ */

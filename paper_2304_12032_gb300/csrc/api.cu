@@ -782,6 +782,26 @@ lfx_status lfx_set_pressure_pin(lfx_state *s, double value) {
   return LFX_OK;
 }
 
+lfx_status lfx_state_amg_levels(const lfx_state *s, int32_t *n_levels, int64_t *rows, int64_t *nnz,
+                                int32_t capacity) {
+  if (!s || !n_levels || capacity < 0 || (capacity > 0 && (!rows || !nnz))) {
+    set_error("lfx_state_amg_levels: invalid argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const lfx_options &o = s->pb->opt;
+  const std::vector<int64_t> *r = &s->pc64.lvl_rows, *z = &s->pc64.lvl_nnz;
+  if (o.precision == LFX_PREC_MIXED) {
+    r = o.smoother_bf16 ? &s->pcbf.lvl_rows : &s->pc32.lvl_rows;
+    z = o.smoother_bf16 ? &s->pcbf.lvl_nnz : &s->pc32.lvl_nnz;
+  }
+  *n_levels = (int32_t)r->size();
+  for (int i = 0; i < (int)r->size() && i < capacity; ++i) {
+    rows[i] = (*r)[i];
+    nnz[i] = (*z)[i];
+  }
+  return LFX_OK;
+}
+
 lfx_status lfx_state_device_bytes(const lfx_state *s, int64_t *bytes) {
   if (!s || !bytes) {
     set_error("lfx_state_device_bytes: NULL argument");

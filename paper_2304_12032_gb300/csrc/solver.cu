@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "amg.h"
 #include "kernels.h"
@@ -32,6 +33,13 @@ constexpr int kRowGroup = LFX_ROW_GROUP;   // lanes per block row in the row ker
 template <class T> struct Vec4T;
 template <> struct Vec4T<double> { using type = D4; };
 template <> struct Vec4T<float> { using type = F4; };
+
+// Arithmetic type of the vector kernels: FP32 vectors (the inner solve) are combined in FP32 and
+// only per-thread partial sums are widened to FP64 for the cross-thread reduction; FP64 vectors
+// stay FP64 throughout.  (FP64 instructions issue at 1/61 of the FP32 rate on this part, so an
+// FP64 accumulator would make the FP32 Krylov kernels arithmetic-bound.)
+template <class T, class X = T> struct AccT { using type = double; };
+template <> struct AccT<float, float> { using type = float; };
 
 template <class T>
 __device__ __forceinline__ typename Vec4T<T>::type ld4(const T *p, int64_t i) {
@@ -171,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(BsrView<S> A, const T *_
       o.x = acc[0]; o.y = acc[1]; o.z = acc[2]; o.w = acc[3];
     }
     st4(y, row, o);
-    nrm = (double)o.x * o.x + (double)o.y * o.y + (double)o.z * o.z + (double)o.w * o.w;
+    nrm = (double)(o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w);
   }
   if (part) {
     double s = cta_sum(nrm);
@@ -202,7 +210,8 @@ __global__ void __launch_bounds__(kThreads) bound_kernel(BsrView<S> A, const T *
                                                          double *part, int mode) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  using Acc = typename AccT<T>::type;
+  Acc a0 = Acc(0), a1 = Acc(0), a2 = Acc(0);
   if (row < A.V) {
     const int32_t kend = A.rowptr[row + 1];
 #pragma unroll 4
@@ -210,19 +219,18 @@ __global__ void __launch_bounds__(kThreads) bound_kernel(BsrView<S> A, const T *
       T blk[16];
       ld_block<S, T>(A.vals, kb, blk);
       if (mode == 0) {
-        a0 += fabs((double)blk[0]) + fabs((double)blk[1]) + fabs((double)blk[2]);
-        a1 += fabs((double)blk[4]) + fabs((double)blk[5]) + fabs((double)blk[6]);
-        a2 += fabs((double)blk[8]) + fabs((double)blk[9]) + fabs((double)blk[10]);
+        a0 += fabs((Acc)blk[0]) + fabs((Acc)blk[1]) + fabs((Acc)blk[2]);
+        a1 += fabs((Acc)blk[4]) + fabs((Acc)blk[5]) + fabs((Acc)blk[6]);
+        a2 += fabs((Acc)blk[8]) + fabs((Acc)blk[9]) + fabs((Acc)blk[10]);
       } else if (mode == 1) {
-        a0 += fabs((double)blk[3]);
-        a1 += fabs((double)blk[7]);
-        a2 += fabs((double)blk[11]);
+        a0 += fabs((Acc)blk[3]);
+        a1 += fabs((Acc)blk[7]);
+        a2 += fabs((Acc)blk[11]);
       } else {
         const auto df = ld4(dinvF, __ldg(A.col + kb));
         const auto g = ld4(gs, __ldg(A.col + kb));
-        a0 += fabs((double)blk[15]) + fabs((double)blk[12]) * fabs((double)df.x) * (double)g.x +
-              fabs((double)blk[13]) * fabs((double)df.y) * (double)g.y +
-              fabs((double)blk[14]) * fabs((double)df.z) * (double)g.z;
+        a0 += fabs((Acc)blk[15]) + fabs((Acc)blk[12]) * fabs((Acc)df.x) * (Acc)g.x +
+              fabs((Acc)blk[13]) * fabs((Acc)df.y) * (Acc)g.y + fabs((Acc)blk[14]) * fabs((Acc)df.z) * (Acc)g.z;
       }
     }
   }
@@ -233,7 +241,7 @@ __global__ void __launch_bounds__(kThreads) bound_kernel(BsrView<S> A, const T *
   if (row < A.V && lane == 0) {
     if (mode == 0) {
       const auto df = ld4(dinvF, row);
-      val = fmax(fabs((double)df.x) * a0, fmax(fabs((double)df.y) * a1, fabs((double)df.z) * a2));
+      val = (double)fmax(fabs((Acc)df.x) * a0, fmax(fabs((Acc)df.y) * a1, fabs((Acc)df.z) * a2));
     } else if (mode == 1) {
       auto o = ld4(gs, row);
       o.x = (T)a0;
@@ -241,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) bound_kernel(BsrView<S> A, const T *
       o.z = (T)a2;
       st4(gs, row, o);
     } else {
-      val = fabs((double)dinvS[row]) * a0;
+      val = (double)(fabs((Acc)dinvS[row]) * a0);
     }
   }
   if (mode != 1) {
@@ -563,92 +571,142 @@ __global__ void add_w_kernel(int64_t V, const T *d, T *x, const KState *st) {
   }
 }
 
-// ---- explicit CSR levels of the Schur AMG (scalar unknowns)
+// ---- explicit CSR levels of the Schur AMG (scalar unknowns).  Values are stored in the
+// preconditioner's vector type T (FP32 for the mixed-precision inner solve, FP64 otherwise).
+template <class VT>
 struct CsrV {
   int64_t n;
   const int32_t *rp, *ci;
-  const double *v;
+  const VT *v;
 };
+
+// sum_k v[k] x[ci[k]*is + io] over the row, G lanes per row (lane = position in the group),
+// four nonzeros per lane in flight; the group's total is returned in every lane of the group.
+// Lanes with valid == false add nothing but take part in the shuffles.
+template <int G, class T>
+__device__ __forceinline__ typename AccT<T>::type csr_row_dot(const int32_t *__restrict__ rp,
+                                                              const int32_t *__restrict__ ci,
+                                                              const T *__restrict__ v, const T *x, int is, int io,
+                                                              int64_t row, int lane, bool valid) {
+  using A = typename AccT<T>::type;
+  A s = A(0);
+  if (valid) {
+    const int32_t k1 = __ldg(rp + row + 1);
+    int32_t k = __ldg(rp + row) + lane;
+    for (; k + 3 * G < k1; k += 4 * G) {
+      int32_t c[4];
+      T w[4], xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = __ldg(ci + k + u * G);
+        w[u] = __ldg(v + k + u * G);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[u] = x[(int64_t)c[u] * is + io];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s += (A)w[u] * (A)xv[u];
+    }
+    for (; k < k1; k += G) s += (A)__ldg(v + k) * (A)x[(int64_t)__ldg(ci + k) * is + io];
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
 
 // out[i*os + oo] = (acc ? out : 0) + alpha * sum_j M_ij in[j*is + io]
 template <class T, int G>
-__global__ void csr_spmv_kernel(CsrV M, const T *in, int is, int io, T *out, int os, int oo, double alpha,
-                                int acc, const KState *st) {
+__global__ void __launch_bounds__(kThreads) csr_spmv_kernel(CsrV<T> M, const T *in, int is, int io, T *out, int os,
+                                                            int oo, double alpha, int acc, const KState *st) {
   if (finished(st)) return;
+  using A = typename AccT<T>::type;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int lane = threadIdx.x % G;
-  double s = 0.0;
-  if (row < M.n)
-    for (int32_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += G) s += M.v[k] * (double)in[(int64_t)M.ci[k] * is + io];
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const A s = csr_row_dot<G>(M.rp, M.ci, M.v, in, is, io, row, lane, row < M.n);
   if (row < M.n && lane == 0) {
     T *p = out + row * os + oo;
-    *p = (T)((acc ? (double)*p : 0.0) + alpha * s);
+    *p = (T)((acc ? (A)*p : A(0)) + (A)alpha * s);
   }
 }
 
 // r = b - A x  (G lanes per row)
 template <class T, int G>
-__global__ void csr_resid_kernel(CsrV M, const T *x, const T *b, T *out, const KState *st) {
+__global__ void __launch_bounds__(kThreads) csr_resid_kernel(CsrV<T> M, const T *x, const T *b, T *out,
+                                                             const KState *st) {
   if (finished(st)) return;
+  using A = typename AccT<T>::type;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int lane = threadIdx.x % G;
-  double s = 0.0;
-  if (row < M.n)
-    for (int32_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += G) s += M.v[k] * (double)x[M.ci[k]];
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (row < M.n && lane == 0) out[row] = (T)((double)b[row] - s);
+  const A s = csr_row_dot<G>(M.rp, M.ci, M.v, x, 1, 0, row, lane, row < M.n);
+  if (row < M.n && lane == 0) out[row] = (T)((A)b[row] - s);
 }
 
 // Chebyshev start on a CSR level: r = dinv rhs; d = init r; x = (add ? x : 0) + d
 template <class T>
-__global__ void csr_cheb_init_kernel(int64_t n, const double *dinv, const T *rhs, T *r, T *d, T *x, double init,
-                                     int add, const KState *st) {
+__global__ void csr_cheb_init_kernel(int64_t n, const T *dinv, const T *rhs, T *r, T *d, T *x, double init, int add,
+                                     const KState *st) {
   if (finished(st)) return;
+  using A = typename AccT<T>::type;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double rv = dinv[i] * (double)rhs[i];
-    const double dv = init * rv;
+    const A rv = (A)dinv[i] * (A)rhs[i];
+    const A dv = (A)init * rv;
     r[i] = (T)rv;
     d[i] = (T)dv;
-    x[i] = (T)((add ? (double)x[i] : 0.0) + dv);
+    x[i] = (T)((add ? (A)x[i] : A(0)) + dv);
   }
 }
 
 // Chebyshev step on a CSR level: y = A d_old; r -= dinv y; d_new = c1 d_old + c2 r; x += d_new
 template <class T, int G>
-__global__ void csr_cheb_step_kernel(CsrV M, const double *dinv, const T *d_old, T *d_new, T *r, T *x, double c1,
-                                     double c2, const KState *st) {
+__global__ void __launch_bounds__(kThreads) csr_cheb_step_kernel(CsrV<T> M, const T *dinv, const T *d_old, T *d_new,
+                                                                 T *r, T *x, double c1, double c2, const KState *st) {
   if (finished(st)) return;
+  using A = typename AccT<T>::type;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int lane = threadIdx.x % G;
-  double s = 0.0;
-  if (row < M.n)
-    for (int32_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += G) s += M.v[k] * (double)d_old[M.ci[k]];
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const A s = csr_row_dot<G>(M.rp, M.ci, M.v, d_old, 1, 0, row, lane, row < M.n);
   if (row < M.n && lane == 0) {
-    const double rv = (double)r[row] - dinv[row] * s;
-    const double dv = c1 * (double)d_old[row] + c2 * rv;
+    const A rv = (A)r[row] - (A)dinv[row] * s;
+    const A dv = (A)c1 * (A)d_old[row] + (A)c2 * rv;
     r[row] = (T)rv;
     d_new[row] = (T)dv;
-    x[row] = (T)((double)x[row] + dv);
+    x[row] = (T)((A)x[row] + dv);
   }
+}
+
+// sum_k Minv[row][k] b[k*is+io] over one warp (eight columns per lane in flight)
+template <class T>
+__device__ __forceinline__ typename AccT<T>::type dense_row_dot(int64_t n, const T *__restrict__ Minv, const T *b,
+                                                                int is, int io, int64_t row, int lane, bool valid) {
+  using A = typename AccT<T>::type;
+  A s = A(0);
+  if (valid) {
+    const T *m = Minv + row * n;
+    int64_t k = lane;
+    for (; k + 7 * 32 < n; k += 8 * 32) {
+      T w[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        w[u] = __ldg(m + k + u * 32);
+        xv[u] = b[(k + u * 32) * is + io];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += (A)w[u] * (A)xv[u];
+    }
+    for (; k < n; k += 32) s += (A)__ldg(m + k) * (A)b[k * is + io];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
 }
 
 // x[i*os+oo] = sum_k Minv[i][k] b[k*is+io]  (dense, n x n, row-major)
 template <class T>
-__global__ void dense_mv_kernel(int64_t n, const double *Minv, const T *b, int is, int io, T *x, int os, int oo,
-                                const KState *st) {
+__global__ void __launch_bounds__(kThreads) dense_mv_kernel(int64_t n, const T *Minv, const T *b, int is, int io,
+                                                            T *x, int os, int oo, const KState *st) {
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
-  double s = 0.0;
-  if (row < n)
-    for (int64_t k = lane; k < n; k += 32) s += Minv[row * n + k] * (double)b[k * is + io];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const auto s = dense_row_dot(n, Minv, b, is, io, row, lane, row < n);
   if (row < n && lane == 0) x[row * os + oo] = (T)s;
 }
 
@@ -660,12 +718,13 @@ template <class T>
 struct CoarseLevel {
   int64_t n, nnext;
   const int32_t *rp, *ci;
-  const double *v, *dinv;
+  const T *v, *dinv;
   const int32_t *Prp, *Pci;
-  const double *Pv;
+  const T *Pv;
   const int32_t *Rrp, *Rci;
-  const double *Rv;
+  const T *Rv;
   T *x, *b, *r, *d0, *d1, *rr;
+  T *xo;   // where the level's final iterate is left (d1 when one smoothing step is fused, else x)
   double init, c1[kMaxSmooth], c2[kMaxSmooth];
 };
 constexpr int kMaxCoarse = 8;
@@ -674,87 +733,101 @@ struct CoarseArgs {
   int L;            // levels in amg[] (level 0 is matrix-free and not part of this launch)
   int s_steps;
   double alpha;
-  const double *coarse_inv;
+  const T *coarse_inv;
   int64_t nc;
   CoarseLevel<T> lv[kMaxCoarse];
 };
-
-template <class T>
-__device__ __forceinline__ double warp_row_dot(const int32_t *rp, const int32_t *ci, const double *v, const T *x,
-                                               int64_t row, int lane) {
-  double s = 0.0;
-  for (int32_t k = rp[row] + lane; k < rp[row + 1]; k += 32) s += v[k] * (double)x[ci[k]];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) amg_coarse_kernel(const CoarseArgs<T> *__restrict__ args, const KState *st) {
   if (finished(st)) return;
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
+  using Ac = typename AccT<T>::type;
   const CoarseArgs<T> &A = *args;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gwarp = tid >> 5, nwarps = nthreads >> 5;
   const int lane = threadIdx.x & 31;
+  // warp-per-row loops: every lane of a warp runs the same trip count, so the shuffles inside
+  // the row dots always see the full warp
+  auto rows_of = [&](int64_t n) { return (n + nwarps - 1) / nwarps; };
   auto cheb_init = [&](const CoarseLevel<T> &D, const T *rhs, int add) {
     for (int64_t i = tid; i < D.n; i += nthreads) {
-      const double rv = D.dinv[i] * (double)rhs[i];
-      const double dv = D.init * rv;
+      const Ac rv = (Ac)D.dinv[i] * (Ac)rhs[i];
+      const Ac dv = (Ac)D.init * rv;
       D.r[i] = (T)rv;
       D.d0[i] = (T)dv;
-      D.x[i] = (T)((add ? (double)D.x[i] : 0.0) + dv);
+      D.x[i] = (T)((add ? (Ac)D.x[i] : Ac(0)) + dv);
     }
   };
   auto cheb_steps = [&](const CoarseLevel<T> &D) {
     for (int k = 1; k < A.s_steps; ++k) {
       const T *dold = (k & 1) ? D.d0 : D.d1;
       T *dnew = (k & 1) ? D.d1 : D.d0;
-      for (int64_t row = gwarp; row < D.n; row += nwarps) {
-        const double s = warp_row_dot(D.rp, D.ci, D.v, dold, row, lane);
-        if (lane == 0) {
-          const double rv = (double)D.r[row] - D.dinv[row] * s;
-          const double dv = D.c1[k] * (double)dold[row] + D.c2[k] * rv;
+      for (int64_t it = 0, row = gwarp; it < rows_of(D.n); ++it, row += nwarps) {
+        const Ac s = csr_row_dot<32>(D.rp, D.ci, D.v, dold, 1, 0, row, lane, row < D.n);
+        if (row < D.n && lane == 0) {
+          const Ac rv = (Ac)D.r[row] - (Ac)D.dinv[row] * s;
+          const Ac dv = (Ac)D.c1[k] * (Ac)dold[row] + (Ac)D.c2[k] * rv;
           D.r[row] = (T)rv;
           dnew[row] = (T)dv;
-          D.x[row] = (T)((double)D.x[row] + dv);
+          D.x[row] = (T)((Ac)D.x[row] + dv);
         }
       }
       grid.sync();
     }
   };
   auto resid = [&](const CoarseLevel<T> &D) {
-    for (int64_t row = gwarp; row < D.n; row += nwarps) {
-      const double s = warp_row_dot(D.rp, D.ci, D.v, D.x, row, lane);
-      if (lane == 0) D.rr[row] = (T)((double)D.b[row] - s);
+    for (int64_t it = 0, row = gwarp; it < rows_of(D.n); ++it, row += nwarps) {
+      const Ac s = csr_row_dot<32>(D.rp, D.ci, D.v, D.x, 1, 0, row, lane, row < D.n);
+      if (row < D.n && lane == 0) D.rr[row] = (T)((Ac)D.b[row] - s);
     }
   };
+  const bool one = A.s_steps == 1;
   // down-sweep
   for (int l = 1; l < A.L - 1; ++l) {
     const CoarseLevel<T> &D = A.lv[l];
-    cheb_init(D, D.b, 0);
-    grid.sync();
-    cheb_steps(D);
-    resid(D);
+    if (one) {
+      // x = init dinv b and rr = b - A x in one pass (x of a neighbour is formed from its b)
+      for (int64_t it = 0, row = gwarp; it < rows_of(D.n); ++it, row += nwarps) {
+        Ac s = Ac(0);
+        const bool valid = row < D.n;
+        if (valid) {
+          const int32_t k1 = __ldg(D.rp + row + 1);
+          for (int32_t k = __ldg(D.rp + row) + lane; k < k1; k += 32) {
+            const int32_t c = __ldg(D.ci + k);
+            s += (Ac)__ldg(D.v + k) * ((Ac)__ldg(D.dinv + c) * (Ac)D.b[c]);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (valid && lane == 0) {
+          const Ac bi = (Ac)D.b[row];
+          D.x[row] = (T)((Ac)D.init * (Ac)D.dinv[row] * bi);
+          D.rr[row] = (T)(bi - (Ac)D.init * s);
+        }
+      }
+    } else {
+      cheb_init(D, D.b, 0);
+      grid.sync();
+      cheb_steps(D);
+      resid(D);
+    }
     grid.sync();
     const CoarseLevel<T> &C = A.lv[l + 1];
-    for (int64_t row = gwarp; row < D.nnext; row += nwarps) {
-      const double s = warp_row_dot(D.Rrp, D.Rci, D.Rv, D.rr, row, lane);
-      if (lane == 0) C.b[row] = (T)s;
+    for (int64_t it = 0, row = gwarp; it < rows_of(D.nnext); ++it, row += nwarps) {
+      const Ac s = csr_row_dot<32>(D.Rrp, D.Rci, D.Rv, D.rr, 1, 0, row, lane, row < D.nnext);
+      if (row < D.nnext && lane == 0) C.b[row] = (T)s;
     }
     grid.sync();
   }
   // coarsest: dense inverse
   {
     const CoarseLevel<T> &C = A.lv[A.L - 1];
-    for (int64_t row = gwarp; row < A.nc; row += nwarps) {
-      double s = 0.0;
-      for (int64_t k = lane; k < A.nc; k += 32) s += A.coarse_inv[row * A.nc + k] * (double)C.b[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) C.x[row] = (T)s;
+    for (int64_t it = 0, row = gwarp; it < rows_of(A.nc); ++it, row += nwarps) {
+      const Ac s = dense_row_dot(A.nc, A.coarse_inv, C.b, 1, 0, row, lane, row < A.nc);
+      if (row < A.nc && lane == 0) C.x[row] = (T)s;
     }
     grid.sync();
   }
@@ -762,16 +835,28 @@ __global__ void __launch_bounds__(kThreads) amg_coarse_kernel(const CoarseArgs<T
   for (int l = A.L - 2; l >= 1; --l) {
     const CoarseLevel<T> &D = A.lv[l];
     const CoarseLevel<T> &C = A.lv[l + 1];
-    for (int64_t row = gwarp; row < D.n; row += nwarps) {
-      const double s = warp_row_dot(D.Prp, D.Pci, D.Pv, C.x, row, lane);
-      if (lane == 0) D.x[row] = (T)((double)D.x[row] + A.alpha * s);
+    const T *xc = (l + 1 == A.L - 1) ? C.x : C.xo;
+    for (int64_t it = 0, row = gwarp; it < rows_of(D.n); ++it, row += nwarps) {
+      const Ac s = csr_row_dot<32>(D.Prp, D.Pci, D.Pv, xc, 1, 0, row, lane, row < D.n);
+      if (row < D.n && lane == 0) D.x[row] = (T)((Ac)D.x[row] + (Ac)A.alpha * s);
     }
     grid.sync();
-    resid(D);
-    grid.sync();
-    cheb_init(D, D.rr, 1);
-    grid.sync();
-    cheb_steps(D);
+    if (one) {
+      // rr = b - A x and the smoothing step x_o = x + init dinv rr in one pass (into d1, since
+      // other rows still read x)
+      for (int64_t it = 0, row = gwarp; it < rows_of(D.n); ++it, row += nwarps) {
+        const Ac s = csr_row_dot<32>(D.rp, D.ci, D.v, D.x, 1, 0, row, lane, row < D.n);
+        if (row < D.n && lane == 0)
+          D.xo[row] = (T)((Ac)D.x[row] + (Ac)D.init * (Ac)D.dinv[row] * ((Ac)D.b[row] - s));
+      }
+      if (l > 1) grid.sync();
+    } else {
+      resid(D);
+      grid.sync();
+      cheb_init(D, D.rr, 1);
+      grid.sync();
+      cheb_steps(D);
+    }
   }
 }
 
@@ -856,8 +941,9 @@ __global__ void __launch_bounds__(kThreads) mdot_kernel(const T *Vb, int64_t ld,
   const V4 *w4 = reinterpret_cast<const V4 *>(w);
   const V4 *b4 = reinterpret_cast<const V4 *>(Vb);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  using A = typename AccT<T>::type;
   for (int v0 = 0; v0 < nvec; v0 += 8) {
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    A acc[8] = {A(0), A(0), A(0), A(0), A(0), A(0), A(0), A(0)};
     const int nv = min(8, nvec - v0);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
       const V4 wv = w4[i];
@@ -865,15 +951,15 @@ __global__ void __launch_bounds__(kThreads) mdot_kernel(const T *Vb, int64_t ld,
       for (int k = 0; k < 8; ++k)
         if (k < nv) {
           const V4 b = b4[(int64_t)(v0 + k) * ld4 + i];
-          acc[k] += (double)wv.x * (double)b.x + (double)wv.y * (double)b.y + (double)wv.z * (double)b.z +
-                    (double)wv.w * (double)b.w;
+          acc[k] += (A)wv.x * (A)b.x + (A)wv.y * (A)b.y + (A)wv.z * (A)b.z + (A)wv.w * (A)b.w;
         }
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
+      double a = (double)acc[k];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-      if (lane == 0) red[k][warp] = acc[k];
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) red[k][warp] = a;
     }
     __syncthreads();
     if ((int)threadIdx.x < nv) {
@@ -907,24 +993,25 @@ __global__ void __launch_bounds__(kThreads) maxpy_kernel(const T *Vb, int64_t ld
                                                          int64_t n, double *part, KState *st) {
   if (finished(st)) return;
   using V4 = typename Vec4T<T>::type;
-  __shared__ double h[kMaxRestart + 1];
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) h[i] = st->hwork[i];
+  using A = typename AccT<T>::type;
+  __shared__ A h[kMaxRestart + 1];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) h[i] = (A)st->hwork[i];
   __syncthreads();
   const int64_t n4 = n >> 2, ld4 = ld >> 2;
   V4 *w4 = reinterpret_cast<V4 *>(w);
   const V4 *b4 = reinterpret_cast<const V4 *>(Vb);
-  double nrm = 0.0;
+  A nrm_t = A(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
     const V4 wv = w4[i];
-    double a0 = (double)wv.x, a1 = (double)wv.y, a2 = (double)wv.z, a3 = (double)wv.w;
+    A a0 = (A)wv.x, a1 = (A)wv.y, a2 = (A)wv.z, a3 = (A)wv.w;
 #pragma unroll 4
     for (int k = 0; k < nvec; ++k) {
       const V4 b = b4[(int64_t)k * ld4 + i];
-      const double hk = h[k];
-      a0 -= hk * (double)b.x;
-      a1 -= hk * (double)b.y;
-      a2 -= hk * (double)b.z;
-      a3 -= hk * (double)b.w;
+      const A hk = h[k];
+      a0 -= hk * (A)b.x;
+      a1 -= hk * (A)b.y;
+      a2 -= hk * (A)b.z;
+      a3 -= hk * (A)b.w;
     }
     V4 o;
     o.x = (T)a0;
@@ -932,8 +1019,9 @@ __global__ void __launch_bounds__(kThreads) maxpy_kernel(const T *Vb, int64_t ld
     o.z = (T)a2;
     o.w = (T)a3;
     w4[i] = o;
-    nrm += a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3;
+    nrm_t += a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3;
   }
+  const double nrm = (double)nrm_t;
   double s = cta_sum(nrm);
   if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
 }
@@ -998,27 +1086,30 @@ __global__ void convert_kernel<double, __nv_bfloat16>(const double *src, __nv_bf
 
 template <class T>
 __global__ void norm_kernel(const T *v, int64_t n, double *part) {
-  double a = 0.0;
+  using A = typename AccT<T>::type;
+  A a = A(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    a += (double)v[i] * (double)v[i];
-  double s = cta_sum(a);
+    a += (A)v[i] * (A)v[i];
+  double s = cta_sum((double)a);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 template <class T>
 __global__ void scale_kernel(const T *w, T *v, int64_t n, const double *sc, const KState *st) {
   if (finished(st)) return;
-  const double s = *sc;
+  using A = typename AccT<T>::type;
+  const A s = (A)*sc;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = (T)((double)w[i] * s);
+    v[i] = (T)((A)w[i] * s);
 }
 // variant used at the start of a cycle (no early exit): v0 = r / beta
 template <class T>
 __global__ void scale_beta_kernel(const T *w, T *v, int64_t n, const KState *st) {
+  using A = typename AccT<T>::type;
   const double b = st->beta;
-  const double s = b > 0.0 ? 1.0 / b : 0.0;
+  const A s = (A)(b > 0.0 ? 1.0 / b : 0.0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = (T)((double)w[i] * s);
+    v[i] = (T)((A)w[i] * s);
 }
 
 // start of a cycle: beta = ||r||, g = (beta, 0, ...), j = 0, done if beta <= tol
@@ -1057,14 +1148,15 @@ __global__ void trisolve_kernel(KState *st) {
 // x += sum_{i<j} y_i z_i
 template <class T, class X>
 __global__ void update_x_kernel(const T *Zb, int64_t ld, X *x, int64_t n, const KState *st) {
-  __shared__ double y[kMaxRestart];
+  using A = typename AccT<T, X>::type;
+  __shared__ A y[kMaxRestart];
   const int j = st->j;
-  for (int i = threadIdx.x; i < j; i += blockDim.x) y[i] = st->y[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) y[i] = (A)st->y[i];
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double a = (double)x[i];
+    A a = (A)x[i];
 #pragma unroll 4
-    for (int k = 0; k < j; ++k) a += y[k] * (double)Zb[(int64_t)k * ld + i];
+    for (int k = 0; k < j; ++k) a += y[k] * (A)Zb[(int64_t)k * ld + i];
     x[i] = (X)a;
   }
 }
@@ -1233,7 +1325,7 @@ lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r
   if (cfg.s_kind == LFX_SMOOTH_AMG && amg.size() == 1) {
     // small problem: the hierarchy is the dense inverse of S itself
     dense_mv_kernel<T><<<(int)((V * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-        V, coarse_inv.as<double>(), Bs.as<T>(), 4, 3, X.as<T>(), 4, 3, ks);
+        V, coarse_inv.as<T>(), Bs.as<T>(), 4, 3, X.as<T>(), 4, 3, ks);
     note_launches(1);
   } else if (cfg.s_kind == LFX_SMOOTH_AMG) {
     // residual of the pre-smoothed level-0 iterate, restriction, coarse V-cycle, prolongation
@@ -1241,7 +1333,7 @@ lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r
     s_resid_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(),
                                                   rr0.as<T>(), nullptr, nullptr, cf, 0, ks);
     const AmgDevLevel &L0 = amg[0];
-    CsrV R0{L0.nnext, L0.Rrp.as<int32_t>(), L0.Rci.as<int32_t>(), L0.Rv.as<double>()};
+    CsrV<T> R0{L0.nnext, L0.Rrp.as<int32_t>(), L0.Rci.as<int32_t>(), L0.Rv.as<T>()};
     csr_spmv_kernel<T, 32><<<(int)((L0.nnext * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
         R0, rr0.as<T>(), 1, 0, amg[1].b.as<T>(), 1, 0, 1.0, 0, ks);
     if (coop_grid > 0) {
@@ -1253,8 +1345,10 @@ lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r
     } else {
       LFX_TRY(vcycle(st, 1, ks));
     }
-    CsrV P0{V, L0.Prp.as<int32_t>(), L0.Pci.as<int32_t>(), L0.Pv.as<double>()};
-    csr_spmv_kernel<T, 8><<<lanes_grid(V, 8), kThreads, 0, st>>>(P0, amg[1].x.as<T>(), 1, 0, X.as<T>(), 4, 3,
+    CsrV<T> P0{V, L0.Prp.as<int32_t>(), L0.Pci.as<int32_t>(), L0.Pv.as<T>()};
+    // the level-1 iterate is in d1 when the coarse launch fused its last smoothing step
+    const T *x1 = (amg.size() > 2 && coop_grid > 0 && cfg.s_steps == 1) ? amg[1].d1.as<T>() : amg[1].x.as<T>();
+    csr_spmv_kernel<T, 8><<<lanes_grid(V, 8), kThreads, 0, st>>>(P0, x1, 1, 0, X.as<T>(), 4, 3,
                                                             amg_alpha, 1, ks);
     // post-smoothing from the corrected iterate
     g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
@@ -1296,6 +1390,13 @@ static lfx_status upload_vec(DBuf &d, const std::vector<T> &h) {
   if (!h.empty()) LFX_CUDA_TRY(cudaMemcpy(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
   return LFX_OK;
 }
+// FP64 host values uploaded in the preconditioner's arithmetic type
+template <class T>
+static lfx_status upload_as(DBuf &d, const std::vector<double> &h) {
+  if (std::is_same<T, double>::value) return upload_vec(d, h);
+  std::vector<T> c(h.begin(), h.end());
+  return upload_vec(d, c);
+}
 
 template <class S, class T>
 lfx_status ASimple<S, T>::upload_amg(const AmgHost &H) {
@@ -1314,18 +1415,18 @@ lfx_status ASimple<S, T>::upload_amg(const AmgHost &H) {
       D.nnext = H.A[l + 1].n;
       LFX_TRY(upload_vec(D.Prp, H.P[l].rp));
       LFX_TRY(upload_vec(D.Pci, H.P[l].ci));
-      LFX_TRY(upload_vec(D.Pv, H.P[l].v));
+      LFX_TRY(upload_as<T>(D.Pv, H.P[l].v));
       LFX_TRY(upload_vec(D.Rrp, H.R[l].rp));
       LFX_TRY(upload_vec(D.Rci, H.R[l].ci));
-      LFX_TRY(upload_vec(D.Rv, H.R[l].v));
+      LFX_TRY(upload_as<T>(D.Rv, H.R[l].v));
       cheb_coefs(H.lam[l], cfg.s_ratio, cfg.s_steps, D.init, D.c1, D.c2);
     }
     if (l >= 1) {
       if (l + 1 < L) {
         LFX_TRY(upload_vec(D.rp, H.A[l].rp));
         LFX_TRY(upload_vec(D.ci, H.A[l].ci));
-        LFX_TRY(upload_vec(D.v, H.A[l].v));
-        LFX_TRY(upload_vec(D.dinv, H.dinv[l]));
+        LFX_TRY(upload_as<T>(D.v, H.A[l].v));
+        LFX_TRY(upload_as<T>(D.dinv, H.dinv[l]));
       }
       const size_t vb = sizeof(T) * (size_t)std::max<int64_t>(D.n, 1);
       LFX_TRY(D.x.alloc(vb));
@@ -1337,7 +1438,13 @@ lfx_status ASimple<S, T>::upload_amg(const AmgHost &H) {
     }
   }
   nc = H.nc;
-  LFX_TRY(upload_vec(coarse_inv, H.coarse_inv));
+  lvl_rows.assign(L, 0);
+  lvl_nnz.assign(L, 0);
+  for (int l = 0; l < L; ++l) {
+    lvl_rows[l] = H.A[l].n;
+    lvl_nnz[l] = (int64_t)H.A[l].ci.size();
+  }
+  LFX_TRY(upload_as<T>(coarse_inv, H.coarse_inv));
   // arguments of the fused coarse V-cycle (one cooperative launch for levels 1..L-1)
   coop_grid = 0;
   int coop = 0, dev = 0, nsm = 0, per_sm = 0;
@@ -1350,7 +1457,7 @@ lfx_status ASimple<S, T>::upload_amg(const AmgHost &H) {
     h.L = L;
     h.s_steps = cfg.s_steps;
     h.alpha = amg_alpha;
-    h.coarse_inv = coarse_inv.as<double>();
+    h.coarse_inv = coarse_inv.as<T>();
     h.nc = nc;
     for (int l = 1; l < L; ++l) {
       const AmgDevLevel &D = amg[l];
@@ -1359,20 +1466,21 @@ lfx_status ASimple<S, T>::upload_amg(const AmgHost &H) {
       c.nnext = D.nnext;
       c.rp = D.rp.as<int32_t>();
       c.ci = D.ci.as<int32_t>();
-      c.v = D.v.as<double>();
-      c.dinv = D.dinv.as<double>();
+      c.v = D.v.as<T>();
+      c.dinv = D.dinv.as<T>();
       c.Prp = D.Prp.as<int32_t>();
       c.Pci = D.Pci.as<int32_t>();
-      c.Pv = D.Pv.as<double>();
+      c.Pv = D.Pv.as<T>();
       c.Rrp = D.Rrp.as<int32_t>();
       c.Rci = D.Rci.as<int32_t>();
-      c.Rv = D.Rv.as<double>();
+      c.Rv = D.Rv.as<T>();
       c.x = D.x.as<T>();
       c.b = D.b.as<T>();
       c.r = D.r.as<T>();
       c.d0 = D.d0.as<T>();
       c.d1 = D.d1.as<T>();
       c.rr = D.rr.as<T>();
+      c.xo = (cfg.s_steps == 1 && l < L - 1) ? D.d1.as<T>() : D.x.as<T>();
       c.init = D.init;
       for (int k = 0; k < kMaxSmooth; ++k) {
         c.c1[k] = D.c1[k];
@@ -1381,7 +1489,7 @@ lfx_status ASimple<S, T>::upload_amg(const AmgHost &H) {
     }
     LFX_TRY(coarse_args.alloc(sizeof(CoarseArgs<T>)));
     LFX_CUDA_TRY(cudaMemcpy(coarse_args.p, &h, sizeof(h), cudaMemcpyHostToDevice));
-    coop_grid = std::min(per_sm, 2) * nsm;
+    coop_grid = std::min(per_sm, 4) * nsm;
   }
   if (!Bs.p) LFX_TRY(Bs.alloc(sizeof(T) * 4 * (size_t)V));
   if (!rr0.p) LFX_TRY(rr0.alloc(sizeof(T) * (size_t)V));
@@ -1399,7 +1507,7 @@ size_t ASimple<S, T>::amg_bytes() const {
   return b;
 }
 
-static inline double H_nnz(const AmgDevLevel &D) { return (double)D.v.bytes / sizeof(double); }
+static inline double H_nnz(const AmgDevLevel &D, size_t elem) { return (double)D.v.bytes / (double)elem; }
 
 // One V-cycle on the explicit levels l >= 1 for amg[l].b -> amg[l].x
 template <class S, class T>
@@ -1408,17 +1516,17 @@ lfx_status ASimple<S, T>::vcycle(cudaStream_t st, int l, const KState *ks) {
   const int L = (int)amg.size();
   if (l == L - 1) {
     dense_mv_kernel<T><<<(int)((D.n * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-        D.n, coarse_inv.as<double>(), D.b.as<T>(), 1, 0, D.x.as<T>(), 1, 0, ks);
+        D.n, coarse_inv.as<T>(), D.b.as<T>(), 1, 0, D.x.as<T>(), 1, 0, ks);
     note_launches(1);
     return LFX_OK;
   }
-  CsrV A{D.n, D.rp.as<int32_t>(), D.ci.as<int32_t>(), D.v.as<double>()};
-  CsrV P{D.n, D.Prp.as<int32_t>(), D.Pci.as<int32_t>(), D.Pv.as<double>()};
-  CsrV R{D.nnext, D.Rrp.as<int32_t>(), D.Rci.as<int32_t>(), D.Rv.as<double>()};
+  CsrV<T> A{D.n, D.rp.as<int32_t>(), D.ci.as<int32_t>(), D.v.as<T>()};
+  CsrV<T> P{D.n, D.Prp.as<int32_t>(), D.Pci.as<int32_t>(), D.Pv.as<T>()};
+  CsrV<T> R{D.nnext, D.Rrp.as<int32_t>(), D.Rci.as<int32_t>(), D.Rv.as<T>()};
   const int vg = vec_grid(D.n), rg = lanes_grid(D.n, 8);
   T *d[2] = {D.d0.as<T>(), D.d1.as<T>()};
-  const double *dinv = D.dinv.as<double>();
-  const bool wide = D.rp.p && D.n > 0 && (double)(H_nnz(D)) / (double)D.n > 24.0;
+  const T *dinv = D.dinv.as<T>();
+  const bool wide = D.rp.p && D.n > 0 && H_nnz(D, sizeof(T)) / (double)D.n > 24.0;
   const int rg32 = (int)((D.n * 32 + kThreads - 1) / kThreads);
   auto cheb_step = [&](int k) {
     if (wide)

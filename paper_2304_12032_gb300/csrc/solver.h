@@ -65,6 +65,7 @@ struct ASimple {
   std::vector<AmgDevLevel> amg;
   DBuf Bs, rr0, coarse_inv, coarse_args;
   int64_t nc = 0;
+  std::vector<int64_t> lvl_rows, lvl_nnz;   // hierarchy shape (rows, nonzeros of A_l per level)
   int coop_grid = 0;   // > 0: the coarse V-cycle runs as one cooperative launch of this many CTAs
   bool amg_ready = false;
   double amg_alpha = 1.0;

@@ -127,6 +127,7 @@ _SIGS = {
     "lfx_asimple_apply_noalloc": ([ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(lfx_options), _P],
                                   ctypes.c_int32),
     "lfx_state_device_bytes": ([_P, _LP], ctypes.c_int32),
+    "lfx_state_amg_levels": ([_P, _IP, _LP, _LP, ctypes.c_int32], ctypes.c_int32),
 }
 
 
@@ -374,6 +375,15 @@ class State:
         b = ctypes.c_int64()
         _check(library().lfx_state_device_bytes(self.h, ctypes.byref(b)))
         return b.value
+
+    def amg_levels(self):
+        """[(rows, nonzeros)] of each level of the Schur multigrid hierarchy (empty before set-up)."""
+        n = ctypes.c_int32()
+        rows = np.zeros(16, dtype=np.int64)
+        nnz = np.zeros(16, dtype=np.int64)
+        _check(library().lfx_state_amg_levels(self.h, ctypes.byref(n), rows.ctypes.data_as(_LP),
+                                              nnz.ctypes.data_as(_LP), 16))
+        return [(int(rows[i]), int(nnz[i])) for i in range(min(n.value, 16))]
 
     # ---- building blocks, for parity tests
     def debug_assemble(self, apply_bcs=True):
