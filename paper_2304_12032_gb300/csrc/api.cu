@@ -122,7 +122,7 @@ struct lfx_state {
   DBuf hist[3];            // D4 [V]; level l = hist[(head + l) % sigma]
   int head = 0;
   DBuf xsol, ubdf, rhs, gdir, nodal, comp_scale;
-  DBuf vals64, vals32, valsbf;
+  DBuf vals64, vals32, nopat;   // nopat: empty (pattern-only views)
   ASimple<double, double> pc64;
   Gmres<double, double> gm64;
   // mixed precision: FP32 inner Krylov with an FP32 or BF16-storage aSIMPLE
@@ -714,7 +714,6 @@ lfx_status lfx_state_create(lfx_problem *pb, const double *u_hist, const double 
   if (o.precision == LFX_PREC_MIXED) {
     LFX_TRY(s->vals32.alloc(sizeof(float) * 16 * m.nnzb));
     if (o.smoother_bf16) {
-      LFX_TRY(s->valsbf.alloc(sizeof(__nv_bfloat16) * 16 * m.nnzb));
       LFX_TRY(s->pcbf.init(V, cfg));
     } else {
       LFX_TRY(s->pc32.init(V, cfg));
@@ -809,7 +808,7 @@ lfx_status lfx_state_device_bytes(const lfx_state *s, int64_t *bytes) {
   }
   size_t b = s->pb->mesh->m.device_bytes() + s->pb->device_bytes() + s->xsol.bytes + s->ubdf.bytes +
              s->rhs.bytes + s->gdir.bytes + s->nodal.bytes + s->vals64.bytes + s->vals32.bytes +
-             s->pc64.device_bytes() + s->pc64.amg_bytes() + s->gm64.device_bytes() + s->valsbf.bytes +
+             s->pc64.device_bytes() + s->pc64.amg_bytes() + s->gm64.device_bytes() +
              s->pc32.device_bytes() + s->pc32.amg_bytes() + s->pcbf.device_bytes() + s->pcbf.amg_bytes() +
              s->gm32.device_bytes() + s->r32.bytes + s->z32.bytes;
   for (int l = 0; l < 3; ++l) b += s->hist[l].bytes;
@@ -903,13 +902,13 @@ int64_t lfx_internal_state_bytes_estimate(const lfx_problem *pb, int64_t *V_out,
   const int64_t amg = o.s_smoother == LFX_SMOOTH_AMG ? 300 * V + 8LL * o.amg_coarse_size * o.amg_coarse_size : 0;
   const int64_t part = 8LL * 152 * 4 * 65 + 8 * (V * 8 / 256 + 64);
   if (o.precision == LFX_PREC_MIXED) {
-    b += 64 * nnzb + (o.smoother_bf16 ? 32 * nnzb : 0);      // FP32 / BF16 copies
+    b += 64 * nnzb + (o.smoother_bf16 ? 40 * nnzb : 80 * nnzb);   // FP32 copy; F, G, (D, C) apart
     b += 7 * v32 + 4 * V + amg;                               // FP32 aSIMPLE work
     b += (2 * (int64_t)o.gmres_restart + 2) * v32 + part;    // inner GMRES
     b += (2 * (int64_t)std::max(1, o.outer_restart) + 2) * v64 + part;   // outer FGMRES
     b += 2 * v32;
   } else {
-    b += 7 * v64 + 8 * V + amg;
+    b += 160 * nnzb + 7 * v64 + 8 * V + amg;                 // F, G, (D, C) apart in FP64
     b += (2 * (int64_t)o.gmres_restart + 2) * v64 + part;
   }
   return b + b / 10;
@@ -928,15 +927,15 @@ lfx_status lfx_problem_state_bytes(const lfx_problem *pb, int64_t *bytes) {
 
 }  // extern "C"
 
-// aSIMPLE set-up for the current matrix: diagonals and eigenvalue estimates every step; the
-// Schur AMG hierarchy (built from the FP64 matrix) on first use and then every amg_refresh
-// steps.  In mixed precision the FP32 (and BF16) copies of the matrix are refreshed first.
+// aSIMPLE set-up for the current matrix: the sub-blocks F, G, (D, C) stored apart in the
+// smoother's storage type (FP64, FP32 or BF16), diagonals and eigenvalue bounds every step; the
+// Schur AMG hierarchy (built from the FP64 matrix) on first use and then every amg_refresh steps.
 template <class S, class T>
-static lfx_status setup_asimple(lfx_state *s, ASimple<S, T> &pc, const BsrView<S> &A) {
+static lfx_status setup_asimple(lfx_state *s, ASimple<S, T> &pc) {
   lfx_problem *pb = s->pb;
   const lfx_options &o = pb->opt;
   const Mesh &m = pb->mesh->m;
-  LFX_TRY(pc.setup(s->stream, A));
+  LFX_TRY(pc.setup_split(s->stream, s->view64(), m.nnzb));
   if (o.s_smoother != LFX_SMOOTH_AMG) return LFX_OK;
   if (pc.amg_ready && !(o.amg_refresh > 0 && s->amg_age >= o.amg_refresh)) {
     ++s->amg_age;
@@ -960,15 +959,12 @@ static lfx_status setup_asimple(lfx_state *s, ASimple<S, T> &pc, const BsrView<S
 static lfx_status prepare_precond(lfx_state *s) {
   const lfx_options &o = s->pb->opt;
   const Mesh &m = s->pb->mesh->m;
-  if (o.precision != LFX_PREC_MIXED) return setup_asimple(s, s->pc64, s->view64());
+  if (o.precision != LFX_PREC_MIXED) return setup_asimple(s, s->pc64);
+  // FP32 copy of the operator for the inner Krylov solve
   const int64_t nv = 16 * m.nnzb;
   LFX_TRY((launch_convert<double, float>(s->stream, s->vals64.as<double>(), s->vals32.as<float>(), nv, nullptr)));
-  if (o.smoother_bf16) {
-    LFX_TRY((launch_convert<double, __nv_bfloat16>(s->stream, s->vals64.as<double>(), s->valsbf.as<__nv_bfloat16>(),
-                                                   nv, nullptr)));
-    return setup_asimple(s, s->pcbf, s->view<__nv_bfloat16>(s->valsbf));
-  }
-  return setup_asimple(s, s->pc32, s->view<float>(s->vals32));
+  if (o.smoother_bf16) return setup_asimple(s, s->pcbf);
+  return setup_asimple(s, s->pc32);
 }
 
 // The configured Krylov solve of the assembled system (rhs -> x, x holds the initial guess).
@@ -995,7 +991,7 @@ static lfx_status run_solve(lfx_state *s, double *x, bool x_zero, int *its, int 
     double r = 0.0;
     lfx_status rc;
     if (o.smoother_bf16) {
-      const BsrView<__nv_bfloat16> Ab = s->view<__nv_bfloat16>(s->valsbf);
+      const BsrView<__nv_bfloat16> Ab = s->view<__nv_bfloat16>(s->nopat);
       auto pc = [s, Ab](cudaStream_t qq, const float *vv, float *zz, const KState *kk) {
         return s->pcbf.apply(qq, Ab, vv, zz, kk);
       };

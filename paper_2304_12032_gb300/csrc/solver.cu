@@ -125,6 +125,23 @@ __device__ __forceinline__ double cta_sum(double v) {
   return s;
 }
 
+// CTA-wide sum with the warp stage in the value's own type (FP32 values are widened to FP64 only
+// per warp); result valid in thread 0.
+template <class A>
+__device__ __forceinline__ double cta_sum_t(A v) {
+  __shared__ double red[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
 // CTA-wide max of one double per thread; result valid in thread 0.
 __device__ __forceinline__ double cta_max(double v) {
   __shared__ double red[kThreads / 32];
@@ -169,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(BsrView<S> A, const T *_
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc[i] = group_sum(acc[i]);
-  double nrm = 0.0;
+  typename AccT<T>::type nrm = 0;
   if (row < A.V && lane == 0) {
     typename Vec4T<T>::type o;
     if (mode == 1) {
@@ -179,10 +196,10 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(BsrView<S> A, const T *_
       o.x = acc[0]; o.y = acc[1]; o.z = acc[2]; o.w = acc[3];
     }
     st4(y, row, o);
-    nrm = (double)(o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w);
+    nrm = o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
   }
   if (part) {
-    double s = cta_sum(nrm);
+    double s = cta_sum_t(nrm);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
   }
 }
@@ -201,12 +218,123 @@ __global__ void reduce_kernel(const double *part, int n, double *out, int root) 
   if (threadIdx.x == 0) *out = root ? sqrt(s) : s;
 }
 
+// ---- access to the aSIMPLE sub-blocks of block k, in the arithmetic type T:
+//   F (3x3, row-major, 9 values), G (velocity rows x pressure column, 3), D (pressure row x
+//   velocity columns) with C appended (4).  Two storages: the full 4x4 blocks (BsrView) and the
+//   blocks stored apart (SplitView), where every pass over the matrix reads only the sub-block
+//   it needs.
+template <class S>
+struct SplitView {
+  int64_t V;
+  const int32_t *rowptr, *col, *diag, *trans;
+  const S *F;    // [nnzb][12]: F00 F01 F02 F10 F11 F12 F20 F21 F22 0 0 0
+  const S *G;    // [nnzb][4]:  G0 G1 G2 0
+  const S *DC;   // [nnzb][4]:  D0 D1 D2 C
+};
+
+// N consecutive values (N a multiple of 4) from an aligned record
+template <int N>
+__device__ __forceinline__ void ld_rec(const double *p, double *o) {
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + i);
+    o[2 * i] = v.x;
+    o[2 * i + 1] = v.y;
+  }
+}
+template <int N>
+__device__ __forceinline__ void ld_rec(const float *p, float *o) {
+#pragma unroll
+  for (int i = 0; i < N / 4; ++i) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + i);
+    o[4 * i] = v.x;
+    o[4 * i + 1] = v.y;
+    o[4 * i + 2] = v.z;
+    o[4 * i + 3] = v.w;
+  }
+}
+template <int N>
+__device__ __forceinline__ void ld_rec(const __nv_bfloat16 *p, float *o) {
+#pragma unroll
+  for (int i = 0; i < N / 4; ++i) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p) + i);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
+    o[4 * i] = a.x;
+    o[4 * i + 1] = a.y;
+    o[4 * i + 2] = b.x;
+    o[4 * i + 3] = b.y;
+  }
+}
+
+template <class S, class T>
+__device__ __forceinline__ void ld_F(const BsrView<S> &A, int64_t k, T f[9]) {
+  T b[16];
+  ld_block<S, T>(A.vals, k, b);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) f[3 * i + j] = b[4 * i + j];
+}
+template <class S, class T>
+__device__ __forceinline__ void ld_G(const BsrView<S> &A, int64_t k, T g[4]) {
+  const S *blk = A.vals + 16 * k;
+  g[0] = (T)blk[3];
+  g[1] = (T)blk[7];
+  g[2] = (T)blk[11];
+  g[3] = T(0);
+}
+template <class S, class T>
+__device__ __forceinline__ void ld_DC(const BsrView<S> &A, int64_t k, T dc[4]) {
+  const S *blk = A.vals + 16 * k + 12;
+  dc[0] = (T)blk[0];
+  dc[1] = (T)blk[1];
+  dc[2] = (T)blk[2];
+  dc[3] = (T)blk[3];
+}
+template <class S, class T>
+__device__ __forceinline__ void ld_F(const SplitView<S> &A, int64_t k, T f[9]) {
+  T b[12];
+  ld_rec<12>(A.F + 12 * k, b);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = b[i];
+}
+template <class S, class T>
+__device__ __forceinline__ void ld_G(const SplitView<S> &A, int64_t k, T g[4]) {
+  ld_rec<4>(A.G + 4 * k, g);
+}
+template <class S, class T>
+__device__ __forceinline__ void ld_DC(const SplitView<S> &A, int64_t k, T dc[4]) {
+  ld_rec<4>(A.DC + 4 * k, dc);
+}
+
+// Blocks stored apart (in the preconditioner's storage type S) from the FP64 4x4 blocks.
+template <class S>
+__global__ void split_kernel(int64_t nnzb, const double *__restrict__ vals, S *F, S *G, S *DC) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnzb; k += (int64_t)gridDim.x * blockDim.x) {
+    double b[16];
+    ld_block<double, double>(vals, k, b);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) F[12 * k + 3 * i + j] = (S)b[4 * i + j];
+#pragma unroll
+    for (int i = 9; i < 12; ++i) F[12 * k + i] = (S)0.0;
+    G[4 * k] = (S)b[3];
+    G[4 * k + 1] = (S)b[7];
+    G[4 * k + 2] = (S)b[11];
+    G[4 * k + 3] = (S)0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) DC[4 * k + i] = (S)b[12 + i];
+  }
+}
+
 // Gershgorin bounds for the Chebyshev intervals (every eigenvalue lies in a Gershgorin disc):
 //   mode 0: per row max_i |dinvF_i| sum_{k,j<3} |F_k[i][j]|                    -> part (max)
 //   mode 1: gs.xyz = sum_k |G_k[i][3]| (absolute row sums of G)                 -> gs
 //   mode 2: |dinvS| (sum_k |C_k| + sum_{k,j} |D_k[3][j]| |dinvF_col,j| gs_col,j) -> part (max)
-template <class S, class T>
-__global__ void __launch_bounds__(kThreads) bound_kernel(BsrView<S> A, const T *dinvF, const T *dinvS, T *gs,
+template <class View, class T>
+__global__ void __launch_bounds__(kThreads) bound_kernel(View A, const T *dinvF, const T *dinvS, T *gs,
                                                          double *part, int mode) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
@@ -216,21 +344,25 @@ __global__ void __launch_bounds__(kThreads) bound_kernel(BsrView<S> A, const T *
     const int32_t kend = A.rowptr[row + 1];
 #pragma unroll 4
     for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      T blk[16];
-      ld_block<S, T>(A.vals, kb, blk);
       if (mode == 0) {
-        a0 += fabs((Acc)blk[0]) + fabs((Acc)blk[1]) + fabs((Acc)blk[2]);
-        a1 += fabs((Acc)blk[4]) + fabs((Acc)blk[5]) + fabs((Acc)blk[6]);
-        a2 += fabs((Acc)blk[8]) + fabs((Acc)blk[9]) + fabs((Acc)blk[10]);
+        T f[9];
+        ld_F(A, kb, f);
+        a0 += fabs((Acc)f[0]) + fabs((Acc)f[1]) + fabs((Acc)f[2]);
+        a1 += fabs((Acc)f[3]) + fabs((Acc)f[4]) + fabs((Acc)f[5]);
+        a2 += fabs((Acc)f[6]) + fabs((Acc)f[7]) + fabs((Acc)f[8]);
       } else if (mode == 1) {
-        a0 += fabs((Acc)blk[3]);
-        a1 += fabs((Acc)blk[7]);
-        a2 += fabs((Acc)blk[11]);
+        T g[4];
+        ld_G(A, kb, g);
+        a0 += fabs((Acc)g[0]);
+        a1 += fabs((Acc)g[1]);
+        a2 += fabs((Acc)g[2]);
       } else {
+        T dc[4];
+        ld_DC(A, kb, dc);
         const auto df = ld4(dinvF, __ldg(A.col + kb));
         const auto g = ld4(gs, __ldg(A.col + kb));
-        a0 += fabs((Acc)blk[15]) + fabs((Acc)blk[12]) * fabs((Acc)df.x) * (Acc)g.x +
-              fabs((Acc)blk[13]) * fabs((Acc)df.y) * (Acc)g.y + fabs((Acc)blk[14]) * fabs((Acc)df.z) * (Acc)g.z;
+        a0 += fabs((Acc)dc[3]) + fabs((Acc)dc[0]) * fabs((Acc)df.x) * (Acc)g.x +
+              fabs((Acc)dc[1]) * fabs((Acc)df.y) * (Acc)g.y + fabs((Acc)dc[2]) * fabs((Acc)df.z) * (Acc)g.z;
       }
     }
   }
@@ -262,22 +394,23 @@ __global__ void __launch_bounds__(kThreads) bound_kernel(BsrView<S> A, const T *
 // aSIMPLE building blocks on the 4x4 blocks (row-major: [i][j], i test comp, j trial comp)
 //   F = [0..2][0..2], G = [0..2][3], D = [3][0..2], C = [3][3]
 // ------------------------------------------------------------------------------------------
-template <class S, class T>
-__global__ void diag_f_kernel(BsrView<S> A, T *dinvF) {
+template <class View, class T>
+__global__ void diag_f_kernel(View A, T *dinvF) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.V; r += (int64_t)gridDim.x * blockDim.x) {
-    const S *d = A.vals + 16 * (int64_t)A.diag[r];
+    T f[9];
+    ld_F(A, A.diag[r], f);
     typename Vec4T<T>::type o;
-    o.x = T(1) / (T)d[0];
-    o.y = T(1) / (T)d[5];
-    o.z = T(1) / (T)d[10];
+    o.x = T(1) / f[0];
+    o.y = T(1) / f[4];
+    o.z = T(1) / f[8];
     o.w = T(0);
     st4(dinvF, r, o);
   }
 }
 
 // diag(S)_a = C_aa - sum_{b,j} D_{a,(b,j)} G_{(b,j),a} / F_{(b,j),(b,j)}
-template <class S, class T>
-__global__ void diag_s_kernel(BsrView<S> A, const T *dinvF, T *dinvS) {
+template <class View, class T>
+__global__ void diag_s_kernel(View A, const T *dinvF, T *dinvS) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
@@ -285,15 +418,18 @@ __global__ void diag_s_kernel(BsrView<S> A, const T *dinvF, T *dinvS) {
     const int32_t kend = A.rowptr[row + 1];
 #pragma unroll 4
     for (int32_t k = A.rowptr[row] + lane; k < kend; k += kRowGroup) {
-      const S *blk = A.vals + 16 * (int64_t)k;              // block (a, b)
-      const S *tb = A.vals + 16 * (int64_t)A.trans[k];      // block (b, a)
+      T dc[4], g[4];
+      ld_DC(A, k, dc);             // block (a, b)
+      ld_G(A, A.trans[k], g);      // block (b, a)
       const auto df = ld4(dinvF, __ldg(A.col + k));
-      acc += (T)blk[12] * (T)tb[3] * df.x + (T)blk[13] * (T)tb[7] * df.y + (T)blk[14] * (T)tb[11] * df.z;
+      acc += dc[0] * g[0] * df.x + dc[1] * g[1] * df.y + dc[2] * g[2] * df.z;
     }
   }
   acc = group_sum(acc);
   if (row < A.V && lane == 0) {
-    const T c = (T)A.vals[16 * (int64_t)A.diag[row] + 15];
+    T dcd[4];
+    ld_DC(A, A.diag[row], dcd);
+    const T c = dcd[3];
     const T dd = c - acc;
     dinvS[row] = dd != T(0) ? T(1) / dd : T(0);   // a vanishing diagonal leaves the unknown unsmoothed
   }
@@ -301,8 +437,8 @@ __global__ void diag_s_kernel(BsrView<S> A, const T *dinvF, T *dinvS) {
 
 // Velocity smoothing step on F.  mode 0 (power): y = dinvF (F v), partial |y|^2.
 // mode 1 (Chebyshev/Jacobi step k): y = F d_old; r -= dinvF y; d_new = c1 d_old + c2 r; x += d_new.
-template <class S, class T>
-__global__ void __launch_bounds__(kThreads) f_step_kernel(BsrView<S> A, const T *dinvF, const T *d_old,
+template <class View, class T>
+__global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF, const T *d_old,
                                                           T *d_new, T *r, T *x, const SmoothCoef *cf,
                                                           int k, int mode, double *part, const KState *st) {
   if (finished(st)) return;
@@ -313,11 +449,11 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(BsrView<S> A, const T 
     const int32_t kend = A.rowptr[row + 1];
 #pragma unroll 4
     for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      T blk[16];
-      ld_block<S, T>(A.vals, kb, blk);
+      T f[9];
+      ld_F(A, kb, f);
       const auto dv = ld4(d_old, __ldg(A.col + kb));
 #pragma unroll
-      for (int i = 0; i < 3; ++i) acc[i] += blk[4 * i] * dv.x + blk[4 * i + 1] * dv.y + blk[4 * i + 2] * dv.z;
+      for (int i = 0; i < 3; ++i) acc[i] += f[3 * i] * dv.x + f[3 * i + 1] * dv.y + f[3 * i + 2] * dv.z;
     }
   }
 #pragma unroll
@@ -351,8 +487,8 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(BsrView<S> A, const T 
 }
 
 // w.xyz = dinvF (G p) with p = in.w   (velocity rows, pressure column)
-template <class S, class T>
-__global__ void __launch_bounds__(kThreads) g_scaled_kernel(BsrView<S> A, const T *dinvF, const T *in,
+template <class View, class T>
+__global__ void __launch_bounds__(kThreads) g_scaled_kernel(View A, const T *dinvF, const T *in,
                                                             T *w, const KState *st) {
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
@@ -362,11 +498,12 @@ __global__ void __launch_bounds__(kThreads) g_scaled_kernel(BsrView<S> A, const 
     const int32_t kend = A.rowptr[row + 1];
 #pragma unroll 4
     for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      const S *blk = A.vals + 16 * (int64_t)kb;
+      T g[4];
+      ld_G(A, kb, g);
       const T p = ld4(in, __ldg(A.col + kb)).w;
-      acc[0] += (T)blk[3] * p;
-      acc[1] += (T)blk[7] * p;
-      acc[2] += (T)blk[11] * p;
+      acc[0] += g[0] * p;
+      acc[1] += g[1] * p;
+      acc[2] += g[2] * p;
     }
   }
 #pragma unroll
@@ -381,8 +518,8 @@ __global__ void __launch_bounds__(kThreads) g_scaled_kernel(BsrView<S> A, const 
 
 // Pressure smoothing step on S = C - D diag(F)^-1 G, with w.xyz = diag(F)^-1 G d_old.w given.
 // mode 0 (power): y.w = dinvS (C v - D w), partial |y|^2.  mode 1: Chebyshev/Jacobi step.
-template <class S, class T>
-__global__ void __launch_bounds__(kThreads) s_step_kernel(BsrView<S> A, const T *dinvS, const T *d_old,
+template <class View, class T>
+__global__ void __launch_bounds__(kThreads) s_step_kernel(View A, const T *dinvS, const T *d_old,
                                                           const T *w, T *d_new, T *r, T *x,
                                                           const SmoothCoef *cf, int k, int mode,
                                                           double *part, const KState *st) {
@@ -394,11 +531,12 @@ __global__ void __launch_bounds__(kThreads) s_step_kernel(BsrView<S> A, const T 
     const int32_t kend = A.rowptr[row + 1];
 #pragma unroll 4
     for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      const S *blk = A.vals + 16 * (int64_t)kb;
+      T dc[4];
+      ld_DC(A, kb, dc);
       const int32_t c = __ldg(A.col + kb);
       const T p = ld4(d_old, c).w;
       const auto wv = ld4(w, c);
-      acc += (T)blk[15] * p - ((T)blk[12] * wv.x + (T)blk[13] * wv.y + (T)blk[14] * wv.z);
+      acc += dc[3] * p - (dc[0] * wv.x + dc[1] * wv.y + dc[2] * wv.z);
     }
   }
   acc = group_sum(acc);
@@ -452,8 +590,8 @@ __global__ void f_init_kernel(int64_t V, const T *dinvF, const T *b, T *r, T *d,
 }
 
 // t = b.w - D x.xyz, then start of the pressure smoothing: r.w = dinvS t, d.w = init r.w, x.w = d.w
-template <class S, class T>
-__global__ void __launch_bounds__(kThreads) d_init_kernel(BsrView<S> A, const T *dinvS, const T *b,
+template <class View, class T>
+__global__ void __launch_bounds__(kThreads) d_init_kernel(View A, const T *dinvS, const T *b,
                                                           T *r, T *d, T *x, const SmoothCoef *cf,
                                                           const KState *st, T *bs) {
   if (finished(st)) return;
@@ -464,9 +602,10 @@ __global__ void __launch_bounds__(kThreads) d_init_kernel(BsrView<S> A, const T 
     const int32_t kend = A.rowptr[row + 1];
 #pragma unroll 4
     for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      const S *blk = A.vals + 16 * (int64_t)kb;
+      T dc[4];
+      ld_DC(A, kb, dc);
       const auto xv = ld4(x, __ldg(A.col + kb));
-      acc += (T)blk[12] * xv.x + (T)blk[13] * xv.y + (T)blk[14] * xv.z;
+      acc += dc[0] * xv.x + dc[1] * xv.y + dc[2] * xv.z;
     }
   }
   acc = group_sum(acc);
@@ -488,8 +627,8 @@ __global__ void __launch_bounds__(kThreads) d_init_kernel(BsrView<S> A, const T 
 }
 
 // z.xyz = x.xyz - dinvF (G x.w), z.w = x.w
-template <class S, class T>
-__global__ void __launch_bounds__(kThreads) final_kernel(BsrView<S> A, const T *dinvF, const T *x, T *z,
+template <class View, class T>
+__global__ void __launch_bounds__(kThreads) final_kernel(View A, const T *dinvF, const T *x, T *z,
                                                          const KState *st) {
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
@@ -499,11 +638,12 @@ __global__ void __launch_bounds__(kThreads) final_kernel(BsrView<S> A, const T *
     const int32_t kend = A.rowptr[row + 1];
 #pragma unroll 4
     for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      const S *blk = A.vals + 16 * (int64_t)kb;
+      T g[4];
+      ld_G(A, kb, g);
       const T p = ld4(x, __ldg(A.col + kb)).w;
-      acc[0] += (T)blk[3] * p;
-      acc[1] += (T)blk[7] * p;
-      acc[2] += (T)blk[11] * p;
+      acc[0] += g[0] * p;
+      acc[1] += g[1] * p;
+      acc[2] += g[2] * p;
     }
   }
 #pragma unroll
@@ -525,8 +665,8 @@ __global__ void __launch_bounds__(kThreads) final_kernel(BsrView<S> A, const T *
 //   mode 0: out[row] = bs.w - (C x.w - D w)                       (for restriction)
 //   mode 1: r.w = dinvS (bs.w - (C x.w - D w)); d.w = init r.w     (post-smoothing start; the
 //           iterate is read at the neighbours here, so x.w += d.w is a separate kernel)
-template <class S, class T>
-__global__ void __launch_bounds__(kThreads) s_resid_kernel(BsrView<S> A, const T *dinvS, T *x, const T *w,
+template <class View, class T>
+__global__ void __launch_bounds__(kThreads) s_resid_kernel(View A, const T *dinvS, T *x, const T *w,
                                                            const T *bs, T *out, T *r, T *d,
                                                            const SmoothCoef *cf, int mode, const KState *st) {
   if (finished(st)) return;
@@ -537,11 +677,12 @@ __global__ void __launch_bounds__(kThreads) s_resid_kernel(BsrView<S> A, const T
     const int32_t kend = A.rowptr[row + 1];
 #pragma unroll 4
     for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      const S *blk = A.vals + 16 * (int64_t)kb;
+      T dc[4];
+      ld_DC(A, kb, dc);
       const int32_t c = __ldg(A.col + kb);
       const T p = ld4(x, c).w;
       const auto wv = ld4(w, c);
-      acc += (T)blk[15] * p - ((T)blk[12] * wv.x + (T)blk[13] * wv.y + (T)blk[14] * wv.z);
+      acc += dc[3] * p - (dc[0] * wv.x + dc[1] * wv.y + dc[2] * wv.z);
     }
   }
   acc = group_sum(acc);
@@ -942,32 +1083,33 @@ __global__ void __launch_bounds__(kThreads) mdot_kernel(const T *Vb, int64_t ld,
   const V4 *b4 = reinterpret_cast<const V4 *>(Vb);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   using A = typename AccT<T>::type;
-  for (int v0 = 0; v0 < nvec; v0 += 8) {
-    A acc[8] = {A(0), A(0), A(0), A(0), A(0), A(0), A(0), A(0)};
-    const int nv = min(8, nvec - v0);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-      const V4 wv = w4[i];
+  // blockIdx.y selects a group of eight basis vectors, so every group is read concurrently
+  const int v0 = 8 * blockIdx.y;
+  if (v0 >= nvec) return;
+  A acc[8] = {A(0), A(0), A(0), A(0), A(0), A(0), A(0), A(0)};
+  const int nv = min(8, nvec - v0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const V4 wv = w4[i];
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (k < nv) {
-          const V4 b = b4[(int64_t)(v0 + k) * ld4 + i];
-          acc[k] += (A)wv.x * (A)b.x + (A)wv.y * (A)b.y + (A)wv.z * (A)b.z + (A)wv.w * (A)b.w;
-        }
-    }
+    for (int k = 0; k < 8; ++k)
+      if (k < nv) {
+        const V4 b = b4[(int64_t)(v0 + k) * ld4 + i];
+        acc[k] += (A)wv.x * (A)b.x + (A)wv.y * (A)b.y + (A)wv.z * (A)b.z + (A)wv.w * (A)b.w;
+      }
+  }
+  // warp sums in the accumulator type (FP64 adds on every lane would bound the FP32 kernel)
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      double a = (double)acc[k];
+  for (int k = 0; k < 8; ++k) {
+    A a = acc[k];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (lane == 0) red[k][warp] = a;
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < nv) {
-      double s = 0.0;
-      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
-      part[(int64_t)(v0 + threadIdx.x) * ldp + blockIdx.x] = s;   // [vector][block]
-    }
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) red[k][warp] = (double)a;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nv) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
+    part[(int64_t)(v0 + threadIdx.x) * ldp + blockIdx.x] = s;   // [vector][block]
   }
 }
 
@@ -1021,8 +1163,7 @@ __global__ void __launch_bounds__(kThreads) maxpy_kernel(const T *Vb, int64_t ld
     w4[i] = o;
     nrm_t += a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3;
   }
-  const double nrm = (double)nrm_t;
-  double s = cta_sum(nrm);
+  double s = cta_sum_t(nrm_t);
   if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
 }
 
@@ -1090,7 +1231,7 @@ __global__ void norm_kernel(const T *v, int64_t n, double *part) {
   A a = A(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     a += (A)v[i] * (A)v[i];
-  double s = cta_sum((double)a);
+  double s = cta_sum_t(a);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -1249,24 +1390,26 @@ lfx_status ASimple<S, T>::init_borrowed(int64_t V_, const SmootherConfig &cfg_, 
 
 template <class S, class T>
 size_t ASimple<S, T>::device_bytes() const {
-  return dinvF.bytes + dinvS.bytes + X.bytes + D0.bytes + D1.bytes + R.bytes + W.bytes + coef.bytes + part.bytes;
+  return dinvF.bytes + dinvS.bytes + X.bytes + D0.bytes + D1.bytes + R.bytes + W.bytes + coef.bytes + part.bytes +
+         sF.bytes + sG.bytes + sDC.bytes;
 }
 
 // Diagonals and (Chebyshev) eigenvalue estimates for the current matrix.
 template <class S, class T>
-lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
+template <class View>
+lfx_status ASimple<S, T>::setup_view(cudaStream_t st, const View &A) {
   const int rg = rows_grid(V), vg = vec_grid(V);
-  diag_f_kernel<S, T><<<vg, kThreads, 0, st>>>(A, dinvF.as<T>());
-  diag_s_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>());
+  diag_f_kernel<View, T><<<vg, kThreads, 0, st>>>(A, dinvF.as<T>());
+  diag_s_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>());
   SmoothCoef *cf = coef.as<SmoothCoef>();
   double *lam_f = &cf->lam_f, *lam_s = &cf->lam_s;
   const bool bound = cfg.n_power <= 0;
   if (bound) {
     // Gershgorin bounds (hold for every eigenvalue; no safety factor)
-    bound_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 0);
+    bound_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 0);
     reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_f, 2);
-    bound_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 1);
-    bound_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 2);
+    bound_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 1);
+    bound_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 2);
     reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_s, 2);
     note_launches(5);
   }
@@ -1274,7 +1417,7 @@ lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
     // power iteration on diag(F)^-1 F from the normalised ones vector (velocity components)
     fill_kernel<T><<<vg, kThreads, 0, st>>>(V, D0.as<T>(), 7, 1.0 / sqrt(3.0 * (double)V));
     for (int it = 0; it < cfg.n_power; ++it) {
-      f_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), D0.as<T>(), D1.as<T>(), nullptr,
+      f_step_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), D0.as<T>(), D1.as<T>(), nullptr,
                                                    nullptr, cf, 0, 0, part.as<double>(), nullptr);
       reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_f, 1);
       div_kernel<T><<<vg, kThreads, 0, st>>>(V, D1.as<T>(), D0.as<T>(), 7, lam_f);
@@ -1284,8 +1427,8 @@ lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
   if (!bound && cfg.s_kind != LFX_SMOOTH_JACOBI) {
     fill_kernel<T><<<vg, kThreads, 0, st>>>(V, D0.as<T>(), 8, 1.0 / sqrt((double)V));
     for (int it = 0; it < cfg.n_power; ++it) {
-      g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), D0.as<T>(), W.as<T>(), nullptr);
-      s_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), D0.as<T>(), W.as<T>(), D1.as<T>(),
+      g_scaled_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), D0.as<T>(), W.as<T>(), nullptr);
+      s_step_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), D0.as<T>(), W.as<T>(), D1.as<T>(),
                                                    nullptr, nullptr, cf, 0, 0, part.as<double>(), nullptr);
       reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_s, 1);
       div_kernel<T><<<vg, kThreads, 0, st>>>(V, D1.as<T>(), D0.as<T>(), 8, lam_s);
@@ -1299,27 +1442,51 @@ lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
   return LFX_OK;
 }
 
+template <class S, class T>
+lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
+  split = false;
+  return setup_view(st, A);
+}
+
+// Sub-blocks stored apart in S, converted from the FP64 blocks; diagonals and bounds from them.
+template <class S, class T>
+lfx_status ASimple<S, T>::setup_split(cudaStream_t st, const BsrView<double> &A64, int64_t nnzb) {
+  if (!sF.p || nnz_split != nnzb) {
+    LFX_TRY(sF.alloc(sizeof(S) * 12 * (size_t)nnzb));
+    LFX_TRY(sG.alloc(sizeof(S) * 4 * (size_t)nnzb));
+    LFX_TRY(sDC.alloc(sizeof(S) * 4 * (size_t)nnzb));
+    nnz_split = nnzb;
+  }
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nnzb + kThreads - 1) / kThreads, 152 * 16));
+  split_kernel<S><<<g, kThreads, 0, st>>>(nnzb, A64.vals, sF.as<S>(), sG.as<S>(), sDC.as<S>());
+  note_launches(1);
+  split = true;
+  const SplitView<S> sv{A64.V, A64.rowptr, A64.col, A64.diag, A64.trans, sF.as<S>(), sG.as<S>(), sDC.as<S>()};
+  return setup_view(st, sv);
+}
+
 // z = P^-1 r (aSIMPLE); r, z are [V][4] vectors of type T (they may not alias the work arrays).
 template <class S, class T>
-lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r, T *z, const KState *ks) {
+template <class View>
+lfx_status ASimple<S, T>::apply_view(cudaStream_t st, const View &A, const T *r, T *z, const KState *ks) {
   const int rg = rows_grid(V), vg = vec_grid(V);
   const SmoothCoef *cf = coef.as<SmoothCoef>();
   T *d[2] = {D0.as<T>(), D1.as<T>()};
   // z_u* ~= F^-1 r_u
   f_init_kernel<T><<<vg, kThreads, 0, st>>>(V, dinvF.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks);
   for (int k = 1; k < cfg.f_steps; ++k)
-    f_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], d[k & 1], R.as<T>(),
+    f_step_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], d[k & 1], R.as<T>(),
                                                  X.as<T>(), cf, k, 1, nullptr, ks);
   // z_p ~= S^-1 (r_p - D z_u*): Chebyshev/Jacobi steps on S, or one AMG V-cycle
   if (cfg.s_kind == LFX_SMOOTH_AMG && !amg_ready) {
     set_error("aSIMPLE: the Schur AMG hierarchy has not been built");
     return LFX_ERR_INVALID_ARG;
   }
-  d_init_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks,
+  d_init_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks,
                                                amg_ready ? Bs.as<T>() : nullptr);
   for (int k = 1; k < cfg.s_steps; ++k) {
-    g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
-    s_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
+    g_scaled_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
+    s_step_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
                                                  R.as<T>(), X.as<T>(), cf, k, 1, nullptr, ks);
   }
   if (cfg.s_kind == LFX_SMOOTH_AMG && amg.size() == 1) {
@@ -1329,8 +1496,8 @@ lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r
     note_launches(1);
   } else if (cfg.s_kind == LFX_SMOOTH_AMG) {
     // residual of the pre-smoothed level-0 iterate, restriction, coarse V-cycle, prolongation
-    g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
-    s_resid_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(),
+    g_scaled_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
+    s_resid_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(),
                                                   rr0.as<T>(), nullptr, nullptr, cf, 0, ks);
     const AmgDevLevel &L0 = amg[0];
     CsrV<T> R0{L0.nnext, L0.Rrp.as<int32_t>(), L0.Rci.as<int32_t>(), L0.Rv.as<T>()};
@@ -1351,19 +1518,19 @@ lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r
     csr_spmv_kernel<T, 8><<<lanes_grid(V, 8), kThreads, 0, st>>>(P0, x1, 1, 0, X.as<T>(), 4, 3,
                                                             amg_alpha, 1, ks);
     // post-smoothing from the corrected iterate
-    g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
-    s_resid_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(), nullptr,
+    g_scaled_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
+    s_resid_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(), nullptr,
                                                   R.as<T>(), d[0], cf, 1, ks);
     add_w_kernel<T><<<vg, kThreads, 0, st>>>(V, d[0], X.as<T>(), ks);
     for (int k = 1; k < cfg.s_steps; ++k) {
-      g_scaled_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
-      s_step_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
+      g_scaled_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
+      s_step_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
                                                    R.as<T>(), X.as<T>(), cf, k, 1, nullptr, ks);
     }
     note_launches(9 + 2 * (cfg.s_steps - 1));
   }
   // z_u = z_u* - diag(F)^-1 G z_p
-  final_kernel<S, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), z, ks);
+  final_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), z, ks);
   note_launches(3 + (cfg.f_steps - 1) + 2 * (cfg.s_steps - 1));
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
@@ -1510,6 +1677,15 @@ size_t ASimple<S, T>::amg_bytes() const {
 static inline double H_nnz(const AmgDevLevel &D, size_t elem) { return (double)D.v.bytes / (double)elem; }
 
 // One V-cycle on the explicit levels l >= 1 for amg[l].b -> amg[l].x
+template <class S, class T>
+lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r, T *z, const KState *ks) {
+  if (split) {
+    const SplitView<S> sv{A.V, A.rowptr, A.col, A.diag, A.trans, sF.as<S>(), sG.as<S>(), sDC.as<S>()};
+    return apply_view(st, sv, r, z, ks);
+  }
+  return apply_view(st, A, r, z, ks);
+}
+
 template <class S, class T>
 lfx_status ASimple<S, T>::vcycle(cudaStream_t st, int l, const KState *ks) {
   AmgDevLevel &D = amg[l];
@@ -1683,7 +1859,8 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
       LFX_CUDA_TRY(cudaEventRecord(tev[n_tev + 1], st));
       n_tev += 2;
       for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
-        mdot_kernel<T><<<nblk_dot, kThreads, 0, st>>>(Vb, n, j + 1, w, n, part.as<double>(), nblk_dot, ks);
+        mdot_kernel<T><<<dim3(nblk_dot, (j + 8) / 8), kThreads, 0, st>>>(Vb, n, j + 1, w, n, part.as<double>(),
+                                                                          nblk_dot, ks);
         mdot_finalize_kernel<<<j + 1, 32, 0, st>>>(part.as<double>(), nblk_dot, nblk_dot, j + 1, ks, pass);
         maxpy_kernel<T><<<vg, kThreads, 0, st>>>(Vb, n, j + 1, w, n, pn, ks);
       }

@@ -64,6 +64,9 @@ struct ASimple {
   // Schur AMG (cfg.s_kind == LFX_SMOOTH_AMG)
   std::vector<AmgDevLevel> amg;
   DBuf Bs, rr0, coarse_inv, coarse_args;
+  DBuf sF, sG, sDC;                // sub-blocks stored apart (setup_split)
+  int64_t nnz_split = 0;
+  bool split = false;
   int64_t nc = 0;
   std::vector<int64_t> lvl_rows, lvl_nnz;   // hierarchy shape (rows, nonzeros of A_l per level)
   int coop_grid = 0;   // > 0: the coarse V-cycle runs as one cooperative launch of this many CTAs
@@ -76,10 +79,21 @@ struct ASimple {
   // Work arrays carved from caller-provided device memory (no allocation); zeroed on st.
   static size_t scratch_bytes(int64_t V);
   lfx_status init_borrowed(int64_t V, const SmootherConfig &cfg, void *base, size_t cap, cudaStream_t st);
+  // Set-up on the full blocks A (the smoother then reads A's 4x4 blocks on every pass) ...
   lfx_status setup(cudaStream_t st, const BsrView<S> &A);
+  // ... or on a copy of the FP64 blocks A64 converted to S with F, G and (D, C) stored apart, so
+  // that each pass reads only the sub-block it needs (nnzb = number of blocks).
+  lfx_status setup_split(cudaStream_t st, const BsrView<double> &A64, int64_t nnzb);
+  // z = P^-1 r; with a split set-up only A's pattern (rowptr, col, diag, trans) is used.
   lfx_status apply(cudaStream_t st, const BsrView<S> &A, const T *r, T *z, const KState *ks);
   lfx_status lambdas(double *lf, double *ls) const;
   size_t device_bytes() const;
+
+ private:
+  template <class View>
+  lfx_status setup_view(cudaStream_t st, const View &A);
+  template <class View>
+  lfx_status apply_view(cudaStream_t st, const View &A, const T *r, T *z, const KState *ks);
 };
 
 // z = M^-1 v on the solver's stream; kernels may return early once ks->done is set.
