@@ -125,6 +125,11 @@ struct lfx_state {
   DBuf vals64, vals32, nopat;   // nopat: empty (pattern-only views)
   ASimple<double, double> pc64;
   Gmres<double, double> gm64;
+  // mixed precision: the matrix is assembled in double-float arithmetic as FP32 high parts
+  // (vals32, also the inner solve's operator) and low parts (vals_lo); the outer FGMRES runs on
+  // hi + lo with FP64 vectors
+  DBuf vals_lo, rhs_hi, rhs_lo, xe_hi, xe_lo, ub_hi, ub_lo, xs_hi, xs_lo;
+  Gmres<DDMat, double> gmdd;
   // mixed precision: FP32 inner Krylov with an FP32 or BF16-storage aSIMPLE
   ASimple<float, float> pc32;
   ASimple<__nv_bfloat16, float> pcbf;
@@ -150,6 +155,13 @@ struct lfx_state {
     return BsrView<S>{m.V, m.d_rowptr.as<int32_t>(), m.d_col.as<int32_t>(), m.d_diag.as<int32_t>(),
                       m.d_trans.as<int32_t>(), v.as<S>()};
   }
+  BsrView<DDMat> view_dd() const {
+    const Mesh &m = pb->mesh->m;
+    return BsrView<DDMat>{m.V, m.d_rowptr.as<int32_t>(), m.d_col.as<int32_t>(), m.d_diag.as<int32_t>(),
+                          m.d_trans.as<int32_t>(), vals32.as<float>(), vals_lo.as<float>(),
+                          xs_hi.as<float4>(), xs_lo.as<float4>()};
+  }
+  bool mixed() const { return pb->opt.precision == LFX_PREC_MIXED; }
   BsrView<double> view64() const {
     const Mesh &m = pb->mesh->m;
     return BsrView<double>{m.V, m.d_rowptr.as<int32_t>(), m.d_col.as<int32_t>(), m.d_diag.as<int32_t>(),
@@ -700,7 +712,7 @@ lfx_status lfx_state_create(lfx_problem *pb, const double *u_hist, const double 
   LFX_CUDA_TRY(cudaMemset(s->nodal.p, 0, s->nodal.bytes));
   LFX_TRY(s->comp_scale.alloc(sizeof(double) * (size_t)m.n_comp));
   const lfx_options &o = pb->opt;
-  LFX_TRY(s->vals64.alloc(sizeof(double) * 16 * m.nnzb));
+  if (o.precision != LFX_PREC_MIXED) LFX_TRY(s->vals64.alloc(sizeof(double) * 16 * m.nnzb));
   SmootherConfig cfg;
   cfg.f_kind = o.f_smoother;
   cfg.f_steps = o.f_steps;
@@ -713,13 +725,18 @@ lfx_status lfx_state_create(lfx_problem *pb, const double *u_hist, const double 
   cfg.n_power = o.n_power;
   if (o.precision == LFX_PREC_MIXED) {
     LFX_TRY(s->vals32.alloc(sizeof(float) * 16 * m.nnzb));
+    LFX_TRY(s->vals_lo.alloc(sizeof(float) * 16 * m.nnzb));
+    LFX_TRY(s->rhs_hi.alloc(sizeof(float) * 4 * V));
+    LFX_TRY(s->rhs_lo.alloc(sizeof(float) * 4 * V));
+    DBuf *f4[6] = {&s->xe_hi, &s->xe_lo, &s->ub_hi, &s->ub_lo, &s->xs_hi, &s->xs_lo};
+    for (DBuf *b : f4) LFX_TRY(b->alloc(sizeof(float4) * V));
     if (o.smoother_bf16) {
       LFX_TRY(s->pcbf.init(V, cfg));
     } else {
       LFX_TRY(s->pc32.init(V, cfg));
     }
     LFX_TRY(s->gm32.init(V, o.gmres_restart));
-    LFX_TRY(s->gm64.init(V, std::max(1, o.outer_restart)));
+    LFX_TRY(s->gmdd.init(V, std::max(1, o.outer_restart)));
     LFX_TRY(s->r32.alloc(sizeof(float) * 4 * V));
     LFX_TRY(s->z32.alloc(sizeof(float) * 4 * V));
   } else {
@@ -810,7 +827,9 @@ lfx_status lfx_state_device_bytes(const lfx_state *s, int64_t *bytes) {
              s->rhs.bytes + s->gdir.bytes + s->nodal.bytes + s->vals64.bytes + s->vals32.bytes +
              s->pc64.device_bytes() + s->pc64.amg_bytes() + s->gm64.device_bytes() +
              s->pc32.device_bytes() + s->pc32.amg_bytes() + s->pcbf.device_bytes() + s->pcbf.amg_bytes() +
-             s->gm32.device_bytes() + s->r32.bytes + s->z32.bytes;
+             s->gm32.device_bytes() + s->r32.bytes + s->z32.bytes + s->gmdd.device_bytes() + s->vals_lo.bytes +
+             s->rhs_hi.bytes + s->rhs_lo.bytes + s->xe_hi.bytes + s->xe_lo.bytes + s->ub_hi.bytes + s->ub_lo.bytes +
+             s->xs_hi.bytes + s->xs_lo.bytes;
   for (int l = 0; l < 3; ++l) b += s->hist[l].bytes;
   *bytes = (int64_t)b;
   return LFX_OK;
@@ -823,10 +842,19 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
   cudaStream_t st = s->stream;
   const double t1 = s->t + pb->P.dt;
   const int sg = s->sigma;
+  const bool mixed = s->mixed();
   LFX_TRY(launch_bdf(st, m.V, sg, s->level(0), sg > 1 ? s->level(1) : nullptr, sg > 2 ? s->level(2) : nullptr,
-                     pb->beta, pb->gamma, s->xsol.as<D4>(), s->ubdf.as<D4>()));
-  LFX_CUDA_TRY(cudaMemsetAsync(s->vals64.p, 0, s->vals64.bytes, st));
-  LFX_CUDA_TRY(cudaMemsetAsync(s->rhs.p, 0, s->rhs.bytes, st));
+                     pb->beta, pb->gamma, s->xsol.as<D4>(), s->ubdf.as<D4>(), s->xe_hi.as<float4>(),
+                     s->xe_lo.as<float4>(), s->ub_hi.as<float4>(), s->ub_lo.as<float4>()));
+  if (mixed) {
+    LFX_CUDA_TRY(cudaMemsetAsync(s->vals32.p, 0, s->vals32.bytes, st));
+    LFX_CUDA_TRY(cudaMemsetAsync(s->vals_lo.p, 0, s->vals_lo.bytes, st));
+    LFX_CUDA_TRY(cudaMemsetAsync(s->rhs_hi.p, 0, s->rhs_hi.bytes, st));
+    LFX_CUDA_TRY(cudaMemsetAsync(s->rhs_lo.p, 0, s->rhs_lo.bytes, st));
+  } else {
+    LFX_CUDA_TRY(cudaMemsetAsync(s->vals64.p, 0, s->vals64.bytes, st));
+    LFX_CUDA_TRY(cudaMemsetAsync(s->rhs.p, 0, s->rhs.bytes, st));
+  }
   AssembleArgs A;
   A.conn = m.d_conn.as<int4>();
   A.slot = m.d_slot.as<int32_t>();
@@ -837,10 +865,27 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
   A.bad = nullptr;
   A.rhs = s->rhs.as<double>();
   A.n_nodes = m.V;
+  A.xyz_hi = m.d_xyz_hi.as<float4>();
+  A.xyz_lo = m.d_xyz_lo.as<float4>();
+  A.xext_hi = s->xe_hi.as<float4>();
+  A.xext_lo = s->xe_lo.as<float4>();
+  A.ubdf_hi = s->ub_hi.as<float4>();
+  A.ubdf_lo = s->ub_lo.as<float4>();
+  A.vals_lo = s->vals_lo.as<float>();
+  A.rhs_hi = s->rhs_hi.as<float>();
+  A.rhs_lo = s->rhs_lo.as<float>();
   LFX_CUDA_TRY(cudaEventRecord(s->ea0, st));
-  LFX_TRY((launch_assemble<double, double>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
-                                           s->vals64.as<double>())));
+  if (mixed) {
+    // double-float arithmetic; badly shaped elements keep FP64 geometry
+    A.bad = pb->n_bad > 0 ? pb->d_bad.as<uint8_t>() : nullptr;
+    LFX_TRY((launch_assemble<dd, float>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
+                                        s->vals32.as<float>())));
+  } else {
+    LFX_TRY((launch_assemble<double, double>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
+                                             s->vals64.as<double>())));
+  }
   LFX_CUDA_TRY(cudaEventRecord(s->ea1, st));
+  if (mixed) LFX_TRY(launch_dd_combine(st, 4 * m.V, s->rhs_hi.as<float>(), s->rhs_lo.as<float>(), s->rhs.as<double>()));
   s->n_asm_launch = (int)m.color_off.size() - 1;
   // boundary data at t^{n+1}
   DirCoef C;
@@ -876,12 +921,24 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
   const int64_t nd = (int64_t)pb->dir_node.size();
   LFX_TRY(launch_dirichlet_values(st, nd, H, pb->d_dir_bc.as<int32_t>(), pb->d_S.as<double>(), C,
                                   s->nodal.as<double>(), nb, s->gdir.as<D4>()));
-  LFX_TRY(launch_apply_dirichlet<double>(st, nd, pb->d_dir_node.as<int32_t>(), s->gdir.as<D4>(), pb->pin_node,
-                                         s->pin_value, m.d_rowptr.as<int32_t>(), m.d_diag.as<int32_t>(),
-                                         s->vals64.as<double>(), s->rhs.as<double>(), s->xsol.as<double>()));
-  if (m.n_comp > 1 && pb->opt.batch_normalize)
-    LFX_TRY(launch_comp_normalize(st, m.V, m.n_comp, m.d_comp_off.as<int32_t>(), s->comp_scale.as<double>(),
-                                  m.d_rowptr.as<int32_t>(), s->vals64.as<double>(), s->rhs.as<double>()));
+  if (mixed)
+    LFX_TRY(launch_apply_dirichlet_dd(st, nd, pb->d_dir_node.as<int32_t>(), s->gdir.as<D4>(), pb->pin_node,
+                                      s->pin_value, m.d_rowptr.as<int32_t>(), m.d_diag.as<int32_t>(),
+                                      s->vals32.as<float>(), s->vals_lo.as<float>(), s->rhs.as<double>(),
+                                      s->xsol.as<double>()));
+  else
+    LFX_TRY(launch_apply_dirichlet<double>(st, nd, pb->d_dir_node.as<int32_t>(), s->gdir.as<D4>(), pb->pin_node,
+                                           s->pin_value, m.d_rowptr.as<int32_t>(), m.d_diag.as<int32_t>(),
+                                           s->vals64.as<double>(), s->rhs.as<double>(), s->xsol.as<double>()));
+  if (m.n_comp > 1 && pb->opt.batch_normalize) {
+    if (mixed)
+      LFX_TRY(launch_comp_normalize_dd(st, m.V, m.n_comp, m.d_comp_off.as<int32_t>(), s->comp_scale.as<double>(),
+                                       m.d_rowptr.as<int32_t>(), s->vals32.as<float>(), s->vals_lo.as<float>(),
+                                       s->rhs.as<double>()));
+    else
+      LFX_TRY(launch_comp_normalize(st, m.V, m.n_comp, m.d_comp_off.as<int32_t>(), s->comp_scale.as<double>(),
+                                    m.d_rowptr.as<int32_t>(), s->vals64.as<double>(), s->rhs.as<double>()));
+  }
   return LFX_OK;
 }
 
@@ -898,11 +955,11 @@ int64_t lfx_internal_state_bytes_estimate(const lfx_problem *pb, int64_t *V_out,
   if (sigma_out) *sigma_out = sigma;
   const int64_t v64 = 32 * V, v32 = 16 * V;
   int64_t b = (sigma + 3) * v64 + 64 * (int64_t)pb->dir_node.size() + 8 * m.n_comp;
-  b += 128 * nnzb;                                           // FP64 matrix
+  b += 128 * nnzb;                                           // FP64 or double-float matrix
   const int64_t amg = o.s_smoother == LFX_SMOOTH_AMG ? 300 * V + 8LL * o.amg_coarse_size * o.amg_coarse_size : 0;
   const int64_t part = 8LL * 152 * 4 * 65 + 8 * (V * 8 / 256 + 64);
   if (o.precision == LFX_PREC_MIXED) {
-    b += 64 * nnzb + (o.smoother_bf16 ? 40 * nnzb : 80 * nnzb);   // FP32 copy; F, G, (D, C) apart
+    b += (o.smoother_bf16 ? 40 * nnzb : 80 * nnzb) + 8 * v32;     // F, G, (D, C) apart; split inputs
     b += 7 * v32 + 4 * V + amg;                               // FP32 aSIMPLE work
     b += (2 * (int64_t)o.gmres_restart + 2) * v32 + part;    // inner GMRES
     b += (2 * (int64_t)std::max(1, o.outer_restart) + 2) * v64 + part;   // outer FGMRES
@@ -927,6 +984,24 @@ lfx_status lfx_problem_state_bytes(const lfx_problem *pb, int64_t *bytes) {
 
 }  // extern "C"
 
+// The assembled matrix as FP64 values on the host (hi + lo for the double-float matrix).
+static lfx_status download_matrix(lfx_state *s, std::vector<double> &h) {
+  const Mesh &m = s->pb->mesh->m;
+  const size_t n = 16 * (size_t)m.nnzb;
+  h.resize(n);
+  if (!s->mixed()) {
+    LFX_CUDA_TRY(cudaMemcpyAsync(h.data(), s->vals64.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+    LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return LFX_OK;
+  }
+  std::vector<float> hi(n), lo(n);
+  LFX_CUDA_TRY(cudaMemcpyAsync(hi.data(), s->vals32.p, sizeof(float) * n, cudaMemcpyDeviceToHost, s->stream));
+  LFX_CUDA_TRY(cudaMemcpyAsync(lo.data(), s->vals_lo.p, sizeof(float) * n, cudaMemcpyDeviceToHost, s->stream));
+  LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  for (size_t i = 0; i < n; ++i) h[i] = (double)hi[i] + (double)lo[i];
+  return LFX_OK;
+}
+
 // aSIMPLE set-up for the current matrix: the sub-blocks F, G, (D, C) stored apart in the
 // smoother's storage type (FP64, FP32 or BF16), diagonals and eigenvalue bounds every step; the
 // Schur AMG hierarchy (built from the FP64 matrix) on first use and then every amg_refresh steps.
@@ -935,15 +1010,17 @@ static lfx_status setup_asimple(lfx_state *s, ASimple<S, T> &pc) {
   lfx_problem *pb = s->pb;
   const lfx_options &o = pb->opt;
   const Mesh &m = pb->mesh->m;
-  LFX_TRY(pc.setup_split(s->stream, s->view64(), m.nnzb));
+  if (s->mixed())
+    LFX_TRY(pc.setup_split(s->stream, s->view<float>(s->vals32), m.nnzb));   // from the high parts
+  else
+    LFX_TRY(pc.setup_split(s->stream, s->view64(), m.nnzb));
   if (o.s_smoother != LFX_SMOOTH_AMG) return LFX_OK;
   if (pc.amg_ready && !(o.amg_refresh > 0 && s->amg_age >= o.amg_refresh)) {
     ++s->amg_age;
     return LFX_OK;
   }
-  std::vector<double> h(16 * (size_t)m.nnzb);
-  LFX_CUDA_TRY(cudaMemcpyAsync(h.data(), s->vals64.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s->stream));
-  LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  std::vector<double> h;
+  LFX_TRY(download_matrix(s, h));
   CsrHost S0 = schur_explicit(m.V, m.row_ptr, m.col_idx, m.diag_idx, h.data());
   AmgParams prm;
   prm.coarse_size = o.amg_coarse_size;
@@ -959,10 +1036,9 @@ static lfx_status setup_asimple(lfx_state *s, ASimple<S, T> &pc) {
 static lfx_status prepare_precond(lfx_state *s) {
   const lfx_options &o = s->pb->opt;
   const Mesh &m = s->pb->mesh->m;
+  (void)m;
   if (o.precision != LFX_PREC_MIXED) return setup_asimple(s, s->pc64);
-  // FP32 copy of the operator for the inner Krylov solve
-  const int64_t nv = 16 * m.nnzb;
-  LFX_TRY((launch_convert<double, float>(s->stream, s->vals64.as<double>(), s->vals32.as<float>(), nv, nullptr)));
+  // the inner Krylov solve's FP32 operator is the high part of the double-float matrix
   if (o.smoother_bf16) return setup_asimple(s, s->pcbf);
   return setup_asimple(s, s->pc32);
 }
@@ -980,8 +1056,8 @@ static lfx_status run_solve(lfx_state *s, double *x, bool x_zero, int *its, int 
     return s->gm64.solve(st, A, pc, s->rhs.as<double>(), x, o.gmres_rtol, o.gmres_max_iters,
                          o.reorthogonalize != 0, 2, x_zero, its, rel);
   }
-  // outer flexible GMRES in FP64 on the FP64 operator; each preconditioner application is an
-  // FP32 GMRES solve (to inner_rtol) with the FP32/BF16 aSIMPLE
+  // outer flexible GMRES with FP64 vectors on the double-float operator; each preconditioner
+  // application is an FP32 GMRES solve (to inner_rtol) with the FP32/BF16 aSIMPLE
   const int64_t n = 4 * s->pb->mesh->m.V;
   const BsrView<float> A32 = s->view<float>(s->vals32);
   s->inner_total = 0;
@@ -1009,7 +1085,7 @@ static lfx_status run_solve(lfx_state *s, double *x, bool x_zero, int *its, int 
     clear_error();
     return launch_convert<float, double>(q, s->z32.as<float>(), z, n, ks);
   };
-  lfx_status rc = s->gm64.solve(st, A, inner, s->rhs.as<double>(), x, o.gmres_rtol, o.outer_max_iters,
+  lfx_status rc = s->gmdd.solve(st, s->view_dd(), inner, s->rhs.as<double>(), x, o.gmres_rtol, o.outer_max_iters,
                                 o.reorthogonalize != 0, 0, x_zero, outer, rel);
   *its = s->inner_total;
   return rc;
@@ -1034,6 +1110,7 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   double rel = 0.0;
   s->gm64.n_tev = 0;
   s->gm32.n_tev = 0;
+  s->gmdd.n_tev = 0;
   lfx_status rc = run_solve(s, s->xsol.as<double>(), false, &its, &outer, &rel);
   if (rc != LFX_OK && rc != LFX_ERR_NOT_CONVERGED) return rc;
   LFX_CUDA_TRY(cudaEventRecord(s->e2, st));
@@ -1060,7 +1137,7 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
       s->gm32.read_spmv_timing(&stats->ms_spmv, &stats->n_spmv);
       int dummy = 0;
       float d2 = 0.0f;
-      s->gm64.read_spmv_timing(&d2, &dummy);
+      s->gmdd.read_spmv_timing(&d2, &dummy);
     } else {
       s->gm64.read_spmv_timing(&stats->ms_spmv, &stats->n_spmv);
     }
@@ -1122,8 +1199,8 @@ lfx_status lfx_debug_assemble(lfx_state *s, int32_t apply_bcs, double *blocks, d
   const Mesh &m = s->pb->mesh->m;
   LFX_TRY(assemble_system(s, apply_bcs != 0));
   s->assembled = true;
-  std::vector<double> v(16 * (size_t)m.nnzb);
-  LFX_CUDA_TRY(cudaMemcpyAsync(v.data(), s->vals64.p, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, s->stream));
+  std::vector<double> v;
+  LFX_TRY(download_matrix(s, v));
   LFX_TRY(vec_to_host(m, s->rhs.as<double>(), rhs, s->stream));
   std::vector<int64_t> rp, ib;
   std::vector<int32_t> ci;
@@ -1143,8 +1220,12 @@ lfx_status lfx_debug_spmv(lfx_state *s, const double *x, double *y) {
   LFX_TRY(dx.alloc(sizeof(D4) * m.V));
   LFX_TRY(dy.alloc(sizeof(D4) * m.V));
   LFX_TRY(vec_to_device(m, x, dx.as<double>(), s->stream));
-  LFX_TRY((launch_spmv<double, double>(s->stream, s->view64(), dx.as<double>(), nullptr, dy.as<double>(), 0,
-                                       nullptr, nullptr)));
+  if (s->mixed())
+    LFX_TRY((launch_spmv<DDMat, double>(s->stream, s->view_dd(), dx.as<double>(), nullptr, dy.as<double>(), 0,
+                                        nullptr, nullptr)));
+  else
+    LFX_TRY((launch_spmv<double, double>(s->stream, s->view64(), dx.as<double>(), nullptr, dy.as<double>(), 0,
+                                         nullptr, nullptr)));
   return vec_to_host(m, dy.as<double>(), y, s->stream);
 }
 
@@ -1185,6 +1266,7 @@ lfx_status lfx_debug_solve(lfx_state *s, double *x, lfx_step_stats *stats) {
   LFX_TRY(prepare_precond(s));
   s->gm64.n_tev = 0;
   s->gm32.n_tev = 0;
+  s->gmdd.n_tev = 0;
   int its = 0, outer = 0;
   double rel = 0;
   lfx_status rc = run_solve(s, dx.as<double>(), true, &its, &outer, &rel);

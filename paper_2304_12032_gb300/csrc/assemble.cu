@@ -8,6 +8,10 @@
 // block 16 values row-major (row = test component, column = trial component).  Elements of one
 // colour share no node, so one launch per colour updates disjoint blocks without atomics.
 //
+// The arithmetic type R is FP64 (the FP64 path), FP32, or double-float (dd: FP32 pairs with a
+// 48-bit significand, for the mixed-precision path: FP64-class accuracy on the FP32 pipes; its
+// inputs arrive pre-split and the matrix is accumulated as FP32 high and low parts).
+//
 // One CTA of 128 threads works on 32 elements at a time:
 //   phase 1: 4 threads per element, thread q evaluates quadrature point q (geometry, u*, tau_M,
 //            tau_C, the LES vector tau_M r_M(u^EXT, p^EXT), ...) into shared memory;
@@ -15,6 +19,9 @@
 //            (a, b) and adds them into global memory (read-modify-write of 128 B / 64 B).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "dd.h"
 #include "lfx_internal.h"
 #include "kernels.h"
 
@@ -26,6 +33,53 @@ constexpr int kCta = 128;
 constexpr int kElems = 32;          // elements per CTA pass
 constexpr double kQA = 0.58541019662496845446;   // (5 + 3 sqrt5) / 20
 constexpr double kQB = 0.13819660112501051518;   // (5 - sqrt5) / 20
+
+// Physical coefficients in the arithmetic type (split once on the host)
+template <class R>
+struct PhysR {
+  R rho, mu, rho_dt, alpha, rho_alpha_dt, tau_t, cr_mu2, f[3];
+};
+template <class R>
+PhysR<R> phys_r(const PhysParams &P) {
+  PhysR<R> q;
+  q.rho = R(P.rho);
+  q.mu = R(P.mu);
+  q.rho_dt = R(P.rho_dt);
+  q.alpha = R(P.alpha);
+  q.rho_alpha_dt = R(P.rho_alpha_dt);
+  q.tau_t = R(P.tau_t);
+  q.cr_mu2 = R(P.cr_mu2);
+  for (int i = 0; i < 3; ++i) q.f[i] = R(P.f[i]);
+  return q;
+}
+
+// four values of node n: FP64 and FP32 from the FP64 array, dd from the split arrays
+template <class R>
+__device__ __forceinline__ void ld_node(const D4 *d, const float4 *, const float4 *, int64_t n, R v[4]) {
+  const D4 a = d[n];
+  v[0] = (R)a.x;
+  v[1] = (R)a.y;
+  v[2] = (R)a.z;
+  v[3] = (R)a.w;
+}
+template <>
+__device__ __forceinline__ void ld_node<dd>(const D4 *, const float4 *hi, const float4 *lo, int64_t n, dd v[4]) {
+  const float4 h = hi[n], l = lo[n];
+  v[0] = dd(h.x, l.x);
+  v[1] = dd(h.y, l.y);
+  v[2] = dd(h.z, l.z);
+  v[3] = dd(h.w, l.w);
+}
+
+// a compile-time constant in the arithmetic type (the split of a literal folds at compile time)
+template <class R>
+__device__ __forceinline__ R cst(double c) {
+  return (R)c;
+}
+template <>
+__device__ __forceinline__ dd cst<dd>(double c) {
+  return dd((float)c, (float)(c - (double)(float)c));
+}
 
 template <class R>
 struct ElemShared {
@@ -49,20 +103,17 @@ struct ElemShared {
 // Geometry of one tetrahedron in precision G: grad phi_a = J^-T grad_ref phi_a, the metric
 // tensor G = J^-T J^-1 (as its 9 entries), g = J^-T 1, |K| = det J / 6.
 template <class G>
-__device__ __forceinline__ void tet_geometry(const D4 *x, G gp[12], G Gm[9], G gv[3], G &vol) {
+__device__ __forceinline__ void tet_geometry(const G x[4][3], G gp[12], G Gm[9], G gv[3], G &vol) {
   G J[3][3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const D4 xc = x[c + 1];
-    J[0][c] = (G)(xc.x - x[0].x);
-    J[1][c] = (G)(xc.y - x[0].y);
-    J[2][c] = (G)(xc.z - x[0].z);
-  }
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) J[r][c] = x[c + 1][r] - x[0][r];
   G c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
   G c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
   G c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
   G det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-  G id = G(1) / det;
+  G id = cst<G>(1.0) / det;
   // inverse: Ji[r][c]
   G Ji[3][3];
   Ji[0][0] = c00 * id;
@@ -87,7 +138,7 @@ __device__ __forceinline__ void tet_geometry(const D4 *x, G gp[12], G Gm[9], G g
   for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int l = 0; l < 3; ++l) Gm[3 * k + l] = Ji[0][k] * Ji[0][l] + Ji[1][k] * Ji[1][l] + Ji[2][k] * Ji[2][l];
-  vol = det / G(6);
+  vol = det / cst<G>(6.0);
 }
 
 // Phase 1a (one thread per element): geometry in FP64 (FP64 assembly, or a badly shaped
@@ -95,10 +146,17 @@ __device__ __forceinline__ void tet_geometry(const D4 *x, G gp[12], G Gm[9], G g
 template <class R>
 __device__ void geom_phase(const AssembleArgs &A, int64_t e, int le, ElemShared<R> &sh) {
   const int4 cn = A.conn[e];
-  D4 x[4] = {A.xyz[cn.x], A.xyz[cn.y], A.xyz[cn.z], A.xyz[cn.w]};
-  const bool fp64_geom = (sizeof(R) == 8) || (A.bad && A.bad[e]);
+  const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
+  const bool fp64_geom = std::is_same<R, double>::value || (A.bad && A.bad[e]);
   if (fp64_geom) {
-    double gp[12], G[9], g[3], v;
+    double x[4][3], gp[12], G[9], g[3], v;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const D4 p = A.xyz[nd[a]];
+      x[a][0] = p.x;
+      x[a][1] = p.y;
+      x[a][2] = p.z;
+    }
     tet_geometry<double>(x, gp, G, g, v);
 #pragma unroll
     for (int k = 0; k < 12; ++k) sh.gphi[le][k] = (R)gp[k];
@@ -107,43 +165,52 @@ __device__ void geom_phase(const AssembleArgs &A, int64_t e, int le, ElemShared<
     sh.igg[le] = (R)(1.0 / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
     sh.w[le] = (R)(0.25 * v);
   } else {
-    float gp[12], G[9], g[3], v;
-    tet_geometry<float>(x, gp, G, g, v);
+    // geometry in the arithmetic type (FP32, or dd from the split coordinates)
+    R x[4][3], gp[12], G[9], g[3], v;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) sh.gphi[le][k] = (R)gp[k];
+    for (int a = 0; a < 4; ++a) {
+      R p[4];
+      ld_node<R>(A.xyz, A.xyz_hi, A.xyz_lo, nd[a], p);
+      x[a][0] = p[0];
+      x[a][1] = p[1];
+      x[a][2] = p[2];
+    }
+    tet_geometry<R>(x, gp, G, g, v);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) sh.Gm[le][k] = (R)G[k];
-    sh.igg[le] = (R)(1.0f / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
-    sh.w[le] = (R)(0.25f * v);
+    for (int k = 0; k < 12; ++k) sh.gphi[le][k] = gp[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sh.Gm[le][k] = G[k];
+    sh.igg[le] = cst<R>(1.0) / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    sh.w[le] = cst<R>(0.25) * v;
   }
 }
 
-// Phase 1b for one (element, quadrature point): u*, u^BDF, tau_M and tau_C (always FP64),
-// the resistive coefficient, and the LES vector tau_M r_M(u^EXT, p^EXT).
+// Phase 1b for one (element, quadrature point): u*, u^BDF, tau_M and tau_C (FP64 for the FP64
+// and FP32 kernels, dd for the dd kernel), the resistive coefficient (FP64), and the LES vector
+// tau_M r_M(u^EXT, p^EXT).
 template <class R>
-__device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, int q, int le,
-                         ElemShared<R> &sh) {
+__device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q, int64_t e, int q,
+                         int le, ElemShared<R> &sh) {
   const int4 cn = A.conn[e];
   const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
-  D4 ue[4], ub[4];
+  R ue[4][4], ub[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    ue[a] = A.xext[nd[a]];
-    ub[a] = A.ubdf[nd[a]];
+    ld_node<R>(A.xext, A.xext_hi, A.xext_lo, nd[a], ue[a]);
+    ld_node<R>(A.ubdf, A.ubdf_hi, A.ubdf_lo, nd[a], ub[a]);
   }
   const R *gp = sh.gphi[le];
   // barycentric coordinates of point q: phi_a(x_q)
   R lam[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) lam[a] = (a == q) ? (R)kQA : (R)kQB;
+  for (int a = 0; a < 4; ++a) lam[a] = (a == q) ? cst<R>(kQA) : cst<R>(kQB);
   // u* = u^EXT(x_q) (semi-implicit, no ALE), u^BDF(x_q)
   R us[3], ubq[3];
-  us[0] = lam[0] * (R)ue[0].x + lam[1] * (R)ue[1].x + lam[2] * (R)ue[2].x + lam[3] * (R)ue[3].x;
-  us[1] = lam[0] * (R)ue[0].y + lam[1] * (R)ue[1].y + lam[2] * (R)ue[2].y + lam[3] * (R)ue[3].y;
-  us[2] = lam[0] * (R)ue[0].z + lam[1] * (R)ue[1].z + lam[2] * (R)ue[2].z + lam[3] * (R)ue[3].z;
-  ubq[0] = lam[0] * (R)ub[0].x + lam[1] * (R)ub[1].x + lam[2] * (R)ub[2].x + lam[3] * (R)ub[3].x;
-  ubq[1] = lam[0] * (R)ub[0].y + lam[1] * (R)ub[1].y + lam[2] * (R)ub[2].y + lam[3] * (R)ub[3].y;
-  ubq[2] = lam[0] * (R)ub[0].z + lam[1] * (R)ub[1].z + lam[2] * (R)ub[2].z + lam[3] * (R)ub[3].z;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    us[i] = lam[0] * ue[0][i] + lam[1] * ue[1][i] + lam[2] * ue[2][i] + lam[3] * ue[3][i];
+    ubq[i] = lam[0] * ub[0][i] + lam[1] * ub[1][i] + lam[2] * ub[2][i] + lam[3] * ub[3][i];
+  }
   R adv[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) adv[a] = us[0] * gp[3 * a] + us[1] * gp[3 * a + 1] + us[2] * gp[3 * a + 2];
@@ -153,68 +220,85 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, 
     const double *ph = A.phi_riis + (int64_t)k * A.n_nodes;
     double phq = 0.0;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) phq += (double)lam[a] * ph[nd[a]];
+    for (int a = 0; a < 4; ++a) phq += ((a == q) ? kQA : kQB) * ph[nd[a]];
     // smoothed Dirac delta of Section 2.1.2: (1 + cos(pi phi/eps)) / (2 eps) inside |phi| <= eps
     const double dl = fabs(phq) > P.riis_eps[k] ? 0.0 : (1.0 + cos(P.riis_pi_eps[k] * phq)) * P.riis_inv2eps[k];
     const double c = P.riis_coef[k] * dl;
     sR += c;
     sR2 += c * c;
   }
-  // tau_M, tau_C in FP64 (Section 2.3)
+  const R sRr = P.n_riis > 0 ? (R)sR : cst<R>(0.0);
+  // tau_M, tau_C (Section 2.3)
   const R *Gm = sh.Gm[le];
-  double uGu = 0.0, GG = 0.0;
+  R taum, tauc;
+  if constexpr (std::is_same<R, dd>::value) {
+    R uGu = cst<R>(0.0), GG = cst<R>(0.0);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      const double Gkl = (double)Gm[3 * k + l];
-      uGu += (double)us[k] * Gkl * (double)us[l];
-      GG += Gkl * Gkl;
+      for (int l = 0; l < 3; ++l) {
+        uGu += us[k] * Gm[3 * k + l] * us[l];
+        GG += Gm[3 * k + l] * Gm[3 * k + l];
+      }
+    R tsum = Q.tau_t + Q.rho * Q.rho * uGu + Q.cr_mu2 * GG;
+    if (P.n_riis > 0) tsum += (R)sR2;
+    taum = dd_rsqrt(tsum);                        // tau_M = tsum^-1/2
+    tauc = tsum * taum * sh.igg[le];              // tau_C = 1/(tau_M g.g) = sqrt(tsum)/(g.g)
+  } else {
+    double uGu = 0.0, GG = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const double Gkl = (double)Gm[3 * k + l];
+        uGu += (double)us[k] * Gkl * (double)us[l];
+        GG += Gkl * Gkl;
+      }
     }
+    const double rho = P.rho;
+    const double tsum = P.tau_t + rho * rho * uGu + P.cr_mu2 * GG + sR2;
+    const double tm = rsqrt(tsum);
+    taum = (R)tm;
+    tauc = (R)(tsum * tm * (double)sh.igg[le]);
   }
-  const double rho = P.rho;
-  const double tsum = P.tau_t + rho * rho * uGu + P.cr_mu2 * GG + sR2;
-  const double taum = rsqrt(tsum);                       // tau_M = tsum^-1/2
-  const double tauc = tsum * taum * (double)sh.igg[le];  // tau_C = 1/(tau_M g.g) = sqrt(tsum)/(g.g)
-  R z[3] = {R(0), R(0), R(0)};
+  R z[3] = {cst<R>(0.0), cst<R>(0.0), cst<R>(0.0)};
   if (P.stab >= 2) {
     // tau_M r_M(u^EXT, p^EXT) with the strong residual of Section 2.3 (-mu Lap u = 0 for P1)
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      R conv = R(0), gpr = R(0);
+      R conv = cst<R>(0.0), gpr = cst<R>(0.0);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const R ua = (i == 0) ? (R)ue[a].x : ((i == 1) ? (R)ue[a].y : (R)ue[a].z);
-        conv += adv[a] * ua;
-        gpr += (R)ue[a].w * gp[3 * a + i];
+        conv += adv[a] * ue[a][i];
+        gpr += ue[a][3] * gp[3 * a + i];
       }
-      const R rm = (R)P.rho_dt * ((R)P.alpha * us[i] - ubq[i]) + (R)rho * conv + gpr + (R)sR * us[i] - (R)P.f[i];
-      z[i] = (R)rho * (R)taum * (us[i] - (R)taum * rm);
+      const R rm = Q.rho_dt * (Q.alpha * us[i] - ubq[i]) + Q.rho * conv + gpr + sRr * us[i] - Q.f[i];
+      z[i] = Q.rho * taum * (us[i] - taum * rm);
     }
   }
-  sh.cs[le][q] = (R)(P.rho_alpha_dt + sR);
-  sh.tm[le][q] = (R)taum;
-  sh.tc[le][q] = (R)tauc;
+  sh.cs[le][q] = Q.rho_alpha_dt + sRr;
+  sh.tm[le][q] = taum;
+  sh.tc[le][q] = tauc;
 #pragma unroll
   for (int a = 0; a < 4; ++a) sh.adv[le][q][a] = adv[a];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     sh.z[le][q][i] = z[i];
-    sh.m[le][q][i] = (R)P.rho_dt * ubq[i] + (R)P.f[i];
+    sh.m[le][q][i] = Q.rho_dt * ubq[i] + Q.f[i];
   }
 }
 
 // Phase 1c for one (element, node n): per-(qp, node) products and per-node sums over the
 // quadrature points, shared by the 16 blocks of the element.
 template <class R>
-__device__ void node_phase(const PhysParams &P, int n, int le, ElemShared<R> &sh) {
+__device__ void node_phase(const PhysParams &P, const PhysR<R> &Q, int n, int le, ElemShared<R> &sh) {
   const R w = sh.w[le];
-  const R rho = (R)P.rho;
+  const R rho = Q.rho;
   const R *gn = sh.gphi[le] + 3 * n;
-  R svp = R(0), ppv = R(0), wv0 = R(0), wv1 = R(0), wv2 = R(0);
+  R svp = cst<R>(0.0), ppv = svp, wv0 = svp, wv1 = svp, wv2 = svp;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const R pn = (n == q) ? (R)kQA : (R)kQB;
+    const R pn = (n == q) ? cst<R>(kQA) : cst<R>(kQB);
     const R an = sh.adv[le][q][n];
     const R tm = sh.tm[le][q];
     const R cbq = sh.cs[le][q] * pn + rho * an;
@@ -234,7 +318,7 @@ __device__ void node_phase(const PhysParams &P, int n, int le, ElemShared<R> &sh
   sh.Wv[le][n][1] = wv1;
   sh.Wv[le][n][2] = wv2;
   if (n == 0) {
-    R tmw = R(0), tcw = R(0), z0 = R(0), z1 = R(0), z2 = R(0);
+    R tmw = cst<R>(0.0), tcw = tmw, z0 = tmw, z1 = tmw, z2 = tmw;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       tmw += w * sh.tm[le][q];
@@ -281,15 +365,15 @@ template <> struct Vec16<float> {
 
 // Phase 2 for one (element, a, b): block (a, b) and right-hand-side entry 4a+b.
 template <class R, class S>
-__device__ void block_phase(const AssembleArgs &A, const PhysParams &P, int64_t e, int le, int a,
-                            int b, const ElemShared<R> &sh, S *vals) {
+__device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q, int64_t e, int le,
+                            int a, int b, const ElemShared<R> &sh, S *vals) {
   const R *ga = sh.gphi[le] + 3 * a;
   const R *gb = sh.gphi[le] + 3 * b;
   const R w = sh.w[le];
   const R gab = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
   // velocity-velocity scalar: sum_q E_q(a) cb_q(b) = mass/dt + resistive + Galerkin advection
   // + SUPG (Eq. fullydiscrete..., Eq. stabilization_form_SUPG)
-  R Mab = R(0), rhs = R(0);
+  R Mab = cst<R>(0.0), rhs = Mab;
   const int i_rhs = b;   // this thread also forms right-hand-side entry (a, i_rhs)
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -298,9 +382,9 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, int64_t 
     if (i_rhs < 3) rhs += sh.m[le][q][i_rhs] * Eqa + w * sh.z[le][q][i_rhs] * sh.mga[le][q][a];
     else if (P.stab >= 1) rhs += w * sh.tm[le][q] * sh.mga[le][q][a];
   }
-  const R vol = R(4) * w;
-  const R mu = (R)P.mu;
-  const R TC = (P.stab >= 1) ? sh.TC[le] : R(0);
+  const R vol = cst<R>(4.0) * w;
+  const R mu = Q.mu;
+  const R TC = (P.stab >= 1) ? sh.TC[le] : cst<R>(0.0);
   const R *Wv = sh.Wv[le][b];
   R blk[16];
 #pragma unroll
@@ -329,20 +413,38 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, int64_t 
       blk[4 * i + 3] = -w * ga[i];
       blk[12 + i] = w * gb[i];
     }
-    blk[15] = R(0);
+    blk[15] = cst<R>(0.0);
   }
-  S out[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) out[k] = (S)blk[k];
   const int32_t s = A.slot[e * 16 + 4 * a + b];
-  Vec16<S>::add(vals + (int64_t)s * 16, out);
   const int4 cn = A.conn[e];
   const int na = (a == 0) ? cn.x : ((a == 1) ? cn.y : ((a == 2) ? cn.z : cn.w));
-  A.rhs[4 * (int64_t)na + i_rhs] += (double)rhs;
+  const int64_t ir = 4 * (int64_t)na + i_rhs;
+  if constexpr (std::is_same<R, dd>::value) {
+    // dd accumulation into the high (vals) and low parts
+    float4 *ph = reinterpret_cast<float4 *>(vals + (int64_t)s * 16);
+    float4 *pl = reinterpret_cast<float4 *>(A.vals_lo + (int64_t)s * 16);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float4 h = ph[k], l = pl[k];
+      const dd v0 = dd(h.x, l.x) + blk[4 * k], v1 = dd(h.y, l.y) + blk[4 * k + 1];
+      const dd v2 = dd(h.z, l.z) + blk[4 * k + 2], v3 = dd(h.w, l.w) + blk[4 * k + 3];
+      ph[k] = make_float4(v0.hi, v1.hi, v2.hi, v3.hi);
+      pl[k] = make_float4(v0.lo, v1.lo, v2.lo, v3.lo);
+    }
+    const dd r = dd(A.rhs_hi[ir], A.rhs_lo[ir]) + rhs;
+    A.rhs_hi[ir] = r.hi;
+    A.rhs_lo[ir] = r.lo;
+  } else {
+    S out[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) out[k] = (S)blk[k];
+    Vec16<S>::add(vals + (int64_t)s * 16, out);
+    A.rhs[ir] += (double)rhs;
+  }
 }
 
 template <class R, class S>
-__global__ void __launch_bounds__(kCta) assemble_color_kernel(AssembleArgs A, PhysParams P,
+__global__ void __launch_bounds__(kCta) assemble_color_kernel(AssembleArgs A, PhysParams P, PhysR<R> Q,
                                                               int64_t e0, int64_t e1, S *vals) {
   __shared__ ElemShared<R> sh;
   const int t = threadIdx.x;
@@ -351,23 +453,30 @@ __global__ void __launch_bounds__(kCta) assemble_color_kernel(AssembleArgs A, Ph
     __syncthreads();
     const int le = t >> 2, q = t & 3;
     const bool live = base + le < e1;
-    if (live) qp_phase<R>(A, P, base + le, q, le, sh);
+    if (live) qp_phase<R>(A, P, Q, base + le, q, le, sh);
     __syncthreads();
-    if (live) node_phase<R>(P, q, le, sh);
+    if (live) node_phase<R>(P, Q, q, le, sh);
     __syncthreads();
 #pragma unroll 1
     for (int pass = 0; pass < kElems * 16 / kCta; ++pass) {
       const int le2 = pass * (kCta / 16) + (t >> 4);
       const int64_t e = base + le2;
-      if (e < e1) block_phase<R, S>(A, P, e, le2, (t >> 2) & 3, t & 3, sh, vals);
+      if (e < e1) block_phase<R, S>(A, P, Q, e, le2, (t >> 2) & 3, t & 3, sh, vals);
     }
     __syncthreads();
   }
 }
 
+__device__ __forceinline__ void split4(const D4 &v, float4 &hi, float4 &lo) {
+  const dd a(v.x), b(v.y), c(v.z), d(v.w);
+  hi = make_float4(a.hi, b.hi, c.hi, d.hi);
+  lo = make_float4(a.lo, b.lo, c.lo, d.lo);
+}
+
 __global__ void bdf_kernel(int64_t V, int order, const D4 *h0, const D4 *h1,
                            const D4 *h2, double b0, double b1, double b2, double g0, double g1,
-                           double g2, D4 *xext, D4 *ubdf) {
+                           double g2, D4 *xext, D4 *ubdf, float4 *xe_hi, float4 *xe_lo,
+                           float4 *ub_hi, float4 *ub_lo) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
     D4 a = h0[i];
     D4 e = D4{g0 * a.x, g0 * a.y, g0 * a.z, g0 * a.w};
@@ -384,6 +493,81 @@ __global__ void bdf_kernel(int64_t V, int order, const D4 *h0, const D4 *h1,
     }
     xext[i] = e;
     ubdf[i] = u;
+    if (xe_hi) {
+      split4(e, xe_hi[i], xe_lo[i]);
+      split4(u, ub_hi[i], ub_lo[i]);
+    }
+  }
+}
+
+__global__ void dd_combine_kernel(int64_t n, const float *hi, const float *lo, double *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)hi[i] + (double)lo[i];
+}
+
+// apply_dirichlet_kernel on a double-float matrix: the diagonal scale s = |A_rr| is taken from
+// hi + lo in FP64 and stored split
+__global__ void apply_dirichlet_dd_kernel(int64_t nd, const int32_t *dnode, const D4 *g, int32_t pin_node,
+                                          double pin_value, const int32_t *rowptr, const int32_t *diag,
+                                          float *hi, float *lo, double *rhs, double *x0) {
+  const int64_t total = 3 * nd + (pin_node >= 0 ? 1 : 0);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    int node, c;
+    double gv;
+    if (k < 3 * nd) {
+      const int64_t d = k / 3;
+      c = (int)(k - 3 * d);
+      node = dnode[d];
+      const D4 gg = g[d];
+      gv = (c == 0) ? gg.x : ((c == 1) ? gg.y : gg.z);
+    } else {
+      node = pin_node;
+      c = 3;
+      gv = pin_value;
+    }
+    const int64_t di = (int64_t)diag[node] * 16 + 5 * c;
+    double s = fabs((double)hi[di] + (double)lo[di]);
+    if (s == 0.0) s = 1.0;
+    for (int32_t kb = rowptr[node]; kb < rowptr[node + 1]; ++kb) {
+      const int64_t o = (int64_t)kb * 16 + 4 * c;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        hi[o + j] = 0.0f;
+        lo[o + j] = 0.0f;
+      }
+    }
+    const dd sd(s);
+    hi[di] = sd.hi;
+    lo[di] = sd.lo;
+    rhs[4 * (int64_t)node + c] = s * gv;
+    x0[4 * (int64_t)node + c] = gv;
+  }
+}
+
+// comp_scale_kernel on a double-float matrix (products in dd)
+__global__ void comp_scale_dd_kernel(int64_t V, int n_comp, const int32_t *comp_off, const double *scale,
+                                     const int32_t *rowptr, float *hi, float *lo, double *rhs) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 4 * V; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = k >> 2;
+    const int i = (int)(k & 3);
+    int lo_c = 0, hi_c = n_comp - 1;
+    while (lo_c < hi_c) {
+      const int mid = (lo_c + hi_c + 1) / 2;
+      if (comp_off[mid] <= r) lo_c = mid;
+      else hi_c = mid - 1;
+    }
+    const double sc = scale[lo_c];
+    const dd scd(sc);
+    for (int32_t kb = rowptr[r]; kb < rowptr[r + 1]; ++kb) {
+      const int64_t o = (int64_t)kb * 16 + 4 * i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const dd v = dd(hi[o + j], lo[o + j]) * scd;
+        hi[o + j] = v.hi;
+        lo[o + j] = v.lo;
+      }
+    }
+    rhs[k] *= sc;
   }
 }
 
@@ -507,10 +691,40 @@ inline int grid_for(int64_t n, int threads) {
 
 lfx_status launch_bdf(cudaStream_t st, int64_t V, int order, const D4 *h0, const D4 *h1,
                       const D4 *h2, const double beta[3], const double gamma[3],
-                      D4 *xext, D4 *ubdf) {
+                      D4 *xext, D4 *ubdf, float4 *xe_hi, float4 *xe_lo, float4 *ub_hi, float4 *ub_lo) {
   note_launches(1);
   bdf_kernel<<<grid_for(V, 256), 256, 0, st>>>(V, order, h0, h1, h2, beta[0], beta[1], beta[2],
-                                               gamma[0], gamma[1], gamma[2], xext, ubdf);
+                                               gamma[0], gamma[1], gamma[2], xext, ubdf, xe_hi, xe_lo,
+                                               ub_hi, ub_lo);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+lfx_status launch_dd_combine(cudaStream_t st, int64_t n, const float *hi, const float *lo, double *out) {
+  if (n == 0) return LFX_OK;
+  note_launches(1);
+  dd_combine_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, hi, lo, out);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+lfx_status launch_apply_dirichlet_dd(cudaStream_t st, int64_t nd, const int32_t *dnode, const D4 *g,
+                                     int32_t pin_node, double pin_value, const int32_t *rowptr,
+                                     const int32_t *diag, float *hi, float *lo, double *rhs, double *x0) {
+  const int64_t total = 3 * nd + (pin_node >= 0 ? 1 : 0);
+  if (total == 0) return LFX_OK;
+  note_launches(1);
+  apply_dirichlet_dd_kernel<<<grid_for(total, 128), 128, 0, st>>>(nd, dnode, g, pin_node, pin_value, rowptr, diag,
+                                                                   hi, lo, rhs, x0);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+lfx_status launch_comp_normalize_dd(cudaStream_t st, int64_t V, int n_comp, const int32_t *comp_off,
+                                    double *scale, const int32_t *rowptr, float *hi, float *lo, double *rhs) {
+  comp_norm_kernel<<<n_comp, 256, 0, st>>>(comp_off, rhs, scale);
+  comp_scale_dd_kernel<<<grid_for(4 * V, 256), 256, 0, st>>>(V, n_comp, comp_off, scale, rowptr, hi, lo, rhs);
+  note_launches(2);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
 }
@@ -518,12 +732,13 @@ lfx_status launch_bdf(cudaStream_t st, int64_t V, int order, const D4 *h0, const
 template <class R, class S>
 lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysParams &P,
                            const int32_t *color_off, int n_colors, S *vals) {
+  const PhysR<R> Q = phys_r<R>(P);
   for (int c = 0; c < n_colors; ++c) {
     const int64_t e0 = color_off[c], e1 = color_off[c + 1];
     if (e1 <= e0) continue;
     int64_t chunks = (e1 - e0 + kElems - 1) / kElems;
     int grid = (int)(chunks < 152 * 8 ? chunks : 152 * 8);
-    assemble_color_kernel<R, S><<<grid, kCta, 0, st>>>(A, P, e0, e1, vals);
+    assemble_color_kernel<R, S><<<grid, kCta, 0, st>>>(A, P, Q, e0, e1, vals);
     note_launches(1);
   }
   LFX_CUDA_TRY(cudaGetLastError());
@@ -534,6 +749,8 @@ template lfx_status launch_assemble<double, double>(cudaStream_t, const Assemble
                                                     const int32_t *, int, double *);
 template lfx_status launch_assemble<float, float>(cudaStream_t, const AssembleArgs &, const PhysParams &,
                                                   const int32_t *, int, float *);
+template lfx_status launch_assemble<dd, float>(cudaStream_t, const AssembleArgs &, const PhysParams &,
+                                               const int32_t *, int, float *);
 
 lfx_status launch_dirichlet_values(cudaStream_t st, int64_t nd, int H, const int32_t *bc_of,
                                    const double *S, const DirCoef &C, const double *N, int nb, D4 *g) {

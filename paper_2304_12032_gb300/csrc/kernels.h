@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dd.h"
 #include "lfx_internal.h"
 
 namespace lfx {
@@ -27,6 +28,13 @@ struct AssembleArgs {
   const uint8_t *bad;        // [T] FP64 geometry flag (mixed assembly), may be null
   double *rhs;               // [V][4]
   int64_t n_nodes;
+  // double-float assembly only: inputs split into FP32 high and low parts (x = hi + lo), the
+  // matrix accumulated as high parts (the vals argument) plus low parts, the rhs likewise
+  const float4 *xyz_hi, *xyz_lo;
+  const float4 *xext_hi, *xext_lo;
+  const float4 *ubdf_hi, *ubdf_lo;
+  float *vals_lo;            // [nnzb][16]
+  float *rhs_hi, *rhs_lo;    // [V][4]
 };
 
 constexpr int kMaxDirCoef = 256;
@@ -34,9 +42,20 @@ struct DirCoef {
   double c[kMaxDirCoef];
 };
 
+// u^EXT / p^EXT and u^BDF at every node (Eq. bdf); when xe_hi is non-null also their
+// double-float splits (hi + lo) for the double-float assembly.
 lfx_status launch_bdf(cudaStream_t st, int64_t V, int order, const D4 *h0, const D4 *h1,
                       const D4 *h2, const double beta[3], const double gamma[3],
-                      D4 *xext, D4 *ubdf);
+                      D4 *xext, D4 *ubdf, float4 *xe_hi = nullptr, float4 *xe_lo = nullptr,
+                      float4 *ub_hi = nullptr, float4 *ub_lo = nullptr);
+// rhs[i] = hi[i] + lo[i] (double-float right-hand side to FP64)
+lfx_status launch_dd_combine(cudaStream_t st, int64_t n, const float *hi, const float *lo, double *out);
+// Dirichlet row replacement and per-component row scaling on a double-float matrix (hi, lo)
+lfx_status launch_apply_dirichlet_dd(cudaStream_t st, int64_t nd, const int32_t *dnode, const D4 *g,
+                                     int32_t pin_node, double pin_value, const int32_t *rowptr,
+                                     const int32_t *diag, float *hi, float *lo, double *rhs, double *x0);
+lfx_status launch_comp_normalize_dd(cudaStream_t st, int64_t V, int n_comp, const int32_t *comp_off,
+                                    double *scale, const int32_t *rowptr, float *hi, float *lo, double *rhs);
 template <class R, class S>
 lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysParams &P,
                            const int32_t *color_off, int n_colors, S *vals);
@@ -65,10 +84,25 @@ struct BsrView {
   const S *vals;             // [nnzb][16]
 };
 
+// A double-float matrix: every value is hi + lo with FP32 parts (the FP32 matrix of the inner
+// solve is its high part).  Products with FP64 vectors first split the operand into FP32 high
+// and low parts in the scratch arrays xs_hi, xs_lo.
+struct DDMat {};
+template <>
+struct BsrView<DDMat> {
+  int64_t V;
+  const int32_t *rowptr, *col, *diag, *trans;
+  const float *hi, *lo;      // [nnzb][16]
+  float4 *xs_hi, *xs_lo;     // [V] operand scratch
+};
+
 // y = A x  (mode 0)  or  y = b - A x  (mode 1); vectors [V][4] of type T.  Optionally writes
 // per-CTA partial sums of y.y into part (deterministic two-stage norm).
 template <class S, class T>
 lfx_status launch_spmv(cudaStream_t st, const BsrView<S> &A, const T *x, const T *b, T *y,
                        int mode, double *part, int *n_part);
+template <>
+lfx_status launch_spmv<DDMat, double>(cudaStream_t st, const BsrView<DDMat> &A, const double *x, const double *b,
+                                      double *y, int mode, double *part, int *n_part);
 
 }  // namespace lfx

@@ -112,6 +112,7 @@ struct Mesh {
   std::vector<int32_t> comp_off;     // [n_comp+1] contiguous internal node range per component
   // device copies
   DBuf d_xyz;       // double4 [V] (x, y, z, 0)
+  DBuf d_xyz_hi, d_xyz_lo;   // float4 [V]: d_xyz split into FP32 high and low parts
   DBuf d_conn;      // int4 [T]
   DBuf d_slot;      // int32 [T][16]
   DBuf d_rowptr;    // int32 [V+1]

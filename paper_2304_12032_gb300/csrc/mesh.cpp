@@ -48,7 +48,7 @@ double signed_det(const double *x0, const double *x1, const double *x2, const do
 }  // namespace
 
 size_t Mesh::device_bytes() const {
-  return d_xyz.bytes + d_conn.bytes + d_slot.bytes + d_rowptr.bytes + d_col.bytes + d_diag.bytes +
+  return d_xyz.bytes + d_xyz_hi.bytes + d_xyz_lo.bytes + d_conn.bytes + d_slot.bytes + d_rowptr.bytes + d_col.bytes + d_diag.bytes +
          d_trans.bytes + d_comp_off.bytes;
 }
 
@@ -314,6 +314,16 @@ lfx_status upload_mesh(Mesh &m) {
   LFX_TRY(m.d_trans.alloc(sizeof(int32_t) * m.nnzb));
   LFX_TRY(m.d_comp_off.alloc(sizeof(int32_t) * m.comp_off.size()));
   LFX_CUDA_TRY(cudaMemcpy(m.d_xyz.p, x4.data(), m.d_xyz.bytes, cudaMemcpyHostToDevice));
+  // FP32 high and low parts of the coordinates (x = hi + lo to 48 bits) for double-float assembly
+  std::vector<float> xh(4 * V), xl(4 * V);
+  for (int64_t i = 0; i < 4 * V; ++i) {
+    xh[i] = (float)x4[i];
+    xl[i] = (float)(x4[i] - (double)xh[i]);
+  }
+  LFX_TRY(m.d_xyz_hi.alloc(sizeof(float) * 4 * V));
+  LFX_TRY(m.d_xyz_lo.alloc(sizeof(float) * 4 * V));
+  LFX_CUDA_TRY(cudaMemcpy(m.d_xyz_hi.p, xh.data(), m.d_xyz_hi.bytes, cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemcpy(m.d_xyz_lo.p, xl.data(), m.d_xyz_lo.bytes, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_conn.p, m.tets.data(), sizeof(int32_t) * 4 * T, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_slot.p, m.slot.data(), sizeof(int32_t) * 16 * T, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_rowptr.p, m.row_ptr.data(), sizeof(int32_t) * (V + 1), cudaMemcpyHostToDevice));

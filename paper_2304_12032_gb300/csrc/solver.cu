@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "amg.h"
+#include "dd.h"
 #include "kernels.h"
 #include "solver.h"
 
@@ -204,6 +205,80 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(BsrView<S> A, const T *_
   }
 }
 
+// ---- double-float operator with FP64 vectors.  The operand is split into FP32 high and low
+// parts first; every block row then accumulates compensated (Ogita, Rump and Oishi's Dot2:
+// products made exact by two_prod, sums by two_sum, the rounding errors gathered in an FP32
+// correction), so the product carries about 48 significant bits while running on the FP32 pipes.
+__global__ void split_vec_kernel(int64_t V, const double *x, float4 *hi, float4 *lo, const KState *st) {
+  if (finished(st)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+    const D4 v = reinterpret_cast<const D4 *>(x)[i];
+    const dd a(v.x), b(v.y), c(v.z), d(v.w);
+    hi[i] = make_float4(a.hi, b.hi, c.hi, d.hi);
+    lo[i] = make_float4(a.lo, b.lo, c.lo, d.lo);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) spmv_dd_kernel(BsrView<DDMat> A, const double *__restrict__ b,
+                                                           double *__restrict__ y, int mode, double *part,
+                                                           const KState *st) {
+  if (finished(st)) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
+  const int lane = threadIdx.x % kRowGroup;
+  float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+  if (row < A.V) {
+    const int32_t k1 = A.rowptr[row + 1];
+#pragma unroll 2
+    for (int32_t k = A.rowptr[row] + lane; k < k1; k += kRowGroup) {
+      float h[16], l[16];
+      ld_block<float, float>(A.hi, k, h);
+      ld_block<float, float>(A.lo, k, l);
+      const int32_t col = __ldg(A.col + k);
+      const float4 xh4 = A.xs_hi[col], xl4 = A.xs_lo[col];
+      const float xh[4] = {xh4.x, xh4.y, xh4.z, xh4.w}, xl[4] = {xl4.x, xl4.y, xl4.z, xl4.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const dd p = two_prod(h[4 * i + j], xh[j]);
+          float e = f_fma(h[4 * i + j], xl[j], p.lo);
+          e = f_fma(l[4 * i + j], xh[j], e);
+          const dd t = two_sum(s[i], p.hi);
+          s[i] = t.hi;
+          c[i] = f_add(c[i], f_add(t.lo, e));
+        }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int o = kRowGroup / 2; o > 0; o >>= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, s[i], o), oc = __shfl_xor_sync(0xffffffffu, c[i], o);
+      const dd t = two_sum(s[i], os);
+      s[i] = t.hi;
+      c[i] = f_add(c[i], f_add(oc, t.lo));
+    }
+  double nrm = 0.0;
+  if (row < A.V && lane == 0) {
+    D4 o;
+    double r[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r[i] = (double)s[i] + (double)c[i];
+    if (mode == 1) {
+      const D4 bv = reinterpret_cast<const D4 *>(b)[row];
+      o = D4{bv.x - r[0], bv.y - r[1], bv.z - r[2], bv.w - r[3]};
+    } else {
+      o = D4{r[0], r[1], r[2], r[3]};
+    }
+    reinterpret_cast<D4 *>(y)[row] = o;
+    nrm = o.x * o.x + o.y * o.y + o.z * o.z + o.w * o.w;
+  }
+  if (part) {
+    double sum = cta_sum(nrm);
+    if (threadIdx.x == 0) part[blockIdx.x] = sum;
+  }
+}
+
 // sum of part[0..n) -> *out (sqrt if root == 1, max instead of sum if root == 2); one CTA
 __global__ void reduce_kernel(const double *part, int n, double *out, int root) {
   double s = 0.0;
@@ -308,12 +383,12 @@ __device__ __forceinline__ void ld_DC(const SplitView<S> &A, int64_t k, T dc[4])
   ld_rec<4>(A.DC + 4 * k, dc);
 }
 
-// Blocks stored apart (in the preconditioner's storage type S) from the FP64 4x4 blocks.
-template <class S>
-__global__ void split_kernel(int64_t nnzb, const double *__restrict__ vals, S *F, S *G, S *DC) {
+// Blocks stored apart (in the preconditioner's storage type S) from the FP64 or FP32 4x4 blocks.
+template <class S, class Src>
+__global__ void split_kernel(int64_t nnzb, const Src *__restrict__ vals, S *F, S *G, S *DC) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnzb; k += (int64_t)gridDim.x * blockDim.x) {
-    double b[16];
-    ld_block<double, double>(vals, k, b);
+    Src b[16];
+    ld_block<Src, Src>(vals, k, b);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -1331,6 +1406,29 @@ template lfx_status launch_spmv<float, float>(cudaStream_t, const BsrView<float>
                                               const float *, float *, int, double *, int *);
 template lfx_status launch_spmv<float, double>(cudaStream_t, const BsrView<float> &, const double *,
                                                const double *, double *, int, double *, int *);
+template <>
+lfx_status launch_spmv<DDMat, double>(cudaStream_t st, const BsrView<DDMat> &A, const double *x, const double *b,
+                                      double *y, int mode, double *part, int *n_part) {
+  split_vec_kernel<<<vec_grid(A.V), kThreads, 0, st>>>(A.V, x, A.xs_hi, A.xs_lo, nullptr);
+  const int g = rows_grid(A.V);
+  spmv_dd_kernel<<<g, kThreads, 0, st>>>(A, b, y, mode, part, nullptr);
+  note_launches(2);
+  if (n_part) *n_part = g;
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+// The Arnoldi product w = A z_j (kernels return at once when the cycle has finished)
+template <class S, class T>
+static void arnoldi_spmv(cudaStream_t st, const BsrView<S> &A, const T *x, T *y, const KState *ks) {
+  spmv_kernel<S, T><<<rows_grid(A.V), kThreads, 0, st>>>(A, x, nullptr, y, 0, nullptr, ks);
+  note_launches(1);
+}
+static void arnoldi_spmv(cudaStream_t st, const BsrView<DDMat> &A, const double *x, double *y, const KState *ks) {
+  split_vec_kernel<<<vec_grid(A.V), kThreads, 0, st>>>(A.V, x, A.xs_hi, A.xs_lo, ks);
+  spmv_dd_kernel<<<rows_grid(A.V), kThreads, 0, st>>>(A, nullptr, y, 0, nullptr, ks);
+  note_launches(2);
+}
 
 template <class S, class T>
 lfx_status ASimple<S, T>::init(int64_t V_, const SmootherConfig &cfg_) {
@@ -1448,9 +1546,19 @@ lfx_status ASimple<S, T>::setup(cudaStream_t st, const BsrView<S> &A) {
   return setup_view(st, A);
 }
 
-// Sub-blocks stored apart in S, converted from the FP64 blocks; diagonals and bounds from them.
+// Sub-blocks stored apart in S, converted from the FP64 (or FP32) blocks; diagonals and bounds
+// from them.
 template <class S, class T>
 lfx_status ASimple<S, T>::setup_split(cudaStream_t st, const BsrView<double> &A64, int64_t nnzb) {
+  return setup_split_from(st, A64, nnzb);
+}
+template <class S, class T>
+lfx_status ASimple<S, T>::setup_split(cudaStream_t st, const BsrView<float> &A32, int64_t nnzb) {
+  return setup_split_from(st, A32, nnzb);
+}
+template <class S, class T>
+template <class Src>
+lfx_status ASimple<S, T>::setup_split_from(cudaStream_t st, const BsrView<Src> &A64, int64_t nnzb) {
   if (!sF.p || nnz_split != nnzb) {
     LFX_TRY(sF.alloc(sizeof(S) * 12 * (size_t)nnzb));
     LFX_TRY(sG.alloc(sizeof(S) * 4 * (size_t)nnzb));
@@ -1458,7 +1566,7 @@ lfx_status ASimple<S, T>::setup_split(cudaStream_t st, const BsrView<double> &A6
     nnz_split = nnzb;
   }
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nnzb + kThreads - 1) / kThreads, 152 * 16));
-  split_kernel<S><<<g, kThreads, 0, st>>>(nnzb, A64.vals, sF.as<S>(), sG.as<S>(), sDC.as<S>());
+  split_kernel<S, Src><<<g, kThreads, 0, st>>>(nnzb, A64.vals, sF.as<S>(), sG.as<S>(), sDC.as<S>());
   note_launches(1);
   split = true;
   const SplitView<S> sv{A64.V, A64.rowptr, A64.col, A64.diag, A64.trans, sF.as<S>(), sG.as<S>(), sDC.as<S>()};
@@ -1855,7 +1963,7 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
         }
       }
       LFX_CUDA_TRY(cudaEventRecord(tev[n_tev], st));
-      spmv_kernel<S, T><<<rows_grid(V), kThreads, 0, st>>>(A, zj, nullptr, w, 0, nullptr, ks);
+      arnoldi_spmv(st, A, zj, w, ks);
       LFX_CUDA_TRY(cudaEventRecord(tev[n_tev + 1], st));
       n_tev += 2;
       for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
@@ -1866,7 +1974,7 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
       }
       givens_kernel<<<1, kThreads, 0, st>>>(pn, vg, ks, j, restart, maxit);
       scale_kernel<T><<<vg, kThreads, 0, st>>>(w, vn, n, &ks->scale, ks);
-      note_launches(3 + 3 * (cgs2 ? 2 : 1));
+      note_launches(2 + 3 * (cgs2 ? 2 : 1));
       LFX_CUDA_TRY(cudaMemcpyAsync(pinned + (j & 3), &ks->done, sizeof(int), cudaMemcpyDeviceToHost, st));
       LFX_CUDA_TRY(cudaEventRecord(ev[j & 3], st));
       launched = j + 1;
@@ -1921,6 +2029,7 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
 
 template struct Gmres<double, double>;
 template struct Gmres<float, float>;
+template struct Gmres<DDMat, double>;
 
 template <class A, class B>
 lfx_status launch_convert(cudaStream_t st, const A *src, B *dst, int64_t n, const KState *ks) {

@@ -84,6 +84,7 @@ struct ASimple {
   // ... or on a copy of the FP64 blocks A64 converted to S with F, G and (D, C) stored apart, so
   // that each pass reads only the sub-block it needs (nnzb = number of blocks).
   lfx_status setup_split(cudaStream_t st, const BsrView<double> &A64, int64_t nnzb);
+  lfx_status setup_split(cudaStream_t st, const BsrView<float> &A32, int64_t nnzb);
   // z = P^-1 r; with a split set-up only A's pattern (rowptr, col, diag, trans) is used.
   lfx_status apply(cudaStream_t st, const BsrView<S> &A, const T *r, T *z, const KState *ks);
   lfx_status lambdas(double *lf, double *ls) const;
@@ -92,6 +93,8 @@ struct ASimple {
  private:
   template <class View>
   lfx_status setup_view(cudaStream_t st, const View &A);
+  template <class Src>
+  lfx_status setup_split_from(cudaStream_t st, const BsrView<Src> &A, int64_t nnzb);
   template <class View>
   lfx_status apply_view(cudaStream_t st, const View &A, const T *r, T *z, const KState *ks);
 };

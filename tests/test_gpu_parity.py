@@ -129,8 +129,9 @@ def test_step_matches_oracle(pair):
 @pytest.mark.parametrize("bf16", [False, True])
 @pytest.mark.parametrize("which", ["beltrami", "vessel_vms_riis", "bifurcation_supg_bdf3"])
 def test_mixed_step_matches_oracle(which, bf16):
-    # FP64 assembly and outer FGMRES, FP32 inner GMRES with an FP32 or BF16-storage aSIMPLE:
-    # the step must still match the FP64 oracle within 1e-6 relative L2.
+    # double-float assembly and outer FGMRES (FP64 vectors, double-float operator), FP32 inner
+    # GMRES with an FP32 or BF16-storage aSIMPLE: the step must still match the FP64 oracle
+    # within 1e-6 relative L2.
     case = CASES[which]()
     ost = C.oracle_step(case)
     _, _, st = C.gpu_state(case, precision="mixed", smoother_bf16=int(bf16), gmres_rtol=1e-10)
