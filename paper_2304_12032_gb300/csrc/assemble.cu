@@ -81,6 +81,16 @@ __device__ __forceinline__ dd cst<dd>(double c) {
   return dd((float)c, (float)(c - (double)(float)c));
 }
 
+// a * b + c (one fused double-float operation for dd; contracted to an FMA otherwise)
+template <class R>
+__device__ __forceinline__ R fmadd(R a, R b, R c) {
+  return a * b + c;
+}
+template <>
+__device__ __forceinline__ dd fmadd<dd>(dd a, dd b, dd c) {
+  return fma_dd(a, b, c);
+}
+
 template <class R>
 struct ElemShared {
   R gphi[kElems][12];      // grad phi_a, a = 0..3
@@ -88,16 +98,18 @@ struct ElemShared {
   R Gm[kElems][9];         // metric tensor G = J^-T J^-1
   R igg[kElems];           // 1 / (g . g), g = J^-T 1
   R cs[kElems][4];         // rho alpha / dt + sum_k (R_k/eps_k) delta_k at each qp
-  R tm[kElems][4];         // tau_M
-  R tc[kElems][4];         // tau_C
+  R wtm[kElems][4];        // w tau_M
+  R wtmr[kElems][4];       // w tau_M rho
+  R wtc[kElems][4];        // w tau_C
   R adv[kElems][4][4];     // [q][a] = u*(x_q) . grad phi_a
-  R z[kElems][4][3];       // rho tau_M (u* - tau_M r_M^EXT) (VMS + LES), 0 without VMS-LES
+  R wz[kElems][4][3];      // w rho tau_M (u* - tau_M r_M^EXT) (VMS + LES), 0 without VMS-LES
   R m[kElems][4][3];       // rho u^BDF / dt + f
   // per (qp, node) and per element sums (phase 1c)
   R E[kElems][4][4];       // [q][a] = w (phi_a(q) + tau_M rho adv_q(a))  (test-function weight)
   R cb[kElems][4][4];      // [q][b] = cs_q phi_b(q) + rho adv_q(b)     (trial-function residual)
   R mga[kElems][4][4];     // [q][a] = m_q . grad phi_a
-  R Svp[kElems][4], Ppv[kElems][4], Wv[kElems][4][3], Zv[kElems][3], TM[kElems], TC[kElems];
+  R wg[kElems][4][3];      // w grad phi_a
+  R Svp[kElems][4], Ppv[kElems][4], Wv[kElems][4][3], Zv[kElems][3], TM[kElems], TC[kElems], muvol[kElems];
 };
 
 // Geometry of one tetrahedron in precision G: grad phi_a = J^-T grad_ref phi_a, the metric
@@ -208,12 +220,12 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR
   R us[3], ubq[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    us[i] = lam[0] * ue[0][i] + lam[1] * ue[1][i] + lam[2] * ue[2][i] + lam[3] * ue[3][i];
-    ubq[i] = lam[0] * ub[0][i] + lam[1] * ub[1][i] + lam[2] * ub[2][i] + lam[3] * ub[3][i];
+    us[i] = fmadd(lam[3], ue[3][i], fmadd(lam[2], ue[2][i], fmadd(lam[1], ue[1][i], lam[0] * ue[0][i])));
+    ubq[i] = fmadd(lam[3], ub[3][i], fmadd(lam[2], ub[2][i], fmadd(lam[1], ub[1][i], lam[0] * ub[0][i])));
   }
   R adv[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) adv[a] = us[0] * gp[3 * a] + us[1] * gp[3 * a + 1] + us[2] * gp[3 * a + 2];
+  for (int a = 0; a < 4; ++a) adv[a] = fmadd(us[2], gp[3 * a + 2], fmadd(us[1], gp[3 * a + 1], us[0] * gp[3 * a]));
   // resistive coefficient sum_k (R_k/eps_k) delta_k and sum_k (R_k/eps_k)^2 delta_k^2
   double sR = 0.0, sR2 = 0.0;
   for (int k = 0; k < P.n_riis; ++k) {
@@ -234,13 +246,16 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR
   if constexpr (std::is_same<R, dd>::value) {
     R uGu = cst<R>(0.0), GG = cst<R>(0.0);
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3; ++k) {
+      R Gu = cst<R>(0.0);
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
-        uGu += us[k] * Gm[3 * k + l] * us[l];
-        GG += Gm[3 * k + l] * Gm[3 * k + l];
+        Gu = fmadd(Gm[3 * k + l], us[l], Gu);
+        GG = fmadd(Gm[3 * k + l], Gm[3 * k + l], GG);
       }
-    R tsum = Q.tau_t + Q.rho * Q.rho * uGu + Q.cr_mu2 * GG;
+      uGu = fmadd(us[k], Gu, uGu);
+    }
+    R tsum = fmadd(Q.cr_mu2, GG, fmadd(Q.rho * Q.rho, uGu, Q.tau_t));
     if (P.n_riis > 0) tsum += (R)sR2;
     taum = dd_rsqrt(tsum);                        // tau_M = tsum^-1/2
     tauc = tsum * taum * sh.igg[le];              // tau_C = 1/(tau_M g.g) = sqrt(tsum)/(g.g)
@@ -269,22 +284,25 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR
       R conv = cst<R>(0.0), gpr = cst<R>(0.0);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        conv += adv[a] * ue[a][i];
-        gpr += ue[a][3] * gp[3 * a + i];
+        conv = fmadd(adv[a], ue[a][i], conv);
+        gpr = fmadd(ue[a][3], gp[3 * a + i], gpr);
       }
-      const R rm = Q.rho_dt * (Q.alpha * us[i] - ubq[i]) + Q.rho * conv + gpr + sRr * us[i] - Q.f[i];
+      const R rm = fmadd(sRr, us[i], fmadd(Q.rho, conv, fmadd(Q.rho_dt, fmadd(Q.alpha, us[i], -ubq[i]), gpr))) - Q.f[i];
       z[i] = Q.rho * taum * (us[i] - taum * rm);
     }
   }
+  const R w = sh.w[le];
+  const R wtm = w * taum;
   sh.cs[le][q] = Q.rho_alpha_dt + sRr;
-  sh.tm[le][q] = taum;
-  sh.tc[le][q] = tauc;
+  sh.wtm[le][q] = wtm;
+  sh.wtmr[le][q] = wtm * Q.rho;
+  sh.wtc[le][q] = w * tauc;
 #pragma unroll
   for (int a = 0; a < 4; ++a) sh.adv[le][q][a] = adv[a];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    sh.z[le][q][i] = z[i];
-    sh.m[le][q][i] = Q.rho_dt * ubq[i] + Q.f[i];
+    sh.wz[le][q][i] = w * z[i];
+    sh.m[le][q][i] = fmadd(Q.rho_dt, ubq[i], Q.f[i]);
   }
 }
 
@@ -295,43 +313,47 @@ __device__ void node_phase(const PhysParams &P, const PhysR<R> &Q, int n, int le
   const R w = sh.w[le];
   const R rho = Q.rho;
   const R *gn = sh.gphi[le] + 3 * n;
+  const R wA = w * cst<R>(kQA), wB = w * cst<R>(kQB);
   R svp = cst<R>(0.0), ppv = svp, wv0 = svp, wv1 = svp, wv2 = svp;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const R pn = (n == q) ? cst<R>(kQA) : cst<R>(kQB);
+    const R wpn = (n == q) ? wA : wB;
     const R an = sh.adv[le][q][n];
-    const R tm = sh.tm[le][q];
-    const R cbq = sh.cs[le][q] * pn + rho * an;
+    const R cbq = fmadd(rho, an, sh.cs[le][q] * pn);
     const R *mq = sh.m[le][q];
     sh.cb[le][q][n] = cbq;
-    sh.E[le][q][n] = (P.stab >= 1) ? w * (pn + tm * rho * an) : w * pn;
-    sh.mga[le][q][n] = mq[0] * gn[0] + mq[1] * gn[1] + mq[2] * gn[2];
-    svp += w * tm * rho * an;
-    ppv += w * tm * cbq;
-    wv0 += w * sh.z[le][q][0] * cbq;
-    wv1 += w * sh.z[le][q][1] * cbq;
-    wv2 += w * sh.z[le][q][2] * cbq;
+    sh.E[le][q][n] = (P.stab >= 1) ? fmadd(sh.wtmr[le][q], an, wpn) : wpn;
+    sh.mga[le][q][n] = fmadd(mq[2], gn[2], fmadd(mq[1], gn[1], mq[0] * gn[0]));
+    svp = fmadd(sh.wtmr[le][q], an, svp);
+    ppv = fmadd(sh.wtm[le][q], cbq, ppv);
+    wv0 = fmadd(sh.wz[le][q][0], cbq, wv0);
+    wv1 = fmadd(sh.wz[le][q][1], cbq, wv1);
+    wv2 = fmadd(sh.wz[le][q][2], cbq, wv2);
   }
   sh.Svp[le][n] = svp;
   sh.Ppv[le][n] = ppv;
   sh.Wv[le][n][0] = wv0;
   sh.Wv[le][n][1] = wv1;
   sh.Wv[le][n][2] = wv2;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sh.wg[le][n][k] = w * gn[k];
   if (n == 0) {
     R tmw = cst<R>(0.0), tcw = tmw, z0 = tmw, z1 = tmw, z2 = tmw;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      tmw += w * sh.tm[le][q];
-      tcw += w * sh.tc[le][q];
-      z0 += w * sh.z[le][q][0];
-      z1 += w * sh.z[le][q][1];
-      z2 += w * sh.z[le][q][2];
+      tmw += sh.wtm[le][q];
+      tcw += sh.wtc[le][q];
+      z0 += sh.wz[le][q][0];
+      z1 += sh.wz[le][q][1];
+      z2 += sh.wz[le][q][2];
     }
     sh.TM[le] = tmw;
     sh.TC[le] = tcw;
     sh.Zv[le][0] = z0;
     sh.Zv[le][1] = z1;
     sh.Zv[le][2] = z2;
+    sh.muvol[le] = Q.mu * (cst<R>(4.0) * w);
   }
 }
 
@@ -369,8 +391,7 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const Ph
                             int a, int b, const ElemShared<R> &sh, S *vals) {
   const R *ga = sh.gphi[le] + 3 * a;
   const R *gb = sh.gphi[le] + 3 * b;
-  const R w = sh.w[le];
-  const R gab = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
+  const R gab = fmadd(ga[2], gb[2], fmadd(ga[1], gb[1], ga[0] * gb[0]));
   // velocity-velocity scalar: sum_q E_q(a) cb_q(b) = mass/dt + resistive + Galerkin advection
   // + SUPG (Eq. fullydiscrete..., Eq. stabilization_form_SUPG)
   R Mab = cst<R>(0.0), rhs = Mab;
@@ -378,40 +399,41 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const Ph
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const R Eqa = sh.E[le][q][a];
-    Mab += Eqa * sh.cb[le][q][b];
-    if (i_rhs < 3) rhs += sh.m[le][q][i_rhs] * Eqa + w * sh.z[le][q][i_rhs] * sh.mga[le][q][a];
-    else if (P.stab >= 1) rhs += w * sh.tm[le][q] * sh.mga[le][q][a];
+    Mab = fmadd(Eqa, sh.cb[le][q][b], Mab);
+    if (i_rhs < 3) rhs = fmadd(sh.m[le][q][i_rhs], Eqa, fmadd(sh.wz[le][q][i_rhs], sh.mga[le][q][a], rhs));
+    else if (P.stab >= 1) rhs = fmadd(sh.wtm[le][q], sh.mga[le][q][a], rhs);
   }
-  const R vol = cst<R>(4.0) * w;
-  const R mu = Q.mu;
+  const R muvol = sh.muvol[le];
   const R TC = (P.stab >= 1) ? sh.TC[le] : cst<R>(0.0);
   const R *Wv = sh.Wv[le][b];
+  const R dg = fmadd(muvol, gab, Mab);                          // + grad-grad diffusion
   R blk[16];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const R tci = TC * ga[i];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      R v = tci * gb[j] + Wv[i] * ga[j];                          // tau_C div-div + VMS/LES
-      if (i == j) v += Mab + mu * vol * gab;                      // + grad-grad diffusion
-      if (P.diffusion != 0) v += mu * vol * ga[j] * gb[i];        // symmetric-gradient part
+      R v = fmadd(tci, gb[j], Wv[i] * ga[j]);                   // tau_C div-div + VMS/LES
+      if (i == j) v += dg;
+      if (P.diffusion != 0) v = fmadd(muvol * ga[j], gb[i], v); // symmetric-gradient part
       blk[4 * i + j] = v;
     }
   }
+  const R *wga = sh.wg[le][a], *wgb = sh.wg[le][b];
   if (P.stab >= 1) {
     const R svp = sh.Svp[le][a], ppv = sh.Ppv[le][b];
     const R *Zv = sh.Zv[le];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      blk[4 * i + 3] = -w * ga[i] + svp * gb[i] + Zv[i] * gab;   // -(p, div v) + SUPG + VMS/LES
-      blk[12 + i] = w * gb[i] + ppv * ga[i];                      // (div u, q) + PSPG
+      blk[4 * i + 3] = fmadd(Zv[i], gab, fmadd(svp, gb[i], -wga[i]));   // -(p, div v) + SUPG + VMS/LES
+      blk[12 + i] = fmadd(ppv, ga[i], wgb[i]);                         // (div u, q) + PSPG
     }
-    blk[15] = sh.TM[le] * gab;                                    // PSPG
+    blk[15] = sh.TM[le] * gab;                                          // PSPG
   } else {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      blk[4 * i + 3] = -w * ga[i];
-      blk[12 + i] = w * gb[i];
+      blk[4 * i + 3] = -wga[i];
+      blk[12 + i] = wgb[i];
     }
     blk[15] = cst<R>(0.0);
   }
@@ -443,8 +465,16 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const Ph
   }
 }
 
+// CTAs per SM the register allocation must allow (4 for the double-float kernel, whose issue
+// rate depends on having enough warps to hide its long dependent FP32 chains)
+template <class R> struct MinCtas { static constexpr int value = 1; };
+#ifndef LFX_ASM_DD_MIN_CTAS
+#define LFX_ASM_DD_MIN_CTAS 4
+#endif
+template <> struct MinCtas<dd> { static constexpr int value = LFX_ASM_DD_MIN_CTAS; };
+
 template <class R, class S>
-__global__ void __launch_bounds__(kCta) assemble_color_kernel(AssembleArgs A, PhysParams P, PhysR<R> Q,
+__global__ void __launch_bounds__(kCta, MinCtas<R>::value) assemble_color_kernel(AssembleArgs A, PhysParams P, PhysR<R> Q,
                                                               int64_t e0, int64_t e1, S *vals) {
   __shared__ ElemShared<R> sh;
   const int t = threadIdx.x;

@@ -30,6 +30,16 @@ constexpr int kThreads = 256;
 #define LFX_ROW_GROUP 4
 #endif
 constexpr int kRowGroup = LFX_ROW_GROUP;   // lanes per block row in the row kernels
+// blocks in flight per lane in the row kernels (full 4x4 blocks / sub-blocks)
+#ifndef LFX_U_FULL
+#define LFX_U_FULL 2
+#endif
+#ifndef LFX_U_F
+#define LFX_U_F 1
+#endif
+#ifndef LFX_U_GDC
+#define LFX_U_GDC 2
+#endif
 
 template <class T> struct Vec4T;
 template <> struct Vec4T<double> { using type = D4; };
@@ -49,6 +59,13 @@ __device__ __forceinline__ typename Vec4T<T>::type ld4(const T *p, int64_t i) {
 template <class T>
 __device__ __forceinline__ void st4(T *p, int64_t i, const typename Vec4T<T>::type &v) {
   reinterpret_cast<typename Vec4T<T>::type *>(p)[i] = v;
+}
+
+// Two packed BF16 values to FP32 (exact: a BF16 value is the top half of its FP32 value).  Bit
+// operations on the integer pipe; the conversion instruction would take FP64-pipe issue slots.
+__device__ __forceinline__ void bf16x2_to_f32(uint32_t w, float &lo, float &hi) {
+  lo = __uint_as_float(w << 16);
+  hi = __uint_as_float(w & 0xffff0000u);
 }
 
 template <class S, class A>
@@ -83,12 +100,7 @@ __device__ __forceinline__ void ld_block<__nv_bfloat16, float>(const __nv_bfloat
     uint4 v = __ldg(p + i);
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[q]);
-      float2 f = __bfloat1622float2(h);
-      b[8 * i + 2 * q] = f.x;
-      b[8 * i + 2 * q + 1] = f.y;
-    }
+    for (int q = 0; q < 4; ++q) bf16x2_to_f32(w[q], b[8 * i + 2 * q], b[8 * i + 2 * q + 1]);
   }
 }
 template <>
@@ -109,6 +121,28 @@ __device__ __forceinline__ A group_sum(A v) {
 #pragma unroll
   for (int o = kRowGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// The blocks k0 + lane, k0 + lane + G, ... (< k1) of one block row, U per lane at a time: for a
+// batch, load(u, k) issues the matrix and index loads of every valid slot, then gather(u) the
+// dependent vector loads, then use(u) consumes them, so that U blocks' loads of each lane are in
+// flight together instead of one dependent pair after another.
+template <int U, class Load, class Gather, class Use>
+__device__ __forceinline__ void row_blocks(int32_t k0, int32_t k1, int lane, Load load, Gather gather, Use use) {
+  for (int32_t kb = k0 + lane; kb < k1; kb += U * kRowGroup) {
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      ok[u] = kb + u * kRowGroup < k1;
+      if (ok[u]) load(u, kb + u * kRowGroup);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (ok[u]) gather(u);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (ok[u]) use(u);
+  }
 }
 
 // CTA-wide sum of one double per thread; result valid in thread 0.
@@ -174,16 +208,23 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(BsrView<S> A, const T *_
   const int lane = threadIdx.x % kRowGroup;
   T acc[4] = {T(0), T(0), T(0), T(0)};
   if (row < A.V) {
-    const int32_t k1 = A.rowptr[row + 1];
-#pragma unroll 4
-    for (int32_t k = A.rowptr[row] + lane; k < k1; k += kRowGroup) {
-      T blk[16];
-      ld_block<S, T>(A.vals, k, blk);
-      const auto xv = ld4(x, __ldg(A.col + k));
+    constexpr int U = LFX_U_FULL;
+    T blk[U][16];
+    int32_t c[U];
+    typename Vec4T<T>::type xv[U];
+    row_blocks<U>(
+        A.rowptr[row], A.rowptr[row + 1], lane,
+        [&](int u, int32_t k) {
+          ld_block<S, T>(A.vals, k, blk[u]);
+          c[u] = __ldg(A.col + k);
+        },
+        [&](int u) { xv[u] = ld4(x, c[u]); },
+        [&](int u) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        acc[i] += blk[4 * i] * xv.x + blk[4 * i + 1] * xv.y + blk[4 * i + 2] * xv.z + blk[4 * i + 3] * xv.w;
-    }
+          for (int i = 0; i < 4; ++i)
+            acc[i] += blk[u][4 * i] * xv[u].x + blk[u][4 * i + 1] * xv[u].y + blk[u][4 * i + 2] * xv[u].z +
+                      blk[u][4 * i + 3] * xv[u].w;
+        });
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc[i] = group_sum(acc[i]);
@@ -333,12 +374,8 @@ __device__ __forceinline__ void ld_rec(const __nv_bfloat16 *p, float *o) {
 #pragma unroll
   for (int i = 0; i < N / 4; ++i) {
     const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p) + i);
-    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
-    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
-    o[4 * i] = a.x;
-    o[4 * i + 1] = a.y;
-    o[4 * i + 2] = b.x;
-    o[4 * i + 3] = b.y;
+    bf16x2_to_f32(v.x, o[4 * i], o[4 * i + 1]);
+    bf16x2_to_f32(v.y, o[4 * i + 2], o[4 * i + 3]);
   }
 }
 
@@ -521,15 +558,21 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF
   const int lane = threadIdx.x % kRowGroup;
   T acc[3] = {T(0), T(0), T(0)};
   if (row < A.V) {
-    const int32_t kend = A.rowptr[row + 1];
-#pragma unroll 4
-    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      T f[9];
-      ld_F(A, kb, f);
-      const auto dv = ld4(d_old, __ldg(A.col + kb));
+    constexpr int U = LFX_U_F;
+    T f[U][9];
+    int32_t c[U];
+    typename Vec4T<T>::type dv[U];
+    row_blocks<U>(
+        A.rowptr[row], A.rowptr[row + 1], lane,
+        [&](int u, int32_t k) {
+          ld_F(A, k, f[u]);
+          c[u] = __ldg(A.col + k);
+        },
+        [&](int u) { dv[u] = ld4(d_old, c[u]); },
+        [&](int u) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) acc[i] += f[3 * i] * dv.x + f[3 * i + 1] * dv.y + f[3 * i + 2] * dv.z;
-    }
+          for (int i = 0; i < 3; ++i) acc[i] += f[u][3 * i] * dv[u].x + f[u][3 * i + 1] * dv[u].y + f[u][3 * i + 2] * dv[u].z;
+        });
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) acc[i] = group_sum(acc[i]);
@@ -570,16 +613,21 @@ __global__ void __launch_bounds__(kThreads) g_scaled_kernel(View A, const T *din
   const int lane = threadIdx.x % kRowGroup;
   T acc[3] = {T(0), T(0), T(0)};
   if (row < A.V) {
-    const int32_t kend = A.rowptr[row + 1];
-#pragma unroll 4
-    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      T g[4];
-      ld_G(A, kb, g);
-      const T p = ld4(in, __ldg(A.col + kb)).w;
-      acc[0] += g[0] * p;
-      acc[1] += g[1] * p;
-      acc[2] += g[2] * p;
-    }
+    constexpr int U = LFX_U_GDC;
+    T g[U][4], p[U];
+    int32_t c[U];
+    row_blocks<U>(
+        A.rowptr[row], A.rowptr[row + 1], lane,
+        [&](int u, int32_t k) {
+          ld_G(A, k, g[u]);
+          c[u] = __ldg(A.col + k);
+        },
+        [&](int u) { p[u] = in[4 * (int64_t)c[u] + 3]; },
+        [&](int u) {
+          acc[0] += g[u][0] * p[u];
+          acc[1] += g[u][1] * p[u];
+          acc[2] += g[u][2] * p[u];
+        });
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) acc[i] = group_sum(acc[i]);
@@ -603,16 +651,21 @@ __global__ void __launch_bounds__(kThreads) s_step_kernel(View A, const T *dinvS
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
   if (row < A.V) {
-    const int32_t kend = A.rowptr[row + 1];
-#pragma unroll 4
-    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      T dc[4];
-      ld_DC(A, kb, dc);
-      const int32_t c = __ldg(A.col + kb);
-      const T p = ld4(d_old, c).w;
-      const auto wv = ld4(w, c);
-      acc += dc[3] * p - (dc[0] * wv.x + dc[1] * wv.y + dc[2] * wv.z);
-    }
+    constexpr int U = LFX_U_GDC;
+    T dc[U][4], p[U];
+    int32_t c[U];
+    typename Vec4T<T>::type wv[U];
+    row_blocks<U>(
+        A.rowptr[row], A.rowptr[row + 1], lane,
+        [&](int u, int32_t k) {
+          ld_DC(A, k, dc[u]);
+          c[u] = __ldg(A.col + k);
+        },
+        [&](int u) {
+          p[u] = d_old[4 * (int64_t)c[u] + 3];
+          wv[u] = ld4(w, c[u]);
+        },
+        [&](int u) { acc += dc[u][3] * p[u] - (dc[u][0] * wv[u].x + dc[u][1] * wv[u].y + dc[u][2] * wv[u].z); });
   }
   acc = group_sum(acc);
   double nrm = 0.0;
@@ -674,14 +727,18 @@ __global__ void __launch_bounds__(kThreads) d_init_kernel(View A, const T *dinvS
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
   if (row < A.V) {
-    const int32_t kend = A.rowptr[row + 1];
-#pragma unroll 4
-    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      T dc[4];
-      ld_DC(A, kb, dc);
-      const auto xv = ld4(x, __ldg(A.col + kb));
-      acc += dc[0] * xv.x + dc[1] * xv.y + dc[2] * xv.z;
-    }
+    constexpr int U = LFX_U_GDC;
+    T dc[U][4];
+    int32_t c[U];
+    typename Vec4T<T>::type xv[U];
+    row_blocks<U>(
+        A.rowptr[row], A.rowptr[row + 1], lane,
+        [&](int u, int32_t k) {
+          ld_DC(A, k, dc[u]);
+          c[u] = __ldg(A.col + k);
+        },
+        [&](int u) { xv[u] = ld4(x, c[u]); },
+        [&](int u) { acc += dc[u][0] * xv[u].x + dc[u][1] * xv[u].y + dc[u][2] * xv[u].z; });
   }
   acc = group_sum(acc);
   if (row < A.V && lane == 0) {
@@ -710,16 +767,21 @@ __global__ void __launch_bounds__(kThreads) final_kernel(View A, const T *dinvF,
   const int lane = threadIdx.x % kRowGroup;
   T acc[3] = {T(0), T(0), T(0)};
   if (row < A.V) {
-    const int32_t kend = A.rowptr[row + 1];
-#pragma unroll 4
-    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      T g[4];
-      ld_G(A, kb, g);
-      const T p = ld4(x, __ldg(A.col + kb)).w;
-      acc[0] += g[0] * p;
-      acc[1] += g[1] * p;
-      acc[2] += g[2] * p;
-    }
+    constexpr int U = LFX_U_GDC;
+    T g[U][4], p[U];
+    int32_t c[U];
+    row_blocks<U>(
+        A.rowptr[row], A.rowptr[row + 1], lane,
+        [&](int u, int32_t k) {
+          ld_G(A, k, g[u]);
+          c[u] = __ldg(A.col + k);
+        },
+        [&](int u) { p[u] = x[4 * (int64_t)c[u] + 3]; },
+        [&](int u) {
+          acc[0] += g[u][0] * p[u];
+          acc[1] += g[u][1] * p[u];
+          acc[2] += g[u][2] * p[u];
+        });
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) acc[i] = group_sum(acc[i]);
@@ -749,16 +811,21 @@ __global__ void __launch_bounds__(kThreads) s_resid_kernel(View A, const T *dinv
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
   if (row < A.V) {
-    const int32_t kend = A.rowptr[row + 1];
-#pragma unroll 4
-    for (int32_t kb = A.rowptr[row] + lane; kb < kend; kb += kRowGroup) {
-      T dc[4];
-      ld_DC(A, kb, dc);
-      const int32_t c = __ldg(A.col + kb);
-      const T p = ld4(x, c).w;
-      const auto wv = ld4(w, c);
-      acc += dc[3] * p - (dc[0] * wv.x + dc[1] * wv.y + dc[2] * wv.z);
-    }
+    constexpr int U = LFX_U_GDC;
+    T dc[U][4], p[U];
+    int32_t c[U];
+    typename Vec4T<T>::type wv[U];
+    row_blocks<U>(
+        A.rowptr[row], A.rowptr[row + 1], lane,
+        [&](int u, int32_t k) {
+          ld_DC(A, k, dc[u]);
+          c[u] = __ldg(A.col + k);
+        },
+        [&](int u) {
+          p[u] = x[4 * (int64_t)c[u] + 3];
+          wv[u] = ld4(w, c[u]);
+        },
+        [&](int u) { acc += dc[u][3] * p[u] - (dc[u][0] * wv[u].x + dc[u][1] * wv[u].y + dc[u][2] * wv[u].z); });
   }
   acc = group_sum(acc);
   if (row < A.V && lane == 0) {
