@@ -27,8 +27,17 @@ sys.path.insert(0, ROOT)
 R_CM, L_CM, U_PEAK, RHO, MU, DT = 1.0, 10.0, 20.0, 1.06, 0.035, 1e-3
 RAMP = 0.05                      # s, sinusoidal ramp of the inflow (Section 2.2.1)
 L2_BYTES = 129 * 2 ** 20
-FP64_PEAK_TFLOPS = 1.20            # measured FMA-throughput probe on this GB300
-ASM_FP64_FLOPS_PER_ELEMENT = 3100  # FP64 flops per tetrahedron of the assembly kernel
+FP64_PEAK_TFLOPS = 1.20            # measured FP64 FMA-throughput probe on this GB300
+FP32_ISSUE_PEAK_T = 35.96          # measured FP32 FMA-issue probe, T thread-instructions/s
+# FP64-class operations of the method per tetrahedron (DFMA x 2 + DADD + DMUL executed by the FP64
+# assembly kernel, counted with ncu): the algorithmic work of one element's assembly
+ASM_FP64_FLOPS_PER_ELEMENT = 3286
+# thread instructions per tetrahedron of the double-float assembly kernel (ncu) and its DRAM
+# bytes per tetrahedron (ncu, one colour launch of 30,832 elements; profiles/)
+ASM_DD_INST_PER_ELEMENT = 42845
+ASM_DD_DRAM_BYTES_PER_ELEMENT = 5297
+# DRAM bytes per block of the FP32 Krylov SpMV (ncu read + write, 2,089,595-block launch)
+SPMV32_DRAM_BYTES_PER_BLOCK = 71.6
 
 
 def _peaks():
@@ -203,21 +212,38 @@ def run_gpu(args):
     spmv_bw = spmv_bytes / (spmv_ms * 1e-3) / 1e9
     roof = {"kernel": f"spmv_kernel ({'FP32' if sv == 4 else 'FP64'} 4x4 block CSR, Arnoldi products)",
             "bound": "hbm", "achieved": round(spmv_bw, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(spmv_bw / peaks["hbm_gbs"], 4), "traffic": None, "peak_source": src + " (burst copy)",
+            "frac": round(spmv_bw / peaks["hbm_gbs"], 4),
+            "traffic": int(SPMV32_DRAM_BYTES_PER_BLOCK * nnzb) if sv == 4 else None, "peak_source": src + " (burst copy)",
             "ms_per_launch": round(spmv_ms, 4), "launches_timed": int(sum(s["n_spmv"] for s in stats)),
             "algorithmic_bytes_per_launch": int(spmv_bytes)}
     asm_ms = sum(s["ms_assembly_kernels"] for s in stats) / len(stats)
     n_asm = stats[0]["n_assembly_launches"]
     asm_bytes = 16 * T + V * (3 * 8 + 8 * 8) + nnzb * 16 * 8 + 4 * V * 8
     asm_flops = ASM_FP64_FLOPS_PER_ELEMENT * T
-    roof_asm = {"kernel": "assemble_color_kernel<double> (all colours of one step)", "bound": "alu",
-                "achieved": round(asm_flops / (asm_ms * 1e-3) / 1e12, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(asm_flops / (asm_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "measured FP64 FMA probe (DESIGN.md)",
-                "hbm_view": {"achieved_gbs": round(asm_bytes / (asm_ms * 1e-3) / 1e9, 1),
-                             "algorithmic_bytes": int(asm_bytes)},
-                "ms_per_step": round(asm_ms, 4), "launches_per_step": n_asm,
-                "fp64_flops_per_element": ASM_FP64_FLOPS_PER_ELEMENT}
+    if prim_prec == "mixed":
+        # double-float assembly: bounded by FP32 instruction issue (FMA pipe), not by HBM
+        inst_rate = ASM_DD_INST_PER_ELEMENT * T / (asm_ms * 1e-3) / 1e12
+        roof_asm = {"kernel": "assemble_color_kernel<dd> (double-float arithmetic on the FP32 pipes; all colours of one step)",
+                    "bound": "alu", "achieved": round(inst_rate, 3), "peak": FP32_ISSUE_PEAK_T,
+                    "unit": "T thread-inst/s", "frac": round(inst_rate / FP32_ISSUE_PEAK_T, 4),
+                    "traffic": int(ASM_DD_DRAM_BYTES_PER_ELEMENT * T / n_asm),
+                    "peak_source": "measured FP32 FMA-issue probe (DESIGN.md)",
+                    "inst_per_element": ASM_DD_INST_PER_ELEMENT,
+                    "fp64_class_tflops": round(asm_flops / (asm_ms * 1e-3) / 1e12, 4),
+                    "fp64_class_flops_per_element": ASM_FP64_FLOPS_PER_ELEMENT,
+                    "hbm_view": {"achieved_gbs": round(asm_bytes / (asm_ms * 1e-3) / 1e9, 1),
+                                 "algorithmic_bytes": int(asm_bytes)},
+                    "ms_per_step": round(asm_ms, 4), "ms_per_launch": round(asm_ms / n_asm, 4),
+                    "launches_per_step": n_asm}
+    else:
+        roof_asm = {"kernel": "assemble_color_kernel<double> (all colours of one step)", "bound": "alu",
+                    "achieved": round(asm_flops / (asm_ms * 1e-3) / 1e12, 4), "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": round(asm_flops / (asm_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
+                    "traffic": None, "peak_source": "measured FP64 FMA probe (DESIGN.md)",
+                    "hbm_view": {"achieved_gbs": round(asm_bytes / (asm_ms * 1e-3) / 1e9, 1),
+                                 "algorithmic_bytes": int(asm_bytes)},
+                    "ms_per_step": round(asm_ms, 4), "ms_per_launch": round(asm_ms / n_asm, 4),
+                    "launches_per_step": n_asm, "fp64_flops_per_element": ASM_FP64_FLOPS_PER_ELEMENT}
     its = [s["iterations"] for s in stats]
     ms = prim["ms"]
     value = world * args.steps / (ms * 1e-3)
@@ -237,8 +263,10 @@ def run_gpu(args):
         "elements_per_s_assembly": round(T / (asm_ms * 1e-3), 1),
         "phase_ms": {"assembly": round(statistics.mean(s["ms_assembly"] for s in stats), 3),
                      "solve": round(statistics.mean(s["ms_solve"] for s in stats), 3)},
-        "roofline": roof,
-        "roofline_assembly": roof_asm,
+        # the dominant kernel of the step is the assembly (one launch per colour); the Krylov SpMV
+        # is the dominant HBM-bound kernel
+        "roofline": roof_asm,
+        "roofline_spmv": roof,
         "e2e": {"value": round(1e3 / e2e_ms * world, 3), "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(prim["launches"]),
