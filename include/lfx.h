@@ -180,7 +180,7 @@ typedef struct lfx_options {
                                    geometry in mixed assembly; default 0.1                       */
   /* Schur AMG (s_smoother == LFX_SMOOTH_AMG) */
   int32_t amg_refresh;          /* rebuild the hierarchy every this many steps (0 = build once) */
-  int32_t amg_coarse_size;      /* dense solve below this many unknowns; default 400           */
+  int32_t amg_coarse_size;      /* dense solve below this many unknowns; default 2000          */
   double amg_theta;             /* strength threshold on coarse levels; default 0.08           */
   double amg_alpha;             /* scaling of the coarse correction; default 1.0               */
   /* batching: a mesh made of several disconnected meshes is stepped as one system; with

@@ -32,7 +32,7 @@ struct AmgHost {
 
 CsrHost schur_explicit(int64_t V, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
                        const std::vector<int32_t> &diag, const double *vals);
-lfx_status amg_setup_host(const CsrHost &S0, const std::vector<int32_t> &node_rp,
+lfx_status amg_setup_host(CsrHost S0, const std::vector<int32_t> &node_rp,
                           const std::vector<int32_t> &node_ci, const AmgParams &prm, AmgHost &H);
 
 }  // namespace lfx

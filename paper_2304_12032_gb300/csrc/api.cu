@@ -318,7 +318,7 @@ void lfx_options_default(lfx_options *o) {
   o->inner_max_iters = 60;
   o->bad_element_quality = 0.1;
   o->amg_refresh = 0;
-  o->amg_coarse_size = 400;
+  o->amg_coarse_size = 2000;
   o->amg_theta = 0.08;
   o->amg_alpha = 1.0;
   o->batch_normalize = 1;
@@ -1026,7 +1026,7 @@ static lfx_status setup_asimple(lfx_state *s, ASimple<S, T> &pc) {
   prm.coarse_size = o.amg_coarse_size;
   prm.theta = o.amg_theta;
   AmgHost H;
-  LFX_TRY(amg_setup_host(S0, m.row_ptr, m.col_idx, prm, H));
+  LFX_TRY(amg_setup_host(std::move(S0), m.row_ptr, m.col_idx, prm, H));
   pc.amg_alpha = o.amg_alpha;
   LFX_TRY(pc.upload_amg(H));
   s->amg_age = 1;

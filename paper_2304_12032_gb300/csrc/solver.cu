@@ -1831,7 +1831,10 @@ lfx_status ASimple<S, T>::upload_amg(const AmgHost &H) {
     }
     LFX_TRY(coarse_args.alloc(sizeof(CoarseArgs<T>)));
     LFX_CUDA_TRY(cudaMemcpy(coarse_args.p, &h, sizeof(h), cudaMemcpyHostToDevice));
-    coop_grid = std::min(per_sm, 4) * nsm;
+#ifndef LFX_COOP_PER_SM
+#define LFX_COOP_PER_SM 4
+#endif
+    coop_grid = std::min(per_sm, LFX_COOP_PER_SM) * nsm;
   }
   if (!Bs.p) LFX_TRY(Bs.alloc(sizeof(T) * 4 * (size_t)V));
   if (!rr0.p) LFX_TRY(rr0.alloc(sizeof(T) * (size_t)V));
