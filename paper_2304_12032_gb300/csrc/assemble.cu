@@ -24,6 +24,7 @@
 #include "dd.h"
 #include "lfx_internal.h"
 #include "kernels.h"
+#include "pdl.h"
 
 namespace lfx {
 
@@ -476,6 +477,7 @@ template <> struct MinCtas<dd> { static constexpr int value = LFX_ASM_DD_MIN_CTA
 template <class R, class S>
 __global__ void __launch_bounds__(kCta, MinCtas<R>::value) assemble_color_kernel(AssembleArgs A, PhysParams P, PhysR<R> Q,
                                                               int64_t e0, int64_t e1, S *vals) {
+  pdl_entry();
   __shared__ ElemShared<R> sh;
   const int t = threadIdx.x;
   for (int64_t base = e0 + (int64_t)blockIdx.x * kElems; base < e1; base += (int64_t)gridDim.x * kElems) {
@@ -507,6 +509,7 @@ __global__ void bdf_kernel(int64_t V, int order, const D4 *h0, const D4 *h1,
                            const D4 *h2, double b0, double b1, double b2, double g0, double g1,
                            double g2, D4 *xext, D4 *ubdf, float4 *xe_hi, float4 *xe_lo,
                            float4 *ub_hi, float4 *ub_lo) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
     D4 a = h0[i];
     D4 e = D4{g0 * a.x, g0 * a.y, g0 * a.z, g0 * a.w};
@@ -531,6 +534,7 @@ __global__ void bdf_kernel(int64_t V, int order, const D4 *h0, const D4 *h1,
 }
 
 __global__ void dd_combine_kernel(int64_t n, const float *hi, const float *lo, double *out) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (double)hi[i] + (double)lo[i];
 }
@@ -540,6 +544,7 @@ __global__ void dd_combine_kernel(int64_t n, const float *hi, const float *lo, d
 __global__ void apply_dirichlet_dd_kernel(int64_t nd, const int32_t *dnode, const D4 *g, int32_t pin_node,
                                           double pin_value, const int32_t *rowptr, const int32_t *diag,
                                           float *hi, float *lo, double *rhs, double *x0) {
+  pdl_entry();
   const int64_t total = 3 * nd + (pin_node >= 0 ? 1 : 0);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     int node, c;
@@ -577,6 +582,7 @@ __global__ void apply_dirichlet_dd_kernel(int64_t nd, const int32_t *dnode, cons
 // comp_scale_kernel on a double-float matrix (products in dd)
 __global__ void comp_scale_dd_kernel(int64_t V, int n_comp, const int32_t *comp_off, const double *scale,
                                      const int32_t *rowptr, float *hi, float *lo, double *rhs) {
+  pdl_entry();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 4 * V; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = k >> 2;
     const int i = (int)(k & 3);
@@ -606,6 +612,7 @@ __global__ void comp_scale_dd_kernel(int64_t V, int n_comp, const int32_t *comp_
 __global__ void dirichlet_values_kernel(int64_t nd, int H, const int32_t *bc_of,
                                         const double *S /* [H][nd][3] */, DirCoef C,
                                         const double *N /* [nd][3] */, int nb, D4 *g) {
+  pdl_entry();
   for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < nd; d += (int64_t)gridDim.x * blockDim.x) {
     const int bc = bc_of[d];
     double v[3] = {0.0, 0.0, 0.0};
@@ -627,6 +634,7 @@ __global__ void dirichlet_values_kernel(int64_t nd, int H, const int32_t *bc_of,
 // -(h n, v) on Neumann faces, precomputed per node as vec = sum_faces A_f n_f / 3
 __global__ void neumann_kernel(int64_t n, const int32_t *node, const int32_t *bc_of,
                                const double *vec /* [n][3] */, DirCoef C, double *rhs) {
+  pdl_entry();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const double h = C.c[bc_of[k]];
     const int64_t r = 4 * (int64_t)node[k];
@@ -642,6 +650,7 @@ __global__ void apply_dirichlet_kernel(int64_t nd, const int32_t *dnode, const D
                                        int32_t pin_node, double pin_value,
                                        const int32_t *rowptr, const int32_t *diag, S *vals,
                                        double *rhs, double *x0) {
+  pdl_entry();
   const int64_t total = 3 * nd + (pin_node >= 0 ? 1 : 0);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     int node, c;
@@ -672,6 +681,7 @@ __global__ void apply_dirichlet_kernel(int64_t nd, const int32_t *dnode, const D
 
 // ||rhs|| of each component (one CTA per component, contiguous node range, fixed order)
 __global__ void comp_norm_kernel(const int32_t *comp_off, const double *rhs, double *scale) {
+  pdl_entry();
   __shared__ double red[256];
   const int c = blockIdx.x;
   const int64_t i0 = 4 * (int64_t)comp_off[c], i1 = 4 * (int64_t)comp_off[c + 1];
@@ -690,6 +700,7 @@ __global__ void comp_norm_kernel(const int32_t *comp_off, const double *rhs, dou
 template <class S>
 __global__ void comp_scale_kernel(int64_t V, int n_comp, const int32_t *comp_off, const double *scale,
                                   const int32_t *rowptr, S *vals, double *rhs) {
+  pdl_entry();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 4 * V; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = k >> 2;
     const int i = (int)(k & 3);
@@ -723,7 +734,7 @@ lfx_status launch_bdf(cudaStream_t st, int64_t V, int order, const D4 *h0, const
                       const D4 *h2, const double beta[3], const double gamma[3],
                       D4 *xext, D4 *ubdf, float4 *xe_hi, float4 *xe_lo, float4 *ub_hi, float4 *ub_lo) {
   note_launches(1);
-  bdf_kernel<<<grid_for(V, 256), 256, 0, st>>>(V, order, h0, h1, h2, beta[0], beta[1], beta[2],
+  pdl_launch(bdf_kernel, grid_for(V, 256), 256, 0, st, V, order, h0, h1, h2, beta[0], beta[1], beta[2],
                                                gamma[0], gamma[1], gamma[2], xext, ubdf, xe_hi, xe_lo,
                                                ub_hi, ub_lo);
   LFX_CUDA_TRY(cudaGetLastError());
@@ -733,7 +744,7 @@ lfx_status launch_bdf(cudaStream_t st, int64_t V, int order, const D4 *h0, const
 lfx_status launch_dd_combine(cudaStream_t st, int64_t n, const float *hi, const float *lo, double *out) {
   if (n == 0) return LFX_OK;
   note_launches(1);
-  dd_combine_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, hi, lo, out);
+  pdl_launch(dd_combine_kernel, grid_for(n, 256), 256, 0, st, n, hi, lo, out);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
 }
@@ -744,7 +755,7 @@ lfx_status launch_apply_dirichlet_dd(cudaStream_t st, int64_t nd, const int32_t 
   const int64_t total = 3 * nd + (pin_node >= 0 ? 1 : 0);
   if (total == 0) return LFX_OK;
   note_launches(1);
-  apply_dirichlet_dd_kernel<<<grid_for(total, 128), 128, 0, st>>>(nd, dnode, g, pin_node, pin_value, rowptr, diag,
+  pdl_launch(apply_dirichlet_dd_kernel, grid_for(total, 128), 128, 0, st, nd, dnode, g, pin_node, pin_value, rowptr, diag,
                                                                    hi, lo, rhs, x0);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
@@ -752,8 +763,8 @@ lfx_status launch_apply_dirichlet_dd(cudaStream_t st, int64_t nd, const int32_t 
 
 lfx_status launch_comp_normalize_dd(cudaStream_t st, int64_t V, int n_comp, const int32_t *comp_off,
                                     double *scale, const int32_t *rowptr, float *hi, float *lo, double *rhs) {
-  comp_norm_kernel<<<n_comp, 256, 0, st>>>(comp_off, rhs, scale);
-  comp_scale_dd_kernel<<<grid_for(4 * V, 256), 256, 0, st>>>(V, n_comp, comp_off, scale, rowptr, hi, lo, rhs);
+  pdl_launch(comp_norm_kernel, n_comp, 256, 0, st, comp_off, rhs, scale);
+  pdl_launch(comp_scale_dd_kernel, grid_for(4 * V, 256), 256, 0, st, V, n_comp, comp_off, scale, rowptr, hi, lo, rhs);
   note_launches(2);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
@@ -768,7 +779,7 @@ lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysPar
     if (e1 <= e0) continue;
     int64_t chunks = (e1 - e0 + kElems - 1) / kElems;
     int grid = (int)(chunks < 152 * 8 ? chunks : 152 * 8);
-    assemble_color_kernel<R, S><<<grid, kCta, 0, st>>>(A, P, Q, e0, e1, vals);
+    pdl_launch(assemble_color_kernel<R, S>, grid, kCta, 0, st, A, P, Q, e0, e1, vals);
     note_launches(1);
   }
   LFX_CUDA_TRY(cudaGetLastError());
@@ -786,7 +797,7 @@ lfx_status launch_dirichlet_values(cudaStream_t st, int64_t nd, int H, const int
                                    const double *S, const DirCoef &C, const double *N, int nb, D4 *g) {
   if (nd == 0) return LFX_OK;
   note_launches(1);
-  dirichlet_values_kernel<<<grid_for(nd, 256), 256, 0, st>>>(nd, H, bc_of, S, C, N, nb, g);
+  pdl_launch(dirichlet_values_kernel, grid_for(nd, 256), 256, 0, st, nd, H, bc_of, S, C, N, nb, g);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
 }
@@ -795,15 +806,15 @@ lfx_status launch_neumann(cudaStream_t st, int64_t n, const int32_t *node, const
                           const double *vec, const DirCoef &C, double *rhs) {
   if (n == 0) return LFX_OK;
   note_launches(1);
-  neumann_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, node, bc_of, vec, C, rhs);
+  pdl_launch(neumann_kernel, grid_for(n, 256), 256, 0, st, n, node, bc_of, vec, C, rhs);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
 }
 
 lfx_status launch_comp_normalize(cudaStream_t st, int64_t V, int n_comp, const int32_t *comp_off, double *scale,
                                  const int32_t *rowptr, double *vals, double *rhs) {
-  comp_norm_kernel<<<n_comp, 256, 0, st>>>(comp_off, rhs, scale);
-  comp_scale_kernel<double><<<grid_for(4 * V, 256), 256, 0, st>>>(V, n_comp, comp_off, scale, rowptr, vals, rhs);
+  pdl_launch(comp_norm_kernel, n_comp, 256, 0, st, comp_off, rhs, scale);
+  pdl_launch(comp_scale_kernel<double>, grid_for(4 * V, 256), 256, 0, st, V, n_comp, comp_off, scale, rowptr, vals, rhs);
   note_launches(2);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
@@ -816,7 +827,7 @@ lfx_status launch_apply_dirichlet(cudaStream_t st, int64_t nd, const int32_t *dn
   int64_t total = 3 * nd + (pin_node >= 0 ? 1 : 0);
   if (total == 0) return LFX_OK;
   note_launches(1);
-  apply_dirichlet_kernel<S><<<grid_for(total, 128), 128, 0, st>>>(nd, dnode, g, pin_node, pin_value,
+  pdl_launch(apply_dirichlet_kernel<S>, grid_for(total, 128), 128, 0, st, nd, dnode, g, pin_node, pin_value,
                                                                   rowptr, diag, vals, rhs, x0);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;

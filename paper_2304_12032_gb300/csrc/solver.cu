@@ -19,6 +19,7 @@
 #include "amg.h"
 #include "dd.h"
 #include "kernels.h"
+#include "pdl.h"
 #include "solver.h"
 
 namespace lfx {
@@ -203,6 +204,7 @@ template <class S, class T>
 __global__ void __launch_bounds__(kThreads) spmv_kernel(BsrView<S> A, const T *__restrict__ x,
                                                         const T *__restrict__ b, T *__restrict__ y,
                                                         int mode, double *part, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
@@ -251,6 +253,7 @@ __global__ void __launch_bounds__(kThreads) spmv_kernel(BsrView<S> A, const T *_
 // products made exact by two_prod, sums by two_sum, the rounding errors gathered in an FP32
 // correction), so the product carries about 48 significant bits while running on the FP32 pipes.
 __global__ void split_vec_kernel(int64_t V, const double *x, float4 *hi, float4 *lo, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
     const D4 v = reinterpret_cast<const D4 *>(x)[i];
@@ -263,6 +266,7 @@ __global__ void split_vec_kernel(int64_t V, const double *x, float4 *hi, float4 
 __global__ void __launch_bounds__(kThreads) spmv_dd_kernel(BsrView<DDMat> A, const double *__restrict__ b,
                                                            double *__restrict__ y, int mode, double *part,
                                                            const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
@@ -322,6 +326,7 @@ __global__ void __launch_bounds__(kThreads) spmv_dd_kernel(BsrView<DDMat> A, con
 
 // sum of part[0..n) -> *out (sqrt if root == 1, max instead of sum if root == 2); one CTA
 __global__ void reduce_kernel(const double *part, int n, double *out, int root) {
+  pdl_entry();
   double s = 0.0;
   if (root == 2) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) s = fmax(s, part[i]);
@@ -423,6 +428,7 @@ __device__ __forceinline__ void ld_DC(const SplitView<S> &A, int64_t k, T dc[4])
 // Blocks stored apart (in the preconditioner's storage type S) from the FP64 or FP32 4x4 blocks.
 template <class S, class Src>
 __global__ void split_kernel(int64_t nnzb, const Src *__restrict__ vals, S *F, S *G, S *DC) {
+  pdl_entry();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnzb; k += (int64_t)gridDim.x * blockDim.x) {
     Src b[16];
     ld_block<Src, Src>(vals, k, b);
@@ -448,6 +454,7 @@ __global__ void split_kernel(int64_t nnzb, const Src *__restrict__ vals, S *F, S
 template <class View, class T>
 __global__ void __launch_bounds__(kThreads) bound_kernel(View A, const T *dinvF, const T *dinvS, T *gs,
                                                          double *part, int mode) {
+  pdl_entry();
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
   using Acc = typename AccT<T>::type;
@@ -508,6 +515,7 @@ __global__ void __launch_bounds__(kThreads) bound_kernel(View A, const T *dinvF,
 // ------------------------------------------------------------------------------------------
 template <class View, class T>
 __global__ void diag_f_kernel(View A, T *dinvF) {
+  pdl_entry();
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.V; r += (int64_t)gridDim.x * blockDim.x) {
     T f[9];
     ld_F(A, A.diag[r], f);
@@ -523,6 +531,7 @@ __global__ void diag_f_kernel(View A, T *dinvF) {
 // diag(S)_a = C_aa - sum_{b,j} D_{a,(b,j)} G_{(b,j),a} / F_{(b,j),(b,j)}
 template <class View, class T>
 __global__ void diag_s_kernel(View A, const T *dinvF, T *dinvS) {
+  pdl_entry();
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
   T acc = T(0);
@@ -553,6 +562,7 @@ template <class View, class T>
 __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF, const T *d_old,
                                                           T *d_new, T *r, T *x, const SmoothCoef *cf,
                                                           int k, int mode, double *part, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
@@ -608,6 +618,7 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF
 template <class View, class T>
 __global__ void __launch_bounds__(kThreads) g_scaled_kernel(View A, const T *dinvF, const T *in,
                                                             T *w, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
@@ -646,6 +657,7 @@ __global__ void __launch_bounds__(kThreads) s_step_kernel(View A, const T *dinvS
                                                           const T *w, T *d_new, T *r, T *x,
                                                           const SmoothCoef *cf, int k, int mode,
                                                           double *part, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
@@ -700,6 +712,7 @@ __global__ void __launch_bounds__(kThreads) s_step_kernel(View A, const T *dinvS
 template <class T>
 __global__ void f_init_kernel(int64_t V, const T *dinvF, const T *b, T *r, T *d, T *x,
                               const SmoothCoef *cf, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
     const T s = (T)cf->f_init;
@@ -722,6 +735,7 @@ template <class View, class T>
 __global__ void __launch_bounds__(kThreads) d_init_kernel(View A, const T *dinvS, const T *b,
                                                           T *r, T *d, T *x, const SmoothCoef *cf,
                                                           const KState *st, T *bs) {
+  pdl_entry();
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
@@ -762,6 +776,7 @@ __global__ void __launch_bounds__(kThreads) d_init_kernel(View A, const T *dinvS
 template <class View, class T>
 __global__ void __launch_bounds__(kThreads) final_kernel(View A, const T *dinvF, const T *x, T *z,
                                                          const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
@@ -806,6 +821,7 @@ template <class View, class T>
 __global__ void __launch_bounds__(kThreads) s_resid_kernel(View A, const T *dinvS, T *x, const T *w,
                                                            const T *bs, T *out, T *r, T *d,
                                                            const SmoothCoef *cf, int mode, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
@@ -846,6 +862,7 @@ __global__ void __launch_bounds__(kThreads) s_resid_kernel(View A, const T *dinv
 // x.w += d.w (elementwise)
 template <class T>
 __global__ void add_w_kernel(int64_t V, const T *d, T *x, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
     auto xx = ld4(x, i);
@@ -900,6 +917,7 @@ __device__ __forceinline__ typename AccT<T>::type csr_row_dot(const int32_t *__r
 template <class T, int G>
 __global__ void __launch_bounds__(kThreads) csr_spmv_kernel(CsrV<T> M, const T *in, int is, int io, T *out, int os,
                                                             int oo, double alpha, int acc, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   using A = typename AccT<T>::type;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -915,6 +933,7 @@ __global__ void __launch_bounds__(kThreads) csr_spmv_kernel(CsrV<T> M, const T *
 template <class T, int G>
 __global__ void __launch_bounds__(kThreads) csr_resid_kernel(CsrV<T> M, const T *x, const T *b, T *out,
                                                              const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   using A = typename AccT<T>::type;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -927,6 +946,7 @@ __global__ void __launch_bounds__(kThreads) csr_resid_kernel(CsrV<T> M, const T 
 template <class T>
 __global__ void csr_cheb_init_kernel(int64_t n, const T *dinv, const T *rhs, T *r, T *d, T *x, double init, int add,
                                      const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   using A = typename AccT<T>::type;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -942,6 +962,7 @@ __global__ void csr_cheb_init_kernel(int64_t n, const T *dinv, const T *rhs, T *
 template <class T, int G>
 __global__ void __launch_bounds__(kThreads) csr_cheb_step_kernel(CsrV<T> M, const T *dinv, const T *d_old, T *d_new,
                                                                  T *r, T *x, double c1, double c2, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   using A = typename AccT<T>::type;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -986,6 +1007,7 @@ __device__ __forceinline__ typename AccT<T>::type dense_row_dot(int64_t n, const
 template <class T>
 __global__ void __launch_bounds__(kThreads) dense_mv_kernel(int64_t n, const T *Minv, const T *b, int is, int io,
                                                             T *x, int os, int oo, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
@@ -1146,6 +1168,7 @@ __global__ void __launch_bounds__(kThreads) amg_coarse_kernel(const CoarseArgs<T
 // power iteration helpers: v = (1/sqrt(n)) on the selected components; v = y / lambda
 template <class T>
 __global__ void fill_kernel(int64_t V, T *v, int comp_mask, double val) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
     auto o = ld4(v, i);
     if (comp_mask & 1) o.x = (T)val;
@@ -1157,6 +1180,7 @@ __global__ void fill_kernel(int64_t V, T *v, int comp_mask, double val) {
 }
 template <class T>
 __global__ void div_kernel(int64_t V, const T *y, T *v, int comp_mask, const double *lam) {
+  pdl_entry();
   const double il = 1.0 / *lam;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
     const auto a = ld4(y, i);
@@ -1173,6 +1197,7 @@ __global__ void div_kernel(int64_t V, const T *y, T *v, int comp_mask, const dou
 // constant Jacobi ones.
 __global__ void coef_kernel(SmoothCoef *cf, int f_kind, int f_steps, double f_omega, double f_ratio,
                             int s_kind, int s_steps, double s_omega, double s_ratio, double safety) {
+  pdl_entry();
   if (threadIdx.x != 0) return;
   for (int which = 0; which < 2; ++which) {
     const int kind = which ? s_kind : f_kind;
@@ -1217,6 +1242,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) mdot_kernel(const T *Vb, int64_t ld, int nvec, const T *w,
                                                         int64_t n, double *part, int ldp,
                                                         const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   using V4 = typename Vec4T<T>::type;
   __shared__ double red[8][kThreads / 32];
@@ -1258,6 +1284,7 @@ __global__ void __launch_bounds__(kThreads) mdot_kernel(const T *Vb, int64_t ld,
 // h[i] = sum_blk part[i][blk]; hcol[i] (+)= h[i]; hwork[i] = h[i].  One warp per vector i.
 __global__ void mdot_finalize_kernel(const double *part, int nblk, int ldp, int nvec, KState *st,
                                      int accumulate) {
+  pdl_entry();
   if (finished(st)) return;
   const int i = blockIdx.x;
   if (i >= nvec) return;
@@ -1275,6 +1302,7 @@ __global__ void mdot_finalize_kernel(const double *part, int nblk, int ldp, int 
 template <class T>
 __global__ void __launch_bounds__(kThreads) maxpy_kernel(const T *Vb, int64_t ld, int nvec, T *w,
                                                          int64_t n, double *part, KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   using V4 = typename Vec4T<T>::type;
   using A = typename AccT<T>::type;
@@ -1311,6 +1339,7 @@ __global__ void __launch_bounds__(kThreads) maxpy_kernel(const T *Vb, int64_t ld
 
 // Arnoldi column j: h_{j+1,j} = ||w||, Givens rotations, residual estimate, stopping test.
 __global__ void givens_kernel(const double *part, int nblk, KState *st, int j, int m, int maxit) {
+  pdl_entry();
   if (finished(st)) return;
   double s = 0.0;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i];
@@ -1355,6 +1384,7 @@ __global__ void givens_kernel(const double *part, int nblk, KState *st, int j, i
 
 template <class A, class B>
 __global__ void convert_kernel(const A *src, B *dst, int64_t n, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = (B)src[i];
@@ -1362,6 +1392,7 @@ __global__ void convert_kernel(const A *src, B *dst, int64_t n, const KState *st
 template <>
 __global__ void convert_kernel<double, __nv_bfloat16>(const double *src, __nv_bfloat16 *dst, int64_t n,
                                                       const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = __double2bfloat16(src[i]);
@@ -1369,6 +1400,7 @@ __global__ void convert_kernel<double, __nv_bfloat16>(const double *src, __nv_bf
 
 template <class T>
 __global__ void norm_kernel(const T *v, int64_t n, double *part) {
+  pdl_entry();
   using A = typename AccT<T>::type;
   A a = A(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1379,6 +1411,7 @@ __global__ void norm_kernel(const T *v, int64_t n, double *part) {
 
 template <class T>
 __global__ void scale_kernel(const T *w, T *v, int64_t n, const double *sc, const KState *st) {
+  pdl_entry();
   if (finished(st)) return;
   using A = typename AccT<T>::type;
   const A s = (A)*sc;
@@ -1388,6 +1421,7 @@ __global__ void scale_kernel(const T *w, T *v, int64_t n, const double *sc, cons
 // variant used at the start of a cycle (no early exit): v0 = r / beta
 template <class T>
 __global__ void scale_beta_kernel(const T *w, T *v, int64_t n, const KState *st) {
+  pdl_entry();
   using A = typename AccT<T>::type;
   const double b = st->beta;
   const A s = (A)(b > 0.0 ? 1.0 / b : 0.0);
@@ -1397,6 +1431,7 @@ __global__ void scale_beta_kernel(const T *w, T *v, int64_t n, const KState *st)
 
 // start of a cycle: beta = ||r||, g = (beta, 0, ...), j = 0, done if beta <= tol
 __global__ void cycle_start_kernel(const double *part, int nblk, KState *st) {
+  pdl_entry();
   double s = 0.0;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i];
   s = cta_sum(s);
@@ -1419,6 +1454,7 @@ __global__ void cycle_start_kernel(const double *part, int nblk, KState *st) {
 
 // y = H(0:j,0:j)^-1 g(0:j) by back substitution (j = completed steps of this cycle)
 __global__ void trisolve_kernel(KState *st) {
+  pdl_entry();
   if (threadIdx.x != 0) return;
   const int j = st->j;
   for (int i = j - 1; i >= 0; --i) {
@@ -1431,6 +1467,7 @@ __global__ void trisolve_kernel(KState *st) {
 // x += sum_{i<j} y_i z_i
 template <class T, class X>
 __global__ void update_x_kernel(const T *Zb, int64_t ld, X *x, int64_t n, const KState *st) {
+  pdl_entry();
   using A = typename AccT<T, X>::type;
   __shared__ A y[kMaxRestart];
   const int j = st->j;
@@ -1461,7 +1498,7 @@ template <class S, class T>
 lfx_status launch_spmv(cudaStream_t st, const BsrView<S> &A, const T *x, const T *b, T *y, int mode,
                        double *part, int *n_part) {
   const int g = rows_grid(A.V);
-  spmv_kernel<S, T><<<g, kThreads, 0, st>>>(A, x, b, y, mode, part, nullptr);
+  pdl_launch(spmv_kernel<S, T>, g, kThreads, 0, st, A, x, b, y, mode, part, nullptr);
   note_launches(1);
   if (n_part) *n_part = g;
   LFX_CUDA_TRY(cudaGetLastError());
@@ -1476,9 +1513,9 @@ template lfx_status launch_spmv<float, double>(cudaStream_t, const BsrView<float
 template <>
 lfx_status launch_spmv<DDMat, double>(cudaStream_t st, const BsrView<DDMat> &A, const double *x, const double *b,
                                       double *y, int mode, double *part, int *n_part) {
-  split_vec_kernel<<<vec_grid(A.V), kThreads, 0, st>>>(A.V, x, A.xs_hi, A.xs_lo, nullptr);
+  pdl_launch(split_vec_kernel, vec_grid(A.V), kThreads, 0, st, A.V, x, A.xs_hi, A.xs_lo, nullptr);
   const int g = rows_grid(A.V);
-  spmv_dd_kernel<<<g, kThreads, 0, st>>>(A, b, y, mode, part, nullptr);
+  pdl_launch(spmv_dd_kernel, g, kThreads, 0, st, A, b, y, mode, part, nullptr);
   note_launches(2);
   if (n_part) *n_part = g;
   LFX_CUDA_TRY(cudaGetLastError());
@@ -1488,12 +1525,12 @@ lfx_status launch_spmv<DDMat, double>(cudaStream_t st, const BsrView<DDMat> &A, 
 // The Arnoldi product w = A z_j (kernels return at once when the cycle has finished)
 template <class S, class T>
 static void arnoldi_spmv(cudaStream_t st, const BsrView<S> &A, const T *x, T *y, const KState *ks) {
-  spmv_kernel<S, T><<<rows_grid(A.V), kThreads, 0, st>>>(A, x, nullptr, y, 0, nullptr, ks);
+  pdl_launch(spmv_kernel<S, T>, rows_grid(A.V), kThreads, 0, st, A, x, nullptr, y, 0, nullptr, ks);
   note_launches(1);
 }
 static void arnoldi_spmv(cudaStream_t st, const BsrView<DDMat> &A, const double *x, double *y, const KState *ks) {
-  split_vec_kernel<<<vec_grid(A.V), kThreads, 0, st>>>(A.V, x, A.xs_hi, A.xs_lo, ks);
-  spmv_dd_kernel<<<rows_grid(A.V), kThreads, 0, st>>>(A, nullptr, y, 0, nullptr, ks);
+  pdl_launch(split_vec_kernel, vec_grid(A.V), kThreads, 0, st, A.V, x, A.xs_hi, A.xs_lo, ks);
+  pdl_launch(spmv_dd_kernel, rows_grid(A.V), kThreads, 0, st, A, nullptr, y, 0, nullptr, ks);
   note_launches(2);
 }
 
@@ -1564,44 +1601,44 @@ template <class S, class T>
 template <class View>
 lfx_status ASimple<S, T>::setup_view(cudaStream_t st, const View &A) {
   const int rg = rows_grid(V), vg = vec_grid(V);
-  diag_f_kernel<View, T><<<vg, kThreads, 0, st>>>(A, dinvF.as<T>());
-  diag_s_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>());
+  pdl_launch(diag_f_kernel<View, T>, vg, kThreads, 0, st, A, dinvF.as<T>());
+  pdl_launch(diag_s_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), dinvS.as<T>());
   SmoothCoef *cf = coef.as<SmoothCoef>();
   double *lam_f = &cf->lam_f, *lam_s = &cf->lam_s;
   const bool bound = cfg.n_power <= 0;
   if (bound) {
     // Gershgorin bounds (hold for every eigenvalue; no safety factor)
-    bound_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 0);
-    reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_f, 2);
-    bound_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 1);
-    bound_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 2);
-    reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_s, 2);
+    pdl_launch(bound_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 0);
+    pdl_launch(reduce_kernel, 1, kThreads, 0, st, part.as<double>(), rg, lam_f, 2);
+    pdl_launch(bound_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 1);
+    pdl_launch(bound_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), dinvS.as<T>(), W.as<T>(), part.as<double>(), 2);
+    pdl_launch(reduce_kernel, 1, kThreads, 0, st, part.as<double>(), rg, lam_s, 2);
     note_launches(5);
   }
   if (!bound && cfg.f_kind == LFX_SMOOTH_CHEBYSHEV) {
     // power iteration on diag(F)^-1 F from the normalised ones vector (velocity components)
-    fill_kernel<T><<<vg, kThreads, 0, st>>>(V, D0.as<T>(), 7, 1.0 / sqrt(3.0 * (double)V));
+    pdl_launch(fill_kernel<T>, vg, kThreads, 0, st, V, D0.as<T>(), 7, 1.0 / sqrt(3.0 * (double)V));
     for (int it = 0; it < cfg.n_power; ++it) {
-      f_step_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), D0.as<T>(), D1.as<T>(), nullptr,
+      pdl_launch(f_step_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), D0.as<T>(), D1.as<T>(), nullptr,
                                                    nullptr, cf, 0, 0, part.as<double>(), nullptr);
-      reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_f, 1);
-      div_kernel<T><<<vg, kThreads, 0, st>>>(V, D1.as<T>(), D0.as<T>(), 7, lam_f);
+      pdl_launch(reduce_kernel, 1, kThreads, 0, st, part.as<double>(), rg, lam_f, 1);
+      pdl_launch(div_kernel<T>, vg, kThreads, 0, st, V, D1.as<T>(), D0.as<T>(), 7, lam_f);
     }
     note_launches(1 + 3 * cfg.n_power);
   }
   if (!bound && cfg.s_kind != LFX_SMOOTH_JACOBI) {
-    fill_kernel<T><<<vg, kThreads, 0, st>>>(V, D0.as<T>(), 8, 1.0 / sqrt((double)V));
+    pdl_launch(fill_kernel<T>, vg, kThreads, 0, st, V, D0.as<T>(), 8, 1.0 / sqrt((double)V));
     for (int it = 0; it < cfg.n_power; ++it) {
-      g_scaled_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), D0.as<T>(), W.as<T>(), nullptr);
-      s_step_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), D0.as<T>(), W.as<T>(), D1.as<T>(),
+      pdl_launch(g_scaled_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), D0.as<T>(), W.as<T>(), nullptr);
+      pdl_launch(s_step_kernel<View, T>, rg, kThreads, 0, st, A, dinvS.as<T>(), D0.as<T>(), W.as<T>(), D1.as<T>(),
                                                    nullptr, nullptr, cf, 0, 0, part.as<double>(), nullptr);
-      reduce_kernel<<<1, kThreads, 0, st>>>(part.as<double>(), rg, lam_s, 1);
-      div_kernel<T><<<vg, kThreads, 0, st>>>(V, D1.as<T>(), D0.as<T>(), 8, lam_s);
+      pdl_launch(reduce_kernel, 1, kThreads, 0, st, part.as<double>(), rg, lam_s, 1);
+      pdl_launch(div_kernel<T>, vg, kThreads, 0, st, V, D1.as<T>(), D0.as<T>(), 8, lam_s);
     }
     note_launches(1 + 4 * cfg.n_power);
   }
   note_launches(3);
-  coef_kernel<<<1, 32, 0, st>>>(cf, cfg.f_kind, cfg.f_steps, cfg.f_omega, cfg.f_ratio, cfg.s_kind,
+  pdl_launch(coef_kernel, 1, 32, 0, st, cf, cfg.f_kind, cfg.f_steps, cfg.f_omega, cfg.f_ratio, cfg.s_kind,
                                 cfg.s_steps, cfg.s_omega, cfg.s_ratio, bound ? 1.0 : 1.1);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
@@ -1633,7 +1670,7 @@ lfx_status ASimple<S, T>::setup_split_from(cudaStream_t st, const BsrView<Src> &
     nnz_split = nnzb;
   }
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nnzb + kThreads - 1) / kThreads, 152 * 16));
-  split_kernel<S, Src><<<g, kThreads, 0, st>>>(nnzb, A64.vals, sF.as<S>(), sG.as<S>(), sDC.as<S>());
+  pdl_launch(split_kernel<S, Src>, g, kThreads, 0, st, nnzb, A64.vals, sF.as<S>(), sG.as<S>(), sDC.as<S>());
   note_launches(1);
   split = true;
   const SplitView<S> sv{A64.V, A64.rowptr, A64.col, A64.diag, A64.trans, sF.as<S>(), sG.as<S>(), sDC.as<S>()};
@@ -1648,35 +1685,35 @@ lfx_status ASimple<S, T>::apply_view(cudaStream_t st, const View &A, const T *r,
   const SmoothCoef *cf = coef.as<SmoothCoef>();
   T *d[2] = {D0.as<T>(), D1.as<T>()};
   // z_u* ~= F^-1 r_u
-  f_init_kernel<T><<<vg, kThreads, 0, st>>>(V, dinvF.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks);
+  pdl_launch(f_init_kernel<T>, vg, kThreads, 0, st, V, dinvF.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks);
   for (int k = 1; k < cfg.f_steps; ++k)
-    f_step_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], d[k & 1], R.as<T>(),
+    pdl_launch(f_step_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), d[(k - 1) & 1], d[k & 1], R.as<T>(),
                                                  X.as<T>(), cf, k, 1, nullptr, ks);
   // z_p ~= S^-1 (r_p - D z_u*): Chebyshev/Jacobi steps on S, or one AMG V-cycle
   if (cfg.s_kind == LFX_SMOOTH_AMG && !amg_ready) {
     set_error("aSIMPLE: the Schur AMG hierarchy has not been built");
     return LFX_ERR_INVALID_ARG;
   }
-  d_init_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks,
+  pdl_launch(d_init_kernel<View, T>, rg, kThreads, 0, st, A, dinvS.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks,
                                                amg_ready ? Bs.as<T>() : nullptr);
   for (int k = 1; k < cfg.s_steps; ++k) {
-    g_scaled_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
-    s_step_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
+    pdl_launch(g_scaled_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
+    pdl_launch(s_step_kernel<View, T>, rg, kThreads, 0, st, A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
                                                  R.as<T>(), X.as<T>(), cf, k, 1, nullptr, ks);
   }
   if (cfg.s_kind == LFX_SMOOTH_AMG && amg.size() == 1) {
     // small problem: the hierarchy is the dense inverse of S itself
-    dense_mv_kernel<T><<<(int)((V * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+    pdl_launch(dense_mv_kernel<T>, (int)((V * 32 + kThreads - 1) / kThreads), kThreads, 0, st, 
         V, coarse_inv.as<T>(), Bs.as<T>(), 4, 3, X.as<T>(), 4, 3, ks);
     note_launches(1);
   } else if (cfg.s_kind == LFX_SMOOTH_AMG) {
     // residual of the pre-smoothed level-0 iterate, restriction, coarse V-cycle, prolongation
-    g_scaled_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
-    s_resid_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(),
+    pdl_launch(g_scaled_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
+    pdl_launch(s_resid_kernel<View, T>, rg, kThreads, 0, st, A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(),
                                                   rr0.as<T>(), nullptr, nullptr, cf, 0, ks);
     const AmgDevLevel &L0 = amg[0];
     CsrV<T> R0{L0.nnext, L0.Rrp.as<int32_t>(), L0.Rci.as<int32_t>(), L0.Rv.as<T>()};
-    csr_spmv_kernel<T, 32><<<(int)((L0.nnext * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+    pdl_launch(csr_spmv_kernel<T, 32>, (int)((L0.nnext * 32 + kThreads - 1) / kThreads), kThreads, 0, st, 
         R0, rr0.as<T>(), 1, 0, amg[1].b.as<T>(), 1, 0, 1.0, 0, ks);
     if (coop_grid > 0) {
       const CoarseArgs<T> *ca = coarse_args.as<CoarseArgs<T>>();
@@ -1690,22 +1727,22 @@ lfx_status ASimple<S, T>::apply_view(cudaStream_t st, const View &A, const T *r,
     CsrV<T> P0{V, L0.Prp.as<int32_t>(), L0.Pci.as<int32_t>(), L0.Pv.as<T>()};
     // the level-1 iterate is in d1 when the coarse launch fused its last smoothing step
     const T *x1 = (amg.size() > 2 && coop_grid > 0 && cfg.s_steps == 1) ? amg[1].d1.as<T>() : amg[1].x.as<T>();
-    csr_spmv_kernel<T, 8><<<lanes_grid(V, 8), kThreads, 0, st>>>(P0, x1, 1, 0, X.as<T>(), 4, 3,
+    pdl_launch(csr_spmv_kernel<T, 8>, lanes_grid(V, 8), kThreads, 0, st, P0, x1, 1, 0, X.as<T>(), 4, 3,
                                                             amg_alpha, 1, ks);
     // post-smoothing from the corrected iterate
-    g_scaled_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
-    s_resid_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(), nullptr,
+    pdl_launch(g_scaled_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
+    pdl_launch(s_resid_kernel<View, T>, rg, kThreads, 0, st, A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(), nullptr,
                                                   R.as<T>(), d[0], cf, 1, ks);
-    add_w_kernel<T><<<vg, kThreads, 0, st>>>(V, d[0], X.as<T>(), ks);
+    pdl_launch(add_w_kernel<T>, vg, kThreads, 0, st, V, d[0], X.as<T>(), ks);
     for (int k = 1; k < cfg.s_steps; ++k) {
-      g_scaled_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
-      s_step_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
+      pdl_launch(g_scaled_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
+      pdl_launch(s_step_kernel<View, T>, rg, kThreads, 0, st, A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
                                                    R.as<T>(), X.as<T>(), cf, k, 1, nullptr, ks);
     }
     note_launches(9 + 2 * (cfg.s_steps - 1));
   }
   // z_u = z_u* - diag(F)^-1 G z_p
-  final_kernel<View, T><<<rg, kThreads, 0, st>>>(A, dinvF.as<T>(), X.as<T>(), z, ks);
+  pdl_launch(final_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), X.as<T>(), z, ks);
   note_launches(3 + (cfg.f_steps - 1) + 2 * (cfg.s_steps - 1));
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
@@ -1869,7 +1906,7 @@ lfx_status ASimple<S, T>::vcycle(cudaStream_t st, int l, const KState *ks) {
   AmgDevLevel &D = amg[l];
   const int L = (int)amg.size();
   if (l == L - 1) {
-    dense_mv_kernel<T><<<(int)((D.n * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+    pdl_launch(dense_mv_kernel<T>, (int)((D.n * 32 + kThreads - 1) / kThreads), kThreads, 0, st, 
         D.n, coarse_inv.as<T>(), D.b.as<T>(), 1, 0, D.x.as<T>(), 1, 0, ks);
     note_launches(1);
     return LFX_OK;
@@ -1884,27 +1921,27 @@ lfx_status ASimple<S, T>::vcycle(cudaStream_t st, int l, const KState *ks) {
   const int rg32 = (int)((D.n * 32 + kThreads - 1) / kThreads);
   auto cheb_step = [&](int k) {
     if (wide)
-      csr_cheb_step_kernel<T, 32><<<rg32, kThreads, 0, st>>>(A, dinv, d[(k - 1) & 1], d[k & 1], D.r.as<T>(),
+      pdl_launch(csr_cheb_step_kernel<T, 32>, rg32, kThreads, 0, st, A, dinv, d[(k - 1) & 1], d[k & 1], D.r.as<T>(),
                                                              D.x.as<T>(), D.c1[k], D.c2[k], ks);
     else
-      csr_cheb_step_kernel<T, 8><<<rg, kThreads, 0, st>>>(A, dinv, d[(k - 1) & 1], d[k & 1], D.r.as<T>(),
+      pdl_launch(csr_cheb_step_kernel<T, 8>, rg, kThreads, 0, st, A, dinv, d[(k - 1) & 1], d[k & 1], D.r.as<T>(),
                                                           D.x.as<T>(), D.c1[k], D.c2[k], ks);
   };
   auto resid = [&]() {
     if (wide)
-      csr_resid_kernel<T, 32><<<rg32, kThreads, 0, st>>>(A, D.x.as<T>(), D.b.as<T>(), D.rr.as<T>(), ks);
+      pdl_launch(csr_resid_kernel<T, 32>, rg32, kThreads, 0, st, A, D.x.as<T>(), D.b.as<T>(), D.rr.as<T>(), ks);
     else
-      csr_resid_kernel<T, 8><<<rg, kThreads, 0, st>>>(A, D.x.as<T>(), D.b.as<T>(), D.rr.as<T>(), ks);
+      pdl_launch(csr_resid_kernel<T, 8>, rg, kThreads, 0, st, A, D.x.as<T>(), D.b.as<T>(), D.rr.as<T>(), ks);
   };
-  csr_cheb_init_kernel<T><<<vg, kThreads, 0, st>>>(D.n, dinv, D.b.as<T>(), D.r.as<T>(), d[0], D.x.as<T>(), D.init, 0, ks);
+  pdl_launch(csr_cheb_init_kernel<T>, vg, kThreads, 0, st, D.n, dinv, D.b.as<T>(), D.r.as<T>(), d[0], D.x.as<T>(), D.init, 0, ks);
   for (int k = 1; k < cfg.s_steps; ++k) cheb_step(k);
   resid();
-  csr_spmv_kernel<T, 32><<<(int)((D.nnext * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+  pdl_launch(csr_spmv_kernel<T, 32>, (int)((D.nnext * 32 + kThreads - 1) / kThreads), kThreads, 0, st, 
       R, D.rr.as<T>(), 1, 0, amg[l + 1].b.as<T>(), 1, 0, 1.0, 0, ks);
   LFX_TRY(vcycle(st, l + 1, ks));
-  csr_spmv_kernel<T, 8><<<rg, kThreads, 0, st>>>(P, amg[l + 1].x.as<T>(), 1, 0, D.x.as<T>(), 1, 0, amg_alpha, 1, ks);
+  pdl_launch(csr_spmv_kernel<T, 8>, rg, kThreads, 0, st, P, amg[l + 1].x.as<T>(), 1, 0, D.x.as<T>(), 1, 0, amg_alpha, 1, ks);
   resid();
-  csr_cheb_init_kernel<T><<<vg, kThreads, 0, st>>>(D.n, dinv, D.rr.as<T>(), D.r.as<T>(), d[0], D.x.as<T>(), D.init, 1, ks);
+  pdl_launch(csr_cheb_init_kernel<T>, vg, kThreads, 0, st, D.n, dinv, D.rr.as<T>(), D.r.as<T>(), d[0], D.x.as<T>(), D.init, 1, ks);
   for (int k = 1; k < cfg.s_steps; ++k) cheb_step(k);
   note_launches(6 + 2 * (cfg.s_steps - 1));
   LFX_CUDA_TRY(cudaGetLastError());
@@ -1990,8 +2027,8 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
   double *pn = part_n.as<double>();
   const int vg = vec_grid(n);
   // ||b||
-  norm_kernel<T><<<vg, kThreads, 0, st>>>(b, n, pn);
-  reduce_kernel<<<1, kThreads, 0, st>>>(pn, vg, &ks->bnorm, 1);
+  pdl_launch(norm_kernel<T>, vg, kThreads, 0, st, b, n, pn);
+  pdl_launch(reduce_kernel, 1, kThreads, 0, st, pn, vg, &ks->bnorm, 1);
   note_launches(2);
   KState hs;
   LFX_CUDA_TRY(cudaMemcpyAsync(&hs, ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
@@ -2018,8 +2055,8 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
     // r = b - A x -> w, beta, v0 = r / beta
     int ng = 0;
     LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, pn, &ng)));
-    cycle_start_kernel<<<1, kThreads, 0, st>>>(pn, ng, ks);
-    scale_beta_kernel<T><<<vg, kThreads, 0, st>>>(w, Vb, n, ks);
+    pdl_launch(cycle_start_kernel, 1, kThreads, 0, st, pn, ng, ks);
+    pdl_launch(scale_beta_kernel<T>, vg, kThreads, 0, st, w, Vb, n, ks);
     note_launches(2);
     int launched = 0;
     for (int j = 0; j < restart; ++j) {
@@ -2037,13 +2074,13 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
       LFX_CUDA_TRY(cudaEventRecord(tev[n_tev + 1], st));
       n_tev += 2;
       for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
-        mdot_kernel<T><<<dim3(nblk_dot, (j + 8) / 8), kThreads, 0, st>>>(Vb, n, j + 1, w, n, part.as<double>(),
+        pdl_launch(mdot_kernel<T>, dim3(nblk_dot, (j + 8) / 8), kThreads, 0, st, Vb, n, j + 1, w, n, part.as<double>(),
                                                                           nblk_dot, ks);
-        mdot_finalize_kernel<<<j + 1, 32, 0, st>>>(part.as<double>(), nblk_dot, nblk_dot, j + 1, ks, pass);
-        maxpy_kernel<T><<<vg, kThreads, 0, st>>>(Vb, n, j + 1, w, n, pn, ks);
+        pdl_launch(mdot_finalize_kernel, j + 1, 32, 0, st, part.as<double>(), nblk_dot, nblk_dot, j + 1, ks, pass);
+        pdl_launch(maxpy_kernel<T>, vg, kThreads, 0, st, Vb, n, j + 1, w, n, pn, ks);
       }
-      givens_kernel<<<1, kThreads, 0, st>>>(pn, vg, ks, j, restart, maxit);
-      scale_kernel<T><<<vg, kThreads, 0, st>>>(w, vn, n, &ks->scale, ks);
+      pdl_launch(givens_kernel, 1, kThreads, 0, st, pn, vg, ks, j, restart, maxit);
+      pdl_launch(scale_kernel<T>, vg, kThreads, 0, st, w, vn, n, &ks->scale, ks);
       note_launches(2 + 3 * (cgs2 ? 2 : 1));
       LFX_CUDA_TRY(cudaMemcpyAsync(pinned + (j & 3), &ks->done, sizeof(int), cudaMemcpyDeviceToHost, st));
       LFX_CUDA_TRY(cudaEventRecord(ev[j & 3], st));
@@ -2055,8 +2092,8 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
       }
     }
     (void)launched;
-    trisolve_kernel<<<1, 32, 0, st>>>(ks);
-    update_x_kernel<T, T><<<vg, kThreads, 0, st>>>(Zb, n, x, n, ks);
+    pdl_launch(trisolve_kernel, 1, 32, 0, st, ks);
+    pdl_launch(update_x_kernel<T, T>, vg, kThreads, 0, st, Zb, n, x, n, ks);
     note_launches(2);
     LFX_CUDA_TRY(cudaMemcpyAsync(&hs, ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
     LFX_CUDA_TRY(cudaStreamSynchronize(st));
@@ -2070,7 +2107,7 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
     if (hs.flag == 1 || total >= maxit) {
       // confirm with the true residual
       LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, pn, &ng)));
-      reduce_kernel<<<1, kThreads, 0, st>>>(pn, ng, &ks->res, 1);
+      pdl_launch(reduce_kernel, 1, kThreads, 0, st, pn, ng, &ks->res, 1);
       note_launches(1);
       double tr = 0.0;
       LFX_CUDA_TRY(cudaMemcpyAsync(&tr, &ks->res, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -2103,7 +2140,7 @@ template struct Gmres<DDMat, double>;
 
 template <class A, class B>
 lfx_status launch_convert(cudaStream_t st, const A *src, B *dst, int64_t n, const KState *ks) {
-  convert_kernel<A, B><<<vec_grid(n), kThreads, 0, st>>>(src, dst, n, ks);
+  pdl_launch(convert_kernel<A, B>, vec_grid(n), kThreads, 0, st, src, dst, n, ks);
   note_launches(1);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
