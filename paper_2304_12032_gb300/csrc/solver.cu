@@ -558,10 +558,13 @@ __global__ void diag_s_kernel(View A, const T *dinvF, T *dinvS) {
 
 // Velocity smoothing step on F.  mode 0 (power): y = dinvF (F v), partial |y|^2.
 // mode 1 (Chebyshev/Jacobi step k): y = F d_old; r -= dinvF y; d_new = c1 d_old + c2 r; x += d_new.
-template <class View, class T>
+// kFirst: step 1 fused with the start of the smoothing (f_init_kernel): d_old = init dinvF b0 and
+// r = dinvF b0 are formed on the fly from b0 by the same operations, so d_old is never stored.
+template <class View, class T, bool kFirst = false>
 __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF, const T *d_old,
                                                           T *d_new, T *r, T *x, const SmoothCoef *cf,
-                                                          int k, int mode, double *part, const KState *st) {
+                                                          int k, int mode, double *part, const KState *st,
+                                                          const T *b0) {
   pdl_entry();
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
@@ -578,7 +581,18 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF
           ld_F(A, k, f[u]);
           c[u] = __ldg(A.col + k);
         },
-        [&](int u) { dv[u] = ld4(d_old, c[u]); },
+        [&](int u) {
+          if constexpr (kFirst) {
+            const T s0 = (T)cf->f_init;
+            const auto dfc = ld4(dinvF, c[u]);
+            const auto bc = ld4(b0, c[u]);
+            dv[u].x = s0 * (dfc.x * bc.x);
+            dv[u].y = s0 * (dfc.y * bc.y);
+            dv[u].z = s0 * (dfc.z * bc.z);
+          } else {
+            dv[u] = ld4(d_old, c[u]);
+          }
+        },
         [&](int u) {
 #pragma unroll
           for (int i = 0; i < 3; ++i) acc[i] += f[u][3 * i] * dv[u].x + f[u][3 * i + 1] * dv[u].y + f[u][3 * i + 2] * dv[u].z;
@@ -597,9 +611,18 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF
     } else {
       const T c1 = (T)cf->f_c1[k], c2 = (T)cf->f_c2[k];
       auto rr = ld4(r, row);
-      const auto dold = ld4(d_old, row);
-      auto dn = ld4(d_new, row);
+      typename Vec4T<T>::type dold;
       auto xx = ld4(x, row);
+      if constexpr (kFirst) {
+        const T s0 = (T)cf->f_init;
+        const auto bv = ld4(b0, row);
+        rr.x = df.x * bv.x; rr.y = df.y * bv.y; rr.z = df.z * bv.z;
+        dold.x = s0 * rr.x; dold.y = s0 * rr.y; dold.z = s0 * rr.z;
+        xx.x = dold.x; xx.y = dold.y; xx.z = dold.z;
+      } else {
+        dold = ld4(d_old, row);
+      }
+      auto dn = ld4(d_new, row);
       rr.x -= df.x * acc[0]; rr.y -= df.y * acc[1]; rr.z -= df.z * acc[2];
       dn.x = c1 * dold.x + c2 * rr.x; dn.y = c1 * dold.y + c2 * rr.y; dn.z = c1 * dold.z + c2 * rr.z;
       xx.x += dn.x; xx.y += dn.y; xx.z += dn.z;
@@ -773,9 +796,11 @@ __global__ void __launch_bounds__(kThreads) d_init_kernel(View A, const T *dinvS
 }
 
 // z.xyz = x.xyz - dinvF (G x.w), z.w = x.w
-template <class View, class T>
+// kAddW: the iterate's pressure is read as x.w + dw.w (the pending update x.w += d.w of the
+// Schur post-smoothing, left to this pass)
+template <class View, class T, bool kAddW = false>
 __global__ void __launch_bounds__(kThreads) final_kernel(View A, const T *dinvF, const T *x, T *z,
-                                                         const KState *st) {
+                                                         const KState *st, const T *dw) {
   pdl_entry();
   if (finished(st)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
@@ -791,7 +816,10 @@ __global__ void __launch_bounds__(kThreads) final_kernel(View A, const T *dinvF,
           ld_G(A, k, g[u]);
           c[u] = __ldg(A.col + k);
         },
-        [&](int u) { p[u] = x[4 * (int64_t)c[u] + 3]; },
+        [&](int u) {
+          p[u] = x[4 * (int64_t)c[u] + 3];
+          if constexpr (kAddW) p[u] += dw[4 * (int64_t)c[u] + 3];
+        },
         [&](int u) {
           acc[0] += g[u][0] * p[u];
           acc[1] += g[u][1] * p[u];
@@ -803,6 +831,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(View A, const T *dinvF,
   if (row < A.V && lane == 0) {
     const auto df = ld4(dinvF, row);
     auto xx = ld4(x, row);
+    if constexpr (kAddW) xx.w += ld4(dw, row).w;
     typename Vec4T<T>::type o;
     o.x = xx.x - df.x * acc[0];
     o.y = xx.y - df.y * acc[1];
@@ -1620,7 +1649,7 @@ lfx_status ASimple<S, T>::setup_view(cudaStream_t st, const View &A) {
     pdl_launch(fill_kernel<T>, vg, kThreads, 0, st, V, D0.as<T>(), 7, 1.0 / sqrt(3.0 * (double)V));
     for (int it = 0; it < cfg.n_power; ++it) {
       pdl_launch(f_step_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), D0.as<T>(), D1.as<T>(), nullptr,
-                                                   nullptr, cf, 0, 0, part.as<double>(), nullptr);
+                                                   nullptr, cf, 0, 0, part.as<double>(), nullptr, nullptr);
       pdl_launch(reduce_kernel, 1, kThreads, 0, st, part.as<double>(), rg, lam_f, 1);
       pdl_launch(div_kernel<T>, vg, kThreads, 0, st, V, D1.as<T>(), D0.as<T>(), 7, lam_f);
     }
@@ -1685,10 +1714,17 @@ lfx_status ASimple<S, T>::apply_view(cudaStream_t st, const View &A, const T *r,
   const SmoothCoef *cf = coef.as<SmoothCoef>();
   T *d[2] = {D0.as<T>(), D1.as<T>()};
   // z_u* ~= F^-1 r_u
-  pdl_launch(f_init_kernel<T>, vg, kThreads, 0, st, V, dinvF.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks);
-  for (int k = 1; k < cfg.f_steps; ++k)
+  bool pending_w = false;
+  if (cfg.f_steps >= 2) {
+    // start of the smoothing fused into step 1 (d_old formed from r on the fly)
+    pdl_launch(f_step_kernel<View, T, true>, rg, kThreads, 0, st, A, dinvF.as<T>(), d[0], d[1], R.as<T>(), X.as<T>(),
+               cf, 1, 1, nullptr, ks, r);
+  } else {
+    pdl_launch(f_init_kernel<T>, vg, kThreads, 0, st, V, dinvF.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks);
+  }
+  for (int k = 2; k < cfg.f_steps; ++k)
     pdl_launch(f_step_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), d[(k - 1) & 1], d[k & 1], R.as<T>(),
-                                                 X.as<T>(), cf, k, 1, nullptr, ks);
+                                                 X.as<T>(), cf, k, 1, nullptr, ks, nullptr);
   // z_p ~= S^-1 (r_p - D z_u*): Chebyshev/Jacobi steps on S, or one AMG V-cycle
   if (cfg.s_kind == LFX_SMOOTH_AMG && !amg_ready) {
     set_error("aSIMPLE: the Schur AMG hierarchy has not been built");
@@ -1733,17 +1769,27 @@ lfx_status ASimple<S, T>::apply_view(cudaStream_t st, const View &A, const T *r,
     pdl_launch(g_scaled_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), X.as<T>(), W.as<T>(), ks);
     pdl_launch(s_resid_kernel<View, T>, rg, kThreads, 0, st, A, dinvS.as<T>(), X.as<T>(), W.as<T>(), Bs.as<T>(), nullptr,
                                                   R.as<T>(), d[0], cf, 1, ks);
-    pdl_launch(add_w_kernel<T>, vg, kThreads, 0, st, V, d[0], X.as<T>(), ks);
+    if (cfg.s_steps == 1) {
+      // x.w += d.w is left to the final pass, which reads x.w (own row and neighbours) as x.w + d.w
+      pending_w = true;
+    } else {
+      pdl_launch(add_w_kernel<T>, vg, kThreads, 0, st, V, d[0], X.as<T>(), ks);
+      note_launches(1);
+    }
     for (int k = 1; k < cfg.s_steps; ++k) {
       pdl_launch(g_scaled_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), d[(k - 1) & 1], W.as<T>(), ks);
       pdl_launch(s_step_kernel<View, T>, rg, kThreads, 0, st, A, dinvS.as<T>(), d[(k - 1) & 1], W.as<T>(), d[k & 1],
                                                    R.as<T>(), X.as<T>(), cf, k, 1, nullptr, ks);
     }
-    note_launches(9 + 2 * (cfg.s_steps - 1));
+    note_launches(8 + 2 * (cfg.s_steps - 1));
   }
   // z_u = z_u* - diag(F)^-1 G z_p
-  pdl_launch(final_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), X.as<T>(), z, ks);
-  note_launches(3 + (cfg.f_steps - 1) + 2 * (cfg.s_steps - 1));
+  if (pending_w)
+    pdl_launch(final_kernel<View, T, true>, rg, kThreads, 0, st, A, dinvF.as<T>(), X.as<T>(), z, ks, d[0]);
+  else
+    pdl_launch(final_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), X.as<T>(), z, ks, nullptr);
+  // start (or fused first step) + further F steps + d_init + final + extra Schur steps
+  note_launches(3 + (cfg.f_steps >= 2 ? cfg.f_steps - 2 : 0) + 2 * (cfg.s_steps - 1));
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
 }
