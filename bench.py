@@ -31,11 +31,11 @@ FP64_PEAK_TFLOPS = 1.20            # measured FP64 FMA-throughput probe on this 
 FP32_ISSUE_PEAK_T = 35.96          # measured FP32 FMA-issue probe, T thread-instructions/s
 # FP64-class operations of the method per tetrahedron (DFMA x 2 + DADD + DMUL executed by the FP64
 # assembly kernel, counted with ncu): the algorithmic work of one element's assembly
-ASM_FP64_FLOPS_PER_ELEMENT = 3286
+ASM_FP64_FLOPS_PER_ELEMENT = 2948
 # thread instructions per tetrahedron of the double-float assembly kernel (ncu) and its DRAM
 # bytes per tetrahedron (ncu, one colour launch of 30,832 elements; profiles/)
-ASM_DD_INST_PER_ELEMENT = 42845
-ASM_DD_DRAM_BYTES_PER_ELEMENT = 5297
+ASM_DD_INST_PER_ELEMENT = 42851
+ASM_DD_DRAM_BYTES_PER_ELEMENT = 5284
 # DRAM bytes per block of the FP32 Krylov SpMV (ncu read + write, 2,089,595-block launch)
 SPMV32_DRAM_BYTES_PER_BLOCK = 71.6
 
