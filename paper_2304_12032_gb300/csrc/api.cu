@@ -106,11 +106,14 @@ struct lfx_problem {
   // RIIS nodal signed distances [n_riis][V]
   DBuf d_phi;
   DBuf d_bad;
+  // element geometry computed once per problem (fixed mesh): FP64 (geo64) or double-float
+  // (geo_hi + geo_lo) [kGeoValues][T]
+  DBuf geo64, geo_hi, geo_lo;
   int32_t pin_node = -1;   // internal
   int64_t n_bad = 0;
   size_t device_bytes() const {
     return d_dir_node.bytes + d_dir_bc.bytes + d_S.bytes + d_neu_node.bytes + d_neu_bc.bytes +
-           d_neu_vec.bytes + d_phi.bytes + d_bad.bytes;
+           d_neu_vec.bytes + d_phi.bytes + d_bad.bytes + geo64.bytes + geo_hi.bytes + geo_lo.bytes;
   }
 };
 
@@ -651,6 +654,27 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
     }
     pb->pin_node = m.node_new[o.pin_pressure_node];
   }
+  // ---- element geometry, once: the mesh does not move, so every step reuses it
+  {
+    AssembleArgs A{};
+    A.conn = m.d_conn.as<int4>();
+    A.xyz = m.d_xyz.as<D4>();
+    A.xyz_hi = m.d_xyz_hi.as<float4>();
+    A.xyz_lo = m.d_xyz_lo.as<float4>();
+    A.n_nodes = V;
+    A.n_elems = m.T;
+    const size_t nv = (size_t)kGeoValues * (size_t)std::max<int64_t>(m.T, 1);
+    if (o.precision == LFX_PREC_MIXED) {
+      A.bad = pb->n_bad > 0 ? pb->d_bad.as<uint8_t>() : nullptr;
+      LFX_TRY(pb->geo_hi.alloc(sizeof(float) * nv));
+      LFX_TRY(pb->geo_lo.alloc(sizeof(float) * nv));
+      LFX_TRY(launch_geometry<dd>(0, A, m.T, nullptr, pb->geo_hi.as<float>(), pb->geo_lo.as<float>()));
+    } else {
+      LFX_TRY(pb->geo64.alloc(sizeof(double) * nv));
+      LFX_TRY(launch_geometry<double>(0, A, m.T, pb->geo64.as<double>(), nullptr, nullptr));
+    }
+    LFX_CUDA_TRY(cudaStreamSynchronize(0));
+  }
   *out = pb.release();
   return LFX_OK;
 }
@@ -874,6 +898,10 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
   A.vals_lo = s->vals_lo.as<float>();
   A.rhs_hi = s->rhs_hi.as<float>();
   A.rhs_lo = s->rhs_lo.as<float>();
+  A.n_elems = m.T;
+  A.geo64 = pb->geo64.as<double>();
+  A.geo_hi = pb->geo_hi.as<float>();
+  A.geo_lo = pb->geo_lo.as<float>();
   LFX_CUDA_TRY(cudaEventRecord(s->ea0, st));
   if (mixed) {
     // double-float arithmetic; badly shaped elements keep FP64 geometry

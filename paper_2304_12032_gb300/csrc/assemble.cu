@@ -157,7 +157,7 @@ __device__ __forceinline__ void tet_geometry(const G x[4][3], G gp[12], G Gm[9],
 // Phase 1a (one thread per element): geometry in FP64 (FP64 assembly, or a badly shaped
 // element in mixed assembly), else FP32.
 template <class R>
-__device__ void geom_phase(const AssembleArgs &A, int64_t e, int le, ElemShared<R> &sh) {
+__device__ void element_geometry(const AssembleArgs &A, int64_t e, R gpo[12], R Go[9], R &igg, R &w) {
   const int4 cn = A.conn[e];
   const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
   const bool fp64_geom = std::is_same<R, double>::value || (A.bad && A.bad[e]);
@@ -172,14 +172,14 @@ __device__ void geom_phase(const AssembleArgs &A, int64_t e, int le, ElemShared<
     }
     tet_geometry<double>(x, gp, G, g, v);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) sh.gphi[le][k] = (R)gp[k];
+    for (int k = 0; k < 12; ++k) gpo[k] = (R)gp[k];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) sh.Gm[le][k] = (R)G[k];
-    sh.igg[le] = (R)(1.0 / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
-    sh.w[le] = (R)(0.25 * v);
+    for (int k = 0; k < 9; ++k) Go[k] = (R)G[k];
+    igg = (R)(1.0 / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
+    w = (R)(0.25 * v);
   } else {
     // geometry in the arithmetic type (FP32, or dd from the split coordinates)
-    R x[4][3], gp[12], G[9], g[3], v;
+    R x[4][3], g[3], v;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       R p[4];
@@ -188,13 +188,81 @@ __device__ void geom_phase(const AssembleArgs &A, int64_t e, int le, ElemShared<
       x[a][1] = p[1];
       x[a][2] = p[2];
     }
-    tet_geometry<R>(x, gp, G, g, v);
+    tet_geometry<R>(x, gpo, Go, g, v);
+    igg = cst<R>(1.0) / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    w = cst<R>(0.25) * v;
+  }
+}
+
+// value k of the geometry cache for element e
+template <class R>
+__device__ __forceinline__ R geo_value(const AssembleArgs &A, int k, int64_t e, int64_t T);
+template <>
+__device__ __forceinline__ double geo_value<double>(const AssembleArgs &A, int k, int64_t e, int64_t T) {
+  return A.geo64[k * T + e];
+}
+template <>
+__device__ __forceinline__ dd geo_value<dd>(const AssembleArgs &A, int k, int64_t e, int64_t T) {
+  return dd(A.geo_hi[k * T + e], A.geo_lo[k * T + e]);
+}
+template <>
+__device__ __forceinline__ float geo_value<float>(const AssembleArgs &A, int k, int64_t e, int64_t T) {
+  return A.geo_hi[k * T + e];
+}
+template <class R>
+__device__ __forceinline__ bool has_geo(const AssembleArgs &A) {
+  return std::is_same<R, double>::value ? A.geo64 != nullptr : A.geo_hi != nullptr;
+}
+
+// Phase 1a: geometry of element e into shared memory (one thread per element), when there is no
+// cache
+template <class R>
+__device__ void geom_phase(const AssembleArgs &A, int64_t e, int le, ElemShared<R> &sh) {
+  R igg, w;
+  element_geometry<R>(A, e, sh.gphi[le], sh.Gm[le], igg, w);
+  sh.igg[le] = igg;
+  sh.w[le] = w;
+}
+
+// Phase 1a from the cache: the CTA's threads load kGeoValues values of each of its elements
+// (for a fixed value index, consecutive elements are consecutive in memory)
+template <class R>
+__device__ void geom_load(const AssembleArgs &A, int64_t base, int64_t e1, int64_t T, ElemShared<R> &sh) {
+  for (int idx = threadIdx.x; idx < kGeoValues * kElems; idx += kCta) {
+    const int k = idx / kElems, le = idx % kElems;
+    const int64_t e = base + le;
+    if (e >= e1) continue;
+    const R v = geo_value<R>(A, k, e, T);
+    if (k < 12) sh.gphi[le][k] = v;
+    else if (k < 21) sh.Gm[le][k - 12] = v;
+    else if (k == 21) sh.igg[le] = v;
+    else sh.w[le] = v;
+  }
+}
+
+template <class R>
+__global__ void geometry_kernel(AssembleArgs A, int64_t T, double *out64, float *out_hi, float *out_lo) {
+  pdl_entry();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < T; e += (int64_t)gridDim.x * blockDim.x) {
+    R gp[12], G[9], igg, w, v[kGeoValues];
+    element_geometry<R>(A, e, gp, G, igg, w);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) sh.gphi[le][k] = gp[k];
+    for (int k = 0; k < 12; ++k) v[k] = gp[k];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) sh.Gm[le][k] = G[k];
-    sh.igg[le] = cst<R>(1.0) / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-    sh.w[le] = cst<R>(0.25) * v;
+    for (int k = 0; k < 9; ++k) v[12 + k] = G[k];
+    v[21] = igg;
+    v[22] = w;
+#pragma unroll
+    for (int k = 0; k < kGeoValues; ++k) {
+      if constexpr (std::is_same<R, double>::value) {
+        out64[k * T + e] = v[k];
+      } else if constexpr (std::is_same<R, dd>::value) {
+        out_hi[k * T + e] = v[k].hi;
+        out_lo[k * T + e] = v[k].lo;
+      } else {
+        out_hi[k * T + e] = v[k];
+      }
+    }
   }
 }
 
@@ -481,7 +549,8 @@ __global__ void __launch_bounds__(kCta, MinCtas<R>::value) assemble_color_kernel
   __shared__ ElemShared<R> sh;
   const int t = threadIdx.x;
   for (int64_t base = e0 + (int64_t)blockIdx.x * kElems; base < e1; base += (int64_t)gridDim.x * kElems) {
-    if (t < kElems && base + t < e1) geom_phase<R>(A, base + t, t, sh);
+    if (has_geo<R>(A)) geom_load<R>(A, base, e1, A.n_elems, sh);
+    else if (t < kElems && base + t < e1) geom_phase<R>(A, base + t, t, sh);
     __syncthreads();
     const int le = t >> 2, q = t & 3;
     const bool live = base + le < e1;
@@ -785,6 +854,18 @@ lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysPar
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
 }
+
+template <class R>
+lfx_status launch_geometry(cudaStream_t st, const AssembleArgs &A, int64_t T, double *out64, float *out_hi,
+                           float *out_lo) {
+  if (T == 0) return LFX_OK;
+  note_launches(1);
+  pdl_launch(geometry_kernel<R>, grid_for(T, 128), 128, 0, st, A, T, out64, out_hi, out_lo);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+template lfx_status launch_geometry<double>(cudaStream_t, const AssembleArgs &, int64_t, double *, float *, float *);
+template lfx_status launch_geometry<dd>(cudaStream_t, const AssembleArgs &, int64_t, double *, float *, float *);
 
 template lfx_status launch_assemble<double, double>(cudaStream_t, const AssembleArgs &, const PhysParams &,
                                                     const int32_t *, int, double *);

@@ -28,6 +28,7 @@ struct AssembleArgs {
   const uint8_t *bad;        // [T] FP64 geometry flag (mixed assembly), may be null
   double *rhs;               // [V][4]
   int64_t n_nodes;
+  int64_t n_elems;
   // double-float assembly only: inputs split into FP32 high and low parts (x = hi + lo), the
   // matrix accumulated as high parts (the vals argument) plus low parts, the rhs likewise
   const float4 *xyz_hi, *xyz_lo;
@@ -35,7 +36,19 @@ struct AssembleArgs {
   const float4 *ubdf_hi, *ubdf_lo;
   float *vals_lo;            // [nnzb][16]
   float *rhs_hi, *rhs_lo;    // [V][4]
+  // per-element geometry computed once (the mesh does not move): kGeoValues values per element,
+  // structure of arrays [kGeoValues][T] (grad phi 12, G 9, 1/(g.g), |K|/4); FP64 kernel: geo64;
+  // double-float kernel: geo_hi + geo_lo.  Null: the kernel computes the geometry itself.
+  const double *geo64;
+  const float *geo_hi, *geo_lo;
 };
+constexpr int kGeoValues = 23;
+
+// Fills the geometry cache of the arithmetic type R (double: out64 [kGeoValues][T]; dd: out_hi,
+// out_lo) for the T elements of A.conn.
+template <class R>
+lfx_status launch_geometry(cudaStream_t st, const AssembleArgs &A, int64_t T, double *out64, float *out_hi,
+                           float *out_lo);
 
 constexpr int kMaxDirCoef = 256;
 struct DirCoef {
