@@ -316,8 +316,10 @@ def run_serving(args):
                L.BC(tag=1, kind="dirichlet", profile="parabolic", time="ramp", p=(0.0, Q, 0.0, RAMP), radius=R_CM),
                L.BC(tag=2, kind="neumann", time="constant", p=(0.0,))]
         mesh = L.Mesh.from_synthetic(m)
-        prob = L.Problem(mesh, RHO, MU, DT, 2, bcs, [], L.default_options(gmres_rtol=1e-8))
-        pool.append((m, mesh, prob))
+        prob = L.Problem(mesh, RHO, MU, DT, 2, bcs, [], L.default_options(
+            gmres_rtol=1e-8, precision=args.serve_precision, **({"smoother_bf16": 1} if args.serve_precision == "mixed" else {})))
+        prob64 = prob if args.serve_precision == "fp64" else L.Problem(mesh, RHO, MU, DT, 2, bcs, [], L.default_options(gmres_rtol=1e-8))
+        pool.append((m, mesh, prob, prob64))
     free = torch.cuda.mem_get_info()[0]
     budget = int(args.serve_budget_frac * free)
     n_req = max(1, int(round(args.rate * args.serve_seconds)))
@@ -331,7 +333,7 @@ def run_serving(args):
         arrival += gaps[k]
         while time.perf_counter() - t0 < arrival:
             time.sleep(0.001)
-        m, mesh, prob = pool[picks[k]]
+        m, mesh, prob, _ = pool[picks[k]]
         V = m.n_nodes
         tickets.append(srv.submit(prob, np.zeros((2, V, 3)), np.zeros((2, V)), 0.0, args.req_steps))
         submit_t.append(time.perf_counter() - t0)
@@ -346,11 +348,11 @@ def run_serving(args):
     total_steps = n_req * args.req_steps
     # sequential FP64 GPU: every distinct pool entry stepped alone, scaled by how often it was picked
     seq_ms = 0.0
-    for j, (m, mesh, prob) in enumerate(pool):
+    for j, (m, mesh, _, prob64) in enumerate(pool):
         cnt = int(np.sum(picks == j))
         if cnt == 0:
             continue
-        s1 = L.State(prob, np.zeros((2, m.n_nodes, 3)), np.zeros((2, m.n_nodes)), 0.0)
+        s1 = L.State(prob64, np.zeros((2, m.n_nodes, 3)), np.zeros((2, m.n_nodes)), 0.0)
         s1.step(allow_not_converged=True)
         torch.cuda.synchronize()
         w0 = time.perf_counter()
@@ -366,7 +368,85 @@ def run_serving(args):
             "speedup_vs_sequential": round((total_steps / wall) / (total_steps / (seq_ms * 1e-3)), 3),
             "max_resident": st["max_active"], "budget_bytes": budget, "workers": args.workers,
             "pool_tets": [int(p[0].n_tets) for p in pool], "arrival_rate_req_s": args.rate,
-            "higher_is_better": True, "dtype": "f64", "data": "synthetic"}
+            "higher_is_better": True, "dtype": "f32+f64" if args.serve_precision == "mixed" else "f64",
+            "precision": args.serve_precision, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args):
+    """Batched workload (config 4): args.batch independent pipe and Y-bifurcation meshes of seeded
+    sizes uniform in [args.batch_min, args.batch_max] tets, stepped as ONE system (one coloured
+    assembly launch per colour and one Krylov solve for all of them; per-mesh row normalisation),
+    against the same meshes stepped one after another (FP64 GPU and mixed)."""
+    import torch
+
+    from paper_2304_12032_gb300 import build as B
+
+    B.build()
+    from paper_2304_12032_gb300 import lfx as L
+    from synthetic import batch, bifurcation, cylinder
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.default_rng(4)
+    t0 = time.time()
+    ms = []
+    for i in range(args.batch):
+        nt = int(rng.uniform(args.batch_min, args.batch_max))
+        if i % 2 == 0:
+            r = float(rng.uniform(0.3, 1.2))
+            ms.append(cylinder(r, 8.0 * r, n_tets=nt, seed=1000 + i))
+        else:
+            s_ = float(rng.uniform(0.3, 1.2)) / 0.6
+            ms.append(bifurcation(n_tets=nt, seed=1000 + i, angle_deg=float(rng.uniform(30, 70)),
+                                  r0=0.6 * s_, r1=0.45 * s_, r2=0.4 * s_))
+    tgen = time.time() - t0
+
+    def member_bcs(i, m, stride):
+        out = [L.BC(tag=0 + stride * i, kind="noslip")]
+        if "radius" in m.meta:
+            R = m.meta["radius"]
+            Q = U_PEAK * math.pi * R * R / 2.0
+            out.append(L.BC(tag=1 + stride * i, kind="dirichlet", profile="parabolic", time="ramp",
+                            p=(0.0, Q, 0.0, RAMP), radius=R))
+        else:
+            out.append(L.BC(tag=1 + stride * i, kind="dirichlet", profile="uniform", time="ramp",
+                            p=(0.0, U_PEAK / 2.0, 0.0, RAMP)))
+        for t in sorted(set(np.unique(m.btags).tolist()) - {0, 1}):
+            out.append(L.BC(tag=int(t) + stride * i, kind="neumann", time="constant", p=(0.0,)))
+        return out
+
+    def steps_time(mesh_syn, bcs, precision, n):
+        opts = L.default_options(precision=precision, gmres_rtol=1e-8, **({"smoother_bf16": 1} if precision == "mixed" else {}))
+        prob = L.Problem(L.Mesh.from_synthetic(mesh_syn), RHO, MU, DT, 2, bcs, [], opts)
+        V = mesh_syn.n_nodes
+        st = L.State(prob, np.zeros((2, V, 3)), np.zeros((2, V)), 0.0)
+        for _ in range(args.warmup):
+            st.step(allow_not_converged=True)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        its = [st.step(allow_not_converged=True)["iterations"] for _ in range(n)]
+        torch.cuda.synchronize()
+        return (time.perf_counter() - w0) / n, its
+
+    u = batch(ms)
+    bcs = sum((member_bcs(i, m, 10) for i, m in enumerate(ms)), [])
+    t_batch, its_b = steps_time(u, bcs, "mixed", args.steps)
+    seq = {"fp64": 0.0, "mixed": 0.0}
+    for prec in seq:
+        for i, m in enumerate(ms):
+            t, _ = steps_time(m, member_bcs(0, m, 10), prec, max(2, args.steps // 2))
+            seq[prec] += t
+    value = args.batch / t_batch
+    line = {"metric": "batched: simulation steps/s of independent meshes stepped as one system",
+            "value": round(value, 2), "unit": "simulation-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_batch_step": round(t_batch * 1e3, 3), "higher_is_better": True,
+            "meshes": args.batch, "total_tets": int(u.n_tets), "total_nodes": int(u.n_nodes),
+            "tets_per_mesh": [int(m.n_tets) for m in ms], "krylov_iterations": its_b,
+            "sequential_fp64_sim_steps_per_s": round(args.batch / seq["fp64"], 2),
+            "sequential_mixed_sim_steps_per_s": round(args.batch / seq["mixed"], 2),
+            "speedup_vs_sequential_fp64": round(value / (args.batch / seq["fp64"]), 3),
+            "speedup_vs_sequential_mixed": round(value / (args.batch / seq["mixed"]), 3),
+            "mesh_gen_s": round(tgen, 1), "dtype": "f32+f64", "data": "synthetic"}
     print(json.dumps(line), flush=True)
 
 
@@ -439,7 +519,10 @@ def main():
     ap.add_argument("--tets", type=int, default=1_000_000)
     ap.add_argument("--cpu-sample-tets", type=int, default=40_000)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--mode", default="step", choices=["step", "serving"])
+    ap.add_argument("--mode", default="step", choices=["step", "serving", "batched"])
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch-min", type=int, default=20_000)
+    ap.add_argument("--batch-max", type=int, default=300_000)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--req-steps", type=int, default=100)
@@ -448,9 +531,12 @@ def main():
     ap.add_argument("--pool", type=int, default=4)
     ap.add_argument("--workers", type=int, default=4)
     ap.add_argument("--serve-budget-frac", type=float, default=0.5)
+    ap.add_argument("--serve-precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
     if args.mode == "serving":
         run_serving(args)
+    elif args.mode == "batched":
+        run_batched(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

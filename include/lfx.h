@@ -193,8 +193,10 @@ void lfx_options_default(lfx_options *opt);
 
 typedef struct lfx_problem lfx_problem;
 /* rho, mu > 0 (Section 2.1.2), dt > 0, bdf_order 1..3 (Eq. bdf).  bcs [n_bcs], riis [n_riis]
- * (n_riis <= 8) are copied; opt may be NULL for defaults.  Precomputes the Dirichlet profiles,
- * the Neumann load vectors and the nodal signed distances, all resident on the device. */
+ * (n_riis <= 8) are copied; opt may be NULL for defaults; n_bcs x (H + 1) <= 1024, where H = 1, or
+ * 1 + 2 x (the largest number of Womersley harmonics).  Precomputes the Dirichlet profiles, the
+ * Neumann load vectors, the nodal signed distances and every element's geometry, all resident on
+ * the device (the mesh does not move). */
 lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, double dt,
                               int32_t bdf_order, const lfx_bc *bcs, int32_t n_bcs,
                               const lfx_riis *riis, int32_t n_riis, const lfx_options *opt,

@@ -50,7 +50,7 @@ template <class R>
 lfx_status launch_geometry(cudaStream_t st, const AssembleArgs &A, int64_t T, double *out64, float *out_hi,
                            float *out_lo);
 
-constexpr int kMaxDirCoef = 256;
+constexpr int kMaxDirCoef = 1024;   // n_bcs x (H + 1) boundary terms (an 8 KB kernel parameter)
 struct DirCoef {
   double c[kMaxDirCoef];
 };
