@@ -183,11 +183,17 @@ typedef struct lfx_options {
   int32_t amg_coarse_size;      /* dense solve below this many unknowns; default 2000          */
   double amg_theta;             /* strength threshold on coarse levels; default 0.08           */
   double amg_alpha;             /* scaling of the coarse correction; default 1.0               */
-  /* batching: a mesh made of several disconnected meshes is stepped as one system; with
-   * batch_normalize (default 1) each component's rows are scaled by 1/||its rhs|| so that the
-   * solve meets every component's own relative tolerance */
+  /* batching: a mesh made of several disconnected meshes is stepped as one system.  With
+   * batch_segmented (default 1) the Krylov solvers run one Arnoldi process per component in
+   * lockstep (own Hessenberg matrix, rotations and stopping test ||r_c|| <= rtol ||b_c|| each,
+   * shared launches), so every component takes about the steps it would take alone.  With
+   * batch_segmented = 0 the union is one Krylov system, and batch_normalize (default 1) scales
+   * each component's rows by 1/||its rhs|| every step so that the union's relative tolerance
+   * approximates every component's own (a Schur AMG hierarchy built at an earlier step then
+   * keeps that step's scale, which slows it when the scales drift) */
   int32_t batch_normalize;
-  int32_t reserved[7];
+  int32_t batch_segmented;
+  int32_t reserved[6];
 } lfx_options;
 void lfx_options_default(lfx_options *opt);
 

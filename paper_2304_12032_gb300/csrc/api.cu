@@ -325,6 +325,7 @@ void lfx_options_default(lfx_options *o) {
   o->amg_theta = 0.08;
   o->amg_alpha = 1.0;
   o->batch_normalize = 1;
+  o->batch_segmented = 1;
 }
 
 // barycentre, unit outward normal, area of the faces carrying `tag` (area weighted)
@@ -767,6 +768,15 @@ lfx_status lfx_state_create(lfx_problem *pb, const double *u_hist, const double 
     LFX_TRY(s->pc64.init(V, cfg));
     LFX_TRY(s->gm64.init(V, o.gmres_restart));
   }
+  if (m.n_comp > 1 && o.batch_segmented) {
+    // one Arnoldi process per component of a batched mesh
+    if (o.precision == LFX_PREC_MIXED) {
+      LFX_TRY(s->gm32.set_segments(m.comp_off));
+      LFX_TRY(s->gmdd.set_segments(m.comp_off));
+    } else {
+      LFX_TRY(s->gm64.set_segments(m.comp_off));
+    }
+  }
   LFX_CUDA_TRY(cudaEventCreate(&s->e0));
   LFX_CUDA_TRY(cudaEventCreate(&s->e1));
   LFX_CUDA_TRY(cudaEventCreate(&s->e2));
@@ -958,7 +968,10 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
     LFX_TRY(launch_apply_dirichlet<double>(st, nd, pb->d_dir_node.as<int32_t>(), s->gdir.as<D4>(), pb->pin_node,
                                            s->pin_value, m.d_rowptr.as<int32_t>(), m.d_diag.as<int32_t>(),
                                            s->vals64.as<double>(), s->rhs.as<double>(), s->xsol.as<double>()));
-  if (m.n_comp > 1 && pb->opt.batch_normalize) {
+  // (segmented solves test every component against its own ||b_c|| and need no scaling; the
+  // Jacobi-scaled smoothers are invariant under it, but a Schur AMG hierarchy built at an earlier
+  // step is not: its coarse operators keep that step's scale)
+  if (m.n_comp > 1 && pb->opt.batch_normalize && !pb->opt.batch_segmented) {
     if (mixed)
       LFX_TRY(launch_comp_normalize_dd(st, m.V, m.n_comp, m.d_comp_off.as<int32_t>(), s->comp_scale.as<double>(),
                                        m.d_rowptr.as<int32_t>(), s->vals32.as<float>(), s->vals_lo.as<float>(),

@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <type_traits>
 
 #include "amg.h"
@@ -1510,6 +1511,383 @@ __global__ void update_x_kernel(const T *Zb, int64_t ld, X *x, int64_t n, const 
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Segmented Krylov kernels.  A batch of independent problems (the connected components of a
+// batched mesh: contiguous node ranges, a block-diagonal matrix) runs one Arnoldi process per
+// component in lockstep: every component has its own Hessenberg matrix, rotations, tolerance
+// and convergence test, exactly as if it were solved alone.  Reductions run over "tasks",
+// node ranges of at most kSegNodes nodes inside one component, one CTA each; a component that
+// has converged carries zero basis vectors until the shared status word ks0 (read by every
+// kernel for early exit, preconditioner included) says that all components have finished.
+// ------------------------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(kThreads) seg_norm_kernel(const T *v, SegTasks tk, double *pn, const KState *st) {
+  pdl_entry();
+  if (finished(st)) return;
+  using V4 = typename Vec4T<T>::type;
+  using A = typename AccT<T>::type;
+  const int t = blockIdx.x;
+  const V4 *v4 = reinterpret_cast<const V4 *>(v);
+  A a = A(0);
+  for (int64_t i = tk.lo[t] + threadIdx.x; i < tk.hi[t]; i += blockDim.x) {
+    const V4 q = v4[i];
+    a += (A)q.x * (A)q.x + (A)q.y * (A)q.y + (A)q.z * (A)q.z + (A)q.w * (A)q.w;
+  }
+  const double s = cta_sum_t(a);
+  if (threadIdx.x == 0) pn[t] = s;
+}
+
+__device__ __forceinline__ double seg_sum(const double *pn, const SegTasks &tk, int c) {
+  double s = 0.0;
+  for (int t = tk.task_off[c]; t < tk.task_off[c + 1]; ++t) s += pn[t];
+  return s;
+}
+
+// ||b_c|| and tol_c = rtol ||b_c|| per component; ks0 gets ||b|| over all components
+__global__ void seg_bnorm_kernel(const double *pn, SegTasks tk, KState *kseg, KState *ks0, double rtol) {
+  pdl_entry();
+  __shared__ double tot[kThreads];
+  double mine = 0.0;
+  for (int c = threadIdx.x; c < tk.n_seg; c += blockDim.x) {
+    const double s = seg_sum(pn, tk, c);
+    mine += s;
+    kseg[c].bnorm = sqrt(s);
+    kseg[c].tol_abs = rtol * sqrt(s);
+    kseg[c].total = 0;
+  }
+  tot[threadIdx.x] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) s += tot[i];
+    ks0->bnorm = sqrt(s);
+    ks0->tol_abs = rtol * sqrt(s);
+    ks0->total = 0;
+    ks0->done = 0;
+    ks0->flag = 0;
+  }
+}
+
+// x_c = 0 for components with b_c = 0 (their solution), so that they start converged
+template <class X>
+__global__ void __launch_bounds__(kThreads) seg_zero_x_kernel(X *x, SegTasks tk, const KState *kseg) {
+  pdl_entry();
+  const int t = blockIdx.x;
+  if (kseg[tk.seg[t]].bnorm != 0.0) return;
+  for (int64_t e = 4 * tk.lo[t] + threadIdx.x; e < 4 * tk.hi[t]; e += blockDim.x) x[e] = X(0);
+}
+
+// start of a cycle: beta_c = ||r_c||, g_c = (beta_c, 0, ...), j_c = 0, done_c if beta_c <= tol_c
+__global__ void seg_cycle_start_kernel(const double *pn, SegTasks tk, KState *kseg, KState *ks0) {
+  pdl_entry();
+  __shared__ int all_done, any_bad;
+  if (threadIdx.x == 0) {
+    all_done = 1;
+    any_bad = 0;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < tk.n_seg; c += blockDim.x) {
+    KState &k = kseg[c];
+    const double beta = sqrt(seg_sum(pn, tk, c));
+    k.beta = beta;
+    k.g[0] = beta;
+    k.j = 0;
+    k.res = beta;
+    k.flag = 0;
+    k.done = 0;
+    k.scale = 0.0;
+    if (!isfinite(beta)) {
+      k.flag = 2;
+      k.done = 1;
+      atomicExch(&any_bad, 1);
+    } else if (beta <= k.tol_abs) {
+      k.flag = 1;
+      k.done = 1;
+    }
+    if (!k.done) atomicExch(&all_done, 0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ks0->j = 0;
+    ks0->flag = any_bad ? 2 : (all_done ? 1 : 0);
+    ks0->done = (all_done || any_bad) ? 1 : 0;
+  }
+}
+
+// v = r / beta_c over each task's nodes (zero for components that start converged)
+template <class T>
+__global__ void __launch_bounds__(kThreads) seg_scale_beta_kernel(const T *w, T *v, SegTasks tk, const KState *kseg) {
+  pdl_entry();
+  using V4 = typename Vec4T<T>::type;
+  using A = typename AccT<T>::type;
+  const int t = blockIdx.x;
+  const KState &k = kseg[tk.seg[t]];
+  const A s = (A)((k.done || !(k.beta > 0.0)) ? 0.0 : 1.0 / k.beta);
+  const V4 *w4 = reinterpret_cast<const V4 *>(w);
+  V4 *v4 = reinterpret_cast<V4 *>(v);
+  for (int64_t i = tk.lo[t] + threadIdx.x; i < tk.hi[t]; i += blockDim.x) {
+    const V4 q = w4[i];
+    V4 o;
+    o.x = (T)((A)q.x * s);
+    o.y = (T)((A)q.y * s);
+    o.z = (T)((A)q.z * s);
+    o.w = (T)((A)q.w * s);
+    v4[i] = o;
+  }
+}
+
+// part[i][task] = the task's share of w . v_i, i < nvec; blockIdx.y selects eight vectors
+template <class T>
+__global__ void __launch_bounds__(kThreads) seg_mdot_kernel(const T *Vb, int64_t ld, int nvec, const T *w,
+                                                            double *part, SegTasks tk, const KState *st) {
+  pdl_entry();
+  if (finished(st)) return;
+  using V4 = typename Vec4T<T>::type;
+  using A = typename AccT<T>::type;
+  __shared__ double red[8][kThreads / 32];
+  const int t = blockIdx.x, v0 = 8 * blockIdx.y;
+  if (v0 >= nvec) return;
+  const int nv = min(8, nvec - v0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ld4 = ld >> 2;
+  const V4 *w4 = reinterpret_cast<const V4 *>(w);
+  const V4 *b4 = reinterpret_cast<const V4 *>(Vb);
+  A acc[8] = {A(0), A(0), A(0), A(0), A(0), A(0), A(0), A(0)};
+  for (int64_t i = tk.lo[t] + threadIdx.x; i < tk.hi[t]; i += blockDim.x) {
+    const V4 wv = w4[i];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < nv) {
+        const V4 b = b4[(int64_t)(v0 + k) * ld4 + i];
+        acc[k] += (A)wv.x * (A)b.x + (A)wv.y * (A)b.y + (A)wv.z * (A)b.z + (A)wv.w * (A)b.w;
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    A a = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) red[k][warp] = (double)a;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nv) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
+    part[(int64_t)(v0 + threadIdx.x) * tk.n_task + t] = s;
+  }
+}
+
+// h_c[i] = sum of component c's task shares; hcol (+)= h, hwork = h.  One warp per (c, i).
+__global__ void seg_finalize_kernel(const double *part, int nvec, SegTasks tk, KState *kseg, const KState *st,
+                                    int accumulate) {
+  pdl_entry();
+  if (finished(st)) return;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= (int64_t)tk.n_seg * nvec) return;
+  const int c = (int)(gw / nvec), i = (int)(gw % nvec);
+  double s = 0.0;
+  for (int t = tk.task_off[c] + lane; t < tk.task_off[c + 1]; t += 32) s += part[(int64_t)i * tk.n_task + t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    kseg[c].hwork[i] = s;
+    kseg[c].hcol[i] = accumulate ? kseg[c].hcol[i] + s : s;
+  }
+}
+
+// w -= sum_i h_c[i] v_i over each task's nodes; the task's share of |w|^2
+template <class T>
+__global__ void __launch_bounds__(kThreads) seg_maxpy_kernel(const T *Vb, int64_t ld, int nvec, T *w, SegTasks tk,
+                                                             const KState *kseg, double *pn, const KState *st) {
+  pdl_entry();
+  if (finished(st)) return;
+  using V4 = typename Vec4T<T>::type;
+  using A = typename AccT<T>::type;
+  __shared__ A h[kMaxRestart + 1];
+  const int t = blockIdx.x;
+  const KState &kc = kseg[tk.seg[t]];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) h[i] = (A)kc.hwork[i];
+  __syncthreads();
+  const int64_t ld4 = ld >> 2;
+  V4 *w4 = reinterpret_cast<V4 *>(w);
+  const V4 *b4 = reinterpret_cast<const V4 *>(Vb);
+  A nrm = A(0);
+  for (int64_t i = tk.lo[t] + threadIdx.x; i < tk.hi[t]; i += blockDim.x) {
+    const V4 wv = w4[i];
+    A a0 = (A)wv.x, a1 = (A)wv.y, a2 = (A)wv.z, a3 = (A)wv.w;
+#pragma unroll 4
+    for (int k = 0; k < nvec; ++k) {
+      const V4 b = b4[(int64_t)k * ld4 + i];
+      const A hk = h[k];
+      a0 -= hk * (A)b.x;
+      a1 -= hk * (A)b.y;
+      a2 -= hk * (A)b.z;
+      a3 -= hk * (A)b.w;
+    }
+    V4 o;
+    o.x = (T)a0;
+    o.y = (T)a1;
+    o.z = (T)a2;
+    o.w = (T)a3;
+    w4[i] = o;
+    nrm += a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3;
+  }
+  const double s = cta_sum_t(nrm);
+  if (threadIdx.x == 0) pn[t] = s;
+}
+
+// Arnoldi column j of every running component: h_{j+1,j} = ||w_c||, Givens rotations, residual
+// estimate and stopping test; ks0 finishes when every component has, or at the restart length
+// or the step limit.
+__global__ void seg_givens_kernel(const double *pn, SegTasks tk, KState *kseg, KState *ks0, int j, int m, int maxit) {
+  pdl_entry();
+  if (finished(ks0)) return;
+  __shared__ int all_done, any_bad;
+  if (threadIdx.x == 0) {
+    all_done = 1;
+    any_bad = 0;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < tk.n_seg; c += blockDim.x) {
+    KState &k = kseg[c];
+    if (k.done) {
+      k.scale = 0.0;
+      continue;
+    }
+    const double hn = sqrt(seg_sum(pn, tk, c));
+    double *H = k.H + (int64_t)j * (kMaxRestart + 1);
+    for (int i = 0; i <= j; ++i) H[i] = k.hcol[i];
+    H[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double q = k.cs[i] * H[i] + k.sn[i] * H[i + 1];
+      H[i + 1] = -k.sn[i] * H[i] + k.cs[i] * H[i + 1];
+      H[i] = q;
+    }
+    const double den = hypot(H[j], H[j + 1]);
+    double cc = 1.0, sn = 0.0;
+    if (den > 0.0) {
+      cc = H[j] / den;
+      sn = H[j + 1] / den;
+    }
+    k.cs[j] = cc;
+    k.sn[j] = sn;
+    H[j] = den;
+    H[j + 1] = 0.0;
+    k.g[j + 1] = -sn * k.g[j];
+    k.g[j] = cc * k.g[j];
+    const double res = fabs(k.g[j + 1]);
+    k.j = j + 1;
+    k.total += 1;
+    k.res = res;
+    k.scale = hn > 0.0 ? 1.0 / hn : 0.0;
+    if (!isfinite(res) || !isfinite(hn)) {
+      k.flag = 2;
+      k.done = 1;
+      atomicExch(&any_bad, 1);
+    } else if (res <= k.tol_abs || hn == 0.0) {
+      k.flag = 1;
+      k.done = 1;
+    }
+    if (k.done) k.scale = 0.0;
+    else atomicExch(&all_done, 0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ks0->j = j + 1;
+    ks0->total += 1;
+    ks0->flag = any_bad ? 2 : (all_done ? 1 : 0);
+    if (all_done || any_bad || j + 1 >= m || ks0->total >= maxit) ks0->done = 1;
+  }
+}
+
+// v_{j+1} = w scale_c (zero for components that have finished)
+template <class T>
+__global__ void __launch_bounds__(kThreads) seg_scale_kernel(const T *w, T *v, SegTasks tk, const KState *kseg,
+                                                             const KState *st) {
+  pdl_entry();
+  if (finished(st)) return;
+  using V4 = typename Vec4T<T>::type;
+  using A = typename AccT<T>::type;
+  const int t = blockIdx.x;
+  const A s = (A)kseg[tk.seg[t]].scale;
+  const V4 *w4 = reinterpret_cast<const V4 *>(w);
+  V4 *v4 = reinterpret_cast<V4 *>(v);
+  for (int64_t i = tk.lo[t] + threadIdx.x; i < tk.hi[t]; i += blockDim.x) {
+    const V4 q = w4[i];
+    V4 o;
+    o.x = (T)((A)q.x * s);
+    o.y = (T)((A)q.y * s);
+    o.z = (T)((A)q.z * s);
+    o.w = (T)((A)q.w * s);
+    v4[i] = o;
+  }
+}
+
+// y_c = H_c(0:j_c, 0:j_c)^-1 g_c by back substitution, one thread per component
+__global__ void seg_trisolve_kernel(SegTasks tk, KState *kseg) {
+  pdl_entry();
+  for (int c = threadIdx.x; c < tk.n_seg; c += blockDim.x) {
+    KState &k = kseg[c];
+    const int j = k.j;
+    for (int i = j - 1; i >= 0; --i) {
+      double s = k.g[i];
+      for (int q = i + 1; q < j; ++q) s -= k.H[(int64_t)q * (kMaxRestart + 1) + i] * k.y[q];
+      const double d = k.H[(int64_t)i * (kMaxRestart + 1) + i];
+      k.y[i] = d != 0.0 ? s / d : 0.0;   // d = 0 only after a breakdown (w = 0)
+    }
+  }
+}
+
+// x += sum_{i < j_c} y_c[i] z_i over each task's nodes
+template <class T, class X>
+__global__ void __launch_bounds__(kThreads) seg_update_x_kernel(const T *Zb, int64_t ld, X *x, SegTasks tk,
+                                                                const KState *kseg) {
+  pdl_entry();
+  using A = typename AccT<T, X>::type;
+  __shared__ A y[kMaxRestart];
+  const int t = blockIdx.x;
+  const KState &k = kseg[tk.seg[t]];
+  const int j = k.j;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) y[i] = (A)k.y[i];
+  __syncthreads();
+  for (int64_t e = 4 * tk.lo[t] + threadIdx.x; e < 4 * tk.hi[t]; e += blockDim.x) {
+    A a = (A)x[e];
+#pragma unroll 4
+    for (int i = 0; i < j; ++i) a += y[i] * (A)Zb[(int64_t)i * ld + e];
+    x[e] = (X)a;
+  }
+}
+
+// true residual per component (pn = task shares of |b - A x|^2): ks0->res = the largest
+// ||r_c|| / ||b_c||, ks0->flag = 1 if every ||r_c|| <= 2 tol_c
+__global__ void seg_confirm_kernel(const double *pn, SegTasks tk, const KState *kseg, KState *ks0) {
+  pdl_entry();
+  __shared__ double worst[kThreads];
+  __shared__ int all_ok, any_bad;
+  if (threadIdx.x == 0) {
+    all_ok = 1;
+    any_bad = 0;
+  }
+  __syncthreads();
+  double w = 0.0;
+  for (int c = threadIdx.x; c < tk.n_seg; c += blockDim.x) {
+    const double tr = sqrt(seg_sum(pn, tk, c));
+    const double b = kseg[c].bnorm;
+    if (!isfinite(tr)) atomicExch(&any_bad, 1);
+    if (!(tr <= 2.0 * kseg[c].tol_abs)) atomicExch(&all_ok, 0);
+    if (b > 0.0) w = fmax(w, tr / b);
+  }
+  worst[threadIdx.x] = w;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) m = fmax(m, worst[i]);
+    ks0->res = any_bad ? NAN : m;
+    ks0->flag = all_ok;
+  }
+}
+
 inline int rows_grid(int64_t V) { return (int)((V * kRowGroup + kThreads - 1) / kThreads); }
 // grid for a CSR kernel with G lanes per row over n rows
 inline int lanes_grid(int64_t n, int G) { return (int)std::max<int64_t>(1, (n * G + kThreads - 1) / kThreads); }
@@ -2056,7 +2434,8 @@ Gmres<S, T>::~Gmres() {
 
 template <class S, class T>
 size_t Gmres<S, T>::device_bytes() const {
-  return basis.bytes + zbasis.bytes + work.bytes + part.bytes + part_n.bytes + state.bytes;
+  return basis.bytes + zbasis.bytes + work.bytes + part.bytes + part_n.bytes + state.bytes + seg_lo.bytes +
+         seg_hi.bytes + seg_id.bytes + seg_toff.bytes + seg_state.bytes + seg_part.bytes + seg_pn.bytes;
 }
 
 // Solve A x = b to ||b - A x|| <= rtol ||b|| from the x passed in.  Returns LFX_OK,
@@ -2066,6 +2445,7 @@ template <class S, class T>
 lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, const T *b, T *x,
                               double rtol, int maxit, bool cgs2, int lag, bool x_zero, int *its_out,
                               double *res_out) {
+  if (n_seg > 1) return solve_seg(st, A, pc, b, x, rtol, maxit, cgs2, lag, x_zero, its_out, res_out);
   if (lag < 0) lag = 0;
   if (lag > 2) lag = 2;
   KState *ks = state.as<KState>();
@@ -2170,6 +2550,167 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
       }
       if (total >= maxit) {
         set_error("GMRES: not converged after %d steps (relative residual %.3e)", total, rel);
+        status = LFX_ERR_NOT_CONVERGED;
+        break;
+      }
+    }
+  }
+  if (its_out) *its_out = total;
+  if (res_out) *res_out = rel;
+  return status;
+}
+
+
+template <class S, class T>
+lfx_status Gmres<S, T>::set_segments(const std::vector<int32_t> &comp_off) {
+  const int ns = (int)comp_off.size() - 1;
+  if (ns < 1 || comp_off[0] != 0 || comp_off[ns] != V) {
+    set_error("GMRES: component offsets do not cover the %lld nodes", (long long)V);
+    return LFX_ERR_INVALID_ARG;
+  }
+  std::vector<int64_t> lo, hi;
+  std::vector<int32_t> id, toff(1, 0);
+  for (int c = 0; c < ns; ++c) {
+    const int64_t a = comp_off[c], b = comp_off[c + 1];
+    if (b < a) {
+      set_error("GMRES: component offsets are not increasing");
+      return LFX_ERR_INVALID_ARG;
+    }
+    const int64_t nt = std::max<int64_t>(1, (b - a + kSegNodes - 1) / kSegNodes);
+    for (int64_t t = 0; t < nt; ++t) {
+      lo.push_back(a + (b - a) * t / nt);
+      hi.push_back(a + (b - a) * (t + 1) / nt);
+      id.push_back(c);
+    }
+    toff.push_back((int32_t)lo.size());
+  }
+  const int nt = (int)lo.size();
+  LFX_TRY(seg_lo.alloc(sizeof(int64_t) * nt));
+  LFX_TRY(seg_hi.alloc(sizeof(int64_t) * nt));
+  LFX_TRY(seg_id.alloc(sizeof(int32_t) * nt));
+  LFX_TRY(seg_toff.alloc(sizeof(int32_t) * (ns + 1)));
+  LFX_TRY(seg_state.alloc(sizeof(KState) * (size_t)ns));
+  LFX_TRY(seg_part.alloc(sizeof(double) * (size_t)nt * (kMaxRestart + 1)));
+  LFX_TRY(seg_pn.alloc(sizeof(double) * (size_t)nt));
+  LFX_CUDA_TRY(cudaMemcpy(seg_lo.p, lo.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemcpy(seg_hi.p, hi.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemcpy(seg_id.p, id.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemcpy(seg_toff.p, toff.data(), sizeof(int32_t) * (ns + 1), cudaMemcpyHostToDevice));
+  LFX_CUDA_TRY(cudaMemset(seg_state.p, 0, sizeof(KState) * (size_t)ns));
+  tasks = SegTasks{seg_lo.as<int64_t>(), seg_hi.as<int64_t>(), seg_id.as<int32_t>(), seg_toff.as<int32_t>(), nt, ns};
+  n_seg = ns;
+  return LFX_OK;
+}
+
+// The header of a KState (status words and scalars), read back by the host
+static constexpr size_t kStateHead = offsetof(KState, H);
+
+// Restarted GMRES over n_seg independent components (see set_segments); the same launches as
+// solve, with every reduction and every small dense step done per component.
+template <class S, class T>
+lfx_status Gmres<S, T>::solve_seg(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, const T *b, T *x,
+                                  double rtol, int maxit, bool cgs2, int lag, bool x_zero, int *its_out,
+                                  double *res_out) {
+  if (lag < 0) lag = 0;
+  if (lag > 2) lag = 2;
+  KState *ks = state.as<KState>(), *kseg = seg_state.as<KState>();
+  T *Vb = basis.as<T>(), *Zb = zbasis.as<T>(), *w = work.as<T>();
+  double *pn = seg_pn.as<double>(), *pd = seg_part.as<double>();
+  const SegTasks tk = tasks;
+  const int nt = tk.n_task;
+  // ||b_c||, tolerances; ks gets ||b||
+  pdl_launch(seg_norm_kernel<T>, nt, kThreads, 0, st, b, tk, pn, nullptr);
+  pdl_launch(seg_bnorm_kernel, 1, kThreads, 0, st, pn, tk, kseg, ks, rtol);
+  note_launches(2);
+  KState hs;
+  LFX_CUDA_TRY(cudaMemcpyAsync(&hs, ks, kStateHead, cudaMemcpyDeviceToHost, st));
+  LFX_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!std::isfinite(hs.bnorm)) {
+    set_error("GMRES: right-hand side is not finite");
+    return LFX_ERR_NONFINITE;
+  }
+  if (hs.bnorm == 0.0 || x_zero) LFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
+  if (hs.bnorm == 0.0) {
+    if (its_out) *its_out = 0;
+    if (res_out) *res_out = 0.0;
+    return LFX_OK;
+  }
+  if (!x_zero) {
+    pdl_launch(seg_zero_x_kernel<T>, nt, kThreads, 0, st, x, tk, kseg);
+    note_launches(1);
+  }
+  int total = 0;
+  double rel = 1.0;
+  lfx_status status = LFX_ERR_NOT_CONVERGED;
+  const int fin_grid = (int)(((int64_t)n_seg * (restart + 1) * 32 + kThreads - 1) / kThreads);
+  for (int cycle = 0; cycle < 100000; ++cycle) {
+    // r = b - A x -> w; beta_c; v0 = r / beta_c
+    LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, nullptr, nullptr)));
+    pdl_launch(seg_norm_kernel<T>, nt, kThreads, 0, st, w, tk, pn, nullptr);
+    pdl_launch(seg_cycle_start_kernel, 1, kThreads, 0, st, pn, tk, kseg, ks);
+    pdl_launch(seg_scale_beta_kernel<T>, nt, kThreads, 0, st, w, Vb, tk, kseg);
+    note_launches(3);
+    for (int j = 0; j < restart; ++j) {
+      T *vj = Vb + (int64_t)j * n, *vn = Vb + (int64_t)(j + 1) * n, *zj = Zb + (int64_t)j * n;
+      LFX_TRY(pc(st, vj, zj, ks));
+      if (n_tev + 2 > (int)tev.size()) {
+        for (int q = 0; q < 64; ++q) {
+          cudaEvent_t e;
+          LFX_CUDA_TRY(cudaEventCreate(&e));
+          tev.push_back(e);
+        }
+      }
+      LFX_CUDA_TRY(cudaEventRecord(tev[n_tev], st));
+      arnoldi_spmv(st, A, zj, w, ks);
+      LFX_CUDA_TRY(cudaEventRecord(tev[n_tev + 1], st));
+      n_tev += 2;
+      for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
+        pdl_launch(seg_mdot_kernel<T>, dim3(nt, (j + 8) / 8), kThreads, 0, st, Vb, n, j + 1, w, pd, tk, ks);
+        pdl_launch(seg_finalize_kernel, fin_grid, kThreads, 0, st, pd, j + 1, tk, kseg, ks, pass);
+        pdl_launch(seg_maxpy_kernel<T>, nt, kThreads, 0, st, Vb, n, j + 1, w, tk, kseg, pn, ks);
+      }
+      pdl_launch(seg_givens_kernel, 1, kThreads, 0, st, pn, tk, kseg, ks, j, restart, maxit);
+      pdl_launch(seg_scale_kernel<T>, nt, kThreads, 0, st, w, vn, tk, kseg, ks);
+      note_launches(2 + 3 * (cgs2 ? 2 : 1));
+      LFX_CUDA_TRY(cudaMemcpyAsync(pinned + (j & 3), &ks->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+      LFX_CUDA_TRY(cudaEventRecord(ev[j & 3], st));
+      if (j >= lag) {
+        LFX_CUDA_TRY(cudaEventSynchronize(ev[(j - lag) & 3]));
+        if (pinned[(j - lag) & 3]) break;
+      }
+    }
+    pdl_launch(seg_trisolve_kernel, 1, kThreads, 0, st, tk, kseg);
+    pdl_launch(seg_update_x_kernel<T, T>, nt, kThreads, 0, st, Zb, n, x, tk, kseg);
+    note_launches(2);
+    LFX_CUDA_TRY(cudaMemcpyAsync(&hs, ks, kStateHead, cudaMemcpyDeviceToHost, st));
+    LFX_CUDA_TRY(cudaStreamSynchronize(st));
+    LFX_CUDA_TRY(cudaGetLastError());
+    total = hs.total;
+    if (hs.flag == 2) {
+      set_error("GMRES: non-finite residual after %d steps", total);
+      status = LFX_ERR_NONFINITE;
+      break;
+    }
+    if (hs.flag == 1 || total >= maxit) {
+      // confirm with every component's true residual
+      LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, nullptr, nullptr)));
+      pdl_launch(seg_norm_kernel<T>, nt, kThreads, 0, st, w, tk, pn, nullptr);
+      pdl_launch(seg_confirm_kernel, 1, kThreads, 0, st, pn, tk, kseg, ks);
+      note_launches(2);
+      LFX_CUDA_TRY(cudaMemcpyAsync(&hs, ks, kStateHead, cudaMemcpyDeviceToHost, st));
+      LFX_CUDA_TRY(cudaStreamSynchronize(st));
+      rel = hs.res;
+      if (!std::isfinite(rel)) {
+        status = LFX_ERR_NONFINITE;
+        set_error("GMRES: non-finite true residual");
+        break;
+      }
+      if (hs.flag == 1) {
+        status = LFX_OK;
+        break;
+      }
+      if (total >= maxit) {
+        set_error("GMRES: not converged after %d steps (largest relative residual %.3e)", total, rel);
         status = LFX_ERR_NOT_CONVERGED;
         break;
       }

@@ -42,6 +42,17 @@ struct KState {
   double hcol[kMaxRestart + 1], hwork[kMaxRestart + 1];
 };
 
+// Independent problems solved together: node ranges of the components of a block-diagonal
+// system, cut into tasks of at most kSegNodes nodes (one CTA each) that never straddle two
+// components.  Device arrays.
+constexpr int64_t kSegNodes = 2048;
+struct SegTasks {
+  const int64_t *lo, *hi;     // [n_task] node range of each task
+  const int32_t *seg;         // [n_task] component of each task
+  const int32_t *task_off;    // [n_seg + 1] first task of each component
+  int n_task, n_seg;
+};
+
 struct AmgHost;
 
 // One explicit level (l >= 1) of the Schur AMG hierarchy on the device, and the transfer
@@ -129,7 +140,19 @@ struct Gmres {
   lfx_status solve(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, const T *b, T *x,
                    double rtol, int maxit, bool cgs2, int lag, bool x_zero, int *its_out,
                    double *res_out);
+  // From now on solve the components [comp_off[c], comp_off[c+1]) (node ranges; A must be block
+  // diagonal over them and the preconditioner must not couple them) as separate problems: one
+  // Arnoldi process per component, each stopped by its own test ||b_c - A x_c|| <= rtol ||b_c||.
+  // *its_out is then the largest step count, *res_out the largest relative residual.
+  lfx_status set_segments(const std::vector<int32_t> &comp_off);
   size_t device_bytes() const;
+
+ private:
+  int n_seg = 0;
+  SegTasks tasks{};
+  DBuf seg_lo, seg_hi, seg_id, seg_toff, seg_state, seg_part, seg_pn;
+  lfx_status solve_seg(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, const T *b, T *x,
+                       double rtol, int maxit, bool cgs2, int lag, bool x_zero, int *its_out, double *res_out);
 };
 
 }  // namespace lfx

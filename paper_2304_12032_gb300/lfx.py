@@ -61,7 +61,8 @@ class lfx_options(ctypes.Structure):
                 ("inner_max_iters", ctypes.c_int32), ("bad_element_quality", ctypes.c_double),
                 ("amg_refresh", ctypes.c_int32), ("amg_coarse_size", ctypes.c_int32),
                 ("amg_theta", ctypes.c_double), ("amg_alpha", ctypes.c_double),
-                ("batch_normalize", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("batch_normalize", ctypes.c_int32), ("batch_segmented", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class lfx_mesh_info(ctypes.Structure):
