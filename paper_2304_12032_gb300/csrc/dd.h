@@ -124,6 +124,20 @@ LFX_HD dd operator/(dd a, dd b) {
 // a * b + c
 LFX_HD dd fma_dd(dd a, dd b, dd c) { return a * b + c; }
 
+// a * b + c in one pass: the product of the high parts and its sum with c.hi are exact (two_prod,
+// two_sum); the cross products and every low-order part are summed in FP32, then renormalised.
+// 15 FP32 operations against 27 for fma_dd.  The error is a few units of 2^-47 of
+// max(|a b|, |c|) (not of the result: under cancellation the relative error of the result grows),
+// which is the accuracy an accumulation of terms needs when its error is judged against the
+// terms' own magnitude.
+LFX_HD dd fma_dd_fast(dd a, dd b, dd c) {
+  const dd p = two_prod(a.hi, b.hi);
+  float e = f_fma(a.hi, b.lo, p.lo);
+  e = f_fma(a.lo, b.hi, e);
+  const dd s = two_sum(p.hi, c.hi);
+  e = f_add(e, f_add(c.lo, s.lo));
+  return fast_two_sum(s.hi, e);
+}
 LFX_HD dd &operator+=(dd &a, dd b) { return a = a + b; }
 LFX_HD dd &operator-=(dd &a, dd b) { return a = a - b; }
 LFX_HD dd &operator*=(dd &a, dd b) { return a = a * b; }

@@ -144,6 +144,11 @@ struct PhysParams {
   double riis_inv2eps[kMaxRiis]; // 1 / (2 eps_k)
 };
 
+// Elements the double-float assembly kernel processes in one wave over the whole device (resident
+// CTAs per SM x SMs x elements per CTA; GB300's 152 SMs x 4 x 32 when no device answers): the
+// quantum the element colouring is balanced to.
+int64_t assemble_wave_elements();
+
 }  // namespace lfx
 
 // opaque handles of the C ABI

@@ -34,6 +34,83 @@ inline uint64_t morton(const double *p, const double *lo, double inv_span) {
   return spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
 }
 
+// Colour sizes rebalanced toward whole waves of the assembly kernel.  A colour of s elements runs
+// as ceil(s / W) waves of W elements (W = resident CTAs x elements per CTA over all SMs), and
+// colours run one after another, so the greedy colouring's decreasing sizes (a 1M-tet mesh: 52.5
+// waves of work in 38 colours, launched as 68 waves) waste most of a wave per colour.  The colour
+// count stays (it is bounded below by the largest number of elements at one node); each colour
+// gets a target of k_c >= 1 whole waves, the extra waves going to the colours with the most
+// elements above their target, until the targets hold all T elements with a quarter wave to
+// spare.  Elements then move from over-full colours to the under-full colour with the most room
+// among those free at all four of their nodes (in practice from the large early colours up into
+// the sparse late ones, which the greedy pass left free almost everywhere), so the colouring
+// stays valid whatever the moves achieve.  Deterministic; returns the colour count.
+int balance_colours(int64_t T, const std::vector<int32_t> &tt, const std::vector<int32_t> &eorder,
+                    std::vector<uint64_t> &used, std::vector<int32_t> &color, int C, int kWords, int64_t W) {
+  if (W <= 0 || C < 2) return C;
+  std::vector<int64_t> sz(C, 0), k(C, 1);
+  for (int64_t e = 0; e < T; ++e) sz[color[e]]++;
+  if (*std::max_element(sz.begin(), sz.end()) <= W) return C;   // every colour is one wave or less
+  int64_t waves = C;
+  while (waves * W < T + W / 4) {
+    int best = 0;
+    for (int c = 1; c < C; ++c)
+      if (sz[c] - k[c] * W > sz[best] - k[best] * W) best = c;
+    ++k[best];
+    ++waves;
+  }
+  auto bit = [&](int32_t n, int c) { return (used[(size_t)n * kWords + c / 64] >> (c % 64)) & 1ULL; };
+  // passes of moves; when elements are left over, the last colour that can still grow (the late
+  // colours are the ones free at most nodes) gets one more wave, while that beats the greedy sizes
+  int64_t greedy_waves = 0;
+  for (int c = 0; c < C; ++c) greedy_waves += (sz[c] + W - 1) / W;
+  int grow = C - 1;
+  for (int pass = 0; pass < 8; ++pass) {
+    for (int64_t s = T - 1; s >= 0; --s) {
+      const int32_t e = eorder[s];
+      const int a = color[e];
+      if (sz[a] <= k[a] * W) continue;
+      const int32_t *nd = &tt[4 * (int64_t)e];
+      int b = -1;
+      int64_t room = 0;
+      for (int c = 0; c < C; ++c) {
+        const int64_t r = k[c] * W - sz[c];
+        if (c == a || r <= room) continue;
+        if (bit(nd[0], c) || bit(nd[1], c) || bit(nd[2], c) || bit(nd[3], c)) continue;
+        b = c;
+        room = r;
+      }
+      if (b < 0) continue;
+      for (int q = 0; q < 4; ++q) {
+        used[(size_t)nd[q] * kWords + a / 64] &= ~(1ULL << (a % 64));
+        used[(size_t)nd[q] * kWords + b / 64] |= 1ULL << (b % 64);
+      }
+      color[e] = b;
+      --sz[a];
+      ++sz[b];
+    }
+    int64_t now = 0;
+    bool over = false;
+    for (int c = 0; c < C; ++c) {
+      now += (sz[c] + W - 1) / W;
+      over |= sz[c] > k[c] * W;
+    }
+    if (!over || now + 1 >= greedy_waves || grow < 0) break;
+    ++k[grow];
+    grow = grow > 0 ? grow - 1 : C - 1;
+  }
+  int n = 0;
+  for (int c = 0; c < C; ++c) n += sz[c] > 0;
+  if (n < C) {   // (not expected: every target is at least one wave)
+    std::vector<int> renum(C, -1);
+    n = 0;
+    for (int c = 0; c < C; ++c)
+      if (sz[c] > 0) renum[c] = n++;
+    for (int64_t e = 0; e < T; ++e) color[e] = renum[color[e]];
+  }
+  return n;
+}
+
 double signed_det(const double *x0, const double *x1, const double *x2, const double *x3) {
   double a[3], b[3], c[3];
   for (int k = 0; k < 3; ++k) {
@@ -196,6 +273,7 @@ lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_
     for (int a = 0; a < 4; ++a) used[(size_t)tt[4 * e + a] * kWords + c / 64] |= 1ULL << (c % 64);
     n_colors = std::max(n_colors, c + 1);
   }
+  n_colors = balance_colours(T, tt, eorder, used, color, n_colors, kWords, assemble_wave_elements());
   // colour-sorted element order (Morton order kept inside each colour)
   m.color_off.assign(n_colors + 1, 0);
   for (int64_t e = 0; e < T; ++e) m.color_off[color[e] + 1]++;

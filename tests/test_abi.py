@@ -119,3 +119,21 @@ def test_pattern_and_colouring(L, which):
         nodes = m.tets[col == k].ravel()
         assert np.unique(nodes).size == nodes.size
     assert info["n_colors"] <= 80
+
+
+def test_colouring_balanced_to_assembly_waves(L):
+    """At 1M tets every colour exceeds one wave of the assembly kernel (GB300: 152 SMs x 4 CTAs x
+    32 elements = 19,456 elements, the value used when no device answers).  The colours are
+    rebalanced so that the waves launched, sum_c ceil(|c| / W), come within two of the work,
+    ceil(T / W) (the greedy sizes of this mesh launch 68 waves for 53 of work), and the colouring
+    stays valid."""
+    m = cylinder(1.0, 10.0, n_tets=1_000_000, seed=2)
+    mesh = L.Mesh.from_synthetic(m)
+    col = mesh.colors()
+    T, W = m.n_tets, 152 * 4 * 32
+    sizes = np.bincount(col)
+    assert sizes.min() > 0
+    waves = int(np.ceil(sizes / W).sum())
+    assert waves <= -(-T // W) + 2, (waves, sizes.tolist())
+    key = np.unique(np.stack([np.repeat(col, 4), m.tets.ravel()], 1), axis=0)
+    assert key.shape[0] == 4 * T       # no node carries two elements of one colour
