@@ -123,6 +123,7 @@ struct lfx_state {
   cudaStream_t stream = nullptr;
   int sigma = 1;
   DBuf hist[3];            // D4 [V]; level l = hist[(head + l) % sigma]
+  mutable DBuf io_u, io_p;  // caller-layout staging on the device: u [sigma][V][3], p [sigma][V]
   int head = 0;
   DBuf xsol, ubdf, rhs, gdir, nodal, comp_scale;
   DBuf vals64, vals32, nopat;   // nopat: empty (pattern-only views)
@@ -683,15 +684,21 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
 void lfx_problem_destroy(lfx_problem *problem) { delete problem; }
 
 // --------------------------------------------------------------------------------- state
-static lfx_status upload_node_field(const Mesh &m, const double *u /*[V][3]*/, const double *p /*[V]*/, D4 *dst,
-                                    cudaStream_t st) {
-  std::vector<D4> h(m.V);
-  for (int64_t i = 0; i < m.V; ++i) {
-    const int64_t o = m.node_old[i];
-    h[i] = D4{u[3 * o], u[3 * o + 1], u[3 * o + 2], p[o]};
-  }
-  LFX_CUDA_TRY(cudaMemcpyAsync(dst, h.data(), sizeof(D4) * m.V, cudaMemcpyHostToDevice, st));
-  LFX_CUDA_TRY(cudaStreamSynchronize(st));
+// History levels from the caller's arrays (u [sigma][V][3], p [sigma][V], caller node order):
+// copied as they are (a pinned caller buffer is read by DMA directly), permuted and interleaved on
+// the device; returns once the caller's buffers may be reused.
+static lfx_status upload_history(lfx_state *s, const double *u_hist, const double *p_hist) {
+  const Mesh &m = s->pb->mesh->m;
+  const int64_t V = m.V;
+  const size_t nu = sizeof(double) * 3 * (size_t)V * s->sigma, np = sizeof(double) * (size_t)V * s->sigma;
+  if (s->io_u.bytes < nu) LFX_TRY(s->io_u.alloc(nu));
+  if (s->io_p.bytes < np) LFX_TRY(s->io_p.alloc(np));
+  LFX_CUDA_TRY(cudaMemcpyAsync(s->io_u.p, u_hist, nu, cudaMemcpyHostToDevice, s->stream));
+  LFX_CUDA_TRY(cudaMemcpyAsync(s->io_p.p, p_hist, np, cudaMemcpyHostToDevice, s->stream));
+  for (int l = 0; l < s->sigma; ++l)
+    LFX_TRY(launch_node_scatter(s->stream, V, m.d_node_old.as<int32_t>(), s->io_u.as<double>() + (size_t)l * 3 * V,
+                                s->io_p.as<double>() + (size_t)l * V, s->level(l)));
+  LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
   return LFX_OK;
 }
 
@@ -701,9 +708,7 @@ extern "C" lfx_status lfx_state_set(lfx_state *s, const double *u_hist, const do
     set_error("lfx_state_set: NULL argument");
     return LFX_ERR_INVALID_ARG;
   }
-  const Mesh &m = s->pb->mesh->m;
-  for (int l = 0; l < s->sigma; ++l)
-    LFX_TRY(upload_node_field(m, u_hist + (size_t)l * 3 * m.V, p_hist + (size_t)l * m.V, s->level(l), s->stream));
+  LFX_TRY(upload_history(s, u_hist, p_hist));
   s->t = t;
   s->assembled = false;
   return LFX_OK;
@@ -724,10 +729,8 @@ lfx_status lfx_state_create(lfx_problem *pb, const double *u_hist, const double 
   s->pb = pb;
   s->sigma = pb->bdf_order;
   s->t = t0;
-  for (int l = 0; l < s->sigma; ++l) {
-    LFX_TRY(s->hist[l].alloc(sizeof(D4) * V));
-    LFX_TRY(upload_node_field(m, u_hist + (size_t)l * 3 * V, p_hist + (size_t)l * V, s->hist[l].as<D4>(), 0));
-  }
+  for (int l = 0; l < s->sigma; ++l) LFX_TRY(s->hist[l].alloc(sizeof(D4) * V));
+  LFX_TRY(upload_history(s.get(), u_hist, p_hist));
   LFX_TRY(s->xsol.alloc(sizeof(D4) * V));
   LFX_TRY(s->ubdf.alloc(sizeof(D4) * V));
   LFX_TRY(s->rhs.alloc(sizeof(D4) * V));
@@ -865,6 +868,7 @@ lfx_status lfx_state_device_bytes(const lfx_state *s, int64_t *bytes) {
              s->rhs_hi.bytes + s->rhs_lo.bytes + s->xe_hi.bytes + s->xe_lo.bytes + s->ub_hi.bytes + s->ub_lo.bytes +
              s->xs_hi.bytes + s->xs_lo.bytes;
   for (int l = 0; l < 3; ++l) b += s->hist[l].bytes;
+  b += s->io_u.bytes + s->io_p.bytes;
   *bytes = (int64_t)b;
   return LFX_OK;
 }
@@ -996,6 +1000,7 @@ int64_t lfx_internal_state_bytes_estimate(const lfx_problem *pb, int64_t *V_out,
   if (sigma_out) *sigma_out = sigma;
   const int64_t v64 = 32 * V, v32 = 16 * V;
   int64_t b = (sigma + 3) * v64 + 64 * (int64_t)pb->dir_node.size() + 8 * m.n_comp;
+  b += sigma * v64;                                          // caller-layout staging (history in, solution out)
   b += 128 * nnzb;                                           // FP64 or double-float matrix
   const int64_t amg = o.s_smoother == LFX_SMOOTH_AMG ? 300 * V + 8LL * o.amg_coarse_size * o.amg_coarse_size : 0;
   const int64_t part = 8LL * 152 * 4 * 65 + 8 * (V * 8 / 256 + 64);
@@ -1192,17 +1197,16 @@ lfx_status lfx_state_get(const lfx_state *s, double *u, double *p) {
     set_error("lfx_state_get: NULL argument");
     return LFX_ERR_INVALID_ARG;
   }
+  // permuted to the caller's layout on the device, then copied straight into the caller's arrays
   const Mesh &m = s->pb->mesh->m;
-  std::vector<D4> h(m.V);
+  const int64_t V = m.V;
+  if (s->io_u.bytes < sizeof(double) * 3 * (size_t)V) LFX_TRY(s->io_u.alloc(sizeof(double) * 3 * (size_t)V));
+  if (s->io_p.bytes < sizeof(double) * (size_t)V) LFX_TRY(s->io_p.alloc(sizeof(double) * (size_t)V));
+  LFX_TRY(launch_node_gather(s->stream, V, m.d_node_old.as<int32_t>(), s->hist[s->head].as<D4>(),
+                             s->io_u.as<double>(), s->io_p.as<double>()));
+  LFX_CUDA_TRY(cudaMemcpyAsync(u, s->io_u.p, sizeof(double) * 3 * (size_t)V, cudaMemcpyDeviceToHost, s->stream));
+  LFX_CUDA_TRY(cudaMemcpyAsync(p, s->io_p.p, sizeof(double) * (size_t)V, cudaMemcpyDeviceToHost, s->stream));
   LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
-  LFX_CUDA_TRY(cudaMemcpy(h.data(), s->hist[s->head].p, sizeof(D4) * m.V, cudaMemcpyDeviceToHost));
-  for (int64_t i = 0; i < m.V; ++i) {
-    const int64_t o = m.node_old[i];
-    u[3 * o] = h[i].x;
-    u[3 * o + 1] = h[i].y;
-    u[3 * o + 2] = h[i].z;
-    p[o] = h[i].w;
-  }
   return LFX_OK;
 }
 

@@ -858,6 +858,44 @@ lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysPar
   return LFX_OK;
 }
 
+namespace {
+__global__ void node_scatter_kernel(int64_t V, const int32_t *node_old, const double *u, const double *p, D4 *dst) {
+  pdl_entry();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = node_old[i];
+    dst[i] = D4{u[3 * o], u[3 * o + 1], u[3 * o + 2], p[o]};
+  }
+}
+__global__ void node_gather_kernel(int64_t V, const int32_t *node_old, const D4 *src, double *u, double *p) {
+  pdl_entry();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = node_old[i];
+    const D4 v = src[i];
+    u[3 * o] = v.x;
+    u[3 * o + 1] = v.y;
+    u[3 * o + 2] = v.z;
+    p[o] = v.w;
+  }
+}
+}  // namespace
+
+lfx_status launch_node_scatter(cudaStream_t st, int64_t V, const int32_t *node_old, const double *u, const double *p,
+                               D4 *dst) {
+  if (V == 0) return LFX_OK;
+  pdl_launch(node_scatter_kernel, grid_for(V, 256), 256, 0, st, V, node_old, u, p, dst);
+  note_launches(1);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+lfx_status launch_node_gather(cudaStream_t st, int64_t V, const int32_t *node_old, const D4 *src, double *u,
+                              double *p) {
+  if (V == 0) return LFX_OK;
+  pdl_launch(node_gather_kernel, grid_for(V, 256), 256, 0, st, V, node_old, src, u, p);
+  note_launches(1);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
 int64_t assemble_wave_elements() {
   int dev = 0, v = 0, sms = 152, per_sm = 4;
   if (cudaGetDevice(&dev) == cudaSuccess &&

@@ -69,6 +69,11 @@ lfx_status launch_apply_dirichlet_dd(cudaStream_t st, int64_t nd, const int32_t 
                                      const int32_t *diag, float *hi, float *lo, double *rhs, double *x0);
 lfx_status launch_comp_normalize_dd(cudaStream_t st, int64_t V, int n_comp, const int32_t *comp_off,
                                     double *scale, const int32_t *rowptr, float *hi, float *lo, double *rhs);
+// Node fields between the caller's layout (u [V][3], p [V], caller node order) and the internal
+// interleaved D4 [V] in internal order (node_old[i] = caller index of internal node i)
+lfx_status launch_node_scatter(cudaStream_t st, int64_t V, const int32_t *node_old, const double *u, const double *p,
+                               D4 *dst);
+lfx_status launch_node_gather(cudaStream_t st, int64_t V, const int32_t *node_old, const D4 *src, double *u, double *p);
 template <class R, class S>
 lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysParams &P,
                            const int32_t *color_off, int n_colors, S *vals);

@@ -120,6 +120,7 @@ struct Mesh {
   DBuf d_diag;      // int32 [V]
   DBuf d_trans;     // int32 [nnzb]
   DBuf d_comp_off;  // int32 [n_comp+1]
+  DBuf d_node_old;  // int32 [V] internal node -> caller node (host arrays in, solutions out)
   size_t device_bytes() const;
 };
 

@@ -126,7 +126,7 @@ double signed_det(const double *x0, const double *x1, const double *x2, const do
 
 size_t Mesh::device_bytes() const {
   return d_xyz.bytes + d_xyz_hi.bytes + d_xyz_lo.bytes + d_conn.bytes + d_slot.bytes + d_rowptr.bytes + d_col.bytes + d_diag.bytes +
-         d_trans.bytes + d_comp_off.bytes;
+         d_trans.bytes + d_comp_off.bytes + d_node_old.bytes;
 }
 
 lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_in, int64_t n_tets,
@@ -391,6 +391,8 @@ lfx_status upload_mesh(Mesh &m) {
   LFX_TRY(m.d_diag.alloc(sizeof(int32_t) * V));
   LFX_TRY(m.d_trans.alloc(sizeof(int32_t) * m.nnzb));
   LFX_TRY(m.d_comp_off.alloc(sizeof(int32_t) * m.comp_off.size()));
+  LFX_TRY(m.d_node_old.alloc(sizeof(int32_t) * V));
+  LFX_CUDA_TRY(cudaMemcpy(m.d_node_old.p, m.node_old.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_xyz.p, x4.data(), m.d_xyz.bytes, cudaMemcpyHostToDevice));
   // FP32 high and low parts of the coordinates (x = hi + lo to 48 bits) for double-float assembly
   std::vector<float> xh(4 * V), xl(4 * V);

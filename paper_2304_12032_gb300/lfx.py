@@ -366,9 +366,16 @@ class State:
         p = np.ascontiguousarray(np.asarray(p_hist, dtype=np.float64).reshape(self.problem.bdf_order, self.V))
         _check(library().lfx_state_set(self.h, _d(u), _d(p), float(t)))
 
-    def get(self):
-        u = np.zeros((self.V, 3))
-        p = np.zeros(self.V)
+    def get(self, u=None, p=None):
+        """u [V][3], p [V] at the current time level; into the given C-contiguous float64 arrays
+        (e.g. views of page-locked buffers, which the copy then reads by DMA) or new ones."""
+        if u is None:
+            u = np.zeros((self.V, 3))
+        if p is None:
+            p = np.zeros(self.V)
+        for a, shape in ((u, (self.V, 3)), (p, (self.V,))):
+            if a.dtype != np.float64 or a.shape != shape or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"State.get: output must be C-contiguous float64 of shape {shape}")
         _check(library().lfx_state_get(self.h, _d(u), _d(p)))
         return u, p
 

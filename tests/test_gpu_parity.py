@@ -4,6 +4,8 @@ Tolerances (FP64 path): assembled entries within 1e-12 relative to the largest e
 scalar row (summation order differs: colour order on the GPU, COO summation in the oracle);
 SpMV and preconditioner within 1e-12 / 1e-10 of the scale of the result; solutions within
 1e-6 relative L2 (BASELINE target), in practice ~1e-9."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -142,3 +144,35 @@ def test_mixed_step_matches_oracle(which, bf16):
     rp_ = np.linalg.norm(p - xref[:, 3]) / np.linalg.norm(xref[:, 3])
     assert ru <= 1e-6 and rp_ <= 1e-6, (which, bf16, ru, rp_, stats)
     assert stats["outer_iterations"] >= 1 and stats["iterations"] >= stats["outer_iterations"]
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_history_in_solution_out_round_trip(pinned):
+    """lfx_state_set copies the caller's arrays as they are and permutes them to the internal node
+    order on the device; lfx_state_get permutes back: without a step, get returns history level 0
+    exactly, in the caller's node order (the mesh renumbers nodes, so a wrong map shows), from
+    pageable or page-locked buffers."""
+    torch = pytest.importorskip("torch")
+    case = CASES["bifurcation_supg_bdf3"]()
+    mesh, prob, st = C.gpu_state(case)
+    V, sig = case.mesh.n_nodes, case.order
+    rng = np.random.default_rng(21)
+
+    def buf(*shape):
+        if pinned:
+            return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        return np.empty(shape)
+
+    uh, ph = buf(sig, V, 3), buf(sig, V)
+    uh[:] = rng.standard_normal((sig, V, 3))
+    ph[:] = rng.standard_normal((sig, V))
+    st.set(uh, ph, 0.25)
+    u, p = buf(V, 3), buf(V)
+    st.get(u, p)
+    assert np.array_equal(u, uh[0]) and np.array_equal(p, ph[0])
+    # the older levels went in too: a step from them matches the oracle's step from the same data
+    ost = C.oracle_step(dataclasses.replace(case, u_hist=uh.copy(), p_hist=ph.copy(), t0=0.25))
+    st.step()
+    u1, p1 = st.get()
+    ref = ost.x.reshape(-1, 4)
+    assert np.linalg.norm(u1 - ref[:, :3]) <= 1e-6 * np.linalg.norm(ref[:, :3])
