@@ -164,8 +164,8 @@ typedef struct lfx_options {
   int32_t reorthogonalize;      /* classical Gram-Schmidt once (0, default) or twice (1); in mixed
                                    precision the FP32 inner solve orthogonalises twice only if 2  */
   /* aSIMPLE: velocity block F and Schur approximation S = C - D diag(F)^-1 G */
-  int32_t f_smoother, f_steps;  /* LFX_SMOOTH_*, steps; default Chebyshev, 3                   */
-  double f_omega, f_ratio;      /* Jacobi damping; Chebyshev lmax/lmin; default 0.7, 20        */
+  int32_t f_smoother, f_steps;  /* LFX_SMOOTH_*, steps; default Chebyshev, 6                   */
+  double f_omega, f_ratio;      /* Jacobi damping; Chebyshev lmax/lmin; default 0.7, 60        */
   int32_t s_smoother, s_steps;  /* default AMG with 1 Chebyshev step pre and post               */
   double s_omega, s_ratio;      /* default 0.7, 30                                             */
   int32_t n_power;              /* 0 (default): Chebyshev lmax = Gershgorin bound (holds for every
@@ -174,7 +174,8 @@ typedef struct lfx_options {
   int32_t smoother_bf16;        /* store the preconditioner blocks in BF16 (FP32 arithmetic)   */
   int32_t outer_restart;        /* FP64 flexible GMRES restart; default 8                       */
   int32_t outer_max_iters;      /* default 40                                                   */
-  double inner_rtol;            /* FP32 inner GMRES tolerance per outer step; default 1e-4     */
+  double inner_rtol;            /* FP32 inner GMRES tolerance per outer step; default 1e-4.
+                                   With inner_adaptive it is the tightest tolerance used      */
   int32_t inner_max_iters;      /* default 60                                                   */
   double bad_element_quality;   /* elements with 6 sqrt2 |K| / e_rms^3 below this keep FP64
                                    geometry in mixed assembly; default 0.1                       */
@@ -193,7 +194,12 @@ typedef struct lfx_options {
    * keeps that step's scale, which slows it when the scales drift) */
   int32_t batch_normalize;
   int32_t batch_segmented;
-  int32_t reserved[6];
+  /* mixed precision: each inner solve's tolerance from the outer flexible GMRES's residual
+   * estimate r and its target tol = gmres_rtol ||b|| (default 1): 1/2 sqrt(tol / r) for the first
+   * inner solve of an outer cycle (two outer steps reach tol), 1/2 tol / r for the later ones (this
+   * step reaches it), kept within [inner_rtol, 0.1].  Single systems only (batches keep inner_rtol). */
+  int32_t inner_adaptive;
+  int32_t reserved[5];
 } lfx_options;
 void lfx_options_default(lfx_options *opt);
 

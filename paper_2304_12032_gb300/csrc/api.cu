@@ -9,6 +9,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -307,9 +308,9 @@ void lfx_options_default(lfx_options *o) {
   o->gmres_rtol = 1e-10;
   o->reorthogonalize = 0;
   o->f_smoother = LFX_SMOOTH_CHEBYSHEV;
-  o->f_steps = 3;
+  o->f_steps = 6;
   o->f_omega = 0.7;
-  o->f_ratio = 20.0;
+  o->f_ratio = 60.0;
   o->s_smoother = LFX_SMOOTH_AMG;
   o->s_steps = 1;
   o->s_omega = 0.7;
@@ -327,6 +328,7 @@ void lfx_options_default(lfx_options *o) {
   o->amg_alpha = 1.0;
   o->batch_normalize = 1;
   o->batch_segmented = 1;
+  o->inner_adaptive = 1;
 }
 
 // barycentre, unit outward normal, area of the faces carrying `tag` (area weighted)
@@ -1107,23 +1109,36 @@ static lfx_status run_solve(lfx_state *s, double *x, bool x_zero, int *its, int 
   const int64_t n = 4 * s->pb->mesh->m.V;
   const BsrView<float> A32 = s->view<float>(s->vals32);
   s->inner_total = 0;
-  auto inner = [s, A32, n, &o](cudaStream_t q, const double *v, double *z, const KState *ks) -> lfx_status {
+  const bool adaptive = o.inner_adaptive && s->pb->mesh->m.n_comp <= 1;
+  auto inner = [s, A32, n, &o, adaptive](cudaStream_t q, const double *v, double *z, const KState *ks) -> lfx_status {
     LFX_TRY((launch_convert<double, float>(q, v, s->r32.as<float>(), n, ks)));
     int it = 0;
     double r = 0.0;
     lfx_status rc;
+    double eta = o.inner_rtol;
+    if (adaptive) {
+      // the outer's progress so far (header of its status: steps of this cycle, target, residual)
+      KState h;
+      LFX_CUDA_TRY(cudaMemcpyAsync(&h, ks, offsetof(KState, H), cudaMemcpyDeviceToHost, q));
+      LFX_CUDA_TRY(cudaStreamSynchronize(q));
+      if (h.res > 0.0 && h.tol_abs > 0.0 && std::isfinite(h.res)) {
+        const double need = h.tol_abs / h.res;
+        eta = 0.5 * (h.j == 0 ? std::sqrt(need) : need);
+        eta = std::min(0.1, std::max(o.inner_rtol, eta));
+      }
+    }
     if (o.smoother_bf16) {
       const BsrView<__nv_bfloat16> Ab = s->view<__nv_bfloat16>(s->nopat);
       auto pc = [s, Ab](cudaStream_t qq, const float *vv, float *zz, const KState *kk) {
         return s->pcbf.apply(qq, Ab, vv, zz, kk);
       };
-      rc = s->gm32.solve(q, A32, pc, s->r32.as<float>(), s->z32.as<float>(), o.inner_rtol, o.inner_max_iters,
+      rc = s->gm32.solve(q, A32, pc, s->r32.as<float>(), s->z32.as<float>(), eta, o.inner_max_iters,
                          o.reorthogonalize == 2, 2, true, &it, &r);
     } else {
       auto pc = [s, A32](cudaStream_t qq, const float *vv, float *zz, const KState *kk) {
         return s->pc32.apply(qq, A32, vv, zz, kk);
       };
-      rc = s->gm32.solve(q, A32, pc, s->r32.as<float>(), s->z32.as<float>(), o.inner_rtol, o.inner_max_iters,
+      rc = s->gm32.solve(q, A32, pc, s->r32.as<float>(), s->z32.as<float>(), eta, o.inner_max_iters,
                          o.reorthogonalize == 2, 2, true, &it, &r);
     }
     s->inner_total += it;

@@ -62,7 +62,7 @@ class lfx_options(ctypes.Structure):
                 ("amg_refresh", ctypes.c_int32), ("amg_coarse_size", ctypes.c_int32),
                 ("amg_theta", ctypes.c_double), ("amg_alpha", ctypes.c_double),
                 ("batch_normalize", ctypes.c_int32), ("batch_segmented", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("inner_adaptive", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class lfx_mesh_info(ctypes.Structure):

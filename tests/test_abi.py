@@ -50,7 +50,8 @@ def test_struct_layouts(L, name):
 def test_options_defaults(L):
     o = L.default_options()
     assert o.stab == 2 and o.diffusion == 0 and o.c_r == 30.0 and o.pin_pressure_node == -1
-    assert o.gmres_restart == 64 and o.f_steps == 3 and o.s_smoother == 2 and o.s_steps == 1 and o.reorthogonalize == 0
+    assert o.gmres_restart == 64 and o.f_steps == 6 and o.f_ratio == 60.0 and o.s_smoother == 2 and o.s_steps == 1
+    assert o.reorthogonalize == 0 and o.inner_adaptive == 1 and o.batch_segmented == 1
 
 
 def _status(L, nodes, tets, bf, tg):
