@@ -197,7 +197,8 @@ typedef struct lfx_options {
   /* mixed precision: each inner solve's tolerance from the outer flexible GMRES's residual
    * estimate r and its target tol = gmres_rtol ||b|| (default 1): 1/2 sqrt(tol / r) for the first
    * inner solve of an outer cycle (two outer steps reach tol), 1/2 tol / r for the later ones (this
-   * step reaches it), kept within [inner_rtol, 0.1].  Single systems only (batches keep inner_rtol). */
+   * step reaches it), kept within [inner_rtol, 0.1]; for a segmented batch the tightest over the
+   * members still running */
   int32_t inner_adaptive;
   int32_t reserved[5];
 } lfx_options;

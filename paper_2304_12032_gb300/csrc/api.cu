@@ -1109,24 +1109,14 @@ static lfx_status run_solve(lfx_state *s, double *x, bool x_zero, int *its, int 
   const int64_t n = 4 * s->pb->mesh->m.V;
   const BsrView<float> A32 = s->view<float>(s->vals32);
   s->inner_total = 0;
-  const bool adaptive = o.inner_adaptive && s->pb->mesh->m.n_comp <= 1;
+  const bool adaptive = o.inner_adaptive != 0;
   auto inner = [s, A32, n, &o, adaptive](cudaStream_t q, const double *v, double *z, const KState *ks) -> lfx_status {
     LFX_TRY((launch_convert<double, float>(q, v, s->r32.as<float>(), n, ks)));
     int it = 0;
     double r = 0.0;
     lfx_status rc;
     double eta = o.inner_rtol;
-    if (adaptive) {
-      // the outer's progress so far (header of its status: steps of this cycle, target, residual)
-      KState h;
-      LFX_CUDA_TRY(cudaMemcpyAsync(&h, ks, offsetof(KState, H), cudaMemcpyDeviceToHost, q));
-      LFX_CUDA_TRY(cudaStreamSynchronize(q));
-      if (h.res > 0.0 && h.tol_abs > 0.0 && std::isfinite(h.res)) {
-        const double need = h.tol_abs / h.res;
-        eta = 0.5 * (h.j == 0 ? std::sqrt(need) : need);
-        eta = std::min(0.1, std::max(o.inner_rtol, eta));
-      }
-    }
+    if (adaptive) LFX_TRY(s->gmdd.inner_tolerance(q, o.inner_rtol, 0.1, &eta));
     if (o.smoother_bf16) {
       const BsrView<__nv_bfloat16> Ab = s->view<__nv_bfloat16>(s->nopat);
       auto pc = [s, Ab](cudaStream_t qq, const float *vv, float *zz, const KState *kk) {

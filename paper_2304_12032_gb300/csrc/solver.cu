@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cstddef>
+#include <cstring>
 #include <type_traits>
 
 #include "amg.h"
@@ -2604,6 +2605,27 @@ lfx_status Gmres<S, T>::set_segments(const std::vector<int32_t> &comp_off) {
 
 // The header of a KState (status words and scalars), read back by the host
 static constexpr size_t kStateHead = offsetof(KState, H);
+
+template <class S, class T>
+lfx_status Gmres<S, T>::inner_tolerance(cudaStream_t st, double lo, double hi, double *eta) {
+  const int ns = n_seg > 1 ? n_seg : 1;
+  std::vector<KState> h(1);
+  std::vector<char> heads((size_t)ns * kStateHead);
+  const void *src = n_seg > 1 ? seg_state.p : state.p;
+  LFX_CUDA_TRY(cudaMemcpy2DAsync(heads.data(), kStateHead, src, sizeof(KState), kStateHead, ns,
+                                 cudaMemcpyDeviceToHost, st));
+  LFX_CUDA_TRY(cudaStreamSynchronize(st));
+  double e = hi;
+  for (int c = 0; c < ns; ++c) {
+    std::memcpy(h.data(), heads.data() + (size_t)c * kStateHead, kStateHead);
+    const KState &k = h[0];
+    if ((n_seg > 1 && k.done) || !(k.res > 0.0) || !(k.tol_abs > 0.0) || !std::isfinite(k.res)) continue;
+    const double need = k.tol_abs / k.res;
+    e = std::min(e, 0.5 * (k.j == 0 ? std::sqrt(need) : need));
+  }
+  *eta = std::max(lo, std::min(hi, e));
+  return LFX_OK;
+}
 
 // Restarted GMRES over n_seg independent components (see set_segments); the same launches as
 // solve, with every reduction and every small dense step done per component.

@@ -145,6 +145,12 @@ struct Gmres {
   // Arnoldi process per component, each stopped by its own test ||b_c - A x_c|| <= rtol ||b_c||.
   // *its_out is then the largest step count, *res_out the largest relative residual.
   lfx_status set_segments(const std::vector<int32_t> &comp_off);
+  // Tolerance for the inner solve that preconditions this (flexible) solve's next step, from the
+  // progress so far: with r the residual estimate and tol the target, 1/2 sqrt(tol / r) at a
+  // cycle's first step (two steps of inner accuracy eta reach tol) and 1/2 tol / r after (this
+  // step reaches it); the tightest over the running components; within [lo, hi].  Reads the
+  // status from the device (synchronises st).
+  lfx_status inner_tolerance(cudaStream_t st, double lo, double hi, double *eta);
   size_t device_bytes() const;
 
  private:
