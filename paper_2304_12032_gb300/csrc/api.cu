@@ -886,18 +886,24 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
   LFX_TRY(launch_bdf(st, m.V, sg, s->level(0), sg > 1 ? s->level(1) : nullptr, sg > 2 ? s->level(2) : nullptr,
                      pb->beta, pb->gamma, s->xsol.as<D4>(), s->ubdf.as<D4>(), s->xe_hi.as<float4>(),
                      s->xe_lo.as<float4>(), s->ub_hi.as<float4>(), s->ub_lo.as<float4>()));
+  // (every block and row written by its first element needs no clearing beforehand)
   if (mixed) {
-    LFX_CUDA_TRY(cudaMemsetAsync(s->vals32.p, 0, s->vals32.bytes, st));
-    LFX_CUDA_TRY(cudaMemsetAsync(s->vals_lo.p, 0, s->vals_lo.bytes, st));
-    LFX_CUDA_TRY(cudaMemsetAsync(s->rhs_hi.p, 0, s->rhs_hi.bytes, st));
-    LFX_CUDA_TRY(cudaMemsetAsync(s->rhs_lo.p, 0, s->rhs_lo.bytes, st));
+    if (!m.all_blocks_touched) {
+      LFX_CUDA_TRY(cudaMemsetAsync(s->vals32.p, 0, s->vals32.bytes, st));
+      LFX_CUDA_TRY(cudaMemsetAsync(s->vals_lo.p, 0, s->vals_lo.bytes, st));
+    }
+    if (!m.all_nodes_touched) {
+      LFX_CUDA_TRY(cudaMemsetAsync(s->rhs_hi.p, 0, s->rhs_hi.bytes, st));
+      LFX_CUDA_TRY(cudaMemsetAsync(s->rhs_lo.p, 0, s->rhs_lo.bytes, st));
+    }
   } else {
-    LFX_CUDA_TRY(cudaMemsetAsync(s->vals64.p, 0, s->vals64.bytes, st));
-    LFX_CUDA_TRY(cudaMemsetAsync(s->rhs.p, 0, s->rhs.bytes, st));
+    if (!m.all_blocks_touched) LFX_CUDA_TRY(cudaMemsetAsync(s->vals64.p, 0, s->vals64.bytes, st));
+    if (!m.all_nodes_touched) LFX_CUDA_TRY(cudaMemsetAsync(s->rhs.p, 0, s->rhs.bytes, st));
   }
   AssembleArgs A;
   A.conn = m.d_conn.as<int4>();
   A.slot = m.d_slot.as<int32_t>();
+  A.first = m.d_first.as<uint16_t>();
   A.xyz = m.d_xyz.as<D4>();
   A.xext = s->xsol.as<D4>();
   A.ubdf = s->ubdf.as<D4>();

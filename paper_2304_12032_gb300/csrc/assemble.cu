@@ -513,27 +513,43 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const Ph
   const int4 cn = A.conn[e];
   const int na = (a == 0) ? cn.x : ((a == 1) ? cn.y : ((a == 2) ? cn.z : cn.w));
   const int64_t ir = 4 * (int64_t)na + i_rhs;
+  // the block's (and the row's) first writer stores instead of reading back zeros
+  const uint32_t fm = A.first ? (uint32_t)A.first[e] : 0u;
+  const bool bfirst = (fm >> (4 * a + b)) & 1u, rfirst = (fm >> (5 * a)) & 1u;
   if constexpr (std::is_same<R, dd>::value) {
     // dd accumulation into the high (vals) and low parts
     float4 *ph = reinterpret_cast<float4 *>(vals + (int64_t)s * 16);
     float4 *pl = reinterpret_cast<float4 *>(A.vals_lo + (int64_t)s * 16);
+    if (bfirst) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      float4 h = ph[k], l = pl[k];
-      const dd v0 = dd(h.x, l.x) + blk[4 * k], v1 = dd(h.y, l.y) + blk[4 * k + 1];
-      const dd v2 = dd(h.z, l.z) + blk[4 * k + 2], v3 = dd(h.w, l.w) + blk[4 * k + 3];
-      ph[k] = make_float4(v0.hi, v1.hi, v2.hi, v3.hi);
-      pl[k] = make_float4(v0.lo, v1.lo, v2.lo, v3.lo);
+      for (int k = 0; k < 4; ++k) {
+        ph[k] = make_float4(blk[4 * k].hi, blk[4 * k + 1].hi, blk[4 * k + 2].hi, blk[4 * k + 3].hi);
+        pl[k] = make_float4(blk[4 * k].lo, blk[4 * k + 1].lo, blk[4 * k + 2].lo, blk[4 * k + 3].lo);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float4 h = ph[k], l = pl[k];
+        const dd v0 = dd(h.x, l.x) + blk[4 * k], v1 = dd(h.y, l.y) + blk[4 * k + 1];
+        const dd v2 = dd(h.z, l.z) + blk[4 * k + 2], v3 = dd(h.w, l.w) + blk[4 * k + 3];
+        ph[k] = make_float4(v0.hi, v1.hi, v2.hi, v3.hi);
+        pl[k] = make_float4(v0.lo, v1.lo, v2.lo, v3.lo);
+      }
     }
-    const dd r = dd(A.rhs_hi[ir], A.rhs_lo[ir]) + rhs;
+    const dd r = rfirst ? rhs : dd(A.rhs_hi[ir], A.rhs_lo[ir]) + rhs;
     A.rhs_hi[ir] = r.hi;
     A.rhs_lo[ir] = r.lo;
   } else {
     S out[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) out[k] = (S)blk[k];
-    Vec16<S>::add(vals + (int64_t)s * 16, out);
-    A.rhs[ir] += (double)rhs;
+    if (bfirst) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) vals[(int64_t)s * 16 + k] = out[k];
+    } else {
+      Vec16<S>::add(vals + (int64_t)s * 16, out);
+    }
+    A.rhs[ir] = rfirst ? (double)rhs : A.rhs[ir] + (double)rhs;
   }
 }
 

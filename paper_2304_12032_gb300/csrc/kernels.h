@@ -21,6 +21,7 @@ struct alignas(16) F4 {
 struct AssembleArgs {
   const int4 *conn;          // [T] internal numbering, colour-sorted
   const int32_t *slot;       // [T][16]
+  const uint16_t *first;     // [T] bit 4a+b: this element writes block (a, b) first (null: add everywhere)
   const D4 *xyz;        // [V] (x, y, z, 0)
   const D4 *xext;       // [V] (u^EXT, p^EXT)
   const D4 *ubdf;       // [V] (u^BDF, 0)

@@ -103,6 +103,9 @@ struct Mesh {
   std::vector<int32_t> diag_idx;     // [V] block index of (i,i)
   std::vector<int32_t> trans_idx;    // [nnzb] block index of (j,i) for block (i,j)
   std::vector<int32_t> slot;         // [T][16] block index of (node a, node b), a*4+b
+  std::vector<uint16_t> first;       // [T] bit 4a+b: the element writes block (a, b) before any other
+  bool all_blocks_touched = false;   // every block of the pattern belongs to some element
+  bool all_nodes_touched = false;    // every node belongs to some element
   std::vector<int32_t> color_off;    // [n_colors+1] offsets into the colour-sorted elements
   std::vector<uint8_t> bad;          // [T] 1 if below the shape-quality threshold
   std::vector<int32_t> bfaces;       // [F][3] outward oriented, internal numbering
@@ -121,6 +124,7 @@ struct Mesh {
   DBuf d_trans;     // int32 [nnzb]
   DBuf d_comp_off;  // int32 [n_comp+1]
   DBuf d_node_old;  // int32 [V] internal node -> caller node (host arrays in, solutions out)
+  DBuf d_first;     // uint16 [T] (first)
   size_t device_bytes() const;
 };
 

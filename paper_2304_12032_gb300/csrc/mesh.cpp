@@ -126,7 +126,7 @@ double signed_det(const double *x0, const double *x1, const double *x2, const do
 
 size_t Mesh::device_bytes() const {
   return d_xyz.bytes + d_xyz_hi.bytes + d_xyz_lo.bytes + d_conn.bytes + d_slot.bytes + d_rowptr.bytes + d_col.bytes + d_diag.bytes +
-         d_trans.bytes + d_comp_off.bytes + d_node_old.bytes;
+         d_trans.bytes + d_comp_off.bytes + d_node_old.bytes + d_first.bytes;
 }
 
 lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_in, int64_t n_tets,
@@ -343,6 +343,31 @@ lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b)
         m.slot[16 * e + 4 * a + b] = find(m.tets[4 * e + a], m.tets[4 * e + b]);
+  // First writers: colours are assembled in element order, so the lowest-numbered element touching
+  // a block writes it first and can store its terms instead of adding them to a cleared matrix; the
+  // first writer of a node's right-hand-side row is the first writer of its diagonal block.
+  m.first.assign(T, 0);
+  {
+    std::vector<uint8_t> seen(m.nnzb, 0), node(V, 0);
+    int64_t blocks = 0, nodes = 0;
+    for (int64_t e = 0; e < T; ++e) {
+      for (int q = 0; q < 16; ++q) {
+        const int32_t s = m.slot[16 * e + q];
+        if (!seen[s]) {
+          seen[s] = 1;
+          ++blocks;
+          m.first[e] |= (uint16_t)(1u << q);
+        }
+      }
+      for (int a = 0; a < 4; ++a)
+        if (!node[m.tets[4 * e + a]]) {
+          node[m.tets[4 * e + a]] = 1;
+          ++nodes;
+        }
+    }
+    m.all_blocks_touched = blocks == m.nnzb;
+    m.all_nodes_touched = nodes == V;
+  }
 
   // ---- boundary faces: internal numbering, outward orientation from the owning tetrahedron
   m.bfaces.resize(3 * F);
@@ -392,6 +417,8 @@ lfx_status upload_mesh(Mesh &m) {
   LFX_TRY(m.d_trans.alloc(sizeof(int32_t) * m.nnzb));
   LFX_TRY(m.d_comp_off.alloc(sizeof(int32_t) * m.comp_off.size()));
   LFX_TRY(m.d_node_old.alloc(sizeof(int32_t) * V));
+  LFX_TRY(m.d_first.alloc(sizeof(uint16_t) * std::max<int64_t>(T, 1)));
+  if (T > 0) LFX_CUDA_TRY(cudaMemcpy(m.d_first.p, m.first.data(), sizeof(uint16_t) * T, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_node_old.p, m.node_old.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_xyz.p, x4.data(), m.d_xyz.bytes, cudaMemcpyHostToDevice));
   // FP32 high and low parts of the coordinates (x = hi + lo to 48 bits) for double-float assembly
