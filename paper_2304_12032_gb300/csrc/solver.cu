@@ -195,6 +195,16 @@ __device__ __forceinline__ double cta_max(double v) {
   return s;
 }
 
+// a smoothing coefficient in the arithmetic type T (the FP32 kernels read the FP32 copy)
+template <class T>
+__device__ __forceinline__ T coef_t(const double &d, const float &) {
+  return (T)d;
+}
+template <>
+__device__ __forceinline__ float coef_t<float>(const double &, const float &f) {
+  return f;
+}
+
 __device__ __forceinline__ bool finished(const KState *st) {
   return st != nullptr && *(volatile const int *)&st->done != 0;
 }
@@ -585,7 +595,7 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF
         },
         [&](int u) {
           if constexpr (kFirst) {
-            const T s0 = (T)cf->f_init;
+            const T s0 = coef_t<T>(cf->f_init, cf->f_initf);
             const auto dfc = ld4(dinvF, c[u]);
             const auto bc = ld4(b0, c[u]);
             dv[u].x = s0 * (dfc.x * bc.x);
@@ -611,12 +621,12 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF
       st4(d_new, row, o);
       nrm = (double)o.x * o.x + (double)o.y * o.y + (double)o.z * o.z;
     } else {
-      const T c1 = (T)cf->f_c1[k], c2 = (T)cf->f_c2[k];
+      const T c1 = coef_t<T>(cf->f_c1[k], cf->f_c1f[k]), c2 = coef_t<T>(cf->f_c2[k], cf->f_c2f[k]);
       auto rr = ld4(r, row);
       typename Vec4T<T>::type dold;
       auto xx = ld4(x, row);
       if constexpr (kFirst) {
-        const T s0 = (T)cf->f_init;
+        const T s0 = coef_t<T>(cf->f_init, cf->f_initf);
         const auto bv = ld4(b0, row);
         rr.x = df.x * bv.x; rr.y = df.y * bv.y; rr.z = df.z * bv.z;
         dold.x = s0 * rr.x; dold.y = s0 * rr.y; dold.z = s0 * rr.z;
@@ -714,7 +724,7 @@ __global__ void __launch_bounds__(kThreads) s_step_kernel(View A, const T *dinvS
       st4(d_new, row, o);
       nrm = (double)o.w * o.w;
     } else {
-      const T c1 = (T)cf->s_c1[k], c2 = (T)cf->s_c2[k];
+      const T c1 = coef_t<T>(cf->s_c1[k], cf->s_c1f[k]), c2 = coef_t<T>(cf->s_c2[k], cf->s_c2f[k]);
       auto rr = ld4(r, row);
       const T dold = ld4(d_old, row).w;
       auto dn = ld4(d_new, row);
@@ -740,7 +750,7 @@ __global__ void f_init_kernel(int64_t V, const T *dinvF, const T *b, T *r, T *d,
   pdl_entry();
   if (finished(st)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
-    const T s = (T)cf->f_init;
+    const T s = coef_t<T>(cf->f_init, cf->f_initf);
     const auto df = ld4(dinvF, i);
     const auto bv = ld4(b, i);
     auto rr = ld4(r, i);
@@ -790,7 +800,7 @@ __global__ void __launch_bounds__(kThreads) d_init_kernel(View A, const T *dinvS
     auto rr = ld4(r, row);
     auto dd = ld4(d, row);
     rr.w = dinvS[row] * t;
-    dd.w = (T)cf->s_init * rr.w;
+    dd.w = coef_t<T>(cf->s_init, cf->s_initf) * rr.w;
     st4(r, row, rr);
     st4(d, row, dd);
     x[4 * row + 3] = dd.w;   // only the pressure component: the velocity part is read at neighbours
@@ -883,7 +893,7 @@ __global__ void __launch_bounds__(kThreads) s_resid_kernel(View A, const T *dinv
       auto rr = ld4(r, row);
       auto dd = ld4(d, row);
       rr.w = dinvS[row] * res;
-      dd.w = (T)cf->s_init * rr.w;
+      dd.w = coef_t<T>(cf->s_init, cf->s_initf) * rr.w;
       st4(r, row, rr);
       st4(d, row, dd);
     }
@@ -947,7 +957,8 @@ __device__ __forceinline__ typename AccT<T>::type csr_row_dot(const int32_t *__r
 // out[i*os + oo] = (acc ? out : 0) + alpha * sum_j M_ij in[j*is + io]
 template <class T, int G>
 __global__ void __launch_bounds__(kThreads) csr_spmv_kernel(CsrV<T> M, const T *in, int is, int io, T *out, int os,
-                                                            int oo, double alpha, int acc, const KState *st) {
+                                                            int oo, typename AccT<T>::type alpha, int acc,
+                                                            const KState *st) {
   pdl_entry();
   if (finished(st)) return;
   using A = typename AccT<T>::type;
@@ -975,7 +986,8 @@ __global__ void __launch_bounds__(kThreads) csr_resid_kernel(CsrV<T> M, const T 
 
 // Chebyshev start on a CSR level: r = dinv rhs; d = init r; x = (add ? x : 0) + d
 template <class T>
-__global__ void csr_cheb_init_kernel(int64_t n, const T *dinv, const T *rhs, T *r, T *d, T *x, double init, int add,
+__global__ void csr_cheb_init_kernel(int64_t n, const T *dinv, const T *rhs, T *r, T *d, T *x,
+                                     typename AccT<T>::type init, int add,
                                      const KState *st) {
   pdl_entry();
   if (finished(st)) return;
@@ -992,7 +1004,8 @@ __global__ void csr_cheb_init_kernel(int64_t n, const T *dinv, const T *rhs, T *
 // Chebyshev step on a CSR level: y = A d_old; r -= dinv y; d_new = c1 d_old + c2 r; x += d_new
 template <class T, int G>
 __global__ void __launch_bounds__(kThreads) csr_cheb_step_kernel(CsrV<T> M, const T *dinv, const T *d_old, T *d_new,
-                                                                 T *r, T *x, double c1, double c2, const KState *st) {
+                                                                 T *r, T *x, typename AccT<T>::type c1,
+                                                                 typename AccT<T>::type c2, const KState *st) {
   pdl_entry();
   if (finished(st)) return;
   using A = typename AccT<T>::type;
@@ -1061,14 +1074,14 @@ struct CoarseLevel {
   const T *Rv;
   T *x, *b, *r, *d0, *d1, *rr;
   T *xo;   // where the level's final iterate is left (d1 when one smoothing step is fused, else x)
-  double init, c1[kMaxSmooth], c2[kMaxSmooth];
+  typename AccT<T>::type init, c1[kMaxSmooth], c2[kMaxSmooth];   // (converted on the host)
 };
 constexpr int kMaxCoarse = 8;
 template <class T>
 struct CoarseArgs {
   int L;            // levels in amg[] (level 0 is matrix-free and not part of this launch)
   int s_steps;
-  double alpha;
+  typename AccT<T>::type alpha;
   const T *coarse_inv;
   int64_t nc;
   CoarseLevel<T> lv[kMaxCoarse];
@@ -1261,6 +1274,14 @@ __global__ void coef_kernel(SmoothCoef *cf, int f_kind, int f_steps, double f_om
     }
     if (which) cf->s_init = init;
     else cf->f_init = init;
+    float *c1f = which ? cf->s_c1f : cf->f_c1f;
+    float *c2f = which ? cf->s_c2f : cf->f_c2f;
+    for (int k = 0; k < kMaxSmooth; ++k) {
+      c1f[k] = (float)c1[k];
+      c2f[k] = (float)c2[k];
+    }
+    if (which) cf->s_initf = (float)init;
+    else cf->f_initf = (float)init;
   }
 }
 

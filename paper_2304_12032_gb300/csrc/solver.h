@@ -28,6 +28,11 @@ struct SmoothCoef {
   double f_init, s_init;          // first step: d_0 = init * diag^-1 b
   double f_c1[kMaxSmooth], f_c2[kMaxSmooth];
   double s_c1[kMaxSmooth], s_c2[kMaxSmooth];
+  // FP32 copies, read by the FP32 kernels (a double -> float conversion takes an FP64 issue slot,
+  // at 1/64 of the FP32 rate on this GPU)
+  float f_initf, s_initf;
+  float f_c1f[kMaxSmooth], f_c2f[kMaxSmooth];
+  float s_c1f[kMaxSmooth], s_c2f[kMaxSmooth];
 };
 
 // Device-resident GMRES status and small dense data (Hessenberg, Givens, g).
