@@ -34,8 +34,8 @@ FP32_ISSUE_PEAK_T = 35.96          # measured FP32 FMA-issue probe, T thread-ins
 ASM_FP64_FLOPS_PER_ELEMENT = 2948
 # thread instructions per tetrahedron of the double-float assembly kernel (ncu) and its DRAM
 # bytes per tetrahedron (ncu, one colour launch of 19,456 elements; profiles/)
-ASM_DD_INST_PER_ELEMENT = 29819
-ASM_DD_DRAM_BYTES_PER_ELEMENT = 5124
+ASM_DD_INST_PER_ELEMENT = 28921
+ASM_DD_DRAM_BYTES_PER_ELEMENT = 4221
 # DRAM bytes per block of the FP32 Krylov SpMV (ncu read + write, 2,089,595-block launch)
 SPMV32_DRAM_BYTES_PER_BLOCK = 71.6
 
