@@ -33,9 +33,9 @@ FP32_ISSUE_PEAK_T = 35.96          # measured FP32 FMA-issue probe, T thread-ins
 # assembly kernel, counted with ncu): the algorithmic work of one element's assembly
 ASM_FP64_FLOPS_PER_ELEMENT = 2948
 # thread instructions per tetrahedron of the double-float assembly kernel (ncu) and its DRAM
-# bytes per tetrahedron (ncu, one colour launch of 19,456 elements; profiles/)
-ASM_DD_INST_PER_ELEMENT = 28921
-ASM_DD_DRAM_BYTES_PER_ELEMENT = 4221
+# bytes per tetrahedron (ncu, one colour launch of 29,184 elements; profiles/)
+ASM_DD_INST_PER_ELEMENT = 28477
+ASM_DD_DRAM_BYTES_PER_ELEMENT = 4331
 # DRAM bytes per block of the FP32 Krylov SpMV (ncu read + write, 2,089,595-block launch)
 SPMV32_DRAM_BYTES_PER_BLOCK = 71.6
 

@@ -553,11 +553,12 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const Ph
   }
 }
 
-// CTAs per SM the register allocation must allow (4 for the double-float kernel, whose issue
-// rate depends on having enough warps to hide its long dependent FP32 chains)
+// CTAs per SM the register allocation must allow for the double-float kernel: 3 (164 registers)
+// measured faster than 4 (128 registers) and 5 (96, with spills) once the element terms used the
+// one-pass multiply-add
 template <class R> struct MinCtas { static constexpr int value = 1; };
 #ifndef LFX_ASM_DD_MIN_CTAS
-#define LFX_ASM_DD_MIN_CTAS 4
+#define LFX_ASM_DD_MIN_CTAS 3
 #endif
 template <> struct MinCtas<dd> { static constexpr int value = LFX_ASM_DD_MIN_CTAS; };
 
@@ -913,7 +914,7 @@ lfx_status launch_node_gather(cudaStream_t st, int64_t V, const int32_t *node_ol
 }
 
 int64_t assemble_wave_elements() {
-  int dev = 0, v = 0, sms = 152, per_sm = 4;
+  int dev = 0, v = 0, sms = 152, per_sm = LFX_ASM_DD_MIN_CTAS;
   if (cudaGetDevice(&dev) == cudaSuccess &&
       cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) {
     sms = v;

@@ -150,7 +150,7 @@ struct PhysParams {
 };
 
 // Elements the double-float assembly kernel processes in one wave over the whole device (resident
-// CTAs per SM x SMs x elements per CTA; GB300's 152 SMs x 4 x 32 when no device answers): the
+// CTAs per SM x SMs x elements per CTA; GB300's 152 SMs x 3 x 32 when no device answers): the
 // quantum the element colouring is balanced to.
 int64_t assemble_wave_elements();
 

@@ -123,15 +123,14 @@ def test_pattern_and_colouring(L, which):
 
 
 def test_colouring_balanced_to_assembly_waves(L):
-    """At 1M tets every colour exceeds one wave of the assembly kernel (GB300: 152 SMs x 4 CTAs x
-    32 elements = 19,456 elements, the value used when no device answers).  The colours are
+    """At 1M tets the colours span several waves of the assembly kernel (GB300: 152 SMs x 3 CTAs x
+    32 elements = 14,592 elements, the value used when no device answers).  The colours are
     rebalanced so that the waves launched, sum_c ceil(|c| / W), come within two of the work,
-    ceil(T / W) (the greedy sizes of this mesh launch 68 waves for 53 of work), and the colouring
-    stays valid."""
+    ceil(T / W), and the colouring stays valid."""
     m = cylinder(1.0, 10.0, n_tets=1_000_000, seed=2)
     mesh = L.Mesh.from_synthetic(m)
     col = mesh.colors()
-    T, W = m.n_tets, 152 * 4 * 32
+    T, W = m.n_tets, 152 * 3 * 32
     sizes = np.bincount(col)
     assert sizes.min() > 0
     waves = int(np.ceil(sizes / W).sum())
