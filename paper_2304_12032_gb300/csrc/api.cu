@@ -141,6 +141,8 @@ struct lfx_state {
   Gmres<float, float> gm32;
   DBuf r32, z32;
   int inner_total = 0;
+  int *inner_its = nullptr;      // page-locked: step counts of the inner solves of one outer solve
+  int inner_cap = 0, n_inner = 0;
   double t = 0.0, pin_value = 0.0;
   bool assembled = false;
   int amg_age = 0;
@@ -152,6 +154,7 @@ struct lfx_state {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e2) cudaEventDestroy(e2);
+    if (inner_its) cudaFreeHost(inner_its);
   }
   D4 *level(int l) { return hist[(head + l) % sigma].as<D4>(); }
   template <class S>
@@ -1116,8 +1119,44 @@ static lfx_status run_solve(lfx_state *s, double *x, bool x_zero, int *its, int 
   const BsrView<float> A32 = s->view<float>(s->vals32);
   s->inner_total = 0;
   const bool adaptive = o.inner_adaptive != 0;
-  auto inner = [s, A32, n, &o, adaptive](cudaStream_t q, const double *v, double *z, const KState *ks) -> lfx_status {
+  // single systems: the inner solves run without host round trips (tolerance from the outer's
+  // status on the device, step counts read back after the outer solve)
+  const bool async_inner = !s->gm32.segmented() && o.inner_max_iters <= s->gm32.restart;
+  if (async_inner && s->inner_cap < o.outer_max_iters + 2) {
+    if (s->inner_its) cudaFreeHost(s->inner_its);
+    s->inner_its = nullptr;
+    s->inner_cap = 0;
+    LFX_CUDA_TRY(cudaMallocHost(&s->inner_its, sizeof(int) * (size_t)(o.outer_max_iters + 2)));
+    s->inner_cap = o.outer_max_iters + 2;
+  }
+  s->n_inner = 0;
+  auto inner = [s, A32, n, &o, adaptive, async_inner](cudaStream_t q, const double *v, double *z,
+                                                      const KState *ks) -> lfx_status {
     LFX_TRY((launch_convert<double, float>(q, v, s->r32.as<float>(), n, ks)));
+    if (async_inner) {
+      int *slot = s->inner_its + std::min(s->n_inner, s->inner_cap - 1);
+      *slot = 0;
+      ++s->n_inner;
+      lfx_status rc;
+      if (o.smoother_bf16) {
+        const BsrView<__nv_bfloat16> Ab = s->view<__nv_bfloat16>(s->nopat);
+        auto pc = [s, Ab](cudaStream_t qq, const float *vv, float *zz, const KState *kk) {
+          return s->pcbf.apply(qq, Ab, vv, zz, kk);
+        };
+        rc = s->gm32.solve_inner(q, A32, pc, s->r32.as<float>(), s->z32.as<float>(), o.inner_rtol,
+                                 adaptive ? ks : nullptr, o.inner_rtol, 0.1, o.inner_max_iters,
+                                 o.reorthogonalize == 2, 2, slot);
+      } else {
+        auto pc = [s, A32](cudaStream_t qq, const float *vv, float *zz, const KState *kk) {
+          return s->pc32.apply(qq, A32, vv, zz, kk);
+        };
+        rc = s->gm32.solve_inner(q, A32, pc, s->r32.as<float>(), s->z32.as<float>(), o.inner_rtol,
+                                 adaptive ? ks : nullptr, o.inner_rtol, 0.1, o.inner_max_iters,
+                                 o.reorthogonalize == 2, 2, slot);
+      }
+      LFX_TRY(rc);
+      return launch_convert<float, double>(q, s->z32.as<float>(), z, n, ks);
+    }
     int it = 0;
     double r = 0.0;
     lfx_status rc;
@@ -1144,6 +1183,10 @@ static lfx_status run_solve(lfx_state *s, double *x, bool x_zero, int *its, int 
   };
   lfx_status rc = s->gmdd.solve(st, s->view_dd(), inner, s->rhs.as<double>(), x, o.gmres_rtol, o.outer_max_iters,
                                 o.reorthogonalize != 0, 0, x_zero, outer, rel);
+  if (async_inner) {
+    // the outer solve ended on a stream synchronisation, after every inner count was copied
+    for (int i = 0; i < std::min(s->n_inner, s->inner_cap); ++i) s->inner_total += s->inner_its[i];
+  }
   *its = s->inner_total;
   return rc;
 }

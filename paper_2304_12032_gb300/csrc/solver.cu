@@ -1504,6 +1504,45 @@ __global__ void cycle_start_kernel(const double *part, int nblk, KState *st) {
   }
 }
 
+// Start of an inner solve from x = 0 (r = b): ||b|| from the partial sums, the tolerance
+// eta ||b|| (eta = rtol, or from the outer flexible solve's status: 1/2 sqrt(tol / r) at its
+// cycle's first step, 1/2 tol / r after, within [lo, hi]), beta = ||b||, g = (beta, 0, ...).
+__global__ void inner_start_kernel(const double *part, int nblk, KState *st, const KState *outer, double rtol,
+                                   double lo, double hi) {
+  pdl_entry();
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i];
+  s = cta_sum(s);
+  if (threadIdx.x != 0) return;
+  const double beta = sqrt(s);
+  double eta = rtol;
+  if (outer != nullptr) {
+    eta = hi;
+    const double r = outer->res, tol = outer->tol_abs;
+    if (r > 0.0 && tol > 0.0 && isfinite(r)) {
+      const double need = tol / r;
+      eta = fmin(hi, 0.5 * (outer->j == 0 ? sqrt(need) : need));
+    }
+    eta = fmax(lo, eta);
+  }
+  st->bnorm = beta;
+  st->tol_abs = eta * beta;
+  st->total = 0;
+  st->beta = beta;
+  st->g[0] = beta;
+  st->j = 0;
+  st->res = beta;
+  st->flag = 0;
+  st->done = 0;
+  if (!isfinite(beta)) {
+    st->flag = 2;
+    st->done = 1;
+  } else if (beta <= st->tol_abs) {   // b = 0: x = 0 is the solution
+    st->flag = 1;
+    st->done = 1;
+  }
+}
+
 // y = H(0:j,0:j)^-1 g(0:j) by back substitution (j = completed steps of this cycle)
 __global__ void trisolve_kernel(KState *st) {
   pdl_entry();
@@ -1512,7 +1551,8 @@ __global__ void trisolve_kernel(KState *st) {
   for (int i = j - 1; i >= 0; --i) {
     double s = st->g[i];
     for (int k = i + 1; k < j; ++k) s -= st->H[(int64_t)k * (kMaxRestart + 1) + i] * st->y[k];
-    st->y[i] = s / st->H[(int64_t)i * (kMaxRestart + 1) + i];
+    const double d = st->H[(int64_t)i * (kMaxRestart + 1) + i];
+    st->y[i] = d != 0.0 ? s / d : 0.0;   // d = 0 only after a breakdown (w = 0)
   }
 }
 
@@ -2762,6 +2802,66 @@ lfx_status Gmres<S, T>::solve_seg(cudaStream_t st, const BsrView<S> &A, const Pr
   if (its_out) *its_out = total;
   if (res_out) *res_out = rel;
   return status;
+}
+
+template <class S, class T>
+lfx_status Gmres<S, T>::solve_inner(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, const T *b, T *x,
+                                    double rtol, const KState *outer, double lo, double hi, int maxit, bool cgs2,
+                                    int lag, int *its_pinned) {
+  if (n_seg > 1 || maxit > restart) {
+    set_error("GMRES: solve_inner needs one component and maxit <= restart");
+    return LFX_ERR_INVALID_ARG;
+  }
+  if (lag < 0) lag = 0;
+  if (lag > 2) lag = 2;
+  KState *ks = state.as<KState>();
+  T *Vb = basis.as<T>(), *Zb = zbasis.as<T>(), *w = work.as<T>();
+  double *pn = part_n.as<double>();
+  const int vg = vec_grid(n);
+  LFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
+  // r = b: ||b||, tolerance, v0 = b / beta
+  pdl_launch(norm_kernel<T>, vg, kThreads, 0, st, b, n, pn);
+  pdl_launch(inner_start_kernel, 1, kThreads, 0, st, pn, vg, ks, outer, rtol, lo, hi);
+  pdl_launch(scale_beta_kernel<T>, vg, kThreads, 0, st, b, Vb, n, ks);
+  note_launches(3);
+  const int steps = std::min(maxit, restart);
+  for (int j = 0; j < steps; ++j) {
+    T *vj = Vb + (int64_t)j * n, *vn = Vb + (int64_t)(j + 1) * n, *zj = Zb + (int64_t)j * n;
+    LFX_TRY(pc(st, vj, zj, ks));
+    if (n_tev + 2 > (int)tev.size()) {
+      for (int q = 0; q < 64; ++q) {
+        cudaEvent_t e;
+        LFX_CUDA_TRY(cudaEventCreate(&e));
+        tev.push_back(e);
+      }
+    }
+    LFX_CUDA_TRY(cudaEventRecord(tev[n_tev], st));
+    arnoldi_spmv(st, A, zj, w, ks);
+    LFX_CUDA_TRY(cudaEventRecord(tev[n_tev + 1], st));
+    n_tev += 2;
+    for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
+      pdl_launch(mdot_kernel<T>, dim3(nblk_dot, (j + 8) / 8), kThreads, 0, st, Vb, n, j + 1, w, n, part.as<double>(),
+                 nblk_dot, ks);
+      pdl_launch(mdot_finalize_kernel, j + 1, 32, 0, st, part.as<double>(), nblk_dot, nblk_dot, j + 1, ks, pass);
+      pdl_launch(maxpy_kernel<T>, vg, kThreads, 0, st, Vb, n, j + 1, w, n, pn, ks);
+    }
+    pdl_launch(givens_kernel, 1, kThreads, 0, st, pn, vg, ks, j, steps, maxit);
+    pdl_launch(scale_kernel<T>, vg, kThreads, 0, st, w, vn, n, &ks->scale, ks);
+    note_launches(2 + 3 * (cgs2 ? 2 : 1));
+    LFX_CUDA_TRY(cudaMemcpyAsync(pinned + (j & 3), &ks->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LFX_CUDA_TRY(cudaEventRecord(ev[j & 3], st));
+    // lagged convergence test: the host runs at most lag steps ahead of the device
+    if (j >= lag) {
+      LFX_CUDA_TRY(cudaEventSynchronize(ev[(j - lag) & 3]));
+      if (pinned[(j - lag) & 3]) break;
+    }
+  }
+  pdl_launch(trisolve_kernel, 1, 32, 0, st, ks);
+  pdl_launch(update_x_kernel<T, T>, vg, kThreads, 0, st, Zb, n, x, n, ks);
+  note_launches(2);
+  if (its_pinned) LFX_CUDA_TRY(cudaMemcpyAsync(its_pinned, &ks->total, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
 }
 
 template struct Gmres<double, double>;

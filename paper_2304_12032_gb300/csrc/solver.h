@@ -156,6 +156,14 @@ struct Gmres {
   // step reaches it); the tightest over the running components; within [lo, hi].  Reads the
   // status from the device (synchronises st).
   lfx_status inner_tolerance(cudaStream_t st, double lo, double hi, double *eta);
+  // One cycle from x = 0, as the preconditioner of a flexible outer solve, without waiting for the
+  // device: the tolerance is eta ||b|| with eta = rtol, or (outer != null) the rule of
+  // inner_tolerance evaluated on the device from the outer's status; no confirmation of the true
+  // residual (the outer solve tests its own).  The step count lands in *its_pinned (page-locked
+  // host memory) once the stream reaches it.  Needs maxit <= restart and one component.
+  lfx_status solve_inner(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, const T *b, T *x, double rtol,
+                         const KState *outer, double lo, double hi, int maxit, bool cgs2, int lag, int *its_pinned);
+  bool segmented() const { return n_seg > 1; }
   size_t device_bytes() const;
 
  private:
