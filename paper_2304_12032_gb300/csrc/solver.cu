@@ -2546,40 +2546,7 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
     pdl_launch(cycle_start_kernel, 1, kThreads, 0, st, pn, ng, ks);
     pdl_launch(scale_beta_kernel<T>, vg, kThreads, 0, st, w, Vb, n, ks);
     note_launches(2);
-    int launched = 0;
-    for (int j = 0; j < restart; ++j) {
-      T *vj = Vb + (int64_t)j * n, *vn = Vb + (int64_t)(j + 1) * n, *zj = Zb + (int64_t)j * n;
-      LFX_TRY(pc(st, vj, zj, ks));
-      if (n_tev + 2 > (int)tev.size()) {
-        for (int q = 0; q < 64; ++q) {
-          cudaEvent_t e;
-          LFX_CUDA_TRY(cudaEventCreate(&e));
-          tev.push_back(e);
-        }
-      }
-      LFX_CUDA_TRY(cudaEventRecord(tev[n_tev], st));
-      arnoldi_spmv(st, A, zj, w, ks);
-      LFX_CUDA_TRY(cudaEventRecord(tev[n_tev + 1], st));
-      n_tev += 2;
-      for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
-        pdl_launch(mdot_kernel<T>, dim3(nblk_dot, (j + 8) / 8), kThreads, 0, st, Vb, n, j + 1, w, n, part.as<double>(),
-                                                                          nblk_dot, ks);
-        pdl_launch(mdot_finalize_kernel, j + 1, 32, 0, st, part.as<double>(), nblk_dot, nblk_dot, j + 1, ks, pass);
-        pdl_launch(maxpy_kernel<T>, vg, kThreads, 0, st, Vb, n, j + 1, w, n, pn, ks);
-      }
-      pdl_launch(givens_kernel, 1, kThreads, 0, st, pn, vg, ks, j, restart, maxit);
-      pdl_launch(scale_kernel<T>, vg, kThreads, 0, st, w, vn, n, &ks->scale, ks);
-      note_launches(2 + 3 * (cgs2 ? 2 : 1));
-      LFX_CUDA_TRY(cudaMemcpyAsync(pinned + (j & 3), &ks->done, sizeof(int), cudaMemcpyDeviceToHost, st));
-      LFX_CUDA_TRY(cudaEventRecord(ev[j & 3], st));
-      launched = j + 1;
-      // lagged convergence test: the device runs at most two steps behind the host
-      if (j >= lag) {
-        LFX_CUDA_TRY(cudaEventSynchronize(ev[(j - lag) & 3]));
-        if (pinned[(j - lag) & 3]) break;
-      }
-    }
-    (void)launched;
+    LFX_TRY(arnoldi_cycle(st, A, pc, restart, maxit, cgs2, lag));
     pdl_launch(trisolve_kernel, 1, 32, 0, st, ks);
     pdl_launch(update_x_kernel<T, T>, vg, kThreads, 0, st, Zb, n, x, n, ks);
     note_launches(2);
@@ -2736,17 +2703,7 @@ lfx_status Gmres<S, T>::solve_seg(cudaStream_t st, const BsrView<S> &A, const Pr
     for (int j = 0; j < restart; ++j) {
       T *vj = Vb + (int64_t)j * n, *vn = Vb + (int64_t)(j + 1) * n, *zj = Zb + (int64_t)j * n;
       LFX_TRY(pc(st, vj, zj, ks));
-      if (n_tev + 2 > (int)tev.size()) {
-        for (int q = 0; q < 64; ++q) {
-          cudaEvent_t e;
-          LFX_CUDA_TRY(cudaEventCreate(&e));
-          tev.push_back(e);
-        }
-      }
-      LFX_CUDA_TRY(cudaEventRecord(tev[n_tev], st));
-      arnoldi_spmv(st, A, zj, w, ks);
-      LFX_CUDA_TRY(cudaEventRecord(tev[n_tev + 1], st));
-      n_tev += 2;
+      LFX_TRY(timed_spmv(st, A, zj, w, ks));
       for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
         pdl_launch(seg_mdot_kernel<T>, dim3(nt, (j + 8) / 8), kThreads, 0, st, Vb, n, j + 1, w, pd, tk, ks);
         pdl_launch(seg_finalize_kernel, fin_grid, kThreads, 0, st, pd, j + 1, tk, kseg, ks, pass);
@@ -2804,6 +2761,57 @@ lfx_status Gmres<S, T>::solve_seg(cudaStream_t st, const BsrView<S> &A, const Pr
   return status;
 }
 
+// The Arnoldi product w = A z, bracketed by CUDA events for the SpMV timing statistics.
+template <class S, class T>
+lfx_status Gmres<S, T>::timed_spmv(cudaStream_t st, const BsrView<S> &A, const T *z, T *w, const KState *ks) {
+  if (n_tev + 2 > (int)tev.size()) {
+    for (int q = 0; q < 64; ++q) {
+      cudaEvent_t e;
+      LFX_CUDA_TRY(cudaEventCreate(&e));
+      tev.push_back(e);
+    }
+  }
+  LFX_CUDA_TRY(cudaEventRecord(tev[n_tev], st));
+  arnoldi_spmv(st, A, z, w, ks);
+  LFX_CUDA_TRY(cudaEventRecord(tev[n_tev + 1], st));
+  n_tev += 2;
+  return LFX_OK;
+}
+
+// Steps j = 0 .. m-1 of one Arnoldi cycle from v_0 (flexible: z_j = M^-1 v_j kept), classical
+// Gram-Schmidt (twice with cgs2), Givens rotations and the stopping test on the device; the host
+// reads the device's stop flag lag steps behind the launches, so the device always has queued work.
+template <class S, class T>
+lfx_status Gmres<S, T>::arnoldi_cycle(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, int m, int maxit,
+                                      bool cgs2, int lag) {
+  KState *ks = state.as<KState>();
+  T *Vb = basis.as<T>(), *Zb = zbasis.as<T>(), *w = work.as<T>();
+  double *pn = part_n.as<double>();
+  const int vg = vec_grid(n);
+  for (int j = 0; j < m; ++j) {
+    T *vj = Vb + (int64_t)j * n, *vn = Vb + (int64_t)(j + 1) * n, *zj = Zb + (int64_t)j * n;
+    LFX_TRY(pc(st, vj, zj, ks));
+    LFX_TRY(timed_spmv(st, A, zj, w, ks));
+    for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
+      pdl_launch(mdot_kernel<T>, dim3(nblk_dot, (j + 8) / 8), kThreads, 0, st, Vb, n, j + 1, w, n, part.as<double>(),
+                 nblk_dot, ks);
+      pdl_launch(mdot_finalize_kernel, j + 1, 32, 0, st, part.as<double>(), nblk_dot, nblk_dot, j + 1, ks, pass);
+      pdl_launch(maxpy_kernel<T>, vg, kThreads, 0, st, Vb, n, j + 1, w, n, pn, ks);
+    }
+    pdl_launch(givens_kernel, 1, kThreads, 0, st, pn, vg, ks, j, m, maxit);
+    pdl_launch(scale_kernel<T>, vg, kThreads, 0, st, w, vn, n, &ks->scale, ks);
+    note_launches(2 + 3 * (cgs2 ? 2 : 1));
+    LFX_CUDA_TRY(cudaMemcpyAsync(pinned + (j & 3), &ks->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LFX_CUDA_TRY(cudaEventRecord(ev[j & 3], st));
+    if (j >= lag) {
+      LFX_CUDA_TRY(cudaEventSynchronize(ev[(j - lag) & 3]));
+      if (pinned[(j - lag) & 3]) break;
+    }
+  }
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
 template <class S, class T>
 lfx_status Gmres<S, T>::solve_inner(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, const T *b, T *x,
                                     double rtol, const KState *outer, double lo, double hi, int maxit, bool cgs2,
@@ -2815,7 +2823,7 @@ lfx_status Gmres<S, T>::solve_inner(cudaStream_t st, const BsrView<S> &A, const 
   if (lag < 0) lag = 0;
   if (lag > 2) lag = 2;
   KState *ks = state.as<KState>();
-  T *Vb = basis.as<T>(), *Zb = zbasis.as<T>(), *w = work.as<T>();
+  T *Vb = basis.as<T>(), *Zb = zbasis.as<T>();
   double *pn = part_n.as<double>();
   const int vg = vec_grid(n);
   LFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
@@ -2824,38 +2832,7 @@ lfx_status Gmres<S, T>::solve_inner(cudaStream_t st, const BsrView<S> &A, const 
   pdl_launch(inner_start_kernel, 1, kThreads, 0, st, pn, vg, ks, outer, rtol, lo, hi);
   pdl_launch(scale_beta_kernel<T>, vg, kThreads, 0, st, b, Vb, n, ks);
   note_launches(3);
-  const int steps = std::min(maxit, restart);
-  for (int j = 0; j < steps; ++j) {
-    T *vj = Vb + (int64_t)j * n, *vn = Vb + (int64_t)(j + 1) * n, *zj = Zb + (int64_t)j * n;
-    LFX_TRY(pc(st, vj, zj, ks));
-    if (n_tev + 2 > (int)tev.size()) {
-      for (int q = 0; q < 64; ++q) {
-        cudaEvent_t e;
-        LFX_CUDA_TRY(cudaEventCreate(&e));
-        tev.push_back(e);
-      }
-    }
-    LFX_CUDA_TRY(cudaEventRecord(tev[n_tev], st));
-    arnoldi_spmv(st, A, zj, w, ks);
-    LFX_CUDA_TRY(cudaEventRecord(tev[n_tev + 1], st));
-    n_tev += 2;
-    for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
-      pdl_launch(mdot_kernel<T>, dim3(nblk_dot, (j + 8) / 8), kThreads, 0, st, Vb, n, j + 1, w, n, part.as<double>(),
-                 nblk_dot, ks);
-      pdl_launch(mdot_finalize_kernel, j + 1, 32, 0, st, part.as<double>(), nblk_dot, nblk_dot, j + 1, ks, pass);
-      pdl_launch(maxpy_kernel<T>, vg, kThreads, 0, st, Vb, n, j + 1, w, n, pn, ks);
-    }
-    pdl_launch(givens_kernel, 1, kThreads, 0, st, pn, vg, ks, j, steps, maxit);
-    pdl_launch(scale_kernel<T>, vg, kThreads, 0, st, w, vn, n, &ks->scale, ks);
-    note_launches(2 + 3 * (cgs2 ? 2 : 1));
-    LFX_CUDA_TRY(cudaMemcpyAsync(pinned + (j & 3), &ks->done, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LFX_CUDA_TRY(cudaEventRecord(ev[j & 3], st));
-    // lagged convergence test: the host runs at most lag steps ahead of the device
-    if (j >= lag) {
-      LFX_CUDA_TRY(cudaEventSynchronize(ev[(j - lag) & 3]));
-      if (pinned[(j - lag) & 3]) break;
-    }
-  }
+  LFX_TRY(arnoldi_cycle(st, A, pc, std::min(maxit, restart), maxit, cgs2, lag));
   pdl_launch(trisolve_kernel, 1, 32, 0, st, ks);
   pdl_launch(update_x_kernel<T, T>, vg, kThreads, 0, st, Zb, n, x, n, ks);
   note_launches(2);

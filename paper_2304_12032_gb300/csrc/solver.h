@@ -167,6 +167,9 @@ struct Gmres {
   size_t device_bytes() const;
 
  private:
+  lfx_status timed_spmv(cudaStream_t st, const BsrView<S> &A, const T *z, T *w, const KState *ks);
+  lfx_status arnoldi_cycle(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, int m, int maxit, bool cgs2,
+                           int lag);
   int n_seg = 0;
   SegTasks tasks{};
   DBuf seg_lo, seg_hi, seg_id, seg_toff, seg_state, seg_part, seg_pn;
