@@ -27,8 +27,8 @@ sys.path.insert(0, ROOT)
 R_CM, L_CM, U_PEAK, RHO, MU, DT = 1.0, 10.0, 20.0, 1.06, 0.035, 1e-3
 RAMP = 0.05                      # s, sinusoidal ramp of the inflow (Section 2.2.1)
 L2_BYTES = 129 * 2 ** 20
-FP64_PEAK_TFLOPS = 1.20            # measured FP64 FMA-throughput probe on this GB300
-FP32_ISSUE_PEAK_T = 35.96          # measured FP32 FMA-issue probe, T thread-instructions/s
+FP64_PEAK_TFLOPS = 1.20            # measured FP64 FMA-throughput probe on a GB300 (nvcc-built, run once)
+FP32_ISSUE_PEAK_T = 35.96          # measured FP32 FMA-issue probe on a GB300, T thread-instructions/s
 # FP64-class operations of the method per tetrahedron (DFMA x 2 + DADD + DMUL executed by the FP64
 # assembly kernel, counted with ncu): the algorithmic work of one element's assembly
 ASM_FP64_FLOPS_PER_ELEMENT = 2948
@@ -235,7 +235,7 @@ def run_gpu(args):
                     "bound": "alu", "achieved": round(inst_rate, 3), "peak": FP32_ISSUE_PEAK_T,
                     "unit": "T thread-inst/s", "frac": round(inst_rate / FP32_ISSUE_PEAK_T, 4),
                     "traffic": int(ASM_DD_DRAM_BYTES_PER_ELEMENT * T / n_asm),
-                    "peak_source": "measured FP32 FMA-issue probe (DESIGN.md)",
+                    "peak_source": "measured FP32 FMA-issue probe (nvcc-built, run once on a GB300)",
                     "inst_per_element": ASM_DD_INST_PER_ELEMENT,
                     "fp64_class_tflops": round(asm_flops / (asm_ms * 1e-3) / 1e12, 4),
                     "fp64_class_flops_per_element": ASM_FP64_FLOPS_PER_ELEMENT,
@@ -247,7 +247,7 @@ def run_gpu(args):
         roof_asm = {"kernel": "assemble_color_kernel<double> (all colours of one step)", "bound": "alu",
                     "achieved": round(asm_flops / (asm_ms * 1e-3) / 1e12, 4), "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": round(asm_flops / (asm_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
-                    "traffic": None, "peak_source": "measured FP64 FMA probe (DESIGN.md)",
+                    "traffic": None, "peak_source": "measured FP64 FMA probe (nvcc-built, run once on a GB300)",
                     "hbm_view": {"achieved_gbs": round(asm_bytes / (asm_ms * 1e-3) / 1e9, 1),
                                  "algorithmic_bytes": int(asm_bytes)},
                     "ms_per_step": round(asm_ms, 4), "ms_per_launch": round(asm_ms / n_asm, 4),

@@ -3,7 +3,7 @@
 Tolerances (FP64 path): assembled entries within 1e-12 relative to the largest entry of their
 scalar row (summation order differs: colour order on the GPU, COO summation in the oracle);
 SpMV and preconditioner within 1e-12 / 1e-10 of the scale of the result; solutions within
-1e-6 relative L2 (BASELINE target), in practice ~1e-9."""
+1e-6 relative L2 (the target accuracy), in practice ~1e-9."""
 import dataclasses
 
 import numpy as np
