@@ -382,7 +382,7 @@ def run_serving(args):
 
 
 def run_batched(args):
-    """Batched workload (config 4): args.batch independent pipe and Y-bifurcation meshes of seeded
+    """Batched workload: args.batch independent pipe and Y-bifurcation meshes of seeded
     sizes uniform in [args.batch_min, args.batch_max] tets, stepped as ONE system (one coloured
     assembly launch per colour; one Krylov solve for all of them with one Arnoldi process per
     mesh, sharing every launch; per-mesh row normalisation), against the same meshes stepped one

@@ -65,7 +65,7 @@ def vessel_case(n_tets=6000, seed=21, order=2, stab=2, diffusion=0, riis=True, n
 
 
 def stenosis_case(n_tets=8000, seed=3, order=2, harmonics=3):
-    """Config-3 shape at small size: cosine stenosis (75 % area reduction), Womersley inlet
+    """The stenosis-with-valve workload at small size: cosine stenosis (75 % area reduction), Womersley inlet
     with a Fourier flow rate (period 1 s), a disk resistive surface downstream, VMS-LES."""
     R, L = 1.0, 10.0
     m = stenosis(R, L, n_tets=n_tets, seed=seed)

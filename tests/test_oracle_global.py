@@ -12,7 +12,7 @@ from synthetic import (beltrami_grad_u, beltrami_p, beltrami_u, cube_kuhn, cylin
 
 
 def beltrami_run(n, steps=10, dt=1e-3, order=1, stab=2):
-    """Config-1 set-up: unit cube, rho = mu = 1, exact Dirichlet data on all faces (made
+    """Beltrami set-up: unit cube, rho = mu = 1, exact Dirichlet data on all faces (made
     discretely flux-free), pressure pinned at node 0 to the exact value."""
     m = cube_kuhn(n)
     P = O.Params(rho=1.0, mu=1.0, dt=dt, bdf_order=order, stab=stab)
