@@ -1504,6 +1504,28 @@ __global__ void cycle_start_kernel(const double *part, int nblk, KState *st) {
   }
 }
 
+// Start of a solve: ||b|| from the partial sums, the tolerance rtol ||b||, the step count.
+__global__ void solve_start_kernel(const double *part, int nblk, KState *st, double rtol) {
+  pdl_entry();
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i];
+  s = cta_sum(s);
+  if (threadIdx.x != 0) return;
+  const double bnorm = sqrt(s);
+  st->bnorm = bnorm;
+  st->tol_abs = rtol * bnorm;
+  st->total = 0;
+}
+
+// x = 0 when *bnorm == 0 (the solution of A x = 0)
+template <class T>
+__global__ void zero_if_b_zero_kernel(T *x, int64_t n, const double *bnorm) {
+  pdl_entry();
+  if (*bnorm != 0.0) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = T(0);
+}
+
 // Start of an inner solve from x = 0 (r = b): ||b|| from the partial sums, the tolerance
 // eta ||b|| (eta = rtol, or from the outer flexible solve's status: 1/2 sqrt(tol / r) at its
 // cycle's first step, 1/2 tol / r after, within [lo, hi]), beta = ||b||, g = (beta, 0, ...).
@@ -2514,75 +2536,68 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
   T *Vb = basis.as<T>(), *Zb = zbasis.as<T>(), *w = work.as<T>();
   double *pn = part_n.as<double>();
   const int vg = vec_grid(n);
-  // ||b||
+  // ||b|| and the tolerance on the device; x = 0 to start from, or as the solution when b = 0
   pdl_launch(norm_kernel<T>, vg, kThreads, 0, st, b, n, pn);
-  pdl_launch(reduce_kernel, 1, kThreads, 0, st, pn, vg, &ks->bnorm, 1);
-  note_launches(2);
-  KState hs;
-  LFX_CUDA_TRY(cudaMemcpyAsync(&hs, ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
-  LFX_CUDA_TRY(cudaStreamSynchronize(st));
-  const double bnorm = hs.bnorm;
-  if (!std::isfinite(bnorm)) {
-    set_error("GMRES: right-hand side is not finite");
-    return LFX_ERR_NONFINITE;
-  }
-  double tol_abs = rtol * bnorm;
-  LFX_CUDA_TRY(cudaMemcpyAsync(&ks->tol_abs, &tol_abs, sizeof(double), cudaMemcpyHostToDevice, st));
-  int zero = 0;
-  LFX_CUDA_TRY(cudaMemcpyAsync(&ks->total, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+  pdl_launch(solve_start_kernel, 1, kThreads, 0, st, pn, vg, ks, rtol);
+  if (x_zero) LFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
+  pdl_launch(zero_if_b_zero_kernel<T>, vg, kThreads, 0, st, x, n, &ks->bnorm);
+  note_launches(3);
   int total = 0;
   double rel = 1.0;
   lfx_status status = LFX_ERR_NOT_CONVERGED;
-  if (bnorm == 0.0 || x_zero) LFX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
-  if (bnorm == 0.0) {
-    if (its_out) *its_out = 0;
-    if (res_out) *res_out = 0.0;
-    return LFX_OK;
-  }
+  KState hs;
+  int ng = 0;
+  bool have_r = false;   // w = b - A x and its partial sums are in place (from the previous cycle)
   for (int cycle = 0; cycle < 100000; ++cycle) {
     // r = b - A x -> w, beta, v0 = r / beta
-    int ng = 0;
-    LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, pn, &ng)));
+    if (!have_r) LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, pn, &ng)));
     pdl_launch(cycle_start_kernel, 1, kThreads, 0, st, pn, ng, ks);
     pdl_launch(scale_beta_kernel<T>, vg, kThreads, 0, st, w, Vb, n, ks);
     note_launches(2);
     LFX_TRY(arnoldi_cycle(st, A, pc, restart, maxit, cgs2, lag));
     pdl_launch(trisolve_kernel, 1, 32, 0, st, ks);
     pdl_launch(update_x_kernel<T, T>, vg, kThreads, 0, st, Zb, n, x, n, ks);
-    note_launches(2);
-    LFX_CUDA_TRY(cudaMemcpyAsync(&hs, ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    // the true residual, which confirms convergence or starts the next cycle; one read of the
+    // status header for both
+    LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, pn, &ng)));
+    pdl_launch(reduce_kernel, 1, kThreads, 0, st, pn, ng, &ks->res, 1);
+    note_launches(3);
+    LFX_CUDA_TRY(cudaMemcpyAsync(&hs, ks, offsetof(KState, H), cudaMemcpyDeviceToHost, st));
     LFX_CUDA_TRY(cudaStreamSynchronize(st));
     LFX_CUDA_TRY(cudaGetLastError());
     total = hs.total;
+    if (!std::isfinite(hs.bnorm)) {
+      set_error("GMRES: right-hand side is not finite");
+      status = LFX_ERR_NONFINITE;
+      break;
+    }
+    if (hs.bnorm == 0.0) {   // x = 0
+      total = 0;
+      rel = 0.0;
+      status = LFX_OK;
+      break;
+    }
     if (hs.flag == 2) {
       set_error("GMRES: non-finite residual after %d steps", total);
       status = LFX_ERR_NONFINITE;
       break;
     }
-    if (hs.flag == 1 || total >= maxit) {
-      // confirm with the true residual
-      LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, pn, &ng)));
-      pdl_launch(reduce_kernel, 1, kThreads, 0, st, pn, ng, &ks->res, 1);
-      note_launches(1);
-      double tr = 0.0;
-      LFX_CUDA_TRY(cudaMemcpyAsync(&tr, &ks->res, sizeof(double), cudaMemcpyDeviceToHost, st));
-      LFX_CUDA_TRY(cudaStreamSynchronize(st));
-      rel = tr / bnorm;
-      if (!std::isfinite(rel)) {
-        status = LFX_ERR_NONFINITE;
-        set_error("GMRES: non-finite true residual");
-        break;
-      }
-      if (tr <= 2.0 * tol_abs) {
-        status = LFX_OK;
-        break;
-      }
-      if (total >= maxit) {
-        set_error("GMRES: not converged after %d steps (relative residual %.3e)", total, rel);
-        status = LFX_ERR_NOT_CONVERGED;
-        break;
-      }
+    rel = hs.res / hs.bnorm;
+    if (!std::isfinite(rel)) {
+      status = LFX_ERR_NONFINITE;
+      set_error("GMRES: non-finite true residual");
+      break;
     }
+    if (hs.res <= 2.0 * hs.tol_abs) {
+      status = LFX_OK;
+      break;
+    }
+    if (total >= maxit) {
+      set_error("GMRES: not converged after %d steps (relative residual %.3e)", total, rel);
+      status = LFX_ERR_NOT_CONVERGED;
+      break;
+    }
+    have_r = true;
   }
   if (its_out) *its_out = total;
   if (res_out) *res_out = rel;
