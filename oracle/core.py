@@ -14,6 +14,13 @@ Readings of the paper used here (it is silent on them):
   * Parabolic/uniform profiles: centre = area-weighted barycentre of the tagged faces, n = the
     normalised area-weighted outward normal of those faces.
   * Neumann data: h(t) enters as -(h n, v) on the tagged faces (P1: A_f/3 per vertex).
+  * Inertial backflow stabilisation (Section 2.2.2, beta > 0 on a Neumann tag): semi-implicit
+    like the rest of the step, the term beta rho/2 |u* . n|_- (u, v) with u* = u^EXT moves to the
+    matrix as c(x) (u, v)_Gamma, c = -beta rho/2 min(u* . n, 0) >= 0, integrated with the
+    degree-2 rule of the three edge midpoints (weights A_f/3).
+  * Resistance condition (Section 2.2.3, u_ALE = 0): implicit in u, the flux term becomes the
+    rank-one matrix C_R w w^T with w_{4a+i} = int_Gamma phi_a n_i (so w . u is the exact flux of
+    a P1 velocity), and p_0(t) enters as -(p_0 n, v) like Neumann data.
 """
 from __future__ import annotations
 
@@ -32,7 +39,8 @@ __all__ = [
     "Params", "BC", "RIIS", "Problem", "load_library", "bdf_coefficients", "element",
     "element_residual", "geometry", "tau", "assemble", "time_law", "boundary_geometry",
     "dirichlet_data", "neumann_rhs", "apply_dirichlet", "solve_direct", "Step",
-    "step", "relative_errors", "disk_sdf", "block_of", "womersley_profile",
+    "step", "relative_errors", "disk_sdf", "block_of", "womersley_profile", "backflow_matrix",
+    "resistance_vectors", "resistance_terms",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -121,7 +129,8 @@ class BC:
     """Boundary condition on one tag (Section 2.2).
 
     kind: 'noslip' | 'dirichlet' (g = theta g(t) s(x)) | 'nodal' (values given per step) |
-          'neumann' (sigma n = -h(t) n).
+          'neumann' (sigma n = -h(t) n, plus beta rho/2 |u . n|_- u when beta > 0) |
+          'resistance' (sigma n = -(p_0(t) + resistance * int u . n) n, p_0 from time/tparams).
     time: 'constant' {value} | 'pulsatile' {gmin, gmax, period} | 'ramp' {g0, g1, t0, tL} |
           'fourier' {period, a (cosine coefficients a_0..a_K), b (sine coefficients, b_0 unused)}.
     space: 'parabolic' {radius} | 'uniform' | 'womersley' {radius; time must be 'fourier'}.
@@ -133,6 +142,8 @@ class BC:
     space: str = "uniform"
     radius: float = 1.0
     theta: float = 1.0
+    beta: float = 0.0              # inertial backflow stabilisation on a Neumann tag (0: off)
+    resistance: float = 0.0        # C_R of a resistance tag
 
 
 @dataclasses.dataclass
@@ -400,6 +411,66 @@ def neumann_rhs(mesh, problem: Problem, t: float) -> np.ndarray:
     return r
 
 
+def _face_area_vectors(nodes, faces):
+    x = nodes[faces]
+    return 0.5 * np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0])    # A_f n_f per face
+
+
+def backflow_matrix(mesh, problem: Problem, uext: np.ndarray) -> sp.csr_matrix:
+    """Inertial backflow stabilisation on the Neumann tags with beta > 0 (Section 2.2.2):
+    c(x) (u, v)_Gamma, c = -beta rho/2 min(u* . n, 0), edge-midpoint rule on each face."""
+    V = mesh.nodes.shape[0]
+    rows, cols, vals = [], [], []
+    rho = problem.params.rho
+    for bc in problem.bcs:
+        if bc.kind != "neumann" or bc.beta <= 0.0:
+            continue
+        f = mesh.bfaces[mesh.btags == bc.tag].astype(np.int64)
+        an = _face_area_vectors(mesh.nodes, f)
+        area = np.linalg.norm(an, axis=1)
+        n = an / area[:, None]
+        for (i, j) in ((0, 1), (1, 2), (0, 2)):
+            um = 0.5 * (uext[f[:, i]] + uext[f[:, j]])               # u* at the edge midpoint
+            c = -bc.beta * rho / 2.0 * np.minimum(np.sum(um * n, axis=1), 0.0) * area / 3.0
+            # phi = 1/2 at the edge's two vertices, 0 at the third
+            for a in (i, j):
+                for b in (i, j):
+                    for comp in range(3):
+                        rows.append(4 * f[:, a] + comp)
+                        cols.append(4 * f[:, b] + comp)
+                        vals.append(0.25 * c)
+    if not rows:
+        return sp.csr_matrix((4 * V, 4 * V))
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(4 * V, 4 * V)).tocsr()
+
+
+def resistance_vectors(mesh, tag) -> np.ndarray:
+    """w with w_{4a+i} = int_Gamma phi_a n_i over the faces of the tag (P1: A_f n_f / 3 per vertex)."""
+    V = mesh.nodes.shape[0]
+    f = mesh.bfaces[mesh.btags == tag].astype(np.int64)
+    an = _face_area_vectors(mesh.nodes, f)
+    w = np.zeros(4 * V)
+    for k in range(3):
+        for i in range(3):
+            np.add.at(w, 4 * f[:, k] + i, an[:, i] / 3.0)
+    return w
+
+
+def resistance_terms(mesh, problem: Problem, t: float):
+    """Resistance tags (Section 2.2.3): the rank-one matrices C_R w w^T (as a list of (C_R, w))
+    and the right-hand side -p_0(t) w summed over the tags."""
+    V = mesh.nodes.shape[0]
+    terms, r = [], np.zeros(4 * V)
+    for bc in problem.bcs:
+        if bc.kind != "resistance":
+            continue
+        w = resistance_vectors(mesh, bc.tag)
+        terms.append((bc.resistance, w))
+        r -= time_law(bc.time, t, bc.tparams) * w
+    return terms, r
+
+
 def apply_dirichlet(A: sp.csr_matrix, b: np.ndarray, rows, values):
     """Replace each constrained row r by s e_r and b_r by s g_r, s = |A_rr| (1 if zero)."""
     A = A.tocsr(copy=True)
@@ -455,6 +526,13 @@ def step(mesh, problem: Problem, u_hist: Sequence[np.ndarray], p_hist: Sequence[
     pext = sum(gamma[j] * p_hist[j] for j in range(s))
     A, b = assemble(prm, mesh.nodes, mesh.tets, ubdf, uext, pext, problem.riis)
     b = b + neumann_rhs(mesh, problem, t_next)
+    A = A + backflow_matrix(mesh, problem, uext)
+    terms, rres = resistance_terms(mesh, problem, t_next)
+    b = b + rres
+    for cr, w in terms:                      # rank-one: dense over the tag's velocity DoFs
+        nz = np.nonzero(w)[0]
+        A = A + sp.coo_matrix((cr * np.outer(w[nz], w[nz]).ravel(),
+                               (np.repeat(nz, nz.size), np.tile(nz, nz.size))), shape=A.shape).tocsr()
     ids, vals = dirichlet_data(mesh, problem, t_next, nodal)
     rows = (4 * ids[:, None] + np.arange(3)[None, :]).ravel()
     rv = vals.ravel()
