@@ -118,13 +118,18 @@ enum { LFX_PROFILE_UNIFORM = 0, LFX_PROFILE_PARABOLIC = 1, LFX_PROFILE_WOMERSLEY
  *            Fourier harmonic of g (needs time.kind == LFX_TIME_FOURIER).
  *  NODAL     u given per node and per step by lfx_set_dirichlet_nodal.
  *  NEUMANN   sigma n = -h(t) n (Eq. bcs-neumann), h = time law; h = 0 is the natural condition.
+ *            With beta > 0, inertial backflow stabilisation (Section 2.2.2): + beta rho/2
+ *            |u . n|_- u, semi-implicit: the matrix gains c (u, v) on the faces with
+ *            c = -beta rho/2 min(u^EXT . n, 0), integrated at the three edge midpoints of each face.
  * Where tags meet: NOSLIP > DIRICHLET/NODAL > NEUMANN.  center/normal: if given_geometry is 0
- * they are computed as the area-weighted barycentre and outward normal of the tagged faces. */
+ * they are computed as the area-weighted barycentre and outward normal of the tagged faces.
+ * beta must be >= 0, and 0 for kinds other than NEUMANN (LFX_ERR_INVALID_ARG otherwise). */
 typedef struct lfx_bc {
   int32_t tag, kind, profile, given_geometry;
   lfx_time_law time;
   double theta, radius;
   double center[3], normal[3];
+  double beta;
 } lfx_bc;
 
 enum { LFX_RIIS_DISK = 0, LFX_RIIS_SDF_NODAL = 1 };

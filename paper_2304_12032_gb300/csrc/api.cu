@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -104,6 +105,11 @@ struct lfx_problem {
   // Neumann data: rhs(node) -= h(t) * vec(node) per Neumann BC
   std::vector<int32_t> neu_node, neu_bc;
   DBuf d_neu_node, d_neu_bc, d_neu_vec;
+  // inertial backflow stabilisation: one task per edge of a face of a Neumann tag with beta > 0
+  // (nodes i, j; the face's area vector A_f n_f; beta rho / 2; the compact indices of blocks
+  // (i,i), (i,j), (j,i), (j,j)); the compact blocks' matrix slots and FP64 accumulators
+  int64_t n_bf_edges = 0, n_bf_blocks = 0;
+  DBuf d_bf_ij, d_bf_an, d_bf_coef, d_bf_slot4, d_bf_blk, d_bf_acc;
   // RIIS nodal signed distances [n_riis][V]
   DBuf d_phi;
   DBuf d_bad;
@@ -114,7 +120,8 @@ struct lfx_problem {
   int64_t n_bad = 0;
   size_t device_bytes() const {
     return d_dir_node.bytes + d_dir_bc.bytes + d_S.bytes + d_neu_node.bytes + d_neu_bc.bytes +
-           d_neu_vec.bytes + d_phi.bytes + d_bad.bytes + geo64.bytes + geo_hi.bytes + geo_lo.bytes;
+           d_neu_vec.bytes + d_phi.bytes + d_bad.bytes + geo64.bytes + geo_hi.bytes + geo_lo.bytes +
+           d_bf_ij.bytes + d_bf_an.bytes + d_bf_coef.bytes + d_bf_slot4.bytes + d_bf_blk.bytes + d_bf_acc.bytes;
   }
 };
 
@@ -477,6 +484,10 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
       set_error("lfx_problem_create: too many Fourier harmonics");
       return LFX_ERR_INVALID_ARG;
     }
+    if (!(bc.beta >= 0.0) || (bc.beta != 0.0 && bc.kind != LFX_BC_NEUMANN)) {
+      set_error("lfx_problem_create: backflow stabilisation beta must be >= 0, and only on Neumann tags");
+      return LFX_ERR_INVALID_ARG;
+    }
     if (bc.kind == LFX_BC_NEUMANN) continue;
     const int p = bc.kind == LFX_BC_NOSLIP ? 3 : 2;
     for (int64_t f = 0; f < m.F; ++f) {
@@ -606,6 +617,67 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
       LFX_CUDA_TRY(cudaMemcpy(pb->d_neu_node.p, pb->neu_node.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice));
       LFX_CUDA_TRY(cudaMemcpy(pb->d_neu_bc.p, pb->neu_bc.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice));
       LFX_CUDA_TRY(cudaMemcpy(pb->d_neu_vec.p, vec.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice));
+    }
+  }
+
+  // ---- inertial backflow stabilisation (Section 2.2.2): tasks per face edge
+  {
+    auto block_of = [&](int32_t r, int32_t c) -> int32_t {
+      const auto b0 = m.col_idx.begin() + m.row_ptr[r], b1 = m.col_idx.begin() + m.row_ptr[r + 1];
+      const auto it = std::lower_bound(b0, b1, c);
+      return (it != b1 && *it == c) ? (int32_t)(it - m.col_idx.begin()) : -1;
+    };
+    std::vector<int32_t> ij, slot4, blk;
+    std::vector<double> an, coef;
+    std::unordered_map<int32_t, int32_t> compact;
+    for (int b = 0; b < n_bcs; ++b) {
+      if (bcs[b].kind != LFX_BC_NEUMANN || bcs[b].beta <= 0.0) continue;
+      for (int64_t f = 0; f < m.F; ++f) {
+        if (m.btags[f] != bcs[b].tag) continue;
+        const int32_t *fv = &m.bfaces[3 * f];
+        const double *x0 = &m.xyz[3 * (int64_t)fv[0]], *x1 = &m.xyz[3 * (int64_t)fv[1]], *x2 = &m.xyz[3 * (int64_t)fv[2]];
+        double u[3], v[3];
+        for (int k = 0; k < 3; ++k) {
+          u[k] = x1[k] - x0[k];
+          v[k] = x2[k] - x0[k];
+        }
+        const double a[3] = {0.5 * (u[1] * v[2] - u[2] * v[1]), 0.5 * (u[2] * v[0] - u[0] * v[2]),
+                             0.5 * (u[0] * v[1] - u[1] * v[0])};
+        const int e[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+        for (int q = 0; q < 3; ++q) {
+          const int32_t i = fv[e[q][0]], j = fv[e[q][1]];
+          ij.push_back(i);
+          ij.push_back(j);
+          for (int k = 0; k < 3; ++k) an.push_back(a[k]);
+          coef.push_back(bcs[b].beta * rho / 2.0);
+          const int32_t pr[4][2] = {{i, i}, {i, j}, {j, i}, {j, j}};
+          for (int t = 0; t < 4; ++t) {
+            const int32_t s = block_of(pr[t][0], pr[t][1]);
+            if (s < 0) {
+              set_error("lfx_problem_create: boundary face edge outside the block pattern");
+              return LFX_ERR_BAD_MESH;
+            }
+            auto ins = compact.emplace(s, (int32_t)blk.size());
+            if (ins.second) blk.push_back(s);
+            slot4.push_back(ins.first->second);
+          }
+        }
+      }
+    }
+    pb->n_bf_edges = (int64_t)coef.size();
+    pb->n_bf_blocks = (int64_t)blk.size();
+    if (pb->n_bf_edges > 0) {
+      LFX_TRY(pb->d_bf_ij.alloc(sizeof(int32_t) * ij.size()));
+      LFX_TRY(pb->d_bf_an.alloc(sizeof(double) * an.size()));
+      LFX_TRY(pb->d_bf_coef.alloc(sizeof(double) * coef.size()));
+      LFX_TRY(pb->d_bf_slot4.alloc(sizeof(int32_t) * slot4.size()));
+      LFX_TRY(pb->d_bf_blk.alloc(sizeof(int32_t) * blk.size()));
+      LFX_TRY(pb->d_bf_acc.alloc(sizeof(double) * blk.size()));
+      LFX_CUDA_TRY(cudaMemcpy(pb->d_bf_ij.p, ij.data(), sizeof(int32_t) * ij.size(), cudaMemcpyHostToDevice));
+      LFX_CUDA_TRY(cudaMemcpy(pb->d_bf_an.p, an.data(), sizeof(double) * an.size(), cudaMemcpyHostToDevice));
+      LFX_CUDA_TRY(cudaMemcpy(pb->d_bf_coef.p, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice));
+      LFX_CUDA_TRY(cudaMemcpy(pb->d_bf_slot4.p, slot4.data(), sizeof(int32_t) * slot4.size(), cudaMemcpyHostToDevice));
+      LFX_CUDA_TRY(cudaMemcpy(pb->d_bf_blk.p, blk.data(), sizeof(int32_t) * blk.size(), cudaMemcpyHostToDevice));
     }
   }
 
@@ -938,6 +1010,12 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
                                              s->vals64.as<double>())));
   }
   LFX_CUDA_TRY(cudaEventRecord(s->ea1, st));
+  if (pb->n_bf_edges > 0)
+    LFX_TRY(launch_backflow(st, pb->n_bf_edges, pb->d_bf_ij.as<int32_t>(), pb->d_bf_an.as<double>(),
+                            pb->d_bf_coef.as<double>(), pb->d_bf_slot4.as<int32_t>(), s->xsol.as<D4>(),
+                            pb->n_bf_blocks, pb->d_bf_blk.as<int32_t>(), pb->d_bf_acc.as<double>(),
+                            mixed ? nullptr : s->vals64.as<double>(), mixed ? s->vals32.as<float>() : nullptr,
+                            mixed ? s->vals_lo.as<float>() : nullptr));
   if (mixed) LFX_TRY(launch_dd_combine(st, 4 * m.V, s->rhs_hi.as<float>(), s->rhs_lo.as<float>(), s->rhs.as<double>()));
   s->n_asm_launch = (int)m.color_off.size() - 1;
   // boundary data at t^{n+1}

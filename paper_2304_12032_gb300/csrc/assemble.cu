@@ -913,6 +913,53 @@ lfx_status launch_node_gather(cudaStream_t st, int64_t V, const int32_t *node_ol
   return LFX_OK;
 }
 
+namespace {
+__global__ void backflow_edge_kernel(int64_t n_edges, const int32_t *ij, const double *an, const double *coef,
+                                     const int32_t *slot4, const D4 *xext, double *acc) {
+  pdl_entry();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_edges; e += (int64_t)gridDim.x * blockDim.x) {
+    const D4 ui = xext[ij[2 * e]], uj = xext[ij[2 * e + 1]];
+    const double un = 0.5 * ((ui.x + uj.x) * an[3 * e] + (ui.y + uj.y) * an[3 * e + 1] + (ui.z + uj.z) * an[3 * e + 2]);
+    const double c = -coef[e] * fmin(un, 0.0) / 3.0 * 0.25;
+    if (c == 0.0) continue;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) atomicAdd(acc + slot4[4 * e + t], c);
+  }
+}
+__global__ void backflow_apply_kernel(int64_t n_blocks, const int32_t *blk, const double *acc, double *vals64,
+                                      float *hi, float *lo) {
+  pdl_entry();
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_blocks; k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = acc[k];
+    const int64_t s = blk[k];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int64_t q = 16 * s + 5 * d;   // diagonal entry (d, d) of the block
+      if (vals64) {
+        vals64[q] += v;
+      } else {
+        const dd r = dd(hi[q], lo[q]) + dd(v);
+        hi[q] = r.hi;
+        lo[q] = r.lo;
+      }
+    }
+  }
+}
+}  // namespace
+
+lfx_status launch_backflow(cudaStream_t st, int64_t n_edges, const int32_t *ij, const double *an, const double *coef,
+                           const int32_t *slot4, const D4 *xext, int64_t n_blocks, const int32_t *blk, double *acc,
+                           double *vals64, float *hi, float *lo) {
+  if (n_edges == 0) return LFX_OK;
+  LFX_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)n_blocks, st));
+  pdl_launch(backflow_edge_kernel, grid_for(n_edges, 256), 256, 0, st, n_edges, ij, an, coef, slot4, xext, acc);
+  pdl_launch(backflow_apply_kernel, grid_for(n_blocks, 256), 256, 0, st, n_blocks, blk, (const double *)acc, vals64,
+             hi, lo);
+  note_launches(2);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
 int64_t assemble_wave_elements() {
   int dev = 0, v = 0, sms = 152, per_sm = LFX_ASM_DD_MIN_CTAS;
   if (cudaGetDevice(&dev) == cudaSuccess &&

@@ -75,6 +75,13 @@ lfx_status launch_comp_normalize_dd(cudaStream_t st, int64_t V, int n_comp, cons
 lfx_status launch_node_scatter(cudaStream_t st, int64_t V, const int32_t *node_old, const double *u, const double *p,
                                D4 *dst);
 lfx_status launch_node_gather(cudaStream_t st, int64_t V, const int32_t *node_old, const D4 *src, double *u, double *p);
+// Inertial backflow stabilisation (Section 2.2.2): for each face edge (i, j), at its midpoint
+// c = -coef min(u^EXT . a, 0) / 3 (a = A_f n_f, weight A_f/3), times phi_a phi_b = 1/4, added to
+// the velocity diagonal of blocks (i,i), (i,j), (j,i), (j,j) through FP64 accumulators; then into
+// the FP64 matrix (vals64) or the double-float one (hi, lo).
+lfx_status launch_backflow(cudaStream_t st, int64_t n_edges, const int32_t *ij, const double *an, const double *coef,
+                           const int32_t *slot4, const D4 *xext, int64_t n_blocks, const int32_t *blk, double *acc,
+                           double *vals64, float *hi, float *lo);
 template <class R, class S>
 lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysParams &P,
                            const int32_t *color_off, int n_colors, S *vals);

@@ -38,7 +38,8 @@ class lfx_time_law(ctypes.Structure):
 class lfx_bc(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_int32), ("kind", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("given_geometry", ctypes.c_int32), ("time", lfx_time_law), ("theta", ctypes.c_double),
-                ("radius", ctypes.c_double), ("center", ctypes.c_double * 3), ("normal", ctypes.c_double * 3)]
+                ("radius", ctypes.c_double), ("center", ctypes.c_double * 3), ("normal", ctypes.c_double * 3),
+                ("beta", ctypes.c_double)]
 
 
 class lfx_riis(ctypes.Structure):
@@ -226,6 +227,7 @@ class BC:
     radius: float = 1.0
     center: Optional[Sequence[float]] = None
     normal: Optional[Sequence[float]] = None
+    beta: float = 0.0               # neumann: inertial backflow stabilisation (0: off)
 
     def c(self) -> lfx_bc:
         s = lfx_bc()
@@ -239,7 +241,7 @@ class BC:
             s.time.a[i] = v
         for i, v in enumerate(self.b):
             s.time.b[i] = v
-        s.theta, s.radius = self.theta, self.radius
+        s.theta, s.radius, s.beta = self.theta, self.radius, self.beta
         if self.center is not None and self.normal is not None:
             s.given_geometry = 1
             for i in range(3):

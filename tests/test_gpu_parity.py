@@ -28,6 +28,7 @@ CASES = {
     "bifurcation_supg_bdf3": lambda: C.bifurcation_case(8000, seed=1003),
     "stenosis_womersley_riis": lambda: C.stenosis_case(8000, seed=3),
     "galerkin_only": lambda: C.vessel_case(3000, seed=23, stab=0, riis=False),
+    "vessel_backflow": lambda: C.vessel_case(5000, seed=24, riis=False, backflow=1.0),
 }
 
 
