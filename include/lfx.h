@@ -108,7 +108,7 @@ typedef struct lfx_time_law {
   double b[LFX_MAX_FOURIER + 1];
 } lfx_time_law;
 
-enum { LFX_BC_NOSLIP = 0, LFX_BC_DIRICHLET = 1, LFX_BC_NODAL = 2, LFX_BC_NEUMANN = 3 };
+enum { LFX_BC_NOSLIP = 0, LFX_BC_DIRICHLET = 1, LFX_BC_NODAL = 2, LFX_BC_NEUMANN = 3, LFX_BC_RESISTANCE = 4 };
 enum { LFX_PROFILE_UNIFORM = 0, LFX_PROFILE_PARABOLIC = 1, LFX_PROFILE_WOMERSLEY = 2 };
 /* One boundary condition on the faces carrying `tag`.
  *  NOSLIP    u = 0 (fixed domain).
@@ -121,15 +121,21 @@ enum { LFX_PROFILE_UNIFORM = 0, LFX_PROFILE_PARABOLIC = 1, LFX_PROFILE_WOMERSLEY
  *            With beta > 0, inertial backflow stabilisation (Section 2.2.2): + beta rho/2
  *            |u . n|_- u, semi-implicit: the matrix gains c (u, v) on the faces with
  *            c = -beta rho/2 min(u^EXT . n, 0), integrated at the three edge midpoints of each face.
- * Where tags meet: NOSLIP > DIRICHLET/NODAL > NEUMANN.  center/normal: if given_geometry is 0
- * they are computed as the area-weighted barycentre and outward normal of the tagged faces.
- * beta must be >= 0, and 0 for kinds other than NEUMANN (LFX_ERR_INVALID_ARG otherwise). */
+ *  RESISTANCE sigma n = -(p_0(t) + resistance * int_Gamma u . n) n (Section 2.2.3), p_0 = time
+ *            law: implicit, the linear operator carries the rank-one term resistance w w^T
+ *            (w_{4a+i} = int_Gamma phi_a n_i) and p_0 enters like Neumann data.  Not available on
+ *            meshes of several disconnected pieces (LFX_ERR_INVALID_ARG at state creation).
+ * Where tags meet: NOSLIP > DIRICHLET/NODAL > NEUMANN/RESISTANCE.  center/normal: if
+ * given_geometry is 0 they are computed as the area-weighted barycentre and outward normal of the
+ * tagged faces.  beta must be >= 0, and 0 for kinds other than NEUMANN; resistance >= 0, and 0 for
+ * kinds other than RESISTANCE (LFX_ERR_INVALID_ARG otherwise). */
 typedef struct lfx_bc {
   int32_t tag, kind, profile, given_geometry;
   lfx_time_law time;
   double theta, radius;
   double center[3], normal[3];
   double beta;
+  double resistance;
 } lfx_bc;
 
 enum { LFX_RIIS_DISK = 0, LFX_RIIS_SDF_NODAL = 1 };

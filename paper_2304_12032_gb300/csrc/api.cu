@@ -110,6 +110,15 @@ struct lfx_problem {
   // (i,i), (i,j), (j,i), (j,j)); the compact blocks' matrix slots and FP64 accumulators
   int64_t n_bf_edges = 0, n_bf_blocks = 0;
   DBuf d_bf_ij, d_bf_an, d_bf_coef, d_bf_slot4, d_bf_blk, d_bf_acc;
+  // resistance tags: rank-one terms C_R w w^T of the operator (see Rank1View)
+  int n_r1_tags = 0;
+  int64_t n_r1_ax = 0;
+  DBuf d_r1_cr, d_r1_off, d_r1_node, d_r1_w, d_r1_ax_node, d_r1_ax_tag, d_r1_ax_w;
+  Rank1View rank1() const {
+    return Rank1View{n_r1_tags, d_r1_cr.as<double>(), d_r1_off.as<int32_t>(), d_r1_node.as<int32_t>(),
+                     d_r1_w.as<double>(), n_r1_ax, d_r1_ax_node.as<int32_t>(), d_r1_ax_tag.as<int32_t>(),
+                     d_r1_ax_w.as<double>()};
+  }
   // RIIS nodal signed distances [n_riis][V]
   DBuf d_phi;
   DBuf d_bad;
@@ -121,7 +130,9 @@ struct lfx_problem {
   size_t device_bytes() const {
     return d_dir_node.bytes + d_dir_bc.bytes + d_S.bytes + d_neu_node.bytes + d_neu_bc.bytes +
            d_neu_vec.bytes + d_phi.bytes + d_bad.bytes + geo64.bytes + geo_hi.bytes + geo_lo.bytes +
-           d_bf_ij.bytes + d_bf_an.bytes + d_bf_coef.bytes + d_bf_slot4.bytes + d_bf_blk.bytes + d_bf_acc.bytes;
+           d_bf_ij.bytes + d_bf_an.bytes + d_bf_coef.bytes + d_bf_slot4.bytes + d_bf_blk.bytes + d_bf_acc.bytes +
+           d_r1_cr.bytes + d_r1_off.bytes + d_r1_node.bytes + d_r1_w.bytes + d_r1_ax_node.bytes + d_r1_ax_tag.bytes +
+           d_r1_ax_w.bytes;
   }
 };
 
@@ -472,7 +483,7 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
   std::vector<int> pri(V, 0), owner(V, -1);
   for (int b = 0; b < n_bcs; ++b) {
     const lfx_bc &bc = bcs[b];
-    if (bc.kind < 0 || bc.kind > 3 || bc.profile < 0 || bc.profile > 2) {
+    if (bc.kind < 0 || bc.kind > 4 || bc.profile < 0 || bc.profile > 2) {
       set_error("lfx_problem_create: invalid boundary condition %d", b);
       return LFX_ERR_INVALID_ARG;
     }
@@ -488,7 +499,11 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
       set_error("lfx_problem_create: backflow stabilisation beta must be >= 0, and only on Neumann tags");
       return LFX_ERR_INVALID_ARG;
     }
-    if (bc.kind == LFX_BC_NEUMANN) continue;
+    if (!(bc.resistance >= 0.0) || (bc.resistance != 0.0 && bc.kind != LFX_BC_RESISTANCE)) {
+      set_error("lfx_problem_create: the resistance coefficient must be >= 0, and only on resistance tags");
+      return LFX_ERR_INVALID_ARG;
+    }
+    if (bc.kind == LFX_BC_NEUMANN || bc.kind == LFX_BC_RESISTANCE) continue;
     const int p = bc.kind == LFX_BC_NOSLIP ? 3 : 2;
     for (int64_t f = 0; f < m.F; ++f) {
       if (m.btags[f] != bc.tag) continue;
@@ -581,8 +596,10 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
   {
     std::vector<std::vector<double>> acc(n_bcs);
     std::vector<double> vec;
+    std::vector<int32_t> r1_off(1, 0), r1_node, ax_node, ax_tag;
+    std::vector<double> r1_w, ax_w, r1_cr;
     for (int b = 0; b < n_bcs; ++b) {
-      if (bcs[b].kind != LFX_BC_NEUMANN) continue;
+      if (bcs[b].kind != LFX_BC_NEUMANN && bcs[b].kind != LFX_BC_RESISTANCE) continue;
       std::vector<double> nv((size_t)V * 3, 0.0);
       std::vector<char> hit(V, 0);
       for (int64_t f = 0; f < m.F; ++f) {
@@ -608,6 +625,38 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
           pb->neu_bc.push_back(b);
           for (int k = 0; k < 3; ++k) vec.push_back(nv[3 * i + k]);
         }
+      if (bcs[b].kind == LFX_BC_RESISTANCE) {
+        // rank-one term: w . x over every node of the tag; the update skips Dirichlet rows
+        const int32_t t = (int32_t)r1_cr.size();
+        r1_cr.push_back(bcs[b].resistance);
+        for (int64_t i = 0; i < V; ++i) {
+          if (!hit[i]) continue;
+          r1_node.push_back((int32_t)i);
+          for (int k = 0; k < 3; ++k) r1_w.push_back(nv[3 * i + k]);
+          if (pri[i] < 2) {
+            ax_node.push_back((int32_t)i);
+            ax_tag.push_back(t);
+            for (int k = 0; k < 3; ++k) ax_w.push_back(nv[3 * i + k]);
+          }
+        }
+        r1_off.push_back((int32_t)r1_node.size());
+      }
+    }
+    pb->n_r1_tags = (int)r1_cr.size();
+    pb->n_r1_ax = (int64_t)ax_node.size();
+    if (pb->n_r1_tags > 0) {
+      auto up = [](DBuf &d, const void *src, size_t bytes) -> lfx_status {
+        LFX_TRY(d.alloc(std::max<size_t>(bytes, 8)));
+        if (bytes) LFX_CUDA_TRY(cudaMemcpy(d.p, src, bytes, cudaMemcpyHostToDevice));
+        return LFX_OK;
+      };
+      LFX_TRY(up(pb->d_r1_cr, r1_cr.data(), sizeof(double) * r1_cr.size()));
+      LFX_TRY(up(pb->d_r1_off, r1_off.data(), sizeof(int32_t) * r1_off.size()));
+      LFX_TRY(up(pb->d_r1_node, r1_node.data(), sizeof(int32_t) * r1_node.size()));
+      LFX_TRY(up(pb->d_r1_w, r1_w.data(), sizeof(double) * r1_w.size()));
+      LFX_TRY(up(pb->d_r1_ax_node, ax_node.data(), sizeof(int32_t) * ax_node.size()));
+      LFX_TRY(up(pb->d_r1_ax_tag, ax_tag.data(), sizeof(int32_t) * ax_tag.size()));
+      LFX_TRY(up(pb->d_r1_ax_w, ax_w.data(), sizeof(double) * ax_w.size()));
     }
     const int64_t nn = (int64_t)pb->neu_node.size();
     LFX_TRY(pb->d_neu_node.alloc(sizeof(int32_t) * nn));
@@ -848,6 +897,19 @@ lfx_status lfx_state_create(lfx_problem *pb, const double *u_hist, const double 
     LFX_TRY(s->pc64.init(V, cfg));
     LFX_TRY(s->gm64.init(V, o.gmres_restart));
   }
+  if (pb->n_r1_tags > 0) {
+    if (m.n_comp > 1) {
+      set_error("lfx_state_create: resistance conditions are not available on meshes of several pieces");
+      return LFX_ERR_INVALID_ARG;
+    }
+    const Rank1View r1 = pb->rank1();
+    if (o.precision == LFX_PREC_MIXED) {
+      LFX_TRY(s->gm32.set_rank1(r1));
+      LFX_TRY(s->gmdd.set_rank1(r1));
+    } else {
+      LFX_TRY(s->gm64.set_rank1(r1));
+    }
+  }
   if (m.n_comp > 1 && o.batch_segmented) {
     // one Arnoldi process per component of a batched mesh
     if (o.precision == LFX_PREC_MIXED) {
@@ -1023,7 +1085,8 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
   memset(&C, 0, sizeof(C));
   const int nb = (int)pb->bcs.size();
   for (int b = 0; b < nb; ++b)
-    if (pb->bcs[b].kind == LFX_BC_NEUMANN) C.c[b] = time_law(pb->bcs[b].time, t1);
+    if (pb->bcs[b].kind == LFX_BC_NEUMANN || pb->bcs[b].kind == LFX_BC_RESISTANCE)
+      C.c[b] = time_law(pb->bcs[b].time, t1);
   LFX_TRY(launch_neumann(st, (int64_t)pb->neu_node.size(), pb->d_neu_node.as<int32_t>(), pb->d_neu_bc.as<int32_t>(),
                          pb->d_neu_vec.as<double>(), C, s->rhs.as<double>()));
   if (!apply_bcs) return LFX_OK;

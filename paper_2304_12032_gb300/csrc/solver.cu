@@ -1972,6 +1972,36 @@ __global__ void seg_confirm_kernel(const double *pn, SegTasks tk, const KState *
   }
 }
 
+// s[t] = w_t . x over the nodes of tag t (one CTA per tag)
+template <class T>
+__global__ void __launch_bounds__(kThreads) rank1_dot_kernel(Rank1View r, const T *x, double *s, const KState *st) {
+  pdl_entry();
+  if (finished(st)) return;
+  const int t = blockIdx.x;
+  double a = 0.0;
+  for (int32_t k = r.dot_off[t] + threadIdx.x; k < r.dot_off[t + 1]; k += blockDim.x) {
+    const int64_t nd = r.dot_node[k];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) a += r.dot_w[3 * (int64_t)k + i] * (double)x[4 * nd + i];
+  }
+  a = cta_sum(a);
+  if (threadIdx.x == 0) s[t] = a;
+}
+
+// y_row += sign cr[t] s[t] w_row over the listed rows
+template <class T>
+__global__ void rank1_axpy_kernel(Rank1View r, const double *s, T *y, double sign, const KState *st) {
+  pdl_entry();
+  if (finished(st)) return;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < r.n_ax; k += (int64_t)gridDim.x * blockDim.x) {
+    const int t = r.ax_tag[k];
+    const double c = sign * r.cr[t] * s[t];
+    const int64_t nd = r.ax_node[k];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[4 * nd + i] = (T)((double)y[4 * nd + i] + c * r.ax_w[3 * k + i]);
+  }
+}
+
 inline int rows_grid(int64_t V) { return (int)((V * kRowGroup + kThreads - 1) / kThreads); }
 // grid for a CSR kernel with G lanes per row over n rows
 inline int lanes_grid(int64_t n, int G) { return (int)std::max<int64_t>(1, (n * G + kThreads - 1) / kThreads); }
@@ -2550,7 +2580,7 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
   bool have_r = false;   // w = b - A x and its partial sums are in place (from the previous cycle)
   for (int cycle = 0; cycle < 100000; ++cycle) {
     // r = b - A x -> w, beta, v0 = r / beta
-    if (!have_r) LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, pn, &ng)));
+    if (!have_r) LFX_TRY(residual(st, A, x, b, w, pn, &ng));
     pdl_launch(cycle_start_kernel, 1, kThreads, 0, st, pn, ng, ks);
     pdl_launch(scale_beta_kernel<T>, vg, kThreads, 0, st, w, Vb, n, ks);
     note_launches(2);
@@ -2559,7 +2589,7 @@ lfx_status Gmres<S, T>::solve(cudaStream_t st, const BsrView<S> &A, const PrecFn
     pdl_launch(update_x_kernel<T, T>, vg, kThreads, 0, st, Zb, n, x, n, ks);
     // the true residual, which confirms convergence or starts the next cycle; one read of the
     // status header for both
-    LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, pn, &ng)));
+    LFX_TRY(residual(st, A, x, b, w, pn, &ng));
     pdl_launch(reduce_kernel, 1, kThreads, 0, st, pn, ng, &ks->res, 1);
     note_launches(3);
     LFX_CUDA_TRY(cudaMemcpyAsync(&hs, ks, offsetof(KState, H), cudaMemcpyDeviceToHost, st));
@@ -2776,6 +2806,40 @@ lfx_status Gmres<S, T>::solve_seg(cudaStream_t st, const BsrView<S> &A, const Pr
   return status;
 }
 
+// w = b - A x (with the rank-one terms) and the partial sums of |w|^2 in pn (*ng of them)
+template <class S, class T>
+lfx_status Gmres<S, T>::residual(cudaStream_t st, const BsrView<S> &A, const T *x, const T *b, T *w, double *pn,
+                                 int *ng) {
+  if (r1.n_tags == 0) return launch_spmv<S, T>(st, A, x, b, w, 1, pn, ng);
+  LFX_TRY((launch_spmv<S, T>(st, A, x, b, w, 1, nullptr, nullptr)));
+  apply_rank1(st, x, w, -1.0, nullptr);
+  const int vg = vec_grid(n);
+  pdl_launch(norm_kernel<T>, vg, kThreads, 0, st, (const T *)w, n, pn);
+  note_launches(1);
+  *ng = vg;
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+template <class S, class T>
+lfx_status Gmres<S, T>::set_rank1(const Rank1View &r) {
+  if (n_seg > 1) {
+    set_error("GMRES: rank-one terms need a single system");
+    return LFX_ERR_INVALID_ARG;
+  }
+  r1 = r;
+  if (r.n_tags > 0) LFX_TRY(r1_s.alloc(sizeof(double) * (size_t)r.n_tags));
+  return LFX_OK;
+}
+
+template <class S, class T>
+void Gmres<S, T>::apply_rank1(cudaStream_t st, const T *x, T *y, double sign, const KState *ks) {
+  pdl_launch(rank1_dot_kernel<T>, r1.n_tags, kThreads, 0, st, r1, x, r1_s.as<double>(), ks);
+  pdl_launch(rank1_axpy_kernel<T>, (int)std::max<int64_t>(1, (r1.n_ax + kThreads - 1) / kThreads), kThreads, 0, st, r1,
+             (const double *)r1_s.as<double>(), y, sign, ks);
+  note_launches(2);
+}
+
 // The Arnoldi product w = A z, bracketed by CUDA events for the SpMV timing statistics.
 template <class S, class T>
 lfx_status Gmres<S, T>::timed_spmv(cudaStream_t st, const BsrView<S> &A, const T *z, T *w, const KState *ks) {
@@ -2788,6 +2852,7 @@ lfx_status Gmres<S, T>::timed_spmv(cudaStream_t st, const BsrView<S> &A, const T
   }
   LFX_CUDA_TRY(cudaEventRecord(tev[n_tev], st));
   arnoldi_spmv(st, A, z, w, ks);
+  if (r1.n_tags > 0) apply_rank1(st, z, w, 1.0, ks);
   LFX_CUDA_TRY(cudaEventRecord(tev[n_tev + 1], st));
   n_tev += 2;
   return LFX_OK;

@@ -58,6 +58,20 @@ struct SegTasks {
   int n_task, n_seg;
 };
 
+// Rank-one terms of the operator (resistance conditions, Section 2.2.3): y += sum_t cr[t] w_t
+// (w_t . x).  The dot product runs over every node of tag t (dot_off[t] .. dot_off[t+1] of
+// dot_node, three components each in dot_w); the update over the listed rows only (ax_*: the
+// tag's nodes that are not Dirichlet rows).  Device arrays.
+struct Rank1View {
+  int n_tags;
+  const double *cr;
+  const int32_t *dot_off, *dot_node;
+  const double *dot_w;
+  int64_t n_ax;
+  const int32_t *ax_node, *ax_tag;
+  const double *ax_w;
+};
+
 struct AmgHost;
 
 // One explicit level (l >= 1) of the Schur AMG hierarchy on the device, and the transfer
@@ -156,6 +170,8 @@ struct Gmres {
   // step reaches it); the tightest over the running components; within [lo, hi].  Reads the
   // status from the device (synchronises st).
   lfx_status inner_tolerance(cudaStream_t st, double lo, double hi, double *eta);
+  // Include rank-one terms in every product with A (single systems only).
+  lfx_status set_rank1(const Rank1View &r);
   // One cycle from x = 0, as the preconditioner of a flexible outer solve, without waiting for the
   // device: the tolerance is eta ||b|| with eta = rtol, or (outer != null) the rule of
   // inner_tolerance evaluated on the device from the outer's status; no confirmation of the true
@@ -167,6 +183,10 @@ struct Gmres {
   size_t device_bytes() const;
 
  private:
+  Rank1View r1{};
+  DBuf r1_s;   // the dot products w_t . x
+  void apply_rank1(cudaStream_t st, const T *x, T *y, double sign, const KState *ks);
+  lfx_status residual(cudaStream_t st, const BsrView<S> &A, const T *x, const T *b, T *w, double *pn, int *ng);
   lfx_status timed_spmv(cudaStream_t st, const BsrView<S> &A, const T *z, T *w, const KState *ks);
   lfx_status arnoldi_cycle(cudaStream_t st, const BsrView<S> &A, const PrecFn<T> &pc, int m, int maxit, bool cgs2,
                            int lag);

@@ -24,7 +24,7 @@ MAX_FOURIER = 16
 (LFX_OK, LFX_ERR_INVALID_ARG, LFX_ERR_BAD_MESH, LFX_ERR_OOM, LFX_ERR_NOT_CONVERGED,
  LFX_ERR_NONFINITE, LFX_ERR_CUDA, LFX_ERR_TIMEOUT, LFX_ERR_BUDGET) = (0, -1, -2, -3, -4, -5, -6, -7, -8)
 TIME = {"constant": 0, "pulsatile": 1, "ramp": 2, "fourier": 3}
-KIND = {"noslip": 0, "dirichlet": 1, "nodal": 2, "neumann": 3}
+KIND = {"noslip": 0, "dirichlet": 1, "nodal": 2, "neumann": 3, "resistance": 4}
 PROFILE = {"uniform": 0, "parabolic": 1, "womersley": 2}
 PREC = {"fp64": 0, "mixed": 1}
 SMOOTH = {"jacobi": 0, "chebyshev": 1, "amg": 2}
@@ -39,7 +39,7 @@ class lfx_bc(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_int32), ("kind", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("given_geometry", ctypes.c_int32), ("time", lfx_time_law), ("theta", ctypes.c_double),
                 ("radius", ctypes.c_double), ("center", ctypes.c_double * 3), ("normal", ctypes.c_double * 3),
-                ("beta", ctypes.c_double)]
+                ("beta", ctypes.c_double), ("resistance", ctypes.c_double)]
 
 
 class lfx_riis(ctypes.Structure):
@@ -217,7 +217,7 @@ def default_options(**kw) -> lfx_options:
 class BC:
     """Python form of lfx_bc (Section 2.2)."""
     tag: int
-    kind: str                       # noslip | dirichlet | nodal | neumann
+    kind: str                       # noslip | dirichlet | nodal | neumann | resistance
     profile: str = "uniform"        # uniform | parabolic | womersley
     time: str = "constant"          # constant | pulsatile | ramp | fourier
     p: Sequence[float] = (0.0,)     # time-law parameters (see lfx_time_law)
@@ -228,6 +228,7 @@ class BC:
     center: Optional[Sequence[float]] = None
     normal: Optional[Sequence[float]] = None
     beta: float = 0.0               # neumann: inertial backflow stabilisation (0: off)
+    resistance: float = 0.0         # resistance: C_R (p holds the time law of p_0)
 
     def c(self) -> lfx_bc:
         s = lfx_bc()
@@ -241,7 +242,7 @@ class BC:
             s.time.a[i] = v
         for i, v in enumerate(self.b):
             s.time.b[i] = v
-        s.theta, s.radius, s.beta = self.theta, self.radius, self.beta
+        s.theta, s.radius, s.beta, s.resistance = self.theta, self.radius, self.beta, self.resistance
         if self.center is not None and self.normal is not None:
             s.given_geometry = 1
             for i in range(3):

@@ -45,11 +45,13 @@ def beltrami_case(n=4, seed=11, order=1, dt=1e-3, stab=2):
                 float(beltrami_p(X[:1], dt)[0]), {t: ue for t in range(1, 7)})
 
 
-def vessel_case(n_tets=6000, seed=21, order=2, stab=2, diffusion=0, riis=True, neumann_h=3.0, backflow=0.0):
+def vessel_case(n_tets=6000, seed=21, order=2, stab=2, diffusion=0, riis=True, neumann_h=3.0, backflow=0.0,
+                resistance=0.0):
     """Cylinder R=1, L=3 with a parabolic pulsatile inlet, a Neumann outlet with nonzero h
     (and inertial backflow stabilisation when backflow > 0: the random history flows back in
     near the outlet rim), a disk-shaped resistive surface at mid-length and random seeded
-    history fields."""
+    history fields.  With resistance > 0 the outlet is a resistance condition instead, with
+    p_0 = neumann_h and C_R = resistance."""
     R, L = 1.0, 3.0
     m = cylinder(R, L, n_tets=n_tets, seed=seed)
     rng = np.random.default_rng(seed)
@@ -62,6 +64,8 @@ def vessel_case(n_tets=6000, seed=21, order=2, stab=2, diffusion=0, riis=True, n
            dict(tag=1, kind="dirichlet", profile="parabolic", time="pulsatile", p=(5.0, 30.0, 0.8),
                 radius=R),
            dict(tag=2, kind="neumann", time="constant", p=(neumann_h,), beta=backflow)]
+    if resistance > 0.0:
+        bcs[2] = dict(tag=2, kind="resistance", time="constant", p=(neumann_h,), resistance=resistance)
     rs = [dict(resistance=1e4, eps=0.25, center=(0.0, 0.0, L / 2), normal=(0.0, 0.0, 1.0), radius=0.6)] if riis else []
     return Case(m, 1.06, 0.035, 1e-3, order, bcs, rs, uh, ph, 0.1, stab, diffusion, (0.0, 0.0, 0.0))
 
@@ -118,7 +122,8 @@ def oracle_problem(case: Case):
         else:
             tp = {"period": p[0], "a": list(b.get("a", [0.0])), "b": list(b.get("b", [0.0]))}
         bcs.append(O.BC(tag=b["tag"], kind=kind, time=time, tparams=tp, space=b.get("profile", "uniform"),
-                        radius=b.get("radius", 1.0), theta=b.get("theta", 1.0), beta=b.get("beta", 0.0)))
+                        radius=b.get("radius", 1.0), theta=b.get("theta", 1.0), beta=b.get("beta", 0.0),
+                        resistance=b.get("resistance", 0.0)))
     riis = [O.RIIS(r["resistance"], r["eps"], O.disk_sdf(case.mesh.nodes, r["center"], r["normal"], r["radius"]))
             for r in case.riis]
     return O.Problem(prm, bcs, riis, pin_node=case.pin_node)
@@ -141,7 +146,8 @@ def gpu_state(case: Case, **opts):
                           pin_pressure_node=case.pin_node, **opts)
     bcs = [L.BC(tag=b["tag"], kind=b["kind"], profile=b.get("profile", "uniform"), time=b.get("time", "constant"),
                 p=b.get("p", (0.0,)), a=b.get("a", ()), b=b.get("b", ()), theta=b.get("theta", 1.0),
-                radius=b.get("radius", 1.0), beta=b.get("beta", 0.0)) for b in case.bcs]
+                radius=b.get("radius", 1.0), beta=b.get("beta", 0.0),
+                resistance=b.get("resistance", 0.0)) for b in case.bcs]
     riis = [L.RIIS(r["resistance"], r["eps"], r["center"], r["normal"], r["radius"]) for r in case.riis]
     prob = L.Problem(mesh, case.rho, case.mu, case.dt, case.order, bcs, riis, o)
     st = L.State(prob, case.u_hist, case.p_hist, case.t0)

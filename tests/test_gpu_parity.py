@@ -196,3 +196,23 @@ def test_history_in_solution_out_round_trip(pinned):
     u1, p1 = st.get()
     ref = ost.x.reshape(-1, 4)
     assert np.linalg.norm(u1 - ref[:, :3]) <= 1e-6 * np.linalg.norm(ref[:, :3])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_resistance_outlet_step_matches_oracle(precision):
+    """Resistance outlet (Section 2.2.3): the rank-one term C_R w w^T rides on every product with
+    the operator (the assembled matrix and the preconditioner leave it out); the oracle assembles it
+    densely and solves directly.  The step must match within 1e-6; without the term the pressure
+    would be off by C_R Q, about half the pressure scale of this case."""
+    case = C.vessel_case(5000, seed=25, riis=False, resistance=0.5)
+    ost = C.oracle_step(case)
+    opts = dict(gmres_rtol=1e-10)
+    if precision == "mixed":
+        opts.update(precision="mixed", smoother_bf16=1)
+    _, _, st = C.gpu_state(case, **opts)
+    stats = st.step()
+    u, p = st.get()
+    xref = ost.x.reshape(-1, 4)
+    ru = np.linalg.norm(u - xref[:, :3]) / np.linalg.norm(xref[:, :3])
+    rp_ = np.linalg.norm(p - xref[:, 3]) / np.linalg.norm(xref[:, 3])
+    assert ru <= 1e-6 and rp_ <= 1e-6, (precision, ru, rp_, stats)
