@@ -130,7 +130,7 @@ def test_step_matches_oracle(pair):
 
 
 @pytest.mark.parametrize("bf16", [False, True])
-@pytest.mark.parametrize("which", ["beltrami", "vessel_vms_riis", "bifurcation_supg_bdf3"])
+@pytest.mark.parametrize("which", ["beltrami", "vessel_vms_riis", "bifurcation_supg_bdf3", "vessel_backflow"])
 def test_mixed_step_matches_oracle(which, bf16):
     # double-float assembly and outer FGMRES (FP64 vectors, double-float operator), FP32 inner
     # GMRES with an FP32 or BF16-storage aSIMPLE: the step must still match the FP64 oracle
