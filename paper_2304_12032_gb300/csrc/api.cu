@@ -416,6 +416,16 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
     set_error("lfx_problem_create: invalid argument");
     return LFX_ERR_INVALID_ARG;
   }
+  // each boundary condition on its own, before anything is allocated
+  for (int32_t b = 0; b < n_bcs; ++b) {
+    const lfx_bc &bc = bcs[b];
+    if (bc.kind < 0 || bc.kind > 4 || bc.profile < 0 || bc.profile > 2 || bc.time.n_harmonics < 0 ||
+        bc.time.n_harmonics > LFX_MAX_FOURIER || !(bc.beta >= 0.0) || (bc.beta != 0.0 && bc.kind != LFX_BC_NEUMANN) ||
+        !(bc.resistance >= 0.0) || (bc.resistance != 0.0 && bc.kind != LFX_BC_RESISTANCE)) {
+      set_error("lfx_problem_create: invalid boundary condition %d (kind, profile, harmonics, beta or resistance)", b);
+      return LFX_ERR_INVALID_ARG;
+    }
+  }
   *out = nullptr;
   std::unique_ptr<lfx_problem> pb(new (std::nothrow) lfx_problem);
   if (!pb) return LFX_ERR_OOM;

@@ -137,3 +137,16 @@ def test_colouring_balanced_to_assembly_waves(L):
     assert waves <= -(-T // W) + 2, (waves, sizes.tolist())
     key = np.unique(np.stack([np.repeat(col, 4), m.tets.ravel()], 1), axis=0)
     assert key.shape[0] == 4 * T       # no node carries two elements of one colour
+
+
+@pytest.mark.parametrize("bc", [dict(tag=0, kind="noslip", beta=1.0), dict(tag=2, kind="neumann", beta=-0.5),
+                                dict(tag=2, kind="neumann", resistance=0.3), dict(tag=2, kind="resistance", resistance=-1.0)])
+def test_outlet_condition_arguments_are_checked_before_allocation(L, bc):
+    """Backflow stabilisation only on Neumann tags, the resistance coefficient only on resistance
+    tags, both non-negative: rejected as invalid arguments before any device memory is touched
+    (so on a host without a GPU as well)."""
+    m = cylinder(1.0, 2.0, n_tets=3000, seed=9)
+    mesh = L.Mesh.from_synthetic(m)
+    with pytest.raises(L.LfxError) as err:
+        L.Problem(mesh, 1.06, 0.035, 1e-3, 2, [L.BC(**bc)], [])
+    assert err.value.status == L.LFX_ERR_INVALID_ARG
