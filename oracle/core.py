@@ -40,7 +40,7 @@ __all__ = [
     "element_residual", "geometry", "tau", "assemble", "time_law", "boundary_geometry",
     "dirichlet_data", "neumann_rhs", "apply_dirichlet", "solve_direct", "Step",
     "step", "relative_errors", "disk_sdf", "block_of", "womersley_profile", "backflow_matrix",
-    "resistance_vectors", "resistance_terms",
+    "resistance_vectors", "resistance_terms", "lifting", "ale_velocity",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -75,9 +75,9 @@ def load_library():
     if _lib is None:
         _lib = ctypes.CDLL(build_library())
         dp = ctypes.POINTER(ctypes.c_double)
-        _lib.orc_element.argtypes = [ctypes.POINTER(_CParams), dp, dp, dp, dp, dp, dp, dp]
+        _lib.orc_element.argtypes = [ctypes.POINTER(_CParams), dp, dp, dp, dp, dp, dp, dp, dp]
         _lib.orc_element.restype = ctypes.c_int
-        _lib.orc_element_residual.argtypes = [ctypes.POINTER(_CParams), dp, dp, dp, dp, dp, dp, dp]
+        _lib.orc_element_residual.argtypes = [ctypes.POINTER(_CParams), dp, dp, dp, dp, dp, dp, dp, dp]
         _lib.orc_element_residual.restype = ctypes.c_int
         _lib.orc_geometry.argtypes = [dp, dp, dp, dp, dp]
         _lib.orc_geometry.restype = ctypes.c_double
@@ -86,7 +86,7 @@ def load_library():
         _lib.orc_delta.argtypes = [ctypes.c_double, ctypes.c_double]
         _lib.orc_delta.restype = ctypes.c_double
         _lib.orc_elements.argtypes = [ctypes.POINTER(_CParams), dp, ctypes.POINTER(ctypes.c_int32),
-                                      ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, dp, dp, dp, dp,
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, dp, dp, dp, dp, dp,
                                       ctypes.c_int64, dp, dp]
         _lib.orc_elements.restype = ctypes.c_int
     return _lib
@@ -218,27 +218,33 @@ def tau(params: Params, G, g, us, deltas=(), riis=()):
     return float(tm[0]), float(tc[0])
 
 
-def element(params: Params, x, ubdf, uext, pext, phinod=None, riis=()):
-    """Element matrix [16,16] and right-hand side [16] (local unknown 4a+c)."""
+def _opt(a, size):
+    return None if a is None else _dp(np.ascontiguousarray(a, dtype=np.float64).reshape(size))
+
+
+def element(params: Params, x, ubdf, uext, pext, phinod=None, riis=(), uale=None):
+    """Element matrix [16,16] and right-hand side [16] (local unknown 4a+c); uale [4][3] is the
+    mesh velocity at the vertices (None: fixed mesh)."""
     lib = load_library()
     cp = params.c_struct(riis)
     args = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (x, ubdf, uext, pext)]
     ph = np.zeros(4 * MAX_RIIS) if phinod is None else np.ascontiguousarray(phinod, dtype=np.float64).ravel()
     A, b = np.zeros(256), np.zeros(16)
-    rc = lib.orc_element(ctypes.byref(cp), *[_dp(a) for a in args], _dp(ph), _dp(A), _dp(b))
+    rc = lib.orc_element(ctypes.byref(cp), *[_dp(a) for a in args], _dp(ph), _opt(uale, 12), _dp(A), _dp(b))
     if rc != 0:
         raise ValueError("degenerate or inverted element")
     return A.reshape(16, 16), b
 
 
-def element_residual(params: Params, x, ubdf, uext, pext, sol, phinod=None, riis=()):
+def element_residual(params: Params, x, ubdf, uext, pext, sol, phinod=None, riis=(), uale=None):
     lib = load_library()
     cp = params.c_struct(riis)
     args = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (x, ubdf, uext, pext)]
     ph = np.zeros(4 * MAX_RIIS) if phinod is None else np.ascontiguousarray(phinod, dtype=np.float64).ravel()
     sol = np.ascontiguousarray(sol, dtype=np.float64).ravel()
     R = np.zeros(16)
-    rc = lib.orc_element_residual(ctypes.byref(cp), *[_dp(a) for a in args], _dp(ph), _dp(sol), _dp(R))
+    rc = lib.orc_element_residual(ctypes.byref(cp), *[_dp(a) for a in args], _dp(ph), _opt(uale, 12), _dp(sol),
+                                  _dp(R))
     if rc != 0:
         raise ValueError("degenerate or inverted element")
     return R
@@ -250,7 +256,7 @@ def _riis_nodal(problem_riis, V):
     return np.ascontiguousarray(np.stack([np.asarray(r.phi_nodal, dtype=np.float64) for r in problem_riis]))
 
 
-def element_batch(params, nodes, tets, elems, ubdf, uext, pext, riis=()):
+def element_batch(params, nodes, tets, elems, ubdf, uext, pext, riis=(), uale=None):
     """Element matrices [n,16,16] and right-hand sides [n,16] for the listed elements."""
     lib = load_library()
     cp = params.c_struct(riis)
@@ -265,7 +271,8 @@ def element_batch(params, nodes, tets, elems, ubdf, uext, pext, riis=()):
                           elems.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n,
                           _dp(np.ascontiguousarray(ubdf, dtype=np.float64)),
                           _dp(np.ascontiguousarray(uext, dtype=np.float64)),
-                          _dp(np.ascontiguousarray(pext, dtype=np.float64)), _dp(ph), V, _dp(A), _dp(b))
+                          _dp(np.ascontiguousarray(pext, dtype=np.float64)), _dp(ph), _opt(uale, 3 * V), V,
+                          _dp(A), _dp(b))
     if rc != 0:
         raise ValueError(f"degenerate element at batch position {-1 - rc}")
     return A.reshape(n, 16, 16), b
@@ -274,15 +281,16 @@ def element_batch(params, nodes, tets, elems, ubdf, uext, pext, riis=()):
 # ----------------------------------------------------------------------------------------
 # global assembly (scalar CSR, 4 unknowns per node, interleaved)
 # ----------------------------------------------------------------------------------------
-def assemble(params: Params, nodes, tets, ubdf, uext, pext, riis=(), chunk: int = 65536):
-    """Sum of element contributions: returns (A csr [4V,4V], b [4V])."""
+def assemble(params: Params, nodes, tets, ubdf, uext, pext, riis=(), chunk: int = 65536, uale=None):
+    """Sum of element contributions: returns (A csr [4V,4V], b [4V]); uale [V,3] is the mesh
+    velocity (None: fixed mesh)."""
     V, T = nodes.shape[0], tets.shape[0]
     N = 4 * V
     A = sp.csr_matrix((N, N))
     b = np.zeros(N)
     for s in range(0, T, chunk):
         e = np.arange(s, min(T, s + chunk))
-        Ae, be = element_batch(params, nodes, tets, e, ubdf, uext, pext, riis)
+        Ae, be = element_batch(params, nodes, tets, e, ubdf, uext, pext, riis, uale)
         dof = (4 * tets[e].astype(np.int64)[:, :, None] + np.arange(4)[None, None, :]).reshape(-1, 16)
         rows = np.broadcast_to(dof[:, :, None], Ae.shape).ravel()
         cols = np.broadcast_to(dof[:, None, :], Ae.shape).ravel()
@@ -471,6 +479,39 @@ def resistance_terms(mesh, problem: Problem, t: float):
     return terms, r
 
 
+def lifting(mesh, nodes_fixed, values, alpha=None):
+    """Domain displacement by harmonic extension (Eq. lifting with sigma^L = grad d): P1 solution
+    of -div(alpha grad d) = 0 in the reference domain, component by component, with d = values at
+    nodes_fixed and zero normal flux elsewhere.  alpha [T] per element (None: 1).  Returns [V,3]."""
+    X, tets = mesh.nodes, mesh.tets.astype(np.int64)
+    V, T = X.shape[0], tets.shape[0]
+    x = X[tets]                                                       # [T,4,3]
+    J = np.stack([x[:, 1] - x[:, 0], x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]], axis=2)   # columns
+    vol = np.abs(np.linalg.det(J)) / 6.0
+    Jinv = np.linalg.inv(J)                                           # rows: gradients of lambda_1..3
+    g = np.concatenate([-Jinv.sum(axis=1, keepdims=True), Jinv], axis=1)   # [T,4,3] grad phi_a
+    a = np.ones(T) if alpha is None else np.asarray(alpha, dtype=np.float64)
+    Ke = (a * vol)[:, None, None] * np.einsum("tai,tbi->tab", g, g)
+    rows = np.broadcast_to(tets[:, :, None], Ke.shape).ravel()
+    cols = np.broadcast_to(tets[:, None, :], Ke.shape).ravel()
+    K = sp.coo_matrix((Ke.ravel(), (rows, cols)), shape=(V, V)).tocsr()
+    fixed = np.asarray(nodes_fixed, dtype=np.int64)
+    free = np.setdiff1d(np.arange(V), fixed)
+    d = np.zeros((V, 3))
+    d[fixed] = values
+    Kff = K[free][:, free].tocsc()
+    rhs = -K[free][:, fixed] @ d[fixed]
+    d[free] = np.column_stack([spla.spsolve(Kff, rhs[:, k]) for k in range(3)])
+    return d
+
+
+def ale_velocity(order: int, d_hist, dt: float):
+    """Mesh velocity u_ALE^{n+1} = (alpha d^{n+1} - sum_j beta_j d^{n-j}) / dt, the BDF derivative of
+    the displacement (Section 2.3), from d_hist = [d^{n+1}, d^n, d^{n-1}, ...] (order + 1 levels)."""
+    alpha, beta, _ = bdf_coefficients(order)
+    return (alpha * d_hist[0] - sum(beta[j] * d_hist[j + 1] for j in range(order))) / dt
+
+
 def apply_dirichlet(A: sp.csr_matrix, b: np.ndarray, rows, values):
     """Replace each constrained row r by s e_r and b_r by s g_r, s = |A_rr| (1 if zero)."""
     A = A.tocsr(copy=True)
@@ -515,16 +556,23 @@ class Step:
 
 def step(mesh, problem: Problem, u_hist: Sequence[np.ndarray], p_hist: Sequence[np.ndarray],
          t_next: float, nodal: Optional[dict] = None, pin_value: float = 0.0,
-         solver: Optional[Callable] = None) -> Step:
+         solver: Optional[Callable] = None, d_hist: Optional[Sequence[np.ndarray]] = None) -> Step:
     """One semi-implicit BDF step from t^n to t^{n+1} = t_next (Eq. fullydiscrete...).
-    u_hist = [u^n, u^{n-1}, ...] ([V,3] each), p_hist likewise ([V])."""
+    u_hist = [u^n, u^{n-1}, ...] ([V,3] each), p_hist likewise ([V]).  On a moving domain (ALE),
+    d_hist = [d^{n+1}, d^n, ...] (order + 1 levels of nodal displacement from the reference mesh,
+    e.g. from ``lifting``): the step is assembled on the configuration x^ + d^{n+1} with
+    u* = u^EXT - u_ALE, u_ALE the BDF derivative of d (Eq. u_star, semi-implicit form)."""
     prm = problem.params
     alpha, beta, gamma = bdf_coefficients(prm.bdf_order)
     s = prm.bdf_order
     ubdf = sum(beta[j] * u_hist[j] for j in range(s))
     uext = sum(gamma[j] * u_hist[j] for j in range(s))
     pext = sum(gamma[j] * p_hist[j] for j in range(s))
-    A, b = assemble(prm, mesh.nodes, mesh.tets, ubdf, uext, pext, problem.riis)
+    uale = None
+    if d_hist is not None:
+        uale = ale_velocity(s, d_hist, prm.dt)
+        mesh = dataclasses.replace(mesh, nodes=mesh.nodes + d_hist[0])
+    A, b = assemble(prm, mesh.nodes, mesh.tets, ubdf, uext, pext, problem.riis, uale=uale)
     b = b + neumann_rhs(mesh, problem, t_next)
     A = A + backflow_matrix(mesh, problem, uext)
     terms, rres = resistance_terms(mesh, problem, t_next)

@@ -119,8 +119,8 @@ typedef struct {
 
 static void element_qp(const orc_params *P, const double x[12], const double gradphi[12],
                        const double G[9], const double g[3], double vol, const double ubdf[12],
-                       const double uext[12], const double pext[4], const double *phinod, int q,
-                       qp_data *d) {
+                       const double uext[12], const double pext[4], const double *phinod,
+                       const double *uale, int q, qp_data *d) {
   double lam[4];
   qp_bary(q, lam);
   d->w = vol / 4.0;
@@ -132,8 +132,12 @@ static void element_qp(const orc_params *P, const double x[12], const double gra
       d->us[i] += lam[a] * uext[3 * a + i];
       d->ubdf[i] += lam[a] * ubdf[3 * a + i];
     }
-    ue[i] = d->us[i];            /* u* = u^EXT (semi-implicit, no ALE) */
+    ue[i] = d->us[i];            /* u^EXT at the point */
   }
+  /* u* = u^EXT - u_ALE (semi-implicit, Eq. u_star); u_ALE = 0 on a fixed mesh (uale NULL) */
+  if (uale)
+    for (int i = 0; i < 3; ++i)
+      for (int a = 0; a < 4; ++a) d->us[i] -= lam[a] * uale[3 * a + i];
   double delta[ORC_MAX_RIIS];
   d->sR = 0;
   for (int k = 0; k < P->n_riis; ++k) {
@@ -162,7 +166,7 @@ static void element_qp(const orc_params *P, const double x[12], const double gra
 /* ---- element matrix and right-hand side ------------------------------------------------ */
 int orc_element(const orc_params *P, const double x[12], const double ubdf[12],
                 const double uext[12], const double pext[4], const double *phinod,
-                double A[256], double b[16]) {
+                const double *uale, double A[256], double b[16]) {
   double gp[12], G[9], g[3], vol;
   double det = orc_geometry(x, gp, G, g, &vol);
   if (!(det > 0)) return -1;
@@ -171,7 +175,7 @@ int orc_element(const orc_params *P, const double x[12], const double ubdf[12],
   const double rho = P->rho, mu = P->mu, ca = P->rho * P->alpha / P->dt;
   for (int q = 0; q < 4; ++q) {
     qp_data d;
-    element_qp(P, x, gp, G, g, vol, ubdf, uext, pext, phinod, q, &d);
+    element_qp(P, x, gp, G, g, vol, ubdf, uext, pext, phinod, uale, q, &d);
     const double w = d.w;
     for (int a = 0; a < 4; ++a) {
       const double *ga = gp + 3 * a;
@@ -240,7 +244,7 @@ int orc_element(const orc_params *P, const double x[12], const double ubdf[12],
  * tested against every basis function.  Used by the finite-difference checks of orc_element. */
 int orc_element_residual(const orc_params *P, const double x[12], const double ubdf[12],
                          const double uext[12], const double pext[4], const double *phinod,
-                         const double sol[16], double R[16]) {
+                         const double *uale, const double sol[16], double R[16]) {
   double gp[12], G[9], g[3], vol;
   double det = orc_geometry(x, gp, G, g, &vol);
   if (!(det > 0)) return -1;
@@ -254,7 +258,7 @@ int orc_element_residual(const orc_params *P, const double x[12], const double u
   divu = gu[0][0] + gu[1][1] + gu[2][2];
   for (int q = 0; q < 4; ++q) {
     qp_data d;
-    element_qp(P, x, gp, G, g, vol, ubdf, uext, pext, phinod, q, &d);
+    element_qp(P, x, gp, G, g, vol, ubdf, uext, pext, phinod, uale, q, &d);
     double u[3] = {0, 0, 0}, p = 0;
     for (int a = 0; a < 4; ++a) {
       for (int i = 0; i < 3; ++i) u[i] += d.phi[a] * sol[4 * a + i];
@@ -301,21 +305,23 @@ int orc_element_residual(const orc_params *P, const double x[12], const double u
 /* ---- batch driver: element matrices for a list of elements of a global mesh ------------ */
 int orc_elements(const orc_params *P, const double *nodes, const int32_t *tets,
                  const int64_t *elems, int64_t n, const double *ubdf, const double *uext,
-                 const double *pext, const double *phinod /* [n_riis][V] */, int64_t n_nodes,
+                 const double *pext, const double *phinod /* [n_riis][V] */,
+                 const double *uale /* [V][3] mesh velocity, or NULL */, int64_t n_nodes,
                  double *A /* [n][256] */, double *b /* [n][16] */) {
   for (int64_t t = 0; t < n; ++t) {
     const int32_t *v = tets + 4 * elems[t];
-    double x[12], ub[12], ue[12], pe[4], ph[4 * ORC_MAX_RIIS];
+    double x[12], ub[12], ue[12], ua[12], pe[4], ph[4 * ORC_MAX_RIIS];
     for (int a = 0; a < 4; ++a) {
       for (int i = 0; i < 3; ++i) {
         x[3 * a + i] = nodes[3 * (int64_t)v[a] + i];
         ub[3 * a + i] = ubdf[3 * (int64_t)v[a] + i];
         ue[3 * a + i] = uext[3 * (int64_t)v[a] + i];
+        ua[3 * a + i] = uale ? uale[3 * (int64_t)v[a] + i] : 0.0;
       }
       pe[a] = pext[v[a]];
       for (int k = 0; k < P->n_riis; ++k) ph[4 * k + a] = phinod[k * n_nodes + v[a]];
     }
-    if (orc_element(P, x, ub, ue, pe, ph, A + 256 * t, b + 16 * t) != 0) return -1 - (int)t;
+    if (orc_element(P, x, ub, ue, pe, ph, uale ? ua : NULL, A + 256 * t, b + 16 * t) != 0) return -1 - (int)t;
   }
   return 0;
 }
