@@ -40,7 +40,7 @@ __all__ = [
     "element_residual", "geometry", "tau", "assemble", "time_law", "boundary_geometry",
     "dirichlet_data", "neumann_rhs", "apply_dirichlet", "solve_direct", "Step",
     "step", "relative_errors", "disk_sdf", "block_of", "womersley_profile", "backflow_matrix",
-    "resistance_vectors", "resistance_terms", "lifting", "ale_velocity",
+    "resistance_vectors", "resistance_terms", "lifting", "ale_velocity", "implicit_step", "ImplicitStep",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -89,6 +89,10 @@ def load_library():
                                       ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, dp, dp, dp, dp, dp,
                                       ctypes.c_int64, dp, dp]
         _lib.orc_elements.restype = ctypes.c_int
+        _lib.orc_elements_implicit.argtypes = [ctypes.POINTER(_CParams), dp, ctypes.POINTER(ctypes.c_int32),
+                                               ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, dp, dp, dp, dp,
+                                               ctypes.c_int64, ctypes.c_double, dp, dp]
+        _lib.orc_elements_implicit.restype = ctypes.c_int
     return _lib
 
 
@@ -590,6 +594,80 @@ def step(mesh, problem: Problem, u_hist: Sequence[np.ndarray], p_hist: Sequence[
     A, b = apply_dirichlet(A, b, rows, rv)
     x = (solver or solve_direct)(A, b)
     return Step(A, b, x, ubdf, uext, pext)
+
+
+@dataclasses.dataclass
+class ImplicitStep:
+    x: np.ndarray             # solution [4V]
+    residuals: list           # ||F|| before each Newton update and at the end
+    scale: float              # ||b|| of the semi-implicit system at the same step (the tolerance's unit)
+
+
+def implicit_step(mesh, problem: Problem, u_hist: Sequence[np.ndarray], p_hist: Sequence[np.ndarray],
+                  t_next: float, nodal: Optional[dict] = None, pin_value: float = 0.0,
+                  d_hist: Optional[Sequence[np.ndarray]] = None, tol: float = 1e-11, max_newton: int = 20,
+                  h: float = 1e-6) -> ImplicitStep:
+    """One step of the fully implicit formulation (Eq. u_star implicit, implicit LES term; Section
+    2.4: linearised by Newton's method).  F(U) = sum_e R_e(U) - Neumann data, R_e the element
+    residual with u* = u - u_ALE, tau_M(u*) and r_M(u, p) taken at U itself; Dirichlet rows
+    F_r = s (U_r - g_r).  Newton from the semi-implicit solution, with element Jacobians by central
+    differences of step h (the element residual depends only on the element's 16 unknowns), until
+    ||F|| <= tol ||b_semi||.  Backflow stabilisation and resistance conditions are not included."""
+    for bc in problem.bcs:
+        if bc.kind == "resistance" or (bc.kind == "neumann" and bc.beta > 0.0):
+            raise NotImplementedError("implicit_step: backflow or resistance conditions")
+    prm = problem.params
+    sgm = prm.bdf_order
+    alpha, beta, gamma = bdf_coefficients(sgm)
+    ubdf = sum(beta[j] * u_hist[j] for j in range(sgm))
+    semi = step(mesh, problem, u_hist, p_hist, t_next, nodal, pin_value, d_hist=d_hist)
+    U = semi.x.copy()
+    uale = None
+    if d_hist is not None:
+        uale = ale_velocity(sgm, d_hist, prm.dt)
+        mesh = dataclasses.replace(mesh, nodes=mesh.nodes + d_hist[0])
+    V, T = mesh.nodes.shape[0], mesh.tets.shape[0]
+    N = 4 * V
+    bN = neumann_rhs(mesh, problem, t_next)
+    ids, vals = dirichlet_data(mesh, problem, t_next, nodal)
+    rows = (4 * ids[:, None] + np.arange(3)[None, :]).ravel()
+    rv = vals.ravel()
+    if problem.pin_node >= 0:
+        rows = np.concatenate([rows, [4 * problem.pin_node + 3]])
+        rv = np.concatenate([rv, [pin_value]])
+    lib = load_library()
+    cp = prm.c_struct(problem.riis)
+    ph = _riis_nodal(problem.riis, V)
+    tets = np.ascontiguousarray(mesh.tets, dtype=np.int32)
+    elems = np.arange(T, dtype=np.int64)
+    nodes = np.ascontiguousarray(mesh.nodes, dtype=np.float64)
+    dof = (4 * tets.astype(np.int64)[:, :, None] + np.arange(4)[None, None, :]).reshape(-1, 16)
+    jr = np.broadcast_to(dof[:, :, None], (T, 16, 16)).ravel()
+    jc = np.broadcast_to(dof[:, None, :], (T, 16, 16)).ravel()
+    free = np.ones(N, dtype=bool)
+    free[rows] = False
+    scale = float(np.linalg.norm(semi.b))
+    norms = []
+    for it in range(max_newton + 1):
+        Je, Re = np.zeros(T * 256), np.zeros(T * 16)
+        rc = lib.orc_elements_implicit(ctypes.byref(cp), _dp(nodes), tets.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       elems.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), T,
+                                       _dp(np.ascontiguousarray(ubdf, dtype=np.float64)),
+                                       _dp(np.ascontiguousarray(U, dtype=np.float64)), _dp(ph),
+                                       _opt(uale, 3 * V), V, h, _dp(Je), _dp(Re))
+        if rc != 0:
+            raise ValueError(f"degenerate element at position {-1 - rc}")
+        F = np.zeros(N)
+        np.add.at(F, dof.ravel(), Re)
+        F -= bN
+        norm = float(np.sqrt(np.sum(F[free] ** 2) + np.sum((U[rows] - rv) ** 2)))
+        norms.append(norm)
+        if norm <= tol * scale or it == max_newton:
+            break
+        Jg = sp.coo_matrix((Je, (jr, jc)), shape=(N, N)).tocsr()
+        A, rhs = apply_dirichlet(Jg, -F, rows, rv - U[rows])
+        U = U + solve_direct(A, rhs)
+    return ImplicitStep(U, norms, scale)
 
 
 # ----------------------------------------------------------------------------------------

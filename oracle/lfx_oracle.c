@@ -325,3 +325,53 @@ int orc_elements(const orc_params *P, const double *nodes, const int32_t *tets,
   }
   return 0;
 }
+
+/* ---- fully implicit formulation (Eq. u_star, implicit; implicit LES term) ---------------
+ * The residual of one element when the advection velocity and the LES residual are taken at the
+ * unknown itself: the semi-implicit residual with u^EXT, p^EXT replaced by the element's own
+ * solution, so that u* = u - u_ALE, tau_M = tau_M(u*) and every r_M is r_M(u, p). */
+int orc_element_residual_implicit(const orc_params *P, const double x[12], const double ubdf[12],
+                                  const double sol[16], const double *phinod, const double *uale,
+                                  double R[16]) {
+  double ue[12], pe[4];
+  for (int a = 0; a < 4; ++a) {
+    for (int i = 0; i < 3; ++i) ue[3 * a + i] = sol[4 * a + i];
+    pe[a] = sol[4 * a + 3];
+  }
+  return orc_element_residual(P, x, ubdf, ue, pe, phinod, uale, sol, R);
+}
+
+/* Residuals R [n][16] and their Jacobians J [n][16][16] by central differences of step h in each
+ * of the 16 local unknowns, for a list of elements of a global mesh at the global solution
+ * sol [V][4] (the building blocks of Newton's method for the implicit formulation). */
+int orc_elements_implicit(const orc_params *P, const double *nodes, const int32_t *tets,
+                          const int64_t *elems, int64_t n, const double *ubdf, const double *sol,
+                          const double *phinod, const double *uale, int64_t n_nodes, double h,
+                          double *J, double *R) {
+  for (int64_t t = 0; t < n; ++t) {
+    const int32_t *v = tets + 4 * elems[t];
+    double x[12], ub[12], ua[12], s[16], ph[4 * ORC_MAX_RIIS];
+    for (int a = 0; a < 4; ++a) {
+      for (int i = 0; i < 3; ++i) {
+        x[3 * a + i] = nodes[3 * (int64_t)v[a] + i];
+        ub[3 * a + i] = ubdf[3 * (int64_t)v[a] + i];
+        ua[3 * a + i] = uale ? uale[3 * (int64_t)v[a] + i] : 0.0;
+      }
+      for (int c = 0; c < 4; ++c) s[4 * a + c] = sol[4 * (int64_t)v[a] + c];
+      for (int k = 0; k < P->n_riis; ++k) ph[4 * k + a] = phinod[k * n_nodes + v[a]];
+    }
+    const double *uap = uale ? ua : NULL;
+    if (orc_element_residual_implicit(P, x, ub, s, ph, uap, R + 16 * t) != 0) return -1 - (int)t;
+    for (int k = 0; k < 16; ++k) {
+      double sp[16], sm[16], Rp[16], Rm[16];
+      memcpy(sp, s, sizeof sp);
+      memcpy(sm, s, sizeof sm);
+      sp[k] += h;
+      sm[k] -= h;
+      orc_element_residual_implicit(P, x, ub, sp, ph, uap, Rp);
+      orc_element_residual_implicit(P, x, ub, sm, ph, uap, Rm);
+      for (int i = 0; i < 16; ++i) J[256 * t + 16 * i + k] = (Rp[i] - Rm[i]) / (2.0 * h);
+    }
+  }
+  return 0;
+}
