@@ -1,6 +1,8 @@
 """Oracle: a plain, slow, FP64 CPU implementation of one semi-implicit BDF step of the paper's
 P1-P1 VMS-LES Navier-Stokes discretisation (Section 2.3) and of the aSIMPLE-preconditioned
-GMRES solve (Section 2.4).
+GMRES solve (Section 2.4); also the outlet conditions of Section 2.2 (backflow stabilisation,
+resistance), the moving-domain parts (lifting, mesh velocity, u* = u^EXT - u_ALE) and the fully
+implicit formulation solved by Newton's method.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
 leg of ``bench.py`` may import it.  It shares no code with the CUDA library (no kernels, no
