@@ -37,7 +37,7 @@ import scipy.sparse.linalg as spla
 
 __all__ = [
     "Params", "BC", "RIIS", "Problem", "load_library", "bdf_coefficients", "element",
-    "element_residual", "geometry", "tau", "assemble", "time_law", "boundary_geometry",
+    "element_residual", "geometry", "tau", "qp_coefficients", "assemble", "time_law", "boundary_geometry",
     "dirichlet_data", "neumann_rhs", "apply_dirichlet", "solve_direct", "Step",
     "step", "relative_errors", "disk_sdf", "block_of", "womersley_profile", "backflow_matrix",
     "resistance_vectors", "resistance_terms", "lifting", "ale_velocity", "implicit_step", "ImplicitStep",
@@ -93,6 +93,9 @@ def load_library():
                                                ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, dp, dp, dp, dp,
                                                ctypes.c_int64, ctypes.c_double, dp, dp]
         _lib.orc_elements_implicit.restype = ctypes.c_int
+        _lib.orc_qp_coefficients.argtypes = [ctypes.POINTER(_CParams), dp, dp, dp, dp, dp, dp,
+                                             ctypes.c_int, dp]
+        _lib.orc_qp_coefficients.restype = ctypes.c_int
     return _lib
 
 
@@ -238,6 +241,23 @@ def element(params: Params, x, ubdf, uext, pext, phinod=None, riis=(), uale=None
     if rc != 0:
         raise ValueError("degenerate or inverted element")
     return A.reshape(16, 16), b
+
+
+def qp_coefficients(params: Params, x, ubdf, uext, pext, q, phinod=None, riis=(), uale=None):
+    """The coefficients of quadrature point q (0..3) of one element, as the element routines use
+    them: dict with tau_m, tau_c, s = tau_M r_M(u^EXT, p^EXT) [3] (the LES factor), us = u* [3],
+    sR = sum_k (R_k/eps_k) delta_k, m = rho u^BDF/dt + f [3], w = quadrature weight."""
+    lib = load_library()
+    cp = params.c_struct(riis)
+    args = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (x, ubdf, uext, pext)]
+    ph = np.zeros(4 * MAX_RIIS) if phinod is None else np.ascontiguousarray(phinod, dtype=np.float64).ravel()
+    out = np.zeros(13)
+    rc = lib.orc_qp_coefficients(ctypes.byref(cp), *[_dp(a) for a in args], _dp(ph), _opt(uale, 12), int(q),
+                                 _dp(out))
+    if rc != 0:
+        raise ValueError("degenerate or inverted element, or q outside 0..3")
+    return {"tau_m": out[0], "tau_c": out[1], "s": out[2:5].copy(), "us": out[5:8].copy(), "sR": out[8],
+            "m": out[9:12].copy(), "w": out[12]}
 
 
 def element_residual(params: Params, x, ubdf, uext, pext, sol, phinod=None, riis=(), uale=None):

@@ -163,6 +163,30 @@ static void element_qp(const orc_params *P, const double x[12], const double gra
   }
 }
 
+/* Per-quadrature-point coefficients of one element, for the tests that pin them one by one:
+ * out[0] = tau_M, out[1] = tau_C, out[2..4] = tau_M r_M(u^EXT, p^EXT) (the LES factor),
+ * out[5..7] = u*, out[8] = sum_k (R_k/eps_k) delta_k, out[9..11] = m = rho u^BDF/dt + f,
+ * out[12] = the quadrature weight. */
+int orc_qp_coefficients(const orc_params *P, const double x[12], const double ubdf[12],
+                        const double uext[12], const double pext[4], const double *phinod,
+                        const double *uale, int q, double out[13]) {
+  double gp[12], G[9], g[3], vol;
+  double det = orc_geometry(x, gp, G, g, &vol);
+  if (!(det > 0) || q < 0 || q > 3) return -1;
+  qp_data d;
+  element_qp(P, x, gp, G, g, vol, ubdf, uext, pext, phinod, uale, q, &d);
+  out[0] = d.tau_m;
+  out[1] = d.tau_c;
+  for (int i = 0; i < 3; ++i) {
+    out[2 + i] = d.s[i];
+    out[5 + i] = d.us[i];
+    out[9 + i] = d.m[i];
+  }
+  out[8] = d.sR;
+  out[12] = d.w;
+  return 0;
+}
+
 /* ---- element matrix and right-hand side ------------------------------------------------ */
 int orc_element(const orc_params *P, const double x[12], const double ubdf[12],
                 const double uext[12], const double pext[4], const double *phinod,
