@@ -211,7 +211,18 @@ typedef struct lfx_options {
    * step reaches it), kept within [inner_rtol, 0.1]; for a segmented batch the tightest over the
    * members still running */
   int32_t inner_adaptive;
-  int32_t reserved[5];
+  /* fully implicit formulation (Eq. u_star in its implicit form and the implicit LES term of
+   * Section 2.3), linearised by Newton's method (Section 2.4): each step first solves the
+   * semi-implicit system, then runs Newton iterations from that solution.  Each iteration
+   * assembles the Jacobian of the element residual (u* = u, tau_M(u*), tau_C(u*), r_M(u, p) at the
+   * iterate, derived analytically) with the right-hand side J U - R(U), and solves for the next
+   * iterate with the configured Krylov method, until ||R|| <= newton_rtol ||b|| (b: the step's
+   * semi-implicit right-hand side; Dirichlet rows s (U_r - g_r)).  Not with backflow
+   * stabilisation or resistance conditions (LFX_ERR_INVALID_ARG at problem creation). */
+  int32_t implicit;             /* 0 (default): semi-implicit; 1: fully implicit with Newton     */
+  int32_t newton_max_iters;     /* default 10; the step returns LFX_ERR_NOT_CONVERGED past it   */
+  int32_t reserved;
+  double newton_rtol;           /* default 1e-10                                                 */
 } lfx_options;
 void lfx_options_default(lfx_options *opt);
 
@@ -256,15 +267,52 @@ typedef struct lfx_step_stats {
   int32_t n_assembly_launches;  /* launches of the assembly kernel in this step (= colours)    */
   float ms_spmv;                /* Arnoldi block SpMV launches of the (inner) Krylov solve      */
   int32_t n_spmv;               /* their number (FP64 matrix on the FP64 path, FP32 in mixed)   */
-  int32_t reserved[3];
+  int32_t newton_iterations;    /* Newton updates taken (fully implicit formulation), else 0    */
+  float ms_newton_assembly;     /* device time of the Newton Jacobian assemblies (CUDA events)  */
+  int32_t reserved;
 } lfx_step_stats;
 
-/* One semi-implicit BDF step t^n -> t^{n+1}: BDF/EXT fields, coloured assembly of the
- * linearised block system (FP64, or FP32 with FP64 geometry for badly shaped elements and FP64
- * tau in mixed mode), Neumann and Dirichlet data, the preconditioned Krylov solve, history
- * shift.  Returns LFX_ERR_NOT_CONVERGED after still advancing the state if the solve hit its
+/* One BDF step t^n -> t^{n+1}: BDF/EXT fields, coloured assembly of the linearised block system,
+ * Neumann and Dirichlet data, the preconditioned Krylov solve, history shift; with
+ * options.implicit, Newton iterations of the fully implicit formulation follow the semi-implicit
+ * solve.  Arithmetic: FP64 on the FP64 path.  In mixed precision every element term is formed in
+ * double-float arithmetic (pairs of FP32 numbers, 48-bit significand) and the matrix is stored as
+ * FP32 high and low parts; elements below options.bad_element_quality take their geometry in FP64;
+ * the RIIS delta and the right-hand side are FP64; the outer flexible GMRES works on FP64 vectors
+ * with the double-float operator, the inner GMRES and aSIMPLE in FP32 (BF16 storage optional).
+ * Returns LFX_ERR_NOT_CONVERGED after still advancing the state if a solve (or Newton) hit its
  * cap; stats may be NULL. */
 lfx_status lfx_step(lfx_state *state, lfx_step_stats *stats);
+
+/* Newton residual history of the last step (fully implicit formulation): res[k] = ||R(U_k)|| /
+ * ||b|| for the iterates U_0 (the semi-implicit solution), U_1, ...; *n entries, of which the first
+ * min(*n, capacity) are written to the caller's host array.  0 entries for semi-implicit steps. */
+lfx_status lfx_state_newton_residuals(const lfx_state *state, double *res, int32_t capacity, int32_t *n);
+
+/* ------------------------------------------------------------------------------------------
+ * Moving domain (arbitrary Lagrangian-Eulerian form, Sections 2.1-2.3): the mesh follows a
+ * displacement d from the reference configuration x^ given at creation.
+ * ------------------------------------------------------------------------------------------ */
+/* Makes the state a moving-mesh state with the displacement levels d^n, d^{n-1}, ...:
+ * d_hist [bdf_order][n_nodes][3] (caller numbering, host, copied).  Every later step then needs
+ * lfx_set_boundary_displacement first.  The boundary conditions must be NOSLIP, NODAL or NEUMANN
+ * without backflow stabilisation (LFX_ERR_INVALID_ARG otherwise; the Dirichlet profiles and the
+ * resistance and backflow terms are tied to the reference configuration), on a mesh of one piece.
+ * Builds, once, the lifting operator: the P1 Laplacian of the reference mesh (Eq. lifting, with
+ * sigma^L = grad d, i.e. harmonic extension). */
+lfx_status lfx_state_set_displacement(lfx_state *state, const double *d_hist);
+/* The displacement d^{n+1} of the next step at n listed nodes (caller numbering; d [n][3], host,
+ * copied).  lfx_step extends it into the domain by the lifting problem (Eq. lifting: K d = 0 on the
+ * other nodes, zero normal flux on the rest of the boundary; conjugate gradients with Jacobi
+ * scaling on the device, from d^n, to a relative residual of 1e-12), assembles the step on the
+ * configuration x^ + d^{n+1} (element geometry and Neumann loads recomputed there) with the
+ * advection velocity u* = u^EXT - u_ALE, u_ALE = (alpha d^{n+1} - sum_j beta_j d^{n-j}) / dt the BDF
+ * derivative of the displacement (Eq. u_star; Section 2.3), and then shifts the displacement levels.
+ * LFX_ERR_NOT_CONVERGED from lfx_step if the lifting does not converge in 20000 iterations. */
+lfx_status lfx_set_boundary_displacement(lfx_state *state, int64_t n, const int32_t *nodes, const double *d);
+/* The displacement of the current time level (after a step: d^{n+1}), d [n_nodes][3] caller
+ * numbering, host; *lifting_iterations (nullable) = CG iterations of the last lifting. */
+lfx_status lfx_state_get_displacement(const lfx_state *state, double *d, int32_t *lifting_iterations);
 
 /* Replace the history (same layout as lfx_state_create) and the time; host pointers, copied
  * on the state's stream before the call returns. */
@@ -280,6 +328,11 @@ lfx_status lfx_state_get(const lfx_state *state, double *u, double *p);
  * solving; then copy it out: block values [nnz_blocks][4][4] in the order of
  * lfx_mesh_get_pattern (caller numbering), rhs [n_nodes][4]. FP64 host buffers. */
 lfx_status lfx_debug_assemble(lfx_state *state, int32_t apply_bcs, double *blocks, double *rhs);
+/* The Newton system of the fully implicit formulation (options.implicit need not be set) at the
+ * iterate U [n_nodes][4] (caller numbering, host): the Jacobian J(U) of the element residuals summed
+ * (block values as in lfx_debug_assemble) and the right-hand side J(U) U - R(U) with the Neumann data,
+ * both before Dirichlet rows; the BDF fields are those of the state's next step.  FP64 host buffers. */
+lfx_status lfx_debug_assemble_newton(lfx_state *state, const double *U, double *blocks, double *rhs);
 /* y = A x with the last assembled matrix; x, y [n_nodes][4] FP64 host buffers, caller numbering. */
 lfx_status lfx_debug_spmv(lfx_state *state, const double *x, double *y);
 /* z = P^-1 r with the aSIMPLE preconditioner of the last assembled matrix (FP64 path);
@@ -291,10 +344,29 @@ lfx_status lfx_debug_precond(lfx_state *state, const double *r, double *z, doubl
  * configured Krylov method; x [n_nodes][4] host buffer. */
 lfx_status lfx_debug_solve(lfx_state *state, double *x, lfx_step_stats *stats);
 
+/* The Schur AMG hierarchy of the FP64 path (s_smoother == LFX_SMOOTH_AMG) as the device holds it
+ * after its set-up (a step or lfx_debug_precond / lfx_debug_solve): level `level` >= 1 below the
+ * matrix-free level 0.  sizes = {n_l, nnz(A_l), n_{l+1}, nnz(P_l)} (n_{l+1} = nnz(P_l) = 0 at the
+ * coarsest level; nnz(A_l) = 0 there too, its dense inverse being all the device keeps; P_0 is
+ * level 0's prolongator, reported with level = 0 and nnz(A_0) = 0).  If the array pointers are
+ * non-NULL they receive A_l (a_rp [n_l+1], a_ci, a_v) and P_l (p_rp [n_l+1], p_ci, p_v), CSR with
+ * int32 indices and FP64 values, and *lam the Gershgorin bound of lambda_max(D^-1 A_l) that sets
+ * the level's Chebyshev interval.  Host buffers; LFX_ERR_INVALID_ARG before the set-up or for a
+ * level out of range. */
+lfx_status lfx_debug_amg_level(lfx_state *state, int32_t level, int64_t sizes[4], int32_t *a_rp,
+                               int32_t *a_ci, double *a_v, int32_t *p_rp, int32_t *p_ci, double *p_v,
+                               double *lam);
+/* One device V-cycle of that hierarchy over levels 1 .. L-1 (the part below the matrix-free level
+ * 0, run by the same launch as inside the preconditioner): x1 = V(b1), b1 and x1 [n_1] FP64 host
+ * buffers in level-1 numbering.  Needs at least 3 levels. */
+lfx_status lfx_debug_amg_vcycle(lfx_state *state, const double *b1, double *x1);
+
 /* ------------------------------------------------------------------------------------------
  * Allocation-free preconditioner application (the paper has no counterpart: this is a service
- * for callers that cannot allocate device memory, e.g. while a CUDA graph is being captured,
- * inside a framework that owns all device memory, or in a loop that must not allocate).
+ * for callers that cannot allocate device memory where they need the preconditioner, e.g. a
+ * solver embedded in a framework that owns all device memory through its own pool, or a
+ * time-critical loop that must not pay for an allocation, which may synchronise the device, or
+ * risk its failure midway).
  *
  * z = P^-1 r with the aSIMPLE preconditioner (the same kernels as lfx_step's) for a 4x4
  * block-CSR matrix the caller already holds on the device: row_ptr [n_nodes+1], col_idx
@@ -306,8 +378,9 @@ lfx_status lfx_debug_solve(lfx_state *state, double *x, lfx_step_stats *stats);
  *
  * No memory is allocated: all intermediate arrays live in one 16 MiB static device array that
  * every GPU loading the library holds until process exit; n_nodes above 65536 is rejected with
- * LFX_ERR_INVALID_ARG.  The first call on a device looks the array's address up (make that
- * first call before any stream capture begins).  Every call reuses the same array and clears
+ * LFX_ERR_INVALID_ARG.  The first call on a device (and the first after that device's context
+ * was reset) looks the array's address up with the device current; make that first call before
+ * any stream capture begins.  Every call reuses the same array and clears
  * it first, so calls whose work overlaps on the GPU (different streams, or different host
  * threads) race and must be serialised by the caller.  Work is queued on cuda_stream (NULL =
  * legacy default stream); the call does not synchronise. */
@@ -367,6 +440,16 @@ lfx_status lfx_server_stats(lfx_server *server, float *latency_ms, int64_t capac
                             int64_t *used_bytes, int64_t *n_waiting, int64_t *max_active);
 /* Stops the workers after their current step and frees every remaining state. */
 void lfx_server_destroy(lfx_server *server);
+
+/* One step of each of n independent simulations (distinct states, each on its own stream set
+ * with lfx_set_stream; states on the same stream run one after another): the steps run
+ * concurrently, one host thread per state, so their kernels overlap on the device; stats [n]
+ * (nullable) receive each step's statistics.  Returns LFX_OK, or the first failure in state order
+ * (a hard error before LFX_ERR_NOT_CONVERGED), with the state's index in lfx_last_error().
+ * Every state has advanced unless its own step failed.  Many small meshes are batched more tightly
+ * by passing them to lfx_mesh_create together as one disconnected mesh: one state then steps all
+ * of them with the same launches (one Krylov process per piece, batch_segmented). */
+lfx_status lfx_batch_step(lfx_state *const *states, int32_t n, lfx_step_stats *stats);
 
 #ifdef __cplusplus
 }

@@ -40,7 +40,7 @@ __all__ = [
     "element_residual", "geometry", "tau", "qp_coefficients", "assemble", "time_law", "boundary_geometry",
     "dirichlet_data", "neumann_rhs", "apply_dirichlet", "solve_direct", "Step",
     "step", "relative_errors", "disk_sdf", "block_of", "womersley_profile", "backflow_matrix",
-    "resistance_vectors", "resistance_terms", "lifting", "ale_velocity", "implicit_step", "ImplicitStep",
+    "resistance_vectors", "resistance_terms", "lifting", "ale_velocity", "implicit_step", "ImplicitStep", "implicit_system",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -655,6 +655,28 @@ def implicit_step(mesh, problem: Problem, u_hist: Sequence[np.ndarray], p_hist: 
     if problem.pin_node >= 0:
         rows = np.concatenate([rows, [4 * problem.pin_node + 3]])
         rv = np.concatenate([rv, [pin_value]])
+    free = np.ones(N, dtype=bool)
+    free[rows] = False
+    scale = float(np.linalg.norm(semi.b))
+    norms = []
+    for it in range(max_newton + 1):
+        Jg, F = _implicit_system(mesh, problem, ubdf, U, uale, h)
+        F -= bN
+        norm = float(np.sqrt(np.sum(F[free] ** 2) + np.sum((U[rows] - rv) ** 2)))
+        norms.append(norm)
+        if norm <= tol * scale or it == max_newton:
+            break
+        A, rhs = apply_dirichlet(Jg, -F, rows, rv - U[rows])
+        U = U + solve_direct(A, rhs)
+    return ImplicitStep(U, norms, scale)
+
+
+def _implicit_system(mesh, problem: Problem, ubdf, U, uale=None, h: float = 1e-6):
+    """Sum over the elements of the implicit element residuals R_e(U) and of their Jacobians by
+    central differences of step h: (J csr [4V,4V], F [4V]), without boundary data."""
+    prm = problem.params
+    V, T = mesh.nodes.shape[0], mesh.tets.shape[0]
+    N = 4 * V
     lib = load_library()
     cp = prm.c_struct(problem.riis)
     ph = _riis_nodal(problem.riis, V)
@@ -664,30 +686,28 @@ def implicit_step(mesh, problem: Problem, u_hist: Sequence[np.ndarray], p_hist: 
     dof = (4 * tets.astype(np.int64)[:, :, None] + np.arange(4)[None, None, :]).reshape(-1, 16)
     jr = np.broadcast_to(dof[:, :, None], (T, 16, 16)).ravel()
     jc = np.broadcast_to(dof[:, None, :], (T, 16, 16)).ravel()
-    free = np.ones(N, dtype=bool)
-    free[rows] = False
-    scale = float(np.linalg.norm(semi.b))
-    norms = []
-    for it in range(max_newton + 1):
-        Je, Re = np.zeros(T * 256), np.zeros(T * 16)
-        rc = lib.orc_elements_implicit(ctypes.byref(cp), _dp(nodes), tets.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                       elems.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), T,
-                                       _dp(np.ascontiguousarray(ubdf, dtype=np.float64)),
-                                       _dp(np.ascontiguousarray(U, dtype=np.float64)), _dp(ph),
-                                       _opt(uale, 3 * V), V, h, _dp(Je), _dp(Re))
-        if rc != 0:
-            raise ValueError(f"degenerate element at position {-1 - rc}")
-        F = np.zeros(N)
-        np.add.at(F, dof.ravel(), Re)
-        F -= bN
-        norm = float(np.sqrt(np.sum(F[free] ** 2) + np.sum((U[rows] - rv) ** 2)))
-        norms.append(norm)
-        if norm <= tol * scale or it == max_newton:
-            break
-        Jg = sp.coo_matrix((Je, (jr, jc)), shape=(N, N)).tocsr()
-        A, rhs = apply_dirichlet(Jg, -F, rows, rv - U[rows])
-        U = U + solve_direct(A, rhs)
-    return ImplicitStep(U, norms, scale)
+    Je, Re = np.zeros(T * 256), np.zeros(T * 16)
+    rc = lib.orc_elements_implicit(ctypes.byref(cp), _dp(nodes), tets.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   elems.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), T,
+                                   _dp(np.ascontiguousarray(ubdf, dtype=np.float64)),
+                                   _dp(np.ascontiguousarray(U, dtype=np.float64)), _dp(ph),
+                                   _opt(uale, 3 * V), V, h, _dp(Je), _dp(Re))
+    if rc != 0:
+        raise ValueError(f"degenerate element at position {-1 - rc}")
+    F = np.zeros(N)
+    np.add.at(F, dof.ravel(), Re)
+    return sp.coo_matrix((Je, (jr, jc)), shape=(N, N)).tocsr(), F
+
+
+def implicit_system(mesh, problem: Problem, u_hist: Sequence[np.ndarray], t_next: float, U, h: float = 1e-6):
+    """The Newton system of the fully implicit formulation at the iterate U [4V] on a fixed mesh:
+    (J, F) with J the sum of the element Jacobians (central differences of step h) and
+    F = sum_e R_e(U) - Neumann data at t_next, before Dirichlet rows."""
+    prm = problem.params
+    _, beta, _ = bdf_coefficients(prm.bdf_order)
+    ubdf = sum(beta[j] * u_hist[j] for j in range(prm.bdf_order))
+    J, F = _implicit_system(mesh, problem, ubdf, np.ascontiguousarray(U, dtype=np.float64).ravel(), None, h)
+    return J, F - neumann_rhs(mesh, problem, t_next)
 
 
 # ----------------------------------------------------------------------------------------

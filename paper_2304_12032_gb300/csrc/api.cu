@@ -44,11 +44,12 @@ static lfx_alloc_fn g_alloc = nullptr;
 static lfx_free_fn g_free = nullptr;
 static void *g_alloc_ctx = nullptr;
 
-void *dalloc(size_t bytes) {
+void *dalloc(size_t bytes, DFree *how) {
   void *p = nullptr;
   if (g_alloc) {
     p = g_alloc(bytes, g_alloc_ctx);
     if (!p) set_error("device allocation of %zu bytes failed (user allocator)", bytes);
+    if (how) *how = DFree{g_free, g_alloc_ctx};
     return p;
   }
   cudaError_t e = cudaMalloc(&p, bytes);
@@ -57,11 +58,12 @@ void *dalloc(size_t bytes) {
     set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
     return nullptr;
   }
+  if (how) *how = DFree{};
   return p;
 }
-void dfree(void *p) {
+void dfree(void *p, const DFree &how) {
   if (!p) return;
-  if (g_free) g_free(p, g_alloc_ctx);
+  if (how.fn) how.fn(p, how.ctx);
   else cudaFree(p);
 }
 
@@ -119,6 +121,9 @@ struct lfx_problem {
                      d_r1_w.as<double>(), n_r1_ax, d_r1_ax_node.as<int32_t>(), d_r1_ax_tag.as<int32_t>(),
                      d_r1_ax_w.as<double>()};
   }
+  // faces of Neumann tags (internal numbering) and their BC index: the loads on a moving mesh
+  int64_t n_neu_faces = 0;
+  DBuf d_neu_faces, d_neu_face_bc;
   // RIIS nodal signed distances [n_riis][V]
   DBuf d_phi;
   DBuf d_bad;
@@ -132,7 +137,7 @@ struct lfx_problem {
            d_neu_vec.bytes + d_phi.bytes + d_bad.bytes + geo64.bytes + geo_hi.bytes + geo_lo.bytes +
            d_bf_ij.bytes + d_bf_an.bytes + d_bf_coef.bytes + d_bf_slot4.bytes + d_bf_blk.bytes + d_bf_acc.bytes +
            d_r1_cr.bytes + d_r1_off.bytes + d_r1_node.bytes + d_r1_w.bytes + d_r1_ax_node.bytes + d_r1_ax_tag.bytes +
-           d_r1_ax_w.bytes;
+           d_r1_ax_w.bytes + d_neu_faces.bytes + d_neu_face_bc.bytes;
   }
 };
 
@@ -166,6 +171,18 @@ struct lfx_state {
   int amg_age = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, ea0 = nullptr, ea1 = nullptr;
   int n_asm_launch = 0;
+  // fully implicit formulation: residual vector, norm partials, Newton history of the last step
+  DBuf fres, npart;
+  std::vector<double> newton_res;
+  // moving domain (ALE): displacement levels d^n, d^{n-1}, ... (level l = dhist[(dhead + l) % sigma]),
+  // the next level d^{n+1}, u_ALE, the moved coordinates and their element geometry, the lifting
+  // Laplacian and its CG work arrays, and the next step's prescribed displacements
+  bool ale = false, have_bnd = false;
+  int dhead = 0, lifting_iters = 0;
+  DBuf dhist[3], dnew, uale, xyz, xyz_hi, xyz_lo, geo64, geo_hi, geo_lo;
+  DBuf lapK, lapDinv, lapFixed, lapR, lapZ, lapP, lapAp, lapPart, lapCg, bnd_node, bnd_val;
+  int64_t n_bnd = 0;
+  D4 *dlevel(int l) { return dhist[(dhead + l) % sigma].as<D4>(); }
   ~lfx_state() {
     if (ea0) cudaEventDestroy(ea0);
     if (ea1) cudaEventDestroy(ea1);
@@ -350,6 +367,9 @@ void lfx_options_default(lfx_options *o) {
   o->batch_normalize = 1;
   o->batch_segmented = 1;
   o->inner_adaptive = 1;
+  o->implicit = 0;
+  o->newton_max_iters = 10;
+  o->newton_rtol = 1e-10;
 }
 
 // barycentre, unit outward normal, area of the faces carrying `tag` (area weighted)
@@ -448,6 +468,17 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
               kMaxSmooth);
     return LFX_ERR_INVALID_ARG;
   }
+  if (o.implicit < 0 || o.implicit > 1 || (o.implicit && (o.newton_max_iters < 1 || !(o.newton_rtol > 0.0)))) {
+    set_error("lfx_problem_create: implicit must be 0 or 1, with newton_max_iters >= 1 and newton_rtol > 0");
+    return LFX_ERR_INVALID_ARG;
+  }
+  if (o.implicit)
+    for (int32_t b = 0; b < n_bcs; ++b)
+      if (bcs[b].kind == LFX_BC_RESISTANCE || (bcs[b].kind == LFX_BC_NEUMANN && bcs[b].beta > 0.0)) {
+        set_error("lfx_problem_create: the fully implicit formulation is not available with backflow "
+                  "stabilisation or resistance conditions (boundary condition %d)", b);
+        return LFX_ERR_INVALID_ARG;
+      }
   // physics (Section 2.1.2, Eq. bdf)
   PhysParams &P = pb->P;
   P.rho = rho;
@@ -667,6 +698,24 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
       LFX_TRY(up(pb->d_r1_ax_node, ax_node.data(), sizeof(int32_t) * ax_node.size()));
       LFX_TRY(up(pb->d_r1_ax_tag, ax_tag.data(), sizeof(int32_t) * ax_tag.size()));
       LFX_TRY(up(pb->d_r1_ax_w, ax_w.data(), sizeof(double) * ax_w.size()));
+    }
+    {
+      std::vector<int32_t> fl, fb;
+      for (int b = 0; b < n_bcs; ++b) {
+        if (bcs[b].kind != LFX_BC_NEUMANN) continue;
+        for (int64_t f = 0; f < m.F; ++f) {
+          if (m.btags[f] != bcs[b].tag) continue;
+          for (int k = 0; k < 3; ++k) fl.push_back(m.bfaces[3 * f + k]);
+          fb.push_back(b);
+        }
+      }
+      pb->n_neu_faces = (int64_t)fb.size();
+      LFX_TRY(pb->d_neu_faces.alloc(sizeof(int32_t) * std::max<size_t>(fl.size(), 1)));
+      LFX_TRY(pb->d_neu_face_bc.alloc(sizeof(int32_t) * std::max<size_t>(fb.size(), 1)));
+      if (!fb.empty()) {
+        LFX_CUDA_TRY(cudaMemcpy(pb->d_neu_faces.p, fl.data(), sizeof(int32_t) * fl.size(), cudaMemcpyHostToDevice));
+        LFX_CUDA_TRY(cudaMemcpy(pb->d_neu_face_bc.p, fb.data(), sizeof(int32_t) * fb.size(), cudaMemcpyHostToDevice));
+      }
     }
     const int64_t nn = (int64_t)pb->neu_node.size();
     LFX_TRY(pb->d_neu_node.alloc(sizeof(int32_t) * nn));
@@ -1022,17 +1071,23 @@ lfx_status lfx_state_device_bytes(const lfx_state *s, int64_t *bytes) {
   return LFX_OK;
 }
 
-// Assembly of the system for t^{n+1} = t + dt into vals64 / rhs, x0 = extrapolation.
-static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
+// Assembly of the system for t^{n+1} = t + dt into vals64 / rhs, x0 = extrapolation.  With
+// newton, the Jacobian of the fully implicit formulation at the iterate held in xsol and the
+// right-hand side J U - R(U) instead (the BDF fields of the step's first assembly are kept).
+static lfx_status assemble_system(lfx_state *s, bool apply_bcs, bool newton = false) {
   lfx_problem *pb = s->pb;
   const Mesh &m = pb->mesh->m;
   cudaStream_t st = s->stream;
   const double t1 = s->t + pb->P.dt;
   const int sg = s->sigma;
   const bool mixed = s->mixed();
-  LFX_TRY(launch_bdf(st, m.V, sg, s->level(0), sg > 1 ? s->level(1) : nullptr, sg > 2 ? s->level(2) : nullptr,
-                     pb->beta, pb->gamma, s->xsol.as<D4>(), s->ubdf.as<D4>(), s->xe_hi.as<float4>(),
-                     s->xe_lo.as<float4>(), s->ub_hi.as<float4>(), s->ub_lo.as<float4>()));
+  if (newton) {
+    if (mixed) LFX_TRY(launch_split_vec(st, m.V, s->xsol.as<double>(), s->xe_hi.as<float4>(), s->xe_lo.as<float4>()));
+  } else {
+    LFX_TRY(launch_bdf(st, m.V, sg, s->level(0), sg > 1 ? s->level(1) : nullptr, sg > 2 ? s->level(2) : nullptr,
+                       pb->beta, pb->gamma, s->xsol.as<D4>(), s->ubdf.as<D4>(), s->xe_hi.as<float4>(),
+                       s->xe_lo.as<float4>(), s->ub_hi.as<float4>(), s->ub_lo.as<float4>()));
+  }
   // (every block and row written by its first element needs no clearing beforehand)
   if (mixed) {
     if (!m.all_blocks_touched) {
@@ -1047,7 +1102,7 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
     if (!m.all_blocks_touched) LFX_CUDA_TRY(cudaMemsetAsync(s->vals64.p, 0, s->vals64.bytes, st));
     if (!m.all_nodes_touched) LFX_CUDA_TRY(cudaMemsetAsync(s->rhs.p, 0, s->rhs.bytes, st));
   }
-  AssembleArgs A;
+  AssembleArgs A{};
   A.conn = m.d_conn.as<int4>();
   A.slot = m.d_slot.as<int32_t>();
   A.first = m.d_first.as<uint16_t>();
@@ -1071,15 +1126,25 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
   A.geo64 = pb->geo64.as<double>();
   A.geo_hi = pb->geo_hi.as<float>();
   A.geo_lo = pb->geo_lo.as<float>();
+  if (s->ale) {
+    // the configuration x^ + d^{n+1} and the advection velocity u^EXT - u_ALE
+    A.xyz = s->xyz.as<D4>();
+    A.xyz_hi = s->xyz_hi.as<float4>();
+    A.xyz_lo = s->xyz_lo.as<float4>();
+    A.geo64 = s->geo64.as<double>();
+    A.geo_hi = s->geo_hi.as<float>();
+    A.geo_lo = s->geo_lo.as<float>();
+    A.uale = s->uale.as<D4>();
+  }
   LFX_CUDA_TRY(cudaEventRecord(s->ea0, st));
   if (mixed) {
     // double-float arithmetic; badly shaped elements keep FP64 geometry
     A.bad = pb->n_bad > 0 ? pb->d_bad.as<uint8_t>() : nullptr;
     LFX_TRY((launch_assemble<dd, float>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
-                                        s->vals32.as<float>())));
+                                        s->vals32.as<float>(), newton)));
   } else {
     LFX_TRY((launch_assemble<double, double>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
-                                             s->vals64.as<double>())));
+                                             s->vals64.as<double>(), newton)));
   }
   LFX_CUDA_TRY(cudaEventRecord(s->ea1, st));
   if (pb->n_bf_edges > 0)
@@ -1097,8 +1162,12 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs) {
   for (int b = 0; b < nb; ++b)
     if (pb->bcs[b].kind == LFX_BC_NEUMANN || pb->bcs[b].kind == LFX_BC_RESISTANCE)
       C.c[b] = time_law(pb->bcs[b].time, t1);
-  LFX_TRY(launch_neumann(st, (int64_t)pb->neu_node.size(), pb->d_neu_node.as<int32_t>(), pb->d_neu_bc.as<int32_t>(),
-                         pb->d_neu_vec.as<double>(), C, s->rhs.as<double>()));
+  if (s->ale)
+    LFX_TRY(launch_neumann_faces(st, pb->n_neu_faces, pb->d_neu_faces.as<int32_t>(), pb->d_neu_face_bc.as<int32_t>(), C,
+                                 s->xyz.as<D4>(), s->rhs.as<double>()));
+  else
+    LFX_TRY(launch_neumann(st, (int64_t)pb->neu_node.size(), pb->d_neu_node.as<int32_t>(), pb->d_neu_bc.as<int32_t>(),
+                           pb->d_neu_vec.as<double>(), C, s->rhs.as<double>()));
   if (!apply_bcs) return LFX_OK;
   memset(&C, 0, sizeof(C));
   const int H = pb->H;
@@ -1342,7 +1411,250 @@ static lfx_status run_solve(lfx_state *s, double *x, bool x_zero, int *its, int 
   return rc;
 }
 
+// ALE before a step: the lifting of the prescribed displacements (CG from d^n), the moved
+// coordinates x^ + d^{n+1} and their element geometry, and u_ALE (Section 2.3).
+static lfx_status ale_prepare(lfx_state *s) {
+  lfx_problem *pb = s->pb;
+  const Mesh &m = pb->mesh->m;
+  cudaStream_t st = s->stream;
+  const int64_t V = m.V;
+  if (!s->have_bnd) {
+    set_error("lfx_step: a moving-mesh state needs lfx_set_boundary_displacement before every step");
+    return LFX_ERR_INVALID_ARG;
+  }
+  LFX_CUDA_TRY(cudaMemcpyAsync(s->dnew.p, s->dlevel(0), sizeof(D4) * (size_t)V, cudaMemcpyDeviceToDevice, st));
+  const LiftingView L{V, m.d_rowptr.as<int32_t>(), m.d_col.as<int32_t>(), s->lapK.as<double>(), s->lapDinv.as<double>(),
+                      s->lapFixed.as<uint8_t>(), s->lapR.as<D4>(), s->lapZ.as<D4>(), s->lapP.as<D4>(),
+                      s->lapAp.as<D4>(), s->lapPart.as<double>(), s->lapCg.p};
+  LFX_TRY(lifting_solve(st, L, s->n_bnd, s->bnd_node.as<int32_t>(), s->bnd_val.as<D4>(), s->dnew.as<D4>(), 1e-12,
+                        20000, &s->lifting_iters));
+  const bool mixed = s->mixed();
+  LFX_TRY(launch_move_nodes(st, V, m.d_xyz.as<D4>(), s->dnew.as<D4>(), s->xyz.as<D4>(),
+                            mixed ? s->xyz_hi.as<float4>() : nullptr, mixed ? s->xyz_lo.as<float4>() : nullptr));
+  AssembleArgs G{};
+  G.conn = m.d_conn.as<int4>();
+  G.xyz = s->xyz.as<D4>();
+  G.xyz_hi = s->xyz_hi.as<float4>();
+  G.xyz_lo = s->xyz_lo.as<float4>();
+  G.n_nodes = V;
+  G.n_elems = m.T;
+  if (mixed) {
+    G.bad = pb->n_bad > 0 ? pb->d_bad.as<uint8_t>() : nullptr;
+    LFX_TRY(launch_geometry<dd>(st, G, m.T, nullptr, s->geo_hi.as<float>(), s->geo_lo.as<float>()));
+  } else {
+    LFX_TRY(launch_geometry<double>(st, G, m.T, s->geo64.as<double>(), nullptr, nullptr));
+  }
+  const int sg = s->sigma;
+  LFX_TRY(launch_mesh_velocity(st, V, sg, s->dnew.as<D4>(), s->dlevel(0), sg > 1 ? s->dlevel(1) : nullptr,
+                               sg > 2 ? s->dlevel(2) : nullptr, pb->P.alpha, pb->beta, pb->P.dt, s->uale.as<D4>()));
+  return LFX_OK;
+}
+
+// ||v|| (n values) on the device, read back (synchronises the stream)
+static lfx_status device_norm(lfx_state *s, const double *v, int64_t n, double *out) {
+  const int64_t V = s->pb->mesh->m.V;
+  const size_t cap = sizeof(double) * (size_t)norm_partials_capacity(V);
+  if (s->npart.bytes < cap) LFX_TRY(s->npart.alloc(cap));
+  int ng = 0;
+  LFX_TRY(launch_norm_partials(s->stream, v, n, s->npart.as<double>(), &ng));
+  std::vector<double> h(ng);
+  LFX_CUDA_TRY(cudaMemcpyAsync(h.data(), s->npart.p, sizeof(double) * ng, cudaMemcpyDeviceToHost, s->stream));
+  LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  double a = 0.0;
+  for (double x : h) a += x;
+  *out = std::sqrt(a);
+  return LFX_OK;
+}
+
+// ||rhs - J U|| for the assembled Newton system and the iterate in xsol (read back)
+static lfx_status newton_residual_norm(lfx_state *s, double *out) {
+  const int64_t V = s->pb->mesh->m.V;
+  if (s->fres.bytes < sizeof(D4) * (size_t)V) LFX_TRY(s->fres.alloc(sizeof(D4) * (size_t)V));
+  const size_t cap = sizeof(double) * (size_t)norm_partials_capacity(V);
+  if (s->npart.bytes < cap) LFX_TRY(s->npart.alloc(cap));
+  int ng = 0;
+  if (s->mixed())
+    LFX_TRY((launch_spmv<DDMat, double>(s->stream, s->view_dd(), s->xsol.as<double>(), s->rhs.as<double>(),
+                                        s->fres.as<double>(), 1, s->npart.as<double>(), &ng)));
+  else
+    LFX_TRY((launch_spmv<double, double>(s->stream, s->view64(), s->xsol.as<double>(), s->rhs.as<double>(),
+                                         s->fres.as<double>(), 1, s->npart.as<double>(), &ng)));
+  std::vector<double> h(ng);
+  LFX_CUDA_TRY(cudaMemcpyAsync(h.data(), s->npart.p, sizeof(double) * ng, cudaMemcpyDeviceToHost, s->stream));
+  LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  double a = 0.0;
+  for (double x : h) a += x;
+  *out = std::sqrt(a);
+  return LFX_OK;
+}
+
+// Newton iterations of the fully implicit formulation (Section 2.4) from the semi-implicit solution
+// in xsol: assemble J(U_k) and b + X U_k, stop once ||R(U_k)|| <= newton_rtol * scale, else solve
+// J U_{k+1} = b + X U_k from U_k.
+static lfx_status newton_loop(lfx_state *s, double scale, int *n_newton, int *its, int *outer, double *rel,
+                              float *ms_asm) {
+  const lfx_options &o = s->pb->opt;
+  s->newton_res.clear();
+  *n_newton = 0;
+  *ms_asm = 0.0f;
+  lfx_status status = LFX_OK;
+  for (int k = 0;; ++k) {
+    LFX_TRY(assemble_system(s, true, true));
+    double fn = 0.0;
+    LFX_TRY(newton_residual_norm(s, &fn));
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, s->ea0, s->ea1) == cudaSuccess) *ms_asm += ms;
+    s->newton_res.push_back(scale > 0.0 ? fn / scale : fn);
+    if (!std::isfinite(fn)) {
+      set_error("Newton: non-finite residual at iteration %d", k);
+      return LFX_ERR_NONFINITE;
+    }
+    if (fn <= o.newton_rtol * scale) break;
+    if (k >= o.newton_max_iters) {
+      set_error("Newton: not converged after %d iterations (relative residual %.3e)", k, fn / scale);
+      status = LFX_ERR_NOT_CONVERGED;
+      break;
+    }
+    LFX_TRY(prepare_precond(s));
+    int it = 0, ou = 0;
+    double r = 0.0;
+    lfx_status rc = run_solve(s, s->xsol.as<double>(), false, &it, &ou, &r);
+    if (rc != LFX_OK && rc != LFX_ERR_NOT_CONVERGED) return rc;
+    *its += it;
+    *outer += ou;
+    *rel = r;
+    ++*n_newton;
+  }
+  return status;
+}
+
 extern "C" {
+
+lfx_status lfx_state_newton_residuals(const lfx_state *s, double *res, int32_t capacity, int32_t *n) {
+  if (!s || !n || capacity < 0 || (capacity > 0 && !res)) {
+    set_error("lfx_state_newton_residuals: invalid argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  *n = (int32_t)s->newton_res.size();
+  for (int32_t k = 0; k < *n && k < capacity; ++k) res[k] = s->newton_res[k];
+  return LFX_OK;
+}
+
+lfx_status lfx_state_set_displacement(lfx_state *s, const double *d_hist) {
+  clear_error();
+  if (!s || !d_hist) {
+    set_error("lfx_state_set_displacement: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  lfx_problem *pb = s->pb;
+  const Mesh &m = pb->mesh->m;
+  for (size_t b = 0; b < pb->bcs.size(); ++b) {
+    const lfx_bc &bc = pb->bcs[b];
+    if (bc.kind == LFX_BC_DIRICHLET || bc.kind == LFX_BC_RESISTANCE || (bc.kind == LFX_BC_NEUMANN && bc.beta > 0.0)) {
+      set_error("lfx_state_set_displacement: on a moving mesh the boundary conditions must be NOSLIP, NODAL or "
+                "NEUMANN without backflow stabilisation (boundary condition %d)", (int)b);
+      return LFX_ERR_INVALID_ARG;
+    }
+  }
+  if (m.n_comp > 1) {
+    set_error("lfx_state_set_displacement: moving meshes of several pieces are not supported");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const int64_t V = m.V;
+  cudaStream_t st = s->stream;
+  if (!s->ale) {
+    const size_t v4 = sizeof(D4) * (size_t)V;
+    for (int l = 0; l < s->sigma; ++l) LFX_TRY(s->dhist[l].alloc(v4));
+    DBuf *b4[] = {&s->dnew, &s->uale, &s->xyz, &s->lapR, &s->lapZ, &s->lapP, &s->lapAp};
+    for (DBuf *b : b4) LFX_TRY(b->alloc(v4));
+    const size_t nv = (size_t)kGeoValues * (size_t)std::max<int64_t>(m.T, 1);
+    if (s->mixed()) {
+      LFX_TRY(s->xyz_hi.alloc(sizeof(float4) * (size_t)V));
+      LFX_TRY(s->xyz_lo.alloc(sizeof(float4) * (size_t)V));
+      LFX_TRY(s->geo_hi.alloc(sizeof(float) * nv));
+      LFX_TRY(s->geo_lo.alloc(sizeof(float) * nv));
+    } else {
+      LFX_TRY(s->geo64.alloc(sizeof(double) * nv));
+    }
+    LFX_TRY(s->lapK.alloc(sizeof(double) * (size_t)m.nnzb));
+    LFX_TRY(s->lapDinv.alloc(sizeof(double) * (size_t)V));
+    LFX_TRY(s->lapFixed.alloc((size_t)V));
+    LFX_TRY(s->lapPart.alloc(sizeof(double) * (size_t)lifting_part_entries(V)));
+    LFX_TRY(s->lapCg.alloc(lifting_cg_state_bytes()));
+    LFX_TRY(launch_lifting_matrix(st, m.T, V, m.nnzb, m.d_slot.as<int32_t>(), m.d_diag.as<int32_t>(),
+                                  pb->geo64.as<double>(), pb->geo_hi.as<float>(), pb->geo_lo.as<float>(),
+                                  s->lapK.as<double>(), s->lapDinv.as<double>()));
+  }
+  // the levels in the caller's layout [sigma][V][3], scattered to the internal order (w = 0)
+  const size_t nu = sizeof(double) * 3 * (size_t)V * s->sigma;
+  if (s->io_u.bytes < nu) LFX_TRY(s->io_u.alloc(nu));
+  if (s->io_p.bytes < sizeof(double) * (size_t)V) LFX_TRY(s->io_p.alloc(sizeof(double) * (size_t)V));
+  LFX_CUDA_TRY(cudaMemcpyAsync(s->io_u.p, d_hist, nu, cudaMemcpyHostToDevice, st));
+  LFX_CUDA_TRY(cudaMemsetAsync(s->io_p.p, 0, sizeof(double) * (size_t)V, st));
+  s->dhead = 0;
+  for (int l = 0; l < s->sigma; ++l)
+    LFX_TRY(launch_node_scatter(st, V, m.d_node_old.as<int32_t>(), s->io_u.as<double>() + (size_t)l * 3 * V,
+                                s->io_p.as<double>(), s->dhist[l].as<D4>()));
+  LFX_CUDA_TRY(cudaStreamSynchronize(st));
+  s->ale = true;
+  s->have_bnd = false;
+  s->assembled = false;
+  return LFX_OK;
+}
+
+lfx_status lfx_set_boundary_displacement(lfx_state *s, int64_t n, const int32_t *nodes, const double *d) {
+  clear_error();
+  if (!s || n < 0 || (n > 0 && (!nodes || !d))) {
+    set_error("lfx_set_boundary_displacement: invalid argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  if (!s->ale) {
+    set_error("lfx_set_boundary_displacement: call lfx_state_set_displacement first");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = s->pb->mesh->m;
+  std::vector<int32_t> in((size_t)std::max<int64_t>(n, 1));
+  std::vector<D4> val((size_t)std::max<int64_t>(n, 1));
+  for (int64_t k = 0; k < n; ++k) {
+    if (nodes[k] < 0 || nodes[k] >= m.V) {
+      set_error("lfx_set_boundary_displacement: node %d out of range", nodes[k]);
+      return LFX_ERR_INVALID_ARG;
+    }
+    in[k] = m.node_new[nodes[k]];
+    val[k] = D4{d[3 * k], d[3 * k + 1], d[3 * k + 2], 0.0};
+  }
+  if (s->bnd_node.bytes < sizeof(int32_t) * in.size()) LFX_TRY(s->bnd_node.alloc(sizeof(int32_t) * in.size()));
+  if (s->bnd_val.bytes < sizeof(D4) * val.size()) LFX_TRY(s->bnd_val.alloc(sizeof(D4) * val.size()));
+  LFX_CUDA_TRY(cudaMemcpyAsync(s->bnd_node.p, in.data(), sizeof(int32_t) * in.size(), cudaMemcpyHostToDevice, s->stream));
+  LFX_CUDA_TRY(cudaMemcpyAsync(s->bnd_val.p, val.data(), sizeof(D4) * val.size(), cudaMemcpyHostToDevice, s->stream));
+  LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->n_bnd = n;
+  s->have_bnd = true;
+  return LFX_OK;
+}
+
+lfx_status lfx_state_get_displacement(const lfx_state *s, double *d, int32_t *lifting_iterations) {
+  clear_error();
+  if (!s || !d) {
+    set_error("lfx_state_get_displacement: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  if (!s->ale) {
+    set_error("lfx_state_get_displacement: not a moving-mesh state");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = s->pb->mesh->m;
+  const int64_t V = m.V;
+  if (s->io_u.bytes < sizeof(double) * 3 * (size_t)V) LFX_TRY(s->io_u.alloc(sizeof(double) * 3 * (size_t)V));
+  if (s->io_p.bytes < sizeof(double) * (size_t)V) LFX_TRY(s->io_p.alloc(sizeof(double) * (size_t)V));
+  lfx_state *sm = const_cast<lfx_state *>(s);
+  LFX_TRY(launch_node_gather(s->stream, V, m.d_node_old.as<int32_t>(), sm->dlevel(0), s->io_u.as<double>(),
+                             s->io_p.as<double>()));
+  LFX_CUDA_TRY(cudaMemcpyAsync(d, s->io_u.p, sizeof(double) * 3 * (size_t)V, cudaMemcpyDeviceToHost, s->stream));
+  LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (lifting_iterations) *lifting_iterations = s->lifting_iters;
+  return LFX_OK;
+}
 
 lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   clear_error();
@@ -1354,8 +1666,11 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   const lfx_options &o = pb->opt;
   cudaStream_t st = s->stream;
   LFX_CUDA_TRY(cudaEventRecord(s->e0, st));
+  if (s->ale) LFX_TRY(ale_prepare(s));
   LFX_TRY(assemble_system(s, true));
   LFX_CUDA_TRY(cudaEventRecord(s->e1, st));
+  double scale = 0.0;
+  if (o.implicit) LFX_TRY(device_norm(s, s->rhs.as<double>(), 4 * pb->mesh->m.V, &scale));
   LFX_TRY(prepare_precond(s));
   int its = 0, outer = 0;
   double rel = 0.0;
@@ -1364,12 +1679,29 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   s->gmdd.n_tev = 0;
   lfx_status rc = run_solve(s, s->xsol.as<double>(), false, &its, &outer, &rel);
   if (rc != LFX_OK && rc != LFX_ERR_NOT_CONVERGED) return rc;
+  int n_newton = 0;
+  float ms_newton = 0.0f, ms_asm_semi = 0.0f;
+  if (o.implicit) {
+    LFX_CUDA_TRY(cudaEventSynchronize(s->ea1));
+    cudaEventElapsedTime(&ms_asm_semi, s->ea0, s->ea1);
+    lfx_status rn = newton_loop(s, scale, &n_newton, &its, &outer, &rel, &ms_newton);
+    if (rn != LFX_OK && rn != LFX_ERR_NOT_CONVERGED) return rn;
+    if (rn == LFX_ERR_NOT_CONVERGED) rc = rn;
+  } else {
+    s->newton_res.clear();
+  }
   LFX_CUDA_TRY(cudaEventRecord(s->e2, st));
-  // history shift: the solution becomes level 0
+  // history shift: the solution becomes level 0 (and d^{n+1} the displacement's level 0)
   const int oldest = (s->head + s->sigma - 1) % s->sigma;
   std::swap(s->hist[oldest].p, s->xsol.p);
   std::swap(s->hist[oldest].bytes, s->xsol.bytes);
   s->head = oldest;
+  if (s->ale) {
+    const int dold = (s->dhead + s->sigma - 1) % s->sigma;
+    std::swap(s->dhist[dold], s->dnew);
+    s->dhead = dold;
+    s->have_bnd = false;
+  }
   s->t += pb->P.dt;
   s->assembled = false;
   LFX_CUDA_TRY(cudaEventSynchronize(s->e2));
@@ -1382,8 +1714,11 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
     cudaEventElapsedTime(&stats->ms_assembly, s->e0, s->e1);
     cudaEventElapsedTime(&stats->ms_solve, s->e1, s->e2);
     cudaEventElapsedTime(&stats->ms_total, s->e0, s->e2);
-    cudaEventElapsedTime(&stats->ms_assembly_kernels, s->ea0, s->ea1);
+    if (o.implicit) stats->ms_assembly_kernels = ms_asm_semi;
+    else cudaEventElapsedTime(&stats->ms_assembly_kernels, s->ea0, s->ea1);
     stats->n_assembly_launches = s->n_asm_launch;
+    stats->newton_iterations = n_newton;
+    stats->ms_newton_assembly = ms_newton;
     if (o.precision == LFX_PREC_MIXED) {
       s->gm32.read_spmv_timing(&stats->ms_spmv, &stats->n_spmv);
       int dummy = 0;
@@ -1459,6 +1794,27 @@ lfx_status lfx_debug_assemble(lfx_state *s, int32_t apply_bcs, double *blocks, d
   return LFX_OK;
 }
 
+lfx_status lfx_debug_assemble_newton(lfx_state *s, const double *U, double *blocks, double *rhs) {
+  clear_error();
+  if (!s || !U || !blocks || !rhs) {
+    set_error("lfx_debug_assemble_newton: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = s->pb->mesh->m;
+  LFX_TRY(assemble_system(s, false));          // the step's BDF fields (u^BDF)
+  LFX_TRY(vec_to_device(m, U, s->xsol.as<double>(), s->stream));
+  LFX_TRY(assemble_system(s, false, true));
+  s->assembled = false;
+  std::vector<double> v;
+  LFX_TRY(download_matrix(s, v));
+  LFX_TRY(vec_to_host(m, s->rhs.as<double>(), rhs, s->stream));
+  std::vector<int64_t> rp, ib;
+  std::vector<int32_t> ci;
+  user_pattern(m, rp, ci, ib);
+  for (int64_t q = 0; q < m.nnzb; ++q) memcpy(blocks + 16 * q, v.data() + 16 * ib[q], 16 * sizeof(double));
+  return LFX_OK;
+}
+
 lfx_status lfx_debug_spmv(lfx_state *s, const double *x, double *y) {
   clear_error();
   if (!s || !x || !y || !s->assembled) {
@@ -1499,6 +1855,54 @@ lfx_status lfx_debug_precond(lfx_state *s, const double *r, double *z, double *l
   LFX_TRY(s->pc64.apply(s->stream, A, dr.as<double>(), dz.as<double>(), nullptr));
   LFX_TRY(vec_to_host(m, dz.as<double>(), z, s->stream));
   return s->pc64.lambdas(lam_f, lam_s);
+}
+
+lfx_status lfx_debug_amg_level(lfx_state *s, int32_t level, int64_t sizes[4], int32_t *a_rp, int32_t *a_ci,
+                               double *a_v, int32_t *p_rp, int32_t *p_ci, double *p_v, double *lam) {
+  clear_error();
+  if (!s || !sizes || s->mixed() || !s->pc64.amg_ready || level < 0 || level >= (int)s->pc64.amg.size()) {
+    set_error("lfx_debug_amg_level: needs the FP64 path with a built Schur AMG hierarchy and a level in range");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const AmgDevLevel &D = s->pc64.amg[level];
+  const bool has_a = level >= 1 && D.rp.p != nullptr, has_p = D.Prp.p != nullptr;
+  const int64_t nnz_a = has_a ? (int64_t)(D.v.bytes / sizeof(double)) : 0;
+  const int64_t nnz_p = has_p ? (int64_t)(D.Pv.bytes / sizeof(double)) : 0;
+  sizes[0] = D.n;
+  sizes[1] = nnz_a;
+  sizes[2] = has_p ? D.nnext : 0;
+  sizes[3] = nnz_p;
+  if (lam) *lam = D.lam;
+  auto get = [&](void *dst, const DBuf &src, size_t bytes) -> lfx_status {
+    if (dst && bytes) LFX_CUDA_TRY(cudaMemcpy(dst, src.p, bytes, cudaMemcpyDeviceToHost));
+    return LFX_OK;
+  };
+  if (has_a) {
+    LFX_TRY(get(a_rp, D.rp, sizeof(int32_t) * (size_t)(D.n + 1)));
+    LFX_TRY(get(a_ci, D.ci, sizeof(int32_t) * (size_t)nnz_a));
+    LFX_TRY(get(a_v, D.v, sizeof(double) * (size_t)nnz_a));
+  }
+  if (has_p) {
+    LFX_TRY(get(p_rp, D.Prp, sizeof(int32_t) * (size_t)(D.n + 1)));
+    LFX_TRY(get(p_ci, D.Pci, sizeof(int32_t) * (size_t)nnz_p));
+    LFX_TRY(get(p_v, D.Pv, sizeof(double) * (size_t)nnz_p));
+  }
+  return LFX_OK;
+}
+
+lfx_status lfx_debug_amg_vcycle(lfx_state *s, const double *b1, double *x1) {
+  clear_error();
+  if (!s || !b1 || !x1 || s->mixed() || !s->pc64.amg_ready || s->pc64.amg.size() < 3) {
+    set_error("lfx_debug_amg_vcycle: needs the FP64 path with a built Schur AMG hierarchy of >= 3 levels");
+    return LFX_ERR_INVALID_ARG;
+  }
+  ASimple<double, double> &pc = s->pc64;
+  AmgDevLevel &L1 = pc.amg[1];
+  LFX_CUDA_TRY(cudaMemcpyAsync(L1.b.p, b1, sizeof(double) * (size_t)L1.n, cudaMemcpyHostToDevice, s->stream));
+  LFX_TRY(pc.coarse_cycle(s->stream, nullptr));
+  LFX_CUDA_TRY(cudaMemcpyAsync(x1, pc.coarse_x(), sizeof(double) * (size_t)L1.n, cudaMemcpyDeviceToHost, s->stream));
+  LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return LFX_OK;
 }
 
 lfx_status lfx_debug_solve(lfx_state *s, double *x, lfx_step_stats *stats) {

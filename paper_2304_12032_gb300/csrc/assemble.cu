@@ -116,6 +116,28 @@ struct ElemShared {
   R Svp[kElems][4], Ppv[kElems][4], Wv[kElems][4][3], Zv[kElems][3], TM[kElems], TC[kElems], muvol[kElems];
 };
 
+// Extra per-element data of the Newton linearisation of the fully implicit formulation (the
+// residual's dependence on u* = u - u_ALE, tau_M(u*), tau_C(u*) and r_M(u, p) at the iterate):
+template <class R>
+struct ImplShared {
+  R Gr[kElems][9];         // grad u of the iterate, (grad u)_ij = d_j u_i (constant on a P1 element)
+  R uq[kElems][4][3];      // u*(x_q)
+  R rq[kElems][4][3];      // r_M(u, p)(x_q)
+  R tm[kElems][4];         // tau_M
+  R tcr[kElems][4];        // tau_C / tau_M
+  R kap[kElems][4][3];     // d tau_M / d u* = -tau_M^3 rho^2 G u*
+  R Gga[kElems][4][3];     // (grad u)^T grad phi_a
+};
+template <class R, bool IMPL>
+struct AsmShared {
+  ElemShared<R> e;
+};
+template <class R>
+struct AsmShared<R, true> {
+  ElemShared<R> e;
+  ImplShared<R> x;
+};
+
 // Geometry of one tetrahedron in precision G: grad phi_a = J^-T grad_ref phi_a, the metric
 // tensor G = J^-T J^-1 (as its 9 entries), g = J^-T 1, |K| = det J / 6.
 template <class G>
@@ -272,9 +294,9 @@ __global__ void geometry_kernel(AssembleArgs A, int64_t T, double *out64, float 
 // Phase 1b for one (element, quadrature point): u*, u^BDF, tau_M and tau_C (FP64 for the FP64
 // and FP32 kernels, dd for the dd kernel), the resistive coefficient (FP64), and the LES vector
 // tau_M r_M(u^EXT, p^EXT).
-template <class R>
+template <class R, bool IMPL>
 __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q, int64_t e, int q,
-                         int le, ElemShared<R> &sh) {
+                         int le, ElemShared<R> &sh, ImplShared<R> *ix) {
   const int4 cn = A.conn[e];
   const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
   R ue[4][4], ub[4][4];
@@ -288,12 +310,23 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR
   R lam[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) lam[a] = (a == q) ? cst<R>(kQA) : cst<R>(kQB);
-  // u* = u^EXT(x_q) (semi-implicit, no ALE), u^BDF(x_q)
-  R us[3], ubq[3];
+  // u^EXT(x_q), u^BDF(x_q), and the advection velocity u* = u^EXT - u_ALE (Eq. u_star; u_ALE = 0 on
+  // a fixed mesh)
+  R uq[3], us[3], ubq[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    us[i] = fmadd(lam[3], ue[3][i], fmadd(lam[2], ue[2][i], fmadd(lam[1], ue[1][i], lam[0] * ue[0][i])));
+    uq[i] = fmadd(lam[3], ue[3][i], fmadd(lam[2], ue[2][i], fmadd(lam[1], ue[1][i], lam[0] * ue[0][i])));
     ubq[i] = fmadd(lam[3], ub[3][i], fmadd(lam[2], ub[2][i], fmadd(lam[1], ub[1][i], lam[0] * ub[0][i])));
+    us[i] = uq[i];
+  }
+  if (A.uale) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const D4 v = A.uale[nd[a]];
+      us[0] = us[0] - lam[a] * (R)v.x;
+      us[1] = us[1] - lam[a] * (R)v.y;
+      us[2] = us[2] - lam[a] * (R)v.z;
+    }
   }
   R adv[4];
 #pragma unroll
@@ -349,6 +382,43 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR
     tauc = (R)(tsum * tm * (double)sh.igg[le]);
   }
   R z[3] = {cst<R>(0.0), cst<R>(0.0), cst<R>(0.0)};
+  if (IMPL) {
+    // the iterate's strong residual r_M(u, p), grad u, and the derivative of tau_M in u*
+    R rmv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R conv = cst<R>(0.0), gpr = cst<R>(0.0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        conv = fmadd(adv[a], ue[a][i], conv);
+        gpr = fmadd(ue[a][3], gp[3 * a + i], gpr);
+      }
+      rmv[i] = fmadd(sRr, uq[i], fmadd(Q.rho, conv, fmadd(Q.rho_dt, fmadd(Q.alpha, uq[i], -ubq[i]), gpr))) - Q.f[i];
+    }
+    const R k3 = -(taum * taum * taum) * (Q.rho * Q.rho);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      R Gu = cst<R>(0.0);
+#pragma unroll
+      for (int l = 0; l < 3; ++l) Gu = fmadd(Gm[3 * k + l], us[l], Gu);
+      ix->kap[le][q][k] = k3 * Gu;
+      ix->uq[le][q][k] = us[k];
+      ix->rq[le][q][k] = rmv[k];
+    }
+    ix->tm[le][q] = taum;
+    ix->tcr[le][q] = tauc / taum;
+    if (q == 0) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          R g = cst<R>(0.0);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) g = fmadd(ue[a][i], gp[3 * a + j], g);
+          ix->Gr[le][3 * i + j] = g;
+        }
+    }
+  }
   if (P.stab >= 2) {
     // tau_M r_M(u^EXT, p^EXT) with the strong residual of Section 2.3 (-mu Lap u = 0 for P1)
 #pragma unroll
@@ -359,7 +429,7 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR
         conv = fmadd(adv[a], ue[a][i], conv);
         gpr = fmadd(ue[a][3], gp[3 * a + i], gpr);
       }
-      const R rm = fmadd(sRr, us[i], fmadd(Q.rho, conv, fmadd(Q.rho_dt, fmadd(Q.alpha, us[i], -ubq[i]), gpr))) - Q.f[i];
+      const R rm = fmadd(sRr, uq[i], fmadd(Q.rho, conv, fmadd(Q.rho_dt, fmadd(Q.alpha, uq[i], -ubq[i]), gpr))) - Q.f[i];
       z[i] = Q.rho * taum * (us[i] - taum * rm);
     }
   }
@@ -380,8 +450,15 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR
 
 // Phase 1c for one (element, node n): per-(qp, node) products and per-node sums over the
 // quadrature points, shared by the 16 blocks of the element.
-template <class R>
-__device__ void node_phase(const PhysParams &P, const PhysR<R> &Q, int n, int le, ElemShared<R> &sh) {
+template <class R, bool IMPL>
+__device__ void node_phase(const PhysParams &P, const PhysR<R> &Q, int n, int le, ElemShared<R> &sh,
+                           ImplShared<R> *ix) {
+  if (IMPL) {
+    const R *g = sh.gphi[le] + 3 * n;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      ix->Gga[le][n][j] = fmadd(ix->Gr[le][6 + j], g[2], fmadd(ix->Gr[le][3 + j], g[1], ix->Gr[le][j] * g[0]));
+  }
   const R w = sh.w[le];
   const R rho = Q.rho;
   const R *gn = sh.gphi[le] + 3 * n;
@@ -458,9 +535,113 @@ template <> struct Vec16<float> {
 };
 
 // Phase 2 for one (element, a, b): block (a, b) and right-hand-side entry 4a+b.
-template <class R, class S>
+// dd values across the 4 lanes (a, b = 0..3) of one block row: sum over b
+template <class R>
+__device__ __forceinline__ R quad_sum(R v, unsigned mask) {
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+template <>
+__device__ __forceinline__ dd quad_sum<dd>(dd v, unsigned mask) {
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) v += dd(__shfl_xor_sync(mask, v.hi, o), __shfl_xor_sync(mask, v.lo, o));
+  return v;
+}
+
+// Newton terms of block (a, b) of the fully implicit formulation: the derivatives of the element
+// residual through u* (advection velocity and SUPG / VMS test functions), tau_M(u*), tau_C(u*) and
+// the second r_M factor of the LES term, which the semi-implicit matrix assembled at the iterate
+// (u^EXT = u, p^EXT = p) leaves out; added to blk.  Returns in ext[i] this block's share
+// (X_ab U_b)_i of the right-hand side J U - R(U) = b(U) + X U.
+template <class R>
+__device__ void newton_block(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q, int64_t e, int le,
+                             int a, int b, const ElemShared<R> &sh, const ImplShared<R> &ix, R blk[16], R ext[4]) {
+  const R *ga = sh.gphi[le] + 3 * a;
+  const R *gb = sh.gphi[le] + 3 * b;
+  const R *Gr = ix.Gr[le];
+  const R *Gga = ix.Gga[le][a];
+  const R rho = Q.rho, w = sh.w[le];
+  const R divu = Gr[0] + Gr[4] + Gr[8];
+  const R z0 = cst<R>(0.0);
+  R Sal = z0, Dd = z0, Yc = z0, Mhk[9], Tv[3] = {z0, z0, z0}, Zb[3] = {z0, z0, z0}, Zp[3] = {z0, z0, z0};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Mhk[k] = z0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const R pa = (a == q) ? cst<R>(kQA) : cst<R>(kQB);
+    const R pb = (b == q) ? cst<R>(kQA) : cst<R>(kQB);
+    const R wpb = w * pb;
+    const R *r = ix.rq[le][q], *u = ix.uq[le][q], *kp = ix.kap[le][q];
+    const R tm = ix.tm[le][q], rt = rho * tm;
+    const R rga = fmadd(r[2], ga[2], fmadd(r[1], ga[1], r[0] * ga[0]));
+    const R adva = sh.adv[le][q][a];
+    R al = rho * pa;                                    // Galerkin (grad u) phi_b e_j
+    R h[3] = {z0, z0, z0};
+    if (P.stab >= 1) {
+      al = fmadd(rho * rt, adva, al);                   // SUPG: r_M's (grad u) part
+      const R c1 = -(ix.tcr[le][q] * divu), c2 = rho * adva;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        h[i] = fmadd(c1, ga[i], c2 * r[i]);              // tau_C(u*) and SUPG tau_M(u*)
+        Tv[i] = fmadd(wpb * rt, r[i], Tv[i]);            // SUPG test function (u* . grad) v
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Zp[j] = fmadd(wpb, fmadd(rt, Gga[j], kp[j] * rga), Zp[j]);   // PSPG
+    }
+    if (P.stab >= 2) {
+      al = al - rho * rt * tm * rga;                    // LES: r_M's (grad u) part
+      const R c3 = rho * rga, t2 = tm + tm;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        h[i] = fmadd(c3, u[i] - t2 * r[i], h[i]);       // VMS/LES tau_M(u*)
+        Zb[i] = fmadd(pb * rho, sh.wz[le][q][i], Zb[i]);   // VMS/LES: second factor's (grad u) part
+      }
+      const R gam = -(w * rt * tm * rga);
+      Dd = fmadd(wpb, rt * rga, fmadd(gam, sh.cb[le][q][b], Dd));   // VMS u* and LES r_M(u) identity parts
+      Yc += gam;
+    }
+    Sal = fmadd(wpb, al, Sal);
+    if (P.stab >= 1) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const R wh = wpb * h[i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Mhk[3 * i + j] = fmadd(wh, kp[j], Mhk[3 * i + j]);
+      }
+    }
+  }
+  // U at node b of the iterate, for the right-hand-side share
+  const int4 cn = A.conn[e];
+  const int nb = (b == 0) ? cn.x : ((b == 1) ? cn.y : ((b == 2) ? cn.z : cn.w));
+  R Ub[4];
+  ld_node<R>(A.xext, A.xext_hi, A.xext_lo, nb, Ub);
+  R ev[4] = {z0, z0, z0, z0};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R x = fmadd(Sal, Gr[3 * i + j], Mhk[3 * i + j]);
+      x = fmadd(Tv[i], ga[j], x);
+      x = fmadd(Zb[i], Gga[j], x);
+      if (i == j) x += Dd;
+      blk[4 * i + j] += x;
+      ev[i] = fmadd(x, Ub[j], ev[i]);
+    }
+    const R y = Yc * gb[i];
+    blk[4 * i + 3] += y;
+    ev[i] = fmadd(y, Ub[3], ev[i]);
+    blk[12 + i] += Zp[i];
+    ev[3] = fmadd(Zp[i], Ub[i], ev[3]);
+  }
+  const unsigned mask = 0xFu << (threadIdx.x & 28);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) ext[i] = quad_sum<R>(ev[i], mask);
+}
+
+template <class R, class S, bool IMPL>
 __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q, int64_t e, int le,
-                            int a, int b, const ElemShared<R> &sh, S *vals) {
+                            int a, int b, const ElemShared<R> &sh, const ImplShared<R> *ix, S *vals) {
   const R *ga = sh.gphi[le] + 3 * a;
   const R *gb = sh.gphi[le] + 3 * b;
   const R gab = fmadd(ga[2], gb[2], fmadd(ga[1], gb[1], ga[0] * gb[0]));
@@ -508,6 +689,11 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const Ph
       blk[12 + i] = wgb[i];
     }
     blk[15] = cst<R>(0.0);
+  }
+  if (IMPL) {
+    R ext[4];
+    newton_block<R>(A, P, Q, e, le, a, b, sh, *ix, blk, ext);
+    rhs += (i_rhs == 0) ? ext[0] : ((i_rhs == 1) ? ext[1] : ((i_rhs == 2) ? ext[2] : ext[3]));
   }
   const int32_t s = A.slot[e * 16 + 4 * a + b];
   const int4 cn = A.conn[e];
@@ -562,11 +748,14 @@ template <class R> struct MinCtas { static constexpr int value = 1; };
 #endif
 template <> struct MinCtas<dd> { static constexpr int value = LFX_ASM_DD_MIN_CTAS; };
 
-template <class R, class S>
-__global__ void __launch_bounds__(kCta, MinCtas<R>::value) assemble_color_kernel(AssembleArgs A, PhysParams P, PhysR<R> Q,
-                                                              int64_t e0, int64_t e1, S *vals) {
+template <class R, class S, bool IMPL>
+__global__ void __launch_bounds__(kCta, IMPL ? 1 : MinCtas<R>::value) assemble_color_kernel(AssembleArgs A, PhysParams P,
+                                                              PhysR<R> Q, int64_t e0, int64_t e1, S *vals) {
   pdl_entry();
-  __shared__ ElemShared<R> sh;
+  __shared__ AsmShared<R, IMPL> shm;
+  ElemShared<R> &sh = shm.e;
+  ImplShared<R> *ix = nullptr;
+  if constexpr (IMPL) ix = &shm.x;
   const int t = threadIdx.x;
   for (int64_t base = e0 + (int64_t)blockIdx.x * kElems; base < e1; base += (int64_t)gridDim.x * kElems) {
     if (has_geo<R>(A)) geom_load<R>(A, base, e1, A.n_elems, sh);
@@ -574,15 +763,15 @@ __global__ void __launch_bounds__(kCta, MinCtas<R>::value) assemble_color_kernel
     __syncthreads();
     const int le = t >> 2, q = t & 3;
     const bool live = base + le < e1;
-    if (live) qp_phase<R>(A, P, Q, base + le, q, le, sh);
+    if (live) qp_phase<R, IMPL>(A, P, Q, base + le, q, le, sh, ix);
     __syncthreads();
-    if (live) node_phase<R>(P, Q, q, le, sh);
+    if (live) node_phase<R, IMPL>(P, Q, q, le, sh, ix);
     __syncthreads();
 #pragma unroll 1
     for (int pass = 0; pass < kElems * 16 / kCta; ++pass) {
       const int le2 = pass * (kCta / 16) + (t >> 4);
       const int64_t e = base + le2;
-      if (e < e1) block_phase<R, S>(A, P, Q, e, le2, (t >> 2) & 3, t & 3, sh, vals);
+      if (e < e1) block_phase<R, S, IMPL>(A, P, Q, e, le2, (t >> 2) & 3, t & 3, sh, ix, vals);
     }
     __syncthreads();
   }
@@ -861,14 +1050,17 @@ lfx_status launch_comp_normalize_dd(cudaStream_t st, int64_t V, int n_comp, cons
 
 template <class R, class S>
 lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysParams &P,
-                           const int32_t *color_off, int n_colors, S *vals) {
+                           const int32_t *color_off, int n_colors, S *vals, bool newton) {
   const PhysR<R> Q = phys_r<R>(P);
   for (int c = 0; c < n_colors; ++c) {
     const int64_t e0 = color_off[c], e1 = color_off[c + 1];
     if (e1 <= e0) continue;
     int64_t chunks = (e1 - e0 + kElems - 1) / kElems;
     int grid = (int)(chunks < 152 * 8 ? chunks : 152 * 8);
-    pdl_launch(assemble_color_kernel<R, S>, grid, kCta, 0, st, A, P, Q, e0, e1, vals);
+    if (newton)
+      pdl_launch(assemble_color_kernel<R, S, true>, grid, kCta, 0, st, A, P, Q, e0, e1, vals);
+    else
+      pdl_launch(assemble_color_kernel<R, S, false>, grid, kCta, 0, st, A, P, Q, e0, e1, vals);
     note_launches(1);
   }
   LFX_CUDA_TRY(cudaGetLastError());
@@ -966,7 +1158,7 @@ int64_t assemble_wave_elements() {
       cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) {
     sms = v;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, assemble_color_kernel<dd, float>, kCta, 0) == cudaSuccess &&
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, assemble_color_kernel<dd, float, false>, kCta, 0) == cudaSuccess &&
         b > 0)
       per_sm = b;
   }
@@ -987,11 +1179,9 @@ template lfx_status launch_geometry<double>(cudaStream_t, const AssembleArgs &, 
 template lfx_status launch_geometry<dd>(cudaStream_t, const AssembleArgs &, int64_t, double *, float *, float *);
 
 template lfx_status launch_assemble<double, double>(cudaStream_t, const AssembleArgs &, const PhysParams &,
-                                                    const int32_t *, int, double *);
-template lfx_status launch_assemble<float, float>(cudaStream_t, const AssembleArgs &, const PhysParams &,
-                                                  const int32_t *, int, float *);
+                                                    const int32_t *, int, double *, bool);
 template lfx_status launch_assemble<dd, float>(cudaStream_t, const AssembleArgs &, const PhysParams &,
-                                               const int32_t *, int, float *);
+                                               const int32_t *, int, float *, bool);
 
 lfx_status launch_dirichlet_values(cudaStream_t st, int64_t nd, int H, const int32_t *bc_of,
                                    const double *S, const DirCoef &C, const double *N, int nb, D4 *g) {

@@ -42,6 +42,8 @@ struct AssembleArgs {
   // double-float kernel: geo_hi + geo_lo.  Null: the kernel computes the geometry itself.
   const double *geo64;
   const float *geo_hi, *geo_lo;
+  // moving mesh: u_ALE at the nodes (the advection velocity is u* = u^EXT - u_ALE); null: fixed mesh
+  const D4 *uale;
 };
 constexpr int kGeoValues = 23;
 
@@ -82,9 +84,11 @@ lfx_status launch_node_gather(cudaStream_t st, int64_t V, const int32_t *node_ol
 lfx_status launch_backflow(cudaStream_t st, int64_t n_edges, const int32_t *ij, const double *an, const double *coef,
                            const int32_t *slot4, const D4 *xext, int64_t n_blocks, const int32_t *blk, double *acc,
                            double *vals64, float *hi, float *lo);
+// newton: the Jacobian of the fully implicit formulation at the iterate held in A.xext (the
+// semi-implicit system assembled there plus the Newton terms) and the right-hand side J U - R(U)
 template <class R, class S>
 lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysParams &P,
-                           const int32_t *color_off, int n_colors, S *vals);
+                           const int32_t *color_off, int n_colors, S *vals, bool newton = false);
 lfx_status launch_dirichlet_values(cudaStream_t st, int64_t nd, int H, const int32_t *bc_of,
                                    const double *S, const DirCoef &C, const double *N, int nb, D4 *g);
 lfx_status launch_neumann(cudaStream_t st, int64_t n, const int32_t *node, const int32_t *bc_of,
@@ -130,5 +134,43 @@ lfx_status launch_spmv(cudaStream_t st, const BsrView<S> &A, const T *x, const T
 template <>
 lfx_status launch_spmv<DDMat, double>(cudaStream_t st, const BsrView<DDMat> &A, const double *x, const double *b,
                                       double *y, int mode, double *part, int *n_part);
+
+// ------------------------------------------------------------------ moving domains (ale.cu)
+// The lifting problem (Eq. lifting): the P1 Laplacian K of the reference mesh over the block pattern
+// (one FP64 value per block) and its work arrays for conjugate gradients with Jacobi scaling.
+struct LiftingView {
+  int64_t V;
+  const int32_t *rowptr, *col;
+  const double *K, *dinv;
+  uint8_t *fixed;          // [V] 1 where the displacement is prescribed
+  D4 *r, *z, *p, *Ap;      // [V]
+  double *part;            // lifting_part_entries(V)
+  void *cg_state;          // lifting_cg_state_bytes()
+};
+lfx_status launch_lifting_matrix(cudaStream_t st, int64_t T, int64_t V, int64_t nnzb, const int32_t *slot,
+                                 const int32_t *diag, const double *geo64, const float *geo_hi, const float *geo_lo,
+                                 double *K, double *dinv);
+// d = harmonic extension: d = fixed_val at fixed_node, K d = 0 on the other nodes (zero normal
+// flux on the free boundary), from the initial guess in d; stops at ||r||_{D^-1} <= rtol of the
+// initial residual for each component (synchronises st every 16 iterations).
+lfx_status lifting_solve(cudaStream_t st, const LiftingView &L, int64_t n_fixed, const int32_t *fixed_node,
+                         const D4 *fixed_val, D4 *d, double rtol, int max_iters, int *iters_out);
+size_t lifting_cg_state_bytes();
+int lifting_part_entries(int64_t V);
+// x = ref + d, and its double-float split when hi is non-null
+lfx_status launch_move_nodes(cudaStream_t st, int64_t V, const D4 *ref, const D4 *d, D4 *x, float4 *hi, float4 *lo);
+// u_ALE = (alpha d^{n+1} - sum_j beta_j d^{n-j}) / dt (Section 2.3)
+lfx_status launch_mesh_velocity(cudaStream_t st, int64_t V, int order, const D4 *dn1, const D4 *d0, const D4 *d1,
+                                const D4 *d2, double alpha, const double beta[3], double dt, D4 *u);
+// Neumann loads -(h n, v) of the listed faces (internal numbering, h = C.c[face_bc]) at coordinates x
+lfx_status launch_neumann_faces(cudaStream_t st, int64_t nf, const int32_t *faces, const int32_t *face_bc,
+                                const DirCoef &C, const D4 *x, double *rhs);
+
+// Per-CTA partial sums of v.v (n values) into part[*n_part]; part needs
+// norm_partials_capacity(V) entries for vectors of up to 4 V values or a residual SpMV of V rows.
+lfx_status launch_norm_partials(cudaStream_t st, const double *v, int64_t n, double *part, int *n_part);
+int norm_partials_capacity(int64_t V);
+// x [V][4] FP64 split into FP32 high and low parts (x = hi + lo)
+lfx_status launch_split_vec(cudaStream_t st, int64_t V, const double *x, float4 *hi, float4 *lo);
 
 }  // namespace lfx

@@ -36,18 +36,25 @@ void clear_error();
 void note_launches(int64_t n);
 
 // ---------------------------------------------------------------- device memory
-void *dalloc(size_t bytes);          // nullptr on failure (error message set)
-void dfree(void *p);
+// Every allocation remembers the free function of the allocator that made it (lfx_set_allocator
+// may switch allocators while buffers made by the previous one are still alive).
+struct DFree {
+  lfx_free_fn fn = nullptr;   // null: cudaFree
+  void *ctx = nullptr;
+};
+void *dalloc(size_t bytes, DFree *how);   // nullptr on failure (error message set)
+void dfree(void *p, const DFree &how);
 
 // A device buffer that frees itself; tracks its size for admission control.
 struct DBuf {
   void *p = nullptr;
   size_t bytes = 0;
   bool owned = true;   // false: a slice of memory owned elsewhere (never freed here)
+  DFree how;           // how to free p
   DBuf() = default;
   DBuf(const DBuf &) = delete;
   DBuf &operator=(const DBuf &) = delete;
-  DBuf(DBuf &&o) noexcept : p(o.p), bytes(o.bytes), owned(o.owned) {
+  DBuf(DBuf &&o) noexcept : p(o.p), bytes(o.bytes), owned(o.owned), how(o.how) {
     o.p = nullptr;
     o.bytes = 0;
   }
@@ -57,6 +64,7 @@ struct DBuf {
       p = o.p;
       bytes = o.bytes;
       owned = o.owned;
+      how = o.how;
       o.p = nullptr;
       o.bytes = 0;
     }
@@ -64,7 +72,7 @@ struct DBuf {
   }
   ~DBuf() { release(); }
   void release() {
-    if (p && owned) dfree(p);
+    if (p && owned) dfree(p, how);
     p = nullptr;
     bytes = 0;
     owned = true;
@@ -78,7 +86,7 @@ struct DBuf {
   lfx_status alloc(size_t n) {
     release();
     if (n == 0) n = 16;
-    p = dalloc(n);
+    p = dalloc(n, &how);
     if (!p) return LFX_ERR_OOM;
     bytes = n;
     return LFX_OK;

@@ -1,14 +1,15 @@
 // lfx_asimple_apply_noalloc: the aSIMPLE preconditioner application (the same kernels as the
 // step's preconditioner) for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at the point where they need the preconditioner: code
-// running while a CUDA graph is being captured (allocation is not allowed inside a capture),
-// solvers embedded in a host framework that owns all device memory through its own pool, or
-// time-critical loops that must not pay an allocation's latency or risk its failure midway.
+// Some callers cannot call cudaMalloc at the point where they need the preconditioner: solvers
+// embedded in a host framework that owns all device memory through its own pool (a second
+// allocator would compete with it for the same HBM), and time-critical loops that must not pay an
+// allocation's latency (cudaMalloc may synchronise the whole device) or risk its failure midway.
 // This entry point takes the caller's matrix and vectors and keeps every intermediate array
 // (inverse diagonals, Chebyshev iterates, coefficients, reduction partials) in one file-scope
 // static device array of fixed size, which exists on every GPU that loads the library until
 // the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -25,10 +26,47 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_asimple_scratch[kNoAllocScratchBytes];
 
 std::mutex g_scratch_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
+// the array's device address per device, with the id of the context it was looked up in: a
+// device reset (or any teardown and re-creation of the context) may load the module again at
+// another address, so a lookup is only reused within the same context
+struct ScratchAddr {
+  void *ptr = nullptr;
+  unsigned long long ctx_id = 0;
+  bool valid = false;
+};
+ScratchAddr g_scratch[kMaxDevices];
 
-// Device address of the static array on the current device, looked up once per device.  The
-// array's name in host code is only a host-side stand-in, never a device address.
+// Id of the calling thread's current context (driver entry points resolved through the runtime,
+// so that the library needs no link to the driver library); false if there is none or the
+// driver does not offer the calls.
+bool current_context_id(unsigned long long *id) {
+  typedef CUresult (*GetCurrentFn)(CUcontext *);
+  typedef CUresult (*GetIdFn)(CUcontext, unsigned long long *);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetIdFn)f;
+    (void)cudaGetLastError();
+  });
+  if (!get_current || !get_id) return false;
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS || !c) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Device address of the static array on the current device: looked up with cudaGetSymbolAddress
+// once per device and context (the first call on a device, and the first after its context was
+// reset), with that device current.  The array's name in host code is only a host-side stand-in,
+// never a device address.
 lfx_status scratch_address(void **out) {
   int dev = 0;
   LFX_CUDA_TRY(cudaGetDevice(&dev));
@@ -36,13 +74,21 @@ lfx_status scratch_address(void **out) {
     lfx::set_error("lfx_asimple_apply_noalloc: device index %d out of range", dev);
     return LFX_ERR_INVALID_ARG;
   }
+  unsigned long long id = 0;
+  bool have_id = current_context_id(&id);
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    LFX_CUDA_TRY(cudaGetSymbolAddress(&p, g_asimple_scratch));
-    g_scratch_ptr[dev] = p;
+  ScratchAddr &c = g_scratch[dev];
+  if (have_id && c.valid && c.ctx_id == id) {
+    *out = c.ptr;
+    return LFX_OK;
   }
-  *out = g_scratch_ptr[dev];
+  void *p = nullptr;
+  LFX_CUDA_TRY(cudaGetSymbolAddress(&p, g_asimple_scratch));
+  if (!have_id) have_id = current_context_id(&id);   // the lookup may have made the context current
+  c.ptr = p;
+  c.ctx_id = id;
+  c.valid = have_id;                                 // without a context id: look it up every call
+  *out = p;
   return LFX_OK;
 }
 

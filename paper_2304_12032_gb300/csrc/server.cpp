@@ -16,6 +16,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -62,35 +63,81 @@ struct lfx_server {
 // Problem-side facts the estimate needs (defined in api.cu).
 int64_t lfx_internal_state_bytes_estimate(const lfx_problem *pb, int64_t *V, int *sigma);
 
-static void admit_locked(lfx_server *sv) {
-  while (!sv->waiting.empty()) {
-    Request *r = sv->waiting.front();
-    if (sv->used + r->bytes > sv->budget) break;
-    sv->waiting.pop_front();
+// Admission.  Under the lock, the waiting requests that fit the budget leave the queue in FIFO
+// order with their bytes reserved; their states and streams are then created without the lock
+// (state creation allocates and uploads, and cudaMalloc may synchronise the device), so workers
+// keep stepping meanwhile; finally, under the lock again, each goes to the ready queue or, if its
+// creation failed, finishes with the error and gives its bytes back (which may admit more).
+// The caller's current device is restored before returning.
+static void admit(lfx_server *sv) {
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  for (;;) {
+    std::vector<Request *> take;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      while (!sv->waiting.empty()) {
+        Request *r = sv->waiting.front();
+        if (sv->used + r->bytes > sv->budget) break;
+        sv->waiting.pop_front();
+        sv->used += r->bytes;
+        take.push_back(r);
+      }
+    }
+    if (take.empty()) break;
     cudaSetDevice(sv->device);
-    lfx_state *st = nullptr;
-    lfx_status rc = lfx_state_create(r->pb, r->u_hist.data(), r->p_hist.data(), r->t0, &st);
-    if (rc == LFX_OK) {
-      if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) == cudaSuccess)
-        rc = lfx_set_stream(st, r->stream);
-      else
-        rc = LFX_ERR_CUDA;
+    struct Made {
+      lfx_state *st = nullptr;
+      cudaStream_t stream = nullptr;
+      lfx_status rc = LFX_OK;
+      std::string err;
+    };
+    std::vector<Made> made(take.size());
+    for (size_t i = 0; i < take.size(); ++i) {
+      Request *r = take[i];
+      Made &m = made[i];
+      m.rc = lfx_state_create(r->pb, r->u_hist.data(), r->p_hist.data(), r->t0, &m.st);
+      if (m.rc == LFX_OK) {
+        if (cudaStreamCreateWithFlags(&m.stream, cudaStreamNonBlocking) == cudaSuccess)
+          m.rc = lfx_set_stream(m.st, m.stream);
+        else
+          m.rc = LFX_ERR_CUDA;
+      }
+      if (m.rc != LFX_OK) {
+        m.err = lfx_last_error();
+        if (m.st) lfx_state_destroy(m.st);
+        if (m.stream) cudaStreamDestroy(m.stream);
+        m.st = nullptr;
+        m.stream = nullptr;
+      }
     }
-    if (rc != LFX_OK) {
-      r->status = rc;
-      r->error = lfx_last_error();
-      r->finished = true;
-      if (st) lfx_state_destroy(st);
-      continue;
+    bool freed = false;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      for (size_t i = 0; i < take.size(); ++i) {
+        Request *r = take[i];
+        const Made &m = made[i];
+        if (m.rc != LFX_OK) {
+          r->status = m.rc;
+          r->error = m.err;
+          r->finished = true;
+          sv->used -= r->bytes;
+          freed = true;
+          continue;
+        }
+        r->st = m.st;
+        r->stream = m.stream;
+        r->admitted = true;
+        sv->admitted_total += 1;
+        sv->active += 1;
+        if (sv->active > sv->max_active) sv->max_active = sv->active;
+        sv->ready.push_back(r);
+      }
     }
-    r->st = st;
-    r->admitted = true;
-    sv->used += r->bytes;
-    sv->admitted_total += 1;
-    sv->active += 1;
-    if (sv->active > sv->max_active) sv->max_active = sv->active;
-    sv->ready.push_back(r);
+    sv->cv.notify_all();
+    if (!freed) break;
   }
+  if (prev >= 0) cudaSetDevice(prev);
 }
 
 static void worker_loop(lfx_server *sv) {
@@ -145,8 +192,8 @@ static void worker_loop(lfx_server *sv) {
       r->finished = true;
       sv->used -= r->bytes;
       sv->active -= 1;
-      admit_locked(sv);
     }
+    admit(sv);
     sv->cv.notify_all();
   }
 }
@@ -194,8 +241,8 @@ lfx_status lfx_server_submit(lfx_server *sv, lfx_problem *pb, const double *u_hi
     *ticket = r->ticket;
     sv->waiting.push_back(r.get());
     sv->all[r->ticket] = std::move(r);
-    admit_locked(sv);
   }
+  admit(sv);
   sv->cv.notify_all();
   return LFX_OK;
 }
@@ -258,6 +305,50 @@ lfx_status lfx_server_stats(lfx_server *sv, float *latency_ms, int64_t capacity,
   if (n_waiting) *n_waiting = (int64_t)sv->waiting.size();
   if (max_active) *max_active = sv->max_active;
   return LFX_OK;
+}
+
+lfx_status lfx_batch_step(lfx_state *const *states, int32_t n, lfx_step_stats *stats) {
+  clear_error();
+  if (n < 0 || (n > 0 && !states)) {
+    set_error("lfx_batch_step: invalid argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    if (!states[i]) {
+      set_error("lfx_batch_step: state %d is NULL", i);
+      return LFX_ERR_INVALID_ARG;
+    }
+    for (int32_t j = 0; j < i; ++j)
+      if (states[j] == states[i]) {
+        set_error("lfx_batch_step: state %d appears twice", i);
+        return LFX_ERR_INVALID_ARG;
+      }
+  }
+  if (n == 0) return LFX_OK;
+  int dev = 0;
+  LFX_CUDA_TRY(cudaGetDevice(&dev));
+  std::vector<lfx_status> rc((size_t)n, LFX_OK);
+  std::vector<std::string> err((size_t)n);
+  // one host thread per state: each state's step runs on its own stream, so the kernels of the n
+  // simulations overlap on the device while every thread waits only for its own solver's flags
+  std::vector<std::thread> th;
+  th.reserve((size_t)n);
+  for (int32_t i = 0; i < n; ++i)
+    th.emplace_back([&, i] {
+      cudaSetDevice(dev);
+      rc[i] = lfx_step(states[i], stats ? stats + i : nullptr);
+      if (rc[i] != LFX_OK) err[i] = lfx_last_error();
+    });
+  for (auto &t : th) t.join();
+  lfx_status out = LFX_OK;
+  for (int32_t i = 0; i < n; ++i) {
+    if (rc[i] == LFX_OK) continue;
+    if (out == LFX_OK || (out == LFX_ERR_NOT_CONVERGED && rc[i] != LFX_ERR_NOT_CONVERGED)) {
+      out = rc[i];
+      set_error("lfx_batch_step: state %d: %s", i, err[i].c_str());
+    }
+  }
+  return out;
 }
 
 void lfx_server_destroy(lfx_server *sv) {

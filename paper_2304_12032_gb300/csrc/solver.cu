@@ -2043,6 +2043,23 @@ lfx_status launch_spmv<DDMat, double>(cudaStream_t st, const BsrView<DDMat> &A, 
   return LFX_OK;
 }
 
+lfx_status launch_norm_partials(cudaStream_t st, const double *v, int64_t n, double *part, int *n_part) {
+  const int g = vec_grid(n);
+  pdl_launch(norm_kernel<double>, g, kThreads, 0, st, v, n, part);
+  note_launches(1);
+  if (n_part) *n_part = g;
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+int norm_partials_capacity(int64_t V) { return std::max(rows_grid(V), vec_grid(4 * V)) + 64; }
+
+lfx_status launch_split_vec(cudaStream_t st, int64_t V, const double *x, float4 *hi, float4 *lo) {
+  pdl_launch(split_vec_kernel, vec_grid(V), kThreads, 0, st, V, x, hi, lo, nullptr);
+  note_launches(1);
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
 // The Arnoldi product w = A z_j (kernels return at once when the cycle has finished)
 template <class S, class T>
 static void arnoldi_spmv(cudaStream_t st, const BsrView<S> &A, const T *x, T *y, const KState *ks) {
@@ -2243,18 +2260,9 @@ lfx_status ASimple<S, T>::apply_view(cudaStream_t st, const View &A, const T *r,
     CsrV<T> R0{L0.nnext, L0.Rrp.as<int32_t>(), L0.Rci.as<int32_t>(), L0.Rv.as<T>()};
     pdl_launch(csr_spmv_kernel<T, 32>, (int)((L0.nnext * 32 + kThreads - 1) / kThreads), kThreads, 0, st, 
         R0, rr0.as<T>(), 1, 0, amg[1].b.as<T>(), 1, 0, 1.0, 0, ks);
-    if (coop_grid > 0) {
-      const CoarseArgs<T> *ca = coarse_args.as<CoarseArgs<T>>();
-      void *kargs[] = {(void *)&ca, (void *)&ks};
-      LFX_CUDA_TRY(cudaLaunchCooperativeKernel((void *)amg_coarse_kernel<T>, dim3(coop_grid), dim3(kThreads), kargs,
-                                               0, st));
-      note_launches(1);
-    } else {
-      LFX_TRY(vcycle(st, 1, ks));
-    }
+    LFX_TRY(coarse_cycle(st, ks));
     CsrV<T> P0{V, L0.Prp.as<int32_t>(), L0.Pci.as<int32_t>(), L0.Pv.as<T>()};
-    // the level-1 iterate is in d1 when the coarse launch fused its last smoothing step
-    const T *x1 = (amg.size() > 2 && coop_grid > 0 && cfg.s_steps == 1) ? amg[1].d1.as<T>() : amg[1].x.as<T>();
+    const T *x1 = coarse_x();
     pdl_launch(csr_spmv_kernel<T, 8>, lanes_grid(V, 8), kThreads, 0, st, P0, x1, 1, 0, X.as<T>(), 4, 3,
                                                             amg_alpha, 1, ks);
     // post-smoothing from the corrected iterate
@@ -2336,6 +2344,7 @@ lfx_status ASimple<S, T>::upload_amg(const AmgHost &H) {
       LFX_TRY(upload_vec(D.Rrp, H.R[l].rp));
       LFX_TRY(upload_vec(D.Rci, H.R[l].ci));
       LFX_TRY(upload_as<T>(D.Rv, H.R[l].v));
+      D.lam = H.lam[l];
       cheb_coefs(H.lam[l], cfg.s_ratio, cfg.s_steps, D.init, D.c1, D.c2);
     }
     if (l >= 1) {
@@ -2437,6 +2446,25 @@ lfx_status ASimple<S, T>::apply(cudaStream_t st, const BsrView<S> &A, const T *r
     return apply_view(st, sv, r, z, ks);
   }
   return apply_view(st, A, r, z, ks);
+}
+
+template <class S, class T>
+lfx_status ASimple<S, T>::coarse_cycle(cudaStream_t st, const KState *ks) {
+  if (coop_grid > 0) {
+    const CoarseArgs<T> *ca = coarse_args.as<CoarseArgs<T>>();
+    void *kargs[] = {(void *)&ca, (void *)&ks};
+    LFX_CUDA_TRY(cudaLaunchCooperativeKernel((void *)amg_coarse_kernel<T>, dim3(coop_grid), dim3(kThreads), kargs,
+                                             0, st));
+    note_launches(1);
+    return LFX_OK;
+  }
+  return vcycle(st, 1, ks);
+}
+
+// the level-1 iterate is in d1 when the coarse launch fused its last smoothing step
+template <class S, class T>
+const T *ASimple<S, T>::coarse_x() const {
+  return (amg.size() > 2 && coop_grid > 0 && cfg.s_steps == 1) ? amg[1].d1.as<T>() : amg[1].x.as<T>();
 }
 
 template <class S, class T>

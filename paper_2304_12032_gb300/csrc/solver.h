@@ -82,6 +82,7 @@ struct AmgDevLevel {
   DBuf Prp, Pci, Pv;             // P_l: n_l x n_{l+1}
   DBuf Rrp, Rci, Rv;             // R_l = P_l^T
   DBuf x, b, r, d0, d1, rr;      // work vectors (l >= 1)
+  double lam = 0.0;              // Gershgorin bound of lambda_max(D^-1 A_l) (l < L-1)
   double init = 0.0;             // Chebyshev coefficients of this level (host-computed)
   double c1[kMaxSmooth] = {}, c2[kMaxSmooth] = {};
 };
@@ -104,6 +105,10 @@ struct ASimple {
   double amg_alpha = 1.0;
   lfx_status upload_amg(const AmgHost &H);
   lfx_status vcycle(cudaStream_t st, int l, const KState *ks);
+  // The V-cycle below level 0 (levels 1 .. L-1) for amg[1].b: one cooperative launch, or the
+  // level-by-level launches; its result is at coarse_x().
+  lfx_status coarse_cycle(cudaStream_t st, const KState *ks);
+  const T *coarse_x() const;
   size_t amg_bytes() const;
   lfx_status init(int64_t V, const SmootherConfig &cfg);
   // Work arrays carved from caller-provided device memory (no allocation); zeroed on st.

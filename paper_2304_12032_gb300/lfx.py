@@ -63,7 +63,9 @@ class lfx_options(ctypes.Structure):
                 ("amg_refresh", ctypes.c_int32), ("amg_coarse_size", ctypes.c_int32),
                 ("amg_theta", ctypes.c_double), ("amg_alpha", ctypes.c_double),
                 ("batch_normalize", ctypes.c_int32), ("batch_segmented", ctypes.c_int32),
-                ("inner_adaptive", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("inner_adaptive", ctypes.c_int32), ("implicit", ctypes.c_int32),
+                ("newton_max_iters", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("newton_rtol", ctypes.c_double)]
 
 
 class lfx_mesh_info(ctypes.Structure):
@@ -78,7 +80,8 @@ class lfx_step_stats(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("t", ctypes.c_double), ("ms_assembly", ctypes.c_float),
                 ("ms_solve", ctypes.c_float), ("ms_total", ctypes.c_float), ("converged", ctypes.c_int32),
                 ("ms_assembly_kernels", ctypes.c_float), ("n_assembly_launches", ctypes.c_int32),
-                ("ms_spmv", ctypes.c_float), ("n_spmv", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("ms_spmv", ctypes.c_float), ("n_spmv", ctypes.c_int32), ("newton_iterations", ctypes.c_int32),
+                ("ms_newton_assembly", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -113,9 +116,14 @@ _SIGS = {
     "lfx_set_pressure_pin": ([_P, ctypes.c_double], ctypes.c_int32),
     "lfx_step": ([_P, ctypes.POINTER(lfx_step_stats)], ctypes.c_int32),
     "lfx_state_get": ([_P, _DP, _DP], ctypes.c_int32),
+    "lfx_state_newton_residuals": ([_P, _DP, ctypes.c_int32, _IP], ctypes.c_int32),
+    "lfx_state_set_displacement": ([_P, _DP], ctypes.c_int32),
+    "lfx_set_boundary_displacement": ([_P, ctypes.c_int64, _IP, _DP], ctypes.c_int32),
+    "lfx_state_get_displacement": ([_P, _DP, _IP], ctypes.c_int32),
     "lfx_state_set": ([_P, _DP, _DP, ctypes.c_double], ctypes.c_int32),
     "lfx_debug_assemble": ([_P, ctypes.c_int32, _DP, _DP], ctypes.c_int32),
     "lfx_debug_spmv": ([_P, _DP, _DP], ctypes.c_int32),
+    "lfx_debug_assemble_newton": ([_P, _DP, _DP, _DP], ctypes.c_int32),
     "lfx_debug_precond": ([_P, _DP, _DP, _DP, _DP], ctypes.c_int32),
     "lfx_debug_solve": ([_P, _DP, ctypes.POINTER(lfx_step_stats)], ctypes.c_int32),
     "lfx_set_allocator": ([ALLOC_FN, FREE_FN, _P], ctypes.c_int32),
@@ -126,9 +134,12 @@ _SIGS = {
     "lfx_server_result": ([_P, ctypes.c_int64, _DP, _DP], ctypes.c_int32),
     "lfx_server_stats": ([_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, _LP, _LP, _LP, _LP], ctypes.c_int32),
     "lfx_server_destroy": ([_P], None),
+    "lfx_batch_step": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(lfx_step_stats)], ctypes.c_int32),
     "lfx_asimple_apply_noalloc": ([ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(lfx_options), _P],
                                   ctypes.c_int32),
     "lfx_state_device_bytes": ([_P, _LP], ctypes.c_int32),
+    "lfx_debug_amg_level": ([_P, ctypes.c_int32, _LP, _IP, _IP, _DP, _IP, _IP, _DP, _DP], ctypes.c_int32),
+    "lfx_debug_amg_vcycle": ([_P, _DP, _DP], ctypes.c_int32),
     "lfx_state_amg_levels": ([_P, _IP, _LP, _LP, ctypes.c_int32], ctypes.c_int32),
 }
 
@@ -382,6 +393,31 @@ class State:
         _check(library().lfx_state_get(self.h, _d(u), _d(p)))
         return u, p
 
+    def set_displacement(self, d_hist):
+        """Moving mesh: displacement levels d^n, d^{n-1}, ... ([bdf_order][V][3])."""
+        d = np.ascontiguousarray(np.asarray(d_hist, dtype=np.float64).reshape(self.problem.bdf_order, self.V, 3))
+        _check(library().lfx_state_set_displacement(self.h, _d(d)))
+
+    def set_boundary_displacement(self, nodes, d):
+        """The next step's displacement d [n][3] at the listed nodes (the lifting extends it)."""
+        nodes = np.ascontiguousarray(nodes, dtype=np.int32)
+        d = np.ascontiguousarray(np.asarray(d, dtype=np.float64).reshape(nodes.size, 3))
+        _check(library().lfx_set_boundary_displacement(self.h, nodes.size, _i(nodes), _d(d)))
+
+    def get_displacement(self):
+        """(d [V][3] of the current time level, CG iterations of the last lifting)."""
+        d = np.zeros((self.V, 3))
+        it = ctypes.c_int32()
+        _check(library().lfx_state_get_displacement(self.h, _d(d), ctypes.byref(it)))
+        return d, it.value
+
+    def newton_residuals(self):
+        """||R(U_k)|| / ||b|| of the last step's Newton iterates (empty for semi-implicit steps)."""
+        n = ctypes.c_int32()
+        out = np.zeros(64)
+        _check(library().lfx_state_newton_residuals(self.h, _d(out), 64, ctypes.byref(n)))
+        return out[:min(n.value, 64)].copy()
+
     def device_bytes(self) -> int:
         b = ctypes.c_int64()
         _check(library().lfx_state_device_bytes(self.h, ctypes.byref(b)))
@@ -404,6 +440,16 @@ class State:
         _check(library().lfx_debug_assemble(self.h, int(apply_bcs), _d(blocks), _d(rhs)))
         return blocks, rhs
 
+    def debug_assemble_newton(self, U):
+        """Jacobian blocks [nnzb,4,4] and right-hand side J U - R(U) [V,4] of the fully implicit
+        formulation at the iterate U [V,4] (no Dirichlet rows)."""
+        U = np.ascontiguousarray(U, dtype=np.float64).reshape(self.V, 4)
+        nnzb = self.problem.mesh.info()["nnz_blocks"]
+        blocks = np.zeros((nnzb, 4, 4))
+        rhs = np.zeros((self.V, 4))
+        _check(library().lfx_debug_assemble_newton(self.h, _d(U), _d(blocks), _d(rhs)))
+        return blocks, rhs
+
     def debug_spmv(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.V, 4)
         y = np.zeros((self.V, 4))
@@ -416,6 +462,32 @@ class State:
         lf, ls = ctypes.c_double(), ctypes.c_double()
         _check(library().lfx_debug_precond(self.h, _d(r), _d(z), ctypes.byref(lf), ctypes.byref(ls)))
         return z, lf.value, ls.value
+
+    def debug_amg_level(self, level):
+        """Level `level` of the device Schur AMG hierarchy (FP64 path): dict with n, A (scipy CSR,
+        None at level 0 and at the coarsest level), P (scipy CSR n_l x n_{l+1}, None at the coarsest)
+        and lam (Gershgorin bound of lambda_max(D^-1 A_l))."""
+        import scipy.sparse as sp
+
+        lib = library()
+        sz = np.zeros(4, dtype=np.int64)
+        lam = ctypes.c_double()
+        _check(lib.lfx_debug_amg_level(self.h, int(level), sz.ctypes.data_as(_LP), None, None, None, None, None,
+                                       None, ctypes.byref(lam)))
+        n, nnz_a, nn, nnz_p = (int(v) for v in sz)
+        arp, aci, av = np.zeros(n + 1, np.int32), np.zeros(max(nnz_a, 1), np.int32), np.zeros(max(nnz_a, 1))
+        prp, pci, pv = np.zeros(n + 1, np.int32), np.zeros(max(nnz_p, 1), np.int32), np.zeros(max(nnz_p, 1))
+        _check(lib.lfx_debug_amg_level(self.h, int(level), sz.ctypes.data_as(_LP), _i(arp), _i(aci), _d(av), _i(prp),
+                                       _i(pci), _d(pv), ctypes.byref(lam)))
+        A = sp.csr_matrix((av[:nnz_a], aci[:nnz_a], arp), shape=(n, n)) if nnz_a else None
+        P = sp.csr_matrix((pv[:nnz_p], pci[:nnz_p], prp), shape=(n, nn)) if nnz_p else None
+        return {"n": n, "A": A, "P": P, "lam": lam.value}
+
+    def debug_amg_vcycle(self, b1):
+        b1 = np.ascontiguousarray(b1, dtype=np.float64)
+        x1 = np.zeros_like(b1)
+        _check(library().lfx_debug_amg_vcycle(self.h, _d(b1), _d(x1)))
+        return x1
 
     def debug_solve(self, allow_not_converged=False):
         x = np.zeros((self.V, 4))
@@ -475,6 +547,16 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def batch_step(states: Sequence[State], allow_not_converged=False):
+    """lfx_batch_step: one step of every state, concurrently (each state on its own stream)."""
+    n = len(states)
+    arr = (_P * max(n, 1))(*[s.h for s in states])
+    stats = (lfx_step_stats * max(n, 1))()
+    rc = library().lfx_batch_step(arr, n, stats)
+    _check(rc, allow=(LFX_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return [stats[i].as_dict() for i in range(n)]
 
 
 def problem_state_bytes(problem: Problem) -> int:

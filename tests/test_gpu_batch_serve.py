@@ -126,3 +126,40 @@ def test_server_admits_by_budget_and_results_match_solo():
         assert np.allclose(u, u1, rtol=0, atol=1e-12 * np.abs(u1).max())
         assert np.allclose(p, p1, rtol=0, atol=1e-12 * np.abs(p1).max())
     srv.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_step_of_independent_states_equals_solo_steps(precision):
+    """lfx_batch_step: independent states on their own streams stepped concurrently (one host
+    thread each) give exactly their solo results (no reduction is shared between states)."""
+    import torch
+
+    from paper_2304_12032_gb300 import build as B
+
+    B.build()
+    from paper_2304_12032_gb300 import lfx as L
+
+    extra = dict(precision="mixed", smoother_bf16=1) if precision == "mixed" else {}
+    ms = _members()
+    probs, hists = [], []
+    for i, m in enumerate(ms):
+        mesh = L.Mesh.from_synthetic(m)
+        bcs = [L.BC(tag=b["tag"], kind=b["kind"], profile=b.get("profile", "uniform"), time=b.get("time", "constant"),
+                    p=b.get("p", (0.0,)), radius=b.get("radius", 1.0)) for b in _bcs(0, m, 0)]
+        probs.append(L.Problem(mesh, RHO, MU, DT, 2, bcs, [], L.default_options(gmres_rtol=1e-10, **extra)))
+        hists.append(_hist(m, 50 + i))
+    solo = []
+    for p, (uh, ph) in zip(probs, hists):
+        st = L.State(p, uh, ph, 0.0)
+        st.step()
+        st.step()
+        solo.append(st.get())
+    streams = [torch.cuda.Stream() for _ in probs]
+    states = [L.State(p, uh, ph, 0.0, stream=s) for p, (uh, ph), s in zip(probs, hists, streams)]
+    for _ in range(2):
+        stats = L.batch_step(states)
+        assert len(stats) == len(states) and all(s["converged"] for s in stats)
+    for st, (us, ps) in zip(states, solo):
+        u, p = st.get()
+        assert np.array_equal(u, us) and np.array_equal(p, ps)

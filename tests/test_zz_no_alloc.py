@@ -1,8 +1,8 @@
 """The allocation-free aSIMPLE entry point (lfx_asimple_apply_noalloc).
 
-It serves callers that cannot allocate device memory while they run (for example code being
-captured into a CUDA graph, or embedded in a framework that owns all device memory): its work
-arrays live in a fixed static device array.  Here it is called through the C ABI on a matrix
+It serves callers that cannot allocate device memory while they run (for example a solver
+embedded in a framework that owns all device memory through its own pool, or a time-critical loop
+that must not pay for an allocation): its work arrays live in a fixed static device array.  Here it is called through the C ABI on a matrix
 held in caller-owned device buffers, twice in a row, and each result is compared with the
 preconditioner of the allocating entry point (lfx_debug_precond) on the same matrix, within
 the tolerance of the preconditioner parity tests.  The file sorts last so that a run stopping
