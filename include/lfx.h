@@ -90,6 +90,17 @@ lfx_status lfx_mesh_get_info(const lfx_mesh *mesh, lfx_mesh_info *info);
 lfx_status lfx_mesh_get_pattern(const lfx_mesh *mesh, int64_t *row_ptr, int32_t *col_idx);
 /* Element colours in the caller's element numbering [n_tets]. */
 lfx_status lfx_mesh_get_colors(const lfx_mesh *mesh, int32_t *colors);
+/* The chunk tables of the chunked assembly, for inspection and tests (host, no device work).
+ * sizes = {chunks, chunk colours, passes, runs, slots per pass}.  Non-NULL arrays receive:
+ * elem_old [n_tets] (caller element of each internal element), chunk_elem_off [chunks+1] (internal
+ * element range of each chunk), chunk_color_off [colours+1] (chunk range of each colour; chunks of
+ * one colour share no node), chunk_pass_off [chunks+1], pass_code [passes][slots per pass] (slot =
+ * element-in-chunk << 4 | a << 2 | b for block (a, b) of that element, 0xffff idle), pass_run_off
+ * [passes+1], run_meta [runs] (first slot | length << 8 | first-writer << 14 | diagonal << 15),
+ * run_row, run_col [runs] (the run's matrix block as caller nodes; both or neither). */
+lfx_status lfx_mesh_get_chunks(const lfx_mesh *mesh, int64_t sizes[5], int32_t *elem_old, int32_t *chunk_elem_off,
+                               int32_t *chunk_color_off, int32_t *chunk_pass_off, uint16_t *pass_code,
+                               int32_t *pass_run_off, uint16_t *run_meta, int32_t *run_row, int32_t *run_col);
 
 /* ------------------------------------------------------------------------------------------
  * Problem: physics (Section 2.1), boundary conditions (Section 2.2), RIIS surfaces (Eq. riis),
@@ -152,6 +163,7 @@ typedef struct lfx_riis {
 } lfx_riis;
 
 enum { LFX_PREC_FP64 = 0, LFX_PREC_MIXED = 1 };
+enum { LFX_ASM_AUTO = 0, LFX_ASM_COLORS = 1, LFX_ASM_CHUNKS = 2, LFX_ASM_PERSISTENT = 3 };
 /* Smoothers of the aSIMPLE blocks.  LFX_SMOOTH_AMG (Schur block only): one V-cycle of a
  * smoothed-aggregation AMG hierarchy of S = C - D diag(F)^-1 G, Chebyshev smoothing (s_steps
  * pre and post) on every level, dense solve on the coarsest. */
@@ -221,7 +233,15 @@ typedef struct lfx_options {
    * stabilisation or resistance conditions (LFX_ERR_INVALID_ARG at problem creation). */
   int32_t implicit;             /* 0 (default): semi-implicit; 1: fully implicit with Newton     */
   int32_t newton_max_iters;     /* default 10; the step returns LFX_ERR_NOT_CONVERGED past it   */
-  int32_t reserved;
+  /* assembly launch shape of the semi-implicit system: LFX_ASM_COLORS (one launch per element
+   * colour, each CTA scattering its elements' blocks), LFX_ASM_CHUNKS (compact 32-element chunks,
+   * their blocks reduced in shared memory and written once per chunk, one launch per chunk colour),
+   * LFX_ASM_PERSISTENT (the chunks in one cooperative launch, colours separated by bounded grid-wide
+   * waits; LFX_ERR_TIMEOUT from lfx_step if a wait gives up), or LFX_ASM_AUTO (default): the first
+   * assembly on the problem times each of the three on the device (two assemblies each) and the
+   * problem keeps the fastest for all its states (lfx_problem_assembly_tuning reports it).  The
+   * Newton assemblies use the colour launches. */
+  int32_t assembly;
   double newton_rtol;           /* default 1e-10                                                 */
 } lfx_options;
 void lfx_options_default(lfx_options *opt);
@@ -237,6 +257,10 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
                               const lfx_riis *riis, int32_t n_riis, const lfx_options *opt,
                               lfx_problem **out);
 void lfx_problem_destroy(lfx_problem *problem);
+/* The assembly launch shape of the problem (options.assembly, or the autotuner's choice once a state
+ * of it has assembled; 0 before that) and the tuning times in ms per assembly of the three shapes
+ * (ms[0..2] = colours, chunks, persistent; 0 where not timed).  Host-only. */
+lfx_status lfx_problem_assembly_tuning(const lfx_problem *problem, int32_t *mode, float ms[3]);
 
 /* ------------------------------------------------------------------------------------------
  * State: BDF history (u^n, ..., u^{n+1-sigma}; p likewise) resident on the device
@@ -265,11 +289,16 @@ typedef struct lfx_step_stats {
   int32_t converged;
   float ms_assembly_kernels;    /* the coloured assembly launches alone (CUDA events)          */
   int32_t n_assembly_launches;  /* launches of the assembly kernel in this step (= colours)    */
-  float ms_spmv;                /* Arnoldi block SpMV launches of the (inner) Krylov solve      */
+  float ms_spmv;                /* device time of the first (up to 4) Arnoldi block SpMV launches
+                                   of the (inner) Krylov solve in this step (CUDA events)         */
   int32_t n_spmv;               /* their number (FP64 matrix on the FP64 path, FP32 in mixed)   */
   int32_t newton_iterations;    /* Newton updates taken (fully implicit formulation), else 0    */
   float ms_newton_assembly;     /* device time of the Newton Jacobian assemblies (CUDA events)  */
-  int32_t reserved;
+  int32_t n_fpass;              /* plain F passes of the preconditioner timed in this step (those
+                                   of its first application)                                     */
+  float ms_fpass_median;        /* their mean duration per pass (CUDA events)                     */
+  int32_t assembly_mode;        /* LFX_ASM_* launch shape the step's assembly used                */
+  int32_t reserved[2];
 } lfx_step_stats;
 
 /* One BDF step t^n -> t^{n+1}: BDF/EXT fields, coloured assembly of the linearised block system,

@@ -37,10 +37,10 @@ import scipy.sparse.linalg as spla
 
 __all__ = [
     "Params", "BC", "RIIS", "Problem", "load_library", "bdf_coefficients", "element",
-    "element_residual", "geometry", "tau", "qp_coefficients", "assemble", "time_law", "boundary_geometry",
+    "element_residual", "element_batch", "geometry", "tau", "qp_coefficients", "assemble", "time_law", "boundary_geometry",
     "dirichlet_data", "neumann_rhs", "apply_dirichlet", "solve_direct", "Step",
     "step", "relative_errors", "disk_sdf", "block_of", "womersley_profile", "backflow_matrix",
-    "resistance_vectors", "resistance_terms", "lifting", "ale_velocity", "implicit_step", "ImplicitStep", "implicit_system",
+    "resistance_vectors", "resistance_terms", "set_threads", "lifting", "ale_velocity", "implicit_step", "ImplicitStep", "implicit_system",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -56,7 +56,7 @@ def build_library(force: bool = False) -> str:
     os.makedirs(_LIB_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math", "-fopenmp",
                                "-ffp-contract=off", "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -96,7 +96,15 @@ def load_library():
         _lib.orc_qp_coefficients.argtypes = [ctypes.POINTER(_CParams), dp, dp, dp, dp, dp, dp,
                                              ctypes.c_int, dp]
         _lib.orc_qp_coefficients.restype = ctypes.c_int
+        _lib.orc_set_threads.argtypes = [ctypes.c_int]
+        _lib.orc_set_threads.restype = ctypes.c_int
+        _lib.orc_set_threads(1)          # one thread unless a caller asks for more
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the C element loops (results do not depend on it); returns the count in use."""
+    return int(load_library().orc_set_threads(int(n)))
 
 
 def _dp(a):

@@ -25,6 +25,9 @@
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAX_RIIS 8
 
@@ -326,12 +329,26 @@ int orc_element_residual(const orc_params *P, const double x[12], const double u
   return 0;
 }
 
+/* Threads of the element loops below (OpenMP builds; each element is computed on its own, so the
+ * results do not depend on the count).  Returns the count in use (1 without OpenMP). */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 /* ---- batch driver: element matrices for a list of elements of a global mesh ------------ */
 int orc_elements(const orc_params *P, const double *nodes, const int32_t *tets,
                  const int64_t *elems, int64_t n, const double *ubdf, const double *uext,
                  const double *pext, const double *phinod /* [n_riis][V] */,
                  const double *uale /* [V][3] mesh velocity, or NULL */, int64_t n_nodes,
                  double *A /* [n][256] */, double *b /* [n][16] */) {
+  int err = 0;
+#pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < n; ++t) {
     const int32_t *v = tets + 4 * elems[t];
     double x[12], ub[12], ue[12], ua[12], pe[4], ph[4 * ORC_MAX_RIIS];
@@ -345,9 +362,12 @@ int orc_elements(const orc_params *P, const double *nodes, const int32_t *tets,
       pe[a] = pext[v[a]];
       for (int k = 0; k < P->n_riis; ++k) ph[4 * k + a] = phinod[k * n_nodes + v[a]];
     }
-    if (orc_element(P, x, ub, ue, pe, ph, uale ? ua : NULL, A + 256 * t, b + 16 * t) != 0) return -1 - (int)t;
+    if (orc_element(P, x, ub, ue, pe, ph, uale ? ua : NULL, A + 256 * t, b + 16 * t) != 0) {
+#pragma omp critical
+      if (err == 0 || -1 - (int)t > err) err = -1 - (int)t;
+    }
   }
-  return 0;
+  return err;
 }
 
 /* ---- fully implicit formulation (Eq. u_star, implicit; implicit LES term) ---------------
@@ -372,6 +392,8 @@ int orc_elements_implicit(const orc_params *P, const double *nodes, const int32_
                           const int64_t *elems, int64_t n, const double *ubdf, const double *sol,
                           const double *phinod, const double *uale, int64_t n_nodes, double h,
                           double *J, double *R) {
+  int err = 0;
+#pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < n; ++t) {
     const int32_t *v = tets + 4 * elems[t];
     double x[12], ub[12], ua[12], s[16], ph[4 * ORC_MAX_RIIS];
@@ -385,7 +407,11 @@ int orc_elements_implicit(const orc_params *P, const double *nodes, const int32_
       for (int k = 0; k < P->n_riis; ++k) ph[4 * k + a] = phinod[k * n_nodes + v[a]];
     }
     const double *uap = uale ? ua : NULL;
-    if (orc_element_residual_implicit(P, x, ub, s, ph, uap, R + 16 * t) != 0) return -1 - (int)t;
+    if (orc_element_residual_implicit(P, x, ub, s, ph, uap, R + 16 * t) != 0) {
+#pragma omp critical
+      if (err == 0 || -1 - (int)t > err) err = -1 - (int)t;
+      continue;
+    }
     for (int k = 0; k < 16; ++k) {
       double sp[16], sm[16], Rp[16], Rm[16];
       memcpy(sp, s, sizeof sp);
@@ -397,5 +423,5 @@ int orc_elements_implicit(const orc_params *P, const double *nodes, const int32_
       for (int i = 0; i < 16; ++i) J[256 * t + 16 * i + k] = (Rp[i] - Rm[i]) / (2.0 * h);
     }
   }
-  return 0;
+  return err;
 }

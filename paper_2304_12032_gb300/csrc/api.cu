@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <unordered_map>
 #include <string>
 #include <vector>
@@ -132,6 +133,13 @@ struct lfx_problem {
   DBuf geo64, geo_hi, geo_lo;
   int32_t pin_node = -1;   // internal
   int64_t n_bad = 0;
+  // assembly launch shape (LFX_ASM_*): options.assembly, or the autotuner's choice (0 until tuned),
+  // with the tuning times (ms per assembly: colours, chunks, persistent) and the device copy of the
+  // chunk colour offsets the persistent launch reads
+  std::mutex tune_mu;
+  int asm_mode = 0;
+  float asm_ms[3] = {0.0f, 0.0f, 0.0f};
+  DBuf d_chunk_color_off;
   size_t device_bytes() const {
     return d_dir_node.bytes + d_dir_bc.bytes + d_S.bytes + d_neu_node.bytes + d_neu_bc.bytes +
            d_neu_vec.bytes + d_phi.bytes + d_bad.bytes + geo64.bytes + geo_hi.bytes + geo_lo.bytes +
@@ -181,6 +189,10 @@ struct lfx_state {
   int dhead = 0, lifting_iters = 0;
   DBuf dhist[3], dnew, uale, xyz, xyz_hi, xyz_lo, geo64, geo_hi, geo_lo;
   DBuf lapK, lapDinv, lapFixed, lapR, lapZ, lapP, lapAp, lapPart, lapCg, bnd_node, bnd_val;
+  // persistent assembly: grid-barrier counter and error word (device), the error word's host copy
+  DBuf asm_sync;
+  int *asm_err_host = nullptr;
+  int asm_mode_used = 0;
   int64_t n_bnd = 0;
   D4 *dlevel(int l) { return dhist[(dhead + l) % sigma].as<D4>(); }
   ~lfx_state() {
@@ -190,6 +202,7 @@ struct lfx_state {
     if (e1) cudaEventDestroy(e1);
     if (e2) cudaEventDestroy(e2);
     if (inner_its) cudaFreeHost(inner_its);
+    if (asm_err_host) cudaFreeHost(asm_err_host);
   }
   D4 *level(int l) { return hist[(head + l) % sigma].as<D4>(); }
   template <class S>
@@ -328,7 +341,43 @@ lfx_status lfx_mesh_get_colors(const lfx_mesh *mesh, int32_t *colors) {
   }
   const Mesh &m = mesh->m;
   for (size_t c = 0; c + 1 < m.color_off.size(); ++c)
-    for (int32_t i = m.color_off[c]; i < m.color_off[c + 1]; ++i) colors[m.elem_old[i]] = (int32_t)c;
+    for (int32_t i = m.color_off[c]; i < m.color_off[c + 1]; ++i) colors[m.elem_old[m.color_elems[i]]] = (int32_t)c;
+  return LFX_OK;
+}
+
+lfx_status lfx_mesh_get_chunks(const lfx_mesh *mesh, int64_t sizes[5], int32_t *elem_old, int32_t *chunk_elem_off,
+                               int32_t *chunk_color_off, int32_t *chunk_pass_off, uint16_t *pass_code,
+                               int32_t *pass_run_off, uint16_t *run_meta, int32_t *run_row, int32_t *run_col) {
+  if (!mesh || !sizes) {
+    set_error("lfx_mesh_get_chunks: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = mesh->m;
+  sizes[0] = (int64_t)m.chunk_elem_off.size() - 1;
+  sizes[1] = (int64_t)m.chunk_color_off.size() - 1;
+  sizes[2] = (int64_t)m.pass_ndiag.size();
+  sizes[3] = (int64_t)m.run_block.size();
+  sizes[4] = 4 * kChunkElems;
+  auto put = [](auto *dst, const auto &v) {
+    if (dst) std::copy(v.begin(), v.end(), dst);
+  };
+  put(elem_old, m.elem_old);
+  put(chunk_elem_off, m.chunk_elem_off);
+  put(chunk_color_off, m.chunk_color_off);
+  put(chunk_pass_off, m.chunk_pass_off);
+  put(pass_code, m.pass_code);
+  put(pass_run_off, m.pass_run_off);
+  put(run_meta, m.run_meta);
+  if (run_row && run_col) {
+    // block index -> (row, column) in the caller's node numbering
+    std::vector<int32_t> row_of(m.nnzb);
+    for (int64_t i = 0; i < m.V; ++i)
+      for (int32_t k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) row_of[k] = (int32_t)i;
+    for (size_t r = 0; r < m.run_block.size(); ++r) {
+      run_row[r] = m.node_old[row_of[m.run_block[r]]];
+      run_col[r] = m.node_old[m.col_idx[m.run_block[r]]];
+    }
+  }
   return LFX_OK;
 }
 
@@ -369,6 +418,7 @@ void lfx_options_default(lfx_options *o) {
   o->inner_adaptive = 1;
   o->implicit = 0;
   o->newton_max_iters = 10;
+  o->assembly = LFX_ASM_AUTO;
   o->newton_rtol = 1e-10;
 }
 
@@ -466,6 +516,10 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
       o.f_smoother > 1 || o.s_smoother < 0 || o.s_smoother > 2) {
     set_error("lfx_problem_create: option out of range (restart <= %d, smoothing steps <= %d)", kMaxRestart,
               kMaxSmooth);
+    return LFX_ERR_INVALID_ARG;
+  }
+  if (o.assembly < LFX_ASM_AUTO || o.assembly > LFX_ASM_PERSISTENT) {
+    set_error("lfx_problem_create: assembly must be one of LFX_ASM_*");
     return LFX_ERR_INVALID_ARG;
   }
   if (o.implicit < 0 || o.implicit > 1 || (o.implicit && (o.newton_max_iters < 1 || !(o.newton_rtol > 0.0)))) {
@@ -862,7 +916,23 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
     }
     LFX_CUDA_TRY(cudaStreamSynchronize(0));
   }
+  LFX_TRY(pb->d_chunk_color_off.alloc(sizeof(int32_t) * m.chunk_color_off.size()));
+  LFX_CUDA_TRY(cudaMemcpy(pb->d_chunk_color_off.p, m.chunk_color_off.data(), sizeof(int32_t) * m.chunk_color_off.size(),
+                          cudaMemcpyHostToDevice));
+  pb->asm_mode = o.assembly;
   *out = pb.release();
+  return LFX_OK;
+}
+
+lfx_status lfx_problem_assembly_tuning(const lfx_problem *pb, int32_t *mode, float ms[3]) {
+  if (!pb || !mode || !ms) {
+    set_error("lfx_problem_assembly_tuning: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  lfx_problem *p = const_cast<lfx_problem *>(pb);
+  std::lock_guard<std::mutex> lk(p->tune_mu);
+  *mode = p->asm_mode;
+  for (int i = 0; i < 3; ++i) ms[i] = p->asm_ms[i];
   return LFX_OK;
 }
 
@@ -1136,17 +1206,73 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs, bool newton = fa
     A.geo_lo = s->geo_lo.as<float>();
     A.uale = s->uale.as<D4>();
   }
-  LFX_CUDA_TRY(cudaEventRecord(s->ea0, st));
-  if (mixed) {
-    // double-float arithmetic; badly shaped elements keep FP64 geometry
-    A.bad = pb->n_bad > 0 ? pb->d_bad.as<uint8_t>() : nullptr;
-    LFX_TRY((launch_assemble<dd, float>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
-                                        s->vals32.as<float>(), newton)));
-  } else {
-    LFX_TRY((launch_assemble<double, double>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
-                                             s->vals64.as<double>(), newton)));
+  A.elist = m.d_color_elems.as<int32_t>();
+  const ChunkArgs CA{m.d_chunk_elem_off.as<int32_t>(), m.d_chunk_pass_off.as<int32_t>(), m.d_pass_code.as<uint16_t>(),
+                     m.d_pass_run_off.as<int32_t>(), m.d_pass_ndiag.as<int32_t>(), m.d_run_meta.as<uint16_t>(),
+                     m.d_run_block.as<int32_t>(), m.d_run_node.as<int32_t>()};
+  const int n_cc = (int)m.chunk_color_off.size() - 1;
+  if (mixed) A.bad = pb->n_bad > 0 ? pb->d_bad.as<uint8_t>() : nullptr;   // badly shaped: FP64 geometry
+  if (!s->asm_sync.p) {
+    LFX_TRY(s->asm_sync.alloc(64));
+    LFX_CUDA_TRY(cudaMallocHost(&s->asm_err_host, sizeof(int)));
+    *s->asm_err_host = 0;
   }
+  unsigned *barrier = s->asm_sync.as<unsigned>();
+  int *err = reinterpret_cast<int *>(s->asm_sync.as<char>() + 32);
+  // one assembly of the semi-implicit system (or the Newton system) in launch shape `mode`
+  auto launch = [&](int mode) -> lfx_status {
+    if (mixed) {
+      if (newton || mode == LFX_ASM_COLORS)
+        return launch_assemble<dd, float>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
+                                          s->vals32.as<float>(), newton);
+      if (mode == LFX_ASM_CHUNKS)
+        return launch_assemble_chunks<dd, float>(st, A, pb->P, CA, m.chunk_color_off.data(), n_cc,
+                                                 s->vals32.as<float>());
+      return launch_assemble_persistent<dd, float>(st, A, pb->P, CA, pb->d_chunk_color_off.as<int32_t>(), n_cc,
+                                                   s->vals32.as<float>(), barrier, err);
+    }
+    if (newton || mode == LFX_ASM_COLORS)
+      return launch_assemble<double, double>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
+                                             s->vals64.as<double>(), newton);
+    if (mode == LFX_ASM_CHUNKS)
+      return launch_assemble_chunks<double, double>(st, A, pb->P, CA, m.chunk_color_off.data(), n_cc,
+                                                    s->vals64.as<double>());
+    return launch_assemble_persistent<double, double>(st, A, pb->P, CA, pb->d_chunk_color_off.as<int32_t>(), n_cc,
+                                                      s->vals64.as<double>(), barrier, err);
+  };
+  int mode = LFX_ASM_COLORS;
+  if (!newton) {
+    std::lock_guard<std::mutex> lk(pb->tune_mu);
+    if (pb->asm_mode == LFX_ASM_AUTO) {
+      // autotuner: each launch shape twice (the second timed) on this state's buffers; the fastest
+      // becomes the problem's shape (every assembly writes the complete system, so the last one run
+      // leaves a valid matrix behind)
+      float best = 0.0f;
+      int pick = LFX_ASM_COLORS;
+      for (int cand = LFX_ASM_COLORS; cand <= LFX_ASM_PERSISTENT; ++cand) {
+        LFX_TRY(launch(cand));
+        LFX_CUDA_TRY(cudaEventRecord(s->ea0, st));
+        LFX_TRY(launch(cand));
+        LFX_CUDA_TRY(cudaEventRecord(s->ea1, st));
+        LFX_CUDA_TRY(cudaEventSynchronize(s->ea1));
+        float ms = 0.0f;
+        LFX_CUDA_TRY(cudaEventElapsedTime(&ms, s->ea0, s->ea1));
+        pb->asm_ms[cand - 1] = ms;
+        if (cand == LFX_ASM_COLORS || ms < best) {
+          best = ms;
+          pick = cand;
+        }
+      }
+      pb->asm_mode = pick;
+    }
+    mode = pb->asm_mode;
+  }
+  s->asm_mode_used = newton ? LFX_ASM_COLORS : mode;
+  LFX_CUDA_TRY(cudaEventRecord(s->ea0, st));
+  LFX_TRY(launch(mode));
   LFX_CUDA_TRY(cudaEventRecord(s->ea1, st));
+  if (!newton && mode == LFX_ASM_PERSISTENT)
+    LFX_CUDA_TRY(cudaMemcpyAsync(s->asm_err_host, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   if (pb->n_bf_edges > 0)
     LFX_TRY(launch_backflow(st, pb->n_bf_edges, pb->d_bf_ij.as<int32_t>(), pb->d_bf_an.as<double>(),
                             pb->d_bf_coef.as<double>(), pb->d_bf_slot4.as<int32_t>(), s->xsol.as<D4>(),
@@ -1154,7 +1280,8 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs, bool newton = fa
                             mixed ? nullptr : s->vals64.as<double>(), mixed ? s->vals32.as<float>() : nullptr,
                             mixed ? s->vals_lo.as<float>() : nullptr));
   if (mixed) LFX_TRY(launch_dd_combine(st, 4 * m.V, s->rhs_hi.as<float>(), s->rhs_lo.as<float>(), s->rhs.as<double>()));
-  s->n_asm_launch = (int)m.color_off.size() - 1;
+  s->n_asm_launch = (newton || mode == LFX_ASM_COLORS) ? (int)m.color_off.size() - 1
+                                                       : (mode == LFX_ASM_CHUNKS ? n_cc : 1);
   // boundary data at t^{n+1}
   DirCoef C;
   memset(&C, 0, sizeof(C));
@@ -1677,6 +1804,9 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   s->gm64.n_tev = 0;
   s->gm32.n_tev = 0;
   s->gmdd.n_tev = 0;
+  s->pc64.n_fev = 0;
+  s->pc32.n_fev = 0;
+  s->pcbf.n_fev = 0;
   lfx_status rc = run_solve(s, s->xsol.as<double>(), false, &its, &outer, &rel);
   if (rc != LFX_OK && rc != LFX_ERR_NOT_CONVERGED) return rc;
   int n_newton = 0;
@@ -1705,6 +1835,11 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   s->t += pb->P.dt;
   s->assembled = false;
   LFX_CUDA_TRY(cudaEventSynchronize(s->e2));
+  if (s->asm_err_host && *s->asm_err_host) {
+    *s->asm_err_host = 0;
+    set_error("lfx_step: a grid-wide wait of the persistent assembly gave up");
+    return LFX_ERR_TIMEOUT;
+  }
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->iterations = its;
@@ -1719,12 +1854,16 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
     stats->n_assembly_launches = s->n_asm_launch;
     stats->newton_iterations = n_newton;
     stats->ms_newton_assembly = ms_newton;
+    stats->assembly_mode = s->asm_mode_used;
     if (o.precision == LFX_PREC_MIXED) {
+      if (o.smoother_bf16) s->pcbf.read_f_timing(&stats->ms_fpass_median, &stats->n_fpass);
+      else s->pc32.read_f_timing(&stats->ms_fpass_median, &stats->n_fpass);
       s->gm32.read_spmv_timing(&stats->ms_spmv, &stats->n_spmv);
       int dummy = 0;
       float d2 = 0.0f;
       s->gmdd.read_spmv_timing(&d2, &dummy);
     } else {
+      s->pc64.read_f_timing(&stats->ms_fpass_median, &stats->n_fpass);
       s->gm64.read_spmv_timing(&stats->ms_spmv, &stats->n_spmv);
     }
     stats->converged = rc == LFX_OK;

@@ -19,6 +19,7 @@
 //            (a, b) and adds them into global memory (read-modify-write of 128 B / 64 B).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "dd.h"
@@ -114,6 +115,7 @@ struct ElemShared {
   R mga[kElems][4][4];     // [q][a] = m_q . grad phi_a
   R wg[kElems][4][3];      // w grad phi_a
   R Svp[kElems][4], Ppv[kElems][4], Wv[kElems][4][3], Zv[kElems][3], TM[kElems], TC[kElems], muvol[kElems];
+  int32_t eid[kElems];     // element of each slot (-1: none)
 };
 
 // Extra per-element data of the Newton linearisation of the fully implicit formulation (the
@@ -252,11 +254,11 @@ __device__ void geom_phase(const AssembleArgs &A, int64_t e, int le, ElemShared<
 // Phase 1a from the cache: the CTA's threads load kGeoValues values of each of its elements
 // (for a fixed value index, consecutive elements are consecutive in memory)
 template <class R>
-__device__ void geom_load(const AssembleArgs &A, int64_t base, int64_t e1, int64_t T, ElemShared<R> &sh) {
+__device__ void geom_load(const AssembleArgs &A, int64_t T, ElemShared<R> &sh) {
   for (int idx = threadIdx.x; idx < kGeoValues * kElems; idx += kCta) {
     const int k = idx / kElems, le = idx % kElems;
-    const int64_t e = base + le;
-    if (e >= e1) continue;
+    const int64_t e = sh.eid[le];
+    if (e < 0) continue;
     const R v = geo_value<R>(A, k, e, T);
     if (k < 12) sh.gphi[le][k] = v;
     else if (k < 21) sh.Gm[le][k - 12] = v;
@@ -639,28 +641,36 @@ __device__ void newton_block(const AssembleArgs &A, const PhysParams &P, const P
   for (int i = 0; i < 4; ++i) ext[i] = quad_sum<R>(ev[i], mask);
 }
 
-template <class R, class S, bool IMPL>
-__device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q, int64_t e, int le,
-                            int a, int b, const ElemShared<R> &sh, const ImplShared<R> *ix, S *vals) {
+// Right-hand-side entry (a, i) of element slot le: (f + rho u^BDF/dt, v) with the SUPG, VMS and
+// LES test functions (velocity rows), PSPG (pressure row)
+template <class R>
+__device__ __forceinline__ R rhs_value(const PhysParams &P, const ElemShared<R> &sh, int le, int a, int i) {
+  R rhs = cst<R>(0.0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const R Eqa = sh.E[le][q][a];
+    if (i < 3) rhs = fmadd(sh.m[le][q][i], Eqa, fmadd(sh.wz[le][q][i], sh.mga[le][q][a], rhs));
+    else if (P.stab >= 1) rhs = fmadd(sh.wtm[le][q], sh.mga[le][q][a], rhs);
+  }
+  return rhs;
+}
+
+// Block (a, b) of element slot le (row = test component, column = trial component)
+template <class R>
+__device__ __forceinline__ void block_values(const PhysParams &P, int le, int a, int b, const ElemShared<R> &sh,
+                                             R blk[16]) {
   const R *ga = sh.gphi[le] + 3 * a;
   const R *gb = sh.gphi[le] + 3 * b;
   const R gab = fmadd(ga[2], gb[2], fmadd(ga[1], gb[1], ga[0] * gb[0]));
   // velocity-velocity scalar: sum_q E_q(a) cb_q(b) = mass/dt + resistive + Galerkin advection
   // + SUPG (Eq. fullydiscrete..., Eq. stabilization_form_SUPG)
-  R Mab = cst<R>(0.0), rhs = Mab;
-  const int i_rhs = b;   // this thread also forms right-hand-side entry (a, i_rhs)
+  R Mab = cst<R>(0.0);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const R Eqa = sh.E[le][q][a];
-    Mab = fmadd(Eqa, sh.cb[le][q][b], Mab);
-    if (i_rhs < 3) rhs = fmadd(sh.m[le][q][i_rhs], Eqa, fmadd(sh.wz[le][q][i_rhs], sh.mga[le][q][a], rhs));
-    else if (P.stab >= 1) rhs = fmadd(sh.wtm[le][q], sh.mga[le][q][a], rhs);
-  }
+  for (int q = 0; q < 4; ++q) Mab = fmadd(sh.E[le][q][a], sh.cb[le][q][b], Mab);
   const R muvol = sh.muvol[le];
   const R TC = (P.stab >= 1) ? sh.TC[le] : cst<R>(0.0);
   const R *Wv = sh.Wv[le][b];
   const R dg = fmadd(muvol, gab, Mab);                          // + grad-grad diffusion
-  R blk[16];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const R tci = TC * ga[i];
@@ -690,6 +700,15 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const Ph
     }
     blk[15] = cst<R>(0.0);
   }
+}
+
+template <class R, class S, bool IMPL>
+__device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q, int64_t e, int le,
+                            int a, int b, const ElemShared<R> &sh, const ImplShared<R> *ix, S *vals) {
+  const int i_rhs = b;   // this thread also forms right-hand-side entry (a, i_rhs)
+  R blk[16];
+  block_values<R>(P, le, a, b, sh, blk);
+  R rhs = rhs_value<R>(P, sh, le, a, i_rhs);
   if (IMPL) {
     R ext[4];
     newton_block<R>(A, P, Q, e, le, a, b, sh, *ix, blk, ext);
@@ -758,22 +777,243 @@ __global__ void __launch_bounds__(kCta, IMPL ? 1 : MinCtas<R>::value) assemble_c
   if constexpr (IMPL) ix = &shm.x;
   const int t = threadIdx.x;
   for (int64_t base = e0 + (int64_t)blockIdx.x * kElems; base < e1; base += (int64_t)gridDim.x * kElems) {
-    if (has_geo<R>(A)) geom_load<R>(A, base, e1, A.n_elems, sh);
-    else if (t < kElems && base + t < e1) geom_phase<R>(A, base + t, t, sh);
+    if (t < kElems) sh.eid[t] = base + t < e1 ? (A.elist ? A.elist[base + t] : (int32_t)(base + t)) : -1;
+    __syncthreads();
+    if (has_geo<R>(A)) geom_load<R>(A, A.n_elems, sh);
+    else if (t < kElems && sh.eid[t] >= 0) geom_phase<R>(A, sh.eid[t], t, sh);
     __syncthreads();
     const int le = t >> 2, q = t & 3;
-    const bool live = base + le < e1;
-    if (live) qp_phase<R, IMPL>(A, P, Q, base + le, q, le, sh, ix);
+    const bool live = sh.eid[le] >= 0;
+    if (live) qp_phase<R, IMPL>(A, P, Q, sh.eid[le], q, le, sh, ix);
     __syncthreads();
     if (live) node_phase<R, IMPL>(P, Q, q, le, sh, ix);
     __syncthreads();
 #pragma unroll 1
     for (int pass = 0; pass < kElems * 16 / kCta; ++pass) {
       const int le2 = pass * (kCta / 16) + (t >> 4);
-      const int64_t e = base + le2;
-      if (e < e1) block_phase<R, S, IMPL>(A, P, Q, e, le2, (t >> 2) & 3, t & 3, sh, ix, vals);
+      const int64_t e = sh.eid[le2];
+      if (e >= 0) block_phase<R, S, IMPL>(A, P, Q, e, le2, (t >> 2) & 3, t & 3, sh, ix, vals);
     }
     __syncthreads();
+  }
+}
+
+// ---- chunked assembly: one CTA per chunk of kElems elements at a time.  The element phases are
+// those of the colour kernel; the 16 x kElems block contributions are then formed one pass of kCta
+// slots at a time into shared memory (slot code le << 4 | a << 2 | b, runs of slots sharing one
+// matrix block, no run straddling two passes), and each run is summed there and written to its
+// block once: 16 threads per run, one value each (a store for the block's first-writing chunk, an
+// add otherwise).  Diagonal runs (a == b) also carry the rows' right-hand sides.  Chunks of one
+// colour share no node, so concurrent CTAs never write the same block or row.
+constexpr int kStage = 17;          // staging row: 16 values + 1 to spread shared-memory banks
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+template <class R>
+struct ChunkShared {
+  ElemShared<R> e;
+  R stage[kCta][kStage];
+  R rst[kCta][4];
+};
+
+// Four consecutive matrix values or one node's four right-hand-side entries (16-byte aligned): their
+// old values are loaded ahead of the stores, so that a thread's loads of several items are in
+// flight together; a store for the first writer, an add otherwise.
+template <class S, class R> struct AccumOut;
+template <>
+struct AccumOut<double, double> {
+  struct Old {
+    double2 a, b;
+  };
+  static __device__ __forceinline__ double *at(const AssembleArgs &A, double *vals, int64_t k, bool is_rhs) {
+    return is_rhs ? A.rhs + k : vals + k;
+  }
+  // (L2 only: in the persistent launch another SM may have written the value since this SM last
+  // cached it)
+  static __device__ __forceinline__ Old load(const AssembleArgs &A, double *vals, int64_t k, bool is_rhs) {
+    const double2 *p = reinterpret_cast<const double2 *>(at(A, vals, k, is_rhs));
+    return Old{__ldcg(p), __ldcg(p + 1)};
+  }
+  static __device__ __forceinline__ void store(const AssembleArgs &A, double *vals, int64_t k, bool is_rhs,
+                                               const double v[4], const Old &o, bool first) {
+    double2 *p = reinterpret_cast<double2 *>(at(A, vals, k, is_rhs));
+    if (first) {
+      p[0] = make_double2(v[0], v[1]);
+      p[1] = make_double2(v[2], v[3]);
+    } else {
+      p[0] = make_double2(o.a.x + v[0], o.a.y + v[1]);
+      p[1] = make_double2(o.b.x + v[2], o.b.y + v[3]);
+    }
+  }
+};
+template <>
+struct AccumOut<float, dd> {
+  struct Old {
+    float4 hi, lo;
+  };
+  static __device__ __forceinline__ Old load(const AssembleArgs &A, float *vals, int64_t k, bool is_rhs) {
+    const float4 *h = reinterpret_cast<const float4 *>(is_rhs ? A.rhs_hi + k : vals + k);
+    const float4 *l = reinterpret_cast<const float4 *>(is_rhs ? A.rhs_lo + k : A.vals_lo + k);
+    return Old{__ldcg(h), __ldcg(l)};
+  }
+  static __device__ __forceinline__ void store(const AssembleArgs &A, float *vals, int64_t k, bool is_rhs,
+                                               const dd v[4], const Old &o, bool first) {
+    float4 *h = reinterpret_cast<float4 *>(is_rhs ? A.rhs_hi + k : vals + k);
+    float4 *l = reinterpret_cast<float4 *>(is_rhs ? A.rhs_lo + k : A.vals_lo + k);
+    dd r[4] = {v[0], v[1], v[2], v[3]};
+    if (!first) {
+      r[0] = dd(o.hi.x, o.lo.x) + v[0];
+      r[1] = dd(o.hi.y, o.lo.y) + v[1];
+      r[2] = dd(o.hi.z, o.lo.z) + v[2];
+      r[3] = dd(o.hi.w, o.lo.w) + v[3];
+    }
+    *h = make_float4(r[0].hi, r[1].hi, r[2].hi, r[3].hi);
+    *l = make_float4(r[0].lo, r[1].lo, r[2].lo, r[3].lo);
+  }
+};
+constexpr int kItemsInFlight = 2;   // reduction items (four values each) per thread loaded together
+
+template <class R, class S>
+__device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q,
+                                            const ChunkArgs &C, int64_t c0, int64_t c1, S *vals, ChunkShared<R> &cs) {
+  ElemShared<R> &sh = cs.e;
+  const int t = threadIdx.x;
+  for (int64_t ch = c0 + blockIdx.x; ch < c1; ch += gridDim.x) {
+    const int64_t e0 = C.elem_off[ch], e1 = C.elem_off[ch + 1];
+    {
+      // the blocks (and rows) this chunk adds to, into L2 ahead of its reduction phases
+      const int rb = C.run_off[C.pass_off[ch]], re = C.run_off[C.pass_off[ch + 1]];
+      for (int r = rb + t; r < re; r += kCta) {
+        const uint32_t meta = C.meta[r];
+        if ((meta >> 14) & 1) continue;
+        const int64_t k = (int64_t)C.block[r] * 16;
+        prefetch_l2(vals + k);
+        if (std::is_same<R, dd>::value) prefetch_l2(A.vals_lo + k);
+        if (meta >> 15) {
+          const int64_t rr = 4 * (int64_t)C.node[r];
+          if (std::is_same<R, dd>::value) {
+            prefetch_l2(A.rhs_hi + rr);
+            prefetch_l2(A.rhs_lo + rr);
+          } else {
+            prefetch_l2(A.rhs + rr);
+          }
+        }
+      }
+    }
+    if (t < kElems) sh.eid[t] = e0 + t < e1 ? (int32_t)(e0 + t) : -1;
+    __syncthreads();
+    if (has_geo<R>(A)) geom_load<R>(A, A.n_elems, sh);
+    else if (t < kElems && sh.eid[t] >= 0) geom_phase<R>(A, sh.eid[t], t, sh);
+    __syncthreads();
+    const int le = t >> 2, q = t & 3;
+    const bool live = sh.eid[le] >= 0;
+    if (live) qp_phase<R, false>(A, P, Q, sh.eid[le], q, le, sh, nullptr);
+    __syncthreads();
+    if (live) node_phase<R, false>(P, Q, q, le, sh, nullptr);
+    __syncthreads();
+    const int p1 = C.pass_off[ch + 1];
+    for (int ps = C.pass_off[ch]; ps < p1; ++ps) {
+      const uint16_t code = C.code[(int64_t)ps * kCta + t];
+      if (code != 0xffffu) {
+        const int l2 = code >> 4, a = (code >> 2) & 3, b = code & 3;
+        R blk[16];
+        block_values<R>(P, l2, a, b, sh, blk);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) cs.stage[t][k] = blk[k];
+        if (a == b) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) cs.rst[t][i] = rhs_value<R>(P, sh, l2, a, i);
+        }
+      }
+      __syncthreads();
+      const int r0 = C.run_off[ps], nr = C.run_off[ps + 1] - r0, nd = C.ndiag[ps];
+      const int items = 4 * nr + nd;     // a block's values in four quarters; a diagonal run's rhs row
+      using Out = AccumOut<S, R>;
+      for (int jb = t; jb < items; jb += kCta * kItemsInFlight) {
+        int64_t where[kItemsInFlight];
+        bool is_rhs[kItemsInFlight], first[kItemsInFlight];
+        typename Out::Old old[kItemsInFlight];
+        R acc[kItemsInFlight][4];
+#pragma unroll
+        for (int i = 0; i < kItemsInFlight; ++i) {
+          const int j = jb + i * kCta;
+          where[i] = -1;
+          if (j >= items) continue;
+          const bool blk_item = j < 4 * nr;
+          const int run = r0 + (blk_item ? j >> 2 : j - 4 * nr);
+          const int v0 = blk_item ? 4 * (j & 3) : 0;
+          const uint32_t meta = C.meta[run];
+          first[i] = (meta >> 14) & 1;
+          is_rhs[i] = !blk_item;
+          where[i] = blk_item ? (int64_t)C.block[run] * 16 + v0 : 4 * (int64_t)C.node[run];
+          if (!first[i]) old[i] = Out::load(A, vals, where[i], is_rhs[i]);
+          const int st0 = meta & 0xff, len = (meta >> 8) & 63;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[i][v] = blk_item ? cs.stage[st0][v0 + v] : cs.rst[st0][v];
+          for (int k = 1; k < len; ++k) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[i][v] += blk_item ? cs.stage[st0 + k][v0 + v] : cs.rst[st0 + k][v];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < kItemsInFlight; ++i)
+          if (where[i] >= 0) Out::store(A, vals, where[i], is_rhs[i], acc[i], old[i], first[i]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// one launch per chunk colour
+template <class R, class S>
+__global__ void __launch_bounds__(kCta, MinCtas<R>::value) assemble_chunk_kernel(AssembleArgs A, PhysParams P,
+                                                                                PhysR<R> Q, ChunkArgs C,
+                                                                                int64_t c0, int64_t c1, S *vals) {
+  pdl_entry();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  chunk_range<R, S>(A, P, Q, C, c0, c1, vals, *reinterpret_cast<ChunkShared<R> *>(smem_raw));
+}
+
+// Grid-wide barrier of a co-resident (cooperatively launched) grid on a counter that only grows:
+// every CTA adds one and waits until the count reaches target = (barrier index + 1) x grid size.
+// The wait is bounded: after kBarrierSpins polls it sets *err and gives up, and so does every CTA
+// that finds *err set, so that no CTA waits on one that has left.  Returns false on failure.
+constexpr unsigned kBarrierSpins = 1u << 24;
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, int *err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    unsigned spins = 0;
+    int good = 1;
+    while (true) {
+      unsigned seen;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(count) : "memory");
+      if (seen >= target) break;
+      if (*(volatile int *)err != 0 || ++spins > kBarrierSpins) {
+        atomicExch(err, 1);
+        good = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// every chunk colour in one cooperative launch, colours separated by grid-wide barriers
+template <class R, class S>
+__global__ void __launch_bounds__(kCta, MinCtas<R>::value) assemble_chunks_persistent_kernel(
+    AssembleArgs A, PhysParams P, PhysR<R> Q, ChunkArgs C, const int32_t *color_off, int n_colors, S *vals,
+    unsigned *barrier, int *err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ChunkShared<R> &cs = *reinterpret_cast<ChunkShared<R> *>(smem_raw);
+  for (int c = 0; c < n_colors; ++c) {
+    chunk_range<R, S>(A, P, Q, C, color_off[c], color_off[c + 1], vals, cs);
+    if (c + 1 < n_colors && !grid_barrier(barrier, (unsigned)(c + 1) * gridDim.x, err)) return;
   }
 }
 
@@ -1046,6 +1286,90 @@ lfx_status launch_comp_normalize_dd(cudaStream_t st, int64_t V, int n_comp, cons
   note_launches(2);
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
+}
+
+template <class R, class S>
+lfx_status launch_assemble_chunks(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
+                                  const int32_t *chunk_color_off, int n_colors, S *vals) {
+  const PhysR<R> Q = phys_r<R>(P);
+  const size_t smem = sizeof(ChunkShared<R>);
+  static bool attr_set = false;
+  if (!attr_set) {
+    LFX_CUDA_TRY(cudaFuncSetAttribute(assemble_chunk_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    attr_set = true;
+  }
+  int dev = 0, nsm = 152, per_sm = 1;
+  LFX_CUDA_TRY(cudaGetDevice(&dev));
+  LFX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  LFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assemble_chunk_kernel<R, S>, kCta, smem));
+  const int64_t resident = (int64_t)nsm * std::max(per_sm, 1);
+  for (int c = 0; c < n_colors; ++c) {
+    const int64_t c0 = chunk_color_off[c], c1 = chunk_color_off[c + 1];
+    if (c1 <= c0) continue;
+    const int grid = (int)std::min<int64_t>(c1 - c0, resident);
+    pdl_launch(assemble_chunk_kernel<R, S>, grid, kCta, smem, st, A, P, Q, C, c0, c1, vals);
+    note_launches(1);
+  }
+  LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+template lfx_status launch_assemble_chunks<double, double>(cudaStream_t, const AssembleArgs &, const PhysParams &,
+                                                           const ChunkArgs &, const int32_t *, int, double *);
+template lfx_status launch_assemble_chunks<dd, float>(cudaStream_t, const AssembleArgs &, const PhysParams &,
+                                                      const ChunkArgs &, const int32_t *, int, float *);
+
+template <class R, class S>
+lfx_status launch_assemble_persistent(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
+                                      const int32_t *d_chunk_color_off, int n_colors, S *vals, unsigned *barrier,
+                                      int *err) {
+  const PhysR<R> Q = phys_r<R>(P);
+  const size_t smem = sizeof(ChunkShared<R>);
+  static bool attr_set = false;
+  if (!attr_set) {
+    LFX_CUDA_TRY(cudaFuncSetAttribute(assemble_chunks_persistent_kernel<R, S>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  int dev = 0, nsm = 152, per_sm = 0, coop = 0;
+  LFX_CUDA_TRY(cudaGetDevice(&dev));
+  LFX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  LFX_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  LFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assemble_chunks_persistent_kernel<R, S>, kCta,
+                                                              smem));
+  if (!coop || per_sm < 1) {
+    set_error("persistent assembly: cooperative launch unavailable");
+    return LFX_ERR_CUDA;
+  }
+  LFX_CUDA_TRY(cudaMemsetAsync(barrier, 0, sizeof(unsigned), st));
+  LFX_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  const int grid = nsm * per_sm;
+  void *args[] = {(void *)&A, (void *)&P, (void *)&Q, (void *)&C, (void *)&d_chunk_color_off, (void *)&n_colors,
+                  (void *)&vals, (void *)&barrier, (void *)&err};
+  LFX_CUDA_TRY(cudaLaunchCooperativeKernel((void *)assemble_chunks_persistent_kernel<R, S>, dim3(grid), dim3(kCta), args,
+                                           smem, st));
+  note_launches(1);
+  return LFX_OK;
+}
+template lfx_status launch_assemble_persistent<double, double>(cudaStream_t, const AssembleArgs &, const PhysParams &,
+                                                               const ChunkArgs &, const int32_t *, int, double *,
+                                                               unsigned *, int *);
+template lfx_status launch_assemble_persistent<dd, float>(cudaStream_t, const AssembleArgs &, const PhysParams &,
+                                                          const ChunkArgs &, const int32_t *, int, float *, unsigned *,
+                                                          int *);
+
+int64_t assemble_chunk_wave() {
+  int dev = 0, v = 0, sms = 152, per_sm = LFX_ASM_DD_MIN_CTAS;
+  if (cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) {
+    sms = v;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, assemble_chunk_kernel<dd, float>, kCta,
+                                                      sizeof(ChunkShared<dd>)) == cudaSuccess && b > 0)
+      per_sm = b;
+  }
+  (void)cudaGetLastError();
+  return (int64_t)sms * per_sm;
 }
 
 template <class R, class S>

@@ -44,6 +44,16 @@ struct AssembleArgs {
   const float *geo_hi, *geo_lo;
   // moving mesh: u_ALE at the nodes (the advection velocity is u* = u^EXT - u_ALE); null: fixed mesh
   const D4 *uale;
+  // per-colour kernel: the elements of the colour ranges (internal ids); null: the ranges are ids
+  const int32_t *elist;
+};
+// chunk tables of the chunked assembly (device copies of the Mesh vectors of the same names)
+struct ChunkArgs {
+  const int32_t *elem_off, *pass_off;
+  const uint16_t *code;
+  const int32_t *run_off, *ndiag;
+  const uint16_t *meta;
+  const int32_t *block, *node;
 };
 constexpr int kGeoValues = 23;
 
@@ -89,6 +99,17 @@ lfx_status launch_backflow(cudaStream_t st, int64_t n_edges, const int32_t *ij, 
 template <class R, class S>
 lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysParams &P,
                            const int32_t *color_off, int n_colors, S *vals, bool newton = false);
+// the semi-implicit system by chunks in ONE cooperative launch over every chunk colour, the colours
+// separated by bounded grid-wide waits; *err (device) is set to 1 if a wait gave up.  d_chunk_color_off:
+// device copy of the colour offsets; barrier: a device counter (zeroed here).
+template <class R, class S>
+lfx_status launch_assemble_persistent(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
+                                      const int32_t *d_chunk_color_off, int n_colors, S *vals, unsigned *barrier,
+                                      int *err);
+// the semi-implicit system by chunks (one launch per chunk colour)
+template <class R, class S>
+lfx_status launch_assemble_chunks(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
+                                  const int32_t *chunk_color_off, int n_colors, S *vals);
 lfx_status launch_dirichlet_values(cudaStream_t st, int64_t nd, int H, const int32_t *bc_of,
                                    const double *S, const DirCoef &C, const double *N, int nb, D4 *g);
 lfx_status launch_neumann(cudaStream_t st, int64_t n, const int32_t *node, const int32_t *bc_of,

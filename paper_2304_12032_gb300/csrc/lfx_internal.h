@@ -114,7 +114,22 @@ struct Mesh {
   std::vector<uint16_t> first;       // [T] bit 4a+b: the element writes block (a, b) before any other
   bool all_blocks_touched = false;   // every block of the pattern belongs to some element
   bool all_nodes_touched = false;    // every node belongs to some element
-  std::vector<int32_t> color_off;    // [n_colors+1] offsets into the colour-sorted elements
+  std::vector<int32_t> color_off;    // [n_colors+1] offsets into color_elems
+  std::vector<int32_t> color_elems;  // [T] internal element ids listed colour by colour (Morton order inside)
+  // chunked assembly: chunks of at most kChunkElems consecutive internal elements (a compact piece of
+  // the Morton order); chunks coloured so that no two chunks of one colour share a node, the internal
+  // element order running chunk by chunk, colour by colour.  Each chunk's (element, a, b) block
+  // contributions are packed into passes of 4 kChunkElems slots, grouped in runs that share one
+  // matrix block, no run straddling two passes.
+  std::vector<int32_t> chunk_elem_off;   // [n_chunks+1] element ranges
+  std::vector<int32_t> chunk_color_off;  // [n_chunk_colors+1] chunk ranges per colour
+  std::vector<int32_t> chunk_pass_off;   // [n_chunks+1] pass ranges
+  std::vector<uint16_t> pass_code;       // [n_passes][4 kChunkElems]: le << 4 | a << 2 | b, 0xffff idle
+  std::vector<int32_t> pass_run_off;     // [n_passes+1] run ranges (diagonal runs first)
+  std::vector<int32_t> pass_ndiag;       // [n_passes] diagonal runs (a == b: also the node's rhs row)
+  std::vector<uint16_t> run_meta;        // slot start (bits 0-7) | length (8-13) | first writer (14) | diagonal (15)
+  std::vector<int32_t> run_block;        // [runs] block index in the pattern
+  std::vector<int32_t> run_node;         // [runs] node of a diagonal run (its rhs row), else -1
   std::vector<uint8_t> bad;          // [T] 1 if below the shape-quality threshold
   std::vector<int32_t> bfaces;       // [F][3] outward oriented, internal numbering
   std::vector<int32_t> btags;        // [F]
@@ -133,6 +148,9 @@ struct Mesh {
   DBuf d_comp_off;  // int32 [n_comp+1]
   DBuf d_node_old;  // int32 [V] internal node -> caller node (host arrays in, solutions out)
   DBuf d_first;     // uint16 [T] (first)
+  DBuf d_color_elems;
+  DBuf d_chunk_elem_off, d_chunk_pass_off, d_pass_code, d_pass_run_off, d_pass_ndiag, d_run_meta, d_run_block,
+      d_run_node;
   size_t device_bytes() const;
 };
 
@@ -157,6 +175,9 @@ struct PhysParams {
   double riis_inv2eps[kMaxRiis]; // 1 / (2 eps_k)
 };
 
+constexpr int kChunkElems = 32;     // elements per chunk (one CTA pass of the assembly kernels)
+// Chunks the chunked double-float assembly kernel processes in one wave (resident CTAs x SMs).
+int64_t assemble_chunk_wave();
 // Elements the double-float assembly kernel processes in one wave over the whole device (resident
 // CTAs per SM x SMs x elements per CTA; GB300's 152 SMs x 3 x 32 when no device answers): the
 // quantum the element colouring is balanced to.

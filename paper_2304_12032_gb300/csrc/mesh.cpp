@@ -45,8 +45,11 @@ inline uint64_t morton(const double *p, const double *lo, double inv_span) {
 // among those free at all four of their nodes (in practice from the large early colours up into
 // the sparse late ones, which the greedy pass left free almost everywhere), so the colouring
 // stays valid whatever the moves achieve.  Deterministic; returns the colour count.
-int balance_colours(int64_t T, const std::vector<int32_t> &tt, const std::vector<int32_t> &eorder,
-                    std::vector<uint64_t> &used, std::vector<int32_t> &color, int C, int kWords, int64_t W) {
+// The same for any items with node sets (elements: 4 nodes; chunks: the nodes of their elements):
+// nodes_of(e, n) returns a pointer to item e's n nodes.
+template <class NodesOf>
+int balance_colours(int64_t T, NodesOf nodes_of, const std::vector<int32_t> &eorder, std::vector<uint64_t> &used,
+                    std::vector<int32_t> &color, int C, int kWords, int64_t W) {
   if (W <= 0 || C < 2) return C;
   std::vector<int64_t> sz(C, 0), k(C, 1);
   for (int64_t e = 0; e < T; ++e) sz[color[e]]++;
@@ -70,18 +73,21 @@ int balance_colours(int64_t T, const std::vector<int32_t> &tt, const std::vector
       const int32_t e = eorder[s];
       const int a = color[e];
       if (sz[a] <= k[a] * W) continue;
-      const int32_t *nd = &tt[4 * (int64_t)e];
+      int nn = 0;
+      const int32_t *nd = nodes_of(e, nn);
       int b = -1;
       int64_t room = 0;
       for (int c = 0; c < C; ++c) {
         const int64_t r = k[c] * W - sz[c];
         if (c == a || r <= room) continue;
-        if (bit(nd[0], c) || bit(nd[1], c) || bit(nd[2], c) || bit(nd[3], c)) continue;
+        bool busy = false;
+        for (int q = 0; q < nn && !busy; ++q) busy = bit(nd[q], c);
+        if (busy) continue;
         b = c;
         room = r;
       }
       if (b < 0) continue;
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < nn; ++q) {
         used[(size_t)nd[q] * kWords + a / 64] &= ~(1ULL << (a % 64));
         used[(size_t)nd[q] * kWords + b / 64] |= 1ULL << (b % 64);
       }
@@ -126,7 +132,9 @@ double signed_det(const double *x0, const double *x1, const double *x2, const do
 
 size_t Mesh::device_bytes() const {
   return d_xyz.bytes + d_xyz_hi.bytes + d_xyz_lo.bytes + d_conn.bytes + d_slot.bytes + d_rowptr.bytes + d_col.bytes + d_diag.bytes +
-         d_trans.bytes + d_comp_off.bytes + d_node_old.bytes + d_first.bytes;
+         d_trans.bytes + d_comp_off.bytes + d_node_old.bytes + d_first.bytes + d_color_elems.bytes +
+         d_chunk_elem_off.bytes + d_chunk_pass_off.bytes + d_pass_code.bytes + d_pass_run_off.bytes +
+         d_pass_ndiag.bytes + d_run_meta.bytes + d_run_block.bytes + d_run_node.bytes;
 }
 
 lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_in, int64_t n_tets,
@@ -273,16 +281,78 @@ lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_
     for (int a = 0; a < 4; ++a) used[(size_t)tt[4 * e + a] * kWords + c / 64] |= 1ULL << (c % 64);
     n_colors = std::max(n_colors, c + 1);
   }
-  n_colors = balance_colours(T, tt, eorder, used, color, n_colors, kWords, assemble_wave_elements());
-  // colour-sorted element order (Morton order kept inside each colour)
+  n_colors = balance_colours(
+      T, [&](int32_t e, int &n) { n = 4; return &tt[4 * (int64_t)e]; }, eorder, used, color, n_colors, kWords,
+      assemble_wave_elements());
+
+  // ---- chunks: kChunkElems consecutive elements of the Morton order, coloured greedily so that no
+  // two chunks of one colour share a node; the internal element order runs chunk by chunk in
+  // colour order (Morton order inside each chunk)
+  const int NE = kChunkElems;
+  const int64_t nch = (T + NE - 1) / NE;
+  std::vector<int32_t> ccolor(nch);
+  int n_ccolors = 0;
+  {
+    std::vector<uint64_t> cused((size_t)V * kWords, 0);
+    std::vector<int32_t> cn_off(nch + 1, 0), cn;
+    for (int64_t k = 0; k < nch; ++k) {
+      const size_t b0 = cn.size();
+      for (int64_t q = k * NE; q < std::min<int64_t>(T, (k + 1) * NE); ++q)
+        for (int a = 0; a < 4; ++a) cn.push_back(tt[4 * (int64_t)eorder[q] + a]);
+      std::sort(cn.begin() + b0, cn.end());
+      cn.erase(std::unique(cn.begin() + b0, cn.end()), cn.end());
+      cn_off[k + 1] = (int32_t)cn.size();
+      int c = -1;
+      for (int w = 0; w < kWords && c < 0; ++w) {
+        uint64_t busy = 0;
+        for (size_t i = b0; i < cn.size(); ++i) busy |= cused[(size_t)cn[i] * kWords + w];
+        if (~busy) c = 64 * w + __builtin_ctzll(~busy);
+      }
+      if (c < 0) {
+        set_error("lfx_mesh_create: chunk colouring needs more than %d colours", 64 * kWords);
+        return LFX_ERR_BAD_MESH;
+      }
+      ccolor[k] = c;
+      for (size_t i = b0; i < cn.size(); ++i) cused[(size_t)cn[i] * kWords + c / 64] |= 1ULL << (c % 64);
+      n_ccolors = std::max(n_ccolors, c + 1);
+    }
+    // chunk colours balanced to whole waves of the chunk kernel (one chunk per resident CTA)
+    std::vector<int32_t> korder(nch);
+    std::iota(korder.begin(), korder.end(), 0);
+    n_ccolors = balance_colours(
+        nch, [&](int32_t k, int &n) { n = cn_off[k + 1] - cn_off[k]; return cn.data() + cn_off[k]; }, korder, cused,
+        ccolor, n_ccolors, kWords, assemble_chunk_wave());
+  }
+  std::vector<int32_t> corder(nch);
+  std::iota(corder.begin(), corder.end(), 0);
+  std::stable_sort(corder.begin(), corder.end(), [&](int32_t a, int32_t b) { return ccolor[a] < ccolor[b]; });
+  m.chunk_color_off.assign(n_ccolors + 1, 0);
+  for (int64_t k = 0; k < nch; ++k) m.chunk_color_off[ccolor[k] + 1]++;
+  for (int c = 0; c < n_ccolors; ++c) m.chunk_color_off[c + 1] += m.chunk_color_off[c];
+  m.elem_old.resize(T);
+  m.chunk_elem_off.assign(nch + 1, 0);
+  {
+    int64_t w = 0;
+    for (int64_t i = 0; i < nch; ++i) {
+      const int64_t k = corder[i];
+      for (int64_t q = k * NE; q < std::min<int64_t>(T, (k + 1) * NE); ++q) m.elem_old[w++] = eorder[q];
+      m.chunk_elem_off[i + 1] = (int32_t)w;
+    }
+  }
+  std::vector<int32_t> elem_new(T);
+  for (int64_t i = 0; i < T; ++i) elem_new[m.elem_old[i]] = (int32_t)i;
+  // element colours (for the per-colour kernels): internal ids listed colour by colour, Morton order
+  // inside each colour
   m.color_off.assign(n_colors + 1, 0);
   for (int64_t e = 0; e < T; ++e) m.color_off[color[e] + 1]++;
   for (int c = 0; c < n_colors; ++c) m.color_off[c + 1] += m.color_off[c];
-  std::vector<int32_t> fill(m.color_off.begin(), m.color_off.end() - 1);
-  m.elem_old.resize(T);
-  for (int64_t s = 0; s < T; ++s) {
-    int32_t e = eorder[s];
-    m.elem_old[fill[color[e]]++] = e;
+  {
+    std::vector<int32_t> fill(m.color_off.begin(), m.color_off.end() - 1);
+    m.color_elems.resize(T);
+    for (int64_t q = 0; q < T; ++q) {
+      const int32_t e = eorder[q];
+      m.color_elems[fill[color[e]]++] = elem_new[e];
+    }
   }
   m.tets.resize(4 * T);
   m.quality.resize(T);
@@ -343,14 +413,16 @@ lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b)
         m.slot[16 * e + 4 * a + b] = find(m.tets[4 * e + a], m.tets[4 * e + b]);
-  // First writers: colours are assembled in element order, so the lowest-numbered element touching
-  // a block writes it first and can store its terms instead of adding them to a cleared matrix; the
-  // first writer of a node's right-hand-side row is the first writer of its diagonal block.
+  // First writers: colours are assembled in the order of color_elems, so the first element of that
+  // order touching a block writes it first and can store its terms instead of adding them to a
+  // cleared matrix; the first writer of a node's right-hand-side row is the first writer of its
+  // diagonal block.
   m.first.assign(T, 0);
   {
     std::vector<uint8_t> seen(m.nnzb, 0), node(V, 0);
     int64_t blocks = 0, nodes = 0;
-    for (int64_t e = 0; e < T; ++e) {
+    for (int64_t i = 0; i < T; ++i) {
+      const int64_t e = m.color_elems[i];
       for (int q = 0; q < 16; ++q) {
         const int32_t s = m.slot[16 * e + q];
         if (!seen[s]) {
@@ -367,6 +439,87 @@ lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_
     }
     m.all_blocks_touched = blocks == m.nnzb;
     m.all_nodes_touched = nodes == V;
+  }
+  // ---- chunk tables: each chunk's 16 block contributions per element grouped into runs by matrix
+  // block, packed first-fit-decreasing into passes of 4 NE slots (no run straddles two passes),
+  // diagonal runs first in each pass; a run's first-writer flag marks the first chunk (in
+  // processing order) touching its block
+  {
+    const int PS = 4 * NE;
+    std::vector<uint8_t> seenb(m.nnzb, 0);
+    m.chunk_pass_off.assign(nch + 1, 0);
+    m.pass_code.clear();
+    m.pass_run_off.assign(1, 0);
+    m.pass_ndiag.clear();
+    m.run_meta.clear();
+    m.run_block.clear();
+    m.run_node.clear();
+    struct Run {
+      int32_t block, node, start, len;
+      bool diag;
+    };
+    std::vector<std::pair<int32_t, uint16_t>> cs;
+    std::vector<Run> runs;
+    std::vector<std::vector<int>> passes;
+    std::vector<int> fillp;
+    for (int64_t k = 0; k < nch; ++k) {
+      const int64_t e0 = m.chunk_elem_off[k], e1 = m.chunk_elem_off[k + 1];
+      cs.clear();
+      for (int64_t e = e0; e < e1; ++e)
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b)
+            cs.push_back({m.slot[16 * e + 4 * a + b], (uint16_t)(((e - e0) << 4) | (a << 2) | b)});
+      std::stable_sort(cs.begin(), cs.end(),
+                       [](const std::pair<int32_t, uint16_t> &x, const std::pair<int32_t, uint16_t> &y) {
+                         return x.first < y.first;
+                       });
+      runs.clear();
+      for (size_t i = 0; i < cs.size();) {
+        size_t j = i;
+        while (j < cs.size() && cs[j].first == cs[i].first) ++j;
+        const uint16_t c0 = cs[i].second;
+        const int a = (c0 >> 2) & 3, b = c0 & 3;
+        Run r{cs[i].first, -1, (int32_t)i, (int32_t)(j - i), a == b};
+        if (r.diag) r.node = m.tets[4 * (e0 + (c0 >> 4)) + a];
+        runs.push_back(r);
+        i = j;
+      }
+      std::vector<int> ord(runs.size());
+      std::iota(ord.begin(), ord.end(), 0);
+      std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return runs[x].len > runs[y].len; });
+      passes.clear();
+      fillp.clear();
+      for (int ri : ord) {
+        size_t p = 0;
+        while (p < passes.size() && fillp[p] + runs[ri].len > PS) ++p;
+        if (p == passes.size()) {
+          passes.emplace_back();
+          fillp.push_back(0);
+        }
+        passes[p].push_back(ri);
+        fillp[p] += runs[ri].len;
+      }
+      for (auto &pl : passes) {
+        std::stable_sort(pl.begin(), pl.end(), [&](int x, int y) { return runs[x].diag && !runs[y].diag; });
+        const size_t base = m.pass_code.size();
+        m.pass_code.resize(base + PS, 0xffff);
+        int at = 0, ndiag = 0;
+        for (int ri : pl) {
+          const Run &r = runs[ri];
+          for (int q = 0; q < r.len; ++q) m.pass_code[base + at + q] = cs[r.start + q].second;
+          const bool first = !seenb[r.block];
+          seenb[r.block] = 1;
+          m.run_meta.push_back((uint16_t)(at | (r.len << 8) | (first ? 1 << 14 : 0) | (r.diag ? 1 << 15 : 0)));
+          m.run_block.push_back(r.block);
+          m.run_node.push_back(r.node);
+          ndiag += r.diag;
+          at += r.len;
+        }
+        m.pass_ndiag.push_back(ndiag);
+        m.pass_run_off.push_back((int32_t)m.run_block.size());
+      }
+      m.chunk_pass_off[k + 1] = m.chunk_pass_off[k] + (int32_t)passes.size();
+    }
   }
 
   // ---- boundary faces: internal numbering, outward orientation from the owning tetrahedron
@@ -419,6 +572,20 @@ lfx_status upload_mesh(Mesh &m) {
   LFX_TRY(m.d_node_old.alloc(sizeof(int32_t) * V));
   LFX_TRY(m.d_first.alloc(sizeof(uint16_t) * std::max<int64_t>(T, 1)));
   if (T > 0) LFX_CUDA_TRY(cudaMemcpy(m.d_first.p, m.first.data(), sizeof(uint16_t) * T, cudaMemcpyHostToDevice));
+  auto up = [](DBuf &d, const void *src, size_t bytes) -> lfx_status {
+    LFX_TRY(d.alloc(std::max<size_t>(bytes, 16)));
+    if (bytes) LFX_CUDA_TRY(cudaMemcpy(d.p, src, bytes, cudaMemcpyHostToDevice));
+    return LFX_OK;
+  };
+  LFX_TRY(up(m.d_color_elems, m.color_elems.data(), sizeof(int32_t) * m.color_elems.size()));
+  LFX_TRY(up(m.d_chunk_elem_off, m.chunk_elem_off.data(), sizeof(int32_t) * m.chunk_elem_off.size()));
+  LFX_TRY(up(m.d_chunk_pass_off, m.chunk_pass_off.data(), sizeof(int32_t) * m.chunk_pass_off.size()));
+  LFX_TRY(up(m.d_pass_code, m.pass_code.data(), sizeof(uint16_t) * m.pass_code.size()));
+  LFX_TRY(up(m.d_pass_run_off, m.pass_run_off.data(), sizeof(int32_t) * m.pass_run_off.size()));
+  LFX_TRY(up(m.d_pass_ndiag, m.pass_ndiag.data(), sizeof(int32_t) * m.pass_ndiag.size()));
+  LFX_TRY(up(m.d_run_meta, m.run_meta.data(), sizeof(uint16_t) * m.run_meta.size()));
+  LFX_TRY(up(m.d_run_block, m.run_block.data(), sizeof(int32_t) * m.run_block.size()));
+  LFX_TRY(up(m.d_run_node, m.run_node.data(), sizeof(int32_t) * m.run_node.size()));
   LFX_CUDA_TRY(cudaMemcpy(m.d_node_old.p, m.node_old.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_xyz.p, x4.data(), m.d_xyz.bytes, cudaMemcpyHostToDevice));
   // FP32 high and low parts of the coordinates (x = hi + lo to 48 bits) for double-float assembly

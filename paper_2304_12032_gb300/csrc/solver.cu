@@ -582,6 +582,22 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kRowGroup;
   const int lane = threadIdx.x % kRowGroup;
   T acc[3] = {T(0), T(0), T(0)};
+  // the row's own vector entries, loaded before the row's blocks so that their latency overlaps
+  // the block loads and gathers
+  const bool owner = row < A.V && lane == 0;
+  typename Vec4T<T>::type df{}, rr{}, xx{}, dold{}, dn{}, bv{};
+  if (owner) {
+    df = ld4(dinvF, row);
+    if (mode == 0) {
+      dn = ld4(d_new, row);
+    } else {
+      rr = ld4(r, row);
+      xx = ld4(x, row);
+      dn = ld4(d_new, row);
+      if constexpr (kFirst) bv = ld4(b0, row);
+      else dold = ld4(d_old, row);
+    }
+  }
   if (row < A.V) {
     constexpr int U = LFX_U_F;
     T f[U][9];
@@ -613,28 +629,20 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF
 #pragma unroll
   for (int i = 0; i < 3; ++i) acc[i] = group_sum(acc[i]);
   double nrm = 0.0;
-  if (row < A.V && lane == 0) {
-    const auto df = ld4(dinvF, row);
+  if (owner) {
     if (mode == 0) {
-      auto o = ld4(d_new, row);
+      auto o = dn;
       o.x = df.x * acc[0]; o.y = df.y * acc[1]; o.z = df.z * acc[2];
       st4(d_new, row, o);
       nrm = (double)o.x * o.x + (double)o.y * o.y + (double)o.z * o.z;
     } else {
       const T c1 = coef_t<T>(cf->f_c1[k], cf->f_c1f[k]), c2 = coef_t<T>(cf->f_c2[k], cf->f_c2f[k]);
-      auto rr = ld4(r, row);
-      typename Vec4T<T>::type dold;
-      auto xx = ld4(x, row);
       if constexpr (kFirst) {
         const T s0 = coef_t<T>(cf->f_init, cf->f_initf);
-        const auto bv = ld4(b0, row);
         rr.x = df.x * bv.x; rr.y = df.y * bv.y; rr.z = df.z * bv.z;
         dold.x = s0 * rr.x; dold.y = s0 * rr.y; dold.z = s0 * rr.z;
         xx.x = dold.x; xx.y = dold.y; xx.z = dold.z;
-      } else {
-        dold = ld4(d_old, row);
       }
-      auto dn = ld4(d_new, row);
       rr.x -= df.x * acc[0]; rr.y -= df.y * acc[1]; rr.z -= df.z * acc[2];
       dn.x = c1 * dold.x + c2 * rr.x; dn.y = c1 * dold.y + c2 * rr.y; dn.z = c1 * dold.z + c2 * rr.z;
       xx.x += dn.x; xx.y += dn.y; xx.z += dn.z;
@@ -2231,9 +2239,25 @@ lfx_status ASimple<S, T>::apply_view(cudaStream_t st, const View &A, const T *r,
   } else {
     pdl_launch(f_init_kernel<T>, vg, kThreads, 0, st, V, dinvF.as<T>(), r, R.as<T>(), d[0], X.as<T>(), cf, ks);
   }
+  // one application per step is timed (the counter is reset per step): an event between two
+  // launches costs the overlap of programmatic dependent launch there
+  const bool timed = cfg.f_steps > 2 && n_fev == 0;
+  if (timed) {
+    if (n_fev + 2 > (int)fev.size())
+      for (int q = 0; q < 32; ++q) {
+        cudaEvent_t e;
+        LFX_CUDA_TRY(cudaEventCreate(&e));
+        fev.push_back(e);
+      }
+    LFX_CUDA_TRY(cudaEventRecord(fev[n_fev], st));
+  }
   for (int k = 2; k < cfg.f_steps; ++k)
     pdl_launch(f_step_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), d[(k - 1) & 1], d[k & 1], R.as<T>(),
                                                  X.as<T>(), cf, k, 1, nullptr, ks, nullptr);
+  if (timed) {
+    LFX_CUDA_TRY(cudaEventRecord(fev[n_fev + 1], st));
+    n_fev += 2;
+  }
   // z_p ~= S^-1 (r_p - D z_u*): Chebyshev/Jacobi steps on S, or one AMG V-cycle
   if (cfg.s_kind == LFX_SMOOTH_AMG && !amg_ready) {
     set_error("aSIMPLE: the Schur AMG hierarchy has not been built");
@@ -2511,6 +2535,30 @@ lfx_status ASimple<S, T>::vcycle(cudaStream_t st, int l, const KState *ks) {
   for (int k = 1; k < cfg.s_steps; ++k) cheb_step(k);
   note_launches(6 + 2 * (cfg.s_steps - 1));
   LFX_CUDA_TRY(cudaGetLastError());
+  return LFX_OK;
+}
+
+template <class S, class T>
+ASimple<S, T>::~ASimple() {
+  for (cudaEvent_t e : fev) cudaEventDestroy(e);
+}
+
+// Median duration of one plain F pass over the applications timed since the last read (the
+// median discards the applications queued after a solve had converged, whose kernels return at
+// once), and the number of passes timed.
+template <class S, class T>
+lfx_status ASimple<S, T>::read_f_timing(float *median_ms_per_pass, int *passes) {
+  std::vector<float> per;
+  for (int i = 0; i + 1 < n_fev; i += 2) {
+    LFX_CUDA_TRY(cudaEventSynchronize(fev[i + 1]));
+    float t = 0.0f;
+    LFX_CUDA_TRY(cudaEventElapsedTime(&t, fev[i], fev[i + 1]));
+    per.push_back(t / (float)(cfg.f_steps - 2));
+  }
+  n_fev = 0;
+  std::sort(per.begin(), per.end());
+  if (median_ms_per_pass) *median_ms_per_pass = per.empty() ? 0.0f : per[per.size() / 2];
+  if (passes) *passes = (int)per.size() * std::max(cfg.f_steps - 2, 0);
   return LFX_OK;
 }
 
@@ -2868,9 +2916,18 @@ void Gmres<S, T>::apply_rank1(cudaStream_t st, const T *x, T *y, double sign, co
   note_launches(2);
 }
 
-// The Arnoldi product w = A z, bracketed by CUDA events for the SpMV timing statistics.
+// The Arnoldi product w = A z, the first kTimedSpmv of them after each reset of n_tev bracketed by
+// CUDA events for the SpMV timing statistics.
+constexpr int kTimedSpmv = 4;
 template <class S, class T>
 lfx_status Gmres<S, T>::timed_spmv(cudaStream_t st, const BsrView<S> &A, const T *z, T *w, const KState *ks) {
+  if (n_tev >= 2 * kTimedSpmv) {
+    // enough samples in this step: an event between two launches costs the overlap of
+    // programmatic dependent launch there
+    arnoldi_spmv(st, A, z, w, ks);
+    if (r1.n_tags > 0) apply_rank1(st, z, w, 1.0, ks);
+    return LFX_OK;
+  }
   if (n_tev + 2 > (int)tev.size()) {
     for (int q = 0; q < 64; ++q) {
       cudaEvent_t e;

@@ -103,6 +103,14 @@ struct ASimple {
   int coop_grid = 0;   // > 0: the coarse V-cycle runs as one cooperative launch of this many CTAs
   bool amg_ready = false;
   double amg_alpha = 1.0;
+  // CUDA-event timing of the plain F passes (velocity smoothing steps 2 .. f_steps-1, the fused
+  // first step excluded) of the first application after each reset of n_fev, kept until read_f_timing
+  std::vector<cudaEvent_t> fev;
+  int n_fev = 0;
+  lfx_status read_f_timing(float *median_ms_per_pass, int *passes);
+  ASimple() = default;
+  ASimple(const ASimple &) = delete;
+  ~ASimple();
   lfx_status upload_amg(const AmgHost &H);
   lfx_status vcycle(cudaStream_t st, int l, const KState *ks);
   // The V-cycle below level 0 (levels 1 .. L-1) for amg[1].b: one cooperative launch, or the

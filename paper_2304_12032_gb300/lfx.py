@@ -27,6 +27,7 @@ TIME = {"constant": 0, "pulsatile": 1, "ramp": 2, "fourier": 3}
 KIND = {"noslip": 0, "dirichlet": 1, "nodal": 2, "neumann": 3, "resistance": 4}
 PROFILE = {"uniform": 0, "parabolic": 1, "womersley": 2}
 PREC = {"fp64": 0, "mixed": 1}
+ASM = {"auto": 0, "colors": 1, "chunks": 2, "persistent": 3}
 SMOOTH = {"jacobi": 0, "chebyshev": 1, "amg": 2}
 
 
@@ -64,7 +65,7 @@ class lfx_options(ctypes.Structure):
                 ("amg_theta", ctypes.c_double), ("amg_alpha", ctypes.c_double),
                 ("batch_normalize", ctypes.c_int32), ("batch_segmented", ctypes.c_int32),
                 ("inner_adaptive", ctypes.c_int32), ("implicit", ctypes.c_int32),
-                ("newton_max_iters", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("newton_max_iters", ctypes.c_int32), ("assembly", ctypes.c_int32),
                 ("newton_rtol", ctypes.c_double)]
 
 
@@ -81,7 +82,9 @@ class lfx_step_stats(ctypes.Structure):
                 ("ms_solve", ctypes.c_float), ("ms_total", ctypes.c_float), ("converged", ctypes.c_int32),
                 ("ms_assembly_kernels", ctypes.c_float), ("n_assembly_launches", ctypes.c_int32),
                 ("ms_spmv", ctypes.c_float), ("n_spmv", ctypes.c_int32), ("newton_iterations", ctypes.c_int32),
-                ("ms_newton_assembly", ctypes.c_float), ("reserved", ctypes.c_int32)]
+                ("ms_newton_assembly", ctypes.c_float), ("n_fpass", ctypes.c_int32),
+                ("ms_fpass_median", ctypes.c_float), ("assembly_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -104,11 +107,14 @@ _SIGS = {
     "lfx_mesh_get_info": ([_P, ctypes.POINTER(lfx_mesh_info)], ctypes.c_int32),
     "lfx_mesh_get_pattern": ([_P, _LP, _IP], ctypes.c_int32),
     "lfx_mesh_get_colors": ([_P, _IP], ctypes.c_int32),
+    "lfx_mesh_get_chunks": ([_P, _LP, _IP, _IP, _IP, _IP, ctypes.POINTER(ctypes.c_uint16), _IP,
+                             ctypes.POINTER(ctypes.c_uint16), _IP, _IP], ctypes.c_int32),
     "lfx_options_default": ([ctypes.POINTER(lfx_options)], None),
     "lfx_problem_create": ([_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                             ctypes.POINTER(lfx_bc), ctypes.c_int32, ctypes.POINTER(lfx_riis), ctypes.c_int32,
                             ctypes.POINTER(lfx_options), ctypes.POINTER(_P)], ctypes.c_int32),
     "lfx_problem_destroy": ([_P], None),
+    "lfx_problem_assembly_tuning": ([_P, _IP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int32),
     "lfx_state_create": ([_P, _DP, _DP, ctypes.c_double, ctypes.POINTER(_P)], ctypes.c_int32),
     "lfx_state_destroy": ([_P], None),
     "lfx_set_stream": ([_P, _P], ctypes.c_int32),
@@ -214,6 +220,8 @@ def default_options(**kw) -> lfx_options:
             v = PREC[v]
         if k in ("f_smoother", "s_smoother") and isinstance(v, str):
             v = SMOOTH[v]
+        if k == "assembly" and isinstance(v, str):
+            v = ASM[v]
         if k == "f":
             for i in range(3):
                 o.f[i] = v[i]
@@ -310,6 +318,29 @@ class Mesh:
         _check(library().lfx_mesh_get_colors(self.h, _i(c)))
         return c
 
+    def chunks(self) -> dict:
+        """The chunked assembly's tables (see lfx_mesh_get_chunks)."""
+        lib = library()
+        sz = np.zeros(5, dtype=np.int64)
+        _check(lib.lfx_mesh_get_chunks(self.h, sz.ctypes.data_as(_LP), None, None, None, None, None, None, None,
+                                       None, None))
+        nch, ncc, npass, nrun, ps = (int(v) for v in sz)
+        T = self.info()["n_tets"]
+        out = {"elem_old": np.zeros(T, np.int32), "chunk_elem_off": np.zeros(nch + 1, np.int32),
+               "chunk_color_off": np.zeros(ncc + 1, np.int32), "chunk_pass_off": np.zeros(nch + 1, np.int32),
+               "pass_code": np.zeros((max(npass, 1), ps), np.uint16), "pass_run_off": np.zeros(npass + 1, np.int32),
+               "run_meta": np.zeros(max(nrun, 1), np.uint16), "run_row": np.zeros(max(nrun, 1), np.int32),
+               "run_col": np.zeros(max(nrun, 1), np.int32)}
+        u16 = ctypes.POINTER(ctypes.c_uint16)
+        _check(lib.lfx_mesh_get_chunks(self.h, sz.ctypes.data_as(_LP), _i(out["elem_old"]), _i(out["chunk_elem_off"]),
+                                       _i(out["chunk_color_off"]), _i(out["chunk_pass_off"]),
+                                       out["pass_code"].ctypes.data_as(u16), _i(out["pass_run_off"]),
+                                       out["run_meta"].ctypes.data_as(u16), _i(out["run_row"]), _i(out["run_col"])))
+        out["pass_code"] = out["pass_code"][:npass]
+        for k in ("run_meta", "run_row", "run_col"):
+            out[k] = out[k][:nrun]
+        return out
+
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
             _lib.lfx_mesh_destroy(self.h)
@@ -337,6 +368,14 @@ class Problem:
         self.h = _P()
         _check(library().lfx_problem_create(mesh.h, rho, mu, dt, bdf_order, arr, len(bcs), rarr, len(riis),
                                             ctypes.byref(self.options), ctypes.byref(self.h)))
+
+    def assembly_tuning(self):
+        """(launch shape in use, {shape: ms per assembly} of the autotuner's timings)."""
+        mode = ctypes.c_int32()
+        ms = (ctypes.c_float * 3)()
+        _check(library().lfx_problem_assembly_tuning(self.h, ctypes.byref(mode), ms))
+        names = ("colors", "chunks", "persistent")
+        return mode.value, {names[i]: ms[i] for i in range(3) if ms[i] > 0}
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

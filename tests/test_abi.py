@@ -150,3 +150,61 @@ def test_outlet_condition_arguments_are_checked_before_allocation(L, bc):
     with pytest.raises(L.LfxError) as err:
         L.Problem(mesh, 1.06, 0.035, 1e-3, 2, [L.BC(**bc)], [])
     assert err.value.status == L.LFX_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("which", ["cylinder", "bifurcation"])
+def test_chunk_tables(L, which):
+    """The chunked assembly's tables (host, no GPU): every element in exactly one chunk of at most 32;
+    chunks of one colour share no node; every (element, a, b) block contribution appears exactly once
+    in its chunk's passes, in a run whose matrix block is (node a, node b); runs do not straddle
+    passes; each block has exactly one first-writer run, the one in the lowest chunk colour."""
+    from synthetic import bifurcation
+
+    m = cylinder(1.0, 3.0, n_tets=20000, seed=7) if which == "cylinder" else bifurcation(n_tets=20000, seed=1002)
+    mesh = L.Mesh.from_synthetic(m)
+    ch = mesh.chunks()
+    T = m.n_tets
+    eo, off, coff = ch["elem_old"], ch["chunk_elem_off"], ch["chunk_color_off"]
+    assert np.array_equal(np.sort(eo), np.arange(T)) and off[0] == 0 and off[-1] == T
+    assert np.diff(off).max() <= 32 and np.diff(off).min() >= 1
+    tets = m.tets[eo]                                      # internal element -> caller nodes
+    nch = off.size - 1
+    ccol = np.zeros(nch, np.int64)
+    for c in range(coff.size - 1):
+        ccol[coff[c]:coff[c + 1]] = c
+        nodes = [np.unique(tets[off[k]:off[k + 1]].ravel()) for k in range(coff[c], coff[c + 1])]
+        alln = np.concatenate(nodes)
+        assert np.unique(alln).size == alln.size, c           # no node in two chunks of one colour
+    pcode, poff, roff, meta = ch["pass_code"], ch["chunk_pass_off"], ch["pass_run_off"], ch["run_meta"]
+    PS = pcode.shape[1]
+    first_of = {}
+    for k in range(nch):
+        seen = np.zeros((off[k + 1] - off[k], 4, 4), np.int64)
+        for p in range(poff[k], poff[k + 1]):
+            codes = pcode[p]
+            covered = np.zeros(PS, bool)
+            for r in range(roff[p], roff[p + 1]):
+                st0, ln = int(meta[r]) & 0xff, (int(meta[r]) >> 8) & 63
+                assert ln >= 1 and st0 + ln <= PS and not covered[st0:st0 + ln].any()
+                covered[st0:st0 + ln] = True
+                cc = codes[st0:st0 + ln].astype(np.int64)
+                le, a, b = cc >> 4, (cc >> 2) & 3, cc & 3
+                rows = tets[off[k] + le, a]
+                cols = tets[off[k] + le, b]
+                assert (rows == ch["run_row"][r]).all() and (cols == ch["run_col"][r]).all()
+                assert bool(int(meta[r]) >> 15) == bool((a == b).all()) and (a == b).all() == (a == b).any()
+                np.add.at(seen, (le, a, b), 1)
+                if (int(meta[r]) >> 14) & 1:
+                    key = (int(ch["run_row"][r]), int(ch["run_col"][r]))
+                    assert key not in first_of
+                    first_of[key] = ccol[k]
+            assert (codes[~covered] == 0xffff).all()
+        assert (seen == 1).all(), k
+    # one first writer per block, in the lowest chunk colour touching it
+    lowest = {}
+    for k in range(nch):
+        for p in range(poff[k], poff[k + 1]):
+            for r in range(roff[p], roff[p + 1]):
+                key = (int(ch["run_row"][r]), int(ch["run_col"][r]))
+                lowest[key] = min(lowest.get(key, 1 << 30), ccol[k])
+    assert first_of == lowest
