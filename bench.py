@@ -226,8 +226,8 @@ def kernel_rooflines(stats, T, V, nnzb, prec, bf16=True):
             "traffic": int(SPMV32_DRAM_BYTES_PER_BLOCK * nnzb) if sv == 4 else None, "peak_source": src + " (burst copy)",
             "ms_per_launch": round(spmv_ms, 5), "launches_per_step": round(its, 1),
             "ms_per_step": round(spmv_ms * its, 4),
-            "timing": "CUDA events around the first 4 Arnoldi SpMV launches of each step; launches per step "
-                      "= Arnoldi steps",
+            "timing": "CUDA events around one Arnoldi SpMV launch in five (at most 4 per step); launches "
+                      "per step = Arnoldi steps",
             "algorithmic_bytes_per_launch": int(spmv_bytes)}
     kernels = {"assembly": asm, "spmv": spmv}
     if fpass:
@@ -304,7 +304,8 @@ def run_gpu(args):
         clk = clocks.stop()
         _, ms = replica_throughput(ms, args.steps, dist, "cuda")
         u, p = st.get()
-        results[prec] = dict(ms=ms, stats=stats, launches=launches, clocks=clk, u=u, p=p, st=st, mesh=mesh)
+        results[prec] = dict(ms=ms, stats=stats, launches=launches, clocks=clk, u=u, p=p, st=st, mesh=mesh,
+                             tuning=prob.assembly_tuning())
     prim = results["mixed"] if "mixed" in results else results[args.precision]
     prim_prec = "mixed" if "mixed" in results else args.precision
     info = prim["mesh"].info()
@@ -344,6 +345,8 @@ def run_gpu(args):
                      "solve": round(statistics.mean(s["ms_solve"] for s in stats), 3)},
         "roofline": roof,
         "kernels": kernels,
+        "assembly_autotuner": {"chosen": {1: "colors", 2: "chunks", 3: "persistent"}.get(prim["tuning"][0], "none"),
+                               "ms_per_assembly": {k: round(v, 4) for k, v in prim["tuning"][1].items()}},
         "e2e": {"value": round(1e3 / e2e_ms * world, 3), "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(prim["launches"]),

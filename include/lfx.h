@@ -289,8 +289,9 @@ typedef struct lfx_step_stats {
   int32_t converged;
   float ms_assembly_kernels;    /* the coloured assembly launches alone (CUDA events)          */
   int32_t n_assembly_launches;  /* launches of the assembly kernel in this step (= colours)    */
-  float ms_spmv;                /* device time of the first (up to 4) Arnoldi block SpMV launches
-                                   of the (inner) Krylov solve in this step (CUDA events)         */
+  float ms_spmv;                /* device time of a sample of the Arnoldi block SpMV launches of
+                                   the (inner) Krylov solve in this step: one in five, at most four
+                                   (CUDA events)                                                 */
   int32_t n_spmv;               /* their number (FP64 matrix on the FP64 path, FP32 in mixed)   */
   int32_t newton_iterations;    /* Newton updates taken (fully implicit formulation), else 0    */
   float ms_newton_assembly;     /* device time of the Newton Jacobian assemblies (CUDA events)  */
@@ -362,6 +363,11 @@ lfx_status lfx_debug_assemble(lfx_state *state, int32_t apply_bcs, double *block
  * (block values as in lfx_debug_assemble) and the right-hand side J(U) U - R(U) with the Neumann data,
  * both before Dirichlet rows; the BDF fields are those of the state's next step.  FP64 host buffers. */
 lfx_status lfx_debug_assemble_newton(lfx_state *state, const double *U, double *blocks, double *rhs);
+/* Failure path of the persistent assembly, for tests: one assembly with the first grid-wide wait's
+ * target set out of reach and its poll limit at 4096, so that the wait runs out; every CTA then
+ * returns.  LFX_ERR_TIMEOUT is the expected result; the state stays usable (the next lfx_step
+ * assembles anew).  Needs a problem whose assembly is the persistent launch (options.assembly).  */
+lfx_status lfx_debug_persistent_timeout(lfx_state *state);
 /* y = A x with the last assembled matrix; x, y [n_nodes][4] FP64 host buffers, caller numbering. */
 lfx_status lfx_debug_spmv(lfx_state *state, const double *x, double *y);
 /* z = P^-1 r with the aSIMPLE preconditioner of the last assembled matrix (FP64 path);

@@ -193,6 +193,7 @@ struct lfx_state {
   DBuf asm_sync;
   int *asm_err_host = nullptr;
   int asm_mode_used = 0;
+  bool force_timeout = false;   // tests: make the persistent assembly's first grid-wide wait run out
   int64_t n_bnd = 0;
   D4 *dlevel(int l) { return dhist[(dhead + l) % sigma].as<D4>(); }
   ~lfx_state() {
@@ -1006,6 +1007,7 @@ lfx_status lfx_state_create(lfx_problem *pb, const double *u_hist, const double 
   cfg.s_omega = o.s_omega;
   cfg.s_ratio = o.s_ratio;
   cfg.n_power = o.n_power;
+  s->pc64.time_f = s->pc32.time_f = s->pcbf.time_f = true;   // F-pass timing for the step statistics
   if (o.precision == LFX_PREC_MIXED) {
     LFX_TRY(s->vals32.alloc(sizeof(float) * 16 * m.nnzb));
     LFX_TRY(s->vals_lo.alloc(sizeof(float) * 16 * m.nnzb));
@@ -1229,7 +1231,7 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs, bool newton = fa
         return launch_assemble_chunks<dd, float>(st, A, pb->P, CA, m.chunk_color_off.data(), n_cc,
                                                  s->vals32.as<float>());
       return launch_assemble_persistent<dd, float>(st, A, pb->P, CA, pb->d_chunk_color_off.as<int32_t>(), n_cc,
-                                                   s->vals32.as<float>(), barrier, err);
+                                                   s->vals32.as<float>(), barrier, err, s->force_timeout);
     }
     if (newton || mode == LFX_ASM_COLORS)
       return launch_assemble<double, double>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
@@ -1238,7 +1240,7 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs, bool newton = fa
       return launch_assemble_chunks<double, double>(st, A, pb->P, CA, m.chunk_color_off.data(), n_cc,
                                                     s->vals64.as<double>());
     return launch_assemble_persistent<double, double>(st, A, pb->P, CA, pb->d_chunk_color_off.as<int32_t>(), n_cc,
-                                                      s->vals64.as<double>(), barrier, err);
+                                                      s->vals64.as<double>(), barrier, err, s->force_timeout);
   };
   int mode = LFX_ASM_COLORS;
   if (!newton) {
@@ -1801,9 +1803,9 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   LFX_TRY(prepare_precond(s));
   int its = 0, outer = 0;
   double rel = 0.0;
-  s->gm64.n_tev = 0;
-  s->gm32.n_tev = 0;
-  s->gmdd.n_tev = 0;
+  s->gm64.n_tev = s->gm64.n_spmv_calls = 0;
+  s->gm32.n_tev = s->gm32.n_spmv_calls = 0;
+  s->gmdd.n_tev = s->gmdd.n_spmv_calls = 0;
   s->pc64.n_fev = 0;
   s->pc32.n_fev = 0;
   s->pcbf.n_fev = 0;
@@ -1951,6 +1953,36 @@ lfx_status lfx_debug_assemble_newton(lfx_state *s, const double *U, double *bloc
   std::vector<int32_t> ci;
   user_pattern(m, rp, ci, ib);
   for (int64_t q = 0; q < m.nnzb; ++q) memcpy(blocks + 16 * q, v.data() + 16 * ib[q], 16 * sizeof(double));
+  return LFX_OK;
+}
+
+lfx_status lfx_debug_persistent_timeout(lfx_state *s) {
+  clear_error();
+  if (!s) {
+    set_error("lfx_debug_persistent_timeout: NULL state");
+    return LFX_ERR_INVALID_ARG;
+  }
+  lfx_problem *pb = s->pb;
+  int mode = 0;
+  {
+    std::lock_guard<std::mutex> lk(pb->tune_mu);
+    mode = pb->asm_mode;
+  }
+  if (mode != LFX_ASM_PERSISTENT) {
+    set_error("lfx_debug_persistent_timeout: the problem's assembly is not the persistent launch");
+    return LFX_ERR_INVALID_ARG;
+  }
+  s->force_timeout = true;
+  lfx_status rc = assemble_system(s, true);
+  s->force_timeout = false;
+  LFX_TRY(rc);
+  LFX_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->assembled = false;
+  if (s->asm_err_host && *s->asm_err_host) {
+    *s->asm_err_host = 0;
+    set_error("persistent assembly: a grid-wide wait gave up");
+    return LFX_ERR_TIMEOUT;
+  }
   return LFX_OK;
 }
 

@@ -979,7 +979,7 @@ __global__ void __launch_bounds__(kCta, MinCtas<R>::value) assemble_chunk_kernel
 // The wait is bounded: after kBarrierSpins polls it sets *err and gives up, and so does every CTA
 // that finds *err set, so that no CTA waits on one that has left.  Returns false on failure.
 constexpr unsigned kBarrierSpins = 1u << 24;
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, int *err) {
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, int *err, unsigned max_spins) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -991,7 +991,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, i
       unsigned seen;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(count) : "memory");
       if (seen >= target) break;
-      if (*(volatile int *)err != 0 || ++spins > kBarrierSpins) {
+      if (*(volatile int *)err != 0 || ++spins > max_spins) {
         atomicExch(err, 1);
         good = 0;
         break;
@@ -1004,16 +1004,19 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, i
   return ok != 0;
 }
 
-// every chunk colour in one cooperative launch, colours separated by grid-wide barriers
+// every chunk colour in one cooperative launch, colours separated by grid-wide barriers (a test
+// can pass unreachable > 0 with a small max_spins to make the first wait run out)
 template <class R, class S>
 __global__ void __launch_bounds__(kCta, MinCtas<R>::value) assemble_chunks_persistent_kernel(
     AssembleArgs A, PhysParams P, PhysR<R> Q, ChunkArgs C, const int32_t *color_off, int n_colors, S *vals,
-    unsigned *barrier, int *err) {
+    unsigned *barrier, int *err, unsigned unreachable, unsigned max_spins) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ChunkShared<R> &cs = *reinterpret_cast<ChunkShared<R> *>(smem_raw);
   for (int c = 0; c < n_colors; ++c) {
     chunk_range<R, S>(A, P, Q, C, color_off[c], color_off[c + 1], vals, cs);
-    if (c + 1 < n_colors && !grid_barrier(barrier, (unsigned)(c + 1) * gridDim.x, err)) return;
+    if (c + 1 < n_colors &&
+        !grid_barrier(barrier, (unsigned)(c + 1) * gridDim.x + unreachable, err, max_spins))
+      return;
   }
 }
 
@@ -1322,7 +1325,7 @@ template lfx_status launch_assemble_chunks<dd, float>(cudaStream_t, const Assemb
 template <class R, class S>
 lfx_status launch_assemble_persistent(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
                                       const int32_t *d_chunk_color_off, int n_colors, S *vals, unsigned *barrier,
-                                      int *err) {
+                                      int *err, bool force_timeout) {
   const PhysR<R> Q = phys_r<R>(P);
   const size_t smem = sizeof(ChunkShared<R>);
   static bool attr_set = false;
@@ -1344,8 +1347,9 @@ lfx_status launch_assemble_persistent(cudaStream_t st, const AssembleArgs &A, co
   LFX_CUDA_TRY(cudaMemsetAsync(barrier, 0, sizeof(unsigned), st));
   LFX_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
   const int grid = nsm * per_sm;
+  unsigned unreachable = force_timeout ? 1u : 0u, max_spins = force_timeout ? (1u << 12) : kBarrierSpins;
   void *args[] = {(void *)&A, (void *)&P, (void *)&Q, (void *)&C, (void *)&d_chunk_color_off, (void *)&n_colors,
-                  (void *)&vals, (void *)&barrier, (void *)&err};
+                  (void *)&vals, (void *)&barrier, (void *)&err, (void *)&unreachable, (void *)&max_spins};
   LFX_CUDA_TRY(cudaLaunchCooperativeKernel((void *)assemble_chunks_persistent_kernel<R, S>, dim3(grid), dim3(kCta), args,
                                            smem, st));
   note_launches(1);
@@ -1353,10 +1357,10 @@ lfx_status launch_assemble_persistent(cudaStream_t st, const AssembleArgs &A, co
 }
 template lfx_status launch_assemble_persistent<double, double>(cudaStream_t, const AssembleArgs &, const PhysParams &,
                                                                const ChunkArgs &, const int32_t *, int, double *,
-                                                               unsigned *, int *);
+                                                               unsigned *, int *, bool);
 template lfx_status launch_assemble_persistent<dd, float>(cudaStream_t, const AssembleArgs &, const PhysParams &,
                                                           const ChunkArgs &, const int32_t *, int, float *, unsigned *,
-                                                          int *);
+                                                          int *, bool);
 
 int64_t assemble_chunk_wave() {
   int dev = 0, v = 0, sms = 152, per_sm = LFX_ASM_DD_MIN_CTAS;

@@ -102,10 +102,12 @@ lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysPar
 // the semi-implicit system by chunks in ONE cooperative launch over every chunk colour, the colours
 // separated by bounded grid-wide waits; *err (device) is set to 1 if a wait gave up.  d_chunk_color_off:
 // device copy of the colour offsets; barrier: a device counter (zeroed here).
+// force_timeout (tests): the first wait's target is one more than the grid, its poll limit 4096, so
+// that it runs out and every CTA returns with *err set.
 template <class R, class S>
 lfx_status launch_assemble_persistent(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
                                       const int32_t *d_chunk_color_off, int n_colors, S *vals, unsigned *barrier,
-                                      int *err);
+                                      int *err, bool force_timeout = false);
 // the semi-implicit system by chunks (one launch per chunk colour)
 template <class R, class S>
 lfx_status launch_assemble_chunks(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,

@@ -1401,24 +1401,36 @@ __global__ void __launch_bounds__(kThreads) maxpy_kernel(const T *Vb, int64_t ld
 __global__ void givens_kernel(const double *part, int nblk, KState *st, int j, int m, int maxit) {
   pdl_entry();
   if (finished(st)) return;
+  // the new Hessenberg column and the earlier rotations, staged in shared memory by every thread:
+  // the rotations then run on one thread from shared memory rather than through global memory
+  __shared__ double h[kMaxRestart + 2], cs[kMaxRestart], sn_[kMaxRestart];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = st->hcol[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    cs[i] = st->cs[i];
+    sn_[i] = st->sn[i];
+  }
   double s = 0.0;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i];
   s = cta_sum(s);
-  if (threadIdx.x != 0) return;
-  const double hn = sqrt(s);
+  __syncthreads();
   double *H = st->H + (int64_t)j * (kMaxRestart + 1);
-  for (int i = 0; i <= j; ++i) H[i] = st->hcol[i];
-  H[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double t = st->cs[i] * H[i] + st->sn[i] * H[i + 1];
-    H[i + 1] = -st->sn[i] * H[i] + st->cs[i] * H[i + 1];
-    H[i] = t;
+  const double hn = sqrt(s);
+  if (threadIdx.x == 0) {
+    h[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * h[i] + sn_[i] * h[i + 1];
+      h[i + 1] = -sn_[i] * h[i] + cs[i] * h[i + 1];
+      h[i] = t;
+    }
   }
-  const double den = hypot(H[j], H[j + 1]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < j; i += blockDim.x) H[i] = h[i];
+  if (threadIdx.x != 0) return;
+  const double den = hypot(h[j], h[j + 1]);
   double c = 1.0, sn = 0.0;
   if (den > 0.0) {
-    c = H[j] / den;
-    sn = H[j + 1] / den;
+    c = h[j] / den;
+    sn = h[j + 1] / den;
   }
   st->cs[j] = c;
   st->sn[j] = sn;
@@ -1574,16 +1586,36 @@ __global__ void inner_start_kernel(const double *part, int nblk, KState *st, con
 }
 
 // y = H(0:j,0:j)^-1 g(0:j) by back substitution (j = completed steps of this cycle)
+// y = R^-1 g for the j x j upper-triangular R of the rotated Hessenberg matrix (column k of R is
+// H[k][0..k]): one warp; R and g staged in shared memory, each back-substitution row's sum over the
+// solved unknowns split over the lanes
 __global__ void trisolve_kernel(KState *st) {
   pdl_entry();
-  if (threadIdx.x != 0) return;
+  __shared__ double R[kMaxRestart][kMaxRestart + 1];
+  __shared__ double y[kMaxRestart], g[kMaxRestart];
   const int j = st->j;
-  for (int i = j - 1; i >= 0; --i) {
-    double s = st->g[i];
-    for (int k = i + 1; k < j; ++k) s -= st->H[(int64_t)k * (kMaxRestart + 1) + i] * st->y[k];
-    const double d = st->H[(int64_t)i * (kMaxRestart + 1) + i];
-    st->y[i] = d != 0.0 ? s / d : 0.0;   // d = 0 only after a breakdown (w = 0)
+  const int lane = threadIdx.x & 31;
+  for (int idx = threadIdx.x; idx < j * j; idx += blockDim.x) {
+    const int k = idx / j, i = idx % j;
+    if (i <= k) R[k][i] = st->H[(int64_t)k * (kMaxRestart + 1) + i];
   }
+  for (int i = threadIdx.x; i < j; i += blockDim.x) g[i] = st->g[i];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int i = j - 1; i >= 0; --i) {
+      double part = 0.0;
+      for (int k = i + 1 + lane; k < j; k += 32) part += R[k][i] * y[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) {
+        const double d = R[i][i];
+        y[i] = d != 0.0 ? (g[i] - part) / d : 0.0;   // d = 0 only after a breakdown (w = 0)
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < j; i += blockDim.x) st->y[i] = y[i];
 }
 
 // x += sum_{i<j} y_i z_i
@@ -2241,7 +2273,7 @@ lfx_status ASimple<S, T>::apply_view(cudaStream_t st, const View &A, const T *r,
   }
   // one application per step is timed (the counter is reset per step): an event between two
   // launches costs the overlap of programmatic dependent launch there
-  const bool timed = cfg.f_steps > 2 && n_fev == 0;
+  const bool timed = time_f && cfg.f_steps > 2 && n_fev == 0;
   if (timed) {
     if (n_fev + 2 > (int)fev.size())
       for (int q = 0; q < 32; ++q) {
@@ -2609,6 +2641,7 @@ lfx_status Gmres<S, T>::read_spmv_timing(float *ms, int *count) {
     ++c;
   }
   n_tev = 0;
+  n_spmv_calls = 0;
   if (ms) *ms = total;
   if (count) *count = c;
   return LFX_OK;
@@ -2916,14 +2949,15 @@ void Gmres<S, T>::apply_rank1(cudaStream_t st, const T *x, T *y, double sign, co
   note_launches(2);
 }
 
-// The Arnoldi product w = A z, the first kTimedSpmv of them after each reset of n_tev bracketed by
-// CUDA events for the SpMV timing statistics.
+// The Arnoldi product w = A z; the 3rd, 8th, 13th, ... of them after each reset of n_tev (at most
+// kTimedSpmv) bracketed by CUDA events for the SpMV timing statistics.
 constexpr int kTimedSpmv = 4;
 template <class S, class T>
 lfx_status Gmres<S, T>::timed_spmv(cudaStream_t st, const BsrView<S> &A, const T *z, T *w, const KState *ks) {
-  if (n_tev >= 2 * kTimedSpmv) {
-    // enough samples in this step: an event between two launches costs the overlap of
-    // programmatic dependent launch there
+  const int call = n_spmv_calls++;
+  if (n_tev >= 2 * kTimedSpmv || call % 5 != 2) {
+    // one product in five is timed, up to kTimedSpmv per step: an event between two launches costs
+    // the overlap of programmatic dependent launch there
     arnoldi_spmv(st, A, z, w, ks);
     if (r1.n_tags > 0) apply_rank1(st, z, w, 1.0, ks);
     return LFX_OK;

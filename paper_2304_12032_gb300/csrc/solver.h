@@ -107,6 +107,7 @@ struct ASimple {
   // first step excluded) of the first application after each reset of n_fev, kept until read_f_timing
   std::vector<cudaEvent_t> fev;
   int n_fev = 0;
+  bool time_f = false;   // off unless the owner asks (the events are created on first use)
   lfx_status read_f_timing(float *median_ms_per_pass, int *passes);
   ASimple() = default;
   ASimple(const ASimple &) = delete;
@@ -161,7 +162,7 @@ struct Gmres {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // CUDA-event timing of the Arnoldi SpMV launches (accumulated until read_spmv_timing)
   std::vector<cudaEvent_t> tev;
-  int n_tev = 0;
+  int n_tev = 0, n_spmv_calls = 0;
   lfx_status read_spmv_timing(float *ms, int *count);
   Gmres() = default;
   Gmres(const Gmres &) = delete;

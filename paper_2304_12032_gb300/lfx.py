@@ -130,6 +130,7 @@ _SIGS = {
     "lfx_debug_assemble": ([_P, ctypes.c_int32, _DP, _DP], ctypes.c_int32),
     "lfx_debug_spmv": ([_P, _DP, _DP], ctypes.c_int32),
     "lfx_debug_assemble_newton": ([_P, _DP, _DP, _DP], ctypes.c_int32),
+    "lfx_debug_persistent_timeout": ([_P], ctypes.c_int32),
     "lfx_debug_precond": ([_P, _DP, _DP, _DP, _DP], ctypes.c_int32),
     "lfx_debug_solve": ([_P, _DP, ctypes.POINTER(lfx_step_stats)], ctypes.c_int32),
     "lfx_set_allocator": ([ALLOC_FN, FREE_FN, _P], ctypes.c_int32),
@@ -488,6 +489,10 @@ class State:
         rhs = np.zeros((self.V, 4))
         _check(library().lfx_debug_assemble_newton(self.h, _d(U), _d(blocks), _d(rhs)))
         return blocks, rhs
+
+    def debug_persistent_timeout(self):
+        """Status of one persistent assembly whose first grid-wide wait is made to run out."""
+        return library().lfx_debug_persistent_timeout(self.h)
 
     def debug_spmv(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.V, 4)

@@ -58,3 +58,23 @@ def test_autotuner_times_every_shape_and_keeps_one():
 
     st2 = L.State(prob, case.u_hist, case.p_hist, case.t0)
     assert st2.step()["assembly_mode"] == mode
+
+
+def test_persistent_assembly_wait_that_runs_out_returns_timeout():
+    """The persistent launch's grid-wide waits are bounded: with the first wait's target made
+    unreachable (a count nothing reaches) the CTAs give up after their poll limit and return, the
+    call reports LFX_ERR_TIMEOUT, and the context stays usable: the next step reassembles and
+    matches a fresh state's step."""
+    from paper_2304_12032_gb300 import lfx as L
+
+    case = C.vessel_case(6000, seed=23)
+    _, prob, st = C.gpu_state(case, assembly="persistent", gmres_rtol=1e-12, gmres_max_iters=3000)
+    assert st.debug_persistent_timeout() == L.LFX_ERR_TIMEOUT
+    assert b"gave up" in L.library().lfx_last_error()
+    st.step()
+    u, p = st.get()
+    fresh = L.State(prob, case.u_hist, case.p_hist, case.t0)
+    fresh.step()
+    u1, p1 = fresh.get()
+    assert np.allclose(u, u1, rtol=0, atol=1e-10 * np.abs(u1).max())
+    assert np.allclose(p, p1, rtol=0, atol=1e-10 * np.abs(p1).max())
