@@ -34,15 +34,11 @@ F_STEPS = 6                        # Chebyshev steps on F per preconditioner app
 # FP64-class operations of the method per tetrahedron (DFMA x 2 + DADD + DMUL executed by the FP64
 # assembly kernel, counted with ncu): the algorithmic work of one element's assembly
 ASM_FP64_FLOPS_PER_ELEMENT = 2948
-# thread instructions per tetrahedron of the double-float assembly kernel (ncu) and its DRAM
-# bytes per tetrahedron (ncu, one colour launch of 29,184 elements; profiles/)
-ASM_DD_INST_PER_ELEMENT = 28477
-ASM_DD_DRAM_BYTES_PER_ELEMENT = 4331
 # DRAM bytes per block of the FP32 Krylov SpMV (ncu read + write, 2,089,595-block launch)
 SPMV32_DRAM_BYTES_PER_BLOCK = 71.6
-# DRAM bytes per block of one BF16 F pass of the preconditioner (ncu read + write, 2,089,595-block
-# launch of the 817,970-tet cylinder; scaled to other sizes by the block count)
-FPASS_BF16_DRAM_BYTES_PER_BLOCK = 34.4
+# DRAM bytes per block of one staged BF16 F pass of the preconditioner (ncu read + write of one
+# launch on the 817,970-tet cylinder, scaled to other sizes by the block count); None until taken
+FPASS_BF16_DRAM_BYTES_PER_BLOCK = None
 
 
 def _peaks():
@@ -195,21 +191,24 @@ def kernel_rooflines(stats, T, V, nnzb, prec, bf16=True):
            "hbm_view": {"achieved_gbs": round(asm_bytes / (asm_ms * 1e-3) / 1e9, 1), "peak_gbs": hbm,
                         "frac": round(asm_bytes / (asm_ms * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": int(asm_bytes)},
            "ms_per_step": round(asm_ms, 4), "ms_per_launch": round(asm_ms / n_asm, 4), "launches_per_step": n_asm}
-    # F pass: the aSIMPLE velocity smoothing step; F sub-blocks (12 values) and their columns, the
-    # row pointers, and per node the reads of d_old, r, x, diag(F)^-1 and the writes of r, d, x
+    # F pass: the aSIMPLE velocity smoothing step; F sub-blocks (12 values; in the staged BF16 pass
+    # the column rides in the record's padding, else 4 more bytes), the row pointers, and per node
+    # the reads of d_old, r, x, diag(F)^-1 and the writes of r, d, x
     its = statistics.mean(s["iterations"] for s in stats)     # Arnoldi steps = preconditioner applications
     f_ms = statistics.median([s["ms_fpass_median"] for s in stats if s["n_fpass"] > 0] or [0.0])
     nf = F_STEPS - 1                                            # F launches per application (the first fused)
     sf = (2 if bf16 else 4) if dd else 8
     sx = 4 if dd else 8
-    f_bytes = nnzb * (12 * sf + 4) + 4 * (V + 1) + V * 4 * sx * 7
+    staged = dd and bf16
+    f_bytes = nnzb * (12 * sf + (0 if staged else 4)) + 4 * (V + 1) + V * 4 * sx * 7
     fpass = None
     if f_ms > 0:
         bw = f_bytes / (f_ms * 1e-3) / 1e9
-        fpass = {"kernel": "f_step_kernel (aSIMPLE velocity smoothing pass, %s F sub-blocks)" %
-                           ("BF16" if dd and bf16 else ("FP32" if dd else "FP64")),
+        fpass = {"kernel": ("f_step_staged_kernel (aSIMPLE velocity smoothing pass, BF16 F sub-blocks staged "
+                            "into shared memory by bulk asynchronous copies)") if staged else
+                           "f_step_kernel (aSIMPLE velocity smoothing pass, %s F sub-blocks)" % ("FP32" if dd else "FP64"),
                  "bound": "hbm", "achieved": round(bw, 1), "peak": hbm, "unit": "GB/s", "frac": round(bw / hbm, 4),
-                 "traffic": int(FPASS_BF16_DRAM_BYTES_PER_BLOCK * nnzb) if dd and bf16 else None,
+                 "traffic": int(FPASS_BF16_DRAM_BYTES_PER_BLOCK * nnzb) if staged and FPASS_BF16_DRAM_BYTES_PER_BLOCK else None,
                  "peak_source": src + " (burst copy)", "ms_per_launch": round(f_ms, 5),
                  "launches_per_step": round(nf * its, 1), "ms_per_step": round(f_ms * nf * its, 4),
                  "timing": "CUDA events around the plain F passes of one preconditioner application per step "
@@ -520,13 +519,26 @@ def run_batched(args):
             st.step(allow_not_converged=True)
         torch.cuda.synchronize()
         w0 = time.perf_counter()
-        its = [st.step(allow_not_converged=True)["iterations"] for _ in range(n)]
+        stats = [st.step(allow_not_converged=True) for _ in range(n)]
         torch.cuda.synchronize()
-        return (time.perf_counter() - w0) / n, its
+        wall = (time.perf_counter() - w0) / n
+        its = [s["iterations"] for s in stats]
+        mode, tuned = prob.assembly_tuning()
+        phases = {"assembly": float(np.median([s["ms_assembly_kernels"] for s in stats])),
+                  "solve": float(np.median([s["ms_solve"] for s in stats])),
+                  "step_events": float(np.median([s["ms_total"] for s in stats])),
+                  "wall": wall * 1e3,
+                  "assembly_shape": {1: "colors", 2: "chunks", 3: "persistent"}.get(mode, "none"),
+                  "autotuner_ms": {k: round(v, 3) for k, v in tuned.items()}}
+        phase_log.append(phases)
+        return wall, its
 
     u = batch(ms)
     bcs = sum((member_bcs(i, m, 10) for i, m in enumerate(ms)), [])
+    phase_log = []
     t_batch, its_b = steps_time(u, bcs, "mixed", args.steps)
+    batch_phases = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in phase_log[0].items()}
+    seq_phase = {"assembly": 0.0, "solve": 0.0}
     t_union, its_u = steps_time(u, bcs, "mixed", max(2, args.steps // 2), segmented=0)
     seq = {"fp64": 0.0, "mixed": 0.0}
     solo_its = []
@@ -536,6 +548,8 @@ def run_batched(args):
             seq[prec] += t
             if prec == "mixed":
                 solo_its.append(max(its))
+                seq_phase["assembly"] += phase_log[-1]["assembly"]
+                seq_phase["solve"] += phase_log[-1]["solve"]
     value = args.batch / t_batch
     line = {"metric": "batched: simulation steps/s of independent meshes stepped as one system",
             "value": round(value, 2), "unit": "simulation-steps/s", "n_gpus": 1, "steps": args.steps,
@@ -543,6 +557,8 @@ def run_batched(args):
             "meshes": args.batch, "total_tets": int(u.n_tets), "total_nodes": int(u.n_nodes),
             "tets_per_mesh": [int(m.n_tets) for m in ms], "krylov_iterations": its_b,
             "krylov_iterations_solo_max": int(max(solo_its)),
+            "phase_ms": batch_phases,
+            "sequential_mixed_phase_ms": {k: round(v, 3) for k, v in seq_phase.items()},
             "union_single_krylov": {"ms_per_batch_step": round(t_union * 1e3, 3), "krylov_iterations": its_u,
                                     "sim_steps_per_s": round(args.batch / t_union, 2)},
             "sequential_fp64_sim_steps_per_s": round(args.batch / seq["fp64"], 2),

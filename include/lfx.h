@@ -243,6 +243,13 @@ typedef struct lfx_options {
    * Newton assemblies use the colour launches. */
   int32_t assembly;
   double newton_rtol;           /* default 1e-10                                                 */
+  /* velocity smoothing passes of the BF16 smoother (smoother_bf16 = 1): 1 (default) the staged
+   * pass, whose persistent CTAs copy whole row tiles of F sub-blocks into shared memory with bulk
+   * asynchronous copies while the previous tile is processed (LFX_ERR_TIMEOUT from lfx_step if a
+   * bounded wait for a tile gives up); 0 the plain pass, each lane loading its blocks itself.  Both
+   * compute the same sums in the same order. */
+  int32_t staged_f;
+  int32_t pad2;
 } lfx_options;
 void lfx_options_default(lfx_options *opt);
 
@@ -368,6 +375,12 @@ lfx_status lfx_debug_assemble_newton(lfx_state *state, const double *U, double *
  * returns.  LFX_ERR_TIMEOUT is the expected result; the state stays usable (the next lfx_step
  * assembles anew).  Needs a problem whose assembly is the persistent launch (options.assembly).  */
 lfx_status lfx_debug_persistent_timeout(lfx_state *state);
+/* Failure path of the staged velocity smoothing pass, for tests: assembles the next step's system,
+ * then applies the BF16 aSIMPLE preconditioner once with every wait for a staged tile given no
+ * polls, so that each wait runs out at once; each CTA waits (bounded) for its copies in flight and
+ * returns.  LFX_ERR_TIMEOUT is the expected result; the state stays usable (the next lfx_step
+ * assembles anew).  Needs a mixed-precision state with smoother_bf16 and staged_f set. */
+lfx_status lfx_debug_staged_timeout(lfx_state *state);
 /* y = A x with the last assembled matrix; x, y [n_nodes][4] FP64 host buffers, caller numbering. */
 lfx_status lfx_debug_spmv(lfx_state *state, const double *x, double *y);
 /* z = P^-1 r with the aSIMPLE preconditioner of the last assembled matrix (FP64 path);
@@ -438,7 +451,9 @@ lfx_status lfx_state_amg_levels(const lfx_state *state, int32_t *n_levels, int64
  * ------------------------------------------------------------------------------------------ */
 typedef void *(*lfx_alloc_fn)(size_t bytes, void *ctx);
 typedef void (*lfx_free_fn)(void *ptr, void *ctx);
-/* Route every later device allocation through alloc/free (NULL, NULL restores cudaMalloc). */
+/* Route every later device allocation through alloc/free (NULL, NULL restores cudaMalloc).  alloc
+ * returns device memory aligned to at least 16 bytes (a pointer that is not is handed back to free
+ * and the allocation fails with LFX_ERR_OOM), or NULL on failure. */
 lfx_status lfx_set_allocator(lfx_alloc_fn alloc, lfx_free_fn free_fn, void *ctx);
 /* Device bytes held by a state together with its problem and mesh (for admission control). */
 lfx_status lfx_state_device_bytes(const lfx_state *state, int64_t *bytes);

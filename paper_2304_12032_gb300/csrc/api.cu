@@ -49,7 +49,16 @@ void *dalloc(size_t bytes, DFree *how) {
   void *p = nullptr;
   if (g_alloc) {
     p = g_alloc(bytes, g_alloc_ctx);
-    if (!p) set_error("device allocation of %zu bytes failed (user allocator)", bytes);
+    if (!p) {
+      set_error("device allocation of %zu bytes failed (user allocator)", bytes);
+      return nullptr;
+    }
+    if ((reinterpret_cast<uintptr_t>(p) & 15u) != 0) {
+      // the kernels load 16-byte vectors and copy 16-byte units from every buffer
+      if (g_free) g_free(p, g_alloc_ctx);
+      set_error("user allocator returned %p, not aligned to 16 bytes", p);
+      return nullptr;
+    }
     if (how) *how = DFree{g_free, g_alloc_ctx};
     return p;
   }
@@ -421,6 +430,7 @@ void lfx_options_default(lfx_options *o) {
   o->newton_max_iters = 10;
   o->assembly = LFX_ASM_AUTO;
   o->newton_rtol = 1e-10;
+  o->staged_f = 1;
 }
 
 // barycentre, unit outward normal, area of the faces carrying `tag` (area weighted)
@@ -517,6 +527,10 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
       o.f_smoother > 1 || o.s_smoother < 0 || o.s_smoother > 2) {
     set_error("lfx_problem_create: option out of range (restart <= %d, smoothing steps <= %d)", kMaxRestart,
               kMaxSmooth);
+    return LFX_ERR_INVALID_ARG;
+  }
+  if (o.staged_f < 0 || o.staged_f > 1) {
+    set_error("lfx_problem_create: staged_f must be 0 or 1");
     return LFX_ERR_INVALID_ARG;
   }
   if (o.assembly < LFX_ASM_AUTO || o.assembly > LFX_ASM_PERSISTENT) {
@@ -1017,6 +1031,7 @@ lfx_status lfx_state_create(lfx_problem *pb, const double *u_hist, const double 
     for (DBuf *b : f4) LFX_TRY(b->alloc(sizeof(float4) * V));
     if (o.smoother_bf16) {
       LFX_TRY(s->pcbf.init(V, cfg));
+      if (o.staged_f && m.ftile_row.size() > 1) s->pcbf.set_tiles(m.d_ftile_row.as<int32_t>(), (int)m.ftile_row.size() - 1);
     } else {
       LFX_TRY(s->pc32.init(V, cfg));
     }
@@ -1822,6 +1837,7 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   } else {
     s->newton_res.clear();
   }
+  if (s->mixed() && o.smoother_bf16) LFX_TRY(s->pcbf.queue_bulk_check(st));
   LFX_CUDA_TRY(cudaEventRecord(s->e2, st));
   // history shift: the solution becomes level 0 (and d^{n+1} the displacement's level 0)
   const int oldest = (s->head + s->sigma - 1) % s->sigma;
@@ -1840,6 +1856,10 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   if (s->asm_err_host && *s->asm_err_host) {
     *s->asm_err_host = 0;
     set_error("lfx_step: a grid-wide wait of the persistent assembly gave up");
+    return LFX_ERR_TIMEOUT;
+  }
+  if (s->pcbf.bulk_failed()) {
+    set_error("lfx_step: a wait for a staged tile of the velocity smoothing pass gave up");
     return LFX_ERR_TIMEOUT;
   }
   if (stats) {
@@ -1981,6 +2001,31 @@ lfx_status lfx_debug_persistent_timeout(lfx_state *s) {
   if (s->asm_err_host && *s->asm_err_host) {
     *s->asm_err_host = 0;
     set_error("persistent assembly: a grid-wide wait gave up");
+    return LFX_ERR_TIMEOUT;
+  }
+  return LFX_OK;
+}
+
+lfx_status lfx_debug_staged_timeout(lfx_state *s) {
+  clear_error();
+  if (!s || !s->mixed() || !s->pb->opt.smoother_bf16 || s->pcbf.n_ftile <= 0) {
+    set_error("lfx_debug_staged_timeout: needs a mixed-precision state with the staged BF16 smoothing pass");
+    return LFX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = s->stream;
+  LFX_TRY(assemble_system(s, true));
+  LFX_TRY(prepare_precond(s));
+  const BsrView<__nv_bfloat16> Ab = s->view<__nv_bfloat16>(s->nopat);
+  LFX_CUDA_TRY(cudaMemsetAsync(s->r32.p, 0, s->r32.bytes, st));
+  s->pcbf.force_bulk_timeout = true;
+  lfx_status rc = s->pcbf.apply(st, Ab, s->r32.as<float>(), s->z32.as<float>(), nullptr);
+  s->pcbf.force_bulk_timeout = false;
+  LFX_TRY(rc);
+  LFX_TRY(s->pcbf.queue_bulk_check(st));
+  LFX_CUDA_TRY(cudaStreamSynchronize(st));
+  s->assembled = false;
+  if (s->pcbf.bulk_failed()) {
+    set_error("staged velocity smoothing pass: a wait for a tile gave up");
     return LFX_ERR_TIMEOUT;
   }
   return LFX_OK;

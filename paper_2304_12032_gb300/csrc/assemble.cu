@@ -96,11 +96,24 @@ __device__ __forceinline__ dd fmadd<dd>(dd a, dd b, dd c) {
   return fma_dd_fast(a, b, c);
 }
 
+// a + b where contributions are summed into a matrix entry, a right-hand side or an element sum:
+// in double-float the accumulating sum, whose error is relative to the operands (the error model
+// of recursive summation), not to the result
+template <class R>
+__device__ __forceinline__ R acc(R a, R b) {
+  return a + b;
+}
+template <>
+__device__ __forceinline__ dd acc<dd>(dd a, dd b) {
+  return add_acc(a, b);
+}
+
 template <class R>
 struct ElemShared {
   R gphi[kElems][12];      // grad phi_a, a = 0..3
   R w[kElems];             // |K| / 4 (quadrature weight)
   R Gm[kElems][9];         // metric tensor G = J^-T J^-1
+  R GG[kElems];            // G : G
   R igg[kElems];           // 1 / (g . g), g = J^-T 1
   R cs[kElems][4];         // rho alpha / dt + sum_k (R_k/eps_k) delta_k at each qp
   R wtm[kElems][4];        // w tau_M
@@ -184,7 +197,7 @@ __device__ __forceinline__ void tet_geometry(const G x[4][3], G gp[12], G Gm[9],
 // Phase 1a (one thread per element): geometry in FP64 (FP64 assembly, or a badly shaped
 // element in mixed assembly), else FP32.
 template <class R>
-__device__ void element_geometry(const AssembleArgs &A, int64_t e, R gpo[12], R Go[9], R &igg, R &w) {
+__device__ void element_geometry(const AssembleArgs &A, int64_t e, R gpo[12], R Go[9], R &GGo, R &igg, R &w) {
   const int4 cn = A.conn[e];
   const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
   const bool fp64_geom = std::is_same<R, double>::value || (A.bad && A.bad[e]);
@@ -202,6 +215,10 @@ __device__ void element_geometry(const AssembleArgs &A, int64_t e, R gpo[12], R 
     for (int k = 0; k < 12; ++k) gpo[k] = (R)gp[k];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Go[k] = (R)G[k];
+    double gg = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) gg += G[k] * G[k];
+    GGo = (R)gg;
     igg = (R)(1.0 / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
     w = (R)(0.25 * v);
   } else {
@@ -216,6 +233,9 @@ __device__ void element_geometry(const AssembleArgs &A, int64_t e, R gpo[12], R 
       x[a][2] = p[2];
     }
     tet_geometry<R>(x, gpo, Go, g, v);
+    GGo = cst<R>(0.0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) GGo = fmadd(Go[k], Go[k], GGo);
     igg = cst<R>(1.0) / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
     w = cst<R>(0.25) * v;
   }
@@ -245,8 +265,9 @@ __device__ __forceinline__ bool has_geo(const AssembleArgs &A) {
 // cache
 template <class R>
 __device__ void geom_phase(const AssembleArgs &A, int64_t e, int le, ElemShared<R> &sh) {
-  R igg, w;
-  element_geometry<R>(A, e, sh.gphi[le], sh.Gm[le], igg, w);
+  R GG, igg, w;
+  element_geometry<R>(A, e, sh.gphi[le], sh.Gm[le], GG, igg, w);
+  sh.GG[le] = GG;
   sh.igg[le] = igg;
   sh.w[le] = w;
 }
@@ -263,7 +284,8 @@ __device__ void geom_load(const AssembleArgs &A, int64_t T, ElemShared<R> &sh) {
     if (k < 12) sh.gphi[le][k] = v;
     else if (k < 21) sh.Gm[le][k - 12] = v;
     else if (k == 21) sh.igg[le] = v;
-    else sh.w[le] = v;
+    else if (k == 22) sh.w[le] = v;
+    else sh.GG[le] = v;
   }
 }
 
@@ -271,14 +293,15 @@ template <class R>
 __global__ void geometry_kernel(AssembleArgs A, int64_t T, double *out64, float *out_hi, float *out_lo) {
   pdl_entry();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < T; e += (int64_t)gridDim.x * blockDim.x) {
-    R gp[12], G[9], igg, w, v[kGeoValues];
-    element_geometry<R>(A, e, gp, G, igg, w);
+    R gp[12], G[9], GG, igg, w, v[kGeoValues];
+    element_geometry<R>(A, e, gp, G, GG, igg, w);
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = gp[k];
 #pragma unroll
     for (int k = 0; k < 9; ++k) v[12 + k] = G[k];
     v[21] = igg;
     v[22] = w;
+    v[23] = GG;
 #pragma unroll
     for (int k = 0; k < kGeoValues; ++k) {
       if constexpr (std::is_same<R, double>::value) {
@@ -291,6 +314,16 @@ __global__ void geometry_kernel(AssembleArgs A, int64_t T, double *out64, float 
       }
     }
   }
+}
+
+// value of lane src (within the warp) among the lanes of mask
+template <class R>
+__device__ __forceinline__ R shfl_from(R v, int src, unsigned mask) {
+  return __shfl_sync(mask, v, src);
+}
+template <>
+__device__ __forceinline__ dd shfl_from<dd>(dd v, int src, unsigned mask) {
+  return dd(__shfl_sync(mask, v.hi, src), __shfl_sync(mask, v.lo, src));
 }
 
 // Phase 1b for one (element, quadrature point): u*, u^BDF, tau_M and tau_C (FP64 for the FP64
@@ -351,32 +384,26 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR
   const R *Gm = sh.Gm[le];
   R taum, tauc;
   if constexpr (std::is_same<R, dd>::value) {
-    R uGu = cst<R>(0.0), GG = cst<R>(0.0);
+    R uGu = cst<R>(0.0);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       R Gu = cst<R>(0.0);
 #pragma unroll
-      for (int l = 0; l < 3; ++l) {
-        Gu = fmadd(Gm[3 * k + l], us[l], Gu);
-        GG = fmadd(Gm[3 * k + l], Gm[3 * k + l], GG);
-      }
+      for (int l = 0; l < 3; ++l) Gu = fmadd(Gm[3 * k + l], us[l], Gu);
       uGu = fmadd(us[k], Gu, uGu);
     }
-    R tsum = fmadd(Q.cr_mu2, GG, fmadd(Q.rho * Q.rho, uGu, Q.tau_t));
+    R tsum = fmadd(Q.cr_mu2, sh.GG[le], fmadd(Q.rho * Q.rho, uGu, Q.tau_t));
     if (P.n_riis > 0) tsum += (R)sR2;
     taum = dd_rsqrt(tsum);                        // tau_M = tsum^-1/2
     tauc = tsum * taum * sh.igg[le];              // tau_C = 1/(tau_M g.g) = sqrt(tsum)/(g.g)
   } else {
-    double uGu = 0.0, GG = 0.0;
+    double uGu = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
 #pragma unroll
-      for (int l = 0; l < 3; ++l) {
-        const double Gkl = (double)Gm[3 * k + l];
-        uGu += (double)us[k] * Gkl * (double)us[l];
-        GG += Gkl * Gkl;
-      }
+      for (int l = 0; l < 3; ++l) uGu += (double)us[k] * (double)Gm[3 * k + l] * (double)us[l];
     }
+    const double GG = (double)sh.GG[le];
     const double rho = P.rho;
     const double tsum = P.tau_t + rho * rho * uGu + P.cr_mu2 * GG + sR2;
     const double tm = rsqrt(tsum);
@@ -384,18 +411,28 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR
     tauc = (R)(tsum * tm * (double)sh.igg[le]);
   }
   R z[3] = {cst<R>(0.0), cst<R>(0.0), cst<R>(0.0)};
+  // grad p^EXT, constant on the element: the element's four threads (one per quadrature point, a
+  // quad of lanes) each form one component (the fourth repeats the third) and exchange them
+  R gpr[3];
+  if (IMPL || P.stab >= 2) {
+    const int c = q < 3 ? q : 2;
+    R g = cst<R>(0.0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) g = fmadd(ue[a][3], gp[3 * a + c], g);
+    const int base = threadIdx.x & 28;
+    const unsigned mask = 0xFu << base;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gpr[i] = shfl_from<R>(g, base + i, mask);
+  }
   if (IMPL) {
     // the iterate's strong residual r_M(u, p), grad u, and the derivative of tau_M in u*
     R rmv[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      R conv = cst<R>(0.0), gpr = cst<R>(0.0);
+      R conv = cst<R>(0.0);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        conv = fmadd(adv[a], ue[a][i], conv);
-        gpr = fmadd(ue[a][3], gp[3 * a + i], gpr);
-      }
-      rmv[i] = fmadd(sRr, uq[i], fmadd(Q.rho, conv, fmadd(Q.rho_dt, fmadd(Q.alpha, uq[i], -ubq[i]), gpr))) - Q.f[i];
+      for (int a = 0; a < 4; ++a) conv = fmadd(adv[a], ue[a][i], conv);
+      rmv[i] = fmadd(sRr, uq[i], fmadd(Q.rho, conv, fmadd(Q.rho_dt, fmadd(Q.alpha, uq[i], -ubq[i]), gpr[i]))) - Q.f[i];
     }
     const R k3 = -(taum * taum * taum) * (Q.rho * Q.rho);
 #pragma unroll
@@ -425,13 +462,10 @@ __device__ void qp_phase(const AssembleArgs &A, const PhysParams &P, const PhysR
     // tau_M r_M(u^EXT, p^EXT) with the strong residual of Section 2.3 (-mu Lap u = 0 for P1)
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      R conv = cst<R>(0.0), gpr = cst<R>(0.0);
+      R conv = cst<R>(0.0);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        conv = fmadd(adv[a], ue[a][i], conv);
-        gpr = fmadd(ue[a][3], gp[3 * a + i], gpr);
-      }
-      const R rm = fmadd(sRr, uq[i], fmadd(Q.rho, conv, fmadd(Q.rho_dt, fmadd(Q.alpha, uq[i], -ubq[i]), gpr))) - Q.f[i];
+      for (int a = 0; a < 4; ++a) conv = fmadd(adv[a], ue[a][i], conv);
+      const R rm = fmadd(sRr, uq[i], fmadd(Q.rho, conv, fmadd(Q.rho_dt, fmadd(Q.alpha, uq[i], -ubq[i]), gpr[i]))) - Q.f[i];
       z[i] = Q.rho * taum * (us[i] - taum * rm);
     }
   }
@@ -493,11 +527,11 @@ __device__ void node_phase(const PhysParams &P, const PhysR<R> &Q, int n, int le
     R tmw = cst<R>(0.0), tcw = tmw, z0 = tmw, z1 = tmw, z2 = tmw;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      tmw += sh.wtm[le][q];
-      tcw += sh.wtc[le][q];
-      z0 += sh.wz[le][q][0];
-      z1 += sh.wz[le][q][1];
-      z2 += sh.wz[le][q][2];
+      tmw = acc(tmw, sh.wtm[le][q]);
+      tcw = acc(tcw, sh.wtc[le][q]);
+      z0 = acc(z0, sh.wz[le][q][0]);
+      z1 = acc(z1, sh.wz[le][q][1]);
+      z2 = acc(z2, sh.wz[le][q][2]);
     }
     sh.TM[le] = tmw;
     sh.TC[le] = tcw;
@@ -677,7 +711,7 @@ __device__ __forceinline__ void block_values(const PhysParams &P, int le, int a,
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       R v = fmadd(tci, gb[j], Wv[i] * ga[j]);                   // tau_C div-div + VMS/LES
-      if (i == j) v += dg;
+      if (i == j) v = acc(v, dg);
       if (P.diffusion != 0) v = fmadd(muvol * ga[j], gb[i], v); // symmetric-gradient part
       blk[4 * i + j] = v;
     }
@@ -722,7 +756,9 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const Ph
   const uint32_t fm = A.first ? (uint32_t)A.first[e] : 0u;
   const bool bfirst = (fm >> (4 * a + b)) & 1u, rfirst = (fm >> (5 * a)) & 1u;
   if constexpr (std::is_same<R, dd>::value) {
-    // dd accumulation into the high (vals) and low parts
+    // dd accumulation into the high (vals) and low parts, with the exact sum: the accumulating
+    // sum, which the chunked kernels use, ran this kernel 3.4x slower on a 1M-tet mesh (same
+    // registers, no spills; cause not identified), so it is not used here
     float4 *ph = reinterpret_cast<float4 *>(vals + (int64_t)s * 16);
     float4 *pl = reinterpret_cast<float4 *>(A.vals_lo + (int64_t)s * 16);
     if (bfirst) {
@@ -862,16 +898,16 @@ struct AccumOut<float, dd> {
     float4 *l = reinterpret_cast<float4 *>(is_rhs ? A.rhs_lo + k : A.vals_lo + k);
     dd r[4] = {v[0], v[1], v[2], v[3]};
     if (!first) {
-      r[0] = dd(o.hi.x, o.lo.x) + v[0];
-      r[1] = dd(o.hi.y, o.lo.y) + v[1];
-      r[2] = dd(o.hi.z, o.lo.z) + v[2];
-      r[3] = dd(o.hi.w, o.lo.w) + v[3];
+      r[0] = acc(dd(o.hi.x, o.lo.x), v[0]);
+      r[1] = acc(dd(o.hi.y, o.lo.y), v[1]);
+      r[2] = acc(dd(o.hi.z, o.lo.z), v[2]);
+      r[3] = acc(dd(o.hi.w, o.lo.w), v[3]);
     }
     *h = make_float4(r[0].hi, r[1].hi, r[2].hi, r[3].hi);
     *l = make_float4(r[0].lo, r[1].lo, r[2].lo, r[3].lo);
   }
 };
-constexpr int kItemsInFlight = 2;   // reduction items (four values each) per thread loaded together
+constexpr int kItemsInFlight = 2;   // reduction items (four values each) per thread loaded together (1 and 4 were slower)
 
 template <class R, class S>
 __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q,
@@ -933,7 +969,7 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
         int64_t where[kItemsInFlight];
         bool is_rhs[kItemsInFlight], first[kItemsInFlight];
         typename Out::Old old[kItemsInFlight];
-        R acc[kItemsInFlight][4];
+        R sum[kItemsInFlight][4];
 #pragma unroll
         for (int i = 0; i < kItemsInFlight; ++i) {
           const int j = jb + i * kCta;
@@ -949,15 +985,15 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
           if (!first[i]) old[i] = Out::load(A, vals, where[i], is_rhs[i]);
           const int st0 = meta & 0xff, len = (meta >> 8) & 63;
 #pragma unroll
-          for (int v = 0; v < 4; ++v) acc[i][v] = blk_item ? cs.stage[st0][v0 + v] : cs.rst[st0][v];
+          for (int v = 0; v < 4; ++v) sum[i][v] = blk_item ? cs.stage[st0][v0 + v] : cs.rst[st0][v];
           for (int k = 1; k < len; ++k) {
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[i][v] += blk_item ? cs.stage[st0 + k][v0 + v] : cs.rst[st0 + k][v];
+            for (int v = 0; v < 4; ++v) sum[i][v] = acc(sum[i][v], blk_item ? cs.stage[st0 + k][v0 + v] : cs.rst[st0 + k][v]);
           }
         }
 #pragma unroll
         for (int i = 0; i < kItemsInFlight; ++i)
-          if (where[i] >= 0) Out::store(A, vals, where[i], is_rhs[i], acc[i], old[i], first[i]);
+          if (where[i] >= 0) Out::store(A, vals, where[i], is_rhs[i], sum[i], old[i], first[i]);
       }
       __syncthreads();
     }

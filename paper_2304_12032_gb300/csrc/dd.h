@@ -92,9 +92,8 @@ LFX_HD dd two_prod(float a, float b) {
 LFX_HD dd operator-(dd a) { return dd(-a.hi, -a.lo); }
 
 // sum with relative error O(2^-47) even under cancellation: the high parts and the low parts
-// are each summed exactly, then renormalised.  (A cheaper variant that adds the low parts in
-// plain FP32 halves the operation count but ran the assembly kernel 2x slower on this GPU, by
-// measurement; this form is kept.)
+// are each summed exactly, then renormalised.  Sums of contributions (matrix entries, element
+// sums) use add_acc below instead, whose error bound is relative to the operands.
 LFX_HD dd operator+(dd a, dd b) {
   dd s = two_sum(a.hi, b.hi);
   const dd t = two_sum(a.lo, b.lo);
@@ -102,6 +101,15 @@ LFX_HD dd operator+(dd a, dd b) {
   return fast_two_sum(s.hi, f_add(s.lo, t.lo));
 }
 LFX_HD dd operator-(dd a, dd b) { return a + (-b); }
+
+// a + b for accumulations: the high parts are summed exactly, the low parts and that sum's error
+// in FP32, then renormalised (11 FP32 operations against 20).  The error is a few units of 2^-47
+// of |a| + |b| (not of the result): the error model of recursive summation in a format with a
+// 48-bit significand, which is what summing element contributions into a matrix entry needs.
+LFX_HD dd add_acc(dd a, dd b) {
+  const dd s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, f_add(s.lo, f_add(a.lo, b.lo)));
+}
 
 LFX_HD dd operator*(dd a, dd b) {
   dd p = two_prod(a.hi, b.hi);

@@ -38,7 +38,7 @@ struct AssembleArgs {
   float *vals_lo;            // [nnzb][16]
   float *rhs_hi, *rhs_lo;    // [V][4]
   // per-element geometry computed once (the mesh does not move): kGeoValues values per element,
-  // structure of arrays [kGeoValues][T] (grad phi 12, G 9, 1/(g.g), |K|/4); FP64 kernel: geo64;
+  // structure of arrays [kGeoValues][T] (grad phi 12, G 9, 1/(g.g), |K|/4, G:G); FP64 kernel: geo64;
   // double-float kernel: geo_hi + geo_lo.  Null: the kernel computes the geometry itself.
   const double *geo64;
   const float *geo_hi, *geo_lo;
@@ -55,7 +55,7 @@ struct ChunkArgs {
   const uint16_t *meta;
   const int32_t *block, *node;
 };
-constexpr int kGeoValues = 23;
+constexpr int kGeoValues = 24;
 
 // Fills the geometry cache of the arithmetic type R (double: out64 [kGeoValues][T]; dd: out_hi,
 // out_lo) for the T elements of A.conn.

@@ -130,6 +130,9 @@ struct Mesh {
   std::vector<uint16_t> run_meta;        // slot start (bits 0-7) | length (8-13) | first writer (14) | diagonal (15)
   std::vector<int32_t> run_block;        // [runs] block index in the pattern
   std::vector<int32_t> run_node;         // [runs] node of a diagonal run (its rhs row), else -1
+  // tiles of the staged velocity smoothing pass: consecutive block rows, at most kFTileRows rows and
+  // kFTileBlocks blocks each ([n_tiles+1] row offsets; empty when some row alone exceeds the limit)
+  std::vector<int32_t> ftile_row;
   std::vector<uint8_t> bad;          // [T] 1 if below the shape-quality threshold
   std::vector<int32_t> bfaces;       // [F][3] outward oriented, internal numbering
   std::vector<int32_t> btags;        // [F]
@@ -151,6 +154,7 @@ struct Mesh {
   DBuf d_color_elems;
   DBuf d_chunk_elem_off, d_chunk_pass_off, d_pass_code, d_pass_run_off, d_pass_ndiag, d_run_meta, d_run_block,
       d_run_node;
+  DBuf d_ftile_row;
   size_t device_bytes() const;
 };
 
@@ -176,6 +180,12 @@ struct PhysParams {
 };
 
 constexpr int kChunkElems = 32;     // elements per chunk (one CTA pass of the assembly kernels)
+// tile limits of the staged velocity smoothing pass (its CTA handles kFTileRows rows with 4 lanes
+// each, and stages at most kFTileBlocks 24-byte BF16 sub-block records in each of two buffers;
+// measured on a 1M-tet mesh against 64-row tiles of 1536, 1024, 768 and 512 blocks: small buffers
+// leave the SM's L1 to the gathers of the iterate)
+constexpr int kFTileRows = 32;
+constexpr int kFTileBlocks = 512;
 // Chunks the chunked double-float assembly kernel processes in one wave (resident CTAs x SMs).
 int64_t assemble_chunk_wave();
 // Elements the double-float assembly kernel processes in one wave over the whole device (resident

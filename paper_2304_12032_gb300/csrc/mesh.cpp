@@ -134,7 +134,7 @@ size_t Mesh::device_bytes() const {
   return d_xyz.bytes + d_xyz_hi.bytes + d_xyz_lo.bytes + d_conn.bytes + d_slot.bytes + d_rowptr.bytes + d_col.bytes + d_diag.bytes +
          d_trans.bytes + d_comp_off.bytes + d_node_old.bytes + d_first.bytes + d_color_elems.bytes +
          d_chunk_elem_off.bytes + d_chunk_pass_off.bytes + d_pass_code.bytes + d_pass_run_off.bytes +
-         d_pass_ndiag.bytes + d_run_meta.bytes + d_run_block.bytes + d_run_node.bytes;
+         d_pass_ndiag.bytes + d_run_meta.bytes + d_run_block.bytes + d_run_node.bytes + d_ftile_row.bytes;
 }
 
 lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_in, int64_t n_tets,
@@ -408,6 +408,18 @@ lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_
   for (int64_t i = 0; i < V; ++i)
     for (int32_t k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k)
       m.trans_idx[k] = find(m.col_idx[k], (int32_t)i);
+  // row tiles of the staged velocity smoothing pass, greedily as long as both limits hold
+  m.ftile_row.assign(1, 0);
+  for (int64_t r0 = 0; r0 < V;) {
+    int64_t r1 = r0;
+    while (r1 < V && r1 - r0 < kFTileRows && m.row_ptr[r1 + 1] - m.row_ptr[r0] <= kFTileBlocks) ++r1;
+    if (r1 == r0) {   // one row alone is over the block limit: no tiles, the plain pass runs
+      m.ftile_row.clear();
+      break;
+    }
+    m.ftile_row.push_back((int32_t)r1);
+    r0 = r1;
+  }
   m.slot.resize((size_t)T * 16);
   for (int64_t e = 0; e < T; ++e)
     for (int a = 0; a < 4; ++a)
@@ -586,6 +598,7 @@ lfx_status upload_mesh(Mesh &m) {
   LFX_TRY(up(m.d_run_meta, m.run_meta.data(), sizeof(uint16_t) * m.run_meta.size()));
   LFX_TRY(up(m.d_run_block, m.run_block.data(), sizeof(int32_t) * m.run_block.size()));
   LFX_TRY(up(m.d_run_node, m.run_node.data(), sizeof(int32_t) * m.run_node.size()));
+  LFX_TRY(up(m.d_ftile_row, m.ftile_row.data(), sizeof(int32_t) * m.ftile_row.size()));
   LFX_CUDA_TRY(cudaMemcpy(m.d_node_old.p, m.node_old.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice));
   LFX_CUDA_TRY(cudaMemcpy(m.d_xyz.p, x4.data(), m.d_xyz.bytes, cudaMemcpyHostToDevice));
   // FP32 high and low parts of the coordinates (x = hi + lo to 48 bits) for double-float assembly

@@ -38,7 +38,7 @@ constexpr int kRowGroup = LFX_ROW_GROUP;   // lanes per block row in the row ker
 #define LFX_U_FULL 2
 #endif
 #ifndef LFX_U_F
-#define LFX_U_F 1
+#define LFX_U_F 2
 #endif
 #ifndef LFX_U_GDC
 #define LFX_U_GDC 2
@@ -438,8 +438,22 @@ __device__ __forceinline__ void ld_DC(const SplitView<S> &A, int64_t k, T dc[4])
 }
 
 // Blocks stored apart (in the preconditioner's storage type S) from the FP64 or FP32 4x4 blocks.
+// Record slots 9..11 of an F sub-block: zero, except in BF16 storage, where slots 9 and 10 carry the
+// block's column index (low and high 16 bits) for the staged pass, which reads records only.
+template <class S>
+__device__ __forceinline__ void put_f_tail(S *rec, int32_t) {
+  rec[9] = rec[10] = rec[11] = (S)0.0;
+}
+template <>
+__device__ __forceinline__ void put_f_tail<__nv_bfloat16>(__nv_bfloat16 *rec, int32_t c) {
+  rec[9] = __ushort_as_bfloat16((unsigned short)((uint32_t)c & 0xffffu));
+  rec[10] = __ushort_as_bfloat16((unsigned short)((uint32_t)c >> 16));
+  rec[11] = __ushort_as_bfloat16(0);
+}
+
 template <class S, class Src>
-__global__ void split_kernel(int64_t nnzb, const Src *__restrict__ vals, S *F, S *G, S *DC) {
+__global__ void split_kernel(int64_t nnzb, const Src *__restrict__ vals, const int32_t *__restrict__ col, S *F, S *G,
+                             S *DC) {
   pdl_entry();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnzb; k += (int64_t)gridDim.x * blockDim.x) {
     Src b[16];
@@ -448,8 +462,7 @@ __global__ void split_kernel(int64_t nnzb, const Src *__restrict__ vals, S *F, S
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) F[12 * k + 3 * i + j] = (S)b[4 * i + j];
-#pragma unroll
-    for (int i = 9; i < 12; ++i) F[12 * k + i] = (S)0.0;
+    put_f_tail<S>(F + 12 * k, col[k]);
     G[4 * k] = (S)b[3];
     G[4 * k + 1] = (S)b[7];
     G[4 * k + 2] = (S)b[11];
@@ -599,7 +612,9 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF
     }
   }
   if (row < A.V) {
-    constexpr int U = LFX_U_F;
+    // two blocks per lane in flight; one in the first pass, whose two gathers per block (b0 and
+    // diag(F)^-1) would otherwise take it to 66 registers and 3 CTAs per SM
+    constexpr int U = kFirst ? 1 : LFX_U_F;
     T f[U][9];
     int32_t c[U];
     typename Vec4T<T>::type dv[U];
@@ -654,6 +669,183 @@ __global__ void __launch_bounds__(kThreads) f_step_kernel(View A, const T *dinvF
   if (part) {
     double s = cta_sum(nrm);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Staged velocity smoothing pass (BF16 sub-blocks).  The plain pass above waits, per lane, on a
+// chain of small dependent loads (row pointer -> 24-byte record and column -> gathered iterate),
+// which leaves HBM idle between them.  Here a persistent CTA walks row tiles (the mesh's table:
+// at most kFTileRows rows and kFTileBlocks blocks each); one thread stages a whole tile's F records
+// (the column index rides in each record's padding) into shared memory with one bulk asynchronous
+// copy completing on an mbarrier, double-buffered, so that the next tile streams in while this one
+// is processed.  Each lane then takes its row's blocks in the plain pass's order (the results are
+// the same bit for bit).  Every wait is bounded (polls tries; a test passes 0): a wait that runs
+// out sets *err, and the CTA waits (bounded again) for its copies in flight before it returns.
+// ------------------------------------------------------------------------------------------
+constexpr int kFTileThreads = kFTileRows * kRowGroup;
+constexpr int64_t kFRec = 24;   // bytes of one BF16 F record (12 values)
+constexpr uint32_t kFStageBytes = (uint32_t)(((kFTileBlocks * kFRec + 32) + 127) / 128 * 128);
+constexpr size_t kFStagedSmem = 128 + 2 * (size_t)kFStageBytes;
+constexpr uint32_t kFWaitPolls = 1u << 22;   // about 0.3 s of polls (32 ns sleeps) per wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// bytes (a multiple of 16) from global src (16-byte aligned) to shared dst (16-byte aligned),
+// completing on bar
+__device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t polls) {
+  for (uint32_t i = 0; i < polls; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(32);
+  }
+  return false;
+}
+
+template <bool kFirst>
+__global__ void __launch_bounds__(kFTileThreads) f_step_staged_kernel(
+    SplitView<__nv_bfloat16> A, const int32_t *__restrict__ tile_row, int n_tiles, const float *dinvF,
+    const float *d_old, float *d_new, float *r, float *x, const SmoothCoef *cf, int k, const KState *st,
+    const float *b0, int *err, uint32_t polls) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  unsigned char *stage0 = smem + 128;
+  pdl_entry();
+  if (finished(st)) return;
+  const unsigned char *recs = reinterpret_cast<const unsigned char *>(A.F);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  // thread 0: the records of tile t (whole 16-byte units around them) into buffer b
+  auto issue = [&](int t, int b) {
+    const int64_t k0 = A.rowptr[tile_row[t]], k1 = A.rowptr[tile_row[t + 1]];
+    const int64_t a0 = (kFRec * k0) & ~(int64_t)15, a1 = (kFRec * k1 + 15) & ~(int64_t)15;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the buffer's earlier reads before the copy
+    mbar_expect_tx(&bar[b], (uint32_t)(a1 - a0));
+    bulk_to_smem(stage0 + (size_t)b * kFStageBytes, recs + a0, (uint32_t)(a1 - a0), &bar[b]);
+  };
+  constexpr int U = 4;   // a row's blocks per lane gathered together (most rows: all of them)
+  const float c1 = cf->f_c1f[k], c2 = cf->f_c2f[k], s0 = cf->f_initf;
+  const int lane = threadIdx.x % kRowGroup;
+  int j = 0, t = blockIdx.x;
+  bool ok = true;
+  if (threadIdx.x == 0 && t < n_tiles) issue(t, 0);
+  for (; t < n_tiles; t += gridDim.x, ++j) {
+    const int b = j & 1;
+    if (threadIdx.x == 0 && t + (int)gridDim.x < n_tiles) issue(t + gridDim.x, b ^ 1);
+    // the row's own data first: its latency overlaps the wait for the staged records
+    const int32_t r0 = tile_row[t], r1 = tile_row[t + 1];
+    const int32_t row = r0 + (int32_t)(threadIdx.x / kRowGroup);
+    const bool has = row < r1, owner = has && lane == 0;
+    const int32_t kt = A.rowptr[r0];
+    int32_t kb = 0, ke = 0;
+    if (has) {
+      kb = A.rowptr[row];
+      ke = A.rowptr[row + 1];
+    }
+    F4 df{}, rr{}, xx{}, dn{}, dold{}, bv{};
+    if (owner) {
+      df = ld4(dinvF, row);
+      rr = ld4(r, row);
+      xx = ld4(x, row);
+      dn = ld4(d_new, row);
+      if constexpr (kFirst) bv = ld4(b0, row);
+      else dold = ld4(d_old, row);
+    }
+    const bool got = mbar_wait_bounded(&bar[b], (uint32_t)(j >> 1) & 1u, polls);
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      break;
+    }
+    // record kk of the tile sits at rec + kFRec (kk - kt) (8-byte aligned)
+    const unsigned char *rec = stage0 + (size_t)b * kFStageBytes + ((kFRec * kt) & 15);
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    for (int32_t kk = kb + lane; kk < ke; kk += U * kRowGroup) {
+      uint2 w[U][3];
+      F4 dv[U];
+      bool v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        v[u] = kk + u * kRowGroup < ke;
+        if (v[u]) {
+          const uint2 *p = reinterpret_cast<const uint2 *>(rec + kFRec * (kk + u * kRowGroup - kt));
+          w[u][0] = p[0];
+          w[u][1] = p[1];
+          w[u][2] = p[2];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!v[u]) continue;
+        const int32_t c = (int32_t)((w[u][2].x >> 16) | (w[u][2].y << 16));
+        if constexpr (kFirst) {
+          const F4 dfc = ld4(dinvF, c), bc = ld4(b0, c);
+          dv[u].x = s0 * (dfc.x * bc.x);
+          dv[u].y = s0 * (dfc.y * bc.y);
+          dv[u].z = s0 * (dfc.z * bc.z);
+        } else {
+          dv[u] = ld4(d_old, c);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!v[u]) continue;
+        float f[10];
+        bf16x2_to_f32(w[u][0].x, f[0], f[1]);
+        bf16x2_to_f32(w[u][0].y, f[2], f[3]);
+        bf16x2_to_f32(w[u][1].x, f[4], f[5]);
+        bf16x2_to_f32(w[u][1].y, f[6], f[7]);
+        bf16x2_to_f32(w[u][2].x, f[8], f[9]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc[i] += f[3 * i] * dv[u].x + f[3 * i + 1] * dv[u].y + f[3 * i + 2] * dv[u].z;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) acc[i] = group_sum(acc[i]);
+    if (owner) {
+      if constexpr (kFirst) {
+        rr.x = df.x * bv.x; rr.y = df.y * bv.y; rr.z = df.z * bv.z;
+        dold.x = s0 * rr.x; dold.y = s0 * rr.y; dold.z = s0 * rr.z;
+        xx.x = dold.x; xx.y = dold.y; xx.z = dold.z;
+      }
+      rr.x -= df.x * acc[0]; rr.y -= df.y * acc[1]; rr.z -= df.z * acc[2];
+      dn.x = c1 * dold.x + c2 * rr.x; dn.y = c1 * dold.y + c2 * rr.y; dn.z = c1 * dold.z + c2 * rr.z;
+      xx.x += dn.x; xx.y += dn.y; xx.z += dn.z;
+      st4(r, row, rr);
+      st4(d_new, row, dn);
+      st4(x, row, xx);
+    }
+    __syncthreads();   // buffer b is refilled at the start of the next iteration
+  }
+  if (!ok && threadIdx.x == 0) {
+    atomicExch(err, 1);
+    // copies still in flight into this CTA's buffers: tile t's, and the next tile's if issued
+    mbar_wait_bounded(&bar[j & 1], (uint32_t)(j >> 1) & 1u, kFWaitPolls);
+    if (t + (int)gridDim.x < n_tiles)
+      mbar_wait_bounded(&bar[(j + 1) & 1], (uint32_t)((j + 1) >> 1) & 1u, kFWaitPolls);
   }
 }
 
@@ -2171,7 +2363,7 @@ lfx_status ASimple<S, T>::init_borrowed(int64_t V_, const SmootherConfig &cfg_, 
 template <class S, class T>
 size_t ASimple<S, T>::device_bytes() const {
   return dinvF.bytes + dinvS.bytes + X.bytes + D0.bytes + D1.bytes + R.bytes + W.bytes + coef.bytes + part.bytes +
-         sF.bytes + sG.bytes + sDC.bytes;
+         sF.bytes + sG.bytes + sDC.bytes + berr.bytes;
 }
 
 // Diagonals and (Chebyshev) eigenvalue estimates for the current matrix.
@@ -2242,17 +2434,70 @@ template <class S, class T>
 template <class Src>
 lfx_status ASimple<S, T>::setup_split_from(cudaStream_t st, const BsrView<Src> &A64, int64_t nnzb) {
   if (!sF.p || nnz_split != nnzb) {
-    LFX_TRY(sF.alloc(sizeof(S) * 12 * (size_t)nnzb));
+    LFX_TRY(sF.alloc(sizeof(S) * 12 * (size_t)nnzb + 16));   // + 16: the staged pass copies whole 16-byte units
     LFX_TRY(sG.alloc(sizeof(S) * 4 * (size_t)nnzb));
     LFX_TRY(sDC.alloc(sizeof(S) * 4 * (size_t)nnzb));
     nnz_split = nnzb;
   }
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nnzb + kThreads - 1) / kThreads, 152 * 16));
-  pdl_launch(split_kernel<S, Src>, g, kThreads, 0, st, nnzb, A64.vals, sF.as<S>(), sG.as<S>(), sDC.as<S>());
+  pdl_launch(split_kernel<S, Src>, g, kThreads, 0, st, nnzb, A64.vals, A64.col, sF.as<S>(), sG.as<S>(), sDC.as<S>());
   note_launches(1);
+  if (std::is_same<S, __nv_bfloat16>::value && !berr.p) {
+    // error word of the staged velocity smoothing pass, and its host copy
+    LFX_TRY(berr.alloc(16));
+    LFX_CUDA_TRY(cudaMemsetAsync(berr.p, 0, 16, st));
+    if (!berr_host) {
+      LFX_CUDA_TRY(cudaMallocHost(&berr_host, sizeof(int)));
+      *berr_host = 0;
+    }
+  }
   split = true;
   const SplitView<S> sv{A64.V, A64.rowptr, A64.col, A64.diag, A64.trans, sF.as<S>(), sG.as<S>(), sDC.as<S>()};
   return setup_view(st, sv);
+}
+
+// The staged pass serves BF16 sub-blocks stored apart, FP32 vectors, a pattern with row tiles.
+template <class S, class T>
+template <class View>
+bool ASimple<S, T>::use_staged(const View &) const {
+  if constexpr (std::is_same<View, SplitView<__nv_bfloat16>>::value && std::is_same<T, float>::value)
+    return ftile != nullptr && n_ftile > 0 && berr.p != nullptr && (reinterpret_cast<uintptr_t>(sF.p) & 15u) == 0;
+  return false;
+}
+
+template <class S, class T>
+template <class View>
+lfx_status ASimple<S, T>::launch_staged(cudaStream_t st, const View &A, bool first, int k, const T *d_old, T *d_new,
+                                        const T *b0, const KState *ks) {
+  if constexpr (std::is_same<View, SplitView<__nv_bfloat16>>::value && std::is_same<T, float>::value) {
+    // one resident wave of persistent CTAs (the occupancy the kernel's shared memory allows)
+    static int grid[2] = {0, 0};
+    const int f = first ? 1 : 0;
+    if (grid[f] == 0) {
+      auto kern = first ? f_step_staged_kernel<true> : f_step_staged_kernel<false>;
+      LFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFStagedSmem));
+      int dev = 0, sms = 0, per = 0;
+      LFX_CUDA_TRY(cudaGetDevice(&dev));
+      LFX_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      LFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kFTileThreads, kFStagedSmem));
+      grid[f] = std::max(1, sms * std::max(per, 1));
+    }
+    const int g = std::min(grid[f], n_ftile);
+    const SmoothCoef *cf = coef.as<SmoothCoef>();
+    const uint32_t polls = force_bulk_timeout ? 0u : kFWaitPolls;
+    if (first)
+      pdl_launch(f_step_staged_kernel<true>, g, kFTileThreads, kFStagedSmem, st, A, ftile, n_ftile, dinvF.as<float>(),
+                 d_old, d_new, R.as<float>(), X.as<float>(), cf, k, ks, b0, berr.as<int>(), polls);
+    else
+      pdl_launch(f_step_staged_kernel<false>, g, kFTileThreads, kFStagedSmem, st, A, ftile, n_ftile, dinvF.as<float>(),
+                 d_old, d_new, R.as<float>(), X.as<float>(), cf, k, ks, b0, berr.as<int>(), polls);
+    note_launches(1);
+    return LFX_OK;
+  } else {
+    (void)st, (void)A, (void)first, (void)k, (void)d_old, (void)d_new, (void)b0, (void)ks;
+    set_error("aSIMPLE: the staged velocity pass needs BF16 sub-blocks and FP32 vectors");
+    return LFX_ERR_INVALID_ARG;
+  }
 }
 
 // z = P^-1 r (aSIMPLE); r, z are [V][4] vectors of type T (they may not alias the work arrays).
@@ -2264,7 +2509,10 @@ lfx_status ASimple<S, T>::apply_view(cudaStream_t st, const View &A, const T *r,
   T *d[2] = {D0.as<T>(), D1.as<T>()};
   // z_u* ~= F^-1 r_u
   bool pending_w = false;
-  if (cfg.f_steps >= 2) {
+  const bool staged = use_staged(A);
+  if (cfg.f_steps >= 2 && staged) {
+    LFX_TRY(launch_staged(st, A, true, 1, d[0], d[1], r, ks));
+  } else if (cfg.f_steps >= 2) {
     // start of the smoothing fused into step 1 (d_old formed from r on the fly)
     pdl_launch(f_step_kernel<View, T, true>, rg, kThreads, 0, st, A, dinvF.as<T>(), d[0], d[1], R.as<T>(), X.as<T>(),
                cf, 1, 1, nullptr, ks, r);
@@ -2283,9 +2531,12 @@ lfx_status ASimple<S, T>::apply_view(cudaStream_t st, const View &A, const T *r,
       }
     LFX_CUDA_TRY(cudaEventRecord(fev[n_fev], st));
   }
-  for (int k = 2; k < cfg.f_steps; ++k)
-    pdl_launch(f_step_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), d[(k - 1) & 1], d[k & 1], R.as<T>(),
-                                                 X.as<T>(), cf, k, 1, nullptr, ks, nullptr);
+  for (int k = 2; k < cfg.f_steps; ++k) {
+    if (staged) LFX_TRY(launch_staged(st, A, false, k, d[(k - 1) & 1], d[k & 1], nullptr, ks));
+    else
+      pdl_launch(f_step_kernel<View, T>, rg, kThreads, 0, st, A, dinvF.as<T>(), d[(k - 1) & 1], d[k & 1], R.as<T>(),
+                 X.as<T>(), cf, k, 1, nullptr, ks, nullptr);
+  }
   if (timed) {
     LFX_CUDA_TRY(cudaEventRecord(fev[n_fev + 1], st));
     n_fev += 2;
@@ -2573,6 +2824,22 @@ lfx_status ASimple<S, T>::vcycle(cudaStream_t st, int l, const KState *ks) {
 template <class S, class T>
 ASimple<S, T>::~ASimple() {
   for (cudaEvent_t e : fev) cudaEventDestroy(e);
+  if (berr_host) cudaFreeHost(berr_host);
+}
+
+template <class S, class T>
+lfx_status ASimple<S, T>::queue_bulk_check(cudaStream_t st) {
+  if (!berr.p || !berr_host) return LFX_OK;
+  LFX_CUDA_TRY(cudaMemcpyAsync(berr_host, berr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LFX_CUDA_TRY(cudaMemsetAsync(berr.p, 0, sizeof(int), st));
+  return LFX_OK;
+}
+
+template <class S, class T>
+bool ASimple<S, T>::bulk_failed() {
+  if (!berr_host || *berr_host == 0) return false;
+  *berr_host = 0;
+  return true;
 }
 
 // Median duration of one plain F pass over the applications timed since the last read (the

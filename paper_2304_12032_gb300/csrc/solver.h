@@ -98,6 +98,23 @@ struct ASimple {
   DBuf sF, sG, sDC;                // sub-blocks stored apart (setup_split)
   int64_t nnz_split = 0;
   bool split = false;
+  // Staged velocity smoothing pass (BF16 sub-blocks): the pattern's row tiles (device, [n_ftile+1]
+  // row offsets; none: the plain pass runs), and a device error word the pass sets when a wait for
+  // a staged tile gives up, with its page-locked host copy
+  const int32_t *ftile = nullptr;
+  int n_ftile = 0;
+  DBuf berr;
+  int *berr_host = nullptr;
+  void set_tiles(const int32_t *d_tile_row, int n_tiles) {
+    ftile = d_tile_row;
+    n_ftile = n_tiles;
+  }
+  // queues the copy of the error word to the host (and its reset) on st; after st has reached it,
+  // bulk_failed() says whether a wait gave up since the previous check
+  lfx_status queue_bulk_check(cudaStream_t st);
+  bool bulk_failed();
+  // tests: make every wait of the staged pass run out at once (then the pass sets the error word)
+  bool force_bulk_timeout = false;
   int64_t nc = 0;
   std::vector<int64_t> lvl_rows, lvl_nnz;   // hierarchy shape (rows, nonzeros of A_l per level)
   int coop_grid = 0;   // > 0: the coarse V-cycle runs as one cooperative launch of this many CTAs
@@ -137,6 +154,11 @@ struct ASimple {
  private:
   template <class View>
   lfx_status setup_view(cudaStream_t st, const View &A);
+  template <class View>
+  bool use_staged(const View &A) const;
+  template <class View>
+  lfx_status launch_staged(cudaStream_t st, const View &A, bool first, int k, const T *d_old, T *d_new, const T *b0,
+                           const KState *ks);
   template <class Src>
   lfx_status setup_split_from(cudaStream_t st, const BsrView<Src> &A, int64_t nnzb);
   template <class View>

@@ -66,7 +66,7 @@ class lfx_options(ctypes.Structure):
                 ("batch_normalize", ctypes.c_int32), ("batch_segmented", ctypes.c_int32),
                 ("inner_adaptive", ctypes.c_int32), ("implicit", ctypes.c_int32),
                 ("newton_max_iters", ctypes.c_int32), ("assembly", ctypes.c_int32),
-                ("newton_rtol", ctypes.c_double)]
+                ("newton_rtol", ctypes.c_double), ("staged_f", ctypes.c_int32), ("pad2", ctypes.c_int32)]
 
 
 class lfx_mesh_info(ctypes.Structure):
@@ -131,6 +131,7 @@ _SIGS = {
     "lfx_debug_spmv": ([_P, _DP, _DP], ctypes.c_int32),
     "lfx_debug_assemble_newton": ([_P, _DP, _DP, _DP], ctypes.c_int32),
     "lfx_debug_persistent_timeout": ([_P], ctypes.c_int32),
+    "lfx_debug_staged_timeout": ([_P], ctypes.c_int32),
     "lfx_debug_precond": ([_P, _DP, _DP, _DP, _DP], ctypes.c_int32),
     "lfx_debug_solve": ([_P, _DP, ctypes.POINTER(lfx_step_stats)], ctypes.c_int32),
     "lfx_set_allocator": ([ALLOC_FN, FREE_FN, _P], ctypes.c_int32),
@@ -493,6 +494,10 @@ class State:
     def debug_persistent_timeout(self):
         """Status of one persistent assembly whose first grid-wide wait is made to run out."""
         return library().lfx_debug_persistent_timeout(self.h)
+
+    def debug_staged_timeout(self):
+        """Status of one BF16 preconditioner application whose staged-tile waits are made to run out."""
+        return library().lfx_debug_staged_timeout(self.h)
 
     def debug_spmv(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.V, 4)

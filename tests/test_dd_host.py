@@ -6,7 +6,8 @@ Bounds (u = 2^-24, the FP32 unit roundoff):
 * the exact sum a + b: relative error of the result <= 2^-44 even under cancellation;
 * fma_dd (a*b then the exact sum) and fma_dd_fast (one pass, low-order parts summed in FP32):
   error <= 2^-44 (|a b| + |c|), the bound the element terms of the assembly are judged by; the
-  fast form must also be correct to that bound under cancellation (a b ~ -c).
+  fast form must also be correct to that bound under cancellation (a b ~ -c);
+* add_acc (the accumulating sum): error <= 2^-44 (|a| + |b|), also under cancellation.
 A dropped cross product or low part is an error of order u = 2^-24 and fails every bound."""
 import os
 import shutil
@@ -28,8 +29,9 @@ PROG = textwrap.dedent(r"""
       float v[6];
       while (std::scanf("%a %a %a %a %a %a", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 6) {
         const dd a(v[0], v[1]), b(v[2], v[3]), c(v[4], v[5]);
-        const dd r[6] = {a * b, a + b, fma_dd(a, b, c), fma_dd_fast(a, b, c), a / b, dd_rsqrt(dd_abs(a))};
-        for (int k = 0; k < 6; ++k) std::printf("%a %a ", r[k].hi, r[k].lo);
+        const dd r[7] = {a * b, a + b, fma_dd(a, b, c), fma_dd_fast(a, b, c), a / b, dd_rsqrt(dd_abs(a)),
+                         add_acc(a, b)};
+        for (int k = 0; k < 7; ++k) std::printf("%a %a ", r[k].hi, r[k].lo);
         std::printf("\n");
       }
       return 0;
@@ -65,7 +67,7 @@ def _run(exe, rows):
         if not line.strip():
             continue
         t = [Fraction(float.fromhex(x)) for x in line.split()]
-        res.append([t[2 * k] + t[2 * k + 1] for k in range(6)])
+        res.append([t[2 * k] + t[2 * k + 1] for k in range(7)])
     return res
 
 
@@ -88,6 +90,7 @@ def _check(rows, res):
         # rsqrt of |a|: compare squared, y^2 |a| = 1 within 2 x 2^-44
         y = out[5]
         assert abs(y * y * abs(a) - 1) <= 2 * bound
+        assert abs(out[6] - s) <= bound * (abs(a) + abs(b))
 
 
 def test_dd_primitives_random(dd_exe):
@@ -120,6 +123,7 @@ def test_dd_primitives_cancellation(dd_exe):
         a, b, c = _exact(r[0], r[1]), _exact(r[2], r[3]), _exact(r[4], r[5])
         s = a + b
         assert abs(out[1] - s) <= bound * abs(s)            # the exact sum keeps relative accuracy
+        assert abs(out[6] - s) <= bound * (abs(a) + abs(b))  # the accumulating sum: of the operands
         scale = abs(a * b) + abs(c)
         assert abs(out[2] - (a * b + c)) <= bound * scale
         assert abs(out[3] - (a * b + c)) <= bound * scale
