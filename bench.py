@@ -103,12 +103,13 @@ def make_case(n_tets, seed=2):
     return m, time.time() - t0
 
 
-def gpu_problem(L, m, precision):
+def gpu_problem(L, m, precision, **more):
     Q = U_PEAK * math.pi * R_CM ** 2 / 2.0
     bcs = [L.BC(tag=0, kind="noslip"),
            L.BC(tag=1, kind="dirichlet", profile="parabolic", time="ramp", p=(0.0, Q, 0.0, RAMP), radius=R_CM),
            L.BC(tag=2, kind="neumann", time="constant", p=(0.0,))]
     extra = dict(smoother_bf16=1) if precision == "mixed" else {}
+    extra.update(more)
     opts = L.default_options(precision=precision, gmres_rtol=1e-8, **extra)
     mesh = L.Mesh.from_synthetic(m)
     prob = L.Problem(mesh, RHO, MU, DT, 2, bcs, [], opts)
@@ -237,6 +238,26 @@ def kernel_rooflines(stats, T, V, nnzb, prec, bf16=True):
     return roof, kernels
 
 
+def implicit_steps(L, m, hist_u, hist_p, t_start, stream, steps):
+    """The fully implicit VMS-LES step (Newton's method, each update one mixed-precision Krylov
+    solve; Section 2.3's implicit u* and LES term) on the same mesh and history: one untimed step,
+    then `steps` steps timed by the step's own CUDA events."""
+    _, prob = gpu_problem(L, m, "mixed", implicit=1, newton_rtol=1e-8)
+    st = L.State(prob, hist_u, hist_p, t_start, stream=stream)
+    st.step(allow_not_converged=True)
+    stats = [st.step(allow_not_converged=True) for _ in range(steps)]
+    ms = statistics.mean(s["ms_total"] for s in stats)
+    newton = statistics.mean(s["newton_iterations"] for s in stats)
+    return {"workload": "the same cylinder and history, fully implicit (Newton) mixed precision, newton_rtol 1e-8",
+            "steps_per_s": round(1e3 / ms, 3), "ms_per_step": round(ms, 3), "steps": steps,
+            "newton_iterations_mean": round(newton, 2),
+            "ms_per_newton_iteration": round(ms / max(newton, 1e-9), 3),
+            "ms_newton_assembly_per_step": round(statistics.mean(s["ms_newton_assembly"] for s in stats), 3),
+            "krylov_iterations_mean": round(statistics.mean(s["iterations"] for s in stats), 1),
+            "converged": all(bool(s["converged"]) for s in stats),
+            "timing": "the step's CUDA events (assembly + Newton loop), mean over the steps"}
+
+
 def timed_steps(L, st, steps, warmup, stream):
     import torch
 
@@ -361,6 +382,8 @@ def run_gpu(args):
                             "gpu_launches": int(r64["launches"])}
         line["speedup_mixed_vs_fp64"] = round(value / v64, 3)
         line["mixed_vs_fp64_rel_l2_after_steps"] = {"u": float(du), "p": float(dp)}
+    if not sten and args.implicit_steps > 0:
+        line["implicit"] = implicit_steps(L, m, hist_u, hist_p, t_start, stream, args.implicit_steps)
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_tets, target_tets=T, stenosis_case=sten)
     if rank == 0:
@@ -850,6 +873,8 @@ def main():
     ap.add_argument("--tets", type=int, default=1_000_000)
     ap.add_argument("--cpu-sample-tets", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--implicit-steps", type=int, default=3,
+                    help="fully implicit (Newton) steps timed after the semi-implicit ones (0: none)")
     ap.add_argument("--mode", default="step", choices=["step", "stenosis", "beltrami", "serving", "batched"])
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--batch-min", type=int, default=20_000)

@@ -2491,8 +2491,7 @@ lfx_status ASimple<S, T>::launch_staged(cudaStream_t st, const View &A, bool fir
     else
       pdl_launch(f_step_staged_kernel<false>, g, kFTileThreads, kFStagedSmem, st, A, ftile, n_ftile, dinvF.as<float>(),
                  d_old, d_new, R.as<float>(), X.as<float>(), cf, k, ks, b0, berr.as<int>(), polls);
-    note_launches(1);
-    return LFX_OK;
+    return LFX_OK;   // counted by the caller with the plain passes it replaces
   } else {
     (void)st, (void)A, (void)first, (void)k, (void)d_old, (void)d_new, (void)b0, (void)ks;
     set_error("aSIMPLE: the staged velocity pass needs BF16 sub-blocks and FP32 vectors");
