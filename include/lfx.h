@@ -226,11 +226,13 @@ typedef struct lfx_options {
   /* fully implicit formulation (Eq. u_star in its implicit form and the implicit LES term of
    * Section 2.3), linearised by Newton's method (Section 2.4): each step first solves the
    * semi-implicit system, then runs Newton iterations from that solution.  Each iteration
-   * assembles the Jacobian of the element residual (u* = u, tau_M(u*), tau_C(u*), r_M(u, p) at the
-   * iterate, derived analytically) with the right-hand side J U - R(U), and solves for the next
-   * iterate with the configured Krylov method, until ||R|| <= newton_rtol ||b|| (b: the step's
-   * semi-implicit right-hand side; Dirichlet rows s (U_r - g_r)).  Not with backflow
-   * stabilisation or resistance conditions (LFX_ERR_INVALID_ARG at problem creation). */
+   * evaluates R(U) = A(U) U - b(U) with the semi-implicit system assembled at the iterate (u^EXT,
+   * p^EXT := U), stops once ||R|| <= newton_rtol ||b|| (b: the step's semi-implicit right-hand
+   * side; Dirichlet rows s (U_r - g_r)), and otherwise assembles the Jacobian of the element
+   * residual (u* = u, tau_M(u*), tau_C(u*), r_M(u, p) at the iterate, derived analytically) with
+   * the right-hand side J U - R(U) and solves for the next iterate with the configured Krylov
+   * method.  Not with backflow stabilisation or resistance conditions (LFX_ERR_INVALID_ARG at
+   * problem creation). */
   int32_t implicit;             /* 0 (default): semi-implicit; 1: fully implicit with Newton     */
   int32_t newton_max_iters;     /* default 10; the step returns LFX_ERR_NOT_CONVERGED past it   */
   /* assembly launch shape of the semi-implicit system: LFX_ASM_COLORS (one launch per element
@@ -301,7 +303,8 @@ typedef struct lfx_step_stats {
                                    (CUDA events)                                                 */
   int32_t n_spmv;               /* their number (FP64 matrix on the FP64 path, FP32 in mixed)   */
   int32_t newton_iterations;    /* Newton updates taken (fully implicit formulation), else 0    */
-  float ms_newton_assembly;     /* device time of the Newton Jacobian assemblies (CUDA events)  */
+  float ms_newton_assembly;     /* device time of the Newton loop's assemblies: the residual
+                                   checks and the Jacobians (CUDA events)                        */
   int32_t n_fpass;              /* plain F passes of the preconditioner timed in this step (those
                                    of its first application)                                     */
   float ms_fpass_median;        /* their mean duration per pass (CUDA events)                     */

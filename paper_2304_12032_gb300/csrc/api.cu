@@ -1161,14 +1161,18 @@ lfx_status lfx_state_device_bytes(const lfx_state *s, int64_t *bytes) {
 // Assembly of the system for t^{n+1} = t + dt into vals64 / rhs, x0 = extrapolation.  With
 // newton, the Jacobian of the fully implicit formulation at the iterate held in xsol and the
 // right-hand side J U - R(U) instead (the BDF fields of the step's first assembly are kept).
-static lfx_status assemble_system(lfx_state *s, bool apply_bcs, bool newton = false) {
+// newton: the Newton system of the fully implicit step at the iterate in xsol; at_iterate: the
+// semi-implicit system with u^EXT, p^EXT taken from the iterate in xsol (its residual A U - b is the
+// implicit residual R(U)); otherwise the semi-implicit system of the step (the BDF fields are formed
+// and xsol receives the extrapolation).
+static lfx_status assemble_system(lfx_state *s, bool apply_bcs, bool newton = false, bool at_iterate = false) {
   lfx_problem *pb = s->pb;
   const Mesh &m = pb->mesh->m;
   cudaStream_t st = s->stream;
   const double t1 = s->t + pb->P.dt;
   const int sg = s->sigma;
   const bool mixed = s->mixed();
-  if (newton) {
+  if (newton || at_iterate) {
     if (mixed) LFX_TRY(launch_split_vec(st, m.V, s->xsol.as<double>(), s->xe_hi.as<float4>(), s->xe_lo.as<float4>()));
   } else {
     LFX_TRY(launch_bdf(st, m.V, sg, s->level(0), sg > 1 ? s->level(1) : nullptr, sg > 2 ? s->level(2) : nullptr,
@@ -1633,7 +1637,7 @@ static lfx_status newton_residual_norm(lfx_state *s, double *out) {
 }
 
 // Newton iterations of the fully implicit formulation (Section 2.4) from the semi-implicit solution
-// in xsol: assemble J(U_k) and b + X U_k, stop once ||R(U_k)|| <= newton_rtol * scale, else solve
+// in xsol: stop once ||R(U_k)|| <= newton_rtol * scale, else assemble J(U_k) and b + X U_k and solve
 // J U_{k+1} = b + X U_k from U_k.
 static lfx_status newton_loop(lfx_state *s, double scale, int *n_newton, int *its, int *outer, double *rel,
                               float *ms_asm) {
@@ -1643,7 +1647,9 @@ static lfx_status newton_loop(lfx_state *s, double scale, int *n_newton, int *it
   *ms_asm = 0.0f;
   lfx_status status = LFX_OK;
   for (int k = 0;; ++k) {
-    LFX_TRY(assemble_system(s, true, true));
+    // R(U_k) = A(U_k) U_k - b(U_k) from the semi-implicit system at the iterate (the chunked
+    // launches); the Newton system is assembled only when an update follows
+    LFX_TRY(assemble_system(s, true, false, true));
     double fn = 0.0;
     LFX_TRY(newton_residual_norm(s, &fn));
     float ms = 0.0f;
@@ -1659,11 +1665,15 @@ static lfx_status newton_loop(lfx_state *s, double scale, int *n_newton, int *it
       status = LFX_ERR_NOT_CONVERGED;
       break;
     }
+    LFX_TRY(assemble_system(s, true, true));
     LFX_TRY(prepare_precond(s));
     int it = 0, ou = 0;
     double r = 0.0;
     lfx_status rc = run_solve(s, s->xsol.as<double>(), false, &it, &ou, &r);
     if (rc != LFX_OK && rc != LFX_ERR_NOT_CONVERGED) return rc;
+    // the Newton assembly's time (its events are reused by the next assembly)
+    if (cudaEventSynchronize(s->ea1) == cudaSuccess && cudaEventElapsedTime(&ms, s->ea0, s->ea1) == cudaSuccess)
+      *ms_asm += ms;
     *its += it;
     *outer += ou;
     *rel = r;
