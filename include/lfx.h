@@ -101,6 +101,11 @@ lfx_status lfx_mesh_get_colors(const lfx_mesh *mesh, int32_t *colors);
 lfx_status lfx_mesh_get_chunks(const lfx_mesh *mesh, int64_t sizes[5], int32_t *elem_old, int32_t *chunk_elem_off,
                                int32_t *chunk_color_off, int32_t *chunk_pass_off, uint16_t *pass_code,
                                int32_t *pass_run_off, uint16_t *run_meta, int32_t *run_row, int32_t *run_col);
+/* The row tiles of the staged velocity smoothing pass, for inspection and tests (host, no device
+ * work).  sizes = {tiles (0: the mesh has none, the plain pass runs), maximum rows per tile,
+ * maximum blocks per tile}.  Non-NULL arrays receive tile_row [tiles+1] (the internal block-row
+ * range of each tile) and row_node [n_nodes] (the caller node of each internal block row). */
+lfx_status lfx_mesh_get_row_tiles(const lfx_mesh *mesh, int64_t sizes[3], int32_t *tile_row, int32_t *row_node);
 
 /* ------------------------------------------------------------------------------------------
  * Problem: physics (Section 2.1), boundary conditions (Section 2.2), RIIS surfaces (Eq. riis),

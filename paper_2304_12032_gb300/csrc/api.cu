@@ -355,6 +355,20 @@ lfx_status lfx_mesh_get_colors(const lfx_mesh *mesh, int32_t *colors) {
   return LFX_OK;
 }
 
+lfx_status lfx_mesh_get_row_tiles(const lfx_mesh *mesh, int64_t sizes[3], int32_t *tile_row, int32_t *row_node) {
+  if (!mesh || !sizes) {
+    set_error("lfx_mesh_get_row_tiles: NULL argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const Mesh &m = mesh->m;
+  sizes[0] = m.ftile_row.empty() ? 0 : (int64_t)m.ftile_row.size() - 1;
+  sizes[1] = kFTileRows;
+  sizes[2] = kFTileBlocks;
+  if (tile_row) std::copy(m.ftile_row.begin(), m.ftile_row.end(), tile_row);
+  if (row_node) std::copy(m.node_old.begin(), m.node_old.end(), row_node);
+  return LFX_OK;
+}
+
 lfx_status lfx_mesh_get_chunks(const lfx_mesh *mesh, int64_t sizes[5], int32_t *elem_old, int32_t *chunk_elem_off,
                                int32_t *chunk_color_off, int32_t *chunk_pass_off, uint16_t *pass_code,
                                int32_t *pass_run_off, uint16_t *run_meta, int32_t *run_row, int32_t *run_col) {

@@ -109,6 +109,7 @@ _SIGS = {
     "lfx_mesh_get_colors": ([_P, _IP], ctypes.c_int32),
     "lfx_mesh_get_chunks": ([_P, _LP, _IP, _IP, _IP, _IP, ctypes.POINTER(ctypes.c_uint16), _IP,
                              ctypes.POINTER(ctypes.c_uint16), _IP, _IP], ctypes.c_int32),
+    "lfx_mesh_get_row_tiles": ([_P, _LP, _IP, _IP], ctypes.c_int32),
     "lfx_options_default": ([ctypes.POINTER(lfx_options)], None),
     "lfx_problem_create": ([_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                             ctypes.POINTER(lfx_bc), ctypes.c_int32, ctypes.POINTER(lfx_riis), ctypes.c_int32,
@@ -319,6 +320,18 @@ class Mesh:
         c = np.zeros(self.info()["n_tets"], dtype=np.int32)
         _check(library().lfx_mesh_get_colors(self.h, _i(c)))
         return c
+
+    def row_tiles(self) -> dict:
+        """The staged velocity pass's row tiles (see lfx_mesh_get_row_tiles)."""
+        lib = library()
+        sz = np.zeros(3, dtype=np.int64)
+        _check(lib.lfx_mesh_get_row_tiles(self.h, sz.ctypes.data_as(_LP), None, None))
+        n = int(sz[0])
+        tile_row = np.zeros(n + 1, np.int32)
+        row_node = np.zeros(self.info()["n_nodes"], np.int32)
+        _check(lib.lfx_mesh_get_row_tiles(self.h, sz.ctypes.data_as(_LP), _i(tile_row) if n else None, _i(row_node)))
+        return {"tile_row": tile_row if n else np.zeros(0, np.int32), "row_node": row_node,
+                "max_rows": int(sz[1]), "max_blocks": int(sz[2])}
 
     def chunks(self) -> dict:
         """The chunked assembly's tables (see lfx_mesh_get_chunks)."""

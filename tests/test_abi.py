@@ -208,3 +208,31 @@ def test_chunk_tables(L, which):
                 key = (int(ch["run_row"][r]), int(ch["run_col"][r]))
                 lowest[key] = min(lowest.get(key, 1 << 30), ccol[k])
     assert first_of == lowest
+
+
+@pytest.mark.parametrize("which", ["cylinder", "bifurcation"])
+def test_row_tiles(L, which):
+    """The staged velocity pass's row tiles (host, no GPU): consecutive block rows from 0 to n_nodes,
+    each within both limits (rows, blocks = the rows' pattern lengths), and greedy: no tile but the
+    last could take its successor's first row without breaking a limit; the internal row order is a
+    permutation of the caller's nodes."""
+    from synthetic import bifurcation
+
+    m = cylinder(1.0, 3.0, n_tets=20000, seed=7) if which == "cylinder" else bifurcation(n_tets=20000, seed=1002)
+    mesh = L.Mesh.from_synthetic(m)
+    t = mesh.row_tiles()
+    rp, _ = mesh.pattern()
+    V = m.n_nodes
+    node = t["row_node"]
+    assert np.array_equal(np.sort(node), np.arange(V))
+    length = (rp[1:] - rp[:-1])[node]               # blocks of each internal row
+    tr = t["tile_row"]
+    assert tr.size >= 2 and tr[0] == 0 and tr[-1] == V and np.all(np.diff(tr) >= 1)
+    cum = np.concatenate([[0], np.cumsum(length)])
+    rows = np.diff(tr)
+    blocks = cum[tr[1:]] - cum[tr[:-1]]
+    assert rows.max() <= t["max_rows"] and blocks.max() <= t["max_blocks"]
+    nxt = tr[1:-1]                                  # first row of each following tile
+    grow_rows = rows[:-1] + 1
+    grow_blocks = blocks[:-1] + length[nxt]
+    assert np.all((grow_rows > t["max_rows"]) | (grow_blocks > t["max_blocks"]))
