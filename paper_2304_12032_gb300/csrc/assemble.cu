@@ -845,11 +845,17 @@ constexpr int kStage = 17;          // staging row: 16 values + 1 to spread shar
 __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
+constexpr int kChunkMaxRuns = 4 * kCta;   // a chunk's slots, the most runs it can have
 template <class R>
 struct ChunkShared {
   ElemShared<R> e;
   R stage[kCta][kStage];
   R rst[kCta][4];
+  // the chunk's tables, staged at its start (runs numbered from the chunk's first run)
+  uint16_t code[kChunkMaxPasses * kCta];
+  uint16_t meta[kChunkMaxRuns];
+  int32_t block[kChunkMaxRuns], node[kChunkMaxRuns];
+  int32_t run_off[kChunkMaxPasses + 1], ndiag[kChunkMaxPasses];
 };
 
 // Four consecutive matrix values or one node's four right-hand-side entries (16-byte aligned): their
@@ -909,47 +915,95 @@ struct AccumOut<float, dd> {
 };
 constexpr int kItemsInFlight = 2;   // reduction items (four values each) per thread loaded together (1 and 4 were slower)
 
+// Geometry of the elements e0..e1-1 of a chunk from the cache (the CTA's threads load kGeoValues
+// values of each; for a fixed value index, consecutive elements are consecutive in memory)
+template <class R>
+__device__ void geom_load_range(const AssembleArgs &A, int64_t T, int64_t e0, int64_t e1, ElemShared<R> &sh) {
+  for (int idx = threadIdx.x; idx < kGeoValues * kElems; idx += kCta) {
+    const int k = idx / kElems, le = idx % kElems;
+    const int64_t e = e0 + le;
+    if (e >= e1) continue;
+    const R v = geo_value<R>(A, k, e, T);
+    if (k < 12) sh.gphi[le][k] = v;
+    else if (k < 21) sh.Gm[le][k - 12] = v;
+    else if (k == 21) sh.igg[le] = v;
+    else if (k == 22) sh.w[le] = v;
+    else sh.GG[le] = v;
+  }
+}
+
+// The chunks c0 + blockIdx.x, c0 + blockIdx.x + gridDim.x, ... (< c1).  Each chunk's slot codes,
+// run tables and pass offsets are staged in shared memory at its start with loads that do not
+// wait on one another (its geometry loads among them), and the next chunk's offsets are loaded
+// while this one is processed, so that no phase waits on a chain of dependent global loads.
 template <class R, class S>
 __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q,
                                             const ChunkArgs &C, int64_t c0, int64_t c1, S *vals, ChunkShared<R> &cs) {
   ElemShared<R> &sh = cs.e;
   const int t = threadIdx.x;
-  for (int64_t ch = c0 + blockIdx.x; ch < c1; ch += gridDim.x) {
-    const int64_t e0 = C.elem_off[ch], e1 = C.elem_off[ch + 1];
-    {
-      // the blocks (and rows) this chunk adds to, into L2 ahead of its reduction phases
-      const int rb = C.run_off[C.pass_off[ch]], re = C.run_off[C.pass_off[ch + 1]];
-      for (int r = rb + t; r < re; r += kCta) {
-        const uint32_t meta = C.meta[r];
-        if ((meta >> 14) & 1) continue;
-        const int64_t k = (int64_t)C.block[r] * 16;
-        prefetch_l2(vals + k);
-        if (std::is_same<R, dd>::value) prefetch_l2(A.vals_lo + k);
-        if (meta >> 15) {
-          const int64_t rr = 4 * (int64_t)C.node[r];
-          if (std::is_same<R, dd>::value) {
-            prefetch_l2(A.rhs_hi + rr);
-            prefetch_l2(A.rhs_lo + rr);
-          } else {
-            prefetch_l2(A.rhs + rr);
-          }
+  int64_t ch = c0 + blockIdx.x;
+  int32_t e0 = 0, e1 = 0, p0 = 0, p1 = 0, rb = 0, re = 0;
+  if (ch < c1) {
+    e0 = C.elem_off[ch];
+    e1 = C.elem_off[ch + 1];
+    p0 = C.pass_off[ch];
+    p1 = C.pass_off[ch + 1];
+    rb = C.run_off[p0];
+    re = C.run_off[p1];
+  }
+  for (; ch < c1; ch += gridDim.x) {
+    const int64_t chn = ch + gridDim.x;
+    int32_t ne0 = 0, ne1 = 0, np0 = 0, np1 = 0;
+    if (chn < c1) {
+      ne0 = C.elem_off[chn];
+      ne1 = C.elem_off[chn + 1];
+      np0 = C.pass_off[chn];
+      np1 = C.pass_off[chn + 1];
+    }
+    const int npass = p1 - p0, nrun = re - rb;
+    for (int i = t; i < npass * kCta; i += kCta) cs.code[i] = C.code[(int64_t)p0 * kCta + i];
+    for (int i = t; i < nrun; i += kCta) {
+      cs.meta[i] = C.meta[rb + i];
+      cs.block[i] = C.block[rb + i];
+      cs.node[i] = C.node[rb + i];
+    }
+    if (t <= npass) cs.run_off[t] = C.run_off[p0 + t] - rb;
+    if (t < npass) cs.ndiag[t] = C.ndiag[p0 + t];
+    if (t < kElems) sh.eid[t] = e0 + t < e1 ? (int32_t)(e0 + t) : -1;
+    if (has_geo<R>(A)) geom_load_range<R>(A, A.n_elems, e0, e1, sh);
+    else if (t < kElems && e0 + t < e1) geom_phase<R>(A, e0 + t, t, sh);
+    __syncthreads();
+    // the blocks (and rows) this chunk adds to, into L2 ahead of its reduction phases
+    for (int r = t; r < nrun; r += kCta) {
+      const uint32_t meta = cs.meta[r];
+      if ((meta >> 14) & 1) continue;
+      const int64_t k = (int64_t)cs.block[r] * 16;
+      prefetch_l2(vals + k);
+      if (std::is_same<R, dd>::value) prefetch_l2(A.vals_lo + k);
+      if (meta >> 15) {
+        const int64_t rr = 4 * (int64_t)cs.node[r];
+        if (std::is_same<R, dd>::value) {
+          prefetch_l2(A.rhs_hi + rr);
+          prefetch_l2(A.rhs_lo + rr);
+        } else {
+          prefetch_l2(A.rhs + rr);
         }
       }
     }
-    if (t < kElems) sh.eid[t] = e0 + t < e1 ? (int32_t)(e0 + t) : -1;
-    __syncthreads();
-    if (has_geo<R>(A)) geom_load<R>(A, A.n_elems, sh);
-    else if (t < kElems && sh.eid[t] >= 0) geom_phase<R>(A, sh.eid[t], t, sh);
-    __syncthreads();
     const int le = t >> 2, q = t & 3;
     const bool live = sh.eid[le] >= 0;
     if (live) qp_phase<R, false>(A, P, Q, sh.eid[le], q, le, sh, nullptr);
     __syncthreads();
     if (live) node_phase<R, false>(P, Q, q, le, sh, nullptr);
+    // the next chunk's run range (its pass offsets have arrived by now)
+    int32_t nrb = 0, nre = 0;
+    if (chn < c1) {
+      nrb = C.run_off[np0];
+      nre = C.run_off[np1];
+    }
     __syncthreads();
-    const int p1 = C.pass_off[ch + 1];
-    for (int ps = C.pass_off[ch]; ps < p1; ++ps) {
-      const uint16_t code = C.code[(int64_t)ps * kCta + t];
+    for (int pi = 0; pi < npass; ++pi) {
+      const uint16_t code = cs.code[pi * kCta + t];
       if (code != 0xffffu) {
         const int l2 = code >> 4, a = (code >> 2) & 3, b = code & 3;
         R blk[16];
@@ -962,7 +1016,7 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
         }
       }
       __syncthreads();
-      const int r0 = C.run_off[ps], nr = C.run_off[ps + 1] - r0, nd = C.ndiag[ps];
+      const int r0 = cs.run_off[pi], nr = cs.run_off[pi + 1] - r0, nd = cs.ndiag[pi];
       const int items = 4 * nr + nd;     // a block's values in four quarters; a diagonal run's rhs row
       using Out = AccumOut<S, R>;
       for (int jb = t; jb < items; jb += kCta * kItemsInFlight) {
@@ -978,10 +1032,10 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
           const bool blk_item = j < 4 * nr;
           const int run = r0 + (blk_item ? j >> 2 : j - 4 * nr);
           const int v0 = blk_item ? 4 * (j & 3) : 0;
-          const uint32_t meta = C.meta[run];
+          const uint32_t meta = cs.meta[run];
           first[i] = (meta >> 14) & 1;
           is_rhs[i] = !blk_item;
-          where[i] = blk_item ? (int64_t)C.block[run] * 16 + v0 : 4 * (int64_t)C.node[run];
+          where[i] = blk_item ? (int64_t)cs.block[run] * 16 + v0 : 4 * (int64_t)cs.node[run];
           if (!first[i]) old[i] = Out::load(A, vals, where[i], is_rhs[i]);
           const int st0 = meta & 0xff, len = (meta >> 8) & 63;
 #pragma unroll
@@ -995,8 +1049,14 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
         for (int i = 0; i < kItemsInFlight; ++i)
           if (where[i] >= 0) Out::store(A, vals, where[i], is_rhs[i], sum[i], old[i], first[i]);
       }
-      __syncthreads();
+      __syncthreads();   // (the last one also frees the staged tables for the next chunk)
     }
+    e0 = ne0;
+    e1 = ne1;
+    p0 = np0;
+    p1 = np1;
+    rb = nrb;
+    re = nre;
   }
 }
 

@@ -180,6 +180,8 @@ struct PhysParams {
 };
 
 constexpr int kChunkElems = 32;     // elements per chunk (one CTA pass of the assembly kernels)
+constexpr int kChunkMaxPasses = 8;  // passes of 4 kChunkElems slots a chunk may take (the kernels stage
+                                    // a chunk's slot codes for this many in shared memory)
 // tile limits of the staged velocity smoothing pass (its CTA handles kFTileRows rows with 4 lanes
 // each, and stages at most kFTileBlocks 24-byte BF16 sub-block records in each of two buffers;
 // measured on a 1M-tet mesh against 64-row tiles of 1536, 1024, 768 and 512 blocks: small buffers

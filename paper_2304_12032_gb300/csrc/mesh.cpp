@@ -530,6 +530,10 @@ lfx_status build_mesh(const double *nodes, int64_t n_nodes, const int32_t *tets_
         m.pass_ndiag.push_back(ndiag);
         m.pass_run_off.push_back((int32_t)m.run_block.size());
       }
+      if ((int)passes.size() > kChunkMaxPasses) {
+        set_error("lfx_mesh_create: a chunk needs %d passes (more than %d)", (int)passes.size(), kChunkMaxPasses);
+        return LFX_ERR_INVALID_ARG;
+      }
       m.chunk_pass_off[k + 1] = m.chunk_pass_off[k] + (int32_t)passes.size();
     }
   }
