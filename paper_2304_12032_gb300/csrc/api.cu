@@ -146,8 +146,8 @@ struct lfx_problem {
   // with the tuning times (ms per assembly: colours, chunks, persistent) and the device copy of the
   // chunk colour offsets the persistent launch reads
   std::mutex tune_mu;
-  int asm_mode = 0;
-  float asm_ms[3] = {0.0f, 0.0f, 0.0f};
+  int asm_mode = 0, asm_mode_newton = 0;   // launch shapes of the semi-implicit and Newton systems
+  float asm_ms[3] = {0.0f, 0.0f, 0.0f}, asm_ms_newton[3] = {0.0f, 0.0f, 0.0f};
   DBuf d_chunk_color_off;
   size_t device_bytes() const {
     return d_dir_node.bytes + d_dir_bc.bytes + d_S.bytes + d_neu_node.bytes + d_neu_bc.bytes +
@@ -948,7 +948,7 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
   LFX_TRY(pb->d_chunk_color_off.alloc(sizeof(int32_t) * m.chunk_color_off.size()));
   LFX_CUDA_TRY(cudaMemcpy(pb->d_chunk_color_off.p, m.chunk_color_off.data(), sizeof(int32_t) * m.chunk_color_off.size(),
                           cudaMemcpyHostToDevice));
-  pb->asm_mode = o.assembly;
+  pb->asm_mode = pb->asm_mode_newton = o.assembly;
   *out = pb.release();
   return LFX_OK;
 }
@@ -1257,28 +1257,31 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs, bool newton = fa
   // one assembly of the semi-implicit system (or the Newton system) in launch shape `mode`
   auto launch = [&](int mode) -> lfx_status {
     if (mixed) {
-      if (newton || mode == LFX_ASM_COLORS)
+      if (mode == LFX_ASM_COLORS)
         return launch_assemble<dd, float>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
                                           s->vals32.as<float>(), newton);
       if (mode == LFX_ASM_CHUNKS)
         return launch_assemble_chunks<dd, float>(st, A, pb->P, CA, m.chunk_color_off.data(), n_cc,
-                                                 s->vals32.as<float>());
+                                                 s->vals32.as<float>(), newton);
       return launch_assemble_persistent<dd, float>(st, A, pb->P, CA, pb->d_chunk_color_off.as<int32_t>(), n_cc,
-                                                   s->vals32.as<float>(), barrier, err, s->force_timeout);
+                                                   s->vals32.as<float>(), barrier, err, s->force_timeout, newton);
     }
-    if (newton || mode == LFX_ASM_COLORS)
+    if (mode == LFX_ASM_COLORS)
       return launch_assemble<double, double>(st, A, pb->P, m.color_off.data(), (int)m.color_off.size() - 1,
                                              s->vals64.as<double>(), newton);
     if (mode == LFX_ASM_CHUNKS)
       return launch_assemble_chunks<double, double>(st, A, pb->P, CA, m.chunk_color_off.data(), n_cc,
-                                                    s->vals64.as<double>());
+                                                    s->vals64.as<double>(), newton);
     return launch_assemble_persistent<double, double>(st, A, pb->P, CA, pb->d_chunk_color_off.as<int32_t>(), n_cc,
-                                                      s->vals64.as<double>(), barrier, err, s->force_timeout);
+                                                      s->vals64.as<double>(), barrier, err, s->force_timeout, newton);
   };
   int mode = LFX_ASM_COLORS;
-  if (!newton) {
+  {
+    // the semi-implicit and the Newton systems are tuned apart (their kernels fit the SMs differently)
     std::lock_guard<std::mutex> lk(pb->tune_mu);
-    if (pb->asm_mode == LFX_ASM_AUTO) {
+    int &tuned = newton ? pb->asm_mode_newton : pb->asm_mode;
+    float *tuned_ms = newton ? pb->asm_ms_newton : pb->asm_ms;
+    if (tuned == LFX_ASM_AUTO) {
       // autotuner: each launch shape twice (the second timed) on this state's buffers; the fastest
       // becomes the problem's shape (every assembly writes the complete system, so the last one run
       // leaves a valid matrix behind)
@@ -1292,21 +1295,21 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs, bool newton = fa
         LFX_CUDA_TRY(cudaEventSynchronize(s->ea1));
         float ms = 0.0f;
         LFX_CUDA_TRY(cudaEventElapsedTime(&ms, s->ea0, s->ea1));
-        pb->asm_ms[cand - 1] = ms;
+        tuned_ms[cand - 1] = ms;
         if (cand == LFX_ASM_COLORS || ms < best) {
           best = ms;
           pick = cand;
         }
       }
-      pb->asm_mode = pick;
+      tuned = pick;
     }
-    mode = pb->asm_mode;
+    mode = tuned;
   }
-  s->asm_mode_used = newton ? LFX_ASM_COLORS : mode;
+  if (!newton) s->asm_mode_used = mode;
   LFX_CUDA_TRY(cudaEventRecord(s->ea0, st));
   LFX_TRY(launch(mode));
   LFX_CUDA_TRY(cudaEventRecord(s->ea1, st));
-  if (!newton && mode == LFX_ASM_PERSISTENT)
+  if (mode == LFX_ASM_PERSISTENT)
     LFX_CUDA_TRY(cudaMemcpyAsync(s->asm_err_host, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   if (pb->n_bf_edges > 0)
     LFX_TRY(launch_backflow(st, pb->n_bf_edges, pb->d_bf_ij.as<int32_t>(), pb->d_bf_an.as<double>(),
@@ -1315,8 +1318,8 @@ static lfx_status assemble_system(lfx_state *s, bool apply_bcs, bool newton = fa
                             mixed ? nullptr : s->vals64.as<double>(), mixed ? s->vals32.as<float>() : nullptr,
                             mixed ? s->vals_lo.as<float>() : nullptr));
   if (mixed) LFX_TRY(launch_dd_combine(st, 4 * m.V, s->rhs_hi.as<float>(), s->rhs_lo.as<float>(), s->rhs.as<double>()));
-  s->n_asm_launch = (newton || mode == LFX_ASM_COLORS) ? (int)m.color_off.size() - 1
-                                                       : (mode == LFX_ASM_CHUNKS ? n_cc : 1);
+  if (!newton)
+    s->n_asm_launch = mode == LFX_ASM_COLORS ? (int)m.color_off.size() - 1 : (mode == LFX_ASM_CHUNKS ? n_cc : 1);
   // boundary data at t^{n+1}
   DirCoef C;
   memset(&C, 0, sizeof(C));

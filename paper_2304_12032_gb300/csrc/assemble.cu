@@ -588,8 +588,8 @@ __device__ __forceinline__ dd quad_sum<dd>(dd v, unsigned mask) {
 // Newton terms of block (a, b) of the fully implicit formulation: the derivatives of the element
 // residual through u* (advection velocity and SUPG / VMS test functions), tau_M(u*), tau_C(u*) and
 // the second r_M factor of the LES term, which the semi-implicit matrix assembled at the iterate
-// (u^EXT = u, p^EXT = p) leaves out; added to blk.  Returns in ext[i] this block's share
-// (X_ab U_b)_i of the right-hand side J U - R(U) = b(U) + X U.
+// (u^EXT = u, p^EXT = p) leaves out; added to blk.  Returns in ext[i] this block's own share
+// (X_ab U_b)_i of the right-hand side J U - R(U) = b(U) + X U (the caller sums it over b).
 template <class R>
 __device__ void newton_block(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q, int64_t e, int le,
                              int a, int b, const ElemShared<R> &sh, const ImplShared<R> &ix, R blk[16], R ext[4]) {
@@ -670,9 +670,8 @@ __device__ void newton_block(const AssembleArgs &A, const PhysParams &P, const P
     blk[12 + i] += Zp[i];
     ev[3] = fmadd(Zp[i], Ub[i], ev[3]);
   }
-  const unsigned mask = 0xFu << (threadIdx.x & 28);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) ext[i] = quad_sum<R>(ev[i], mask);
+  for (int i = 0; i < 4; ++i) ext[i] = ev[i];
 }
 
 // Right-hand-side entry (a, i) of element slot le: (f + rho u^BDF/dt, v) with the SUPG, VMS and
@@ -744,8 +743,12 @@ __device__ void block_phase(const AssembleArgs &A, const PhysParams &P, const Ph
   block_values<R>(P, le, a, b, sh, blk);
   R rhs = rhs_value<R>(P, sh, le, a, i_rhs);
   if (IMPL) {
+    // the row's share sum_b (X_ab U_b): the quad of lanes of blocks (a, 0..3) sums it
     R ext[4];
     newton_block<R>(A, P, Q, e, le, a, b, sh, *ix, blk, ext);
+    const unsigned mask = 0xFu << (threadIdx.x & 28);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ext[i] = quad_sum<R>(ext[i], mask);
     rhs += (i_rhs == 0) ? ext[0] : ((i_rhs == 1) ? ext[1] : ((i_rhs == 2) ? ext[2] : ext[3]));
   }
   const int32_t s = A.slot[e * 16 + 4 * a + b];
@@ -846,7 +849,13 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 constexpr int kChunkMaxRuns = 4 * kCta;   // a chunk's slots, the most runs it can have
+struct ChunkNoImpl {};
 template <class R>
+struct ChunkImpl {
+  ImplShared<R> x;
+  R ext[kElems][4][4][4];   // [element][a][b][i]: block (a, b)'s share (X_ab U_b)_i of row a's right-hand side
+};
+template <class R, bool IMPL = false>
 struct ChunkShared {
   ElemShared<R> e;
   R stage[kCta][kStage];
@@ -856,6 +865,7 @@ struct ChunkShared {
   uint16_t meta[kChunkMaxRuns];
   int32_t block[kChunkMaxRuns], node[kChunkMaxRuns];
   int32_t run_off[kChunkMaxPasses + 1], ndiag[kChunkMaxPasses];
+  typename std::conditional<IMPL, ChunkImpl<R>, ChunkNoImpl>::type n;   // Newton data (IMPL)
 };
 
 // Four consecutive matrix values or one node's four right-hand-side entries (16-byte aligned): their
@@ -936,10 +946,13 @@ __device__ void geom_load_range(const AssembleArgs &A, int64_t T, int64_t e0, in
 // run tables and pass offsets are staged in shared memory at its start with loads that do not
 // wait on one another (its geometry loads among them), and the next chunk's offsets are loaded
 // while this one is processed, so that no phase waits on a chain of dependent global loads.
-template <class R, class S>
+template <class R, class S, bool IMPL>
 __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q,
-                                            const ChunkArgs &C, int64_t c0, int64_t c1, S *vals, ChunkShared<R> &cs) {
+                                            const ChunkArgs &C, int64_t c0, int64_t c1, S *vals,
+                                            ChunkShared<R, IMPL> &cs) {
   ElemShared<R> &sh = cs.e;
+  ImplShared<R> *ix = nullptr;
+  if constexpr (IMPL) ix = &cs.n.x;
   const int t = threadIdx.x;
   int64_t ch = c0 + blockIdx.x;
   int32_t e0 = 0, e1 = 0, p0 = 0, p1 = 0, rb = 0, re = 0;
@@ -992,9 +1005,9 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
     }
     const int le = t >> 2, q = t & 3;
     const bool live = sh.eid[le] >= 0;
-    if (live) qp_phase<R, false>(A, P, Q, sh.eid[le], q, le, sh, nullptr);
+    if (live) qp_phase<R, IMPL>(A, P, Q, sh.eid[le], q, le, sh, ix);
     __syncthreads();
-    if (live) node_phase<R, false>(P, Q, q, le, sh, nullptr);
+    if (live) node_phase<R, IMPL>(P, Q, q, le, sh, ix);
     // the next chunk's run range (its pass offsets have arrived by now)
     int32_t nrb = 0, nre = 0;
     if (chn < c1) {
@@ -1008,6 +1021,12 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
         const int l2 = code >> 4, a = (code >> 2) & 3, b = code & 3;
         R blk[16];
         block_values<R>(P, l2, a, b, sh, blk);
+        if constexpr (IMPL) {
+          R ev[4];
+          newton_block<R>(A, P, Q, e0 + l2, l2, a, b, sh, *ix, blk, ev);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) cs.n.ext[l2][a][b][i] = ev[i];
+        }
 #pragma unroll
         for (int k = 0; k < 16; ++k) cs.stage[t][k] = blk[k];
         if (a == b) {
@@ -1051,6 +1070,31 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
       }
       __syncthreads();   // (the last one also frees the staged tables for the next chunk)
     }
+    if constexpr (IMPL) {
+      // Newton right-hand side: every node row of the chunk (one diagonal run each) gains the
+      // shares sum_b (X_ab U_b) of the elements of its run, added once to the row
+      using Out = AccumOut<S, R>;
+      for (int pi = 0; pi < npass; ++pi) {
+        const int r0 = cs.run_off[pi], nd = cs.ndiag[pi];
+        for (int j = t; j < nd; j += kCta) {
+          const uint32_t meta = cs.meta[r0 + j];
+          const int st0 = meta & 0xff, len = (meta >> 8) & 63;
+          R sum[4];
+          for (int k = 0; k < len; ++k) {
+            const uint16_t code = cs.code[pi * kCta + st0 + k];
+            const int l2 = code >> 4, a = (code >> 2) & 3;
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb)
+#pragma unroll
+              for (int i = 0; i < 4; ++i) sum[i] = (k == 0 && bb == 0) ? cs.n.ext[l2][a][0][i] : acc(sum[i], cs.n.ext[l2][a][bb][i]);
+          }
+          const int64_t where = 4 * (int64_t)cs.node[r0 + j];
+          const typename Out::Old old = Out::load(A, vals, where, true);
+          Out::store(A, vals, where, true, sum, old, false);
+        }
+      }
+      __syncthreads();
+    }
     e0 = ne0;
     e1 = ne1;
     p0 = np0;
@@ -1060,14 +1104,15 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
   }
 }
 
-// one launch per chunk colour
-template <class R, class S>
-__global__ void __launch_bounds__(kCta, MinCtas<R>::value) assemble_chunk_kernel(AssembleArgs A, PhysParams P,
-                                                                                PhysR<R> Q, ChunkArgs C,
-                                                                                int64_t c0, int64_t c1, S *vals) {
+// one launch per chunk colour (IMPL: the Newton system of the fully implicit step)
+template <class R, class S, bool IMPL>
+__global__ void __launch_bounds__(kCta, IMPL ? 1 : MinCtas<R>::value) assemble_chunk_kernel(AssembleArgs A, PhysParams P,
+                                                                                          PhysR<R> Q, ChunkArgs C,
+                                                                                          int64_t c0, int64_t c1,
+                                                                                          S *vals) {
   pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  chunk_range<R, S>(A, P, Q, C, c0, c1, vals, *reinterpret_cast<ChunkShared<R> *>(smem_raw));
+  chunk_range<R, S, IMPL>(A, P, Q, C, c0, c1, vals, *reinterpret_cast<ChunkShared<R, IMPL> *>(smem_raw));
 }
 
 // Grid-wide barrier of a co-resident (cooperatively launched) grid on a counter that only grows:
@@ -1102,14 +1147,14 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, i
 
 // every chunk colour in one cooperative launch, colours separated by grid-wide barriers (a test
 // can pass unreachable > 0 with a small max_spins to make the first wait run out)
-template <class R, class S>
-__global__ void __launch_bounds__(kCta, MinCtas<R>::value) assemble_chunks_persistent_kernel(
+template <class R, class S, bool IMPL>
+__global__ void __launch_bounds__(kCta, IMPL ? 1 : MinCtas<R>::value) assemble_chunks_persistent_kernel(
     AssembleArgs A, PhysParams P, PhysR<R> Q, ChunkArgs C, const int32_t *color_off, int n_colors, S *vals,
     unsigned *barrier, int *err, unsigned unreachable, unsigned max_spins) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ChunkShared<R> &cs = *reinterpret_cast<ChunkShared<R> *>(smem_raw);
+  ChunkShared<R, IMPL> &cs = *reinterpret_cast<ChunkShared<R, IMPL> *>(smem_raw);
   for (int c = 0; c < n_colors; ++c) {
-    chunk_range<R, S>(A, P, Q, C, color_off[c], color_off[c + 1], vals, cs);
+    chunk_range<R, S, IMPL>(A, P, Q, C, color_off[c], color_off[c + 1], vals, cs);
     if (c + 1 < n_colors &&
         !grid_barrier(barrier, (unsigned)(c + 1) * gridDim.x + unreachable, err, max_spins))
       return;
@@ -1387,46 +1432,53 @@ lfx_status launch_comp_normalize_dd(cudaStream_t st, int64_t V, int n_comp, cons
   return LFX_OK;
 }
 
-template <class R, class S>
-lfx_status launch_assemble_chunks(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
-                                  const int32_t *chunk_color_off, int n_colors, S *vals) {
+template <class R, class S, bool IMPL>
+lfx_status launch_chunks_impl(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
+                              const int32_t *chunk_color_off, int n_colors, S *vals) {
   const PhysR<R> Q = phys_r<R>(P);
-  const size_t smem = sizeof(ChunkShared<R>);
+  const size_t smem = sizeof(ChunkShared<R, IMPL>);
   static bool attr_set = false;
   if (!attr_set) {
-    LFX_CUDA_TRY(cudaFuncSetAttribute(assemble_chunk_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LFX_CUDA_TRY(cudaFuncSetAttribute(assemble_chunk_kernel<R, S, IMPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     attr_set = true;
   }
   int dev = 0, nsm = 152, per_sm = 1;
   LFX_CUDA_TRY(cudaGetDevice(&dev));
   LFX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  LFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assemble_chunk_kernel<R, S>, kCta, smem));
+  LFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assemble_chunk_kernel<R, S, IMPL>, kCta, smem));
   const int64_t resident = (int64_t)nsm * std::max(per_sm, 1);
   for (int c = 0; c < n_colors; ++c) {
     const int64_t c0 = chunk_color_off[c], c1 = chunk_color_off[c + 1];
     if (c1 <= c0) continue;
     const int grid = (int)std::min<int64_t>(c1 - c0, resident);
-    pdl_launch(assemble_chunk_kernel<R, S>, grid, kCta, smem, st, A, P, Q, C, c0, c1, vals);
+    pdl_launch(assemble_chunk_kernel<R, S, IMPL>, grid, kCta, smem, st, A, P, Q, C, c0, c1, vals);
     note_launches(1);
   }
   LFX_CUDA_TRY(cudaGetLastError());
   return LFX_OK;
 }
-template lfx_status launch_assemble_chunks<double, double>(cudaStream_t, const AssembleArgs &, const PhysParams &,
-                                                           const ChunkArgs &, const int32_t *, int, double *);
-template lfx_status launch_assemble_chunks<dd, float>(cudaStream_t, const AssembleArgs &, const PhysParams &,
-                                                      const ChunkArgs &, const int32_t *, int, float *);
 
 template <class R, class S>
-lfx_status launch_assemble_persistent(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
-                                      const int32_t *d_chunk_color_off, int n_colors, S *vals, unsigned *barrier,
-                                      int *err, bool force_timeout) {
+lfx_status launch_assemble_chunks(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
+                                  const int32_t *chunk_color_off, int n_colors, S *vals, bool newton) {
+  return newton ? launch_chunks_impl<R, S, true>(st, A, P, C, chunk_color_off, n_colors, vals)
+                : launch_chunks_impl<R, S, false>(st, A, P, C, chunk_color_off, n_colors, vals);
+}
+template lfx_status launch_assemble_chunks<double, double>(cudaStream_t, const AssembleArgs &, const PhysParams &,
+                                                           const ChunkArgs &, const int32_t *, int, double *, bool);
+template lfx_status launch_assemble_chunks<dd, float>(cudaStream_t, const AssembleArgs &, const PhysParams &,
+                                                      const ChunkArgs &, const int32_t *, int, float *, bool);
+
+template <class R, class S, bool IMPL>
+lfx_status launch_persistent_impl(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
+                                  const int32_t *d_chunk_color_off, int n_colors, S *vals, unsigned *barrier, int *err,
+                                  bool force_timeout) {
   const PhysR<R> Q = phys_r<R>(P);
-  const size_t smem = sizeof(ChunkShared<R>);
+  const size_t smem = sizeof(ChunkShared<R, IMPL>);
   static bool attr_set = false;
   if (!attr_set) {
-    LFX_CUDA_TRY(cudaFuncSetAttribute(assemble_chunks_persistent_kernel<R, S>,
+    LFX_CUDA_TRY(cudaFuncSetAttribute(assemble_chunks_persistent_kernel<R, S, IMPL>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_set = true;
   }
@@ -1434,8 +1486,8 @@ lfx_status launch_assemble_persistent(cudaStream_t st, const AssembleArgs &A, co
   LFX_CUDA_TRY(cudaGetDevice(&dev));
   LFX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   LFX_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  LFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assemble_chunks_persistent_kernel<R, S>, kCta,
-                                                              smem));
+  LFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assemble_chunks_persistent_kernel<R, S, IMPL>,
+                                                              kCta, smem));
   if (!coop || per_sm < 1) {
     set_error("persistent assembly: cooperative launch unavailable");
     return LFX_ERR_CUDA;
@@ -1446,17 +1498,27 @@ lfx_status launch_assemble_persistent(cudaStream_t st, const AssembleArgs &A, co
   unsigned unreachable = force_timeout ? 1u : 0u, max_spins = force_timeout ? (1u << 12) : kBarrierSpins;
   void *args[] = {(void *)&A, (void *)&P, (void *)&Q, (void *)&C, (void *)&d_chunk_color_off, (void *)&n_colors,
                   (void *)&vals, (void *)&barrier, (void *)&err, (void *)&unreachable, (void *)&max_spins};
-  LFX_CUDA_TRY(cudaLaunchCooperativeKernel((void *)assemble_chunks_persistent_kernel<R, S>, dim3(grid), dim3(kCta), args,
-                                           smem, st));
+  LFX_CUDA_TRY(cudaLaunchCooperativeKernel((void *)assemble_chunks_persistent_kernel<R, S, IMPL>, dim3(grid), dim3(kCta),
+                                           args, smem, st));
   note_launches(1);
   return LFX_OK;
 }
+
+template <class R, class S>
+lfx_status launch_assemble_persistent(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
+                                      const int32_t *d_chunk_color_off, int n_colors, S *vals, unsigned *barrier,
+                                      int *err, bool force_timeout, bool newton) {
+  return newton ? launch_persistent_impl<R, S, true>(st, A, P, C, d_chunk_color_off, n_colors, vals, barrier, err,
+                                                     force_timeout)
+                : launch_persistent_impl<R, S, false>(st, A, P, C, d_chunk_color_off, n_colors, vals, barrier, err,
+                                                      force_timeout);
+}
 template lfx_status launch_assemble_persistent<double, double>(cudaStream_t, const AssembleArgs &, const PhysParams &,
                                                                const ChunkArgs &, const int32_t *, int, double *,
-                                                               unsigned *, int *, bool);
+                                                               unsigned *, int *, bool, bool);
 template lfx_status launch_assemble_persistent<dd, float>(cudaStream_t, const AssembleArgs &, const PhysParams &,
                                                           const ChunkArgs &, const int32_t *, int, float *, unsigned *,
-                                                          int *, bool);
+                                                          int *, bool, bool);
 
 int64_t assemble_chunk_wave() {
   int dev = 0, v = 0, sms = 152, per_sm = LFX_ASM_DD_MIN_CTAS;
@@ -1464,8 +1526,8 @@ int64_t assemble_chunk_wave() {
       cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) {
     sms = v;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, assemble_chunk_kernel<dd, float>, kCta,
-                                                      sizeof(ChunkShared<dd>)) == cudaSuccess && b > 0)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, assemble_chunk_kernel<dd, float, false>, kCta,
+                                                      sizeof(ChunkShared<dd, false>)) == cudaSuccess && b > 0)
       per_sm = b;
   }
   (void)cudaGetLastError();

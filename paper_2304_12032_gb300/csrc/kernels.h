@@ -99,19 +99,19 @@ lfx_status launch_backflow(cudaStream_t st, int64_t n_edges, const int32_t *ij, 
 template <class R, class S>
 lfx_status launch_assemble(cudaStream_t st, const AssembleArgs &A, const PhysParams &P,
                            const int32_t *color_off, int n_colors, S *vals, bool newton = false);
-// the semi-implicit system by chunks in ONE cooperative launch over every chunk colour, the colours
-// separated by bounded grid-wide waits; *err (device) is set to 1 if a wait gave up.  d_chunk_color_off:
-// device copy of the colour offsets; barrier: a device counter (zeroed here).
-// force_timeout (tests): the first wait's target is one more than the grid, its poll limit 4096, so
-// that it runs out and every CTA returns with *err set.
+// the semi-implicit system (newton: the Newton system at the iterate) by chunks in ONE cooperative
+// launch over every chunk colour, the colours separated by bounded grid-wide waits; *err (device)
+// is set to 1 if a wait gave up.  d_chunk_color_off: device copy of the colour offsets; barrier: a
+// device counter (zeroed here).  force_timeout (tests): the first wait's target is one more than
+// the grid, its poll limit 4096, so that it runs out and every CTA returns with *err set.
 template <class R, class S>
 lfx_status launch_assemble_persistent(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
                                       const int32_t *d_chunk_color_off, int n_colors, S *vals, unsigned *barrier,
-                                      int *err, bool force_timeout = false);
-// the semi-implicit system by chunks (one launch per chunk colour)
+                                      int *err, bool force_timeout = false, bool newton = false);
+// the semi-implicit system (newton: the Newton system) by chunks, one launch per chunk colour
 template <class R, class S>
 lfx_status launch_assemble_chunks(cudaStream_t st, const AssembleArgs &A, const PhysParams &P, const ChunkArgs &C,
-                                  const int32_t *chunk_color_off, int n_colors, S *vals);
+                                  const int32_t *chunk_color_off, int n_colors, S *vals, bool newton = false);
 lfx_status launch_dirichlet_values(cudaStream_t st, int64_t nd, int H, const int32_t *bc_of,
                                    const double *S, const DirCoef &C, const double *N, int nb, D4 *g);
 lfx_status launch_neumann(cudaStream_t st, int64_t n, const int32_t *node, const int32_t *bc_of,

@@ -6,7 +6,9 @@ term of Section 2.3, linearised by Newton's method, Section 2.4).
   tau_C(u*) and r_M(u, p) at U itself), within 1e-6 of each scalar row's largest entry (the
   differences' own error is about 1e-9 relative); the right-hand side J U - R(U) likewise, scaled
   by the row's largest entry times max |U|.  FP64 and double-float assembly, with and without a
-  resistive surface, VMS-LES and SUPG-PSPG.
+  resistive surface, VMS-LES and SUPG-PSPG; in each launch shape (element colours, chunk colours,
+  one persistent launch: the chunked kernels sum each row's Newton share over its blocks in a
+  final pass per chunk).
 * A whole implicit step through lfx_step matches the oracle's implicit_step (Newton with a direct
   solve from the semi-implicit solution) within 1e-6 relative L2, in FP64 and mixed precision; the
   Newton history reaches the tolerance in a few iterations with a first contraction below 1e-2."""
@@ -34,9 +36,10 @@ JAC = {
 }
 
 
+@pytest.mark.parametrize("shape", ["colors", "chunks", "persistent"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("which", list(JAC))
-def test_newton_jacobian_matches_finite_differences_of_the_oracle(which, precision):
+def test_newton_jacobian_matches_finite_differences_of_the_oracle(which, precision, shape):
     import oracle as O
 
     case = JAC[which]()
@@ -45,7 +48,7 @@ def test_newton_jacobian_matches_finite_differences_of_the_oracle(which, precisi
     U = np.concatenate([case.u_hist[0], case.p_hist[0][:, None]], axis=1) + 0.5 * rng.standard_normal((V, 4))
     prob = C.oracle_problem(case)
     J, F = O.implicit_system(case.mesh, prob, list(case.u_hist), case.t0 + case.dt, U.ravel())
-    opts = {} if precision == "fp64" else dict(precision="mixed")
+    opts = dict(assembly=shape) if precision == "fp64" else dict(precision="mixed", assembly=shape)
     mesh, _, st = C.gpu_state(case, **opts)
     blocks, rhs = st.debug_assemble_newton(U)
     rp, ci = mesh.pattern()
