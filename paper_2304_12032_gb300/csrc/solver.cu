@@ -755,7 +755,6 @@ __global__ void __launch_bounds__(kFTileThreads) f_step_staged_kernel(
   if (threadIdx.x == 0 && t < n_tiles) issue(t, 0);
   for (; t < n_tiles; t += gridDim.x, ++j) {
     const int b = j & 1;
-    if (threadIdx.x == 0 && t + (int)gridDim.x < n_tiles) issue(t + gridDim.x, b ^ 1);
     // the row's own data first: its latency overlaps the wait for the staged records
     const int32_t r0 = tile_row[t], r1 = tile_row[t + 1];
     const int32_t row = r0 + (int32_t)(threadIdx.x / kRowGroup);
@@ -780,6 +779,8 @@ __global__ void __launch_bounds__(kFTileThreads) f_step_staged_kernel(
       ok = false;
       break;
     }
+    // past this barrier every thread is done with the previous tile: its buffer takes the next one
+    if (threadIdx.x == 0 && t + (int)gridDim.x < n_tiles) issue(t + gridDim.x, b ^ 1);
     // record kk of the tile sits at rec + kFRec (kk - kt) (8-byte aligned)
     const unsigned char *rec = stage0 + (size_t)b * kFStageBytes + ((kFRec * kt) & 15);
     float acc[3] = {0.0f, 0.0f, 0.0f};
@@ -838,14 +839,12 @@ __global__ void __launch_bounds__(kFTileThreads) f_step_staged_kernel(
       st4(d_new, row, dn);
       st4(x, row, xx);
     }
-    __syncthreads();   // buffer b is refilled at the start of the next iteration
   }
   if (!ok && threadIdx.x == 0) {
     atomicExch(err, 1);
-    // copies still in flight into this CTA's buffers: tile t's, and the next tile's if issued
+    // the copy still in flight into this CTA's buffers: tile t's (the next one is issued only
+    // after the wait for tile t)
     mbar_wait_bounded(&bar[j & 1], (uint32_t)(j >> 1) & 1u, kFWaitPolls);
-    if (t + (int)gridDim.x < n_tiles)
-      mbar_wait_bounded(&bar[(j + 1) & 1], (uint32_t)((j + 1) >> 1) & 1u, kFWaitPolls);
   }
 }
 
