@@ -103,12 +103,16 @@ def make_case(n_tets, seed=2):
     return m, time.time() - t0
 
 
+ASSEMBLY = {}   # options.assembly when --assembly names a shape
+
+
 def gpu_problem(L, m, precision, **more):
     Q = U_PEAK * math.pi * R_CM ** 2 / 2.0
     bcs = [L.BC(tag=0, kind="noslip"),
            L.BC(tag=1, kind="dirichlet", profile="parabolic", time="ramp", p=(0.0, Q, 0.0, RAMP), radius=R_CM),
            L.BC(tag=2, kind="neumann", time="constant", p=(0.0,))]
     extra = dict(smoother_bf16=1) if precision == "mixed" else {}
+    extra.update(ASSEMBLY)
     extra.update(more)
     opts = L.default_options(precision=precision, gmres_rtol=1e-8, **extra)
     mesh = L.Mesh.from_synthetic(m)
@@ -741,6 +745,7 @@ def stenosis_problem(L, m, precision):
            L.BC(tag=2, kind="neumann", time="constant", p=(0.0,))]
     riis = [L.RIIS(1.0e4, 0.05, (0.0, 0.0, 5.0), (0.0, 0.0, 1.0), 0.5)]
     extra = dict(smoother_bf16=1) if precision == "mixed" else {}
+    extra.update(ASSEMBLY)
     opts = L.default_options(precision=precision, gmres_rtol=1e-8, **extra)
     mesh = L.Mesh.from_synthetic(m)
     return mesh, L.Problem(mesh, RHO, MU, 5e-4, 2, bcs, riis, opts)
@@ -873,6 +878,8 @@ def main():
     ap.add_argument("--tets", type=int, default=1_000_000)
     ap.add_argument("--cpu-sample-tets", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--assembly", default="auto", choices=["auto", "colors", "chunks", "persistent"],
+                    help="assembly launch shape (auto: the library's autotuner picks)")
     ap.add_argument("--implicit-steps", type=int, default=3,
                     help="fully implicit (Newton) steps timed after the semi-implicit ones (0: none)")
     ap.add_argument("--mode", default="step", choices=["step", "stenosis", "beltrami", "serving", "batched"])
@@ -889,6 +896,8 @@ def main():
     ap.add_argument("--serve-budget-frac", type=float, default=0.5)
     ap.add_argument("--serve-precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
+    if args.assembly != "auto":
+        ASSEMBLY["assembly"] = args.assembly
     if args.mode == "serving":
         run_serving(args)
     elif args.mode == "beltrami" and args.impl != "reference":
