@@ -334,6 +334,7 @@ def run_gpu(args):
     prim_prec = "mixed" if "mixed" in results else args.precision
     info = prim["mesh"].info()
     st = prim["st"]
+    amg = st.amg_levels()
     # ---- end to end through the public API, every step: the history in from page-locked host
     # buffers, the step, the solution out into the level-0 slot of the same buffers (DMA both
     # ways); the host then shifts its history levels, as a caller advancing the simulation does.
@@ -362,6 +363,7 @@ def run_gpu(args):
                    "n_colors": info["n_colors"], "precision": prim_prec, "bdf_order": 2, "dt": dt_w,
                    "gmres_rtol": 1e-8, "krylov_iterations_mean": statistics.mean(its),
                    "outer_iterations_mean": statistics.mean(s["outer_iterations"] for s in stats),
+                   "schur_amg_levels": {"rows": [r for r, _ in amg], "nnz": [z for _, z in amg]},
                    "l2": "inputs larger than L2 (FP64 matrix %.0f MB > 129 MB)" % (nnzb * 16 * 8 / 1e6),
                    "mesh_gen_s": round(tgen, 1), "start": f"from rest, {args.warmup} FP64 warm-up steps"},
         "elements_per_s_assembly": round(T / (asm_ms * 1e-3), 1),
