@@ -1437,14 +1437,14 @@ lfx_status launch_chunks_impl(cudaStream_t st, const AssembleArgs &A, const Phys
                               const int32_t *chunk_color_off, int n_colors, S *vals) {
   const PhysR<R> Q = phys_r<R>(P);
   const size_t smem = sizeof(ChunkShared<R, IMPL>);
-  static bool attr_set = false;
-  if (!attr_set) {
-    LFX_CUDA_TRY(cudaFuncSetAttribute(assemble_chunk_kernel<R, S, IMPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    attr_set = true;
-  }
   int dev = 0, nsm = 152, per_sm = 1;
   LFX_CUDA_TRY(cudaGetDevice(&dev));
+  static int attr_dev = -1;   // the attribute is per device: set again after a device switch
+  if (attr_dev != dev) {
+    LFX_CUDA_TRY(cudaFuncSetAttribute(assemble_chunk_kernel<R, S, IMPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    attr_dev = dev;
+  }
   LFX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   LFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assemble_chunk_kernel<R, S, IMPL>, kCta, smem));
   const int64_t resident = (int64_t)nsm * std::max(per_sm, 1);
@@ -1476,14 +1476,14 @@ lfx_status launch_persistent_impl(cudaStream_t st, const AssembleArgs &A, const 
                                   bool force_timeout) {
   const PhysR<R> Q = phys_r<R>(P);
   const size_t smem = sizeof(ChunkShared<R, IMPL>);
-  static bool attr_set = false;
-  if (!attr_set) {
-    LFX_CUDA_TRY(cudaFuncSetAttribute(assemble_chunks_persistent_kernel<R, S, IMPL>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-  }
   int dev = 0, nsm = 152, per_sm = 0, coop = 0;
   LFX_CUDA_TRY(cudaGetDevice(&dev));
+  static int attr_dev = -1;   // the attribute is per device: set again after a device switch
+  if (attr_dev != dev) {
+    LFX_CUDA_TRY(cudaFuncSetAttribute(assemble_chunks_persistent_kernel<R, S, IMPL>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_dev = dev;
+  }
   LFX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   LFX_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   LFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, assemble_chunks_persistent_kernel<R, S, IMPL>,

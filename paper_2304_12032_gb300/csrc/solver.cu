@@ -2470,16 +2470,19 @@ lfx_status ASimple<S, T>::launch_staged(cudaStream_t st, const View &A, bool fir
                                         const T *b0, const KState *ks) {
   if constexpr (std::is_same<View, SplitView<__nv_bfloat16>>::value && std::is_same<T, float>::value) {
     // one resident wave of persistent CTAs (the occupancy the kernel's shared memory allows)
-    static int grid[2] = {0, 0};
+    // (the attribute and the occupancy are per device: looked up again after a device switch)
+    static int grid[2] = {0, 0}, grid_dev[2] = {-1, -1};
     const int f = first ? 1 : 0;
-    if (grid[f] == 0) {
+    int dev = 0;
+    LFX_CUDA_TRY(cudaGetDevice(&dev));
+    if (grid_dev[f] != dev) {
       auto kern = first ? f_step_staged_kernel<true> : f_step_staged_kernel<false>;
       LFX_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFStagedSmem));
-      int dev = 0, sms = 0, per = 0;
-      LFX_CUDA_TRY(cudaGetDevice(&dev));
+      int sms = 0, per = 0;
       LFX_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       LFX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kFTileThreads, kFStagedSmem));
       grid[f] = std::max(1, sms * std::max(per, 1));
+      grid_dev[f] = dev;
     }
     const int g = std::min(grid[f], n_ftile);
     const SmoothCoef *cf = coef.as<SmoothCoef>();
