@@ -37,8 +37,11 @@ ASM_FP64_FLOPS_PER_ELEMENT = 2948
 # DRAM bytes per block of the FP32 Krylov SpMV (ncu read + write, 2,089,595-block launch)
 SPMV32_DRAM_BYTES_PER_BLOCK = 71.6
 # DRAM bytes per block of one staged BF16 F pass of the preconditioner (ncu read + write of one
-# launch on the 817,970-tet cylinder, scaled to other sizes by the block count); None until taken
-FPASS_BF16_DRAM_BYTES_PER_BLOCK = None
+# launch on the 817,970-tet cylinder, scaled to other sizes by the block count)
+FPASS_BF16_DRAM_BYTES_PER_BLOCK = 29.8
+# DRAM bytes per element of one whole persistent double-float assembly (ncu read + write of one
+# launch on the 817,970-tet cylinder, scaled by the element count)
+ASM_DD_PERSISTENT_DRAM_BYTES_PER_ELEMENT = 1782
 
 
 def _peaks():
@@ -189,7 +192,8 @@ def kernel_rooflines(stats, T, V, nnzb, prec, bf16=True):
            "bound": "alu", "achieved": round(asm_flops / (asm_ms * 1e-3) / 1e12, 4),
            "peak": pipe, "unit": "TFLOP/s (FP64-class flops of the method)",
            "frac": round(asm_flops / (asm_ms * 1e-3) / 1e12 / pipe, 4),
-           "traffic": None,
+           "traffic": int(ASM_DD_PERSISTENT_DRAM_BYTES_PER_ELEMENT * T)
+                      if dd and stats[0].get("assembly_mode", 0) == 3 else None,
            "peak_source": "measured FP32 FMA probe x 2 flops (the pipe double-float runs on)" if dd else
                           "measured FP64 FMA probe x 2 flops",
            "flops_per_element": ASM_FP64_FLOPS_PER_ELEMENT,
