@@ -945,7 +945,8 @@ __device__ void geom_load_range(const AssembleArgs &A, int64_t T, int64_t e0, in
 // The chunks c0 + blockIdx.x, c0 + blockIdx.x + gridDim.x, ... (< c1).  Each chunk's slot codes,
 // run tables and pass offsets are staged in shared memory at its start with loads that do not
 // wait on one another (its geometry loads among them), and the next chunk's offsets are loaded
-// while this one is processed, so that no phase waits on a chain of dependent global loads.
+// while this one is processed, so that no phase waits on a chain of dependent global loads; its
+// node fields and geometry are prefetched into L2 during this chunk's first pass.
 template <class R, class S, bool IMPL>
 __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q,
                                             const ChunkArgs &C, int64_t c0, int64_t c1, S *vals,
@@ -973,6 +974,10 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
       np0 = C.pass_off[chn];
       np1 = C.pass_off[chn + 1];
     }
+    // the next chunk's nodes, for the L2 prefetch of its node data during this chunk's passes
+    int4 ncn = make_int4(0, 0, 0, 0);
+    const bool nlive = chn < c1 && t < kElems && ne0 + t < ne1;
+    if (nlive) ncn = A.conn[ne0 + t];
     const int npass = p1 - p0, nrun = re - rb;
     for (int i = t; i < npass * kCta; i += kCta) cs.code[i] = C.code[(int64_t)p0 * kCta + i];
     for (int i = t; i < nrun; i += kCta) {
@@ -1032,6 +1037,34 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
         if (a == b) {
 #pragma unroll
           for (int i = 0; i < 4; ++i) cs.rst[t][i] = rhs_value<R>(P, sh, l2, a, i);
+        }
+      }
+      if (pi == 0) {
+        // the next chunk's node fields and geometry into L2 while this chunk computes
+        if (nlive) {
+          const int nn[4] = {ncn.x, ncn.y, ncn.z, ncn.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            if (std::is_same<R, dd>::value) {
+              prefetch_l2(A.xext_hi + nn[a]);
+              prefetch_l2(A.xext_lo + nn[a]);
+              prefetch_l2(A.ubdf_hi + nn[a]);
+              prefetch_l2(A.ubdf_lo + nn[a]);
+            } else {
+              prefetch_l2(A.xext + nn[a]);
+              prefetch_l2(A.ubdf + nn[a]);
+            }
+          }
+        }
+        if (chn < c1 && has_geo<R>(A) && t < 2 * kGeoValues) {
+          const int k = t >> 1;
+          const int64_t at = (int64_t)k * A.n_elems + ne0 + ((t & 1) ? ne1 - ne0 - 1 : 0);
+          if (std::is_same<R, dd>::value) {
+            prefetch_l2(A.geo_hi + at);
+            prefetch_l2(A.geo_lo + at);
+          } else {
+            prefetch_l2(A.geo64 + at);
+          }
         }
       }
       __syncthreads();
