@@ -946,7 +946,8 @@ __device__ void geom_load_range(const AssembleArgs &A, int64_t T, int64_t e0, in
 // run tables and pass offsets are staged in shared memory at its start with loads that do not
 // wait on one another (its geometry loads among them), and the next chunk's offsets are loaded
 // while this one is processed, so that no phase waits on a chain of dependent global loads; its
-// node fields and geometry are prefetched into L2 during this chunk's first pass.
+// node fields and geometry are prefetched into L2 during this chunk's first pass, its tables
+// during the second.
 template <class R, class S, bool IMPL>
 __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysParams &P, const PhysR<R> &Q,
                                             const ChunkArgs &C, int64_t c0, int64_t c1, S *vals,
@@ -1065,6 +1066,23 @@ __device__ __forceinline__ void chunk_range(const AssembleArgs &A, const PhysPar
           } else {
             prefetch_l2(A.geo64 + at);
           }
+        }
+      }
+      if (pi == 1 && chn < c1) {
+        // the next chunk's slot codes and run tables into L2 (128-byte lines, one per thread)
+        const char *base[4] = {reinterpret_cast<const char *>(C.code + (int64_t)np0 * kCta),
+                               reinterpret_cast<const char *>(C.meta + nrb), reinterpret_cast<const char *>(C.block + nrb),
+                               reinterpret_cast<const char *>(C.node + nrb)};
+        const int64_t bytes[4] = {(int64_t)(np1 - np0) * kCta * 2, (int64_t)(nre - nrb) * 2, (int64_t)(nre - nrb) * 4,
+                                  (int64_t)(nre - nrb) * 4};
+        int idx = t;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t first = reinterpret_cast<uintptr_t>(base[q]) >> 7;
+          const int64_t last = bytes[q] > 0 ? (reinterpret_cast<uintptr_t>(base[q]) + bytes[q] - 1) >> 7 : first - 1;
+          const int nl = (int)(last - first + 1);
+          if (idx >= 0 && idx < nl) prefetch_l2(reinterpret_cast<const void *>((first + idx) << 7));
+          idx -= nl;
         }
       }
       __syncthreads();
