@@ -41,7 +41,7 @@ SPMV32_DRAM_BYTES_PER_BLOCK = 71.6
 FPASS_BF16_DRAM_BYTES_PER_BLOCK = 29.8
 # DRAM bytes per element of one whole persistent double-float assembly (ncu read + write of one
 # launch on the 817,970-tet cylinder, scaled by the element count)
-ASM_DD_PERSISTENT_DRAM_BYTES_PER_ELEMENT = 1782
+ASM_DD_PERSISTENT_DRAM_BYTES_PER_ELEMENT = 1793
 
 
 def _peaks():
