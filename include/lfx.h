@@ -247,7 +247,8 @@ typedef struct lfx_options {
    * waits; LFX_ERR_TIMEOUT from lfx_step if a wait gives up), or LFX_ASM_AUTO (default): the first
    * assembly on the problem times each of the three on the device (two assemblies each) and the
    * problem keeps the fastest for all its states (lfx_problem_assembly_tuning reports it).  The
-   * Newton assemblies use the colour launches. */
+   * Newton system of the fully implicit formulation is timed and chosen apart from it, at its own
+   * first assembly, since its kernels fit the SMs differently. */
   int32_t assembly;
   double newton_rtol;           /* default 1e-10                                                 */
   /* velocity smoothing passes of the BF16 smoother (smoother_bf16 = 1): 1 (default) the staged
@@ -301,8 +302,9 @@ typedef struct lfx_step_stats {
   double t;                     /* time reached                                                */
   float ms_assembly, ms_solve, ms_total;   /* device time per phase (CUDA events)              */
   int32_t converged;
-  float ms_assembly_kernels;    /* the coloured assembly launches alone (CUDA events)          */
-  int32_t n_assembly_launches;  /* launches of the assembly kernel in this step (= colours)    */
+  float ms_assembly_kernels;    /* the assembly kernel's launches alone (CUDA events)          */
+  int32_t n_assembly_launches;  /* launches of the assembly kernel in this step: element colours,
+                                   chunk colours, or 1 for the persistent launch                */
   float ms_spmv;                /* device time of a sample of the Arnoldi block SpMV launches of
                                    the (inner) Krylov solve in this step: one in five, at most four
                                    (CUDA events)                                                 */
