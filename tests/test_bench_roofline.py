@@ -12,6 +12,9 @@ mixed-precision step and check:
 * the dominant kernel, which is the one with the most device time per step;
 * the ncu-derived `traffic`.  It is reported only for the launch shape and precision it was
   captured on: the persistent double-float assembly and the staged BF16 F pass.
+
+The clock record of the timed region (nvidia-smi samples) is checked as well: the median SM
+clock, the maximum clock and the throttle reasons seen.  Only this process's GPU counts.
 """
 import pytest
 
@@ -100,3 +103,36 @@ def test_fp64_step_rooflines(bench):
     # FP64 SpMV: 16 x 8 B values + a 4 B column per block, row pointers, x and y (32 B per node each)
     assert k["spmv"]["algorithmic_bytes_per_launch"] == NNZB * 132 + 4 * (V + 1) + 2 * 32 * V
     assert k["spmv"]["traffic"] is None
+
+
+class _FakeSmi:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_record_from_samples(bench, monkeypatch):
+    # nvidia-smi rows: index, clocks.sm, clocks.max.sm, power.draw, active reasons, hw_slowdown,
+    # hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+    monkeypatch.setenv("LOCAL_RANK", "0")
+    c = bench.Clocks()
+    c.proc = _FakeSmi()
+    c.samples = [
+        ["0", "2070", "2070", "900.1", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["0", "1980", "2070", "1390.0", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+        ["0", "2070", "2070", "950.0", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["1", "900", "2070", "300.0", "0x8", "Active", "Not Active", "Not Active", "Not Active"],  # other GPU
+    ]
+    rec = c.stop()
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0 and rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"]           # kept and noted; the other GPU's slowdown is not ours
+    c = bench.Clocks()
+    c.proc = _FakeSmi()
+    c.samples = [["0", "1500", "2070", "1200.0", "0x2", "Not Active", "Active", "Not Active", "Not Active"]]
+    assert c.stop()["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_clock_record_without_nvidia_smi(bench):
+    assert bench.Clocks().stop()["reasons"] == ["nvidia-smi unavailable"]
