@@ -79,7 +79,9 @@ typedef struct lfx_mesh_info {
   int32_t n_colors;            /* element colours                                            */
   int32_t n_flipped;           /* tetrahedra whose orientation was fixed                     */
   int32_t max_color_size, min_color_size;
-  int64_t n_bad_elements;      /* elements below the shape-quality threshold (FP64 geometry) */
+  int64_t n_bad_elements;      /* elements whose shape quality 6 sqrt2 |K| / e_rms^3 is below the
+                                  default bad_element_quality (0.1): their geometry is FP64 in
+                                  mixed assembly                                               */
   int32_t n_components;        /* connected components: independent meshes batched together  */
   int32_t pad;
 } lfx_mesh_info;

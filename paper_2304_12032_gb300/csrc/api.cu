@@ -283,6 +283,9 @@ lfx_status lfx_mesh_create(const double *nodes, int64_t n_nodes, const int32_t *
 
 void lfx_mesh_destroy(lfx_mesh *mesh) { delete mesh; }
 
+// default shape-quality threshold below which an element keeps FP64 geometry in mixed assembly
+constexpr double kDefaultBadElementQuality = 0.1;
+
 lfx_status lfx_mesh_get_info(const lfx_mesh *mesh, lfx_mesh_info *info) {
   if (!mesh || !info) {
     set_error("lfx_mesh_get_info: NULL argument");
@@ -303,7 +306,9 @@ lfx_status lfx_mesh_get_info(const lfx_mesh *mesh, lfx_mesh_info *info) {
   }
   info->max_color_size = mx;
   info->min_color_size = mn;
-  info->n_bad_elements = 0;
+  int64_t n_bad = 0;
+  for (const double q : m.quality) n_bad += q < kDefaultBadElementQuality ? 1 : 0;
+  info->n_bad_elements = n_bad;
   info->n_components = m.n_comp;
   return LFX_OK;
 }
@@ -432,7 +437,7 @@ void lfx_options_default(lfx_options *o) {
   o->outer_max_iters = 40;
   o->inner_rtol = 1e-4;
   o->inner_max_iters = 60;
-  o->bad_element_quality = 0.1;
+  o->bad_element_quality = kDefaultBadElementQuality;
   o->amg_refresh = 0;
   o->amg_coarse_size = 2000;
   o->amg_theta = 0.08;

@@ -97,6 +97,37 @@ def test_flipped_tets_are_counted(L):
     assert mesh.info()["n_flipped"] == len(t[::5])
 
 
+def _shape_quality(nodes, tets):
+    """6 sqrt2 |K| / e_rms^3: 1 for a regular tetrahedron, 0 for a flat one."""
+    x = nodes[tets]
+    det = np.einsum("ij,ij->i", np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]), x[:, 3] - x[:, 0])
+    e2 = sum(((x[:, a] - x[:, b]) ** 2).sum(1) for a in range(4) for b in range(a + 1, 4))
+    return np.abs(det) / 6.0 * 6.0 * np.sqrt(2.0) / np.sqrt(e2 / 6.0) ** 3
+
+
+def test_mesh_info_counts_components_and_badly_shaped_elements(L):
+    # three pieces: a Kuhn cube, a shifted copy of it, and a pair of tetrahedra sharing a face, one
+    # of them a sliver (quality about 0.05, below the default threshold 0.1)
+    c = cube_kuhn(2)
+    pair_nodes = np.array([[10.0, 0, 0], [11.0, 0, 0], [10.0, 1.0, 0], [10.3, 0.3, 0.5], [10.3, 0.3, -0.02]])
+    nodes = np.vstack([c.nodes, c.nodes + [3.0, 0, 0], pair_nodes])
+    V = c.n_nodes
+    pair = np.array([[0, 1, 2, 3], [0, 2, 1, 4]]) + 2 * V
+    tets = np.vstack([c.tets, c.tets + V, pair]).astype(np.int32)
+    bfaces = np.vstack([c.bfaces, c.bfaces + V]).astype(np.int32)
+    btags = np.concatenate([c.btags, c.btags]).astype(np.int32)
+    q = _shape_quality(nodes, tets)
+    assert q[-1] < 0.1 < q[:-1].min()
+    info = L.Mesh(nodes, tets, bfaces, btags).info()
+    assert info["n_components"] == 3
+    assert info["n_bad_elements"] == int((q < 0.1).sum()) == 1
+    assert info["n_tets"] == len(tets) and info["n_flipped"] == 0
+    # the synthetic cylinder has none below the threshold
+    m = cylinder(1.0, 4.0, n_tets=20000, seed=3)
+    assert L.Mesh(m.nodes, m.tets, m.bfaces, m.btags).info()["n_bad_elements"] == int(
+        (_shape_quality(m.nodes, m.tets) < 0.1).sum())
+
+
 def _adjacency(m):
     pairs = np.concatenate([np.stack([m.tets[:, a], m.tets[:, b]], 1) for a in range(4) for b in range(4)])
     key = np.unique(pairs[:, 0].astype(np.int64) * m.n_nodes + pairs[:, 1])
