@@ -529,17 +529,10 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
   *out = nullptr;
   std::unique_ptr<lfx_problem> pb(new (std::nothrow) lfx_problem);
   if (!pb) return LFX_ERR_OOM;
-  const Mesh &m = mesh->m;
-  if (!m.uploaded) {
-    // device copies are made on first use, so that mesh set-up itself needs no GPU
-    Mesh &mm = const_cast<lfx_mesh *>(mesh)->m;
-    LFX_TRY(upload_mesh(mm));
-    mm.uploaded = true;
-  }
-  pb->mesh = mesh;
   if (opt) pb->opt = *opt;
   else lfx_options_default(&pb->opt);
   lfx_options &o = pb->opt;
+  // the options, too, are checked before anything is allocated on the device
   if (o.stab < 0 || o.stab > 2 || o.diffusion < 0 || o.diffusion > 2 || o.gmres_restart < 1 ||
       o.gmres_restart > kMaxRestart || o.f_steps < 1 || o.f_steps > kMaxSmooth || o.s_steps < 1 ||
       o.s_steps > kMaxSmooth || o.precision < 0 || o.precision > 1 || o.n_power < 0 || o.f_smoother < 0 ||
@@ -567,6 +560,14 @@ lfx_status lfx_problem_create(const lfx_mesh *mesh, double rho, double mu, doubl
                   "stabilisation or resistance conditions (boundary condition %d)", b);
         return LFX_ERR_INVALID_ARG;
       }
+  const Mesh &m = mesh->m;
+  if (!m.uploaded) {
+    // device copies are made on first use, so that mesh set-up itself needs no GPU
+    Mesh &mm = const_cast<lfx_mesh *>(mesh)->m;
+    LFX_TRY(upload_mesh(mm));
+    mm.uploaded = true;
+  }
+  pb->mesh = mesh;
   // physics (Section 2.1.2, Eq. bdf)
   PhysParams &P = pb->P;
   P.rho = rho;

@@ -183,6 +183,32 @@ def test_outlet_condition_arguments_are_checked_before_allocation(L, bc):
     assert err.value.status == L.LFX_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("opt", [dict(staged_f=2), dict(assembly=7), dict(assembly=-1), dict(implicit=2),
+                                 dict(implicit=1, newton_max_iters=0), dict(implicit=1, newton_rtol=0.0),
+                                 dict(gmres_restart=0), dict(f_steps=0), dict(s_smoother=5), dict(precision=3),
+                                 dict(stab=3), dict(diffusion=-1)])
+def test_options_are_checked_before_allocation(L, opt):
+    """Options out of range are rejected as invalid arguments before any device memory is touched
+    (so on a host without a GPU as well)."""
+    m = cylinder(1.0, 2.0, n_tets=3000, seed=9)
+    mesh = L.Mesh.from_synthetic(m)
+    bcs = [L.BC(tag=0, kind="noslip"), L.BC(tag=1, kind="dirichlet"), L.BC(tag=2, kind="neumann")]
+    with pytest.raises(L.LfxError) as err:
+        L.Problem(mesh, 1.06, 0.035, 1e-3, 2, bcs, [], L.default_options(**opt))
+    assert err.value.status == L.LFX_ERR_INVALID_ARG
+
+
+def test_implicit_formulation_rejects_outlet_terms_before_allocation(L):
+    m = cylinder(1.0, 2.0, n_tets=3000, seed=9)
+    mesh = L.Mesh.from_synthetic(m)
+    for outlet in (L.BC(tag=2, kind="resistance", resistance=10.0), L.BC(tag=2, kind="neumann", beta=1.0)):
+        bcs = [L.BC(tag=0, kind="noslip"), L.BC(tag=1, kind="dirichlet"), outlet]
+        with pytest.raises(L.LfxError) as err:
+            L.Problem(mesh, 1.06, 0.035, 1e-3, 2, bcs, [], L.default_options(implicit=1))
+        assert err.value.status == L.LFX_ERR_INVALID_ARG
+        assert b"implicit" in L.library().lfx_last_error()
+
+
 @pytest.mark.parametrize("which", ["cylinder", "bifurcation"])
 def test_chunk_tables(L, which):
     """The chunked assembly's tables (host, no GPU): every element in exactly one chunk of at most 32;
