@@ -198,6 +198,26 @@ def test_options_are_checked_before_allocation(L, opt):
     assert err.value.status == L.LFX_ERR_INVALID_ARG
 
 
+def test_host_arguments_rejected_without_a_gpu(L):
+    """Arguments the host can reject by themselves: a server without a positive budget or with a
+    worker count outside 1..64, one allocator function without the other, queries on NULL handles
+    and unknown struct names."""
+    lib = L.library()
+    h = L._P()
+    for budget, workers in ((0, 4), (-1, 4), (1 << 30, 0), (1 << 30, 65)):
+        assert lib.lfx_server_create(budget, workers, ctypes.byref(h)) == L.LFX_ERR_INVALID_ARG
+    assert lib.lfx_server_create(1 << 30, 4, None) == L.LFX_ERR_INVALID_ARG
+    done = ctypes.c_int32()
+    assert lib.lfx_server_poll(None, 0, ctypes.byref(done), None, None) == L.LFX_ERR_INVALID_ARG
+    fa = L.ALLOC_FN(lambda n, ctx: None)
+    assert lib.lfx_set_allocator(fa, L.FREE_FN(), None) == L.LFX_ERR_INVALID_ARG
+    assert b"both" in lib.lfx_last_error()
+    assert lib.lfx_set_allocator(L.ALLOC_FN(), L.FREE_FN(), None) == L.LFX_OK      # back to cudaMalloc
+    info = L.lfx_mesh_info()
+    assert lib.lfx_mesh_get_info(None, ctypes.byref(info)) == L.LFX_ERR_INVALID_ARG
+    assert lib.lfx_sizeof(b"no_such_struct") == -1
+
+
 def test_implicit_formulation_rejects_outlet_terms_before_allocation(L):
     m = cylinder(1.0, 2.0, n_tets=3000, seed=9)
     mesh = L.Mesh.from_synthetic(m)
