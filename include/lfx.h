@@ -421,6 +421,25 @@ lfx_status lfx_debug_amg_level(lfx_state *state, int32_t level, int64_t sizes[4]
  * buffers in level-1 numbering.  Needs at least 3 levels. */
 lfx_status lfx_debug_amg_vcycle(lfx_state *state, const double *b1, double *x1);
 
+/* The same host set-up of the Schur AMG hierarchy, run on the host alone for a caller-held matrix
+ * (no state, no device work: tests of the host logic run without a GPU).  The matrix is the 4x4
+ * block-CSR system of a step in host memory: row_ptr [n_nodes+1], col_idx [nnz_blocks] (the node
+ * graph, which also drives the finest aggregation), diag_idx [n_nodes] (position of block (i,i)),
+ * blocks [nnz_blocks][4][4] FP64 row-major with unknowns (u_x, u_y, u_z, p) per node.  The set-up
+ * forms S = C - D diag(F)^-1 G explicitly, then aggregates, smooths the prolongators, forms the
+ * Galerkin coarse operators, their Gershgorin bounds and the dense inverse of the coarsest one,
+ * with opt's amg_coarse_size and amg_theta (NULL = defaults).  It runs whole at every call and
+ * reports level `level`: sizes = {levels, n_l, nnz(A_l), n_{l+1}, nnz(P_l)}, with n_{l+1} and nnz(P_l)
+ * 0 at the coarsest level.  Non-NULL arrays receive A_l (a_rp [n_l+1], a_ci, a_v; A_0 = S), P_l
+ * (p_rp [n_l+1], p_ci, p_v), *lam (the Gershgorin bound of lambda_max(D^-1 A_l), 0 at the coarsest
+ * level) and, at the coarsest level, coarse_inv [n_l][n_l] (A_l^-1, row-major).  Host buffers,
+ * CSR with int32 indices.  LFX_ERR_INVALID_ARG for NULL inputs, a pattern or diagonal index out of
+ * range, or a level beyond the last. */
+lfx_status lfx_debug_amg_host(int64_t n_nodes, const int32_t *row_ptr, const int32_t *col_idx,
+                              const int32_t *diag_idx, const double *blocks, const lfx_options *opt,
+                              int32_t level, int64_t sizes[5], int32_t *a_rp, int32_t *a_ci, double *a_v,
+                              int32_t *p_rp, int32_t *p_ci, double *p_v, double *lam, double *coarse_inv);
+
 /* ------------------------------------------------------------------------------------------
  * Allocation-free preconditioner application (the paper has no counterpart: this is a service
  * for callers that cannot allocate device memory where they need the preconditioner, e.g. a

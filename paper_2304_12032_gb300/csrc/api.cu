@@ -2144,6 +2144,72 @@ lfx_status lfx_debug_amg_level(lfx_state *s, int32_t level, int64_t sizes[4], in
   return LFX_OK;
 }
 
+lfx_status lfx_debug_amg_host(int64_t n, const int32_t *row_ptr, const int32_t *col_idx, const int32_t *diag_idx,
+                              const double *blocks, const lfx_options *opt, int32_t level, int64_t sizes[5],
+                              int32_t *a_rp, int32_t *a_ci, double *a_v, int32_t *p_rp, int32_t *p_ci, double *p_v,
+                              double *lam, double *coarse_inv) {
+  clear_error();
+  if (n < 1 || n >= INT32_MAX || !row_ptr || !col_idx || !diag_idx || !blocks || !sizes || level < 0 ||
+      row_ptr[0] != 0) {
+    set_error("lfx_debug_amg_host: invalid argument");
+    return LFX_ERR_INVALID_ARG;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) {
+      set_error("lfx_debug_amg_host: row_ptr decreases at row %lld", (long long)i);
+      return LFX_ERR_INVALID_ARG;
+    }
+  const int64_t nnz = row_ptr[n];
+  for (int64_t k = 0; k < nnz; ++k)
+    if (col_idx[k] < 0 || col_idx[k] >= n) {
+      set_error("lfx_debug_amg_host: column index out of range at %lld", (long long)k);
+      return LFX_ERR_INVALID_ARG;
+    }
+  for (int64_t i = 0; i < n; ++i)
+    if (diag_idx[i] < row_ptr[i] || diag_idx[i] >= row_ptr[i + 1] || col_idx[diag_idx[i]] != i) {
+      set_error("lfx_debug_amg_host: diag_idx[%lld] is not the position of block (i, i)", (long long)i);
+      return LFX_ERR_INVALID_ARG;
+    }
+  lfx_options o;
+  if (opt) o = *opt;
+  else lfx_options_default(&o);
+  if (o.amg_coarse_size < 1 || !(o.amg_theta >= 0.0)) {
+    set_error("lfx_debug_amg_host: amg_coarse_size >= 1 and amg_theta >= 0 needed");
+    return LFX_ERR_INVALID_ARG;
+  }
+  const std::vector<int32_t> rp(row_ptr, row_ptr + n + 1), ci(col_idx, col_idx + nnz), dg(diag_idx, diag_idx + n);
+  CsrHost S0 = schur_explicit(n, rp, ci, dg, blocks);
+  AmgParams prm;
+  prm.coarse_size = o.amg_coarse_size;
+  prm.theta = o.amg_theta;
+  AmgHost H;
+  LFX_TRY(amg_setup_host(std::move(S0), rp, ci, prm, H));
+  const int levels = (int)H.A.size();
+  if (level >= levels) {
+    set_error("lfx_debug_amg_host: level %d beyond the last of %d", level, levels);
+    return LFX_ERR_INVALID_ARG;
+  }
+  const CsrHost &A = H.A[level];
+  const bool has_p = level + 1 < levels;
+  sizes[0] = levels;
+  sizes[1] = A.n;
+  sizes[2] = (int64_t)A.v.size();
+  sizes[3] = has_p ? H.P[level].m : 0;
+  sizes[4] = has_p ? (int64_t)H.P[level].v.size() : 0;
+  if (a_rp) std::copy(A.rp.begin(), A.rp.end(), a_rp);
+  if (a_ci) std::copy(A.ci.begin(), A.ci.end(), a_ci);
+  if (a_v) std::copy(A.v.begin(), A.v.end(), a_v);
+  if (has_p) {
+    const CsrHost &P = H.P[level];
+    if (p_rp) std::copy(P.rp.begin(), P.rp.end(), p_rp);
+    if (p_ci) std::copy(P.ci.begin(), P.ci.end(), p_ci);
+    if (p_v) std::copy(P.v.begin(), P.v.end(), p_v);
+  }
+  if (lam) *lam = has_p ? H.lam[level] : 0.0;
+  if (!has_p && coarse_inv) std::copy(H.coarse_inv.begin(), H.coarse_inv.end(), coarse_inv);
+  return LFX_OK;
+}
+
 lfx_status lfx_debug_amg_vcycle(lfx_state *s, const double *b1, double *x1) {
   clear_error();
   if (!s || !b1 || !x1 || s->mixed() || !s->pc64.amg_ready || s->pc64.amg.size() < 3) {

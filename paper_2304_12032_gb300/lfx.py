@@ -149,6 +149,8 @@ _SIGS = {
     "lfx_state_device_bytes": ([_P, _LP], ctypes.c_int32),
     "lfx_debug_amg_level": ([_P, ctypes.c_int32, _LP, _IP, _IP, _DP, _IP, _IP, _DP, _DP], ctypes.c_int32),
     "lfx_debug_amg_vcycle": ([_P, _DP, _DP], ctypes.c_int32),
+    "lfx_debug_amg_host": ([ctypes.c_int64, _IP, _IP, _IP, _DP, ctypes.POINTER(lfx_options), ctypes.c_int32, _LP,
+                            _IP, _IP, _DP, _IP, _IP, _DP, _DP, _DP], ctypes.c_int32),
     "lfx_state_amg_levels": ([_P, _IP, _LP, _LP, ctypes.c_int32], ctypes.c_int32),
 }
 
@@ -360,6 +362,41 @@ class Mesh:
         if getattr(self, "h", None) and _lib is not None:
             _lib.lfx_mesh_destroy(self.h)
             self.h = None
+
+
+def debug_amg_host(row_ptr, col_idx, diag_idx, blocks, options: Optional[lfx_options] = None):
+    """The Schur AMG set-up on the host alone (lfx_debug_amg_host) for a 4x4 block-CSR system held in
+    host memory: a list of levels, each a dict with n, A (scipy CSR; A_0 = S = C - D diag(F)^-1 G),
+    P (scipy CSR n_l x n_{l+1}; None at the coarsest level), lam (Gershgorin bound of
+    lambda_max(D^-1 A_l)) and, at the coarsest level, coarse_inv (its dense inverse)."""
+    import scipy.sparse as sp
+
+    lib = library()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    dg = np.ascontiguousarray(diag_idx, dtype=np.int32)
+    bl = np.ascontiguousarray(blocks, dtype=np.float64).reshape(-1, 16)
+    n = int(rp.size - 1)
+    opt = ctypes.byref(options) if options is not None else None
+    levels, out = 1, []
+    while len(out) < levels:
+        level = len(out)
+        sz = np.zeros(5, dtype=np.int64)
+        lam = ctypes.c_double()
+        _check(lib.lfx_debug_amg_host(n, _i(rp), _i(ci), _i(dg), _d(bl), opt, level, sz.ctypes.data_as(_LP), None,
+                                      None, None, None, None, None, ctypes.byref(lam), None))
+        levels, nl, nnz_a, nn, nnz_p = (int(v) for v in sz)
+        last = level == levels - 1
+        arp, aci, av = np.zeros(nl + 1, np.int32), np.zeros(max(nnz_a, 1), np.int32), np.zeros(max(nnz_a, 1))
+        prp, pci, pv = np.zeros(nl + 1, np.int32), np.zeros(max(nnz_p, 1), np.int32), np.zeros(max(nnz_p, 1))
+        inv = np.zeros((nl, nl)) if last else None
+        _check(lib.lfx_debug_amg_host(n, _i(rp), _i(ci), _i(dg), _d(bl), opt, level, sz.ctypes.data_as(_LP),
+                                      _i(arp), _i(aci), _d(av), _i(prp), _i(pci), _d(pv), ctypes.byref(lam),
+                                      _d(inv) if last else None))
+        A = sp.csr_matrix((av[:nnz_a], aci[:nnz_a], arp), shape=(nl, nl))
+        P = None if last else sp.csr_matrix((pv[:nnz_p], pci[:nnz_p], prp), shape=(nl, nn))
+        out.append({"n": nl, "A": A, "P": P, "lam": lam.value, "coarse_inv": inv})
+    return out
 
 
 class Problem:
