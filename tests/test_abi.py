@@ -200,8 +200,9 @@ def test_options_are_checked_before_allocation(L, opt):
 
 def test_host_arguments_rejected_without_a_gpu(L):
     """Arguments the host can reject by themselves: a server without a positive budget or with a
-    worker count outside 1..64, one allocator function without the other, queries on NULL handles
-    and unknown struct names."""
+    worker count outside 1..64, one allocator function without the other, queries on NULL handles,
+    unknown struct names, more than eight resistive surfaces, and the allocation-free
+    preconditioner's size and smoother limits."""
     lib = L.library()
     h = L._P()
     for budget, workers in ((0, 4), (-1, 4), (1 << 30, 0), (1 << 30, 65)):
@@ -216,6 +217,27 @@ def test_host_arguments_rejected_without_a_gpu(L):
     info = L.lfx_mesh_info()
     assert lib.lfx_mesh_get_info(None, ctypes.byref(info)) == L.LFX_ERR_INVALID_ARG
     assert lib.lfx_sizeof(b"no_such_struct") == -1
+    m = cylinder(1.0, 2.0, n_tets=3000, seed=9)
+    mesh = L.Mesh.from_synthetic(m)
+    disks = [L.RIIS(center=(0.0, 0.0, 1.0), normal=(0.0, 0.0, 1.0), radius=0.5, resistance=1e3, eps=0.05)] * 9
+    with pytest.raises(L.LfxError) as err:
+        L.Problem(mesh, 1.06, 0.035, 1e-3, 2, [L.BC(tag=0, kind="noslip")], disks)
+    assert err.value.status == L.LFX_ERR_INVALID_ARG
+    # the allocation-free preconditioner: at most 65,536 block rows, Jacobi or Chebyshev smoothers only
+    # (the arguments are checked before any pointer is used, so host stand-ins serve here)
+    dummy = np.zeros(8)
+    ptr = dummy.ctypes.data
+
+    def noalloc(n, opt=None):
+        return lib.lfx_asimple_apply_noalloc(n, ptr, ptr, ptr, ptr, ptr, ptr, ptr,
+                                             ctypes.byref(opt) if opt is not None else None, None)
+
+    assert noalloc(0) == L.LFX_ERR_INVALID_ARG
+    assert noalloc(65537) == L.LFX_ERR_INVALID_ARG
+    assert b"65536" in lib.lfx_last_error()
+    assert noalloc(100, L.default_options(s_smoother="amg")) == L.LFX_ERR_INVALID_ARG
+    assert noalloc(100, L.default_options(s_smoother="chebyshev", f_steps=0)) == L.LFX_ERR_INVALID_ARG
+    assert lib.lfx_asimple_apply_noalloc(100, None, ptr, ptr, ptr, ptr, ptr, ptr, None, None) == L.LFX_ERR_INVALID_ARG
 
 
 def test_implicit_formulation_rejects_outlet_terms_before_allocation(L):
