@@ -1,0 +1,84 @@
+"""The seeded synthetic inputs that stand in for the paper's meshes: the recipes hold what the
+design notes state (host only, no GPU).
+
+* Seeded: the same seed gives the same mesh bit for bit; another seed gives another mesh.
+* Shuffled: node order carries no spatial order.  The library's space-filling-curve renumbering
+  is exercised, not bypassed.
+* Valid: every tetrahedron is positively oriented; the tagged faces are exactly the boundary faces.
+* Tagged as in Test II: the wall is tag 0, the inlet (z = 0) tag 1, the outlet (z = L) tag 2.  The
+  wall nodes lie on the cylinder, or on the stenosed radius r_s(z) = R (1 - s (1 + cos(pi
+  (z - z_c) / h))) within |z - z_c| <= h.
+* Shaped like Table tab:mesh of the paper (Section 4): 5.4-6.3 tetrahedra per vertex at 100k
+  tets and an edge ratio below 17.  The count is within 5 % of the requested one.
+* Batched unions keep every member's nodes, and offset member i's tags by 10 i.
+"""
+import numpy as np
+import pytest
+
+import synthetic as S
+from synthetic.meshes import _signed_volumes, boundary_faces
+
+
+def _same(a, b):
+    return all(np.array_equal(getattr(a, k), getattr(b, k)) for k in ("nodes", "tets", "bfaces", "btags"))
+
+
+def _face_keys(f):
+    return set(map(tuple, np.sort(f, axis=1)))
+
+
+def test_seeded_and_shuffled():
+    a = S.cylinder(1.0, 10.0, n_tets=20000, seed=2)
+    assert _same(a, S.cylinder(1.0, 10.0, n_tets=20000, seed=2))
+    assert not _same(a, S.cylinder(1.0, 10.0, n_tets=20000, seed=5))
+    assert abs(np.corrcoef(np.arange(a.n_nodes), a.nodes[:, 2])[0, 1]) < 0.1
+
+
+@pytest.mark.parametrize("make", [lambda: S.cylinder(1.0, 10.0, n_tets=20000, seed=2),
+                                  lambda: S.stenosis(1.0, 10.0, n_tets=20000, seed=3),
+                                  lambda: S.bifurcation(n_tets=20000, seed=1001)])
+def test_valid_oriented_and_tagged(make):
+    m = make()
+    assert np.all(_signed_volumes(m.nodes, m.tets) > 0.0)
+    assert _face_keys(m.bfaces) == _face_keys(boundary_faces(m.nodes, m.tets))
+    assert len(_face_keys(m.bfaces)) == len(m.bfaces)
+    tags = set(np.unique(m.btags).tolist())
+    assert {0, 1, 2} <= tags
+
+
+def test_cylinder_tags_and_table_statistics():
+    m = S.cylinder(1.0, 10.0, n_tets=100_000, seed=2)
+    z = m.nodes[m.bfaces][:, :, 2]
+    assert np.all(z[m.btags == 1] == 0.0) and np.all(z[m.btags == 2] == 10.0)
+    wall = np.unique(m.bfaces[m.btags == 0])
+    assert np.abs(np.hypot(m.nodes[wall, 0], m.nodes[wall, 1]) - 1.0).max() < 1e-12
+    st = S.mesh_stats(m)
+    assert 5.4 <= st["tets_per_vertex"] <= 6.3
+    assert st["q_max"] < 17.0
+    assert abs(m.n_tets - 100_000) <= 5_000
+
+
+def test_stenosis_wall_follows_the_radial_map():
+    m = S.stenosis(1.0, 10.0, n_tets=50_000, seed=3, z_center=3.0, half_length=1.0, severity=0.25)
+    wall = np.unique(m.bfaces[m.btags == 0])
+    x = m.nodes[wall]
+    r, z = np.hypot(x[:, 0], x[:, 1]), x[:, 2]
+    rs = np.where(np.abs(z - 3.0) <= 1.0, 1.0 - 0.25 * (1.0 + np.cos(np.pi * (z - 3.0))), 1.0)
+    assert np.abs(r - rs).max() < 1e-12
+    assert r.min() == pytest.approx(0.5, abs=0.02)        # the throat keeps half the radius: 75 % of the area gone
+
+
+def test_bifurcation_has_an_inlet_and_two_outlets():
+    m = S.bifurcation(n_tets=30_000, seed=1001)
+    assert set(np.unique(m.btags).tolist()) == {0, 1, 2, 3}
+    for tag in (1, 2, 3):
+        assert np.count_nonzero(m.btags == tag) > 10
+
+
+def test_batch_union_offsets_members():
+    a = S.cylinder(1.0, 10.0, n_tets=20000, seed=2)
+    b = S.bifurcation(n_tets=20_000, seed=1001)
+    u = S.batch([a, b])
+    assert u.n_nodes == a.n_nodes + b.n_nodes and u.n_tets == a.n_tets + b.n_tets
+    assert np.array_equal(u.nodes[:a.n_nodes], a.nodes) and np.array_equal(u.tets[a.n_tets:], b.tets + a.n_nodes)
+    assert set(np.unique(u.btags).tolist()) == set(np.unique(a.btags).tolist()) | {10 + t for t in np.unique(b.btags)}
