@@ -157,7 +157,8 @@ def test_colouring_balanced_to_assembly_waves(L):
     """At 1M tets the colours span several waves of the assembly kernel (GB300: 152 SMs x 3 CTAs x
     32 elements = 14,592 elements, the value used when no device answers).  The colours are
     rebalanced so that the waves launched, sum_c ceil(|c| / W), come within two of the work,
-    ceil(T / W), and the colouring stays valid."""
+    ceil(T / W), and the colouring stays valid.  The chunk colours of the chunked assembly come
+    within two waves of 456 chunks (one 32-element chunk per CTA) of theirs."""
     m = cylinder(1.0, 10.0, n_tets=1_000_000, seed=2)
     mesh = L.Mesh.from_synthetic(m)
     col = mesh.colors()
@@ -168,6 +169,12 @@ def test_colouring_balanced_to_assembly_waves(L):
     assert waves <= -(-T // W) + 2, (waves, sizes.tolist())
     key = np.unique(np.stack([np.repeat(col, 4), m.tets.ravel()], 1), axis=0)
     assert key.shape[0] == 4 * T       # no node carries two elements of one colour
+    # the chunk colours of the chunked assembly, balanced to waves of 456 chunks (152 x 3 CTAs)
+    ch = mesh.chunks()
+    csz = np.diff(ch["chunk_color_off"])
+    nch = int(csz.sum())
+    assert csz.min() > 0 and nch == ch["chunk_elem_off"].size - 1
+    assert int(np.ceil(csz / 456).sum()) <= -(-nch // 456) + 2, csz.tolist()
 
 
 @pytest.mark.parametrize("bc", [dict(tag=0, kind="noslip", beta=1.0), dict(tag=2, kind="neumann", beta=-0.5),
