@@ -484,7 +484,11 @@ typedef void *(*lfx_alloc_fn)(size_t bytes, void *ctx);
 typedef void (*lfx_free_fn)(void *ptr, void *ctx);
 /* Route every later device allocation through alloc/free (NULL, NULL restores cudaMalloc).  alloc
  * returns device memory aligned to at least 16 bytes (a pointer that is not is handed back to free
- * and the allocation fails with LFX_ERR_OOM), or NULL on failure. */
+ * and the allocation fails with LFX_ERR_OOM), or NULL on failure.  Each allocation is released
+ * through the free function (and ctx) that was current when it was made, so the hook may change
+ * while handles are alive, provided the earlier free function stays callable until they are
+ * destroyed.  The hook is process-wide and not synchronised: set it while no other call of the
+ * library is running.  Giving one function without the other is LFX_ERR_INVALID_ARG. */
 lfx_status lfx_set_allocator(lfx_alloc_fn alloc, lfx_free_fn free_fn, void *ctx);
 /* Device bytes held by a state together with its problem and mesh (for admission control). */
 lfx_status lfx_state_device_bytes(const lfx_state *state, int64_t *bytes);
