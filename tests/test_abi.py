@@ -30,6 +30,17 @@ def _declared():
     return sorted(n for n in names if not n.endswith("_fn"))
 
 
+def test_no_fallback_without_the_library(L, monkeypatch, tmp_path):
+    """Without liblfx.so the binding raises instead of computing anything another way."""
+    monkeypatch.setattr(L, "_lib", None)
+    monkeypatch.setattr(L, "LIB_PATH", str(tmp_path / "liblfx.so"))
+    m = cube_kuhn(2)
+    with pytest.raises(ImportError):
+        L.Mesh(m.nodes, m.tets, m.bfaces, m.btags)
+    with pytest.raises(ImportError):
+        L.default_options()
+
+
 def test_every_declared_symbol_is_exported(L):
     lib = L.library()
     missing = [n for n in _declared() if not hasattr(lib, n)]
