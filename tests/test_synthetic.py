@@ -13,6 +13,8 @@ design notes state (host only, no GPU).
   table's two tetrahedral meshes, and the largest edge ratio stays below the table's largest.
   The count is within 5 % of the requested one.
 * Batched unions keep every member's nodes, and offset member i's tags by 10 i.
+* The Beltrami flow of Appendix A, which gives the Beltrami histories, boundary data and error
+  norms, is an exact Navier-Stokes solution for any rho and mu (checked by finite differences).
 """
 import os
 
@@ -102,3 +104,33 @@ def test_batch_union_offsets_members():
     assert u.n_nodes == a.n_nodes + b.n_nodes and u.n_tets == a.n_tets + b.n_tets
     assert np.array_equal(u.nodes[:a.n_nodes], a.nodes) and np.array_equal(u.tets[a.n_tets:], b.tets + a.n_nodes)
     assert set(np.unique(u.btags).tolist()) == set(np.unique(a.btags).tolist()) | {10 + t for t in np.unique(b.btags)}
+
+
+@pytest.mark.parametrize("rho,mu", [(1.0, 1.0), (1.06, 0.035)])
+def test_beltrami_flow_solves_navier_stokes(rho, mu):
+    """The closed form of Appendix A used for the Beltrami data and errors: by central differences
+    at random points, u is divergence-free, beltrami_grad_u is its gradient, and
+    rho (du/dt + (u . grad) u) - mu lap u + grad p = 0 with no forcing.  A wrong sign, factor or
+    decay rate in u or p leaves a residual of the size of the terms."""
+    X = np.random.default_rng(0).uniform(-1.0, 1.0, (50, 3))
+    t, h, H = 0.3, 1e-5, 1e-3
+
+    def U(Y, s):
+        return S.beltrami_u(Y, s, rho, mu)
+
+    def P(Y, s):
+        return S.beltrami_p(Y, s, rho, mu)
+
+    G, gp, lap = np.zeros((50, 3, 3)), np.zeros((50, 3)), np.zeros((50, 3))
+    for j in range(3):
+        e, E = np.eye(3)[j] * h, np.eye(3)[j] * H
+        G[:, :, j] = (U(X + e, t) - U(X - e, t)) / (2 * h)
+        gp[:, j] = (P(X + e, t) - P(X - e, t)) / (2 * h)
+        lap += (U(X + E, t) - 2 * U(X, t) + U(X - E, t)) / H ** 2
+    dudt = (U(X, t + h) - U(X, t - h)) / (2 * h)
+    adv = np.einsum("nij,nj->ni", G, U(X, t))
+    terms = [rho * dudt, rho * adv, mu * lap, gp]
+    scale = sum(np.abs(v).max() for v in terms)
+    assert np.abs(np.trace(G, axis1=1, axis2=2)).max() <= 1e-9 * np.abs(G).max()
+    assert np.abs(G - S.beltrami_grad_u(X, t, rho, mu)).max() <= 1e-8 * np.abs(G).max()
+    assert np.abs(terms[0] + terms[1] - terms[2] + terms[3]).max() <= 1e-6 * scale
