@@ -14,7 +14,8 @@ design notes state (host only, no GPU).
   The count is within 5 % of the requested one.
 * Batched unions keep every member's nodes, and offset member i's tags by 10 i.
 * The Beltrami flow of Appendix A, which gives the Beltrami histories, boundary data and error
-  norms, is an exact Navier-Stokes solution for any rho and mu (checked by finite differences).
+  norms, is an exact Navier-Stokes solution for any rho and mu (checked by finite differences);
+  so is the steady Poiseuille pipe flow, with the flow rate its peak velocity implies.
 """
 import os
 
@@ -134,3 +135,30 @@ def test_beltrami_flow_solves_navier_stokes(rho, mu):
     assert np.abs(np.trace(G, axis1=1, axis2=2)).max() <= 1e-9 * np.abs(G).max()
     assert np.abs(G - S.beltrami_grad_u(X, t, rho, mu)).max() <= 1e-8 * np.abs(G).max()
     assert np.abs(terms[0] + terms[1] - terms[2] + terms[3]).max() <= 1e-6 * scale
+
+
+def test_poiseuille_flow_solves_navier_stokes():
+    """The steady pipe flow: divergence-free, no advection ((u . grad) u = 0 for an axial field that
+    varies across the pipe only), -mu lap u + grad p = 0 inside the pipe, p = 0 at the outlet, and
+    flow rate pi R^2 U / 2 (the unit-flow-rate parabolic profile scaled by it)."""
+    R, Lp, U, mu = 1.0, 10.0, 20.0, 0.035
+    rng = np.random.default_rng(1)
+    r, th = 0.9 * R * np.sqrt(rng.uniform(size=40)), rng.uniform(0, 2 * np.pi, 40)
+    X = np.stack([r * np.cos(th), r * np.sin(th), rng.uniform(0.5, Lp - 0.5, 40)], 1)
+    h, H = 1e-6, 1e-3
+    G, gp, lap = np.zeros((40, 3, 3)), np.zeros((40, 3)), np.zeros((40, 3))
+    for j in range(3):
+        e, E = np.eye(3)[j] * h, np.eye(3)[j] * H
+        G[:, :, j] = (S.poiseuille_u(X + e, R, U) - S.poiseuille_u(X - e, R, U)) / (2 * h)
+        gp[:, j] = (S.poiseuille_p(X + e, R, Lp, U, mu) - S.poiseuille_p(X - e, R, Lp, U, mu)) / (2 * h)
+        lap += (S.poiseuille_u(X + E, R, U) - 2 * S.poiseuille_u(X, R, U) + S.poiseuille_u(X - E, R, U)) / H ** 2
+    u = S.poiseuille_u(X, R, U)
+    assert np.abs(np.trace(G, axis1=1, axis2=2)).max() <= 1e-8 * U
+    assert np.abs(np.einsum("nij,nj->ni", G, u)).max() <= 1e-8 * U * U
+    assert np.abs(-mu * lap + gp).max() <= 1e-6 * np.abs(gp).max()
+    assert np.abs(S.poiseuille_p(np.array([[0.3, 0.2, Lp]]), R, Lp, U, mu)).max() == 0.0
+    # flow rate through a cross-section (polar quadrature, exact for the quadratic profile)
+    rq, wq = np.polynomial.legendre.leggauss(4)
+    rr = 0.5 * R * (rq + 1.0)
+    q = np.sum(0.5 * R * wq * 2 * np.pi * rr * S.poiseuille_u(np.stack([rr, 0 * rr, 0 * rr + 1.0], 1), R, U)[:, 2])
+    assert q == pytest.approx(np.pi * R ** 2 * U / 2.0, rel=1e-12)
