@@ -162,3 +162,30 @@ def test_poiseuille_flow_solves_navier_stokes():
     rr = 0.5 * R * (rq + 1.0)
     q = np.sum(0.5 * R * wq * 2 * np.pi * rr * S.poiseuille_u(np.stack([rr, 0 * rr, 0 * rr + 1.0], 1), R, U)[:, 2])
     assert q == pytest.approx(np.pi * R ** 2 * U / 2.0, rel=1e-12)
+
+
+def test_zero_net_flux_correction_of_all_dirichlet_data():
+    """Beltrami data on the whole boundary of the Kuhn cube: after the correction the discrete net
+    flux of the piecewise-linear data (each face's area vector times the mean of its three nodal
+    values) is zero.  The correction is small, because the exact field is divergence-free and the
+    flux of the P1 interpolant only carries its interpolation error."""
+    m = S.cube_kuhn(6)
+    bd = np.unique(m.bfaces)
+    g = S.beltrami_u(m.nodes, 0.01)
+
+    def flux(values):
+        full = np.zeros_like(m.nodes)
+        full[bd] = values
+        x = m.nodes[m.bfaces]
+        area_vec = 0.5 * np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0])
+        # outward: the cube's centre lies on the inner side of every face
+        inward = np.einsum("ij,ij->i", area_vec, x.mean(axis=1) - 0.5) < 0
+        area_vec[inward] *= -1
+        return np.sum(area_vec * full[m.bfaces].mean(axis=1))
+
+    before = flux(g[bd])
+    fixed = S.zero_net_flux(m.nodes, m.bfaces, bd, g[bd])
+    scale = np.sum(np.abs(g[bd])) / bd.size
+    assert abs(before) > 1e-8 * scale                    # the P1 data alone are not flux-free
+    assert abs(flux(fixed)) <= 1e-13 * scale
+    assert np.abs(fixed - g[bd]).max() <= 1e-2 * np.abs(g[bd]).max()
