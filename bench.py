@@ -404,7 +404,7 @@ def run_gpu(args):
 
 def run_serving(args):
     """Serving workload (continuous batching): Poisson arrivals (mean args.rate req/s) of
-    simulations on cylinder / stenosis geometries drawn from a pre-generated pool (sizes
+    simulations on cube / cylinder / stenosis geometries drawn from a pre-generated pool (sizes
     log-uniform in [args.serve_min, args.serve_max] tets), each asking for args.req_steps BDF2
     steps, admitted by a device-memory budget into the native request loop.  Reports p50/p99
     per-step latency and aggregate steps/s, beside the same requests run back to back on one
