@@ -330,7 +330,10 @@ typedef struct lfx_step_stats {
  * the RIIS delta and the right-hand side are FP64; the outer flexible GMRES works on FP64 vectors
  * with the double-float operator, the inner GMRES and aSIMPLE in FP32 (BF16 storage optional).
  * Returns LFX_ERR_NOT_CONVERGED after still advancing the state if a solve (or Newton) hit its
- * cap; stats may be NULL. */
+ * cap.  Every other error returns before the history is shifted, so the state keeps its time
+ * level and history: after LFX_ERR_TIMEOUT (a bounded device wait gave up) the step can be
+ * repeated as it is, after LFX_ERR_NONFINITE once lfx_state_set has replaced the history.
+ * stats may be NULL. */
 lfx_status lfx_step(lfx_state *state, lfx_step_stats *stats);
 
 /* Newton residual history of the last step (fully implicit formulation): res[k] = ||R(U_k)|| /

@@ -1877,6 +1877,20 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
   }
   if (s->mixed() && o.smoother_bf16) LFX_TRY(s->pcbf.queue_bulk_check(st));
   LFX_CUDA_TRY(cudaEventRecord(s->e2, st));
+  LFX_CUDA_TRY(cudaEventSynchronize(s->e2));
+  s->assembled = false;
+  // a bounded wait that gave up leaves the state as it was: the history is not shifted, and a
+  // repeated step assembles anew from it (the extrapolation is rewritten at every assembly)
+  if (s->asm_err_host && *s->asm_err_host) {
+    *s->asm_err_host = 0;
+    set_error("lfx_step: a grid-wide wait of the persistent assembly gave up; the state was not advanced");
+    return LFX_ERR_TIMEOUT;
+  }
+  if (s->pcbf.bulk_failed()) {
+    set_error("lfx_step: a wait for a staged tile of the velocity smoothing pass gave up; the state was not "
+              "advanced");
+    return LFX_ERR_TIMEOUT;
+  }
   // history shift: the solution becomes level 0 (and d^{n+1} the displacement's level 0)
   const int oldest = (s->head + s->sigma - 1) % s->sigma;
   std::swap(s->hist[oldest].p, s->xsol.p);
@@ -1889,17 +1903,6 @@ lfx_status lfx_step(lfx_state *s, lfx_step_stats *stats) {
     s->have_bnd = false;
   }
   s->t += pb->P.dt;
-  s->assembled = false;
-  LFX_CUDA_TRY(cudaEventSynchronize(s->e2));
-  if (s->asm_err_host && *s->asm_err_host) {
-    *s->asm_err_host = 0;
-    set_error("lfx_step: a grid-wide wait of the persistent assembly gave up");
-    return LFX_ERR_TIMEOUT;
-  }
-  if (s->pcbf.bulk_failed()) {
-    set_error("lfx_step: a wait for a staged tile of the velocity smoothing pass gave up");
-    return LFX_ERR_TIMEOUT;
-  }
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->iterations = its;
