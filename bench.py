@@ -865,11 +865,11 @@ def run_reference(args):
             "value": round(value, 5), "unit": "steps/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(sec * 1e3 * target / T, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "poiseuille_cylinder_1022138_tets (sampled)", "sample_tets": T},
+            "config": {"workload": f"poiseuille_cylinder_{target}_tets"},
             "cpu_baseline": {"value": round(value, 5), "unit": "steps/s", "cores": int(used), "kind": "oracle",
                              "cpu_model": cpu_model(), "extrapolated": True,
-                             "sample": f"{args.steps} oracle steps on a {T}-tet cylinder (element loop on {used} "
-                                       f"threads), scaled linearly to {target} tets"},
+                             "sample": f"{args.steps} oracle steps on a {T}-tet cylinder of the same recipe (element "
+                                       f"loop on {used} threads), scaled linearly to {target} tets", "sample_tets": T},
             "e2e": {"value": round(value, 5), "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -136,3 +136,27 @@ def test_clock_record_from_samples(bench, monkeypatch):
 
 def test_clock_record_without_nvidia_smi(bench):
     assert bench.Clocks().stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference`: the FP64 oracle on the host cores, on a bounded sample of the
+    headline workload, prints one JSON line with the main arm's metric, unit, direction and workload
+    name, its cpu_baseline record and an end-to-end entry with no host-device bytes."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                          "--cpu-sample-tets", "20000"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "steps/s" and d["higher_is_better"]
+    assert d["metric"].startswith("time steps/s at 1M P1 tets")
+    assert d["config"] == {"workload": "poiseuille_cylinder_1022138_tets"}
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "sample" in cb
+    assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
