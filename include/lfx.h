@@ -186,9 +186,9 @@ typedef struct lfx_options {
   double f[3];                  /* constant body force f; default 0                            */
   int32_t pin_pressure_node;    /* caller node whose pressure is fixed (all-Dirichlet flows);
                                    -1 = none.  Value per step: lfx_set_pressure_pin.           */
-  int32_t precision;            /* LFX_PREC_FP64 or LFX_PREC_MIXED                             */
+  int32_t precision;            /* LFX_PREC_FP64 (default) or LFX_PREC_MIXED                   */
   /* linear solve: GMRES(restart) right-preconditioned by aSIMPLE */
-  int32_t gmres_restart;        /* default 40                                                  */
+  int32_t gmres_restart;        /* default 64                                                  */
   int32_t gmres_max_iters;      /* total Arnoldi steps cap; default 1000                       */
   double gmres_rtol;            /* stop when ||b - A x|| <= rtol ||b||; default 1e-10         */
   int32_t reorthogonalize;      /* classical Gram-Schmidt once (0, default) or twice (1); in mixed
