@@ -6,7 +6,8 @@ The program checks:
 * a two-tetrahedron mesh: counts, the flipped element, the pattern (both nodes of the shared
   face couple to all five nodes, the two apexes to the face's three nodes and themselves);
 * argument errors returned as statuses, with a message;
-* the allocation-free preconditioner refusing an oversized matrix before touching any pointer.
+* the allocation-free preconditioner refusing an oversized matrix before touching any pointer;
+* the header's enumerations equal the binding's constants.
 """
 import os
 import shutil
@@ -70,6 +71,16 @@ int main(void) {
   CHECK(lfx_asimple_apply_noalloc(70000, (const int32_t *)dummy, (const int32_t *)dummy, (const int32_t *)dummy,
                                   (const int32_t *)dummy, dummy, dummy, dummy, NULL, NULL) == LFX_ERR_INVALID_ARG);
   lfx_mesh_destroy(mesh);
+  /* the enumerations, for the binding's constants */
+  printf("status %d %d %d %d %d %d %d %d %d\n", LFX_OK, LFX_ERR_INVALID_ARG, LFX_ERR_BAD_MESH, LFX_ERR_OOM,
+         LFX_ERR_NOT_CONVERGED, LFX_ERR_NONFINITE, LFX_ERR_CUDA, LFX_ERR_TIMEOUT, LFX_ERR_BUDGET);
+  printf("kind %d %d %d %d %d\n", LFX_BC_NOSLIP, LFX_BC_DIRICHLET, LFX_BC_NODAL, LFX_BC_NEUMANN, LFX_BC_RESISTANCE);
+  printf("profile %d %d %d\n", LFX_PROFILE_UNIFORM, LFX_PROFILE_PARABOLIC, LFX_PROFILE_WOMERSLEY);
+  printf("time %d %d %d %d\n", LFX_TIME_CONSTANT, LFX_TIME_PULSATILE, LFX_TIME_RAMP, LFX_TIME_FOURIER);
+  printf("prec %d %d\n", LFX_PREC_FP64, LFX_PREC_MIXED);
+  printf("asm %d %d %d %d\n", LFX_ASM_AUTO, LFX_ASM_COLORS, LFX_ASM_CHUNKS, LFX_ASM_PERSISTENT);
+  printf("smooth %d %d %d\n", LFX_SMOOTH_JACOBI, LFX_SMOOTH_CHEBYSHEV, LFX_SMOOTH_AMG);
+  printf("fourier %d\n", LFX_MAX_FOURIER);
   printf("OK\n");
   return 0;
 }
@@ -94,4 +105,18 @@ def test_plain_c_program_uses_the_boundary(lib, tmp_path):
     subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"), str(src),
                     "-o", str(exe), "-L", libdir, "-llfx", "-Wl,-rpath," + libdir], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
-    assert out.returncode == 0 and out.stdout.strip() == "OK", out.stdout + out.stderr
+    lines = out.stdout.strip().splitlines()
+    assert out.returncode == 0 and lines[-1] == "OK", out.stdout + out.stderr
+    got = {ln.split()[0]: [int(v) for v in ln.split()[1:]] for ln in lines[:-1]}
+    from paper_2304_12032_gb300 import lfx as L
+
+    assert got["status"] == [L.LFX_OK, L.LFX_ERR_INVALID_ARG, L.LFX_ERR_BAD_MESH, L.LFX_ERR_OOM,
+                             L.LFX_ERR_NOT_CONVERGED, L.LFX_ERR_NONFINITE, L.LFX_ERR_CUDA, L.LFX_ERR_TIMEOUT,
+                             L.LFX_ERR_BUDGET]
+    assert got["kind"] == [L.KIND[k] for k in ("noslip", "dirichlet", "nodal", "neumann", "resistance")]
+    assert got["profile"] == [L.PROFILE[k] for k in ("uniform", "parabolic", "womersley")]
+    assert got["time"] == [L.TIME[k] for k in ("constant", "pulsatile", "ramp", "fourier")]
+    assert got["prec"] == [L.PREC["fp64"], L.PREC["mixed"]]
+    assert got["asm"] == [L.ASM[k] for k in ("auto", "colors", "chunks", "persistent")]
+    assert got["smooth"] == [L.SMOOTH[k] for k in ("jacobi", "chebyshev", "amg")]
+    assert got["fourier"] == [L.MAX_FOURIER]
